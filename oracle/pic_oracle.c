@@ -1,0 +1,824 @@
+/*
+ * Plain FP64 CPU oracle of the manufactured-solution PIC + DSMC time step of
+ * Freno, McDoniel, Moore and Matula, "Code-Verification Techniques for
+ * Particle-in-Cell Simulations with Direct Simulation Monte Carlo Collisions".
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library. It shares no code, header,
+ * table or constant generator with the CUDA path, and it never calls it.
+ *
+ * Everything is written for a reader checking it against the paper: plain
+ * loops, array-of-structures layouts ([particle][component]), FP64
+ * throughout, no blocking, no fusion, no reordering beyond what the paper
+ * states. It must be compiled with -ffp-contract=off so that x86 and Arm
+ * builds give the same bits.
+ *
+ * Workload (the paper's Sec. 3 machinery applied to a simpler distribution):
+ *   periodic unit cube [0,1)^3, n^3 cells of size h = 1/n, node i at x = i h;
+ *   f_x(x,t) = N prod_d (1 + A sin(2 pi (x_d - c t)))                 (Eq. fx)
+ *   f_v(v,t) = prod_d Normal(v_d; mu_d, s^2), constant in time         (Eq. fv)
+ *   phi^M(x,t) = phibar e^{t/(2T)} prod_d sin(2 pi (x_d - s_d))        (Sec. 5.2)
+ *   hard-sphere cross section sigma(g) = sigma0, isotropic scattering  (Eq. chi_iso)
+ *
+ * Parity status of each function is given beside it; every function here is
+ * pinned by tests in tests/test_oracle_pins.py (closed forms, invariants,
+ * library special cases, quadrature, brute force).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+  int64_t n;            /* cells per axis                                 */
+  int64_t np;           /* computational particles N_p                   */
+  int64_t K;            /* N_avg, outcomes per collision call; 0 = off    */
+  int64_t cg_maxit;
+  uint64_t seed;
+  int64_t couple_qm_zero;  /* q/m = 0: field does not push particles      */
+  int64_t couple_q_zero;   /* q = 0: particles do not source the field    */
+  double dt, qm, q, eps0, nphys;
+  double sigma0, gmax;
+  double fx_amp, fx_speed;
+  double vmean[3];
+  double vsig;
+  double phi_amp, phi_T;
+  double phi_shift[3];
+  double cg_tol;
+} orc_cfg;
+
+/* ------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
+ * published multipliers, key bumped by the published Weyl constants between
+ * rounds. Pinned by the published known-answer vectors.
+ * ---------------------------------------------------------------------- */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; round++) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void philox4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                    uint64_t seed, uint32_t out[4]) {
+  uint32_t ctr[4] = {c0, c1, c2, c3};
+  uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+  orc_philox(ctr, key, out);
+}
+
+/* Uniforms used by the method's draws. Both are odd multiples of a power of
+ * two, hence exactly representable and strictly inside (0, 1).           */
+double orc_u52(uint32_t hi, uint32_t lo) {
+  uint64_t m = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12); /* 52 bits */
+  return (double)(2 * m + 1) * 0x1p-53;
+}
+double orc_u32(uint32_t w) { return (double)(2 * (uint64_t)w + 1) * 0x1p-33; }
+/* floor(U * c) with U = w / 2^32: Algorithm 1's "floor(rand * N) + 1", 0-based */
+uint32_t orc_index(uint32_t w, uint32_t c) {
+  return (uint32_t)(((uint64_t)w * (uint64_t)c) >> 32);
+}
+
+/* ------------------------------------------------------------------------
+ * Manufactured distribution, Sec. 3.1 / 3.2.
+ * ---------------------------------------------------------------------- */
+
+/* f_{x_d}(x,t) = 1 + A sin(2 pi (x - c t)), unit integral over [0,1).    */
+double orc_fxd(const orc_cfg* cf, double x, double t) {
+  return 1.0 + cf->fx_amp * sin(2.0 * ORC_PI * (x - cf->fx_speed * t));
+}
+
+/* F_{x_d}(x,t) = int_0^x f_{x_d}(x',t) dx' in closed form (Sec. 3.1).   */
+double orc_Fxd(const orc_cfg* cf, double x, double t) {
+  double A = cf->fx_amp, c = cf->fx_speed;
+  return x + A / (2.0 * ORC_PI) *
+                 (cos(2.0 * ORC_PI * (0.0 - c * t)) - cos(2.0 * ORC_PI * (x - c * t)));
+}
+
+/* x^M(t) solves F_x(x^M, t) = xi on [0,1] (Eq. mms_sol). F is increasing,
+ * so plain bisection to the last representable bracket.                  */
+double orc_xM(const orc_cfg* cf, double xi, double t) {
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (orc_Fxd(cf, mid, t) < xi) lo = mid; else hi = mid;
+  }
+  /* return the bracket end with the smaller residual */
+  double rl = fabs(orc_Fxd(cf, lo, t) - xi), rh = fabs(orc_Fxd(cf, hi, t) - xi);
+  return rl <= rh ? lo : hi;
+}
+
+/* xdot^M = -(1/f_x(x^M,t)) int_0^{x^M} d/dt f_x(x',t) dx' (Sec. 3.2). With
+ * d/dt f = -2 pi A c cos(2 pi (x - c t)), the integral is
+ * -A c [sin(2 pi (x^M - c t)) - sin(2 pi (0 - c t))].                      */
+double orc_xMdot(const orc_cfg* cf, double xM, double t) {
+  double A = cf->fx_amp, c = cf->fx_speed;
+  double integral = -A * c * (sin(2.0 * ORC_PI * (xM - c * t)) -
+                              sin(2.0 * ORC_PI * (0.0 - c * t)));
+  return -integral / orc_fxd(cf, xM, t);
+}
+
+/* Standard normal CDF Phi(z) = erfc(-z/sqrt 2)/2.                        */
+static double orc_Phi(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
+
+/* v^M solves F_v(v^M) = xi for the Gaussian f_v (Eq. mms_sol); f_v does not
+ * depend on t, so v^M is constant and vdot^M = 0. Bisection on Phi in the
+ * lower tail; for xi > 1/2 the symmetry Phi^{-1}(xi) = -Phi^{-1}(1 - xi)
+ * (1 - xi is exact there) keeps the upper tail well conditioned.          */
+static double orc_Phi_inv(double xi) {
+  if (xi > 0.5) return -orc_Phi_inv(1.0 - xi);
+  double lo = -40.0, hi = 0.0;
+  for (int it = 0; it < 400; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (orc_Phi(mid) < xi) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+double orc_vM(const orc_cfg* cf, int d, double xi) {
+  return cf->vmean[d] + cf->vsig * orc_Phi_inv(xi);
+}
+
+/* phi^M and its derivatives (Sec. 5.2 form on the unit cube).            */
+double orc_phiM(const orc_cfg* cf, const double x[3], double t) {
+  double val = cf->phi_amp * exp(t / (2.0 * cf->phi_T));
+  for (int d = 0; d < 3; d++) val *= sin(2.0 * ORC_PI * (x[d] - cf->phi_shift[d]));
+  return val;
+}
+/* E^M = -grad phi^M (Eq. potential).                                     */
+void orc_EM(const orc_cfg* cf, const double x[3], double t, double E[3]) {
+  double amp = cf->phi_amp * exp(t / (2.0 * cf->phi_T));
+  double s[3], c[3];
+  for (int d = 0; d < 3; d++) {
+    s[d] = sin(2.0 * ORC_PI * (x[d] - cf->phi_shift[d]));
+    c[d] = cos(2.0 * ORC_PI * (x[d] - cf->phi_shift[d]));
+  }
+  E[0] = -amp * 2.0 * ORC_PI * c[0] * s[1] * s[2];
+  E[1] = -amp * 2.0 * ORC_PI * s[0] * c[1] * s[2];
+  E[2] = -amp * 2.0 * ORC_PI * s[0] * s[1] * c[2];
+}
+/* Laplacian of phi^M: each factor contributes -(2 pi)^2.                 */
+double orc_lap_phiM(const orc_cfg* cf, const double x[3], double t) {
+  return -3.0 * (2.0 * ORC_PI) * (2.0 * ORC_PI) * orc_phiM(cf, x, t);
+}
+/* rho^M = q f_x (Sec. 3.4).                                              */
+double orc_rhoM(const orc_cfg* cf, double q, const double x[3], double t) {
+  double f = cf->nphys;
+  for (int d = 0; d < 3; d++) f *= orc_fxd(cf, x[d], t);
+  return q * f;
+}
+
+/* ------------------------------------------------------------------------
+ * Expected velocity change for hard spheres, Eq. vel_change_1c with
+ * sigma(g) = sigma0 and a Gaussian f_v. The paper's closed form needs odd
+ * powers of g; for sigma = sigma0 the integral is instead
+ *   E_{v_q ~ N(mu, s^2 I)} [ |v_q - v_p| (v_q - v_p) ] = s R(a) m,
+ *   m = mu - v_p,  a = |m| / s,
+ *   R(a) = sqrt(2/pi) (1 + 1/a^2) e^{-a^2/2} + (a + 2/a - 1/a^3) erf(a/sqrt 2)
+ * (Stein's lemma on E|X| of a noncentral 3D normal). For a < 0.1 the same
+ * function is summed as its even power series R = sqrt(2/pi) sum_j c_j a^{2j}
+ * to avoid the cancellation of the 1/a terms.
+ * ---------------------------------------------------------------------- */
+double orc_hs_R(double a) {
+  if (a < 0.1) {
+    /* c_j = d_j + d_{j+1} + e_{j-1} + 2 e_j - e_{j+1} with the Taylor
+     * coefficients d_k of e^{-a^2/2} and e_k of sqrt(pi/2) erf(a/sqrt 2).  */
+    double d[12], e[12];
+    double fact = 1.0, pow2 = 1.0;
+    for (int k = 0; k < 12; k++) {
+      if (k > 0) { fact *= (double)k; pow2 *= 2.0; }
+      double sgn = (k % 2 == 0) ? 1.0 : -1.0;
+      d[k] = sgn / (pow2 * fact);
+      e[k] = sgn / (pow2 * fact * (double)(2 * k + 1));
+    }
+    double sum = 0.0, a2 = a * a, ap = 1.0;
+    for (int j = 0; j < 10; j++) {
+      double cj = d[j] + d[j + 1] + (j > 0 ? e[j - 1] : 0.0) + 2.0 * e[j] - e[j + 1];
+      sum += cj * ap;
+      ap *= a2;
+    }
+    return sqrt(2.0 / ORC_PI) * sum;
+  }
+  double a2 = a * a;
+  return sqrt(2.0 / ORC_PI) * (1.0 + 1.0 / a2) * exp(-0.5 * a2) +
+         (a + 2.0 / a - 1.0 / (a2 * a)) * erf(a / sqrt(2.0));
+}
+
+/* <Delta v_p^M>_coll = w dt (c - 1) sigma0 / (2 dV) * E[|v_q - v_p|(v_q - v_p)]
+ * (Eq. vel_change_1c), c = particles in p's cell.                          */
+void orc_hs_source(const orc_cfg* cf, const double vp[3], int64_t ccell, double out[3]) {
+  double h = 1.0 / (double)cf->n;
+  double dV = h * h * h;
+  double w = cf->nphys / (double)cf->np;
+  double pref = w * cf->dt * (double)(ccell - 1) * cf->sigma0 / (2.0 * dV);
+  double m[3], a2 = 0.0;
+  for (int d = 0; d < 3; d++) {
+    m[d] = cf->vmean[d] - vp[d];
+    a2 += m[d] * m[d];
+  }
+  double a = sqrt(a2) / cf->vsig;
+  double R = orc_hs_R(a);
+  for (int d = 0; d < 3; d++) out[d] = pref * cf->vsig * R * m[d];
+}
+
+/* ------------------------------------------------------------------------
+ * State
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  orc_cfg c;
+  double t0;
+  int64_t step;
+  double* xi;   /* [np][6]: xi_x, xi_y, xi_z, xi_u, xi_v, xi_w */
+  double* x;    /* [np][3] */
+  double* v;    /* [np][3] */
+  double* rho;  /* [n^3]   */
+  double* phi;  /* [n^3]   */
+  double* E;    /* [n^3][3] */
+  int32_t* cell;  /* [np]  */
+  int32_t* count; /* [n^3] */
+  int32_t* start; /* [n^3 + 1] */
+  int32_t* perm;  /* [np]: pids sorted by (cell, pid) */
+  int64_t n_cand, n_coll, n_gmax, n_tie;
+  int64_t cg_iters;
+  double cg_res;
+} orc_state;
+
+static int64_t ncell(const orc_cfg* c) { return c->n * c->n * c->n; }
+
+/* Sampling of xi (Sec. 3.2): per particle, three Philox blocks with counter
+ * (pid_lo, pid_hi, 0, 0xFFFFFF00 | j), each giving two 52-bit uniforms.    */
+void orc_sample_xi(const orc_cfg* cf, int64_t pid, double xi[6]) {
+  for (int j = 0; j < 3; j++) {
+    uint32_t o[4];
+    philox4((uint32_t)(pid & 0xFFFFFFFF), (uint32_t)((uint64_t)pid >> 32), 0u,
+            0xFFFFFF00u | (uint32_t)j, cf->seed, o);
+    xi[2 * j + 0] = orc_u52(o[0], o[1]);
+    xi[2 * j + 1] = orc_u52(o[2], o[3]);
+  }
+}
+
+orc_state* orc_create(const orc_cfg* cf) {
+  orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
+  if (!s) return NULL;
+  s->c = *cf;
+  int64_t np = cf->np, nc = ncell(cf);
+  s->xi = (double*)calloc((size_t)(6 * np + 1), sizeof(double));
+  s->x = (double*)calloc((size_t)(3 * np + 1), sizeof(double));
+  s->v = (double*)calloc((size_t)(3 * np + 1), sizeof(double));
+  s->rho = (double*)calloc((size_t)nc, sizeof(double));
+  s->phi = (double*)calloc((size_t)nc, sizeof(double));
+  s->E = (double*)calloc((size_t)(3 * nc), sizeof(double));
+  s->cell = (int32_t*)calloc((size_t)(np + 1), sizeof(int32_t));
+  s->count = (int32_t*)calloc((size_t)nc, sizeof(int32_t));
+  s->start = (int32_t*)calloc((size_t)(nc + 1), sizeof(int32_t));
+  s->perm = (int32_t*)calloc((size_t)(np + 1), sizeof(int32_t));
+  if (!s->xi || !s->x || !s->v || !s->rho || !s->phi || !s->E || !s->cell ||
+      !s->count || !s->start || !s->perm)
+    return NULL;
+  for (int64_t p = 0; p < np; p++) orc_sample_xi(cf, p, s->xi + 6 * p);
+  return s;
+}
+
+void orc_destroy(orc_state* s) {
+  if (!s) return;
+  free(s->xi); free(s->x); free(s->v); free(s->rho); free(s->phi); free(s->E);
+  free(s->cell); free(s->count); free(s->start); free(s->perm);
+  free(s);
+}
+
+static double time_at(const orc_state* s, double steps) {
+  return s->t0 + steps * s->c.dt;
+}
+
+/* ------------------------------------------------------------------------
+ * Cells and the (cell, pid) order. Cell i_d = floor(x_d n), clamped to
+ * [0, n-1]; linear index x-fastest. A stable counting sort of the pids in
+ * increasing order gives ascending pid inside each cell.
+ * ---------------------------------------------------------------------- */
+int32_t orc_cell_of(const orc_cfg* cf, const double x[3]) {
+  int64_t n = cf->n, i[3];
+  for (int d = 0; d < 3; d++) {
+    double f = floor(x[d] * (double)n);
+    int64_t k = (int64_t)f;
+    if (k < 0) k = 0;
+    if (k > n - 1) k = n - 1;
+    i[d] = k;
+  }
+  return (int32_t)(i[0] + n * (i[1] + n * i[2]));
+}
+
+void orc_sort(orc_state* s) {
+  const orc_cfg* cf = &s->c;
+  int64_t np = cf->np, nc = ncell(cf);
+  for (int64_t k = 0; k < nc; k++) s->count[k] = 0;
+  for (int64_t p = 0; p < np; p++) {
+    s->cell[p] = orc_cell_of(cf, s->x + 3 * p);
+    s->count[s->cell[p]]++;
+  }
+  s->start[0] = 0;
+  for (int64_t k = 0; k < nc; k++) s->start[k + 1] = s->start[k] + s->count[k];
+  int32_t* fill = (int32_t*)calloc((size_t)nc, sizeof(int32_t));
+  for (int64_t p = 0; p < np; p++) {
+    int32_t k = s->cell[p];
+    s->perm[s->start[k] + fill[k]] = (int32_t)p;
+    fill[k]++;
+  }
+  free(fill);
+}
+
+/* ------------------------------------------------------------------------
+ * Cloud-in-cell deposit (Sec. 2): rho_node = (q w / h^3) sum_p S(x_p - X),
+ * S the product of 1D hats 1 - |x - X|/h over the 8 nodes around x_p.
+ * ---------------------------------------------------------------------- */
+static int64_t node_index(int64_t n, int64_t i, int64_t j, int64_t k) {
+  i = ((i % n) + n) % n;
+  j = ((j % n) + n) % n;
+  k = ((k % n) + n) % n;
+  return i + n * (j + n * k);
+}
+
+/* hat weights of the two nodes below/above x along one axis              */
+static void hat_weights(double xd, int64_t n, int64_t* i0, double w[2]) {
+  double u = xd * (double)n; /* position in units of h */
+  int64_t i = (int64_t)floor(u);
+  if (i < 0) i = 0;
+  if (i > n - 1) i = n - 1;
+  *i0 = i;
+  w[0] = 1.0 - fabs(u - (double)i);
+  w[1] = 1.0 - fabs(u - (double)(i + 1));
+}
+
+void orc_deposit(orc_state* s) {
+  const orc_cfg* cf = &s->c;
+  int64_t n = cf->n, nc = ncell(cf);
+  double h = 1.0 / (double)n;
+  double q = cf->couple_q_zero ? 0.0 : cf->q;
+  double w = cf->nphys / (double)cf->np;
+  double scale = q * w / (h * h * h);
+  for (int64_t k = 0; k < nc; k++) s->rho[k] = 0.0;
+  for (int64_t p = 0; p < cf->np; p++) {
+    int64_t i0[3];
+    double wt[3][2];
+    for (int d = 0; d < 3; d++) hat_weights(s->x[3 * p + d], n, &i0[d], wt[d]);
+    for (int c = 0; c < 2; c++)
+      for (int b = 0; b < 2; b++)
+        for (int a = 0; a < 2; a++)
+          s->rho[node_index(n, i0[0] + a, i0[1] + b, i0[2] + c)] +=
+              scale * wt[0][a] * wt[1][b] * wt[2][c];
+  }
+}
+
+/* Field gather with the same hats (Sec. 2, "interpolated onto the particles"). */
+void orc_gather(const orc_cfg* cf, const double* E, const double x[3], double Ep[3]) {
+  int64_t n = cf->n, i0[3];
+  double wt[3][2];
+  for (int d = 0; d < 3; d++) hat_weights(x[d], n, &i0[d], wt[d]);
+  Ep[0] = Ep[1] = Ep[2] = 0.0;
+  for (int c = 0; c < 2; c++)
+    for (int b = 0; b < 2; b++)
+      for (int a = 0; a < 2; a++) {
+        int64_t node = node_index(n, i0[0] + a, i0[1] + b, i0[2] + c);
+        double ww = wt[0][a] * wt[1][b] * wt[2][c];
+        for (int d = 0; d < 3; d++) Ep[d] += ww * E[3 * node + d];
+      }
+}
+
+/* ------------------------------------------------------------------------
+ * Poisson with the manufactured source (Eq. poisson_mms), periodic:
+ *   -Lap_h phi = b,  b = rho/eps0 - Lap phi^M - rho^M/eps0, minus its mean,
+ * Lap_h the 7-point Laplacian at nodes; zero-mean phi (Sec. 2).
+ * ---------------------------------------------------------------------- */
+void orc_rhs(const orc_state* s, double t, double* b) {
+  const orc_cfg* cf = &s->c;
+  int64_t n = cf->n, nc = ncell(cf);
+  double h = 1.0 / (double)n;
+  double q = cf->couple_q_zero ? 0.0 : cf->q;
+  double mean = 0.0;
+  for (int64_t k = 0; k < n; k++)
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t i = 0; i < n; i++) {
+        int64_t id = i + n * (j + n * k);
+        double X[3] = {(double)i * h, (double)j * h, (double)k * h};
+        b[id] = s->rho[id] / cf->eps0 - orc_lap_phiM(cf, X, t) -
+                orc_rhoM(cf, q, X, t) / cf->eps0;
+        mean += b[id];
+      }
+  mean /= (double)nc;
+  for (int64_t id = 0; id < nc; id++) b[id] -= mean;
+}
+
+/* y = -Lap_h x with periodic wrap                                        */
+void orc_neg_lap(int64_t n, const double* xv, double* y) {
+  double inv_h2 = (double)n * (double)n;
+  for (int64_t k = 0; k < n; k++)
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t i = 0; i < n; i++) {
+        double sum = xv[node_index(n, i + 1, j, k)] + xv[node_index(n, i - 1, j, k)] +
+                     xv[node_index(n, i, j + 1, k)] + xv[node_index(n, i, j - 1, k)] +
+                     xv[node_index(n, i, j, k + 1)] + xv[node_index(n, i, j, k - 1)];
+        y[i + n * (j + n * k)] = (6.0 * xv[i + n * (j + n * k)] - sum) * inv_h2;
+      }
+}
+
+static double dot(int64_t m, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < m; i++) s += a[i] * b[i];
+  return s;
+}
+
+/* Textbook conjugate gradients (Hestenes-Stiefel) from the warm start in
+ * phi, stopping at ||r|| <= tol ||b||; the result is projected to zero mean.
+ * Returns the iteration count, or -1 if maxit was reached.               */
+int64_t orc_cg(int64_t n, const double* b, double* phi, double tol, int64_t maxit,
+               double* res_out) {
+  int64_t m = n * n * n;
+  double* r = (double*)malloc((size_t)m * sizeof(double));
+  double* p = (double*)malloc((size_t)m * sizeof(double));
+  double* Ap = (double*)malloc((size_t)m * sizeof(double));
+  orc_neg_lap(n, phi, Ap);
+  for (int64_t i = 0; i < m; i++) r[i] = b[i] - Ap[i];
+  for (int64_t i = 0; i < m; i++) p[i] = r[i];
+  double bb = dot(m, b, b), rr = dot(m, r, r);
+  int64_t it = 0, status = 0;
+  if (bb == 0.0) {
+    for (int64_t i = 0; i < m; i++) phi[i] = 0.0;
+    rr = 0.0;
+  } else {
+    while (!(sqrt(rr) <= tol * sqrt(bb))) {
+      if (it >= maxit) { status = -1; break; }
+      orc_neg_lap(n, p, Ap);
+      double alpha = rr / dot(m, p, Ap);
+      for (int64_t i = 0; i < m; i++) phi[i] += alpha * p[i];
+      for (int64_t i = 0; i < m; i++) r[i] -= alpha * Ap[i];
+      double rr_new = dot(m, r, r);
+      it++;
+      if (sqrt(rr_new) <= tol * sqrt(bb)) { rr = rr_new; break; }
+      double beta = rr_new / rr;
+      for (int64_t i = 0; i < m; i++) p[i] = r[i] + beta * p[i];
+      rr = rr_new;
+    }
+  }
+  double mean = 0.0;
+  for (int64_t i = 0; i < m; i++) mean += phi[i];
+  mean /= (double)m;
+  for (int64_t i = 0; i < m; i++) phi[i] -= mean;
+  if (res_out) *res_out = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
+  free(r); free(p); free(Ap);
+  return status < 0 ? -1 : it;
+}
+
+/* E = -grad phi by second-order central differences at nodes (Sec. 4.1). */
+void orc_efield(int64_t n, const double* phi, double* E) {
+  double h = 1.0 / (double)n;
+  for (int64_t k = 0; k < n; k++)
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t i = 0; i < n; i++) {
+        int64_t id = i + n * (j + n * k);
+        E[3 * id + 0] = -(phi[node_index(n, i + 1, j, k)] - phi[node_index(n, i - 1, j, k)]) / (2.0 * h);
+        E[3 * id + 1] = -(phi[node_index(n, i, j + 1, k)] - phi[node_index(n, i, j - 1, k)]) / (2.0 * h);
+        E[3 * id + 2] = -(phi[node_index(n, i, j, k + 1)] - phi[node_index(n, i, j, k - 1)]) / (2.0 * h);
+      }
+}
+
+int64_t orc_field(orc_state* s, double t) {
+  const orc_cfg* cf = &s->c;
+  int64_t nc = ncell(cf);
+  double* b = (double*)malloc((size_t)nc * sizeof(double));
+  orc_deposit(s);
+  orc_rhs(s, t, b);
+  double res = 0.0;
+  int64_t it = orc_cg(cf->n, b, s->phi, cf->cg_tol, cf->cg_maxit, &res);
+  s->cg_iters = it;
+  s->cg_res = res;
+  orc_efield(cf->n, s->phi, s->E);
+  free(b);
+  return it;
+}
+
+/* ------------------------------------------------------------------------
+ * Algorithm 1 (no-time-counter, binary elastic, same species and weight),
+ * run K times from the same pre-collision velocities and averaged
+ * (Eq. avg_outcome). Draws for call counter c0 = 2 step + phase, cell k,
+ * outcome o:
+ *   N_pairs : Philox(c0, k, 0xFFFFFFFF, o<<8)      -> U52(w0, w1)
+ *   pair s  : Philox(c0, k, s, o<<8 | 0)  = (p, q, accept, epsilon)
+ *             Philox(c0, k, s, o<<8 | 1)  = (chi, q redraw, q redraw, q redraw)
+ *             Philox(c0, k, s, o<<8 | b), b >= 2: four more q redraws each
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int64_t n_cand, n_coll, n_gmax, n_tie;
+} orc_dsmc_stats;
+
+/* P_coll,max = (sigma g)_max w dt / dV (Algorithm 1; Eq. p_coll at g where
+ * sigma g peaks). For hard spheres (sigma g)_max = sigma0 g_max.          */
+double orc_pmax(const orc_cfg* cf) {
+  double h = 1.0 / (double)cf->n;
+  double dV = h * h * h;
+  double w = cf->nphys / (double)cf->np;
+  double sg_max = cf->sigma0 * cf->gmax;
+  return sg_max * w * cf->dt / dV;
+}
+
+static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint32_t o,
+                            int64_t c, double* vloc /* [c][3], updated in place */,
+                            orc_dsmc_stats* st) {
+  double sg_max = cf->sigma0 * cf->gmax;              /* (sigma g)_max, hard sphere */
+  double Pmax = orc_pmax(cf);
+  uint32_t u[4];
+  philox4(c0, cellk, 0xFFFFFFFFu, o << 8, cf->seed, u);
+  double npairs_real = ((double)(c * (c - 1)) * Pmax) * 0.5 + orc_u52(u[0], u[1]);
+  int64_t npairs = (int64_t)floor(npairs_real);       /* Algorithm 1, line 4 */
+  for (int64_t sl = 0; sl < npairs; sl++) {
+    uint32_t b0[4], b1[4];
+    philox4(c0, cellk, (uint32_t)sl, (o << 8) | 0u, cf->seed, b0);
+    philox4(c0, cellk, (uint32_t)sl, (o << 8) | 1u, cf->seed, b1);
+    uint32_t p = orc_index(b0[0], (uint32_t)c);
+    uint32_t q = orc_index(b0[1], (uint32_t)c);
+    /* redraw q while q == p: words b1[1..3], then blocks 2, 3, ... */
+    int widx = 1;
+    uint32_t blk[4] = {b1[0], b1[1], b1[2], b1[3]};
+    uint32_t bnum = 1;
+    while (q == p) {
+      if (widx == 4) {
+        bnum++;
+        if (bnum > 255) { q = (p + 1) % (uint32_t)c; break; }
+        philox4(c0, cellk, (uint32_t)sl, (o << 8) | bnum, cf->seed, blk);
+        widx = 0;
+      }
+      q = orc_index(blk[widx], (uint32_t)c);
+      widx++;
+    }
+    st->n_cand++;
+    double* vp = vloc + 3 * p;
+    double* vq = vloc + 3 * q;
+    double dx = vp[0] - vq[0], dy = vp[1] - vq[1], dz = vp[2] - vq[2];
+    double g = sqrt(dx * dx + dy * dy + dz * dz);
+    double ratio = (cf->sigma0 * g) / sg_max;         /* sigma(g) g / (sigma g)_max */
+    double U = orc_u32(b0[2]);
+    if (g > cf->gmax) st->n_gmax++;
+    if (fabs(U - ratio) < 1e-12) st->n_tie++;
+    if (U < ratio) {
+      double eps = 2.0 * ORC_PI * orc_u32(b0[3]);     /* epsilon = 2 pi U        */
+      double cchi = 1.0 - 2.0 * orc_u32(b1[0]);       /* chi = acos(1 - 2U)      */
+      double schi = sqrt(1.0 - cchi * cchi);
+      double n[3] = {cos(eps) * schi, sin(eps) * schi, cchi}; /* Eq. n (lab frame) */
+      double gp[3], vcm[3];
+      for (int d = 0; d < 3; d++) {
+        gp[d] = g * n[d];
+        vcm[d] = (vp[d] + vq[d]) / 2.0;
+      }
+      for (int d = 0; d < 3; d++) {
+        vp[d] = vcm[d] + gp[d] / 2.0;
+        vq[d] = vcm[d] - gp[d] / 2.0;
+      }
+      st->n_coll++;
+    }
+  }
+}
+
+/* <Delta v_p>_coll for every particle (pid-indexed dv[np][3]) from the
+ * cells in s->perm/start/count and the velocities v.                     */
+void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
+  const orc_cfg* cf = &s->c;
+  int64_t nc = ncell(cf);
+  orc_dsmc_stats st = {0, 0, 0, 0};
+  for (int64_t p = 0; p < 3 * cf->np; p++) dv[p] = 0.0;
+  if (cf->K <= 0) return;
+  double* v0 = NULL;
+  double* vloc = NULL;
+  double* acc = NULL;
+  int64_t cap = 0;
+  for (int64_t k = 0; k < nc; k++) {
+    int64_t c = s->count[k];
+    if (c < 2) continue;
+    if (c > cap) {
+      cap = c;
+      v0 = (double*)realloc(v0, (size_t)(3 * c) * sizeof(double));
+      vloc = (double*)realloc(vloc, (size_t)(3 * c) * sizeof(double));
+      acc = (double*)realloc(acc, (size_t)(3 * c) * sizeof(double));
+    }
+    for (int64_t j = 0; j < c; j++) {
+      int32_t pid = s->perm[s->start[k] + j];
+      for (int d = 0; d < 3; d++) {
+        v0[3 * j + d] = v[3 * pid + d];
+        acc[3 * j + d] = 0.0;
+      }
+    }
+    for (int64_t o = 0; o < cf->K; o++) {
+      memcpy(vloc, v0, (size_t)(3 * c) * sizeof(double));
+      ntc_one_outcome(cf, c0, (uint32_t)k, (uint32_t)o, c, vloc, &st);
+      for (int64_t j = 0; j < 3 * c; j++) acc[j] += vloc[j] - v0[j];
+    }
+    for (int64_t j = 0; j < c; j++) {
+      int32_t pid = s->perm[s->start[k] + j];
+      for (int d = 0; d < 3; d++) dv[3 * pid + d] = acc[3 * j + d] / (double)cf->K;
+    }
+  }
+  free(v0); free(vloc); free(acc);
+  s->n_cand += st.n_cand;
+  s->n_coll += st.n_coll;
+  s->n_gmax += st.n_gmax;
+  s->n_tie += st.n_tie;
+}
+
+/* Analytic source for every particle, using its cell's count.            */
+void orc_source_all(orc_state* s, const double* v, double* dvM) {
+  const orc_cfg* cf = &s->c;
+  for (int64_t p = 0; p < cf->np; p++) {
+    if (cf->K <= 0) {
+      dvM[3 * p] = dvM[3 * p + 1] = dvM[3 * p + 2] = 0.0;
+      continue;
+    }
+    orc_hs_source(cf, v + 3 * p, s->count[s->cell[p]], dvM + 3 * p);
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * Initialisation and the velocity-Verlet step (Eq. velocity_verlet).
+ * ---------------------------------------------------------------------- */
+void orc_sample(orc_state* s, double t0) {
+  const orc_cfg* cf = &s->c;
+  s->t0 = t0;
+  s->step = 0;
+  for (int64_t p = 0; p < cf->np; p++) {
+    for (int d = 0; d < 3; d++) {
+      s->x[3 * p + d] = orc_xM(cf, s->xi[6 * p + d], t0);
+      s->v[3 * p + d] = orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+    }
+  }
+  for (int64_t i = 0; i < ncell(cf); i++) s->phi[i] = 0.0;
+  orc_sort(s);
+  orc_field(s, t0);
+}
+
+void orc_set_state(orc_state* s, const double* x, const double* v, double t0, int64_t step) {
+  const orc_cfg* cf = &s->c;
+  s->t0 = t0;
+  s->step = step;
+  memcpy(s->x, x, (size_t)(3 * cf->np) * sizeof(double));
+  memcpy(s->v, v, (size_t)(3 * cf->np) * sizeof(double));
+  orc_sort(s);
+  orc_field(s, time_at(s, (double)step));
+}
+
+double orc_wrap(double x) {
+  double y = x - floor(x);
+  if (y >= 1.0) y = 0.0;
+  return y;
+}
+
+/* the Lorentz term dt q/m (E_p - E_p^M) for every particle at time t     */
+static void lorentz_term(orc_state* s, double t, double* out) {
+  const orc_cfg* cf = &s->c;
+  double qm = cf->couple_qm_zero ? 0.0 : cf->qm;
+  for (int64_t p = 0; p < cf->np; p++) {
+    double Ep[3], EMp[3];
+    orc_gather(cf, s->E, s->x + 3 * p, Ep);
+    orc_EM(cf, s->x + 3 * p, t, EMp);
+    for (int d = 0; d < 3; d++) out[3 * p + d] = cf->dt * qm * (Ep[d] - EMp[d]);
+  }
+}
+
+void orc_step(orc_state* s, int64_t nsteps) {
+  const orc_cfg* cf = &s->c;
+  int64_t np = cf->np;
+  double* L = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
+  double* dv = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
+  double* dvM = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
+  double* vh = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
+  const double vdotM = 0.0; /* the Gaussian f_v does not depend on t */
+  for (int64_t it = 0; it < nsteps; it++) {
+    int64_t n = s->step;
+    double tn = time_at(s, (double)n);
+    double th = time_at(s, (double)n + 0.5);
+    double tn1 = time_at(s, (double)(n + 1));
+    /* v^{n+1/2}: Lorentz term, collision call A at (x^n, v^n)             */
+    lorentz_term(s, tn, L);
+    orc_dsmc_avg(s, s->v, (uint32_t)(2 * n + 0), dv);
+    orc_source_all(s, s->v, dvM);
+    for (int64_t j = 0; j < 3 * np; j++)
+      vh[j] = s->v[j] + 0.5 * (L[j] + dv[j] - dvM[j] + cf->dt * vdotM);
+    /* x^{n+1} = x^n + dt (v + xdot^M - v^M)^{n+1/2}, wrapped              */
+    for (int64_t p = 0; p < np; p++) {
+      for (int d = 0; d < 3; d++) {
+        double xm = orc_xM(cf, s->xi[6 * p + d], th);
+        double xmd = orc_xMdot(cf, xm, th);
+        double vm = orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+        s->x[3 * p + d] = orc_wrap(s->x[3 * p + d] + cf->dt * (vh[3 * p + d] + xmd - vm));
+      }
+    }
+    /* field at t^{n+1} from x^{n+1}                                       */
+    orc_sort(s);
+    orc_field(s, tn1);
+    /* v^{n+1}: Lorentz term at x^{n+1}, collision call B at (x^{n+1}, v^{n+1/2}) */
+    lorentz_term(s, tn1, L);
+    orc_dsmc_avg(s, vh, (uint32_t)(2 * n + 1), dv);
+    orc_source_all(s, vh, dvM);
+    for (int64_t j = 0; j < 3 * np; j++)
+      s->v[j] = vh[j] + 0.5 * (L[j] + dv[j] - dvM[j] + cf->dt * vdotM);
+    s->step = n + 1;
+  }
+  free(L); free(dv); free(dvM); free(vh);
+}
+
+/* One K-averaged collision call on the current state (cells of x, v); the
+ * phase selects the counter 2 step + phase; the source uses f_v (constant). */
+void orc_collide_avg(orc_state* s, int64_t phase, double* dv, double* dvM) {
+  orc_dsmc_avg(s, s->v, (uint32_t)(2 * s->step + phase), dv);
+  orc_source_all(s, s->v, dvM);
+}
+
+/* ------------------------------------------------------------------------
+ * Error norms at t = t0 + step dt (Sec. 4.3): eps_2 = sqrt(mean e^2) and
+ * eps_inf = max |e| for x, y, z (minimum-image), u, v, w, and phi at nodes.
+ * out[0..6] = eps_2, out[7..13] = eps_inf.
+ * ---------------------------------------------------------------------- */
+void orc_errors(const orc_state* s, double out[14]) {
+  const orc_cfg* cf = &s->c;
+  double t = time_at(s, (double)s->step);
+  double s2[7] = {0}, mx[7] = {0};
+  for (int64_t p = 0; p < cf->np; p++) {
+    for (int d = 0; d < 3; d++) {
+      double e = s->x[3 * p + d] - orc_xM(cf, s->xi[6 * p + d], t);
+      e -= floor(e + 0.5);
+      s2[d] += e * e;
+      if (fabs(e) > mx[d]) mx[d] = fabs(e);
+      double ev = s->v[3 * p + d] - orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+      s2[3 + d] += ev * ev;
+      if (fabs(ev) > mx[3 + d]) mx[3 + d] = fabs(ev);
+    }
+  }
+  int64_t n = cf->n;
+  double h = 1.0 / (double)n;
+  for (int64_t k = 0; k < n; k++)
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t i = 0; i < n; i++) {
+        double X[3] = {(double)i * h, (double)j * h, (double)k * h};
+        double e = s->phi[i + n * (j + n * k)] - orc_phiM(cf, X, t);
+        s2[6] += e * e;
+        if (fabs(e) > mx[6]) mx[6] = fabs(e);
+      }
+  for (int a = 0; a < 6; a++) out[a] = sqrt(s2[a] / (double)cf->np);
+  out[6] = sqrt(s2[6] / (double)(n * n * n));
+  for (int a = 0; a < 7; a++) out[7 + a] = mx[a];
+}
+
+/* ------------------------------------------------------------------------
+ * Accessors for the Python wrapper.
+ * ---------------------------------------------------------------------- */
+void orc_get_state(const orc_state* s, double* x, double* v) {
+  memcpy(x, s->x, (size_t)(3 * s->c.np) * sizeof(double));
+  memcpy(v, s->v, (size_t)(3 * s->c.np) * sizeof(double));
+}
+void orc_get_xi(const orc_state* s, double* xi) {
+  memcpy(xi, s->xi, (size_t)(6 * s->c.np) * sizeof(double));
+}
+void orc_get_field(const orc_state* s, double* rho, double* phi, double* E) {
+  int64_t nc = ncell(&s->c);
+  if (rho) memcpy(rho, s->rho, (size_t)nc * sizeof(double));
+  if (phi) memcpy(phi, s->phi, (size_t)nc * sizeof(double));
+  if (E) memcpy(E, s->E, (size_t)(3 * nc) * sizeof(double));
+}
+void orc_get_sort(const orc_state* s, int32_t* cell, int32_t* count, int32_t* start,
+                  int32_t* perm) {
+  int64_t nc = ncell(&s->c);
+  if (cell) memcpy(cell, s->cell, (size_t)s->c.np * sizeof(int32_t));
+  if (count) memcpy(count, s->count, (size_t)nc * sizeof(int32_t));
+  if (start) memcpy(start, s->start, (size_t)(nc + 1) * sizeof(int32_t));
+  if (perm) memcpy(perm, s->perm, (size_t)s->c.np * sizeof(int32_t));
+}
+void orc_get_stats(const orc_state* s, int64_t out[6], double* cg_res) {
+  out[0] = s->n_cand; out[1] = s->n_coll; out[2] = s->n_gmax; out[3] = s->n_tie;
+  out[4] = s->cg_iters; out[5] = s->step;
+  if (cg_res) *cg_res = s->cg_res;
+}
+void orc_reset_stats(orc_state* s) { s->n_cand = s->n_coll = s->n_gmax = s->n_tie = 0; }
+void orc_set_phi(orc_state* s, const double* phi) {
+  memcpy(s->phi, phi, (size_t)ncell(&s->c) * sizeof(double));
+}
+/* Single-cell NTC outcome for brute-force tests: velocities [c][3] updated
+ * in place, returns the number of collisions.                            */
+int64_t orc_ntc_cell(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint32_t o, int64_t c,
+                     double* v) {
+  orc_dsmc_stats st = {0, 0, 0, 0};
+  ntc_one_outcome(cf, c0, cellk, o, c, v, &st);
+  return st.n_coll;
+}

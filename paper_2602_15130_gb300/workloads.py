@@ -1,0 +1,87 @@
+"""Synthetic manufactured-solution workloads (parameter recipes only).
+
+Every workload is the periodic unit cube [0,1)^3 with the separable
+manufactured position density prod_d (1 + 0.3 sin(2 pi (x_d - 0.1 t))),
+Gaussian velocities (mean 0.2, sigma 1 per axis), q/m = q = eps0 = 1, one
+physical particle in the box (w = 1/N_p, mean charge density 1), the
+manufactured potential phi^M = 0.1 e^{t/2} prod_d sin(2 pi (x_d - s_d)) with
+s = (1/7, 1/5, 1/3) (the form of the paper's Sec. 5.2 on the unit cube) and
+hard-sphere collisions with isotropic scattering.
+
+The hard-sphere cross section sigma0 is chosen so that a particle undergoes
+``coll_per_call`` expected collisions per collision call at the recipe's own
+particles per cell and time step: with the mean relative speed of two
+Gaussian samples <g> = 4 s / sqrt(pi), Eq. p_coll gives
+(c - 1) sigma0 <g> w dt / dV = coll_per_call.
+
+Nothing here performs any step of the method; these are inputs.
+"""
+from __future__ import annotations
+
+import math
+
+G_MAX = 10.0 * math.sqrt(3.0)  # g_max = 10 sqrt(3) vbar with vbar = sigma_v = 1
+
+
+def hard_sphere_sigma0(ppc: float, dt: float, coll_per_call: float = 0.1, v_sigma: float = 1.0) -> float:
+    mean_g = 4.0 * v_sigma / math.sqrt(math.pi)
+    # w / dV = (1/N_p) / (1/n^3) = 1 / ppc
+    return coll_per_call * ppc / ((ppc - 1.0) * mean_g * dt)
+
+
+def base(n: int, n_particles: int, dt: float, K: int, sigma0: float, seed: int = 0, **kw) -> dict:
+    p = dict(
+        n=n, n_particles=n_particles, dt=dt, K=K, sigma0=sigma0, g_max=G_MAX, seed=seed,
+        qm=1.0, q=1.0, eps0=1.0, n_phys=1.0,
+        fx_amp=0.3, fx_speed=0.1, v_mean=(0.2, 0.2, 0.2), v_sigma=1.0,
+        phi_amp=0.1, phi_T=1.0, phi_shift=(1.0 / 7.0, 1.0 / 5.0, 1.0 / 3.0),
+        couple_qm_zero=0, couple_q_zero=0, cg_tol=1e-10, cg_maxit=20000,
+    )
+    p.update(kw)
+    return p
+
+
+def smallest(**kw) -> dict:
+    """8^3 cells, 4,096 particles, dt = 0.01, 10 steps, K = 16, seed 0,
+    about 0.1 collisions per particle per step."""
+    n, npart, dt = 8, 4096, 0.01
+    p = base(n, npart, dt, 16, hard_sphere_sigma0(npart / n ** 3, dt), steps=10)
+    p.update(kw)
+    return p
+
+
+REFINE_PPC = 32
+REFINE_DT0 = 0.02
+REFINE_T_END = 0.5
+
+
+def refinement_level(level: int, collisions: bool = True, **kw) -> dict:
+    """Refinement sweep level l = 0..4: n = 8 * 2^l, 32 particles per cell,
+    dt = 0.02 / 2^l, 0.5 time units, K = 16 (or 0 with collisions off).
+    sigma0 is fixed from level 0 (it is physics, not discretisation)."""
+    n = 8 * 2 ** level
+    dt = REFINE_DT0 / 2 ** level
+    sigma0 = hard_sphere_sigma0(REFINE_PPC, REFINE_DT0)
+    p = base(n, REFINE_PPC * n ** 3, dt, 16 if collisions else 0, sigma0,
+             steps=int(round(REFINE_T_END / dt)))
+    p.update(kw)
+    return p
+
+
+def precision_form(**kw) -> dict:
+    """128^3 cells, 64 particles per cell (134,217,728), K = 32, dt = 0.005,
+    200 steps; sigma0 from the 0.1-collision rule at these settings."""
+    n, ppc, dt = 128, 64, 0.005
+    p = base(n, ppc * n ** 3, dt, 32, hard_sphere_sigma0(ppc, dt), steps=200)
+    p.update(kw)
+    return p
+
+
+def scaled(p: dict, n: int) -> dict:
+    """Same particles per cell, K and dt on an n^3 mesh (used for bounded
+    samples of a large workload)."""
+    q = dict(p)
+    ppc = p["n_particles"] / p["n"] ** 3
+    q["n"] = n
+    q["n_particles"] = int(round(ppc * n ** 3))
+    return q
