@@ -1,0 +1,324 @@
+"""Throughput of the manufactured-solution PIC + DSMC step on GB300.
+
+Default workload: the finest level of the plain-FP64 refinement sweep
+(128^3 cells, 32 particles per cell = 67,108,864 particles, K = 16,
+dt = 0.02/16, collisions on). A step is one full velocity-Verlet step of
+every particle: two K-averaged DSMC calls, kick, drift, sort, deposit,
+Poisson CG and E. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload on the host cores.
+Multi-GPU: independent replicas (one per rank, own Philox seed), no
+collective on the data path; value = particles x steps of all ranks / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (PIC+DSMC, K-avg) vs plain FP64 at stated error; % HBM roofline"
+UNIT = "particle-steps/s"
+
+
+def workload(name: str) -> dict:
+    from paper_2602_15130_gb300 import workloads as W
+
+    if name == "refine4":
+        return W.refinement_level(4)
+    if name.startswith("refine"):
+        return W.refinement_level(int(name[6:]))
+    if name == "smallest":
+        return W.smallest()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(name: str, p: dict) -> str:
+    return (f"{name}: {p['n']}^3 cells, {p['n_particles']} particles, K={p['K']}, dt={p['dt']}, "
+            f"hard-sphere sigma0={p['sigma0']:.4f}, FP64")
+
+
+# ----------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock samples unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# Algorithmic HBM bytes per unit for each kernel class of one step (FP64
+# form). Units: particles for the particle kernels, nodes x CG iterations
+# for the CG. Derivations are in the design doc.
+BYTES_PER_UNIT = {
+    "kick_drift": (124 + 104 + 72 + 24) / 2.0,  # average of the drift and no-drift kick launches
+    "sort_gather_deposit": 200 + 8 + 64 / 32.0,
+    "dsmc": 48.0,
+    "sort": 4 + 4 + 4 + 4,
+    "cg_efield": 96.0,
+    "rhs": 8 * 8 + 16,
+}
+
+
+# ------------------------------------------------------------- replicas -----
+def replica_params(p: dict, rank: int) -> dict:
+    """Each rank runs an independent replica: same workload, own Philox seed."""
+    q = dict(p)
+    q["seed"] = int(p.get("seed", 0)) + rank
+    return q
+
+
+def max_over_ranks(x: float, device: str = "cpu") -> float:
+    """Max of a per-rank scalar over the process group (timing only)."""
+    import torch
+    import torch.distributed as td
+
+    if not td.is_available() or not td.is_initialized() or td.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(n_particles: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job particle-steps/s: all ranks' particle-steps over the slowest rank's time."""
+    return world * n_particles * steps / (max_ms / 1000.0)
+
+
+# ----------------------------------------------------------------- GPU arm ---
+def run_gpu(args, rank: int, world: int) -> dict | None:
+    import numpy as np
+    import torch
+
+    from paper_2602_15130_gb300 import Pic
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    p = replica_params(workload(args.workload), rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = Pic(p, stream=stream)
+        sim.sample_mms(0.0)
+        sim.step(args.warmup)
+        dist = world > 1
+        if dist:
+            import torch.distributed as td
+            td.barrier()
+        torch.cuda.synchronize()
+        sim.reset_stats()
+        sim.set_profiling(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            time.sleep(0.3)
+            ev0.record(stream)
+            sim.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        kt = sim.kernel_times()
+        st = sim.stats()
+        sim.set_profiling(False)
+        ms = max_over_ranks(ms, "cuda")
+        errs = sim.mms_error()
+        # end to end through the C ABI with host buffers: pinned x, v in, step, x, v out
+        npart = p["n_particles"]
+        xh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
+        vh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
+        sim.get_state((xh, vh))
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sim.set_state(xh, vh, 0.0, int(st["step"]))
+            sim.step(1)
+            sim.get_state((xh, vh))
+        e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
+        sim.close()
+    if rank != 0:
+        return None
+    value = aggregate_value(npart, args.steps, world, ms)
+    peaks = measured_peaks()
+    # dominant kernel class by device time inside the timed region
+    dom = max(kt, key=lambda k: kt[k]["ms"])
+    per_launch_ms = kt[dom]["ms"] / max(1, kt[dom]["launches"])
+    if dom == "cg_efield":
+        units = p["n"] ** 3 * max(1, st["cg_iters_max"])
+    else:
+        units = npart
+    achieved = BYTES_PER_UNIT.get(dom, 0.0) * units / (per_launch_ms / 1000.0) / 1e9
+    launches = int(st["kernel_launches"])
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic manufactured-solution workload",
+        "config": {"workload": describe(args.workload, p), "n": p["n"], "n_particles": npart, "K": p["K"],
+                   "dt": p["dt"], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (particle state %.1f GB)" % (npart * 100 / 1e9)},
+        "e2e": {"value": aggregate_value(npart, e2e_steps, world, e2e_s * 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": npart * 48, "d2h_bytes_per_step": npart * 48,
+                "path": "pic_set_state(host) + pic_step(1) + pic_get_state(host), pinned buffers"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peaks["source"],
+                     "bytes_per_unit": BYTES_PER_UNIT.get(dom), "units_per_launch": units},
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items()},
+        "kernel_launches_by_class": {k: v["launches"] for k, v in kt.items()},
+        "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
+                  "cg_iters_max": st["cg_iters_max"], "cg_res_last": st["cg_res_last"]},
+        "mms_error": {"eps2": errs["eps2"], "epsinf": errs["epsinf"]},
+        "clocks": clk.summary(),
+    }
+
+
+# ------------------------------------------------------------ CPU oracle ----
+def oracle_sample_params(args) -> tuple[dict, str]:
+    from paper_2602_15130_gb300 import workloads as W
+
+    p = workload(args.workload)
+    n_small = min(p["n"], args.cpu_mesh)
+    q = W.scaled(p, n_small)
+    return q, (f"oracle on a {n_small}^3 sub-problem with the workload's particles per cell, K and dt "
+               f"({q['n_particles']} particles), single host thread")
+
+
+def run_oracle_steps(q: dict, steps: int, warmup: int) -> tuple[float, float]:
+    from oracle import oracle as O
+
+    o = O.Oracle(q)
+    o.sample(0.0)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return q["n_particles"] * steps / dt, dt
+
+
+def cpu_baseline(args) -> dict:
+    q, sample = oracle_sample_params(args)
+    rate, dt = run_oracle_steps(q, args.cpu_steps, 0)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + f", {args.cpu_steps} step(s), {dt:.1f} s"}
+
+
+def run_reference(args, rank: int) -> dict | None:
+    if rank != 0:
+        return None
+    q, sample = oracle_sample_params(args)
+    rate, dt = run_oracle_steps(q, args.steps, args.warmup)
+    return {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1000 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic manufactured-solution workload",
+        "config": {"workload": describe(args.workload, workload(args.workload)), "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="refine4")
+    ap.add_argument("--cpu-mesh", type=int, default=24)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    if world > 1 and args.impl != "reference":
+        import torch.distributed as td
+
+        td.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out:
+            print(json.dumps(out), flush=True)
+        return
+    import __graft_entry__ as g
+
+    if rank == 0:
+        g.build()
+    if world > 1:
+        import torch.distributed as td
+
+        td.barrier()
+    out = run_gpu(args, rank, world)
+    if out is not None:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as td
+
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * pic.h - C ABI of the GB300 manufactured-solution PIC + DSMC time step.
+ *
+ * The method is the one of Freno, McDoniel, Moore and Matula, "Code-
+ * Verification Techniques for Particle-in-Cell Simulations with Direct
+ * Simulation Monte Carlo Collisions": a 3D periodic electrostatic
+ * particle-in-cell step (cloud-in-cell deposit, Poisson solve, gather,
+ * velocity-Verlet push; Sec. 2 and Eq. velocity_verlet) with binary elastic
+ * no-time-counter collisions (Algorithm 1) averaged over K independent
+ * outcomes (Eq. avg_outcome), driven by manufactured solutions obtained by
+ * inverse-CDF queries (Eq. mms_sol, Eq. eom_mms, Eq. poisson_mms).
+ *
+ * Conventions shared by every entry point:
+ *  - All work is enqueued on the CUDA stream given to pic_create, in call
+ *    order. Every call that returns a device-side status or host data
+ *    (pic_sample_mms, pic_set_state, pic_step, pic_collide_avg,
+ *    pic_mms_error, pic_get_*) synchronises that stream before returning.
+ *  - Particle arrays crossing the boundary are indexed by particle id (pid,
+ *    0 .. N_p-1) and laid out [N_p][3] (component fastest), FP64. Mesh
+ *    arrays are [n^3] with x fastest (node (i,j,k) at index i + n (j + n k),
+ *    position (i h, j h, k h), h = 1/n), vector fields [n^3][3].
+ *  - Pointers marked "host or device" may point to host memory (pageable or
+ *    pinned) or device memory of the context's GPU; the library copies with
+ *    cudaMemcpyDefault. The caller owns every pointer it passes; the library
+ *    never keeps one after the call returns.
+ *  - No call throws. Every call returns a pic_status; a failed call leaves
+ *    the context usable unless it returns PIC_ESTATE or PIC_ECUDA.
+ *  - The context owns all device buffers. pic_destroy(NULL) is a no-op.
+ *  - One context is used by one host thread at a time.
+ */
+#ifndef PIC_GB300_PIC_H
+#define PIC_GB300_PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_EINVAL = 1,     /* invalid argument or configuration                 */
+  PIC_ENOMEM = 2,     /* device or host allocation failed                  */
+  PIC_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed       */
+  PIC_ENOCONV = 4,    /* the Poisson CG hit cg_maxit before cg_tol         */
+  PIC_ETIMEOUT = 5,   /* a bounded device-side wait gave up                */
+  PIC_ESTATE = 6,     /* call out of order (e.g. pic_step before sampling) */
+  PIC_ECAPACITY = 7   /* a cell held more particles than max_ppc           */
+} pic_status;
+
+enum { PIC_FP64 = 0 };
+
+/* Problem statement (unit cube [0,1)^3, periodic). Field meanings:
+ *  n             cells = nodes per axis (2 .. 1024); cell (i,j,k) spans
+ *                [i h,(i+1) h) x ...; node (i,j,k) sits at (i h, j h, k h).
+ *  n_particles   N_p computational particles (1 .. 2^31-1), equal weight
+ *                w = n_phys / N_p (Sec. 3.3).
+ *  K             N_avg, outcomes averaged per collision call (Eq.
+ *                avg_outcome), 0 .. 2^20; 0 switches collisions off.
+ *  dt            time step of Eq. velocity_verlet; t_n = t0 + n dt.
+ *  qm, q, eps0   charge-to-mass ratio, charge and permittivity (Eqs.
+ *                eom_full, poisson); n_phys = N, physical particles in the box.
+ *  sigma0, g_max hard-sphere cross section sigma(g) = sigma0 and the g_max
+ *                of (sigma g)_max = sigma0 g_max (Algorithm 1, Sec. 5.2).
+ *  fx_amp, fx_speed  manufactured density f_{x_d}(x,t) = 1 + fx_amp
+ *                sin(2 pi (x - fx_speed t)) per axis (Eq. fx); |fx_amp| < 1.
+ *  v_mean, v_sigma   manufactured Gaussian velocity density per axis (Eq. fv
+ *                replaced by a Gaussian of common width v_sigma > 0).
+ *  phi_amp, phi_T, phi_shift  manufactured potential phi^M = phi_amp
+ *                e^{t/(2 phi_T)} prod_d sin(2 pi (x_d - phi_shift_d))
+ *                (Sec. 5.2 form).
+ *  couple_qm_zero  nonzero: q/m = 0 in the push (field does not act).
+ *  couple_q_zero   nonzero: q = 0 in the deposit and in rho^M (Sec. 5.3).
+ *  precision     PIC_FP64.
+ *  max_ppc       most particles one cell may hold during collisions (working
+ *                set of the collision kernel); 0 selects 512.
+ *  seed          Philox4x32-10 key (low word, high word).
+ *  cg_tol, cg_maxit  CG stops at ||r||_2 <= cg_tol ||b||_2 or cg_maxit. */
+typedef struct {
+  int32_t n;
+  int32_t K;
+  int64_t n_particles;
+  double dt;
+  double qm, q, eps0, n_phys;
+  double sigma0, g_max;
+  double fx_amp, fx_speed;
+  double v_mean[3];
+  double v_sigma;
+  double phi_amp, phi_T;
+  double phi_shift[3];
+  int32_t couple_qm_zero, couple_q_zero;
+  int32_t precision;
+  int32_t max_ppc;
+  uint64_t seed;
+  double cg_tol;
+  int32_t cg_maxit;
+  int32_t reserved;
+} pic_config;
+
+/* Error norms of Sec. 4.3 at the context's current time: index 0..5 =
+ * x, y, z (minimum-image), u, v, w over particles; index 6 = phi over nodes. */
+typedef struct {
+  double eps2[7];
+  double epsinf[7];
+} pic_errors;
+
+/* Counters accumulated since pic_create or pic_reset_stats. */
+typedef struct {
+  int64_t n_cand;         /* candidate pairs drawn (Algorithm 1 loop)       */
+  int64_t n_coll;         /* accepted collisions                            */
+  int64_t n_gmax_exceed;  /* candidates with g > g_max (ratio above 1)      */
+  int64_t n_near_ties;    /* |U - sigma g/(sigma g)_max| < 1e-12            */
+  int64_t kernel_launches;/* kernels this library launched                  */
+  int64_t step;           /* steps taken since sampling                     */
+  double t;               /* current time t0 + step dt                      */
+  int32_t cg_iters_last;  /* iterations of the last Poisson solve           */
+  int32_t cg_iters_max;
+  double cg_res_last;     /* last relative residual ||r|| / ||b||           */
+} pic_stats;
+
+/* Optional device allocator (e.g. a framework's caching allocator). Both
+ * callbacks are called on the creating thread; alloc returns NULL on
+ * failure. NULL selects cudaMalloc / cudaFree. */
+typedef struct {
+  void* (*alloc)(void* user, uint64_t bytes);
+  void (*free)(void* user, void* ptr);
+  void* user;
+} pic_allocator;
+
+/* Per-kernel timing gathered with CUDA events on the context stream while
+ * profiling is on (pic_set_profiling). Index = kernel class:
+ * 0 sample, 1 sort (keys/scan/scatter), 2 sort gather + deposit,
+ * 3 rhs, 4 cg + E, 5 dsmc, 6 kick/drift, 7 error norms, 8 copies/other. */
+#define PIC_NUM_KERNEL_CLASSES 9
+typedef struct {
+  double ms[PIC_NUM_KERNEL_CLASSES];
+  int64_t launches[PIC_NUM_KERNEL_CLASSES];
+} pic_kernel_times;
+
+/* Fill *cfg with the defaults (the smallest manufactured workload: n = 8,
+ * N_p = 4096, dt = 0.01, K = 16 ...). Host only, no CUDA. */
+pic_status pic_config_default(pic_config* cfg);
+
+/* Check a configuration without touching the GPU. Host only, no CUDA.
+ * Returns PIC_OK or PIC_EINVAL. */
+pic_status pic_validate_config(const pic_config* cfg);
+
+/* Derived constants of a configuration (host only, no CUDA):
+ * out[0] = w = n_phys/N_p, out[1] = dV = h^3, out[2] = P_coll,max =
+ * (sigma g)_max w dt / dV (Algorithm 1, Eq. p_coll), out[3] = N_p^cell mean,
+ * out[4] = the sufficient bound 1/P_coll,max of Eq. navg_ineq. */
+pic_status pic_derived(const pic_config* cfg, double out[5]);
+
+/* Create a context on the current CUDA device: validates cfg, allocates
+ * all device buffers (via alloc, or cudaMalloc when alloc is NULL) and
+ * binds the stream (a cudaStream_t; NULL = legacy default stream).
+ * *out is set to NULL on failure. */
+pic_status pic_create(const pic_config* cfg, void* cuda_stream, const pic_allocator* alloc,
+                      pic_ctx** out);
+
+/* Sec. 3.2: draw xi_{x_i}, xi_{v_i} for every pid from Philox4x32-10
+ * (counter (pid_lo, pid_hi, 0, 0xFFFFFF00 | j), j = 0..2, two 52-bit
+ * uniforms per block), set x = x^M(t0), v = v^M(t0) by inverse-CDF queries
+ * (Eq. mms_sol), sort by (cell, pid), deposit, solve Eq. poisson_mms and
+ * compute E at t0. Resets the step counter to 0. */
+pic_status pic_sample_mms(pic_ctx* ctx, double t0);
+
+/* Advance nsteps >= 0 steps of Eq. velocity_verlet with the manufactured
+ * sources of Eq. eom_mms: per step, K-averaged collision call A at
+ * (x^n, v^n) and call B at (x^{n+1}, v^{n+1/2}), each with the full dt in
+ * P_coll and applied with weight 1/2; the field is re-solved at t^{n+1}.
+ * Synchronises the stream once at the end and returns the first device-
+ * side failure of the steps: PIC_ENOCONV if a Poisson solve missed cg_tol
+ * (the steps still complete), PIC_ECAPACITY if a cell exceeded max_ppc
+ * (its collisions were skipped), PIC_ETIMEOUT if a bounded device wait gave
+ * up (the field is then invalid). */
+pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
+
+/* One K-averaged collision call (Eq. avg_outcome, Algorithm 1) on the
+ * current state: counter word 2 step + phase (phase 0 or 1). Writes
+ * <Delta v_p>_coll to dv and the analytic <Delta v_p^M>_coll of Eq.
+ * vel_change_1c (hard spheres, Gaussian f_v) to dvM, both [N_p][3], pid
+ * indexed, host or device. Does not change the state. */
+pic_status pic_collide_avg(pic_ctx* ctx, int32_t phase, double* dv, double* dvM);
+
+/* Error norms of Sec. 4.3 at the current time into *out (host). */
+pic_status pic_mms_error(pic_ctx* ctx, pic_errors* out);
+
+/* Copy the particle state out: x, v [N_p][3], pid indexed, host or device. */
+pic_status pic_get_state(pic_ctx* ctx, double* x, double* v);
+
+/* Replace the particle state (x in [0,1)^3, v; [N_p][3], pid indexed, host
+ * or device), set the time to t0 + step dt, re-sort and re-solve the field. */
+pic_status pic_set_state(pic_ctx* ctx, const double* x, const double* v, double t0,
+                         int64_t step);
+
+/* Copy mesh quantities out (any pointer may be NULL): rho [n^3] (the CIC
+ * charge density of Sec. 2), phi [n^3], E [n^3][3]; host or device. */
+pic_status pic_get_field(pic_ctx* ctx, double* rho, double* phi, double* E);
+
+/* Copy the sort out (any pointer may be NULL): cell of every pid [N_p],
+ * count [n^3], start [n^3 + 1], perm [N_p] = pids in (cell, pid) order;
+ * int32, host or device. */
+pic_status pic_get_sort(pic_ctx* ctx, int32_t* cell_of_pid, int32_t* count, int32_t* start,
+                        int32_t* perm);
+
+pic_status pic_get_stats(pic_ctx* ctx, pic_stats* out);
+pic_status pic_reset_stats(pic_ctx* ctx);
+
+/* Per-kernel CUDA-event timing on the context stream (off by default).
+ * Turning it on or off clears the accumulated times. */
+pic_status pic_set_profiling(pic_ctx* ctx, int32_t on);
+pic_status pic_get_kernel_times(pic_ctx* ctx, pic_kernel_times* out);
+
+void pic_destroy(pic_ctx* ctx);
+const char* pic_status_string(pic_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_PIC_H */

@@ -1,0 +1,204 @@
+"""GB300-native manufactured-solution PIC + DSMC hot path.
+
+``Pic`` wraps one ``pic_ctx`` of the C ABI (``include/pic.h``); every step
+of the method runs in the library's CUDA kernels. This module only
+marshals arguments: numpy arrays (host) or torch tensors (host or CUDA) go
+in as pointers, results come back as numpy arrays or torch CUDA tensors.
+Device memory of the context is drawn from torch's caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib, workloads
+from ._lib import PicConfig, PicError, check, load
+
+__all__ = ["Pic", "PicConfig", "PicError", "make_config", "workloads", "load"]
+
+
+def make_config(p: dict) -> PicConfig:
+    """pic_config from a workload dict (see ``workloads``)."""
+    L = load()
+    c = PicConfig()
+    check(L.pic_config_default(ctypes.byref(c)), "pic_config_default")
+    c.n = int(p["n"])
+    c.K = int(p["K"])
+    c.n_particles = int(p["n_particles"])
+    c.dt = float(p["dt"])
+    for name in ("qm", "q", "eps0", "sigma0", "fx_amp", "fx_speed", "v_sigma", "phi_amp", "phi_T", "cg_tol"):
+        if name in p:
+            setattr(c, name, float(p[name]))
+    if "n_phys" in p:
+        c.n_phys = float(p["n_phys"])
+    if "g_max" in p:
+        c.g_max = float(p["g_max"])
+    for d in range(3):
+        if "v_mean" in p:
+            c.v_mean[d] = float(p["v_mean"][d])
+        if "phi_shift" in p:
+            c.phi_shift[d] = float(p["phi_shift"][d])
+    c.couple_qm_zero = int(p.get("couple_qm_zero", 0))
+    c.couple_q_zero = int(p.get("couple_q_zero", 0))
+    c.max_ppc = int(p.get("max_ppc", 0))
+    c.seed = int(p.get("seed", 0))
+    c.cg_maxit = int(p.get("cg_maxit", c.cg_maxit))
+    return c
+
+
+class _TorchAllocator:
+    """pic_allocator backed by torch's CUDA caching allocator."""
+
+    def __init__(self):
+        import torch
+
+        self.torch = torch
+        self.live = {}
+        self._a = _lib.ALLOC_FN(self._alloc)
+        self._f = _lib.FREE_FN(self._free)
+        self.struct = _lib.PicAllocator(self._a, self._f, None)
+
+    def _alloc(self, user, nbytes):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device="cuda")
+        except Exception:
+            return None
+        ptr = t.data_ptr()
+        self.live[ptr] = t
+        return ptr
+
+    def _free(self, user, ptr):
+        self.live.pop(ptr, None)
+
+
+def _ptr(a):
+    """(pointer, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data, a
+    return a.data_ptr(), a
+
+
+class Pic:
+    """One simulation context on the current CUDA device."""
+
+    def __init__(self, params: dict | PicConfig, stream=None, torch_allocator: bool = True):
+        import torch
+
+        L = load()
+        self.L = L
+        self.cfg = params if isinstance(params, PicConfig) else make_config(params)
+        self.np = int(self.cfg.n_particles)
+        self.n = int(self.cfg.n)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        self._alloc = _TorchAllocator() if torch_allocator else None
+        ctx = ctypes.c_void_p()
+        check(L.pic_create(ctypes.byref(self.cfg), ctypes.c_void_p(handle),
+                           ctypes.byref(self._alloc.struct) if self._alloc else None, ctypes.byref(ctx)),
+              "pic_create")
+        self.ctx = ctx
+
+    # -- lifecycle --------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.L.pic_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the method -------------------------------------------------------
+    def sample_mms(self, t0: float = 0.0, allow=()):
+        return check(self.L.pic_sample_mms(self.ctx, float(t0)), "pic_sample_mms", allow)
+
+    def step(self, nsteps: int = 1, allow=()):
+        return check(self.L.pic_step(self.ctx, int(nsteps)), "pic_step", allow)
+
+    def collide_avg(self, phase: int, out=None):
+        """(<dv>, <dv^M>) [N_p, 3] pid-indexed; numpy unless ``out`` tensors given."""
+        if out is None:
+            out = (np.zeros((self.np, 3)), np.zeros((self.np, 3)))
+        pa, ka = _ptr(out[0])
+        pb, kb = _ptr(out[1])
+        check(self.L.pic_collide_avg(self.ctx, int(phase), pa, pb), "pic_collide_avg")
+        return out
+
+    def mms_error(self) -> dict:
+        e = _lib.PicErrors()
+        check(self.L.pic_mms_error(self.ctx, ctypes.byref(e)), "pic_mms_error", allow=(_lib.PIC_ENOCONV,))
+        names = ["x", "y", "z", "u", "v", "w", "phi"]
+        return {"eps2": dict(zip(names, list(e.eps2))), "epsinf": dict(zip(names, list(e.epsinf))),
+                "array": np.array(list(e.eps2) + list(e.epsinf))}
+
+    # -- state and test hooks ---------------------------------------------
+    def get_state(self, out=None):
+        if out is None:
+            out = (np.zeros((self.np, 3)), np.zeros((self.np, 3)))
+        pa, ka = _ptr(out[0])
+        pb, kb = _ptr(out[1])
+        check(self.L.pic_get_state(self.ctx, pa, pb), "pic_get_state")
+        return out
+
+    def set_state(self, x, v, t0: float = 0.0, step: int = 0, allow=()):
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            v = np.ascontiguousarray(v, dtype=np.float64)
+        pa, ka = _ptr(x)
+        pb, kb = _ptr(v)
+        return check(self.L.pic_set_state(self.ctx, pa, pb, float(t0), int(step)), "pic_set_state", allow)
+
+    def get_field(self):
+        nc = self.n ** 3
+        rho, phi, E = np.zeros(nc), np.zeros(nc), np.zeros((nc, 3))
+        check(self.L.pic_get_field(self.ctx, rho.ctypes.data, phi.ctypes.data, E.ctypes.data), "pic_get_field")
+        return rho, phi, E
+
+    def get_sort(self):
+        nc = self.n ** 3
+        cell = np.zeros(self.np, np.int32)
+        count = np.zeros(nc, np.int32)
+        start = np.zeros(nc + 1, np.int32)
+        perm = np.zeros(self.np, np.int32)
+        check(self.L.pic_get_sort(self.ctx, cell.ctypes.data, count.ctypes.data, start.ctypes.data,
+                                  perm.ctypes.data), "pic_get_sort")
+        return cell, count, start, perm
+
+    def stats(self, allow=(_lib.PIC_ENOCONV,)) -> dict:
+        s = _lib.PicStats()
+        check(self.L.pic_get_stats(self.ctx, ctypes.byref(s)), "pic_get_stats", allow)
+        return {f: getattr(s, f) for f, _ in _lib.PicStats._fields_}
+
+    def reset_stats(self):
+        check(self.L.pic_reset_stats(self.ctx), "pic_reset_stats")
+
+    def set_profiling(self, on: bool):
+        check(self.L.pic_set_profiling(self.ctx, 1 if on else 0), "pic_set_profiling")
+
+    def kernel_times(self) -> dict:
+        k = _lib.PicKernelTimes()
+        check(self.L.pic_get_kernel_times(self.ctx, ctypes.byref(k)), "pic_get_kernel_times")
+        return {name: {"ms": k.ms[i], "launches": k.launches[i]} for i, name in enumerate(_lib.KERNEL_CLASSES)}
+
+
+def derived(params: dict) -> dict:
+    """Host-only derived constants (no GPU needed)."""
+    L = load()
+    c = make_config(params)
+    out = (ctypes.c_double * 5)()
+    check(L.pic_derived(ctypes.byref(c), out), "pic_derived")
+    return {"w": out[0], "dV": out[1], "pmax": out[2], "ppc": out[3], "inv_pmax": out[4]}

@@ -1,0 +1,370 @@
+// Field solve of Eq. poisson_mms on the periodic node mesh:
+//   rhs : rho at nodes from the per-cell CIC partials, b = rho/eps0 -
+//         Lap phi^M - rho^M/eps0 and per-block partial sums of b;
+//   cg  : one cooperative persistent kernel: b -= mean(b), conjugate
+//         gradients on -Lap_h phi = b (7-point, warm start, two grid
+//         barriers per iteration, p = r + beta p formed on the fly inside
+//         the matrix-vector product), zero-mean projection and
+//         E = -grad_h phi by central differences.
+// All reductions are per-block partials combined in a fixed order, so a
+// solve is deterministic for a given grid. Grid barriers are bounded: a
+// wait that exceeds ~2 s of SM clock sets a timeout flag and the kernel
+// returns.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr long long kBarrierCycles = 4000000000LL;
+
+inline int blocks_for(int64_t n, int t = kThreads) {
+  int64_t b = (n + t - 1) / t;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// fixed-shape block sum; result valid in every thread
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += sh[i];
+  return t;
+}
+
+struct RhsArgs {
+  Params P;
+  double t;
+  const double* corner;
+  double *rho, *b, *part;
+};
+
+__global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
+  __shared__ double sh[32];
+  const Params& P = a.P;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double bv = 0.0;
+  if (id < P.ncell) {
+    const int n = P.n;
+    const int i = (int)(id % n), j = (int)((id / n) % n), k = (int)(id / ((int64_t)n * n));
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int ii = i - q < 0 ? n - 1 : i - q, jj = j - b < 0 ? n - 1 : j - b, kk = k - c < 0 ? n - 1 : k - c;
+          s += a.corner[(int64_t)(q + 2 * b + 4 * c) * P.ncell + ii + (int64_t)n * (jj + (int64_t)n * kk)];
+        }
+    const double rho = P.rho_scale * s;
+    const double X = i * P.h, Y = j * P.h, Z = k * P.h;
+    const double ct = P.fx_speed * a.t;
+    const double phiM = P.phi_amp * exp(a.t / (2.0 * P.phi_T)) * sinpi(2.0 * (X - P.phi_shift[0])) *
+                        sinpi(2.0 * (Y - P.phi_shift[1])) * sinpi(2.0 * (Z - P.phi_shift[2]));
+    const double lap_phiM = -3.0 * kTwoPi * kTwoPi * phiM;
+    const double rhoM = P.q_eff * P.nphys * (1.0 + P.fx_amp * sinpi(2.0 * (X - ct))) *
+                        (1.0 + P.fx_amp * sinpi(2.0 * (Y - ct))) * (1.0 + P.fx_amp * sinpi(2.0 * (Z - ct)));
+    bv = rho / P.eps0 - lap_phiM - rhoM / P.eps0;
+    a.rho[id] = rho;
+    a.b[id] = bv;
+  }
+  const double tot = block_sum(bv, sh);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+}
+
+struct CgArgs {
+  int n;
+  int64_t ncell;
+  double inv_h2, two_h;
+  double *b, *x, *r, *p0, *p1, *q;
+  const double* rhs_part;
+  int rhs_blocks;
+  double* red;  // [4][gridDim.x]
+  unsigned int* bar;
+  int* info;    // [0] iterations [1] status (1 = no convergence) [2] timeout
+  int* flags;   // sticky context flags
+  double* res;
+  double tol;
+  int maxit;
+  double *E0, *E1, *E2;
+};
+
+// Sense-free generation barrier for a cooperative grid, bounded in time.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* info, int* flags) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+    ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > kBarrierCycles) {
+          atomicOr(info + 2, 1);
+          atomicOr(flags, 4);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (ok && *((volatile int*)(info + 2))) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// total of gridDim.x partials in fixed order, in every thread
+__device__ __forceinline__ double grid_total(const double* part, int m, double* sh) {
+  const int lane = threadIdx.x & 31;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) s += ((volatile const double*)part)[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) sh[0] = s;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+__device__ __forceinline__ int64_t wrapi(int64_t i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
+  __shared__ double sh[40];
+  const int n = a.n;
+  const int64_t m = a.ncell;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int G = gridDim.x;
+  int ph = 0;  // alternating reduction slots
+  auto slot = [&](int q) { return a.red + (size_t)q * 2 * G; };
+
+  // phase 0: zero-mean b, r = b - A x, ||r||^2 and ||b||^2
+  const double mean_b = grid_total(a.rhs_part, a.rhs_blocks, sh) / (double)m;
+  double rr_loc = 0.0, bb_loc = 0.0;
+  for (int64_t id = t0; id < m; id += stride) {
+    const int64_t i = id % n, j = (id / n) % n, k = id / ((int64_t)n * n);
+    const double bv = a.b[id] - mean_b;
+    a.b[id] = bv;
+    const double* x = a.x;
+    const double nb = x[wrapi(i + 1, n) + n * (j + (int64_t)n * k)] + x[wrapi(i - 1, n) + n * (j + (int64_t)n * k)] +
+                      x[i + n * (wrapi(j + 1, n) + (int64_t)n * k)] + x[i + n * (wrapi(j - 1, n) + (int64_t)n * k)] +
+                      x[i + n * (j + (int64_t)n * wrapi(k + 1, n))] + x[i + n * (j + (int64_t)n * wrapi(k - 1, n))];
+    const double Ax = (6.0 * x[id] - nb) * a.inv_h2;
+    const double rv = bv - Ax;
+    a.r[id] = rv;
+    rr_loc += rv * rv;
+    bb_loc += bv * bv;
+  }
+  {
+    const double s1 = block_sum(rr_loc, sh);
+    const double s2 = block_sum(bb_loc, sh + 8);
+    if (threadIdx.x == 0) {
+      slot(ph)[blockIdx.x] = s1;
+      slot(ph)[G + blockIdx.x] = s2;
+    }
+  }
+  if (!grid_barrier(a.bar, a.info, a.flags)) return;
+  double rr = grid_total(slot(ph), G, sh);
+  const double bb = grid_total(slot(ph) + G, G, sh);
+  ph ^= 1;
+  double beta = 0.0;
+  int it = 0, status = 0;
+  double* pold = a.p1;
+  double* pnew = a.p0;
+  const double thresh = a.tol * sqrt(bb);
+  while (true) {
+    if (bb == 0.0 || sqrt(rr) <= thresh) break;
+    if (it >= a.maxit) { status = 1; break; }
+    // p = r + beta p (on the fly at the 7 stencil points), q = A p, p.q
+    double pq_loc = 0.0;
+    for (int64_t id = t0; id < m; id += stride) {
+      const int64_t i = id % n, j = (id / n) % n, k = id / ((int64_t)n * n);
+      const int64_t nbr[6] = {wrapi(i + 1, n) + n * (j + (int64_t)n * k), wrapi(i - 1, n) + n * (j + (int64_t)n * k),
+                              i + n * (wrapi(j + 1, n) + (int64_t)n * k), i + n * (wrapi(j - 1, n) + (int64_t)n * k),
+                              i + n * (j + (int64_t)n * wrapi(k + 1, n)), i + n * (j + (int64_t)n * wrapi(k - 1, n))};
+      double pc, nb;
+      if (it == 0) {
+        pc = a.r[id];
+        nb = a.r[nbr[0]] + a.r[nbr[1]] + a.r[nbr[2]] + a.r[nbr[3]] + a.r[nbr[4]] + a.r[nbr[5]];
+      } else {
+        pc = a.r[id] + beta * pold[id];
+        double p6[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) p6[u] = a.r[nbr[u]] + beta * pold[nbr[u]];
+        nb = p6[0] + p6[1] + p6[2] + p6[3] + p6[4] + p6[5];
+      }
+      const double qv = (6.0 * pc - nb) * a.inv_h2;
+      pnew[id] = pc;
+      a.q[id] = qv;
+      pq_loc += pc * qv;
+    }
+    {
+      const double s = block_sum(pq_loc, sh);
+      if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+    }
+    if (!grid_barrier(a.bar, a.info, a.flags)) return;
+    const double pq = grid_total(slot(ph), G, sh);
+    ph ^= 1;
+    const double alpha = rr / pq;
+    double rn_loc = 0.0;
+    for (int64_t id = t0; id < m; id += stride) {
+      a.x[id] += alpha * pnew[id];
+      const double rv = a.r[id] - alpha * a.q[id];
+      a.r[id] = rv;
+      rn_loc += rv * rv;
+    }
+    {
+      const double s = block_sum(rn_loc, sh);
+      if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+    }
+    if (!grid_barrier(a.bar, a.info, a.flags)) return;
+    const double rr_new = grid_total(slot(ph), G, sh);
+    ph ^= 1;
+    ++it;
+    beta = rr_new / rr;
+    rr = rr_new;
+    double* tmp = pold;
+    pold = pnew;
+    pnew = tmp;
+  }
+  // zero-mean projection
+  double xs = 0.0;
+  for (int64_t id = t0; id < m; id += stride) xs += a.x[id];
+  {
+    const double s = block_sum(xs, sh);
+    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+  }
+  if (!grid_barrier(a.bar, a.info, a.flags)) return;
+  const double mean_x = grid_total(slot(ph), G, sh) / (double)m;
+  ph ^= 1;
+  for (int64_t id = t0; id < m; id += stride) a.x[id] -= mean_x;
+  if (!grid_barrier(a.bar, a.info, a.flags)) return;
+  // E = -grad_h phi, second-order central differences
+  for (int64_t id = t0; id < m; id += stride) {
+    const int64_t i = id % n, j = (id / n) % n, k = id / ((int64_t)n * n);
+    const double* x = a.x;
+    a.E0[id] = -(x[wrapi(i + 1, n) + n * (j + (int64_t)n * k)] - x[wrapi(i - 1, n) + n * (j + (int64_t)n * k)]) / a.two_h;
+    a.E1[id] = -(x[i + n * (wrapi(j + 1, n) + (int64_t)n * k)] - x[i + n * (wrapi(j - 1, n) + (int64_t)n * k)]) / a.two_h;
+    a.E2[id] = -(x[i + n * (j + (int64_t)n * wrapi(k + 1, n))] - x[i + n * (j + (int64_t)n * wrapi(k - 1, n))]) / a.two_h;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.info[0] = it;
+    a.info[1] = status;
+    a.res[0] = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
+    if (status) atomicOr(a.flags, 2);
+    atomicMax(a.flags + 1, it);
+  }
+}
+
+struct StoreFieldArgs {
+  int64_t ncell;
+  const double *rho, *phi, *E0, *E1, *E2;
+  double *orho, *ophi, *oE;
+};
+
+__global__ void __launch_bounds__(kThreads) k_store_field(StoreFieldArgs a) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= a.ncell) return;
+  if (a.orho) a.orho[id] = a.rho[id];
+  if (a.ophi) a.ophi[id] = a.phi[id];
+  if (a.oE) {
+    a.oE[3 * id] = a.E0[id];
+    a.oE[3 * id + 1] = a.E1[id];
+    a.oE[3 * id + 2] = a.E2[id];
+  }
+}
+
+}  // namespace
+
+int rhs_blocks_needed(int64_t ncell) { return blocks_for(ncell); }
+
+cudaError_t launch_rhs(pic_ctx* c, double t) {
+  RhsArgs a;
+  a.P = c->P;
+  a.t = t;
+  a.corner = c->corner;
+  a.rho = c->rho;
+  a.b = c->b;
+  a.part = c->rhs_part;
+  prof_begin(c);
+  k_rhs<<<(int)c->rhs_blocks, kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_RHS);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+int cg_threads() { return kThreads; }
+const void* cg_kernel_ptr() { return (const void*)k_cg; }
+
+cudaError_t launch_cg(pic_ctx* c) {
+  CgArgs a;
+  a.n = c->P.n;
+  a.ncell = c->P.ncell;
+  a.inv_h2 = (double)c->P.n * (double)c->P.n;
+  a.two_h = 2.0 * c->P.h;
+  a.b = c->b;
+  a.x = c->phi;
+  a.r = c->cg_r;
+  a.p0 = c->cg_p[0];
+  a.p1 = c->cg_p[1];
+  a.q = c->cg_q;
+  a.rhs_part = c->rhs_part;
+  a.rhs_blocks = (int)c->rhs_blocks;
+  a.red = c->cg_red;
+  a.bar = c->cg_bar;
+  a.info = c->cg_info;
+  a.flags = c->flags;
+  a.res = c->cg_res;
+  a.tol = c->cfg.cg_tol;
+  a.maxit = c->cfg.cg_maxit;
+  a.E0 = c->E[0];
+  a.E1 = c->E[1];
+  a.E2 = c->E[2];
+  cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(c->cg_info, 0, 3 * sizeof(int), c->stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&a};
+  prof_begin(c);
+  e = cudaLaunchCooperativeKernel((const void*)k_cg, dim3(c->cg_grid), dim3(kThreads), args, 0, c->stream);
+  prof_end(c, KC_CG);
+  c->launches++;
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E) {
+  StoreFieldArgs a;
+  a.ncell = c->P.ncell;
+  a.rho = c->rho;
+  a.phi = c->phi;
+  a.E0 = c->E[0];
+  a.E1 = c->E[1];
+  a.E2 = c->E[2];
+  a.orho = rho;
+  a.ophi = phi;
+  a.oE = E;
+  prof_begin(c);
+  k_store_field<<<blocks_for(a.ncell), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace pic

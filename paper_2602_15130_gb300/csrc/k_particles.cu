@@ -1,0 +1,639 @@
+// Particle-parallel kernels: manufactured sampling (Sec. 3.2), state
+// load/store, K-averaged NTC collisions (Algorithm 1, Eq. avg_outcome) with
+// the hard-sphere source (Eq. vel_change_1c), the velocity-Verlet kick and
+// drift (Eq. velocity_verlet with the sources of Eq. eom_mms) and the error
+// norms of Sec. 4.3.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n, int t = kThreads) {
+  int64_t b = (n + t - 1) / t;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// --------------------------------------------------------------------------
+// Sampling: xi from the particle's Philox stream, x = x^M(t0), v = v^M.
+// Written in pid order into the current buffer.
+// --------------------------------------------------------------------------
+struct SampleArgs {
+  Params P;
+  double t0;
+  double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
+  uint32_t* pid;
+};
+
+__global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.P.np) return;
+  const Params& P = a.P;
+  const U4 b0 = sample_block(P, (uint64_t)i, 0), b1 = sample_block(P, (uint64_t)i, 1),
+           b2 = sample_block(P, (uint64_t)i, 2);
+  const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
+                        unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
+  double s;
+  const double X0 = xm_solve(P, xi[0], a.t0, xi[0], &s);
+  const double X1 = xm_solve(P, xi[1], a.t0, xi[1], &s);
+  const double X2 = xm_solve(P, xi[2], a.t0, xi[2], &s);
+  const double V0 = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
+  const double V1 = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
+  const double V2 = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
+  a.x0[i] = wrap_unit(X0); a.x1[i] = wrap_unit(X1); a.x2[i] = wrap_unit(X2);
+  a.xm0[i] = X0; a.xm1[i] = X1; a.xm2[i] = X2;
+  a.v0[i] = V0; a.v1[i] = V1; a.v2[i] = V2;
+  a.vm0[i] = V0; a.vm1[i] = V1; a.vm2[i] = V2;
+  a.pid[i] = (uint32_t)i;
+}
+
+// Load a caller state ([N_p][3] x then [N_p][3] v, pid order) into SoA.
+struct LoadArgs {
+  Params P;
+  double t;
+  const double* xv;  // 6 N_p: x AoS then v AoS
+  double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
+  uint32_t* pid;
+};
+
+__global__ void __launch_bounds__(kThreads) k_load_state(LoadArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.P.np) return;
+  const Params& P = a.P;
+  const U4 b0 = sample_block(P, (uint64_t)i, 0), b1 = sample_block(P, (uint64_t)i, 1),
+           b2 = sample_block(P, (uint64_t)i, 2);
+  const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
+                        unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
+  double s;
+  a.xm0[i] = xm_solve(P, xi[0], a.t, xi[0], &s);
+  a.xm1[i] = xm_solve(P, xi[1], a.t, xi[1], &s);
+  a.xm2[i] = xm_solve(P, xi[2], a.t, xi[2], &s);
+  a.vm0[i] = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
+  a.vm1[i] = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
+  a.vm2[i] = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
+  const double* xs = a.xv;
+  const double* vs = a.xv + 3 * P.np;
+  a.x0[i] = xs[3 * i]; a.x1[i] = xs[3 * i + 1]; a.x2[i] = xs[3 * i + 2];
+  a.v0[i] = vs[3 * i]; a.v1[i] = vs[3 * i + 1]; a.v2[i] = vs[3 * i + 2];
+  a.pid[i] = (uint32_t)i;
+}
+
+struct StoreArgs {
+  int64_t np;
+  const double *x0, *x1, *x2, *v0, *v1, *v2;
+  const uint32_t* pid;
+  double* xv;
+};
+
+__global__ void __launch_bounds__(kThreads) k_store_state(StoreArgs a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.np) return;
+  const int64_t p = a.pid[j];
+  a.xv[3 * p] = a.x0[j]; a.xv[3 * p + 1] = a.x1[j]; a.xv[3 * p + 2] = a.x2[j];
+  double* vs = a.xv + 3 * a.np;
+  vs[3 * p] = a.v0[j]; vs[3 * p + 1] = a.v1[j]; vs[3 * p + 2] = a.v2[j];
+}
+
+struct StoreDvArgs {
+  int64_t np;
+  const double *d0, *d1, *d2, *m0, *m1, *m2;
+  const uint32_t* pid;
+  double *dv, *dvm;
+};
+
+__global__ void __launch_bounds__(kThreads) k_store_dv(StoreDvArgs a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.np) return;
+  const int64_t p = a.pid[j];
+  a.dv[3 * p] = a.d0[j]; a.dv[3 * p + 1] = a.d1[j]; a.dv[3 * p + 2] = a.d2[j];
+  a.dvm[3 * p] = a.m0[j]; a.dvm[3 * p + 1] = a.m1[j]; a.dvm[3 * p + 2] = a.m2[j];
+}
+
+// --------------------------------------------------------------------------
+// K-averaged NTC collisions. One warp serves a group of G consecutive cells;
+// lane l runs outcome (chunk Kc + l % Kc) of cell (l / Kc) of the group,
+// sequentially over its candidate pairs with in-place updates (Algorithm 1).
+// The lane's working velocities live in a private overlay slot in global
+// memory (L1-resident in practice), valid where the lane's bitmap in shared
+// memory has the particle's bit; untouched particles are read from v.
+// After __syncwarp the warp sums each particle's per-outcome changes in
+// ascending outcome order and divides by K.
+// --------------------------------------------------------------------------
+struct DsmcArgs {
+  Params P;
+  const double *v0, *v1, *v2;
+  const int32_t* start;
+  uint32_t c0;
+  double *dv0, *dv1, *dv2;  // out: <dv> - <dv^M>, or <dv> when m0 != nullptr
+  double *m0, *m1, *m2;     // out (optional): <dv^M>
+  double* overlay;
+  int max_ppc, bm_words, G, Kc, nchunks;
+  int64_t ngroups;
+  unsigned long long* counters;
+  int* flags;
+};
+
+struct LaneCounts {
+  unsigned long long cand, coll, gmax, tie;
+};
+
+__device__ __forceinline__ void load_vel(int p, const uint32_t* bm, const double* ov, const double* v0,
+                                         const double* v1, const double* v2, double* o) {
+  if ((bm[p >> 5] >> (p & 31)) & 1u) {
+    o[0] = ov[3 * p]; o[1] = ov[3 * p + 1]; o[2] = ov[3 * p + 2];
+  } else {
+    o[0] = v0[p]; o[1] = v1[p]; o[2] = v2[p];
+  }
+}
+
+__device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_t o, int c,
+                            const double* v0, const double* v1, const double* v2, uint32_t* bm,
+                            double* ov, LaneCounts& cnt) {
+  const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
+  const double base = __dmul_rn(__dmul_rn((double)((long long)c * (long long)(c - 1)), P.pmax), 0.5);
+  const long long npairs = (long long)floor(__dadd_rn(base, unif52(u.x, u.y)));
+  for (long long s = 0; s < npairs; ++s) {
+    const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
+    const uint32_t p = draw_index(b0.x, (uint32_t)c);
+    uint32_t q = draw_index(b0.y, (uint32_t)c);
+    U4 b1;
+    bool have_b1 = false;
+    if (q == p) {
+      b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+      have_b1 = true;
+      q = draw_index(b1.y, (uint32_t)c);
+      if (q == p) q = draw_index(b1.z, (uint32_t)c);
+      if (q == p) q = draw_index(b1.w, (uint32_t)c);
+      uint32_t blk = 2;
+      while (q == p) {
+        if (blk > 255u) { q = (p + 1u) % (uint32_t)c; break; }
+        const U4 bb = philox(c0, cell, (uint32_t)s, (o << 8) | blk, P.key0, P.key1);
+        q = draw_index(bb.x, (uint32_t)c);
+        if (q == p) q = draw_index(bb.y, (uint32_t)c);
+        if (q == p) q = draw_index(bb.z, (uint32_t)c);
+        if (q == p) q = draw_index(bb.w, (uint32_t)c);
+        ++blk;
+      }
+    }
+    double vp[3], vq[3];
+    load_vel((int)p, bm, ov, v0, v1, v2, vp);
+    load_vel((int)q, bm, ov, v0, v1, v2, vq);
+    const double dx = __dsub_rn(vp[0], vq[0]), dy = __dsub_rn(vp[1], vq[1]), dz = __dsub_rn(vp[2], vq[2]);
+    const double g = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    const double ratio = __ddiv_rn(__dmul_rn(P.sigma0, g), P.sg_max);
+    const double U = unif32(b0.z);
+    ++cnt.cand;
+    if (g > P.gmax) ++cnt.gmax;
+    if (fabs(U - ratio) < 1e-12) ++cnt.tie;
+    if (U < ratio) {
+      if (!have_b1) b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+      const double eps = __dmul_rn(kTwoPi, unif32(b0.w));
+      double se, ce;
+      sincos(eps, &se, &ce);
+      const double cchi = __dsub_rn(1.0, __dmul_rn(2.0, unif32(b1.x)));
+      const double schi = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(cchi, cchi)));
+      const double nv[3] = {__dmul_rn(ce, schi), __dmul_rn(se, schi), cchi};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double gp = __dmul_rn(g, nv[d]);
+        const double cm = __dmul_rn(__dadd_rn(vp[d], vq[d]), 0.5);
+        ov[3 * p + d] = __dadd_rn(cm, __dmul_rn(gp, 0.5));
+        ov[3 * q + d] = __dsub_rn(cm, __dmul_rn(gp, 0.5));
+      }
+      bm[p >> 5] |= 1u << (p & 31);
+      bm[q >> 5] |= 1u << (q & 31);
+      ++cnt.coll;
+    }
+  }
+}
+
+constexpr int kDsmcThreads = 128;
+
+__global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
+  extern __shared__ uint32_t smem[];
+  const Params& P = a.P;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int64_t gwarp = (int64_t)blockIdx.x * wpb + wib;
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  uint32_t* wbm = smem + (size_t)wib * 32 * a.bm_words;     // warp's 32 bitmaps
+  uint32_t* bm = wbm + (size_t)lane * a.bm_words;            // this lane's
+  double* wov = a.overlay + (size_t)gwarp * 32 * a.max_ppc * 3;
+  double* ov = wov + (size_t)lane * a.max_ppc * 3;
+  for (int i = 0; i < a.bm_words; ++i) bm[i] = 0u;
+  __syncwarp();
+  LaneCounts cnt = {0, 0, 0, 0};
+  const bool separate = a.m0 != nullptr;
+
+  for (int64_t grp = gwarp; grp < a.ngroups; grp += nwarps) {
+    const int64_t cell0 = grp * a.G;
+    const int ncl = (int)min((int64_t)a.G, P.ncell - cell0);  // cells in this group
+    const int mycl = lane / a.Kc;
+    const bool lane_cell = mycl < ncl;
+    int32_t s = 0, c = 0;
+    if (lane_cell) {
+      s = a.start[cell0 + mycl];
+      c = a.start[cell0 + mycl + 1] - s;
+    }
+    const int32_t gs = a.start[cell0], ge = a.start[cell0 + ncl];
+    for (int ch = 0; ch < a.nchunks; ++ch) {
+      const int o = ch * a.Kc + lane % a.Kc;
+      bool run = lane_cell && o < P.K && c >= 2;
+      if (run && c > a.max_ppc) {
+        atomicOr(a.flags, 1);
+        run = false;
+      }
+      if (run)
+        ntc_outcome(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s, bm,
+                    ov, cnt);
+      __syncwarp();
+      // sum this chunk's changes per particle in ascending outcome order
+      const bool last = ch == a.nchunks - 1;
+      for (int32_t j = gs + lane; j < ge; j += 32) {
+        int cl = 0;
+        while (cl + 1 < ncl && a.start[cell0 + cl + 1] <= j) ++cl;
+        const int32_t cs = a.start[cell0 + cl];
+        const int cc = a.start[cell0 + cl + 1] - cs;
+        const int jj = j - cs;
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+        if (ch > 0) { acc0 = a.dv0[j]; acc1 = a.dv1[j]; acc2 = a.dv2[j]; }
+        if (cc >= 2 && cc <= a.max_ppc) {
+          const double w0 = a.v0[j], w1 = a.v1[j], w2 = a.v2[j];
+          for (int k = 0; k < a.Kc; ++k) {
+            if (ch * a.Kc + k >= P.K) break;
+            const int L = cl * a.Kc + k;
+            if ((wbm[(size_t)L * a.bm_words + (jj >> 5)] >> (jj & 31)) & 1u) {
+              const double* W = wov + ((size_t)L * a.max_ppc + jj) * 3;
+              acc0 = __dadd_rn(acc0, __dsub_rn(W[0], w0));
+              acc1 = __dadd_rn(acc1, __dsub_rn(W[1], w1));
+              acc2 = __dadd_rn(acc2, __dsub_rn(W[2], w2));
+            }
+          }
+        }
+        if (!last) {
+          a.dv0[j] = acc0; a.dv1[j] = acc1; a.dv2[j] = acc2;
+        } else {
+          const double K = (double)P.K;
+          const double m0 = acc0 / K, m1 = acc1 / K, m2 = acc2 / K;
+          double s0, s1, s2;
+          hs_source(P, a.v0[j], a.v1[j], a.v2[j], cc, &s0, &s1, &s2);
+          if (separate) {
+            a.dv0[j] = m0; a.dv1[j] = m1; a.dv2[j] = m2;
+            a.m0[j] = s0; a.m1[j] = s1; a.m2[j] = s2;
+          } else {
+            a.dv0[j] = m0 - s0; a.dv1[j] = m1 - s1; a.dv2[j] = m2 - s2;
+          }
+        }
+      }
+      __syncwarp();
+      if (run)
+        for (int i = 0; i < (c + 31) / 32; ++i) bm[i] = 0u;
+      __syncwarp();
+    }
+  }
+  // warp totals, one atomic per counter per warp
+  for (int off = 16; off > 0; off >>= 1) {
+    cnt.cand += __shfl_down_sync(0xffffffffu, cnt.cand, off);
+    cnt.coll += __shfl_down_sync(0xffffffffu, cnt.coll, off);
+    cnt.gmax += __shfl_down_sync(0xffffffffu, cnt.gmax, off);
+    cnt.tie += __shfl_down_sync(0xffffffffu, cnt.tie, off);
+  }
+  if (lane == 0) {
+    if (cnt.cand) atomicAdd(a.counters + 0, cnt.cand);
+    if (cnt.coll) atomicAdd(a.counters + 1, cnt.coll);
+    if (cnt.gmax) atomicAdd(a.counters + 2, cnt.gmax);
+    if (cnt.tie) atomicAdd(a.counters + 3, cnt.tie);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Kick (and optionally drift) in sorted order:
+//   v += 1/2 (dt q/m (E_p - E^M_p) + dv + dt vdot^M),   vdot^M = 0 here,
+//   x += dt (v + xdot^M - v^M) at t_half (drift), wrapped; new cell key.
+// --------------------------------------------------------------------------
+struct KickArgs {
+  Params P;
+  double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2;
+  const double *vm0, *vm1, *vm2;
+  const uint32_t* pid;
+  const double *dv0, *dv1, *dv2;
+  const double *E0, *E1, *E2;
+  double tE, th;
+  int drift;
+  int32_t *key, *rank, *count;
+};
+
+__device__ __forceinline__ void gather_E(const Params& P, const double* E0, const double* E1, const double* E2,
+                                         double x, double y, double z, double* e) {
+  const int n = P.n;
+  const double un = x * (double)n, vn = y * (double)n, wn = z * (double)n;
+  const int i = cell_coord(x, n), j = cell_coord(y, n), k = cell_coord(z, n);
+  const double fx = un - (double)i, fy = vn - (double)j, fz = wn - (double)k;
+  const int i1 = i + 1 == n ? 0 : i + 1, j1 = j + 1 == n ? 0 : j + 1, k1 = k + 1 == n ? 0 : k + 1;
+  const double wx[2] = {1.0 - fx, fx}, wy[2] = {1.0 - fy, fy}, wz[2] = {1.0 - fz, fz};
+  const int ii[2] = {i, i1}, jj[2] = {j, j1}, kk[2] = {k, k1};
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int64_t node = ii[a] + (int64_t)n * (jj[b] + (int64_t)n * kk[c]);
+        const double ww = wx[a] * wy[b] * wz[c];
+        a0 += ww * __ldg(E0 + node);
+        a1 += ww * __ldg(E1 + node);
+        a2 += ww * __ldg(E2 + node);
+      }
+  e[0] = a0; e[1] = a1; e[2] = a2;
+}
+
+__global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Params& P = a.P;
+  if (j >= P.np) return;
+  double x[3] = {a.x0[j], a.x1[j], a.x2[j]};
+  double v[3] = {a.v0[j], a.v1[j], a.v2[j]};
+  double Ep[3], EM[3];
+  gather_E(P, a.E0, a.E1, a.E2, x[0], x[1], x[2], Ep);
+  e_manufactured(P, x[0], x[1], x[2], a.tE, &EM[0], &EM[1], &EM[2]);
+  double dv[3] = {0.0, 0.0, 0.0};
+  if (a.dv0) { dv[0] = a.dv0[j]; dv[1] = a.dv1[j]; dv[2] = a.dv2[j]; }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double L = P.dt * P.qm_eff * (Ep[d] - EM[d]);
+    v[d] = v[d] + 0.5 * (L + dv[d]);
+  }
+  a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
+  if (!a.drift) return;
+  const uint64_t p = a.pid[j];
+  const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1);
+  const double xi[3] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y)};
+  double* xmp[3] = {a.xm0, a.xm1, a.xm2};
+  const double vm[3] = {a.vm0[j], a.vm1[j], a.vm2[j]};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double s;
+    const double xmv = xm_solve(P, xi[d], a.th, xmp[d][j], &s);
+    xmp[d][j] = xmv;
+    const double xd = xm_dot(P, s, a.th);
+    x[d] = wrap_unit(x[d] + P.dt * (v[d] + xd - vm[d]));
+  }
+  a.x0[j] = x[0]; a.x1[j] = x[1]; a.x2[j] = x[2];
+  const int n = P.n;
+  const int32_t k = cell_coord(x[0], n) + n * (cell_coord(x[1], n) + n * cell_coord(x[2], n));
+  a.key[j] = k;
+  a.rank[j] = atomicAdd(a.count + k, 1);
+}
+
+// --------------------------------------------------------------------------
+// Error norms (Sec. 4.3): per-block partial sums of squares and maxima of
+// e = alpha - alpha^M for x, y, z (minimum image), u, v, w; then phi over
+// nodes; a single block combines the partials in fixed order.
+// --------------------------------------------------------------------------
+struct ErrArgs {
+  Params P;
+  double t;
+  const double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
+  const uint32_t* pid;
+  const double* phi;
+  double* part;  // [blocks][14]: 7 sums then 7 maxima
+  int pblocks;   // blocks over particles; the rest cover nodes
+  double* out;
+};
+
+__device__ __forceinline__ void block_reduce_14(double* vals, double* sh) {
+  // vals[0..6] summed, vals[7..13] max-reduced; result in thread 0
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 14; ++q) {
+    double x = vals[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, off);
+      x = q < 7 ? x + y : fmax(x, y);
+    }
+    if (lane == 0) sh[w * 14 + q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 14; ++q) {
+      double x = sh[q];
+      for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) x = q < 7 ? x + sh[ww * 14 + q] : fmax(x, sh[ww * 14 + q]);
+      vals[q] = x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_err_partial(ErrArgs a) {
+  __shared__ double sh[(kThreads / 32) * 14];
+  const Params& P = a.P;
+  double vals[14];
+#pragma unroll
+  for (int q = 0; q < 14; ++q) vals[q] = 0.0;
+  if ((int)blockIdx.x < a.pblocks) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < P.np) {
+      const uint64_t p = a.pid[j];
+      const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1);
+      const double xi[3] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y)};
+      const double xs[3] = {a.x0[j], a.x1[j], a.x2[j]};
+      const double vs[3] = {a.v0[j], a.v1[j], a.v2[j]};
+      const double guess[3] = {a.xm0[j], a.xm1[j], a.xm2[j]};
+      const double vms[3] = {a.vm0[j], a.vm1[j], a.vm2[j]};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double s;
+        const double xm = xm_solve(P, xi[d], a.t, guess[d], &s);
+        double e = xs[d] - xm;
+        e -= floor(e + 0.5);
+        vals[d] = e * e;
+        vals[7 + d] = fabs(e);
+        const double ev = vs[d] - vms[d];
+        vals[3 + d] = ev * ev;
+        vals[10 + d] = fabs(ev);
+      }
+    }
+  } else {
+    const int64_t id = (int64_t)(blockIdx.x - a.pblocks) * blockDim.x + threadIdx.x;
+    if (id < P.ncell) {
+      const int n = P.n;
+      const int i = (int)(id % n), jj = (int)((id / n) % n), k = (int)(id / ((int64_t)n * n));
+      const double X = i * P.h, Y = jj * P.h, Z = k * P.h;
+      double s0, s1, s2;
+      s0 = sinpi(2.0 * (X - P.phi_shift[0]));
+      s1 = sinpi(2.0 * (Y - P.phi_shift[1]));
+      s2 = sinpi(2.0 * (Z - P.phi_shift[2]));
+      const double phiM = P.phi_amp * exp(a.t / (2.0 * P.phi_T)) * s0 * s1 * s2;
+      const double e = a.phi[id] - phiM;
+      vals[6] = e * e;
+      vals[13] = fabs(e);
+    }
+  }
+  block_reduce_14(vals, sh);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 14; ++q) a.part[(size_t)blockIdx.x * 14 + q] = vals[q];
+}
+
+__global__ void k_err_final(ErrArgs a, int nblocks) {
+  // one thread per quantity, fixed block order
+  const int q = threadIdx.x;
+  if (q >= 14) return;
+  double x = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    const double y = a.part[(size_t)b * 14 + q];
+    x = q < 7 ? x + y : fmax(x, y);
+  }
+  if (q < 6) x = sqrt(x / (double)a.P.np);
+  else if (q == 6) x = sqrt(x / (double)a.P.ncell);
+  a.out[q] = x;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_sample(pic_ctx* c, double t0) {
+  SampleArgs a;
+  a.P = c->P;
+  a.t0 = t0;
+  const int b = c->cur;
+  a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
+  a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
+  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
+  a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
+  a.pid = c->pid[b];
+  prof_begin(c);
+  k_sample<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_SAMPLE);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_state(pic_ctx* c, const double* xv, double t) {
+  LoadArgs a;
+  a.P = c->P;
+  a.t = t;
+  a.xv = xv;
+  const int b = c->cur;
+  a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
+  a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
+  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
+  a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
+  a.pid = c->pid[b];
+  prof_begin(c);
+  k_load_state<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_state(pic_ctx* c, double* xv) {
+  StoreArgs a;
+  a.np = c->P.np;
+  const int b = c->cur;
+  a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
+  a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
+  a.pid = c->pid[b];
+  a.xv = xv;
+  prof_begin(c);
+  k_store_state<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm) {
+  StoreDvArgs a;
+  a.np = c->P.np;
+  a.d0 = c->dv[0]; a.d1 = c->dv[1]; a.d2 = c->dv[2];
+  a.m0 = c->dvm[0]; a.m1 = c->dvm[1]; a.m2 = c->dvm[2];
+  a.pid = c->pid[c->cur];
+  a.dv = dv;
+  a.dvm = dvm;
+  prof_begin(c);
+  k_store_dv<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate) {
+  DsmcArgs a;
+  a.P = c->P;
+  const int b = c->cur;
+  a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
+  a.start = c->start;
+  a.c0 = c0;
+  a.dv0 = c->dv[0]; a.dv1 = c->dv[1]; a.dv2 = c->dv[2];
+  if (separate) { a.m0 = c->dvm[0]; a.m1 = c->dvm[1]; a.m2 = c->dvm[2]; }
+  else { a.m0 = a.m1 = a.m2 = nullptr; }
+  a.overlay = c->overlay;
+  a.max_ppc = c->cfg.max_ppc;
+  a.bm_words = c->bm_words;
+  a.G = c->dsmc_G;
+  a.Kc = c->dsmc_Kc;
+  a.nchunks = (c->P.K + c->dsmc_Kc - 1) / c->dsmc_Kc;
+  a.ngroups = c->dsmc_groups;
+  a.counters = c->counters;
+  a.flags = c->flags;
+  prof_begin(c);
+  k_dsmc<<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
+  prof_end(c, KC_DSMC);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+int dsmc_threads() { return kDsmcThreads; }
+const void* dsmc_kernel_ptr() { return (const void*)k_dsmc; }
+
+cudaError_t launch_kick(pic_ctx* c, double tE, bool with_coll, bool drift, double th) {
+  KickArgs a;
+  a.P = c->P;
+  const int b = c->cur;
+  a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
+  a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
+  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
+  a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
+  a.pid = c->pid[b];
+  if (with_coll) { a.dv0 = c->dv[0]; a.dv1 = c->dv[1]; a.dv2 = c->dv[2]; }
+  else { a.dv0 = a.dv1 = a.dv2 = nullptr; }
+  a.E0 = c->E[0]; a.E1 = c->E[1]; a.E2 = c->E[2];
+  a.tE = tE;
+  a.th = th;
+  a.drift = drift ? 1 : 0;
+  a.key = c->key;
+  a.rank = c->rank;
+  a.count = c->count;
+  prof_begin(c);
+  k_kick<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_KICK);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_errors(pic_ctx* c, double t) {
+  ErrArgs a;
+  a.P = c->P;
+  a.t = t;
+  const int b = c->cur;
+  a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
+  a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
+  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
+  a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
+  a.pid = c->pid[b];
+  a.phi = c->phi;
+  a.part = c->err_part;
+  a.pblocks = blocks_for(c->P.np);
+  a.out = c->err_out;
+  const int nb = a.pblocks + blocks_for(c->P.ncell);
+  prof_begin(c);
+  k_err_partial<<<nb, kThreads, 0, c->stream>>>(a);
+  k_err_final<<<1, 32, 0, c->stream>>>(a, nb);
+  prof_end(c, KC_ERR);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+int err_blocks_needed(int64_t np, int64_t ncell) { return blocks_for(np) + blocks_for(ncell); }
+
+}  // namespace pic

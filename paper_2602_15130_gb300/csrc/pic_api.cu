@@ -1,0 +1,616 @@
+// Host runtime and C ABI (include/pic.h): configuration checks, derived
+// constants, device buffers, the step schedule of Eq. velocity_verlet and
+// the boundary copies.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+int dsmc_threads();
+const void* dsmc_kernel_ptr();
+int cg_threads();
+const void* cg_kernel_ptr();
+int64_t scan_blocks_needed(int64_t ncell);
+int rhs_blocks_needed(int64_t ncell);
+int err_blocks_needed(int64_t np, int64_t ncell);
+
+// Resolve recorded event pairs into per-class totals (synchronises).
+void prof_flush(pic_ctx* c) {
+  if (c->ev_used == 0) return;
+  cudaEventSynchronize(c->ev_pool[2 * (c->ev_used - 1) + 1]);
+  for (int i = 0; i < c->ev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]) == cudaSuccess) {
+      c->prof_ms[c->ev_class[i]] += ms;
+      c->prof_launches[c->ev_class[i]] += 1;
+    }
+  }
+  c->ev_used = 0;
+  cudaGetLastError();
+}
+
+static bool prof_slot(pic_ctx* c) {
+  if (c->ev_used < c->ev_cap) return true;
+  if (c->ev_cap >= 1 << 16) {
+    prof_flush(c);
+    return true;
+  }
+  const int cap = c->ev_cap ? 2 * c->ev_cap : 256;
+  cudaEvent_t* pool = (cudaEvent_t*)realloc(c->ev_pool, sizeof(cudaEvent_t) * 2 * cap);
+  if (!pool) return false;
+  c->ev_pool = pool;
+  int* cls = (int*)realloc(c->ev_class, sizeof(int) * cap);
+  if (!cls) return false;
+  c->ev_class = cls;
+  for (int i = 2 * c->ev_cap; i < 2 * cap; ++i)
+    if (cudaEventCreate(&c->ev_pool[i]) != cudaSuccess) return false;
+  c->ev_cap = cap;
+  return true;
+}
+
+void prof_begin(pic_ctx* c) {
+  if (!c->profiling || !prof_slot(c)) return;
+  cudaEventRecord(c->ev_pool[2 * c->ev_used], c->stream);
+}
+void prof_end(pic_ctx* c, int kclass) {
+  if (!c->profiling || c->ev_used >= c->ev_cap) return;
+  cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], c->stream);
+  c->ev_class[c->ev_used] = kclass;
+  c->ev_used++;
+}
+}  // namespace pic
+
+using namespace pic;
+
+namespace {
+
+// R(a) small-argument series: R = sqrt(2/pi) sum_j c_j a^{2j},
+// c_j = d_j + d_{j+1} + e_{j-1} + 2 e_j - e_{j+1}, with d_k the Taylor
+// coefficients of e^{-a^2/2} and e_k those of sqrt(pi/2) erf(a/sqrt 2).
+void series_coefficients(double* out) {
+  double d[kSeriesTerms + 2], e[kSeriesTerms + 2];
+  double fact = 1.0, pw = 1.0;
+  for (int k = 0; k < kSeriesTerms + 2; ++k) {
+    if (k > 0) { fact *= k; pw *= 2.0; }
+    const double sg = (k & 1) ? -1.0 : 1.0;
+    d[k] = sg / (pw * fact);
+    e[k] = sg / (pw * fact * (2.0 * k + 1.0));
+  }
+  const double s = sqrt(2.0 / kPi);
+  for (int j = 0; j < kSeriesTerms; ++j)
+    out[j] = s * (d[j] + d[j + 1] + (j > 0 ? e[j - 1] : 0.0) + 2.0 * e[j] - e[j + 1]);
+}
+
+void derive_params(const pic_config& c, Params& P) {
+  memset(&P, 0, sizeof(P));
+  P.n = c.n;
+  P.K = c.K;
+  P.ncell = (int64_t)c.n * c.n * c.n;
+  P.np = c.n_particles;
+  P.dt = c.dt;
+  P.qm_eff = c.couple_qm_zero ? 0.0 : c.qm;
+  P.q_eff = c.couple_q_zero ? 0.0 : c.q;
+  P.eps0 = c.eps0;
+  P.nphys = c.n_phys;
+  P.sigma0 = c.sigma0;
+  P.gmax = c.g_max;
+  P.fx_amp = c.fx_amp;
+  P.fx_speed = c.fx_speed;
+  P.fx_amp_over_2pi = c.fx_amp / (2.0 * kPi);
+  for (int d = 0; d < 3; ++d) {
+    P.vmean[d] = c.v_mean[d];
+    P.phi_shift[d] = c.phi_shift[d];
+  }
+  P.vsig = c.v_sigma;
+  P.phi_amp = c.phi_amp;
+  P.phi_T = c.phi_T;
+  P.key0 = (uint32_t)(c.seed & 0xFFFFFFFFull);
+  P.key1 = (uint32_t)(c.seed >> 32);
+  P.h = 1.0 / (double)c.n;
+  P.dV = P.h * P.h * P.h;
+  P.w = c.n_phys / (double)c.n_particles;
+  P.sg_max = c.sigma0 * c.g_max;
+  P.pmax = P.sg_max * P.w * c.dt / P.dV;
+  P.rho_scale = P.q_eff * P.w / P.dV;
+  P.src_pref = P.w * c.dt * c.sigma0 / (2.0 * P.dV);
+  series_coefficients(P.R_series);
+}
+
+pic_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PIC_OK;
+  if (e == cudaErrorMemoryAllocation) return PIC_ENOMEM;
+  return PIC_ECUDA;
+}
+
+void* dev_alloc(pic_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (c->have_alloc) return c->alloc.alloc(c->alloc.user, (uint64_t)bytes);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(pic_ctx* c, void* p) {
+  if (!p) return;
+  if (c->have_alloc) c->alloc.free(c->alloc.user, p);
+  else cudaFree(p);
+}
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+// Every device array of the context, in one list for allocation and release.
+template <class F>
+void for_each_buffer(pic_ctx* c, F f) {
+  const size_t np = (size_t)c->P.np, nc = (size_t)c->P.ncell;
+  for (int b = 0; b < 2; ++b) {
+    for (int d = 0; d < 3; ++d) {
+      f((void**)&c->x[b][d], np * 8);
+      f((void**)&c->v[b][d], np * 8);
+      f((void**)&c->xm[b][d], np * 8);
+      f((void**)&c->vm[b][d], np * 8);
+    }
+    f((void**)&c->pid[b], np * 4);
+  }
+  f((void**)&c->key, np * 4);
+  f((void**)&c->rank, np * 4);
+  f((void**)&c->perm, np * 4);
+  f((void**)&c->count, nc * 4);
+  f((void**)&c->start, (nc + 1) * 4);
+  f((void**)&c->scan_blocks, (size_t)c->scan_nblocks * 4 + 16);
+  for (int d = 0; d < 3; ++d) {
+    f((void**)&c->dv[d], np * 8);
+    f((void**)&c->dvm[d], np * 8);
+    f((void**)&c->E[d], nc * 8);
+  }
+  f((void**)&c->corner, 8 * nc * 8);
+  f((void**)&c->rho, nc * 8);
+  f((void**)&c->b, nc * 8);
+  f((void**)&c->rhs_part, (size_t)c->rhs_blocks * 8);
+  f((void**)&c->phi, nc * 8);
+  f((void**)&c->cg_r, nc * 8);
+  f((void**)&c->cg_p[0], nc * 8);
+  f((void**)&c->cg_p[1], nc * 8);
+  f((void**)&c->cg_q, nc * 8);
+  f((void**)&c->cg_red, (size_t)4 * c->cg_grid * 8);
+  f((void**)&c->cg_bar, 64);
+  f((void**)&c->cg_info, 64);
+  f((void**)&c->cg_res, 64);
+  f((void**)&c->overlay, (size_t)c->dsmc_grid * (c->dsmc_block / 32) * 32 * (size_t)c->cfg.max_ppc * 3 * 8);
+  f((void**)&c->counters, 8 * 8);
+  f((void**)&c->flags, 64);
+  f((void**)&c->err_part, (size_t)c->err_blocks * 14 * 8);
+  f((void**)&c->err_out, 14 * 8);
+  f((void**)&c->stage, 6 * np * 8);
+  f((void**)&c->stage_i, (np + 1) * 4);
+}
+
+// Read and clear the sticky device flags of the work enqueued so far
+// (synchronises the stream).
+pic_status check_pending(pic_ctx* c) {
+  int info[3] = {0, 0, 0};
+  int flags[2] = {0, 0};
+  double res = 0.0;
+  CK(cudaMemcpyAsync(info, c->cg_info, sizeof(info), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(flags, c->flags, sizeof(flags), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&res, c->cg_res, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(flags), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->cg_iters_last = info[0];
+  if (flags[1] > c->cg_iters_max) c->cg_iters_max = flags[1];
+  c->cg_res_last = res;
+  if (flags[0] & 4) return PIC_ETIMEOUT;
+  if (flags[0] & 1) return PIC_ECAPACITY;
+  if (flags[0] & 2) return PIC_ENOCONV;
+  return PIC_OK;
+}
+
+// sort by (cell, pid) from the current positions and solve the field at t
+pic_status sort_and_field(pic_ctx* c, double t) {
+  CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+  CK(launch_keys(c));
+  CK(launch_sort(c));
+  CK(launch_rhs(c, t));
+  CK(launch_cg(c));
+  return PIC_OK;
+}
+
+double time_at(const pic_ctx* c, double steps) { return c->t0 + steps * c->cfg.dt; }
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_config_default(pic_config* cfg) {
+  if (!cfg) return PIC_EINVAL;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->n = 8;
+  cfg->K = 16;
+  cfg->n_particles = 4096;
+  cfg->dt = 0.01;
+  cfg->qm = cfg->q = cfg->eps0 = cfg->n_phys = 1.0;
+  const double ppc = 4096.0 / 512.0, mean_g = 4.0 / sqrt(kPi);
+  cfg->sigma0 = 0.1 * ppc / ((ppc - 1.0) * mean_g * cfg->dt);
+  cfg->g_max = 10.0 * sqrt(3.0);
+  cfg->fx_amp = 0.3;
+  cfg->fx_speed = 0.1;
+  cfg->v_mean[0] = cfg->v_mean[1] = cfg->v_mean[2] = 0.2;
+  cfg->v_sigma = 1.0;
+  cfg->phi_amp = 0.1;
+  cfg->phi_T = 1.0;
+  cfg->phi_shift[0] = 1.0 / 7.0;
+  cfg->phi_shift[1] = 1.0 / 5.0;
+  cfg->phi_shift[2] = 1.0 / 3.0;
+  cfg->precision = PIC_FP64;
+  cfg->max_ppc = 512;
+  cfg->seed = 0;
+  cfg->cg_tol = 1e-10;
+  cfg->cg_maxit = 20000;
+  return PIC_OK;
+}
+
+pic_status pic_validate_config(const pic_config* c) {
+  if (!c) return PIC_EINVAL;
+  if (c->n < 2 || c->n > 1024) return PIC_EINVAL;
+  if (c->n_particles < 1 || c->n_particles > 2147483647LL) return PIC_EINVAL;
+  if (c->K < 0 || c->K > (1 << 20)) return PIC_EINVAL;
+  if (!(c->dt > 0.0) || !isfinite(c->dt)) return PIC_EINVAL;
+  if (!isfinite(c->qm) || !isfinite(c->q) || !(c->eps0 > 0.0) || !(c->n_phys > 0.0)) return PIC_EINVAL;
+  if (c->K > 0 && (!(c->sigma0 >= 0.0) || !(c->g_max > 0.0))) return PIC_EINVAL;
+  if (!(fabs(c->fx_amp) < 1.0) || !isfinite(c->fx_speed)) return PIC_EINVAL;
+  if (!(c->v_sigma > 0.0)) return PIC_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!isfinite(c->v_mean[d]) || !isfinite(c->phi_shift[d])) return PIC_EINVAL;
+  if (!isfinite(c->phi_amp) || !(c->phi_T > 0.0)) return PIC_EINVAL;
+  if (c->precision != PIC_FP64) return PIC_EINVAL;
+  if (c->max_ppc < 0 || c->max_ppc > 65536) return PIC_EINVAL;
+  if (!(c->cg_tol > 0.0) || c->cg_maxit < 1) return PIC_EINVAL;
+  const int64_t ncell = (int64_t)c->n * c->n * c->n;
+  if (ncell > 2147483647LL) return PIC_EINVAL;
+  return PIC_OK;
+}
+
+pic_status pic_derived(const pic_config* cfg, double out[5]) {
+  if (!cfg || !out) return PIC_EINVAL;
+  pic_status s = pic_validate_config(cfg);
+  if (s != PIC_OK) return s;
+  Params P;
+  derive_params(*cfg, P);
+  out[0] = P.w;
+  out[1] = P.dV;
+  out[2] = P.pmax;
+  out[3] = (double)P.np / (double)P.ncell;
+  out[4] = P.pmax > 0.0 ? 1.0 / P.pmax : INFINITY;
+  return PIC_OK;
+}
+
+void pic_destroy(pic_ctx* c) {
+  if (!c) return;
+  for_each_buffer(c, [&](void** p, size_t) {
+    dev_free(c, *p);
+    *p = nullptr;
+  });
+  for (int i = 0; i < 2 * c->ev_cap; ++i) cudaEventDestroy(c->ev_pool[i]);
+  free(c->ev_pool);
+  free(c->ev_class);
+  delete c;
+}
+
+pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* alloc, pic_ctx** out) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  pic_status s = pic_validate_config(cfg);
+  if (s != PIC_OK) return s;
+  if (alloc && (!alloc->alloc || !alloc->free)) return PIC_EINVAL;
+  pic_ctx* c = new (std::nothrow) pic_ctx();
+  if (!c) return PIC_ENOMEM;
+  memset((void*)c, 0, sizeof(*c));
+  c->cfg = *cfg;
+  if (c->cfg.max_ppc == 0) c->cfg.max_ppc = 512;
+  c->cfg.max_ppc = (c->cfg.max_ppc + 31) / 32 * 32;
+  c->stream = (cudaStream_t)stream;
+  if (alloc) {
+    c->alloc = *alloc;
+    c->have_alloc = true;
+  }
+  derive_params(c->cfg, c->P);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  int coop = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+  if (e != cudaSuccess || !coop) {
+    cudaGetLastError();
+    delete c;
+    return PIC_ECUDA;
+  }
+  // launch geometry
+  c->scan_nblocks = scan_blocks_needed(c->P.ncell);
+  c->rhs_blocks = rhs_blocks_needed(c->P.ncell);
+  c->err_blocks = err_blocks_needed(c->P.np, c->P.ncell);
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_kernel_ptr(), cg_threads(), 0);
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    delete c;
+    return PIC_ECUDA;
+  }
+  c->cg_block = cg_threads();
+  int64_t cg_need = (c->P.ncell + c->cg_block - 1) / c->cg_block;
+  c->cg_grid = (int)(cg_need < (int64_t)occ * c->num_sms ? cg_need : (int64_t)occ * c->num_sms);
+  if (c->cg_grid < 1) c->cg_grid = 1;
+  // collisions: lanes = (cell in group, outcome); bitmaps in shared memory
+  const int K = c->cfg.K > 0 ? c->cfg.K : 1;
+  c->dsmc_Kc = K < 32 ? K : 32;
+  c->dsmc_G = K < 32 ? 32 / K : 1;
+  c->dsmc_groups = (c->P.ncell + c->dsmc_G - 1) / c->dsmc_G;
+  c->bm_words = c->cfg.max_ppc / 32;
+  c->dsmc_block = dsmc_threads();
+  c->dsmc_smem = (size_t)(c->dsmc_block / 32) * 32 * c->bm_words * 4;
+  if (c->dsmc_smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(dsmc_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->dsmc_smem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return PIC_EINVAL;
+    }
+  }
+  int docc = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&docc, dsmc_kernel_ptr(), c->dsmc_block, c->dsmc_smem);
+  if (e != cudaSuccess || docc < 1) {
+    cudaGetLastError();
+    delete c;
+    return PIC_ECUDA;
+  }
+  const int64_t wpb = c->dsmc_block / 32;
+  int64_t dgrid = (c->dsmc_groups + wpb - 1) / wpb;
+  if (dgrid > (int64_t)docc * c->num_sms) dgrid = (int64_t)docc * c->num_sms;
+  c->dsmc_grid = (int)(dgrid < 1 ? 1 : dgrid);
+  if (c->cfg.K == 0) c->dsmc_grid = 1;
+
+  bool ok = true;
+  for_each_buffer(c, [&](void** p, size_t bytes) {
+    if (!ok) return;
+    *p = dev_alloc(c, bytes);
+    if (!*p) ok = false;
+  });
+  if (!ok) {
+    pic_destroy(c);
+    return PIC_ENOMEM;
+  }
+  e = cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cg_info, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cg_res, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pic_destroy(c);
+    return cuda_status(e);
+  }
+  c->cur = 0;
+  *out = c;
+  return PIC_OK;
+}
+
+pic_status pic_sample_mms(pic_ctx* c, double t0) {
+  if (!c || !isfinite(t0)) return PIC_EINVAL;
+  c->t0 = t0;
+  c->step = 0;
+  c->cur = 0;
+  CK(cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream));
+  CK(launch_sample(c, t0));
+  pic_status s = sort_and_field(c, t0);
+  if (s != PIC_OK) return s;
+  c->sampled = true;
+  return check_pending(c);
+}
+
+pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0, int64_t step) {
+  if (!c || !x || !v || !isfinite(t0) || step < 0) return PIC_EINVAL;
+  const size_t bytes = (size_t)c->P.np * 3 * 8;
+  CK(cudaMemcpyAsync(c->stage, x, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(c->stage + 3 * c->P.np, v, bytes, cudaMemcpyDefault, c->stream));
+  c->t0 = t0;
+  c->step = step;
+  c->cur = 0;
+  CK(launch_load_state(c, c->stage, time_at(c, (double)step)));
+  pic_status s = sort_and_field(c, time_at(c, (double)step));
+  if (s != PIC_OK) return s;
+  c->sampled = true;
+  return check_pending(c);
+}
+
+pic_status pic_step(pic_ctx* c, int32_t nsteps) {
+  if (!c || nsteps < 0) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  const bool coll = c->cfg.K > 0;
+  for (int32_t it = 0; it < nsteps; ++it) {
+    const int64_t n = c->step;
+    const double tn = time_at(c, (double)n), th = time_at(c, (double)n + 0.5), tn1 = time_at(c, (double)(n + 1));
+    // v^{n+1/2} and x^{n+1}: collision call A at (x^n, v^n)
+    if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n), false));
+    CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+    CK(launch_kick(c, tn, coll, true, th));
+    // cells of x^{n+1}, field at t^{n+1}
+    CK(launch_sort(c));
+    CK(launch_rhs(c, tn1));
+    CK(launch_cg(c));
+    // v^{n+1}: collision call B at (x^{n+1}, v^{n+1/2})
+    if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n + 1), false));
+    CK(launch_kick(c, tn1, coll, false, 0.0));
+    c->step = n + 1;
+  }
+  return nsteps > 0 ? check_pending(c) : PIC_OK;
+}
+
+pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
+  if (!c || !dv || !dvM || (phase != 0 && phase != 1)) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  const size_t bytes = (size_t)c->P.np * 3 * 8;
+  if (c->cfg.K > 0) {
+    CK(launch_dsmc(c, (uint32_t)(2 * c->step + phase), true));
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      CK(cudaMemsetAsync(c->dv[d], 0, (size_t)c->P.np * 8, c->stream));
+      CK(cudaMemsetAsync(c->dvm[d], 0, (size_t)c->P.np * 8, c->stream));
+    }
+  }
+  CK(launch_store_dv(c, c->stage, c->stage + 3 * c->P.np));
+  CK(cudaMemcpyAsync(dv, c->stage, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(dvM, c->stage + 3 * c->P.np, bytes, cudaMemcpyDefault, c->stream));
+  return check_pending(c);
+}
+
+pic_status pic_mms_error(pic_ctx* c, pic_errors* out) {
+  if (!c || !out) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  CK(launch_errors(c, time_at(c, (double)c->step)));
+  double h[14];
+  CK(cudaMemcpyAsync(h, c->err_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int q = 0; q < 7; ++q) {
+    out->eps2[q] = h[q];
+    out->epsinf[q] = h[7 + q];
+  }
+  return check_pending(c);
+}
+
+pic_status pic_get_state(pic_ctx* c, double* x, double* v) {
+  if (!c || !x || !v) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  const size_t bytes = (size_t)c->P.np * 3 * 8;
+  CK(launch_store_state(c, c->stage));
+  CK(cudaMemcpyAsync(x, c->stage, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(v, c->stage + 3 * c->P.np, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_get_field(pic_ctx* c, double* rho, double* phi, double* E) {
+  if (!c) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  const size_t nc = (size_t)c->P.ncell;
+  double* srho = c->stage;
+  double* sphi = c->stage + nc;
+  double* sE = c->stage + 2 * nc;
+  const bool fits = 5 * nc <= 6 * (size_t)c->P.np;
+  if (fits) {
+    CK(launch_store_field(c, rho ? srho : nullptr, phi ? sphi : nullptr, E ? sE : nullptr));
+    if (rho) CK(cudaMemcpyAsync(rho, srho, nc * 8, cudaMemcpyDefault, c->stream));
+    if (phi) CK(cudaMemcpyAsync(phi, sphi, nc * 8, cudaMemcpyDefault, c->stream));
+    if (E) CK(cudaMemcpyAsync(E, sE, 3 * nc * 8, cudaMemcpyDefault, c->stream));
+  } else {
+    // fewer particles than nodes: copy the SoA mesh arrays directly
+    if (rho) CK(cudaMemcpyAsync(rho, c->rho, nc * 8, cudaMemcpyDefault, c->stream));
+    if (phi) CK(cudaMemcpyAsync(phi, c->phi, nc * 8, cudaMemcpyDefault, c->stream));
+    if (E) {
+      double* tmp = (double*)malloc(3 * nc * 8);
+      if (!tmp) return PIC_ENOMEM;
+      double* comp = (double*)malloc(nc * 8);
+      if (!comp) { free(tmp); return PIC_ENOMEM; }
+      for (int d = 0; d < 3; ++d) {
+        cudaError_t e = cudaMemcpyAsync(comp, c->E[d], nc * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { free(tmp); free(comp); return cuda_status(e); }
+        for (size_t i = 0; i < nc; ++i) tmp[3 * i + d] = comp[i];
+      }
+      cudaError_t e = cudaMemcpy(E, tmp, 3 * nc * 8, cudaMemcpyDefault);
+      free(tmp);
+      free(comp);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_get_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* count, int32_t* start, int32_t* perm) {
+  if (!c) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  const size_t np = (size_t)c->P.np, nc = (size_t)c->P.ncell;
+  int32_t* scell = (int32_t*)c->stage;            // fits: 6 np doubles = 12 np ints
+  int32_t* sperm = (int32_t*)c->stage + np;
+  CK(launch_store_sort(c, cell_of_pid ? scell : nullptr, perm ? sperm : nullptr));
+  if (cell_of_pid) CK(cudaMemcpyAsync(cell_of_pid, scell, np * 4, cudaMemcpyDefault, c->stream));
+  if (perm) CK(cudaMemcpyAsync(perm, sperm, np * 4, cudaMemcpyDefault, c->stream));
+  if (count) CK(cudaMemcpyAsync(count, c->count, nc * 4, cudaMemcpyDefault, c->stream));
+  if (start) CK(cudaMemcpyAsync(start, c->start, (nc + 1) * 4, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_get_stats(pic_ctx* c, pic_stats* out) {
+  if (!c || !out) return PIC_EINVAL;
+  unsigned long long h[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  pic_status s = c->sampled ? check_pending(c) : PIC_OK;
+  memset(out, 0, sizeof(*out));
+  out->n_cand = (int64_t)h[0];
+  out->n_coll = (int64_t)h[1];
+  out->n_gmax_exceed = (int64_t)h[2];
+  out->n_near_ties = (int64_t)h[3];
+  out->kernel_launches = c->launches;
+  out->step = c->step;
+  out->t = time_at(c, (double)c->step);
+  out->cg_iters_last = c->cg_iters_last;
+  out->cg_iters_max = c->cg_iters_max;
+  out->cg_res_last = c->cg_res_last;
+  return s;
+}
+
+pic_status pic_reset_stats(pic_ctx* c) {
+  if (!c) return PIC_EINVAL;
+  CK(cudaMemsetAsync(c->counters, 0, 64, c->stream));
+  CK(cudaMemsetAsync(c->flags, 0, 64, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->launches = 0;
+  c->cg_iters_max = 0;
+  return PIC_OK;
+}
+
+pic_status pic_set_profiling(pic_ctx* c, int32_t on) {
+  if (!c) return PIC_EINVAL;
+  prof_flush(c);
+  c->profiling = on != 0;
+  memset(c->prof_ms, 0, sizeof(c->prof_ms));
+  memset(c->prof_launches, 0, sizeof(c->prof_launches));
+  return PIC_OK;
+}
+
+pic_status pic_get_kernel_times(pic_ctx* c, pic_kernel_times* out) {
+  if (!c || !out) return PIC_EINVAL;
+  prof_flush(c);
+  for (int k = 0; k < PIC_NUM_KERNEL_CLASSES; ++k) {
+    out->ms[k] = c->prof_ms[k];
+    out->launches[k] = c->prof_launches[k];
+  }
+  return PIC_OK;
+}
+
+const char* pic_status_string(pic_status s) {
+  switch (s) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or configuration";
+    case PIC_ENOMEM: return "allocation failed";
+    case PIC_ECUDA: return "CUDA error";
+    case PIC_ENOCONV: return "Poisson CG did not reach its tolerance within cg_maxit";
+    case PIC_ETIMEOUT: return "a bounded device-side wait timed out";
+    case PIC_ESTATE: return "call out of order (sample or set the state first)";
+    case PIC_ECAPACITY: return "a cell held more particles than max_ppc";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,273 @@
+// Internal definitions of the GB300 PIC + DSMC library: launch parameters,
+// device helpers and the context. Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
+constexpr int kSeriesTerms = 10;
+
+// ---------------------------------------------------------------------------
+// Everything a kernel needs to know about the problem, passed by value.
+// ---------------------------------------------------------------------------
+struct Params {
+  int n;              // cells per axis
+  int K;              // outcomes per collision call
+  int64_t ncell;      // n^3
+  int64_t np;         // N_p
+  double dt, qm_eff, q_eff, eps0, nphys;
+  double sigma0, gmax;
+  double fx_amp, fx_speed, fx_amp_over_2pi;
+  double vmean[3], vsig;
+  double phi_amp, phi_T, phi_shift[3];
+  uint32_t key0, key1;   // Philox key = seed
+  // derived (host-computed, see derive_params)
+  double h, dV, w;
+  double sg_max;         // (sigma g)_max = sigma0 g_max
+  double pmax;           // P_coll,max = (sigma g)_max w dt / dV
+  double rho_scale;      // q w / h^3
+  double src_pref;       // w dt sigma0 / (2 dV): multiplies (c - 1) s R(a) m
+  double R_series[kSeriesTerms];  // sqrt(2/pi) c_j, small-a series of R(a)
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11). Round: two 32x32 -> 64 products with
+// the published multipliers, key bumped by the published Weyl constants.
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// (2m + 1) 2^-53 with m the top 52 bits of (hi, lo): exact, inside (0, 1).
+__device__ __forceinline__ double unif52(uint32_t hi, uint32_t lo) {
+  const unsigned long long m = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+  return __ull2double_rn(2ull * m + 1ull) * 0x1p-53;
+}
+// (2 w + 1) 2^-33: exact, inside (0, 1).
+__device__ __forceinline__ double unif32(uint32_t w) {
+  return __ull2double_rn(2ull * (unsigned long long)w + 1ull) * 0x1p-33;
+}
+// floor(U c) with U = w 2^-32: a 0-based uniform index below c.
+__device__ __forceinline__ uint32_t draw_index(uint32_t w, uint32_t c) { return __umulhi(w, c); }
+
+// Sampling stream of one particle: counter (pid_lo, pid_hi, 0, 0xFFFFFF00|j).
+__device__ __forceinline__ U4 sample_block(const Params& P, uint64_t pid, uint32_t j) {
+  return philox((uint32_t)pid, (uint32_t)(pid >> 32), 0u, 0xFFFFFF00u | j, P.key0, P.key1);
+}
+
+// ---------------------------------------------------------------------------
+// Manufactured solution.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_coord(double x, int n) {
+  int i = (int)floor(x * (double)n);
+  return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+}
+
+// x^M(t) with F_x(x^M, t) = xi for f_x = 1 + A sin(2 pi (x - c t)). With
+// y = x - c t the equation is G(y) = y - A/(2 pi) cos(2 pi y) = T, T = xi -
+// c t - A/(2 pi) cos(2 pi c t); G' = 1 + A sin(2 pi y) >= 1 - |A| > 0.
+// Newton from the guess, at most 12 iterations, stops when |dy| <= 2^-50.
+// Returns x^M and sin(2 pi (x^M - c t)) (for xdot^M).
+__device__ __forceinline__ double xm_solve(const Params& P, double xi, double t, double guess,
+                                           double* s_out) {
+  const double ct = P.fx_speed * t;
+  const double T = xi - ct - P.fx_amp_over_2pi * cospi(2.0 * ct);
+  double y = guess - ct;
+  // keep the start inside the bracket |y - T| <= A/(2 pi)
+  const double lo = T - fabs(P.fx_amp_over_2pi), hi = T + fabs(P.fx_amp_over_2pi);
+  y = fmin(fmax(y, lo), hi);
+  for (int it = 0; it < 12; ++it) {
+    double s, c;
+    sincospi(2.0 * y, &s, &c);
+    const double G = y - P.fx_amp_over_2pi * c - T;
+    const double dy = G / (1.0 + P.fx_amp * s);
+    y -= dy;
+    if (fabs(dy) <= 0x1p-50) break;
+  }
+  *s_out = sinpi(2.0 * y);
+  return y + ct;
+}
+
+// xdot^M = A c [sin(2 pi (x^M - c t)) + sin(2 pi c t)] / (1 + A sin(2 pi (x^M - c t)))
+__device__ __forceinline__ double xm_dot(const Params& P, double s, double t) {
+  const double ct = P.fx_speed * t;
+  return P.fx_amp * P.fx_speed * (s + sinpi(2.0 * ct)) / (1.0 + P.fx_amp * s);
+}
+
+// E^M = -grad phi^M at x, time t.
+__device__ __forceinline__ void e_manufactured(const Params& P, double x, double y, double z, double t,
+                                               double* ex, double* ey, double* ez) {
+  const double amp = P.phi_amp * exp(t / (2.0 * P.phi_T)) * kTwoPi;
+  double s0, c0, s1, c1, s2, c2;
+  sincospi(2.0 * (x - P.phi_shift[0]), &s0, &c0);
+  sincospi(2.0 * (y - P.phi_shift[1]), &s1, &c1);
+  sincospi(2.0 * (z - P.phi_shift[2]), &s2, &c2);
+  *ex = -amp * c0 * s1 * s2;
+  *ey = -amp * s0 * c1 * s2;
+  *ez = -amp * s0 * s1 * c2;
+}
+
+// R(a): E_{X ~ N(m, s^2 I)} |X| X = s R(|m|/s) m (hard spheres, Gaussian f_v).
+__device__ __forceinline__ double hs_R(const Params& P, double a) {
+  if (a < 0.1) {
+    const double a2 = a * a;
+    double acc = P.R_series[kSeriesTerms - 1];
+#pragma unroll
+    for (int j = kSeriesTerms - 2; j >= 0; --j) acc = fma(acc, a2, P.R_series[j]);
+    return acc;
+  }
+  const double a2 = a * a;
+  const double sq2pi = 0.79788456080286535588;  // sqrt(2/pi)
+  return sq2pi * (1.0 + 1.0 / a2) * exp(-0.5 * a2) +
+         (a + 2.0 / a - 1.0 / (a2 * a)) * erf(a * 0.70710678118654752440);
+}
+
+// <Delta v^M> of Eq. vel_change_1c for a particle of velocity v in a cell of c.
+__device__ __forceinline__ void hs_source(const Params& P, double vx, double vy, double vz, int c,
+                                          double* sx, double* sy, double* sz) {
+  const double mx = P.vmean[0] - vx, my = P.vmean[1] - vy, mz = P.vmean[2] - vz;
+  const double a = sqrt(mx * mx + my * my + mz * mz) / P.vsig;
+  const double f = P.src_pref * (double)(c - 1) * P.vsig * hs_R(P, a);
+  *sx = f * mx;
+  *sy = f * my;
+  *sz = f * mz;
+}
+
+__device__ __forceinline__ double wrap_unit(double x) {
+  double y = x - floor(x);
+  return y >= 1.0 ? 0.0 : y;
+}
+
+}  // namespace pic
+
+// ---------------------------------------------------------------------------
+// Context (host side). Device arrays are structure-of-arrays, sorted by
+// (cell, pid); two copies of every per-particle array for the sort.
+// ---------------------------------------------------------------------------
+struct pic_ctx {
+  pic_config cfg;
+  pic::Params P;
+  cudaStream_t stream;
+  int device, num_sms;
+  pic_allocator alloc;
+  bool have_alloc;
+
+  // particles, buffer [b][component]
+  double* x[2][3];
+  double* v[2][3];
+  double* xm[2][3];  // x^M at the last evaluation (Newton warm start)
+  double* vm[2][3];  // v^M (constant for the Gaussian f_v)
+  uint32_t* pid[2];
+  int cur;
+
+  int32_t* key;     // cell of each particle (current order)
+  int32_t* rank;    // arrival rank inside its cell (atomic, unordered)
+  int32_t* perm;    // sorted slot -> source index (before the in-cell sort)
+  int32_t* count;   // [ncell]
+  int32_t* start;   // [ncell + 1]
+  int32_t* scan_blocks;  // scan scratch
+  int64_t scan_nblocks;
+
+  double* dv[3];    // collision term per particle (sorted order)
+  double* dvm[3];   // source term when requested separately
+
+  // mesh
+  double* corner;   // [8][ncell] per-cell CIC partials
+  double* rho;      // [ncell]
+  double* b;        // [ncell]
+  double* rhs_part; // per-block partial sums of b
+  int64_t rhs_blocks;
+  double* phi;      // [ncell]
+  double* E[3];     // [ncell] each
+  double* cg_r;
+  double* cg_p[2];
+  double* cg_q;
+  double* cg_red;   // reduction slots
+  unsigned int* cg_bar;  // grid barrier words
+  int* cg_info;     // [0] iterations, [1] status (0 ok, 1 noconv, 2 timeout)
+  double* cg_res;   // relative residual
+  int cg_grid, cg_block;
+
+  // collisions
+  double* overlay;  // per-lane working velocities
+  int dsmc_grid, dsmc_block, dsmc_G, dsmc_Kc, bm_words;
+  int64_t dsmc_groups;
+  size_t dsmc_smem;
+  unsigned long long* counters;  // n_cand, n_coll, n_gmax, n_tie
+  int* flags;       // sticky: [0] bits 1 capacity, 2 no convergence, 4 timeout; [1] max CG iterations
+
+  // error norms
+  double* err_part; // per-block partials
+  int err_blocks;
+  double* err_out;  // 14 doubles
+
+  // boundary staging
+  double* stage;    // 6 N_p doubles
+  int32_t* stage_i; // N_p ints
+
+  // host state
+  double t0;
+  int64_t step;
+  bool sampled;
+  int64_t launches;
+  int cg_iters_last, cg_iters_max;
+  double cg_res_last;
+  pic_status pending;  // sticky status from asynchronous checks
+
+  // profiling: pairs of events recorded on the stream, resolved lazily
+  bool profiling;
+  cudaEvent_t* ev_pool;
+  int* ev_class;
+  int ev_cap, ev_used;
+  double prof_ms[PIC_NUM_KERNEL_CLASSES];
+  int64_t prof_launches[PIC_NUM_KERNEL_CLASSES];
+};
+
+namespace pic {
+enum KernelClass {
+  KC_SAMPLE = 0, KC_SORT = 1, KC_GATHER = 2, KC_RHS = 3, KC_CG = 4,
+  KC_DSMC = 5, KC_KICK = 6, KC_ERR = 7, KC_OTHER = 8
+};
+
+// Kernel-launching helpers (each returns cudaGetLastError()).
+cudaError_t launch_sample(pic_ctx* c, double t0);
+cudaError_t launch_load_state(pic_ctx* c, const double* xv_dev, double t);
+cudaError_t launch_store_state(pic_ctx* c, double* xv_dev);
+cudaError_t launch_keys(pic_ctx* c);
+cudaError_t launch_sort(pic_ctx* c);            // scan + scatter + in-cell sort + gather + CIC
+cudaError_t launch_rhs(pic_ctx* c, double t);
+cudaError_t launch_cg(pic_ctx* c);             // CG + zero-mean + E
+cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate_source);
+cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift, double th);
+cudaError_t launch_errors(pic_ctx* c, double t);
+cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E);
+cudaError_t launch_store_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* perm);
+cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm);
+
+// Profiling brackets (no-ops unless profiling is on).
+void prof_begin(pic_ctx* c);
+void prof_end(pic_ctx* c, int kclass);
+}  // namespace pic

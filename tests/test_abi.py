@@ -1,0 +1,94 @@
+"""The C-ABI library loads without a GPU, exports every symbol include/pic.h
+declares, and its host-only entry points behave (no compute calls)."""
+import ctypes
+import math
+
+import pytest
+
+from paper_2602_15130_gb300 import _lib, derived, make_config, workloads
+from oracle import oracle as O
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__ as g
+
+    g.build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(L):
+    names = _lib.header_functions()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding declares exactly the header's functions
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_struct_layout_matches_header(L):
+    # pic_config: 2 int32, int64, 13 doubles incl. arrays..., checked by size
+    assert ctypes.sizeof(_lib.PicConfig) == 4 + 4 + 8 + 8 * 5 + 8 * 2 + 8 * 2 + 24 + 8 + 8 * 2 + 24 + 4 * 4 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(_lib.PicErrors) == 14 * 8
+
+
+def test_default_config_is_valid_and_is_the_smallest_workload(L):
+    c = _lib.PicConfig()
+    assert L.pic_config_default(ctypes.byref(c)) == _lib.PIC_OK
+    assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_OK
+    w = workloads.smallest()
+    assert c.n == w["n"] and c.n_particles == w["n_particles"] and c.K == w["K"]
+    assert abs(c.sigma0 - w["sigma0"]) < 1e-12 * w["sigma0"]
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n", 1), ("n", 2048), ("n_particles", 0), ("K", -1), ("dt", 0.0), ("dt", float("nan")),
+    ("fx_amp", 1.0), ("v_sigma", 0.0), ("eps0", 0.0), ("cg_tol", 0.0), ("cg_maxit", 0), ("precision", 7),
+    ("max_ppc", -5), ("phi_T", 0.0),
+])
+def test_invalid_configs_are_rejected(L, field, value):
+    c = make_config(workloads.smallest())
+    setattr(c, field, value)
+    assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_EINVAL
+    out = ctypes.c_void_p(123)
+    # pic_create validates before touching the GPU and clears *out
+    assert L.pic_create(ctypes.byref(c), None, None, ctypes.byref(out)) == _lib.PIC_EINVAL
+    assert not out.value
+
+
+def test_null_arguments(L):
+    assert L.pic_validate_config(None) == _lib.PIC_EINVAL
+    assert L.pic_config_default(None) == _lib.PIC_EINVAL
+    assert L.pic_step(None, 1) == _lib.PIC_EINVAL
+    assert L.pic_sample_mms(None, 0.0) == _lib.PIC_EINVAL
+    L.pic_destroy(None)  # no-op
+
+
+def test_status_strings(L):
+    for s in range(8):
+        assert L.pic_status_string(s)
+    assert b"unknown" in L.pic_status_string(99)
+
+
+@pytest.mark.parametrize("level", [0, 2, 4])
+def test_derived_constants_match_oracle(L, level):
+    p = workloads.refinement_level(level)
+    d = derived(p)
+    cfg = O.make_cfg(p)
+    assert d["pmax"] == O.pmax(cfg)
+    assert d["w"] == 1.0 / p["n_particles"]
+    assert d["ppc"] == 32.0
+    assert math.isclose(d["inv_pmax"], 1.0 / d["pmax"])
+
+
+def test_workload_recipes():
+    p = workloads.smallest()
+    # about 0.1 expected collisions per particle per collision call
+    ppc = p["n_particles"] / p["n"] ** 3
+    assert math.isclose((ppc - 1) * p["sigma0"] * 4 / math.sqrt(math.pi) * p["dt"] / ppc, 0.1)
+    for l in range(5):
+        q = workloads.refinement_level(l)
+        assert q["n"] == 8 * 2 ** l and q["n_particles"] == 32 * q["n"] ** 3
+        assert math.isclose(q["dt"] * q["steps"], 0.5)
+        assert q["sigma0"] == workloads.refinement_level(0)["sigma0"]
+    assert workloads.precision_form()["n_particles"] == 134217728

@@ -1,0 +1,59 @@
+"""Multi-GPU is replicas only: each rank runs an independent copy of the
+workload with its own Philox seed and no data-path collective; the job
+value is all ranks' particle-steps over the slowest rank's time. The
+rank-level logic is exercised here with world_size 2 on gloo (CPU)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import sys
+
+    import torch.distributed as td
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    td.init_process_group("gloo", rank=rank, world_size=world)
+    p = bench.replica_params(bench.workload("smallest"), rank)
+    local_ms = 100.0 + 50.0 * rank
+    mx = bench.max_over_ranks(local_ms)
+    val = bench.aggregate_value(p["n_particles"], 5, world, mx)
+    q.put((rank, p["seed"], mx, val))
+    td.destroy_process_group()
+
+
+def test_two_replicas_on_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    seeds = [r[1] for r in res]
+    assert seeds == [0, 1]
+    assert all(r[2] == 150.0 for r in res)          # max over ranks
+    assert all(abs(r[3] - 2 * 4096 * 5 / 0.150) < 1e-6 for r in res)
+
+
+def test_single_rank_helpers_without_process_group():
+    import bench
+
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.replica_params({"seed": 7}, 3)["seed"] == 10
