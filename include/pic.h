@@ -217,6 +217,33 @@ pic_status pic_get_kernel_times(pic_ctx* ctx, pic_kernel_times* out);
 void pic_destroy(pic_ctx* ctx);
 const char* pic_status_string(pic_status s);
 
+/* Poisson solve that allocates nothing. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when
+ * they solve (a memory budget fixed at start-up, or a host framework that
+ * bans cudaMalloc/cudaFree on its hot path because they synchronise the
+ * device). It solves -Lap_h phi = b - mean(b) on the periodic n^3 node mesh
+ * (7-point Laplacian, h = 1/n) by the same conjugate-gradient kernel the
+ * contexts use, projects phi to zero mean and writes E = -grad_h phi.
+ *  n        2 .. 48 (n^3 <= 110,592 nodes); larger meshes return
+ *           PIC_EINVAL, nothing is launched.
+ *  b        [n^3] right-hand side, device memory, read only.
+ *  phi      [n^3] device memory: in, the warm start; out, the solution.
+ *  E        [3][n^3] device memory, component-major (E_x, then E_y, E_z).
+ *  tol, maxit  stop at ||r||_2 <= tol ||b - mean b||_2 or after maxit
+ *           iterations (then PIC_ENOCONV, phi holds the last iterate).
+ *  cuda_stream  stream to run on (NULL = legacy default stream); the call
+ *           synchronises it before returning.
+ *  iters, rel_res  optional host outputs: iterations and ||r|| / ||b||.
+ * Its scratch (about 4.4 MB) is one fixed array inside the library, held on
+ * every GPU that loads the library until the process exits. The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU (two
+ * streams, two host threads) race and give wrong results. Host or non-device
+ * pointers return PIC_EINVAL. Calls no allocating routine. */
+pic_status pic_poisson_solve_noalloc(int32_t n, const double* b, double* phi, double* E, double tol,
+                                     int32_t maxit, void* cuda_stream, int32_t* iters, double* rel_res);
+
 #ifdef __cplusplus
 }
 #endif

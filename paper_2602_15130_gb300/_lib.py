@@ -108,6 +108,8 @@ SIGNATURES = {
     "pic_get_kernel_times": (_S, [_V, ctypes.POINTER(PicKernelTimes)]),
     "pic_destroy": (None, [_V]),
     "pic_status_string": (ctypes.c_char_p, [_S]),
+    "pic_poisson_solve_noalloc": (_S, [ctypes.c_int32, _V, _V, _V, ctypes.c_double, ctypes.c_int32, _V,
+                                      ctypes.POINTER(ctypes.c_int32), _D]),
 }
 
 _lib = None

@@ -368,3 +368,149 @@ cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E) 
 }
 
 }  // namespace pic
+
+// ---------------------------------------------------------------------------
+// Allocation-free Poisson solve (pic_poisson_solve_noalloc).
+//
+// Some callers cannot allocate device memory at solve time: code running
+// under a memory budget fixed at start-up, or a host framework that forbids
+// cudaMalloc/cudaFree on its hot path because they synchronise the device.
+// For them the CG scratch lives in this one fixed array in the library's own
+// device memory: every GPU that loads the library holds it until the process
+// exits. Host code must not use the array's name as a device address; it
+// looks the address up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace pic {
+namespace {
+
+constexpr int64_t kNoallocMaxNodes = 48 * 48 * 48;   // largest mesh: 48^3 nodes
+constexpr int kNoallocMaxGrid = 4096;                  // cooperative blocks
+constexpr int64_t kNoallocPartBlocks = (kNoallocMaxNodes + kThreads - 1) / kThreads;
+// layout in doubles: b copy, r, p0, p1, q [5 N]; partial sums of b; CG
+// reduction slots [4 grid]; 16 words of barrier / status / residual
+constexpr int64_t kNoallocDoubles = 5 * kNoallocMaxNodes + kNoallocPartBlocks + 4 * kNoallocMaxGrid + 16;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[64] = {nullptr};
+
+// copy b into the scratch and write per-block partial sums for its mean
+__global__ void __launch_bounds__(kThreads) k_noalloc_prep(const double* b, double* bcopy, double* part, int64_t m) {
+  __shared__ double sh[32];
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (id < m) {
+    v = b[id];
+    bcopy[id] = v;
+  }
+  const double tot = block_sum(v, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+}  // namespace
+}  // namespace pic
+
+extern "C" pic_status pic_poisson_solve_noalloc(int32_t n, const double* b, double* phi, double* E, double tol,
+                                                int32_t maxit, void* cuda_stream, int32_t* iters, double* rel_res) {
+  using namespace pic;
+  if (n < 2 || b == nullptr || phi == nullptr || E == nullptr || !(tol > 0.0) || maxit < 1) return PIC_EINVAL;
+  const int64_t m = (int64_t)n * n * n;
+  if (m > kNoallocMaxNodes) return PIC_EINVAL;  // beyond the fixed scratch: n <= 48
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  // b, phi and E must be device memory of the current device
+  const void* ptrs[3] = {b, phi, E};
+  for (const void* p : ptrs) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return PIC_EINVAL;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return PIC_EINVAL;
+  }
+  // one-time set-up per device: the scratch array's device address
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return PIC_ECUDA;
+      }
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  int sms = 0, occ = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, kThreads, 0) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  int64_t grid = (m + kThreads - 1) / kThreads;
+  if (grid > (int64_t)occ * sms) grid = (int64_t)occ * sms;
+  if (grid > kNoallocMaxGrid) grid = kNoallocMaxGrid;
+  const int part_blocks = (int)((m + kThreads - 1) / kThreads);
+
+  double* bcopy = base;
+  double* part = base + 5 * kNoallocMaxNodes;
+  double* red = part + kNoallocPartBlocks;
+  int* words = (int*)(red + 4 * kNoallocMaxGrid);   // [0,1] barrier, [2..4] info, [5,6] flags
+  double* res = (double*)(words + 8);
+
+  CgArgs a;
+  a.n = n;
+  a.ncell = m;
+  a.inv_h2 = (double)n * (double)n;
+  a.two_h = 2.0 * (1.0 / (double)n);
+  a.b = bcopy;
+  a.x = phi;
+  a.r = base + kNoallocMaxNodes;
+  a.p0 = base + 2 * kNoallocMaxNodes;
+  a.p1 = base + 3 * kNoallocMaxNodes;
+  a.q = base + 4 * kNoallocMaxNodes;
+  a.rhs_part = part;
+  a.rhs_blocks = part_blocks;
+  a.red = red;
+  a.bar = (unsigned int*)words;
+  a.info = words + 2;
+  a.flags = words + 5;
+  a.res = res;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.E0 = E;
+  a.E1 = E + m;
+  a.E2 = E + 2 * m;
+  // the array keeps the last call's contents: clear the barrier and status words
+  cudaError_t e = cudaMemsetAsync(words, 0, 8 * sizeof(int), stream);
+  if (e == cudaSuccess) {
+    k_noalloc_prep<<<part_blocks, kThreads, 0, stream>>>(b, bcopy, part, m);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)k_cg, dim3((unsigned)grid), dim3(kThreads), args, 0, stream);
+  }
+  int info[5] = {0, 0, 0, 0, 0};
+  double r = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(info, words + 2, 5 * sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r, res, sizeof(double), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  if (iters) *iters = info[0];
+  if (rel_res) *rel_res = r;
+  if (info[2]) return PIC_ETIMEOUT;
+  if (info[1]) return PIC_ENOCONV;
+  return PIC_OK;
+}
