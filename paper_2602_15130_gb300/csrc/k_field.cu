@@ -2,10 +2,10 @@
 //   rhs : rho at nodes from the per-cell CIC partials, b = rho/eps0 -
 //         Lap phi^M - rho^M/eps0 and per-block partial sums of b;
 //   cg  : one cooperative persistent kernel: b -= mean(b), conjugate
-//         gradients on -Lap_h phi = b (7-point, warm start, two grid
-//         barriers per iteration, p = r + beta p formed on the fly inside
-//         the matrix-vector product), zero-mean projection and
-//         E = -grad_h phi by central differences.
+//         gradients on -Lap_h phi = b (7-point, warm start, three grid
+//         barriers per iteration: p update, q = A p with p.q, x/r update
+//         with r.r), zero-mean projection and E = -grad_h phi by central
+//         differences.
 // All reductions are per-block partials combined in a fixed order, so a
 // solve is deterministic for a given grid. Grid barriers are bounded: a
 // wait that exceeds ~2 s of SM clock sets a timeout flag and the kernel
@@ -38,7 +38,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 struct RhsArgs {
   Params P;
-  double t;
+  TimeTerms tt;
   const double* corner;
   double *rho, *b, *part;
 };
@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
         }
     const double rho = P.rho_scale * s;
     const double X = i * P.h, Y = j * P.h, Z = k * P.h;
-    const double ct = P.fx_speed * a.t;
-    const double phiM = P.phi_amp * exp(a.t / (2.0 * P.phi_T)) * sinpi(2.0 * (X - P.phi_shift[0])) *
+    const double ct = a.tt.ct;
+    const double phiM = a.tt.em_amp / kTwoPi * sinpi(2.0 * (X - P.phi_shift[0])) *
                         sinpi(2.0 * (Y - P.phi_shift[1])) * sinpi(2.0 * (Z - P.phi_shift[2]));
     const double lap_phiM = -3.0 * kTwoPi * kTwoPi * phiM;
     const double rhoM = P.q_eff * P.nphys * (1.0 + P.fx_amp * sinpi(2.0 * (X - ct))) *
@@ -142,14 +142,29 @@ __device__ __forceinline__ double grid_total(const double* part, int m, double* 
   return sh[0];
 }
 
-__device__ __forceinline__ int64_t wrapi(int64_t i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// the six periodic neighbours of node id = i + n (j + n k), 32-bit indices
+// (n^3 < 2^31): x+, x-, y+, y-, z+, z-
+struct Nbr {
+  int xp, xm, yp, ym, zp, zm;
+};
+__device__ __forceinline__ Nbr neighbours(int id, int n, int nn) {
+  const int i = id % n, j = (id / n) % n, k = id / nn;
+  Nbr b;
+  b.xp = i == n - 1 ? id - (n - 1) : id + 1;
+  b.xm = i == 0 ? id + (n - 1) : id - 1;
+  b.yp = j == n - 1 ? id - (n - 1) * n : id + n;
+  b.ym = j == 0 ? id + (n - 1) * n : id - n;
+  b.zp = k == n - 1 ? id - (n - 1) * nn : id + nn;
+  b.zm = k == 0 ? id + (n - 1) * nn : id - nn;
+  return b;
+}
 
 __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
   __shared__ double sh[40];
-  const int n = a.n;
-  const int64_t m = a.ncell;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = a.n, nn = a.n * a.n;
+  const int m = (int)a.ncell;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int G = gridDim.x;
   int ph = 0;  // alternating reduction slots
   auto slot = [&](int q) { return a.red + (size_t)q * 2 * G; };
@@ -157,14 +172,12 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
   // phase 0: zero-mean b, r = b - A x, ||r||^2 and ||b||^2
   const double mean_b = grid_total(a.rhs_part, a.rhs_blocks, sh) / (double)m;
   double rr_loc = 0.0, bb_loc = 0.0;
-  for (int64_t id = t0; id < m; id += stride) {
-    const int64_t i = id % n, j = (id / n) % n, k = id / ((int64_t)n * n);
+  for (int id = t0; id < m; id += stride) {
+    const Nbr q = neighbours(id, n, nn);
     const double bv = a.b[id] - mean_b;
     a.b[id] = bv;
     const double* x = a.x;
-    const double nb = x[wrapi(i + 1, n) + n * (j + (int64_t)n * k)] + x[wrapi(i - 1, n) + n * (j + (int64_t)n * k)] +
-                      x[i + n * (wrapi(j + 1, n) + (int64_t)n * k)] + x[i + n * (wrapi(j - 1, n) + (int64_t)n * k)] +
-                      x[i + n * (j + (int64_t)n * wrapi(k + 1, n))] + x[i + n * (j + (int64_t)n * wrapi(k - 1, n))];
+    const double nb = x[q.xp] + x[q.xm] + x[q.yp] + x[q.ym] + x[q.zp] + x[q.zm];
     const double Ax = (6.0 * x[id] - nb) * a.inv_h2;
     const double rv = bv - Ax;
     a.r[id] = rv;
@@ -185,32 +198,25 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
   ph ^= 1;
   double beta = 0.0;
   int it = 0, status = 0;
-  double* pold = a.p1;
-  double* pnew = a.p0;
+  double* p = a.p0;
   const double thresh = a.tol * sqrt(bb);
   while (true) {
     if (bb == 0.0 || sqrt(rr) <= thresh) break;
     if (it >= a.maxit) { status = 1; break; }
-    // p = r + beta p (on the fly at the 7 stencil points), q = A p, p.q
+    // p = r + beta p
+    if (it == 0) {
+      for (int id = t0; id < m; id += stride) p[id] = a.r[id];
+    } else {
+      for (int id = t0; id < m; id += stride) p[id] = a.r[id] + beta * p[id];
+    }
+    if (!grid_barrier(a.bar, a.info, a.flags)) return;
+    // q = A p, p.q
     double pq_loc = 0.0;
-    for (int64_t id = t0; id < m; id += stride) {
-      const int64_t i = id % n, j = (id / n) % n, k = id / ((int64_t)n * n);
-      const int64_t nbr[6] = {wrapi(i + 1, n) + n * (j + (int64_t)n * k), wrapi(i - 1, n) + n * (j + (int64_t)n * k),
-                              i + n * (wrapi(j + 1, n) + (int64_t)n * k), i + n * (wrapi(j - 1, n) + (int64_t)n * k),
-                              i + n * (j + (int64_t)n * wrapi(k + 1, n)), i + n * (j + (int64_t)n * wrapi(k - 1, n))};
-      double pc, nb;
-      if (it == 0) {
-        pc = a.r[id];
-        nb = a.r[nbr[0]] + a.r[nbr[1]] + a.r[nbr[2]] + a.r[nbr[3]] + a.r[nbr[4]] + a.r[nbr[5]];
-      } else {
-        pc = a.r[id] + beta * pold[id];
-        double p6[6];
-#pragma unroll
-        for (int u = 0; u < 6; ++u) p6[u] = a.r[nbr[u]] + beta * pold[nbr[u]];
-        nb = p6[0] + p6[1] + p6[2] + p6[3] + p6[4] + p6[5];
-      }
+    for (int id = t0; id < m; id += stride) {
+      const Nbr q = neighbours(id, n, nn);
+      const double nb = p[q.xp] + p[q.xm] + p[q.yp] + p[q.ym] + p[q.zp] + p[q.zm];
+      const double pc = p[id];
       const double qv = (6.0 * pc - nb) * a.inv_h2;
-      pnew[id] = pc;
       a.q[id] = qv;
       pq_loc += pc * qv;
     }
@@ -223,8 +229,8 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
     ph ^= 1;
     const double alpha = rr / pq;
     double rn_loc = 0.0;
-    for (int64_t id = t0; id < m; id += stride) {
-      a.x[id] += alpha * pnew[id];
+    for (int id = t0; id < m; id += stride) {
+      a.x[id] += alpha * p[id];
       const double rv = a.r[id] - alpha * a.q[id];
       a.r[id] = rv;
       rn_loc += rv * rv;
@@ -239,13 +245,10 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
     ++it;
     beta = rr_new / rr;
     rr = rr_new;
-    double* tmp = pold;
-    pold = pnew;
-    pnew = tmp;
   }
   // zero-mean projection
   double xs = 0.0;
-  for (int64_t id = t0; id < m; id += stride) xs += a.x[id];
+  for (int id = t0; id < m; id += stride) xs += a.x[id];
   {
     const double s = block_sum(xs, sh);
     if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
@@ -253,15 +256,15 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
   if (!grid_barrier(a.bar, a.info, a.flags)) return;
   const double mean_x = grid_total(slot(ph), G, sh) / (double)m;
   ph ^= 1;
-  for (int64_t id = t0; id < m; id += stride) a.x[id] -= mean_x;
+  for (int id = t0; id < m; id += stride) a.x[id] -= mean_x;
   if (!grid_barrier(a.bar, a.info, a.flags)) return;
   // E = -grad_h phi, second-order central differences
-  for (int64_t id = t0; id < m; id += stride) {
-    const int64_t i = id % n, j = (id / n) % n, k = id / ((int64_t)n * n);
+  for (int id = t0; id < m; id += stride) {
+    const Nbr q = neighbours(id, n, nn);
     const double* x = a.x;
-    a.E0[id] = -(x[wrapi(i + 1, n) + n * (j + (int64_t)n * k)] - x[wrapi(i - 1, n) + n * (j + (int64_t)n * k)]) / a.two_h;
-    a.E1[id] = -(x[i + n * (wrapi(j + 1, n) + (int64_t)n * k)] - x[i + n * (wrapi(j - 1, n) + (int64_t)n * k)]) / a.two_h;
-    a.E2[id] = -(x[i + n * (j + (int64_t)n * wrapi(k + 1, n))] - x[i + n * (j + (int64_t)n * wrapi(k - 1, n))]) / a.two_h;
+    a.E0[id] = -(x[q.xp] - x[q.xm]) / a.two_h;
+    a.E1[id] = -(x[q.yp] - x[q.ym]) / a.two_h;
+    a.E2[id] = -(x[q.zp] - x[q.zm]) / a.two_h;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[0] = it;
@@ -297,7 +300,7 @@ int rhs_blocks_needed(int64_t ncell) { return blocks_for(ncell); }
 cudaError_t launch_rhs(pic_ctx* c, double t) {
   RhsArgs a;
   a.P = c->P;
-  a.t = t;
+  a.tt = time_terms(c->P, t);
   a.corner = c->corner;
   a.rho = c->rho;
   a.b = c->b;

@@ -21,7 +21,7 @@ inline int blocks_for(int64_t n, int t = kThreads) {
 // --------------------------------------------------------------------------
 struct SampleArgs {
   Params P;
-  double t0;
+  TimeTerms tt;
   double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
   uint32_t* pid;
 };
@@ -35,9 +35,9 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a) {
   const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                         unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
   double s;
-  const double X0 = xm_solve(P, xi[0], a.t0, xi[0], &s);
-  const double X1 = xm_solve(P, xi[1], a.t0, xi[1], &s);
-  const double X2 = xm_solve(P, xi[2], a.t0, xi[2], &s);
+  const double X0 = xm_solve(P, a.tt, xi[0], xi[0], &s);
+  const double X1 = xm_solve(P, a.tt, xi[1], xi[1], &s);
+  const double X2 = xm_solve(P, a.tt, xi[2], xi[2], &s);
   const double V0 = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
   const double V1 = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
   const double V2 = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a) {
 // Load a caller state ([N_p][3] x then [N_p][3] v, pid order) into SoA.
 struct LoadArgs {
   Params P;
-  double t;
+  TimeTerms tt;
   const double* xv;  // 6 N_p: x AoS then v AoS
   double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
   uint32_t* pid;
@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(kThreads) k_load_state(LoadArgs a) {
   const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                         unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
   double s;
-  a.xm0[i] = xm_solve(P, xi[0], a.t, xi[0], &s);
-  a.xm1[i] = xm_solve(P, xi[1], a.t, xi[1], &s);
-  a.xm2[i] = xm_solve(P, xi[2], a.t, xi[2], &s);
+  a.xm0[i] = xm_solve(P, a.tt, xi[0], xi[0], &s);
+  a.xm1[i] = xm_solve(P, a.tt, xi[1], xi[1], &s);
+  a.xm2[i] = xm_solve(P, a.tt, xi[2], xi[2], &s);
   a.vm0[i] = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
   a.vm1[i] = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
   a.vm2[i] = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
           a.dv0[j] = acc0; a.dv1[j] = acc1; a.dv2[j] = acc2;
         } else {
           const double K = (double)P.K;
-          const double m0 = acc0 / K, m1 = acc1 / K, m2 = acc2 / K;
+          const double m0 = acc0 != 0.0 ? acc0 / K : 0.0, m1 = acc1 != 0.0 ? acc1 / K : 0.0,
+                       m2 = acc2 != 0.0 ? acc2 / K : 0.0;
           double s0, s1, s2;
           hs_source(P, a.v0[j], a.v1[j], a.v2[j], cc, &s0, &s1, &s2);
           if (separate) {
@@ -319,7 +320,9 @@ struct KickArgs {
   const uint32_t* pid;
   const double *dv0, *dv1, *dv2;
   const double *E0, *E1, *E2;
-  double tE, th;
+  double *L0, *L1, *L2;  // Lorentz term dt q/m (E_p - E^M_p)
+  int lor_mode;          // 0: compute, 1: compute and store, 2: load
+  TimeTerms tE, th;
   int drift;
   int32_t *key, *rank, *count;
 };
@@ -355,16 +358,23 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
   if (j >= P.np) return;
   double x[3] = {a.x0[j], a.x1[j], a.x2[j]};
   double v[3] = {a.v0[j], a.v1[j], a.v2[j]};
-  double Ep[3], EM[3];
-  gather_E(P, a.E0, a.E1, a.E2, x[0], x[1], x[2], Ep);
-  e_manufactured(P, x[0], x[1], x[2], a.tE, &EM[0], &EM[1], &EM[2]);
+  double L[3];
+  if (a.lor_mode == 2) {
+    L[0] = a.L0[j]; L[1] = a.L1[j]; L[2] = a.L2[j];
+  } else {
+    double Ep[3], EM[3];
+    gather_E(P, a.E0, a.E1, a.E2, x[0], x[1], x[2], Ep);
+    e_manufactured(P, a.tE, x[0], x[1], x[2], &EM[0], &EM[1], &EM[2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L[d] = P.dt * P.qm_eff * (Ep[d] - EM[d]);
+    if (a.lor_mode == 1) {
+      a.L0[j] = L[0]; a.L1[j] = L[1]; a.L2[j] = L[2];
+    }
+  }
   double dv[3] = {0.0, 0.0, 0.0};
   if (a.dv0) { dv[0] = a.dv0[j]; dv[1] = a.dv1[j]; dv[2] = a.dv2[j]; }
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double L = P.dt * P.qm_eff * (Ep[d] - EM[d]);
-    v[d] = v[d] + 0.5 * (L + dv[d]);
-  }
+  for (int d = 0; d < 3; ++d) v[d] = v[d] + 0.5 * (L[d] + dv[d]);
   a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
   if (!a.drift) return;
   const uint64_t p = a.pid[j];
@@ -375,9 +385,9 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double s;
-    const double xmv = xm_solve(P, xi[d], a.th, xmp[d][j], &s);
+    const double xmv = xm_solve(P, a.th, xi[d], xmp[d][j], &s);
     xmp[d][j] = xmv;
-    const double xd = xm_dot(P, s, a.th);
+    const double xd = xm_dot(P, a.th, s);
     x[d] = wrap_unit(x[d] + P.dt * (v[d] + xd - vm[d]));
   }
   a.x0[j] = x[0]; a.x1[j] = x[1]; a.x2[j] = x[2];
@@ -394,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
 // --------------------------------------------------------------------------
 struct ErrArgs {
   Params P;
-  double t;
+  TimeTerms tt;
   const double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
   const uint32_t* pid;
   const double* phi;
@@ -444,7 +454,7 @@ __global__ void __launch_bounds__(kThreads) k_err_partial(ErrArgs a) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         double s;
-        const double xm = xm_solve(P, xi[d], a.t, guess[d], &s);
+        const double xm = xm_solve(P, a.tt, xi[d], guess[d], &s);
         double e = xs[d] - xm;
         e -= floor(e + 0.5);
         vals[d] = e * e;
@@ -464,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) k_err_partial(ErrArgs a) {
       s0 = sinpi(2.0 * (X - P.phi_shift[0]));
       s1 = sinpi(2.0 * (Y - P.phi_shift[1]));
       s2 = sinpi(2.0 * (Z - P.phi_shift[2]));
-      const double phiM = P.phi_amp * exp(a.t / (2.0 * P.phi_T)) * s0 * s1 * s2;
+      const double phiM = a.tt.em_amp / kTwoPi * s0 * s1 * s2;
       const double e = a.phi[id] - phiM;
       vals[6] = e * e;
       vals[13] = fabs(e);
@@ -475,18 +485,32 @@ __global__ void __launch_bounds__(kThreads) k_err_partial(ErrArgs a) {
     for (int q = 0; q < 14; ++q) a.part[(size_t)blockIdx.x * 14 + q] = vals[q];
 }
 
-__global__ void k_err_final(ErrArgs a, int nblocks) {
-  // one thread per quantity, fixed block order
-  const int q = threadIdx.x;
-  if (q >= 14) return;
-  double x = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
-    const double y = a.part[(size_t)b * 14 + q];
-    x = q < 7 ? x + y : fmax(x, y);
+constexpr int kFinalThreads = 512;
+
+// one block: each thread sums a fixed strided subset, then a fixed tree
+__global__ void __launch_bounds__(kFinalThreads) k_err_final(ErrArgs a, int nblocks) {
+  __shared__ double sh[kFinalThreads];
+  for (int q = 0; q < 14; ++q) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      const double y = a.part[(size_t)b * 14 + q];
+      x = q < 7 ? x + y : fmax(x, y);
+    }
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sh[threadIdx.x] = q < 7 ? sh[threadIdx.x] + sh[threadIdx.x + w]
+                                                       : fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double r = sh[0];
+      if (q < 6) r = sqrt(r / (double)a.P.np);
+      else if (q == 6) r = sqrt(r / (double)a.P.ncell);
+      a.out[q] = r;
+    }
+    __syncthreads();
   }
-  if (q < 6) x = sqrt(x / (double)a.P.np);
-  else if (q == 6) x = sqrt(x / (double)a.P.ncell);
-  a.out[q] = x;
 }
 
 }  // namespace
@@ -495,7 +519,7 @@ __global__ void k_err_final(ErrArgs a, int nblocks) {
 cudaError_t launch_sample(pic_ctx* c, double t0) {
   SampleArgs a;
   a.P = c->P;
-  a.t0 = t0;
+  a.tt = time_terms(c->P, t0);
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
@@ -512,7 +536,7 @@ cudaError_t launch_sample(pic_ctx* c, double t0) {
 cudaError_t launch_load_state(pic_ctx* c, const double* xv, double t) {
   LoadArgs a;
   a.P = c->P;
-  a.t = t;
+  a.tt = time_terms(c->P, t);
   a.xv = xv;
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
@@ -598,8 +622,12 @@ cudaError_t launch_kick(pic_ctx* c, double tE, bool with_coll, bool drift, doubl
   if (with_coll) { a.dv0 = c->dv[0]; a.dv1 = c->dv[1]; a.dv2 = c->dv[2]; }
   else { a.dv0 = a.dv1 = a.dv2 = nullptr; }
   a.E0 = c->E[0]; a.E1 = c->E[1]; a.E2 = c->E[2];
-  a.tE = tE;
-  a.th = th;
+  a.L0 = c->lor[0]; a.L1 = c->lor[1]; a.L2 = c->lor[2];
+  // the kick without drift closes a step at the time level where the next
+  // step's first kick starts: keep its Lorentz term for that kick
+  a.lor_mode = drift ? (c->lor_valid ? 2 : 0) : 1;
+  a.tE = time_terms(c->P, tE);
+  a.th = time_terms(c->P, th);
   a.drift = drift ? 1 : 0;
   a.key = c->key;
   a.rank = c->rank;
@@ -608,13 +636,14 @@ cudaError_t launch_kick(pic_ctx* c, double tE, bool with_coll, bool drift, doubl
   k_kick<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
   prof_end(c, KC_KICK);
   c->launches++;
+  c->lor_valid = !drift;
   return cudaGetLastError();
 }
 
 cudaError_t launch_errors(pic_ctx* c, double t) {
   ErrArgs a;
   a.P = c->P;
-  a.t = t;
+  a.tt = time_terms(c->P, t);
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
@@ -628,7 +657,7 @@ cudaError_t launch_errors(pic_ctx* c, double t) {
   const int nb = a.pblocks + blocks_for(c->P.ncell);
   prof_begin(c);
   k_err_partial<<<nb, kThreads, 0, c->stream>>>(a);
-  k_err_final<<<1, 32, 0, c->stream>>>(a, nb);
+  k_err_final<<<1, kFinalThreads, 0, c->stream>>>(a, nb);
   prof_end(c, KC_ERR);
   c->launches += 2;
   return cudaGetLastError();
@@ -636,4 +665,16 @@ cudaError_t launch_errors(pic_ctx* c, double t) {
 
 int err_blocks_needed(int64_t np, int64_t ncell) { return blocks_for(np) + blocks_for(ncell); }
 
+}  // namespace pic
+
+namespace pic {
+TimeTerms time_terms(const Params& P, double t) {
+  TimeTerms tt;
+  tt.t = t;
+  tt.ct = P.fx_speed * t;
+  tt.cos2ct = cos(kTwoPi * tt.ct);
+  tt.sin2ct = sin(kTwoPi * tt.ct);
+  tt.em_amp = kTwoPi * P.phi_amp * exp(t / (2.0 * P.phi_T));
+  return tt;
+}
 }  // namespace pic

@@ -216,17 +216,29 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather(GatherArgs a) {
     // arrival order of the atomic ranks
     __syncwarp();
     for (int32_t e = lane; e < cnt; e += 32) add_cic(a, s + e, ci, cj, ck, acc);
-    // fixed-shape butterfly: every lane ends with the same sums
+    // fixed-shape transpose reduction of the 8 corner sums across the warp:
+    // each xor level halves the values a lane keeps (4 + 2 + 1 adds), two
+    // more levels finish the sum; lane l then holds corner
+    // 4 [l & 16] + 2 [l & 8] + [l & 4]
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    double a4[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int i = 0; i < 4; ++i) {
+      const double send = u16 ? acc[i] : acc[4 + i];
+      a4[i] = (u16 ? acc[4 + i] : acc[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    double a2[2];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
-    if (lane < 8) {
-      double val = acc[0];
-#pragma unroll
-      for (int q = 1; q < 8; ++q)
-        if (lane == q) val = acc[q];
-      a.corner[(int64_t)lane * a.ncell + cell] = val;
+    for (int i = 0; i < 2; ++i) {
+      const double send = u8 ? a4[i] : a4[2 + i];
+      a2[i] = (u8 ? a4[2 + i] : a4[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    double a1 = (u4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, u4 ? a2[0] : a2[1], 4);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+    if ((lane & 3) == 0) {
+      const int corner = (u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0);
+      a.corner[(int64_t)corner * a.ncell + cell] = a1;
     }
   }
 }

@@ -106,6 +106,7 @@ void derive_params(const pic_config& c, Params& P) {
     P.phi_shift[d] = c.phi_shift[d];
   }
   P.vsig = c.v_sigma;
+  P.inv_vsig = 1.0 / c.v_sigma;
   P.phi_amp = c.phi_amp;
   P.phi_T = c.phi_T;
   P.key0 = (uint32_t)(c.seed & 0xFFFFFFFFull);
@@ -169,6 +170,7 @@ void for_each_buffer(pic_ctx* c, F f) {
   f((void**)&c->start, (nc + 1) * 4);
   f((void**)&c->scan_blocks, (size_t)c->scan_nblocks * 4 + 16);
   for (int d = 0; d < 3; ++d) {
+    f((void**)&c->lor[d], np * 8);
     f((void**)&c->dv[d], np * 8);
     f((void**)&c->dvm[d], np * 8);
     f((void**)&c->E[d], nc * 8);
@@ -217,6 +219,7 @@ pic_status check_pending(pic_ctx* c) {
 
 // sort by (cell, pid) from the current positions and solve the field at t
 pic_status sort_and_field(pic_ctx* c, double t) {
+  c->lor_valid = false;
   CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
   CK(launch_keys(c));
   CK(launch_sort(c));

@@ -24,7 +24,7 @@ struct Params {
   double dt, qm_eff, q_eff, eps0, nphys;
   double sigma0, gmax;
   double fx_amp, fx_speed, fx_amp_over_2pi;
-  double vmean[3], vsig;
+  double vmean[3], vsig, inv_vsig;
   double phi_amp, phi_T, phi_shift[3];
   uint32_t key0, key1;   // Philox key = seed
   // derived (host-computed, see derive_params)
@@ -86,70 +86,77 @@ __device__ __forceinline__ int cell_coord(double x, int n) {
   return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
 }
 
+// Time-only terms of the manufactured solution at one time t (host-computed
+// once per launch): c t, cos(2 pi c t), sin(2 pi c t) and the amplitude
+// 2 pi phibar e^{t/(2T)} of grad phi^M.
+struct TimeTerms {
+  double t, ct, cos2ct, sin2ct, em_amp;
+};
+
 // x^M(t) with F_x(x^M, t) = xi for f_x = 1 + A sin(2 pi (x - c t)). With
 // y = x - c t the equation is G(y) = y - A/(2 pi) cos(2 pi y) = T, T = xi -
-// c t - A/(2 pi) cos(2 pi c t); G' = 1 + A sin(2 pi y) >= 1 - |A| > 0.
-// Newton from the guess, at most 12 iterations, stops when |dy| <= 2^-50.
+// c t - A/(2 pi) cos(2 pi c t); G' = 1 + A sin(2 pi y) >= 1 - |A| > 0 and
+// |G''/(2 G')| <= 2 pi |A| / (2 (1 - |A|)) < 1.35. Newton from the guess
+// (clamped into the bracket |y - T| <= A/(2 pi)); once a correction is at
+// most 2^-27 the next one would be below 1.35 * 2^-54, under half an ulp of
+// y = O(1), so the loop stops there and updates sin(2 pi y) to first order
+// (error (2 pi dy)^2 / 2 <= 1e-15 relative to the O(1) terms it enters).
 // Returns x^M and sin(2 pi (x^M - c t)) (for xdot^M).
-__device__ __forceinline__ double xm_solve(const Params& P, double xi, double t, double guess,
+__device__ __forceinline__ double xm_solve(const Params& P, const TimeTerms& tt, double xi, double guess,
                                            double* s_out) {
-  const double ct = P.fx_speed * t;
-  const double T = xi - ct - P.fx_amp_over_2pi * cospi(2.0 * ct);
-  double y = guess - ct;
-  // keep the start inside the bracket |y - T| <= A/(2 pi)
+  const double T = xi - tt.ct - P.fx_amp_over_2pi * tt.cos2ct;
   const double lo = T - fabs(P.fx_amp_over_2pi), hi = T + fabs(P.fx_amp_over_2pi);
-  y = fmin(fmax(y, lo), hi);
+  double y = fmin(fmax(guess - tt.ct, lo), hi);
   for (int it = 0; it < 12; ++it) {
     double s, c;
     sincospi(2.0 * y, &s, &c);
-    const double G = y - P.fx_amp_over_2pi * c - T;
-    const double dy = G / (1.0 + P.fx_amp * s);
+    const double dy = (y - P.fx_amp_over_2pi * c - T) / (1.0 + P.fx_amp * s);
     y -= dy;
-    if (fabs(dy) <= 0x1p-50) break;
+    if (fabs(dy) <= 0x1p-27) {
+      *s_out = s - kTwoPi * c * dy;
+      return y + tt.ct;
+    }
   }
   *s_out = sinpi(2.0 * y);
-  return y + ct;
+  return y + tt.ct;
 }
 
 // xdot^M = A c [sin(2 pi (x^M - c t)) + sin(2 pi c t)] / (1 + A sin(2 pi (x^M - c t)))
-__device__ __forceinline__ double xm_dot(const Params& P, double s, double t) {
-  const double ct = P.fx_speed * t;
-  return P.fx_amp * P.fx_speed * (s + sinpi(2.0 * ct)) / (1.0 + P.fx_amp * s);
+__device__ __forceinline__ double xm_dot(const Params& P, const TimeTerms& tt, double s) {
+  return P.fx_amp * P.fx_speed * (s + tt.sin2ct) / (1.0 + P.fx_amp * s);
 }
 
-// E^M = -grad phi^M at x, time t.
-__device__ __forceinline__ void e_manufactured(const Params& P, double x, double y, double z, double t,
+// E^M = -grad phi^M at x (time terms in tt).
+__device__ __forceinline__ void e_manufactured(const Params& P, const TimeTerms& tt, double x, double y, double z,
                                                double* ex, double* ey, double* ez) {
-  const double amp = P.phi_amp * exp(t / (2.0 * P.phi_T)) * kTwoPi;
   double s0, c0, s1, c1, s2, c2;
   sincospi(2.0 * (x - P.phi_shift[0]), &s0, &c0);
   sincospi(2.0 * (y - P.phi_shift[1]), &s1, &c1);
   sincospi(2.0 * (z - P.phi_shift[2]), &s2, &c2);
-  *ex = -amp * c0 * s1 * s2;
-  *ey = -amp * s0 * c1 * s2;
-  *ez = -amp * s0 * s1 * c2;
+  *ex = -tt.em_amp * c0 * s1 * s2;
+  *ey = -tt.em_amp * s0 * c1 * s2;
+  *ez = -tt.em_amp * s0 * s1 * c2;
 }
 
 // R(a): E_{X ~ N(m, s^2 I)} |X| X = s R(|m|/s) m (hard spheres, Gaussian f_v).
 __device__ __forceinline__ double hs_R(const Params& P, double a) {
+  const double a2 = a * a;
   if (a < 0.1) {
-    const double a2 = a * a;
     double acc = P.R_series[kSeriesTerms - 1];
 #pragma unroll
     for (int j = kSeriesTerms - 2; j >= 0; --j) acc = fma(acc, a2, P.R_series[j]);
     return acc;
   }
-  const double a2 = a * a;
+  const double ia = 1.0 / a, ia2 = ia * ia;
   const double sq2pi = 0.79788456080286535588;  // sqrt(2/pi)
-  return sq2pi * (1.0 + 1.0 / a2) * exp(-0.5 * a2) +
-         (a + 2.0 / a - 1.0 / (a2 * a)) * erf(a * 0.70710678118654752440);
+  return sq2pi * (1.0 + ia2) * exp(-0.5 * a2) + (a + 2.0 * ia - ia2 * ia) * erf(a * 0.70710678118654752440);
 }
 
 // <Delta v^M> of Eq. vel_change_1c for a particle of velocity v in a cell of c.
 __device__ __forceinline__ void hs_source(const Params& P, double vx, double vy, double vz, int c,
                                           double* sx, double* sy, double* sz) {
   const double mx = P.vmean[0] - vx, my = P.vmean[1] - vy, mz = P.vmean[2] - vz;
-  const double a = sqrt(mx * mx + my * my + mz * mz) / P.vsig;
+  const double a = sqrt(mx * mx + my * my + mz * mz) * P.inv_vsig;
   const double f = P.src_pref * (double)(c - 1) * P.vsig * hs_R(P, a);
   *sx = f * mx;
   *sy = f * my;
@@ -192,6 +199,8 @@ struct pic_ctx {
   int64_t scan_nblocks;
 
   double* dv[3];    // collision term per particle (sorted order)
+  double* lor[3];   // dt q/m (E_p - E^M_p) of the last kick without drift
+  bool lor_valid;   // lor matches the current order, positions and field
   double* dvm[3];   // source term when requested separately
 
   // mesh
@@ -261,8 +270,10 @@ cudaError_t launch_sort(pic_ctx* c);            // scan + scatter + in-cell sort
 cudaError_t launch_rhs(pic_ctx* c, double t);
 cudaError_t launch_cg(pic_ctx* c);             // CG + zero-mean + E
 cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate_source);
+// kick at time tE; drift to th if drift. Reuses / refreshes c->lor.
 cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift, double th);
 cudaError_t launch_errors(pic_ctx* c, double t);
+TimeTerms time_terms(const Params& P, double t);
 cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E);
 cudaError_t launch_store_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* perm);
 cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm);
