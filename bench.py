@@ -1,12 +1,17 @@
 """Throughput of the manufactured-solution PIC + DSMC step on GB300.
 
-Default workload: the finest level of the plain-FP64 refinement sweep
-(128^3 cells, 32 particles per cell = 67,108,864 particles, K = 16,
-dt = 0.02/16, collisions on). A step is one full velocity-Verlet step of
-every particle: two K-averaged DSMC calls, kick, drift, sort, deposit,
-Poisson CG and E. Prints one JSON line (rank 0).
+Default workload: the finest level of the refinement sweep (128^3 cells,
+32 particles per cell = 67,108,864 particles, K = 16, dt = 0.02/16,
+collisions on). The headline value is the precision form (FP32 particle
+state, int32 cell + FP32 offset, FP64-accurate charge sums, CG inner
+products and error norms); the plain FP64 path runs the same workload
+beside it, and both sets of MMS error norms are reported. A step is one
+full velocity-Verlet step of every particle: two K-averaged DSMC calls,
+kick, drift, sort, deposit, Poisson CG and E. Prints one JSON line
+(rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload refine4|precision|refineL|smallest] [--form mixed|fp64]
 
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on a bounded sample of the same workload on the host cores.
@@ -35,6 +40,8 @@ UNIT = "particle-steps/s"
 def workload(name: str) -> dict:
     from paper_2602_15130_gb300 import workloads as W
 
+    if name == "precision":
+        return W.precision_form()
     if name == "refine4":
         return W.refinement_level(4)
     if name.startswith("refine"):
@@ -45,8 +52,9 @@ def workload(name: str) -> dict:
 
 
 def describe(name: str, p: dict) -> str:
+    form = "precision form (FP32 state, FP64-accurate sums)" if p.get("precision") else "plain FP64"
     return (f"{name}: {p['n']}^3 cells, {p['n_particles']} particles, K={p['K']}, dt={p['dt']}, "
-            f"hard-sphere sigma0={p['sigma0']:.4f}, FP64")
+            f"hard-sphere sigma0={p['sigma0']:.4f}, {form}")
 
 
 # ----------------------------------------------------------------- clocks ----
@@ -105,16 +113,26 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-# Algorithmic HBM bytes per unit for each kernel class of one step (FP64
-# form). Units: particles for the particle kernels, nodes x CG iterations
-# for the CG. Derivations are in the design doc.
+# Algorithmic HBM bytes per unit for each kernel class of one step. Units:
+# particles for the particle kernels, nodes x CG iterations for the CG. The
+# derivations are listed in the design doc (data layout and roofline section).
 BYTES_PER_UNIT = {
-    "kick_drift": (124 + 104 + 72 + 24) / 2.0,  # average of the drift and no-drift kick launches
-    "sort_gather_deposit": 200 + 8 + 64 / 32.0,
-    "dsmc": 48.0,
-    "sort": 4 + 4 + 4 + 4,
-    "cg_efield": 96.0,
-    "rhs": 8 * 8 + 16,
+    "fp64": {
+        "kick_drift": (228 + 120) / 2.0,   # mean of the drift (228 B) and closing (120 B) kick launches
+        "sort_gather_deposit": 208 + 64 / 32.0,
+        "dsmc": 48.0,
+        "sort": 12.0,
+        "cg_efield": 88.0,
+        "rhs": 8 * 8 + 16,                 # per node: 8 corner partials in, rho and b out
+    },
+    "mixed": {
+        "kick_drift": (100 + 64) / 2.0,
+        "sort_gather_deposit": 88 + 64 / 32.0,
+        "dsmc": 24.0,
+        "sort": 12.0,
+        "cg_efield": 44.0,
+        "rhs": 8 * 8 + 8 + 4,              # per node: 8 corner partials in, rho (FP64) and b (FP32) out
+    },
 }
 
 
@@ -144,15 +162,20 @@ def aggregate_value(n_particles: int, steps: int, world: int, max_ms: float) -> 
 
 
 # ----------------------------------------------------------------- GPU arm ---
-def run_gpu(args, rank: int, world: int) -> dict | None:
+def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> dict | None:
     import numpy as np
     import torch
 
-    from paper_2602_15130_gb300 import Pic
+    from paper_2602_15130_gb300 import Pic, workloads as W
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    p = replica_params(workload(args.workload), rank)
+    p = workload(args.workload)
+    if form == "mixed":
+        p = W.mixed(p)
+    else:
+        p = dict(p, precision=0)
+    p = replica_params(p, rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = Pic(p, stream=stream)
@@ -178,8 +201,17 @@ def run_gpu(args, rank: int, world: int) -> dict | None:
         sim.set_profiling(False)
         ms = max_over_ranks(ms, "cuda")
         errs = sim.mms_error()
-        # end to end through the C ABI with host buffers: pinned x, v in, step, x, v out
         npart = p["n_particles"]
+        if not with_e2e:
+            sim.close()
+            if rank != 0:
+                return None
+            return {"value": aggregate_value(npart, args.steps, world, ms), "ms_per_step": ms / args.steps,
+                    "kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items()},
+                    "mms_error": {"eps2": errs["eps2"], "epsinf": errs["epsinf"]},
+                    "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
+                              "cg_iters_max": st["cg_iters_max"]}, "clocks": clk.summary()}
+        # end to end through the C ABI with host buffers: pinned x, v in, step, x, v out
         xh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
         vh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
         sim.get_state((xh, vh))
@@ -198,30 +230,41 @@ def run_gpu(args, rank: int, world: int) -> dict | None:
         return None
     value = aggregate_value(npart, args.steps, world, ms)
     peaks = measured_peaks()
+    bpu = BYTES_PER_UNIT[form]
+
+    def units_of(k):
+        if k == "cg_efield":
+            return p["n"] ** 3 * max(1, st["cg_iters_max"])
+        return p["n"] ** 3 if k == "rhs" else npart
+
+    def hbm_gbs(k):
+        per_launch_ms = kt[k]["ms"] / max(1, kt[k]["launches"])
+        return bpu.get(k, 0.0) * units_of(k) / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
+
     # dominant kernel class by device time inside the timed region
     dom = max(kt, key=lambda k: kt[k]["ms"])
-    per_launch_ms = kt[dom]["ms"] / max(1, kt[dom]["launches"])
-    if dom == "cg_efield":
-        units = p["n"] ** 3 * max(1, st["cg_iters_max"])
-    else:
-        units = npart
-    achieved = BYTES_PER_UNIT.get(dom, 0.0) * units / (per_launch_ms / 1000.0) / 1e9
+    achieved = hbm_gbs(dom)
+    step_kernels = {k: {"ms_per_launch": round(kt[k]["ms"] / max(1, kt[k]["launches"]), 4),
+                        "bytes_per_unit": bpu[k], "achieved_gbs": round(hbm_gbs(k), 1),
+                        "frac_of_measured_hbm": round(hbm_gbs(k) / peaks["hbm_gbs"], 4)}
+                    for k in bpu if kt.get(k, {}).get("launches")}
     launches = int(st["kernel_launches"])
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic manufactured-solution workload",
+        "vs_baseline": None, "dtype": "f32" if form == "mixed" else "f64",
+        "data": "synthetic manufactured-solution workload",
         "config": {"workload": describe(args.workload, p), "n": p["n"], "n_particles": npart, "K": p["K"],
-                   "dt": p["dt"], "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (particle state %.1f GB)" % (npart * 100 / 1e9)},
+                   "dt": p["dt"], "form": form, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (particle state %.1f GB)" % (npart * (44 if form == "mixed" else 100) / 1e9)},
         "e2e": {"value": aggregate_value(npart, e2e_steps, world, e2e_s * 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": npart * 48, "d2h_bytes_per_step": npart * 48,
                 "path": "pic_set_state(host) + pic_step(1) + pic_get_state(host), pinned buffers"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "peak_source": peaks["source"],
-                     "bytes_per_unit": BYTES_PER_UNIT.get(dom), "units_per_launch": units},
+                     "peak_source": peaks["source"], "bytes_per_unit": bpu.get(dom), "units_per_launch": units_of(dom)},
+        "step_kernels_hbm": step_kernels,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items()},
         "kernel_launches_by_class": {k: v["launches"] for k, v in kt.items()},
         "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
@@ -284,6 +327,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="refine4")
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-beside", action="store_true")
     ap.add_argument("--cpu-mesh", type=int, default=24)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -309,8 +354,14 @@ def main():
         import torch.distributed as td
 
         td.barrier()
-    out = run_gpu(args, rank, world)
+    out = run_gpu(args, rank, world, args.form)
+    beside = None
+    if args.form == "mixed" and not args.no_fp64_beside:
+        beside = run_gpu(args, rank, world, "fp64", with_e2e=False)
     if out is not None:
+        if beside is not None:
+            out["fp64_beside"] = beside
+            out["speedup_vs_fp64"] = out["value"] / beside["value"]
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out), flush=True)

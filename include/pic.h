@@ -50,7 +50,7 @@ typedef enum {
   PIC_ECAPACITY = 7   /* a cell held more particles than max_ppc           */
 } pic_status;
 
-enum { PIC_FP64 = 0 };
+enum { PIC_FP64 = 0, PIC_MIXED = 1 };
 
 /* Problem statement (unit cube [0,1)^3, periodic). Field meanings:
  *  n             cells = nodes per axis (2 .. 1024); cell (i,j,k) spans
@@ -73,7 +73,11 @@ enum { PIC_FP64 = 0 };
  *                (Sec. 5.2 form).
  *  couple_qm_zero  nonzero: q/m = 0 in the push (field does not act).
  *  couple_q_zero   nonzero: q = 0 in the deposit and in rho^M (Sec. 5.3).
- *  precision     PIC_FP64.
+ *  precision     PIC_FP64: every step in FP64. PIC_MIXED (the precision
+ *                form): positions as int32 cell + FP32 offset, FP32
+ *                velocities, gather, manufactured terms and scattering, FP32
+ *                field and CG vectors; per-cell charge sums, CG inner
+ *                products and residual, and the error norms FP64-accurate.
  *  max_ppc       most particles one cell may hold during collisions (working
  *                set of the collision kernel); 0 selects 512.
  *  seed          Philox4x32-10 key (low word, high word).

@@ -42,6 +42,7 @@ def make_config(p: dict) -> PicConfig:
     c.couple_qm_zero = int(p.get("couple_qm_zero", 0))
     c.couple_q_zero = int(p.get("couple_q_zero", 0))
     c.max_ppc = int(p.get("max_ppc", 0))
+    c.precision = int(p.get("precision", 0))
     c.seed = int(p.get("seed", 0))
     c.cg_maxit = int(p.get("cg_maxit", c.cg_maxit))
     return c

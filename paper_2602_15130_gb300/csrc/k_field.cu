@@ -41,6 +41,7 @@ struct RhsArgs {
   TimeTerms tt;
   const double* corner;
   double *rho, *b, *part;
+  float* b32;  // precision form: b in FP32 (b may then be null)
 };
 
 __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
@@ -71,7 +72,8 @@ __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
                         (1.0 + P.fx_amp * sinpi(2.0 * (Y - ct))) * (1.0 + P.fx_amp * sinpi(2.0 * (Z - ct)));
     bv = rho / P.eps0 - lap_phiM - rhoM / P.eps0;
     a.rho[id] = rho;
-    a.b[id] = bv;
+    if (a.b) a.b[id] = bv;
+    if (a.b32) a.b32[id] = (float)bv;
   }
   const double tot = block_sum(bv, sh);
   if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
@@ -303,7 +305,8 @@ cudaError_t launch_rhs(pic_ctx* c, double t) {
   a.tt = time_terms(c->P, t);
   a.corner = c->corner;
   a.rho = c->rho;
-  a.b = c->b;
+  a.b = c->mixed ? nullptr : c->b;
+  a.b32 = c->mixed ? c->bf : nullptr;
   a.part = c->rhs_part;
   prof_begin(c);
   k_rhs<<<(int)c->rhs_blocks, kThreads, 0, c->stream>>>(a);

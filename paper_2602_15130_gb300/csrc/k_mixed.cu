@@ -1,0 +1,1086 @@
+// Precision form (PIC_MIXED) of the step. Particle state per particle:
+// int32 cell, FP32 offset inside the cell in cell units [0,1)^3, FP32
+// velocity, FP32 v^M and the pid; velocities, field gather, manufactured
+// terms and scattering are FP32. Kept FP64-accurate: the per-cell charge
+// sums, the CG inner products and residual, and the error norms. On this
+// GPU the FP64 pipe runs at 1/58 of the FP32 rate, so the FP64-accurate
+// sums are formed in double-float arithmetic (an unevaluated sum hi + lo
+// of two floats, error-free TwoSum / TwoProd of Knuth and Dekker, relative
+// error about 2^-44) on the FP32 pipe and only the few per-block totals are
+// combined in true FP64.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n, int t = kThreads) {
+  int64_t b = (n + t - 1) / t;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------- helpers --
+struct TimeTermsF {
+  float ct, cos2ct, sin2ct, em_amp;
+};
+
+TimeTermsF to_float(const TimeTerms& t) {
+  TimeTermsF f;
+  f.ct = (float)t.ct;
+  f.cos2ct = (float)t.cos2ct;
+  f.sin2ct = (float)t.sin2ct;
+  f.em_amp = (float)t.em_amp;
+  return f;
+}
+
+// top 24 bits of a Philox word as an FP32 uniform in (0, 1): exact
+__device__ __forceinline__ float unif24(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 0x1p-24f; }
+
+// double-float: hi + lo with |lo| <= ulp(hi)/2
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return DF{s, e};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = two_sum(a.hi, b.hi);
+  const float lo = s.lo + a.lo + b.lo;
+  const float hi = s.hi + lo;
+  return DF{hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+  DF s = two_sum(a.hi, b);
+  const float lo = s.lo + a.lo;
+  const float hi = s.hi + lo;
+  return DF{hi, lo - (hi - s.hi)};
+}
+// a += x y exactly up to the double-float rounding (TwoProd by fma)
+__device__ __forceinline__ DF df_fma(DF a, float x, float y) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);
+  DF s = two_sum(a.hi, p);
+  const float lo = s.lo + a.lo + e;
+  const float hi = s.hi + lo;
+  return DF{hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ DF df_shfl_xor(DF a, int off) {
+  return DF{__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+}
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+// FP32 x^M: Newton from y = T (within A/(2 pi) of the root); stops when a
+// correction is below 2^-23 (the FP32 resolution of y); returns x^M and
+// sin(2 pi (x^M - c t)).
+__device__ __forceinline__ float xm_solve_f(float A, float A2pi, const TimeTermsF& tt, float xi, float* s_out) {
+  const float T = xi - tt.ct - A2pi * tt.cos2ct;
+  float y = T, s = 0.f, c = 1.f;
+  for (int it = 0; it < 8; ++it) {
+    sincospif(2.f * y, &s, &c);
+    const float dy = (y - A2pi * c - T) / (1.f + A * s);
+    y -= dy;
+    if (fabsf(dy) <= 0x1p-23f) break;
+  }
+  *s_out = sinpif(2.f * y);
+  return y + tt.ct;
+}
+
+__device__ __forceinline__ float hs_R_f(const Params& P, float a) {
+  const float a2 = a * a;
+  if (a < 0.1f) {
+    float acc = (float)P.R_series[4];
+#pragma unroll
+    for (int j = 3; j >= 0; --j) acc = fmaf(acc, a2, (float)P.R_series[j]);
+    return acc;
+  }
+  const float ia = 1.f / a, ia2 = ia * ia;
+  return 0.7978845608f * (1.f + ia2) * __expf(-0.5f * a2) + (a + 2.f * ia - ia2 * ia) * erff(a * 0.7071067812f);
+}
+
+// --------------------------------------------------------------- sampling --
+struct Sample32Args {
+  Params P;
+  TimeTerms tt;
+  const double* xv;  // optional caller state (pid order, [N][3] x then [N][3] v)
+  int32_t* cell;
+  float *o0, *o1, *o2, *v0, *v1, *v2, *m0, *m1, *m2;
+  uint32_t* pid;
+};
+
+__global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Params& P = a.P;
+  if (i >= P.np) return;
+  const U4 b0 = sample_block(P, (uint64_t)i, 0), b1 = sample_block(P, (uint64_t)i, 1),
+           b2 = sample_block(P, (uint64_t)i, 2);
+  const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
+                        unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
+  double x[3], v[3], vm[3];
+  for (int d = 0; d < 3; ++d) {
+    double s;
+    vm[d] = P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
+    if (a.xv) {
+      x[d] = a.xv[3 * i + d];
+      v[d] = a.xv[3 * P.np + 3 * i + d];
+    } else {
+      x[d] = wrap_unit(xm_solve(P, a.tt, xi[d], xi[d], &s));
+      v[d] = vm[d];
+    }
+  }
+  const int n = P.n;
+  int ci[3];
+  float off[3];
+  for (int d = 0; d < 3; ++d) {
+    ci[d] = cell_coord(x[d], n);
+    float o = (float)(x[d] * (double)n - (double)ci[d]);
+    off[d] = o >= 1.f ? 0x1.fffffep-1f : (o < 0.f ? 0.f : o);
+  }
+  a.cell[i] = ci[0] + n * (ci[1] + n * ci[2]);
+  a.o0[i] = off[0]; a.o1[i] = off[1]; a.o2[i] = off[2];
+  a.v0[i] = (float)v[0]; a.v1[i] = (float)v[1]; a.v2[i] = (float)v[2];
+  a.m0[i] = (float)vm[0]; a.m1[i] = (float)vm[1]; a.m2[i] = (float)vm[2];
+  a.pid[i] = (uint32_t)i;
+}
+
+struct Keys32Args {
+  int64_t np;
+  const int32_t* cell;
+  int32_t *key, *rank, *count;
+};
+
+__global__ void __launch_bounds__(kThreads) k_keys32(Keys32Args a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.np) return;
+  const int32_t k = a.cell[j];
+  a.key[j] = k;
+  a.rank[j] = atomicAdd(a.count + k, 1);
+}
+
+struct Store32Args {
+  int64_t np;
+  int n;
+  double h;
+  const int32_t* cell;
+  const float *o0, *o1, *o2, *v0, *v1, *v2;
+  const uint32_t* pid;
+  double* xv;
+  int32_t* cell_of_pid;
+};
+
+__global__ void __launch_bounds__(kThreads) k_store_state32(Store32Args a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.np) return;
+  const int64_t p = a.pid[j];
+  const int n = a.n, c = a.cell[j];
+  if (a.cell_of_pid) a.cell_of_pid[p] = c;
+  if (!a.xv) return;
+  const int ci = c % n, cj = (c / n) % n, ck = c / (n * n);
+  a.xv[3 * p] = ((double)ci + (double)a.o0[j]) * a.h;
+  a.xv[3 * p + 1] = ((double)cj + (double)a.o1[j]) * a.h;
+  a.xv[3 * p + 2] = ((double)ck + (double)a.o2[j]) * a.h;
+  double* vs = a.xv + 3 * a.np;
+  vs[3 * p] = a.v0[j]; vs[3 * p + 1] = a.v1[j]; vs[3 * p + 2] = a.v2[j];
+}
+
+// ----------------------------------------------------- sort gather + CIC --
+struct Gather32Args {
+  int n;
+  int64_t ncell;
+  const int32_t *start, *perm;
+  const float* in[9];   // o0..2, v0..2, m0..2
+  float* out[9];
+  const uint32_t* pid_in;
+  uint32_t* pid_out;
+  int32_t* cell_out;
+  double* corner;       // [8][ncell]
+};
+
+constexpr int kGatherThreads = 256;
+
+__global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t cell = gw; cell < a.ncell; cell += nw) {
+    const int32_t s = a.start[cell];
+    const int32_t cnt = a.start[cell + 1] - s;
+    for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
+      const int32_t e = e0 + lane;
+      int32_t src = 0;
+      uint32_t mp = 0xFFFFFFFFu;
+      if (e < cnt) {
+        src = a.perm[s + e];
+        mp = a.pid_in[src];
+      }
+      int32_t r = 0;
+      for (int32_t f0 = 0; f0 < cnt; f0 += 32) {
+        const uint32_t other = f0 == e0 ? mp : ((f0 + lane < cnt) ? a.pid_in[a.perm[s + f0 + lane]] : 0xFFFFFFFFu);
+        const int lim = min(32, cnt - f0);
+        for (int l = 0; l < lim; ++l) r += __shfl_sync(0xffffffffu, other, l) < mp ? 1 : 0;
+      }
+      if (e < cnt) {
+        const int32_t dst = s + r;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src];
+        a.pid_out[dst] = mp;
+        a.cell_out[dst] = (int32_t)cell;
+      }
+    }
+    __syncwarp();
+    // per-cell CIC weights in sorted order, double-float sums
+    DF acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = DF{0.f, 0.f};
+    for (int32_t e = lane; e < cnt; e += 32) {
+      const float ox = a.out[0][s + e], oy = a.out[1][s + e], oz = a.out[2][s + e];
+      const float wx[2] = {1.f - ox, ox}, wy[2] = {1.f - oy, oy}, wz[2] = {1.f - oz, oz};
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const float wyz = wy[b] * wz[c];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) acc[q + 2 * b + 4 * c] = df_fma(acc[q + 2 * b + 4 * c], wx[q], wyz);
+        }
+    }
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    DF a4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a4[i] = df_add(u16 ? acc[4 + i] : acc[i], df_shfl_xor(u16 ? acc[i] : acc[4 + i], 16));
+    DF a2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) a2[i] = df_add(u8 ? a4[2 + i] : a4[i], df_shfl_xor(u8 ? a4[i] : a4[2 + i], 8));
+    DF a1 = df_add(u4 ? a2[1] : a2[0], df_shfl_xor(u4 ? a2[0] : a2[1], 4));
+    a1 = df_add(a1, df_shfl_xor(a1, 2));
+    a1 = df_add(a1, df_shfl_xor(a1, 1));
+    if ((lane & 3) == 0) {
+      const int corner = (u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0);
+      a.corner[(int64_t)corner * a.ncell + cell] = df_to_double(a1);
+    }
+  }
+}
+
+// ----------------------------------------------------------- collisions --
+struct Dsmc32Args {
+  Params P;
+  const float *v0, *v1, *v2;
+  const int32_t* start;
+  uint32_t c0;
+  float *dv0, *dv1, *dv2;  // out: <dv> - <dv^M>, or <dv> when m0 != nullptr
+  float *m0, *m1, *m2;     // out (optional): <dv^M>
+  float* overlay;
+  int max_ppc, bm_words, G, Kc, nchunks;
+  int64_t ngroups;
+  unsigned long long* counters;
+  int* flags;
+};
+
+struct Counts32 {
+  unsigned long long cand, coll, gmax, tie;
+};
+
+__device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const float* ov, const float* v0,
+                                           const float* v1, const float* v2, float* o) {
+  if ((bm[p >> 5] >> (p & 31)) & 1u) {
+    o[0] = ov[3 * p]; o[1] = ov[3 * p + 1]; o[2] = ov[3 * p + 2];
+  } else {
+    o[0] = v0[p]; o[1] = v1[p]; o[2] = v2[p];
+  }
+}
+
+__device__ void ntc_outcome_f(const Params& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
+                              const float* v1, const float* v2, uint32_t* bm, float* ov, Counts32& cnt) {
+  const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
+  const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * (float)P.pmax;
+  const int npairs = (int)floorf(base + unif24(u.x));
+  const float gmax = (float)P.gmax;
+  for (int s = 0; s < npairs; ++s) {
+    const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
+    const uint32_t p = draw_index(b0.x, (uint32_t)c);
+    uint32_t q = draw_index(b0.y, (uint32_t)c);
+    U4 b1;
+    bool have_b1 = false;
+    if (q == p) {
+      b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+      have_b1 = true;
+      q = draw_index(b1.y, (uint32_t)c);
+      if (q == p) q = draw_index(b1.z, (uint32_t)c);
+      if (q == p) q = draw_index(b1.w, (uint32_t)c);
+      uint32_t blk = 2;
+      while (q == p) {
+        if (blk > 255u) { q = (p + 1u) % (uint32_t)c; break; }
+        const U4 bb = philox(c0, cell, (uint32_t)s, (o << 8) | blk, P.key0, P.key1);
+        q = draw_index(bb.x, (uint32_t)c);
+        if (q == p) q = draw_index(bb.y, (uint32_t)c);
+        if (q == p) q = draw_index(bb.z, (uint32_t)c);
+        if (q == p) q = draw_index(bb.w, (uint32_t)c);
+        ++blk;
+      }
+    }
+    float vp[3], vq[3];
+    load_vel_f((int)p, bm, ov, v0, v1, v2, vp);
+    load_vel_f((int)q, bm, ov, v0, v1, v2, vq);
+    const float dx = vp[0] - vq[0], dy = vp[1] - vq[1], dz = vp[2] - vq[2];
+    const float g2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    // accept if U < sigma g / (sigma g)_max = g / g_max, i.e. (U g_max)^2 < g^2
+    const float ug = unif24(b0.z) * gmax;
+    const float ug2 = ug * ug;
+    ++cnt.cand;
+    if (g2 > gmax * gmax) ++cnt.gmax;
+    if (fabsf(ug2 - g2) < 2e-6f * g2) ++cnt.tie;
+    if (ug2 < g2) {
+      if (!have_b1) b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+      float se, ce;
+      sincospif(2.f * unif24(b0.w), &se, &ce);
+      const float cchi = 1.f - 2.f * unif24(b1.x);
+      const float schi = sqrtf(fmaxf(0.f, 1.f - cchi * cchi));
+      const float g = sqrtf(g2);
+      const float nv[3] = {ce * schi, se * schi, cchi};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float cm = 0.5f * (vp[d] + vq[d]);
+        const float hg = 0.5f * g * nv[d];
+        ov[3 * p + d] = cm + hg;
+        ov[3 * q + d] = cm - hg;
+      }
+      bm[p >> 5] |= 1u << (p & 31);
+      bm[q >> 5] |= 1u << (q & 31);
+      ++cnt.coll;
+    }
+  }
+}
+
+constexpr int kDsmcThreads = 128;
+
+__global__ void __launch_bounds__(kDsmcThreads) k_dsmc32(Dsmc32Args a) {
+  extern __shared__ uint32_t smem[];
+  const Params& P = a.P;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int64_t gwarp = (int64_t)blockIdx.x * wpb + wib;
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  uint32_t* wbm = smem + (size_t)wib * 32 * a.bm_words;
+  uint32_t* bm = wbm + (size_t)lane * a.bm_words;
+  float* wov = a.overlay + (size_t)gwarp * 32 * a.max_ppc * 3;
+  float* ov = wov + (size_t)lane * a.max_ppc * 3;
+  for (int i = 0; i < a.bm_words; ++i) bm[i] = 0u;
+  __syncwarp();
+  Counts32 cnt = {0, 0, 0, 0};
+  const bool separate = a.m0 != nullptr;
+  const float invK = 1.f / (float)P.K;
+  const float mu0 = (float)P.vmean[0], mu1 = (float)P.vmean[1], mu2 = (float)P.vmean[2];
+  const float vs = (float)P.vsig, ivs = (float)P.inv_vsig, pref = (float)P.src_pref;
+
+  for (int64_t grp = gwarp; grp < a.ngroups; grp += nwarps) {
+    const int64_t cell0 = grp * a.G;
+    const int ncl = (int)min((int64_t)a.G, P.ncell - cell0);
+    const int mycl = lane / a.Kc;
+    const bool lane_cell = mycl < ncl;
+    int32_t s = 0, c = 0;
+    if (lane_cell) {
+      s = a.start[cell0 + mycl];
+      c = a.start[cell0 + mycl + 1] - s;
+    }
+    const int32_t gs = a.start[cell0], ge = a.start[cell0 + ncl];
+    for (int ch = 0; ch < a.nchunks; ++ch) {
+      const int o = ch * a.Kc + lane % a.Kc;
+      bool run = lane_cell && o < P.K && c >= 2;
+      if (run && c > a.max_ppc) {
+        atomicOr(a.flags, 1);
+        run = false;
+      }
+      if (run)
+        ntc_outcome_f(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s, bm, ov,
+                      cnt);
+      __syncwarp();
+      const bool last = ch == a.nchunks - 1;
+      for (int32_t j = gs + lane; j < ge; j += 32) {
+        int cl = 0;
+        while (cl + 1 < ncl && a.start[cell0 + cl + 1] <= j) ++cl;
+        const int32_t cs = a.start[cell0 + cl];
+        const int cc = a.start[cell0 + cl + 1] - cs;
+        const int jj = j - cs;
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+        if (ch > 0) { acc0 = a.dv0[j]; acc1 = a.dv1[j]; acc2 = a.dv2[j]; }
+        if (cc >= 2 && cc <= a.max_ppc) {
+          const float w0 = a.v0[j], w1 = a.v1[j], w2 = a.v2[j];
+          for (int k = 0; k < a.Kc; ++k) {
+            if (ch * a.Kc + k >= P.K) break;
+            const int L = cl * a.Kc + k;
+            if ((wbm[(size_t)L * a.bm_words + (jj >> 5)] >> (jj & 31)) & 1u) {
+              const float* W = wov + ((size_t)L * a.max_ppc + jj) * 3;
+              acc0 += W[0] - w0;
+              acc1 += W[1] - w1;
+              acc2 += W[2] - w2;
+            }
+          }
+        }
+        if (!last) {
+          a.dv0[j] = acc0; a.dv1[j] = acc1; a.dv2[j] = acc2;
+        } else {
+          const float vx = a.v0[j], vy = a.v1[j], vz = a.v2[j];
+          const float mx = mu0 - vx, my = mu1 - vy, mz = mu2 - vz;
+          const float am = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz))) * ivs;
+          const float f = pref * (float)(cc - 1) * vs * hs_R_f(P, am);
+          if (separate) {
+            a.dv0[j] = acc0 * invK; a.dv1[j] = acc1 * invK; a.dv2[j] = acc2 * invK;
+            a.m0[j] = f * mx; a.m1[j] = f * my; a.m2[j] = f * mz;
+          } else {
+            a.dv0[j] = fmaf(acc0, invK, -f * mx);
+            a.dv1[j] = fmaf(acc1, invK, -f * my);
+            a.dv2[j] = fmaf(acc2, invK, -f * mz);
+          }
+        }
+      }
+      __syncwarp();
+      if (run)
+        for (int i = 0; i < (c + 31) / 32; ++i) bm[i] = 0u;
+      __syncwarp();
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    cnt.cand += __shfl_down_sync(0xffffffffu, cnt.cand, off);
+    cnt.coll += __shfl_down_sync(0xffffffffu, cnt.coll, off);
+    cnt.gmax += __shfl_down_sync(0xffffffffu, cnt.gmax, off);
+    cnt.tie += __shfl_down_sync(0xffffffffu, cnt.tie, off);
+  }
+  if (lane == 0) {
+    if (cnt.cand) atomicAdd(a.counters + 0, cnt.cand);
+    if (cnt.coll) atomicAdd(a.counters + 1, cnt.coll);
+    if (cnt.gmax) atomicAdd(a.counters + 2, cnt.gmax);
+    if (cnt.tie) atomicAdd(a.counters + 3, cnt.tie);
+  }
+}
+
+// ------------------------------------------------------------ kick/drift --
+struct Kick32Args {
+  Params P;
+  const int32_t* cell;
+  float *o0, *o1, *o2, *v0, *v1, *v2;
+  const float *m0, *m1, *m2;
+  const uint32_t* pid;
+  const float *dv0, *dv1, *dv2;
+  const float *E0, *E1, *E2;
+  float *L0, *L1, *L2;
+  int lor_mode;  // 0: compute, 1: compute and store, 2: load
+  TimeTermsF tE, th;
+  int drift;
+  int32_t *key, *rank, *count;
+};
+
+__global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Params& P = a.P;
+  if (j >= P.np) return;
+  const int n = P.n, nn = n * n;
+  const int c = a.cell[j];
+  int ci[3] = {c % n, (c / n) % n, c / nn};
+  float o[3] = {a.o0[j], a.o1[j], a.o2[j]};
+  float v[3] = {a.v0[j], a.v1[j], a.v2[j]};
+  float L[3];
+  if (a.lor_mode == 2) {
+    L[0] = a.L0[j]; L[1] = a.L1[j]; L[2] = a.L2[j];
+  } else {
+    const int i1 = ci[0] + 1 == n ? 0 : ci[0] + 1, j1 = ci[1] + 1 == n ? 0 : ci[1] + 1,
+              k1 = ci[2] + 1 == n ? 0 : ci[2] + 1;
+    const int ii[2] = {ci[0], i1}, jj[2] = {ci[1] * n, j1 * n}, kk[2] = {ci[2] * nn, k1 * nn};
+    const float wx[2] = {1.f - o[0], o[0]}, wy[2] = {1.f - o[1], o[1]}, wz[2] = {1.f - o[2], o[2]};
+    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int node = ii[q] + jj[b] + kk[cc];
+          const float w = wx[q] * wy[b] * wz[cc];
+          e0 = fmaf(w, __ldg(a.E0 + node), e0);
+          e1 = fmaf(w, __ldg(a.E1 + node), e1);
+          e2 = fmaf(w, __ldg(a.E2 + node), e2);
+        }
+    const float h = (float)P.h;
+    float s0, c0, s1, c1, s2, c2;
+    sincospif(2.f * (((float)ci[0] + o[0]) * h - (float)P.phi_shift[0]), &s0, &c0);
+    sincospif(2.f * (((float)ci[1] + o[1]) * h - (float)P.phi_shift[1]), &s1, &c1);
+    sincospif(2.f * (((float)ci[2] + o[2]) * h - (float)P.phi_shift[2]), &s2, &c2);
+    const float amp = a.tE.em_amp, k = (float)(P.dt * P.qm_eff);
+    L[0] = k * (e0 + amp * c0 * s1 * s2);
+    L[1] = k * (e1 + amp * s0 * c1 * s2);
+    L[2] = k * (e2 + amp * s0 * s1 * c2);
+    if (a.lor_mode == 1) {
+      a.L0[j] = L[0]; a.L1[j] = L[1]; a.L2[j] = L[2];
+    }
+  }
+  float dv[3] = {0.f, 0.f, 0.f};
+  if (a.dv0) { dv[0] = a.dv0[j]; dv[1] = a.dv1[j]; dv[2] = a.dv2[j]; }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, L[d] + dv[d], v[d]);
+  a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
+  if (!a.drift) return;
+  const uint64_t p = a.pid[j];
+  const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1);
+  const float xi[3] = {unif24(b0.x), unif24(b0.z), unif24(b1.x)};
+  const float vm[3] = {a.m0[j], a.m1[j], a.m2[j]};
+  const float A = (float)P.fx_amp, A2pi = (float)P.fx_amp_over_2pi, Ac = (float)(P.fx_amp * P.fx_speed);
+  const float dtn = (float)(P.dt * (double)n);
+  float* op[3] = {a.o0, a.o1, a.o2};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float s;
+    xm_solve_f(A, A2pi, a.th, xi[d], &s);
+    const float xd = Ac * (s + a.th.sin2ct) / (1.f + A * s);
+    float on = fmaf(dtn, v[d] + xd - vm[d], o[d]);
+    const float fl = floorf(on);
+    on -= fl;
+    int shift = (int)fl;
+    if (on >= 1.f) { on = 0.f; shift += 1; }
+    int cd = (ci[d] + shift) % n;
+    ci[d] = cd < 0 ? cd + n : cd;
+    op[d][j] = on;
+  }
+  const int32_t k = ci[0] + n * (ci[1] + n * ci[2]);
+  a.key[j] = k;
+  a.rank[j] = atomicAdd(a.count + k, 1);
+}
+
+// ---------------------------------------------------------------- CG32 --
+struct Cg32Args {
+  int n;
+  int64_t ncell;
+  float inv_h2, inv_2h;
+  float *b, *x, *r, *p, *q;
+  const double* rhs_part;
+  int rhs_blocks;
+  double* red;
+  unsigned int* bar;
+  int* info;
+  int* flags;
+  double* res;
+  double tol;
+  int maxit;
+  float *E0, *E1, *E2;
+};
+
+constexpr long long kBarrierCycles = 4000000000LL;
+
+__device__ __forceinline__ bool grid_barrier32(unsigned int* bar, int* info, int* flags) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+    ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > kBarrierCycles) {
+          atomicOr(info + 2, 1);
+          atomicOr(flags, 4);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (ok && *((volatile int*)(info + 2))) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// block total of a double-float partial, returned in FP64 to every thread
+__device__ __forceinline__ double block_total_df(DF v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
+  __syncthreads();
+  if (lane == 0) sh[w] = df_to_double(v);
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += sh[i];
+  return t;
+}
+
+__device__ __forceinline__ double grid_total32(const double* part, int m, double* sh) {
+  const int lane = threadIdx.x & 31;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) s += ((volatile const double*)part)[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) sh[0] = s;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+struct Nbr {
+  int xp, xm, yp, ym, zp, zm;
+};
+__device__ __forceinline__ Nbr neighbours(int id, int n, int nn) {
+  const int i = id % n, j = (id / n) % n, k = id / nn;
+  Nbr b;
+  b.xp = i == n - 1 ? id - (n - 1) : id + 1;
+  b.xm = i == 0 ? id + (n - 1) : id - 1;
+  b.yp = j == n - 1 ? id - (n - 1) * n : id + n;
+  b.ym = j == 0 ? id + (n - 1) * n : id - n;
+  b.zp = k == n - 1 ? id - (n - 1) * nn : id + nn;
+  b.zm = k == 0 ? id + (n - 1) * nn : id - nn;
+  return b;
+}
+
+// FP32 vectors and stencil; inner products and the residual in double-float
+// per thread, FP64 across blocks; same phases as the FP64 solver.
+__global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
+  __shared__ double sh[40];
+  const int n = a.n, nn = a.n * a.n;
+  const int m = (int)a.ncell;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int G = gridDim.x;
+  int ph = 0;
+  auto slot = [&](int q) { return a.red + (size_t)q * 2 * G; };
+
+  const float mean_b = (float)(grid_total32(a.rhs_part, a.rhs_blocks, sh) / (double)m);
+  DF rr_loc{0.f, 0.f}, bb_loc{0.f, 0.f};
+  for (int id = t0; id < m; id += stride) {
+    const Nbr q = neighbours(id, n, nn);
+    const float bv = a.b[id] - mean_b;
+    a.b[id] = bv;
+    const float* x = a.x;
+    const float nb = x[q.xp] + x[q.xm] + x[q.yp] + x[q.ym] + x[q.zp] + x[q.zm];
+    const float rv = bv - (6.f * x[id] - nb) * a.inv_h2;
+    a.r[id] = rv;
+    rr_loc = df_fma(rr_loc, rv, rv);
+    bb_loc = df_fma(bb_loc, bv, bv);
+  }
+  {
+    const double s1 = block_total_df(rr_loc, sh);
+    const double s2 = block_total_df(bb_loc, sh + 8);
+    if (threadIdx.x == 0) {
+      slot(ph)[blockIdx.x] = s1;
+      slot(ph)[G + blockIdx.x] = s2;
+    }
+  }
+  if (!grid_barrier32(a.bar, a.info, a.flags)) return;
+  double rr = grid_total32(slot(ph), G, sh);
+  const double bb = grid_total32(slot(ph) + G, G, sh);
+  ph ^= 1;
+  double beta = 0.0;
+  int it = 0, status = 0;
+  const double thresh = a.tol * sqrt(bb);
+  while (true) {
+    if (bb == 0.0 || sqrt(rr) <= thresh) break;
+    if (it >= a.maxit) { status = 1; break; }
+    const float bf = (float)beta;
+    if (it == 0) {
+      for (int id = t0; id < m; id += stride) a.p[id] = a.r[id];
+    } else {
+      for (int id = t0; id < m; id += stride) a.p[id] = fmaf(bf, a.p[id], a.r[id]);
+    }
+    if (!grid_barrier32(a.bar, a.info, a.flags)) return;
+    DF pq_loc{0.f, 0.f};
+    for (int id = t0; id < m; id += stride) {
+      const Nbr q = neighbours(id, n, nn);
+      const float* p = a.p;
+      const float nb = p[q.xp] + p[q.xm] + p[q.yp] + p[q.ym] + p[q.zp] + p[q.zm];
+      const float pc = p[id];
+      const float qv = (6.f * pc - nb) * a.inv_h2;
+      a.q[id] = qv;
+      pq_loc = df_fma(pq_loc, pc, qv);
+    }
+    {
+      const double s = block_total_df(pq_loc, sh);
+      if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+    }
+    if (!grid_barrier32(a.bar, a.info, a.flags)) return;
+    const double pq = grid_total32(slot(ph), G, sh);
+    ph ^= 1;
+    const float alpha = (float)(rr / pq);
+    DF rn_loc{0.f, 0.f};
+    for (int id = t0; id < m; id += stride) {
+      a.x[id] = fmaf(alpha, a.p[id], a.x[id]);
+      const float rv = fmaf(-alpha, a.q[id], a.r[id]);
+      a.r[id] = rv;
+      rn_loc = df_fma(rn_loc, rv, rv);
+    }
+    {
+      const double s = block_total_df(rn_loc, sh);
+      if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+    }
+    if (!grid_barrier32(a.bar, a.info, a.flags)) return;
+    const double rr_new = grid_total32(slot(ph), G, sh);
+    ph ^= 1;
+    ++it;
+    beta = rr_new / rr;
+    rr = rr_new;
+  }
+  DF xs{0.f, 0.f};
+  for (int id = t0; id < m; id += stride) xs = df_add_f(xs, a.x[id]);
+  {
+    const double s = block_total_df(xs, sh);
+    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+  }
+  if (!grid_barrier32(a.bar, a.info, a.flags)) return;
+  const float mean_x = (float)(grid_total32(slot(ph), G, sh) / (double)m);
+  ph ^= 1;
+  for (int id = t0; id < m; id += stride) a.x[id] -= mean_x;
+  if (!grid_barrier32(a.bar, a.info, a.flags)) return;
+  for (int id = t0; id < m; id += stride) {
+    const Nbr q = neighbours(id, n, nn);
+    const float* x = a.x;
+    a.E0[id] = -(x[q.xp] - x[q.xm]) * a.inv_2h;
+    a.E1[id] = -(x[q.yp] - x[q.ym]) * a.inv_2h;
+    a.E2[id] = -(x[q.zp] - x[q.zm]) * a.inv_2h;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.info[0] = it;
+    a.info[1] = status;
+    a.res[0] = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
+    if (status) atomicOr(a.flags, 2);
+    atomicMax(a.flags + 1, it);
+  }
+}
+
+// --------------------------------------------------------- error norms --
+struct Err32Args {
+  Params P;
+  TimeTerms tt;
+  const int32_t* cell;
+  const float *o0, *o1, *o2, *v0, *v1, *v2;
+  const uint32_t* pid;
+  const float* phi;
+  double* part;
+  int pblocks;
+};
+
+__global__ void __launch_bounds__(kThreads) k_err_partial32(Err32Args a) {
+  __shared__ double sh[(kThreads / 32) * 14];
+  const Params& P = a.P;
+  double vals[14];
+#pragma unroll
+  for (int q = 0; q < 14; ++q) vals[q] = 0.0;
+  if ((int)blockIdx.x < a.pblocks) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < P.np) {
+      const uint64_t p = a.pid[j];
+      const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1), b2 = sample_block(P, p, 2);
+      const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
+                            unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
+      const int n = P.n, c = a.cell[j];
+      const int ci[3] = {c % n, (c / n) % n, c / (n * n)};
+      const float os[3] = {a.o0[j], a.o1[j], a.o2[j]};
+      const float vs[3] = {a.v0[j], a.v1[j], a.v2[j]};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double s;
+        const double xm = xm_solve(P, a.tt, xi[d], xi[d], &s);
+        double e = ((double)ci[d] + (double)os[d]) * P.h - xm;
+        e -= floor(e + 0.5);
+        vals[d] = e * e;
+        vals[7 + d] = fabs(e);
+        const double ev = (double)vs[d] - (P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]));
+        vals[3 + d] = ev * ev;
+        vals[10 + d] = fabs(ev);
+      }
+    }
+  } else {
+    const int64_t id = (int64_t)(blockIdx.x - a.pblocks) * blockDim.x + threadIdx.x;
+    if (id < P.ncell) {
+      const int n = P.n;
+      const int i = (int)(id % n), jj = (int)((id / n) % n), k = (int)(id / ((int64_t)n * n));
+      const double phiM = a.tt.em_amp / kTwoPi * sinpi(2.0 * (i * P.h - P.phi_shift[0])) *
+                          sinpi(2.0 * (jj * P.h - P.phi_shift[1])) * sinpi(2.0 * (k * P.h - P.phi_shift[2]));
+      const double e = (double)a.phi[id] - phiM;
+      vals[6] = e * e;
+      vals[13] = fabs(e);
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 14; ++q) {
+    double x = vals[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, off);
+      x = q < 7 ? x + y : fmax(x, y);
+    }
+    if (lane == 0) sh[w * 14 + q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 14) {
+    const int q = threadIdx.x;
+    double x = sh[q];
+    for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) x = q < 7 ? x + sh[ww * 14 + q] : fmax(x, sh[ww * 14 + q]);
+    a.part[(size_t)blockIdx.x * 14 + q] = x;
+  }
+}
+
+struct StoreField32Args {
+  int64_t ncell;
+  const float *phi, *E0, *E1, *E2;
+  double *ophi, *oE;
+};
+
+__global__ void __launch_bounds__(kThreads) k_store_field32(StoreField32Args a) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= a.ncell) return;
+  if (a.ophi) a.ophi[id] = a.phi[id];
+  if (a.oE) {
+    a.oE[3 * id] = a.E0[id];
+    a.oE[3 * id + 1] = a.E1[id];
+    a.oE[3 * id + 2] = a.E2[id];
+  }
+}
+
+struct StoreDv32Args {
+  int64_t np;
+  const float *d0, *d1, *d2, *m0, *m1, *m2;
+  const uint32_t* pid;
+  double *dv, *dvm;
+};
+
+__global__ void __launch_bounds__(kThreads) k_store_dv32(StoreDv32Args a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.np) return;
+  const int64_t p = a.pid[j];
+  a.dv[3 * p] = a.d0[j]; a.dv[3 * p + 1] = a.d1[j]; a.dv[3 * p + 2] = a.d2[j];
+  a.dvm[3 * p] = a.m0[j]; a.dvm[3 * p + 1] = a.m1[j]; a.dvm[3 * p + 2] = a.m2[j];
+}
+
+}  // namespace
+
+// ============================================================== launches ==
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv) {
+  Sample32Args a;
+  a.P = c->P;
+  a.tt = time_terms(c->P, t0);
+  a.xv = xv;
+  const int b = c->cur;
+  a.cell = c->cell32[b];
+  a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
+  a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
+  a.m0 = c->vmf[b][0]; a.m1 = c->vmf[b][1]; a.m2 = c->vmf[b][2];
+  a.pid = c->pid[b];
+  prof_begin(c);
+  k_sample32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, xv ? KC_OTHER : KC_SAMPLE);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keys32(pic_ctx* c) {
+  Keys32Args a;
+  a.np = c->P.np;
+  a.cell = c->cell32[c->cur];
+  a.key = c->key;
+  a.rank = c->rank;
+  a.count = c->count;
+  prof_begin(c);
+  k_keys32<<<blocks_for(a.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_SORT);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather32(pic_ctx* c) {
+  Gather32Args g;
+  g.n = c->P.n;
+  g.ncell = c->P.ncell;
+  g.start = c->start;
+  g.perm = c->perm;
+  const int b = c->cur, o = 1 - c->cur;
+  for (int d = 0; d < 3; ++d) {
+    g.in[d] = c->off[b][d]; g.in[3 + d] = c->vf[b][d]; g.in[6 + d] = c->vmf[b][d];
+    g.out[d] = c->off[o][d]; g.out[3 + d] = c->vf[o][d]; g.out[6 + d] = c->vmf[o][d];
+  }
+  g.pid_in = c->pid[b];
+  g.pid_out = c->pid[o];
+  g.cell_out = c->cell32[o];
+  g.corner = c->corner;
+  int64_t blocks = (c->P.ncell * 32 + kGatherThreads - 1) / kGatherThreads;
+  const int64_t cap = (int64_t)c->num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  prof_begin(c);
+  k_sort_gather32<<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
+  prof_end(c, KC_GATHER);
+  c->launches++;
+  c->cur = o;
+  return cudaGetLastError();
+}
+
+int dsmc32_threads() { return kDsmcThreads; }
+const void* dsmc32_kernel_ptr() { return (const void*)k_dsmc32; }
+int cg32_threads() { return kThreads; }
+const void* cg32_kernel_ptr() { return (const void*)k_cg32; }
+
+cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate) {
+  Dsmc32Args a;
+  a.P = c->P;
+  const int b = c->cur;
+  a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
+  a.start = c->start;
+  a.c0 = c0;
+  a.dv0 = c->dvf[0]; a.dv1 = c->dvf[1]; a.dv2 = c->dvf[2];
+  if (separate) { a.m0 = c->dvmf[0]; a.m1 = c->dvmf[1]; a.m2 = c->dvmf[2]; }
+  else { a.m0 = a.m1 = a.m2 = nullptr; }
+  a.overlay = c->overlay32;
+  a.max_ppc = c->cfg.max_ppc;
+  a.bm_words = c->bm_words;
+  a.G = c->dsmc_G;
+  a.Kc = c->dsmc_Kc;
+  a.nchunks = (c->P.K + c->dsmc_Kc - 1) / c->dsmc_Kc;
+  a.ngroups = c->dsmc_groups;
+  a.counters = c->counters;
+  a.flags = c->flags;
+  prof_begin(c);
+  k_dsmc32<<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
+  prof_end(c, KC_DSMC);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, double th) {
+  Kick32Args a;
+  a.P = c->P;
+  const int b = c->cur;
+  a.cell = c->cell32[b];
+  a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
+  a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
+  a.m0 = c->vmf[b][0]; a.m1 = c->vmf[b][1]; a.m2 = c->vmf[b][2];
+  a.pid = c->pid[b];
+  if (with_coll) { a.dv0 = c->dvf[0]; a.dv1 = c->dvf[1]; a.dv2 = c->dvf[2]; }
+  else { a.dv0 = a.dv1 = a.dv2 = nullptr; }
+  a.E0 = c->Ef[0]; a.E1 = c->Ef[1]; a.E2 = c->Ef[2];
+  a.L0 = c->lorf[0]; a.L1 = c->lorf[1]; a.L2 = c->lorf[2];
+  a.lor_mode = drift ? (c->lor_valid ? 2 : 0) : 1;
+  a.tE = to_float(time_terms(c->P, tE));
+  a.th = to_float(time_terms(c->P, th));
+  a.drift = drift ? 1 : 0;
+  a.key = c->key;
+  a.rank = c->rank;
+  a.count = c->count;
+  prof_begin(c);
+  k_kick32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_KICK);
+  c->launches++;
+  c->lor_valid = !drift;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg32(pic_ctx* c) {
+  Cg32Args a;
+  a.n = c->P.n;
+  a.ncell = c->P.ncell;
+  a.inv_h2 = (float)((double)c->P.n * (double)c->P.n);
+  a.inv_2h = (float)(0.5 * (double)c->P.n);
+  a.b = c->bf;
+  a.x = c->phif;
+  a.r = c->cgf_r;
+  a.p = c->cgf_p;
+  a.q = c->cgf_q;
+  a.rhs_part = c->rhs_part;
+  a.rhs_blocks = (int)c->rhs_blocks;
+  a.red = c->cg_red;
+  a.bar = c->cg_bar;
+  a.info = c->cg_info;
+  a.flags = c->flags;
+  a.res = c->cg_res;
+  a.tol = c->cfg.cg_tol;
+  a.maxit = c->cfg.cg_maxit;
+  a.E0 = c->Ef[0];
+  a.E1 = c->Ef[1];
+  a.E2 = c->Ef[2];
+  cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(c->cg_info, 0, 3 * sizeof(int), c->stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&a};
+  prof_begin(c);
+  e = cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(c->cg_grid), dim3(kThreads), args, 0, c->stream);
+  prof_end(c, KC_CG);
+  c->launches++;
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_errors32(pic_ctx* c, double t) {
+  Err32Args a;
+  a.P = c->P;
+  a.tt = time_terms(c->P, t);
+  const int b = c->cur;
+  a.cell = c->cell32[b];
+  a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
+  a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
+  a.pid = c->pid[b];
+  a.phi = c->phif;
+  a.part = c->err_part;
+  a.pblocks = blocks_for(c->P.np);
+  const int nb = a.pblocks + blocks_for(c->P.ncell);
+  prof_begin(c);
+  k_err_partial32<<<nb, kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_ERR);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_state32(pic_ctx* c, double* xv, int32_t* cell_of_pid) {
+  Store32Args a;
+  a.np = c->P.np;
+  a.n = c->P.n;
+  a.h = c->P.h;
+  const int b = c->cur;
+  a.cell = c->cell32[b];
+  a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
+  a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
+  a.pid = c->pid[b];
+  a.xv = xv;
+  a.cell_of_pid = cell_of_pid;
+  prof_begin(c);
+  k_store_state32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_field32(pic_ctx* c, double* phi, double* E) {
+  StoreField32Args a;
+  a.ncell = c->P.ncell;
+  a.phi = c->phif;
+  a.E0 = c->Ef[0]; a.E1 = c->Ef[1]; a.E2 = c->Ef[2];
+  a.ophi = phi;
+  a.oE = E;
+  prof_begin(c);
+  k_store_field32<<<blocks_for(a.ncell), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_dv32(pic_ctx* c, double* dv, double* dvm) {
+  StoreDv32Args a;
+  a.np = c->P.np;
+  a.d0 = c->dvf[0]; a.d1 = c->dvf[1]; a.d2 = c->dvf[2];
+  a.m0 = c->dvmf[0]; a.m1 = c->dvmf[1]; a.m2 = c->dvmf[2];
+  a.pid = c->pid[c->cur];
+  a.dv = dv;
+  a.dvm = dvm;
+  prof_begin(c);
+  k_store_dv32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace pic

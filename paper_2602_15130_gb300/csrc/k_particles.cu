@@ -665,6 +665,16 @@ cudaError_t launch_errors(pic_ctx* c, double t) {
 
 int err_blocks_needed(int64_t np, int64_t ncell) { return blocks_for(np) + blocks_for(ncell); }
 
+cudaError_t launch_err_final(pic_ctx* c, int nb) {
+  ErrArgs a;
+  a.P = c->P;
+  a.part = c->err_part;
+  a.out = c->err_out;
+  k_err_final<<<1, kFinalThreads, 0, c->stream>>>(a, nb);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 }  // namespace pic
 
 namespace pic {

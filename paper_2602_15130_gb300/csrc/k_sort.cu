@@ -263,7 +263,7 @@ cudaError_t launch_keys(pic_ctx* c) {
 
 int64_t scan_blocks_needed(int64_t ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 
-cudaError_t launch_sort(pic_ctx* c) {
+cudaError_t launch_scan_scatter(pic_ctx* c) {
   const int64_t m = c->P.ncell;
   const int64_t nb = scan_blocks_needed(m);
   prof_begin(c);
@@ -279,6 +279,13 @@ cudaError_t launch_sort(pic_ctx* c) {
   k_scatter<<<blocks_for(s.np), kThreads, 0, c->stream>>>(s);
   prof_end(c, KC_SORT);
   c->launches += 4;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort(pic_ctx* c) {
+  const int64_t m = c->P.ncell;
+  cudaError_t e = launch_scan_scatter(c);
+  if (e != cudaSuccess) return e;
 
   GatherArgs g;
   g.n = c->P.n;

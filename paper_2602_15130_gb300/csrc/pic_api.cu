@@ -17,6 +17,10 @@ const void* cg_kernel_ptr();
 int64_t scan_blocks_needed(int64_t ncell);
 int rhs_blocks_needed(int64_t ncell);
 int err_blocks_needed(int64_t np, int64_t ncell);
+int dsmc32_threads();
+const void* dsmc32_kernel_ptr();
+int cg32_threads();
+const void* cg32_kernel_ptr();
 
 // Resolve recorded event pairs into per-class totals (synchronises).
 void prof_flush(pic_ctx* c) {
@@ -154,41 +158,64 @@ void dev_free(pic_ctx* c, void* p) {
 template <class F>
 void for_each_buffer(pic_ctx* c, F f) {
   const size_t np = (size_t)c->P.np, nc = (size_t)c->P.ncell;
-  for (int b = 0; b < 2; ++b) {
+  const size_t lanes = (size_t)c->dsmc_grid * (c->dsmc_block / 32) * 32 * (size_t)c->cfg.max_ppc * 3;
+  if (!c->mixed) {
+    for (int b = 0; b < 2; ++b)
+      for (int d = 0; d < 3; ++d) {
+        f((void**)&c->x[b][d], np * 8);
+        f((void**)&c->v[b][d], np * 8);
+        f((void**)&c->xm[b][d], np * 8);
+        f((void**)&c->vm[b][d], np * 8);
+      }
     for (int d = 0; d < 3; ++d) {
-      f((void**)&c->x[b][d], np * 8);
-      f((void**)&c->v[b][d], np * 8);
-      f((void**)&c->xm[b][d], np * 8);
-      f((void**)&c->vm[b][d], np * 8);
+      f((void**)&c->lor[d], np * 8);
+      f((void**)&c->dv[d], np * 8);
+      f((void**)&c->dvm[d], np * 8);
+      f((void**)&c->E[d], nc * 8);
     }
-    f((void**)&c->pid[b], np * 4);
+    f((void**)&c->b, nc * 8);
+    f((void**)&c->phi, nc * 8);
+    f((void**)&c->cg_r, nc * 8);
+    f((void**)&c->cg_p[0], nc * 8);
+    f((void**)&c->cg_p[1], nc * 8);
+    f((void**)&c->cg_q, nc * 8);
+    f((void**)&c->overlay, lanes * 8);
+  } else {
+    for (int b = 0; b < 2; ++b) {
+      f((void**)&c->cell32[b], np * 4);
+      for (int d = 0; d < 3; ++d) {
+        f((void**)&c->off[b][d], np * 4);
+        f((void**)&c->vf[b][d], np * 4);
+        f((void**)&c->vmf[b][d], np * 4);
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      f((void**)&c->lorf[d], np * 4);
+      f((void**)&c->dvf[d], np * 4);
+      f((void**)&c->dvmf[d], np * 4);
+      f((void**)&c->Ef[d], nc * 4);
+    }
+    f((void**)&c->bf, nc * 4);
+    f((void**)&c->phif, nc * 4);
+    f((void**)&c->cgf_r, nc * 4);
+    f((void**)&c->cgf_p, nc * 4);
+    f((void**)&c->cgf_q, nc * 4);
+    f((void**)&c->overlay32, lanes * 4);
   }
+  for (int b = 0; b < 2; ++b) f((void**)&c->pid[b], np * 4);
   f((void**)&c->key, np * 4);
   f((void**)&c->rank, np * 4);
   f((void**)&c->perm, np * 4);
   f((void**)&c->count, nc * 4);
   f((void**)&c->start, (nc + 1) * 4);
   f((void**)&c->scan_blocks, (size_t)c->scan_nblocks * 4 + 16);
-  for (int d = 0; d < 3; ++d) {
-    f((void**)&c->lor[d], np * 8);
-    f((void**)&c->dv[d], np * 8);
-    f((void**)&c->dvm[d], np * 8);
-    f((void**)&c->E[d], nc * 8);
-  }
   f((void**)&c->corner, 8 * nc * 8);
   f((void**)&c->rho, nc * 8);
-  f((void**)&c->b, nc * 8);
   f((void**)&c->rhs_part, (size_t)c->rhs_blocks * 8);
-  f((void**)&c->phi, nc * 8);
-  f((void**)&c->cg_r, nc * 8);
-  f((void**)&c->cg_p[0], nc * 8);
-  f((void**)&c->cg_p[1], nc * 8);
-  f((void**)&c->cg_q, nc * 8);
   f((void**)&c->cg_red, (size_t)4 * c->cg_grid * 8);
   f((void**)&c->cg_bar, 64);
   f((void**)&c->cg_info, 64);
   f((void**)&c->cg_res, 64);
-  f((void**)&c->overlay, (size_t)c->dsmc_grid * (c->dsmc_block / 32) * 32 * (size_t)c->cfg.max_ppc * 3 * 8);
   f((void**)&c->counters, 8 * 8);
   f((void**)&c->flags, 64);
   f((void**)&c->err_part, (size_t)c->err_blocks * 14 * 8);
@@ -221,10 +248,18 @@ pic_status check_pending(pic_ctx* c) {
 pic_status sort_and_field(pic_ctx* c, double t) {
   c->lor_valid = false;
   CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-  CK(launch_keys(c));
-  CK(launch_sort(c));
-  CK(launch_rhs(c, t));
-  CK(launch_cg(c));
+  if (c->mixed) {
+    CK(launch_keys32(c));
+    CK(launch_scan_scatter(c));
+    CK(launch_gather32(c));
+    CK(launch_rhs(c, t));
+    CK(launch_cg32(c));
+  } else {
+    CK(launch_keys(c));
+    CK(launch_sort(c));
+    CK(launch_rhs(c, t));
+    CK(launch_cg(c));
+  }
   return PIC_OK;
 }
 
@@ -275,7 +310,7 @@ pic_status pic_validate_config(const pic_config* c) {
   for (int d = 0; d < 3; ++d)
     if (!isfinite(c->v_mean[d]) || !isfinite(c->phi_shift[d])) return PIC_EINVAL;
   if (!isfinite(c->phi_amp) || !(c->phi_T > 0.0)) return PIC_EINVAL;
-  if (c->precision != PIC_FP64) return PIC_EINVAL;
+  if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return PIC_EINVAL;
   if (c->max_ppc < 0 || c->max_ppc > 65536) return PIC_EINVAL;
   if (!(c->cg_tol > 0.0) || c->cg_maxit < 1) return PIC_EINVAL;
   const int64_t ncell = (int64_t)c->n * c->n * c->n;
@@ -322,6 +357,7 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   if (c->cfg.max_ppc == 0) c->cfg.max_ppc = 512;
   c->cfg.max_ppc = (c->cfg.max_ppc + 31) / 32 * 32;
   c->stream = (cudaStream_t)stream;
+  c->mixed = c->cfg.precision == PIC_MIXED;
   if (alloc) {
     c->alloc = *alloc;
     c->have_alloc = true;
@@ -341,7 +377,8 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   c->rhs_blocks = rhs_blocks_needed(c->P.ncell);
   c->err_blocks = err_blocks_needed(c->P.np, c->P.ncell);
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_kernel_ptr(), cg_threads(), 0);
+  const void* cg_fn = c->mixed ? cg32_kernel_ptr() : cg_kernel_ptr();
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_fn, cg_threads(), 0);
   if (e != cudaSuccess || occ < 1) {
     cudaGetLastError();
     delete c;
@@ -357,10 +394,11 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   c->dsmc_G = K < 32 ? 32 / K : 1;
   c->dsmc_groups = (c->P.ncell + c->dsmc_G - 1) / c->dsmc_G;
   c->bm_words = c->cfg.max_ppc / 32;
-  c->dsmc_block = dsmc_threads();
+  c->dsmc_block = c->mixed ? dsmc32_threads() : dsmc_threads();
+  const void* dsmc_fn = c->mixed ? dsmc32_kernel_ptr() : dsmc_kernel_ptr();
   c->dsmc_smem = (size_t)(c->dsmc_block / 32) * 32 * c->bm_words * 4;
   if (c->dsmc_smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(dsmc_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->dsmc_smem);
+    e = cudaFuncSetAttribute(dsmc_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->dsmc_smem);
     if (e != cudaSuccess) {
       cudaGetLastError();
       delete c;
@@ -368,7 +406,7 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
     }
   }
   int docc = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&docc, dsmc_kernel_ptr(), c->dsmc_block, c->dsmc_smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&docc, dsmc_fn, c->dsmc_block, c->dsmc_smem);
   if (e != cudaSuccess || docc < 1) {
     cudaGetLastError();
     delete c;
@@ -390,7 +428,8 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
     pic_destroy(c);
     return PIC_ENOMEM;
   }
-  e = cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream);
+  e = c->mixed ? cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream)
+               : cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cg_info, 0, 64, c->stream);
@@ -411,8 +450,13 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
   c->t0 = t0;
   c->step = 0;
   c->cur = 0;
-  CK(cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream));
-  CK(launch_sample(c, t0));
+  if (c->mixed) {
+    CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
+    CK(launch_sample32(c, t0, nullptr));
+  } else {
+    CK(cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream));
+    CK(launch_sample(c, t0));
+  }
   pic_status s = sort_and_field(c, t0);
   if (s != PIC_OK) return s;
   c->sampled = true;
@@ -427,7 +471,8 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
   c->t0 = t0;
   c->step = step;
   c->cur = 0;
-  CK(launch_load_state(c, c->stage, time_at(c, (double)step)));
+  if (c->mixed) CK(launch_sample32(c, time_at(c, (double)step), c->stage));
+  else CK(launch_load_state(c, c->stage, time_at(c, (double)step)));
   pic_status s = sort_and_field(c, time_at(c, (double)step));
   if (s != PIC_OK) return s;
   c->sampled = true;
@@ -441,17 +486,29 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
   for (int32_t it = 0; it < nsteps; ++it) {
     const int64_t n = c->step;
     const double tn = time_at(c, (double)n), th = time_at(c, (double)n + 0.5), tn1 = time_at(c, (double)(n + 1));
-    // v^{n+1/2} and x^{n+1}: collision call A at (x^n, v^n)
-    if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n), false));
-    CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-    CK(launch_kick(c, tn, coll, true, th));
-    // cells of x^{n+1}, field at t^{n+1}
-    CK(launch_sort(c));
-    CK(launch_rhs(c, tn1));
-    CK(launch_cg(c));
-    // v^{n+1}: collision call B at (x^{n+1}, v^{n+1/2})
-    if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n + 1), false));
-    CK(launch_kick(c, tn1, coll, false, 0.0));
+    if (c->mixed) {
+      if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n), false));
+      CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+      CK(launch_kick32(c, tn, coll, true, th));
+      CK(launch_scan_scatter(c));
+      CK(launch_gather32(c));
+      CK(launch_rhs(c, tn1));
+      CK(launch_cg32(c));
+      if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n + 1), false));
+      CK(launch_kick32(c, tn1, coll, false, 0.0));
+    } else {
+      // v^{n+1/2} and x^{n+1}: collision call A at (x^n, v^n)
+      if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n), false));
+      CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+      CK(launch_kick(c, tn, coll, true, th));
+      // cells of x^{n+1}, field at t^{n+1}
+      CK(launch_sort(c));
+      CK(launch_rhs(c, tn1));
+      CK(launch_cg(c));
+      // v^{n+1}: collision call B at (x^{n+1}, v^{n+1/2})
+      if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n + 1), false));
+      CK(launch_kick(c, tn1, coll, false, 0.0));
+    }
     c->step = n + 1;
   }
   return nsteps > 0 ? check_pending(c) : PIC_OK;
@@ -461,15 +518,27 @@ pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
   if (!c || !dv || !dvM || (phase != 0 && phase != 1)) return PIC_EINVAL;
   if (!c->sampled) return PIC_ESTATE;
   const size_t bytes = (size_t)c->P.np * 3 * 8;
-  if (c->cfg.K > 0) {
-    CK(launch_dsmc(c, (uint32_t)(2 * c->step + phase), true));
-  } else {
-    for (int d = 0; d < 3; ++d) {
-      CK(cudaMemsetAsync(c->dv[d], 0, (size_t)c->P.np * 8, c->stream));
-      CK(cudaMemsetAsync(c->dvm[d], 0, (size_t)c->P.np * 8, c->stream));
+  if (c->mixed) {
+    if (c->cfg.K > 0) {
+      CK(launch_dsmc32(c, (uint32_t)(2 * c->step + phase), true));
+    } else {
+      for (int d = 0; d < 3; ++d) {
+        CK(cudaMemsetAsync(c->dvf[d], 0, (size_t)c->P.np * 4, c->stream));
+        CK(cudaMemsetAsync(c->dvmf[d], 0, (size_t)c->P.np * 4, c->stream));
+      }
     }
+    CK(launch_store_dv32(c, c->stage, c->stage + 3 * c->P.np));
+  } else {
+    if (c->cfg.K > 0) {
+      CK(launch_dsmc(c, (uint32_t)(2 * c->step + phase), true));
+    } else {
+      for (int d = 0; d < 3; ++d) {
+        CK(cudaMemsetAsync(c->dv[d], 0, (size_t)c->P.np * 8, c->stream));
+        CK(cudaMemsetAsync(c->dvm[d], 0, (size_t)c->P.np * 8, c->stream));
+      }
+    }
+    CK(launch_store_dv(c, c->stage, c->stage + 3 * c->P.np));
   }
-  CK(launch_store_dv(c, c->stage, c->stage + 3 * c->P.np));
   CK(cudaMemcpyAsync(dv, c->stage, bytes, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(dvM, c->stage + 3 * c->P.np, bytes, cudaMemcpyDefault, c->stream));
   return check_pending(c);
@@ -478,7 +547,12 @@ pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
 pic_status pic_mms_error(pic_ctx* c, pic_errors* out) {
   if (!c || !out) return PIC_EINVAL;
   if (!c->sampled) return PIC_ESTATE;
-  CK(launch_errors(c, time_at(c, (double)c->step)));
+  if (c->mixed) {
+    CK(launch_errors32(c, time_at(c, (double)c->step)));
+    CK(launch_err_final(c, c->err_blocks));
+  } else {
+    CK(launch_errors(c, time_at(c, (double)c->step)));
+  }
   double h[14];
   CK(cudaMemcpyAsync(h, c->err_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -493,7 +567,8 @@ pic_status pic_get_state(pic_ctx* c, double* x, double* v) {
   if (!c || !x || !v) return PIC_EINVAL;
   if (!c->sampled) return PIC_ESTATE;
   const size_t bytes = (size_t)c->P.np * 3 * 8;
-  CK(launch_store_state(c, c->stage));
+  if (c->mixed) CK(launch_store_state32(c, c->stage, nullptr));
+  else CK(launch_store_state(c, c->stage));
   CK(cudaMemcpyAsync(x, c->stage, bytes, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(v, c->stage + 3 * c->P.np, bytes, cudaMemcpyDefault, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -504,35 +579,42 @@ pic_status pic_get_field(pic_ctx* c, double* rho, double* phi, double* E) {
   if (!c) return PIC_EINVAL;
   if (!c->sampled) return PIC_ESTATE;
   const size_t nc = (size_t)c->P.ncell;
-  double* srho = c->stage;
-  double* sphi = c->stage + nc;
-  double* sE = c->stage + 2 * nc;
-  const bool fits = 5 * nc <= 6 * (size_t)c->P.np;
+  double* sphi = c->stage;
+  double* sE = c->stage + nc;
+  const bool fits = 4 * nc <= 6 * (size_t)c->P.np;
+  if (rho) CK(cudaMemcpyAsync(rho, c->rho, nc * 8, cudaMemcpyDefault, c->stream));
   if (fits) {
-    CK(launch_store_field(c, rho ? srho : nullptr, phi ? sphi : nullptr, E ? sE : nullptr));
-    if (rho) CK(cudaMemcpyAsync(rho, srho, nc * 8, cudaMemcpyDefault, c->stream));
+    if (c->mixed) CK(launch_store_field32(c, phi ? sphi : nullptr, E ? sE : nullptr));
+    else CK(launch_store_field(c, nullptr, phi ? sphi : nullptr, E ? sE : nullptr));
     if (phi) CK(cudaMemcpyAsync(phi, sphi, nc * 8, cudaMemcpyDefault, c->stream));
     if (E) CK(cudaMemcpyAsync(E, sE, 3 * nc * 8, cudaMemcpyDefault, c->stream));
-  } else {
-    // fewer particles than nodes: copy the SoA mesh arrays directly
-    if (rho) CK(cudaMemcpyAsync(rho, c->rho, nc * 8, cudaMemcpyDefault, c->stream));
-    if (phi) CK(cudaMemcpyAsync(phi, c->phi, nc * 8, cudaMemcpyDefault, c->stream));
-    if (E) {
-      double* tmp = (double*)malloc(3 * nc * 8);
-      if (!tmp) return PIC_ENOMEM;
-      double* comp = (double*)malloc(nc * 8);
-      if (!comp) { free(tmp); return PIC_ENOMEM; }
-      for (int d = 0; d < 3; ++d) {
-        cudaError_t e = cudaMemcpyAsync(comp, c->E[d], nc * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) { free(tmp); free(comp); return cuda_status(e); }
-        for (size_t i = 0; i < nc; ++i) tmp[3 * i + d] = comp[i];
+  } else if (phi || E) {
+    // fewer particles than nodes: stage through host memory
+    const size_t esz = c->mixed ? 4 : 8;
+    unsigned char* comp = (unsigned char*)malloc(nc * esz);
+    double* tmp = (double*)malloc(3 * nc * 8);
+    if (!comp || !tmp) { free(comp); free(tmp); return PIC_ENOMEM; }
+    const void* srcs[4] = {c->mixed ? (const void*)c->phif : (const void*)c->phi,
+                           c->mixed ? (const void*)c->Ef[0] : (const void*)c->E[0],
+                           c->mixed ? (const void*)c->Ef[1] : (const void*)c->E[1],
+                           c->mixed ? (const void*)c->Ef[2] : (const void*)c->E[2]};
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+      if ((q == 0 && !phi) || (q > 0 && !E)) continue;
+      e = cudaMemcpyAsync(comp, srcs[q], nc * esz, cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) break;
+      for (size_t i = 0; i < nc; ++i) {
+        const double val = c->mixed ? (double)((const float*)comp)[i] : ((const double*)comp)[i];
+        if (q == 0) tmp[i] = val;
+        else tmp[3 * i + (q - 1)] = val;
       }
-      cudaError_t e = cudaMemcpy(E, tmp, 3 * nc * 8, cudaMemcpyDefault);
-      free(tmp);
-      free(comp);
-      if (e != cudaSuccess) return cuda_status(e);
+      if (q == 0) e = cudaMemcpy(phi, tmp, nc * 8, cudaMemcpyDefault);
     }
+    if (e == cudaSuccess && E) e = cudaMemcpy(E, tmp, 3 * nc * 8, cudaMemcpyDefault);
+    free(comp);
+    free(tmp);
+    if (e != cudaSuccess) return cuda_status(e);
   }
   CK(cudaStreamSynchronize(c->stream));
   return PIC_OK;
@@ -544,7 +626,12 @@ pic_status pic_get_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* count, int32_
   const size_t np = (size_t)c->P.np, nc = (size_t)c->P.ncell;
   int32_t* scell = (int32_t*)c->stage;            // fits: 6 np doubles = 12 np ints
   int32_t* sperm = (int32_t*)c->stage + np;
-  CK(launch_store_sort(c, cell_of_pid ? scell : nullptr, perm ? sperm : nullptr));
+  if (c->mixed) {
+    if (cell_of_pid) CK(launch_store_state32(c, nullptr, scell));
+    if (perm) CK(cudaMemcpyAsync(sperm, c->pid[c->cur], np * 4, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(launch_store_sort(c, cell_of_pid ? scell : nullptr, perm ? sperm : nullptr));
+  }
   if (cell_of_pid) CK(cudaMemcpyAsync(cell_of_pid, scell, np * 4, cudaMemcpyDefault, c->stream));
   if (perm) CK(cudaMemcpyAsync(perm, sperm, np * 4, cudaMemcpyDefault, c->stream));
   if (count) CK(cudaMemcpyAsync(count, c->count, nc * 4, cudaMemcpyDefault, c->stream));

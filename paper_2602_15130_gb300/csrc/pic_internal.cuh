@@ -182,6 +182,8 @@ struct pic_ctx {
   pic_allocator alloc;
   bool have_alloc;
 
+  bool mixed;       // precision form (PIC_MIXED)
+
   // particles, buffer [b][component]
   double* x[2][3];
   double* v[2][3];
@@ -202,6 +204,22 @@ struct pic_ctx {
   double* lor[3];   // dt q/m (E_p - E^M_p) of the last kick without drift
   bool lor_valid;   // lor matches the current order, positions and field
   double* dvm[3];   // source term when requested separately
+
+  // precision form: int32 cell + FP32 offset, FP32 v and v^M, FP32 mesh
+  int32_t* cell32[2];
+  float* off[2][3];
+  float* vf[2][3];
+  float* vmf[2][3];
+  float* dvf[3];
+  float* dvmf[3];
+  float* lorf[3];
+  float* Ef[3];
+  float* phif;
+  float* bf;
+  float* cgf_r;
+  float* cgf_p;
+  float* cgf_q;
+  float* overlay32;
 
   // mesh
   double* corner;   // [8][ncell] per-cell CIC partials
@@ -277,6 +295,19 @@ TimeTerms time_terms(const Params& P, double t);
 cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E);
 cudaError_t launch_store_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* perm);
 cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm);
+cudaError_t launch_scan_scatter(pic_ctx* c);   // scan of counts + scatter into perm
+cudaError_t launch_err_final(pic_ctx* c, int nblocks);
+// precision form
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv_dev);
+cudaError_t launch_keys32(pic_ctx* c);
+cudaError_t launch_gather32(pic_ctx* c);
+cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate_source);
+cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_collisions, bool drift, double th);
+cudaError_t launch_cg32(pic_ctx* c);
+cudaError_t launch_errors32(pic_ctx* c, double t);
+cudaError_t launch_store_state32(pic_ctx* c, double* xv_dev, int32_t* cell_of_pid);
+cudaError_t launch_store_field32(pic_ctx* c, double* phi, double* E);
+cudaError_t launch_store_dv32(pic_ctx* c, double* dv, double* dvm);
 
 // Profiling brackets (no-ops unless profiling is on).
 void prof_begin(pic_ctx* c);

@@ -68,13 +68,27 @@ def refinement_level(level: int, collisions: bool = True, **kw) -> dict:
     return p
 
 
+PRECISION_CG_TOL = 1e-6
+
+
 def precision_form(**kw) -> dict:
     """128^3 cells, 64 particles per cell (134,217,728), K = 32, dt = 0.005,
-    200 steps; sigma0 from the 0.1-collision rule at these settings."""
+    200 steps, FP32 particle state (int32 cell + FP32 offset); sigma0 from
+    the 0.1-collision rule at these settings; CG to a relative residual of
+    1e-6 (FP32 vectors)."""
     n, ppc, dt = 128, 64, 0.005
-    p = base(n, ppc * n ** 3, dt, 32, hard_sphere_sigma0(ppc, dt), steps=200)
+    p = base(n, ppc * n ** 3, dt, 32, hard_sphere_sigma0(ppc, dt), steps=200, precision=1,
+             cg_tol=PRECISION_CG_TOL)
     p.update(kw)
     return p
+
+
+def mixed(p: dict) -> dict:
+    """The same workload in the precision form."""
+    q = dict(p)
+    q["precision"] = 1
+    q["cg_tol"] = max(p.get("cg_tol", 1e-10), PRECISION_CG_TOL)
+    return q
 
 
 def scaled(p: dict, n: int) -> dict:

@@ -1,0 +1,138 @@
+"""Precision form (PIC_MIXED) against the FP64 oracle and the FP64 GPU path.
+
+Stated error of the precision form (checked here):
+  - sampling: positions within 1e-7 (absolute, FP32 offsets in a cell of
+    width h), velocities within 1e-6 relative; sort bit-exact;
+  - charge density within 1e-6 relative, potential and field within 1e-4
+    relative (FP32 vectors, CG to 1e-6);
+  - collisions: candidate pairs identical except where FP32 changes an
+    N_pairs floor; accept decisions identical except FP32 near ties; all
+    but a small fraction of particles (those touched by a differing
+    decision) within 2e-5 of the oracle's <dv>;
+  - steps: all but a small fraction of particles within 1e-5 (positions)
+    and 1e-4 (velocities) after 10 steps; error norms within 3% of the
+    FP64 ones, so the precision form does not raise the error floor.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import oracle as O
+from paper_2602_15130_gb300 import Pic, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+def mixed(**kw):
+    return workloads.mixed(workloads.smallest(**kw))
+
+
+def dpos(a, b):
+    d = np.abs(a - b)
+    return np.minimum(d, 1.0 - d)
+
+
+CASES = {"smallest": mixed(), "ragged": mixed(n=12, n_particles=12 ** 3 * 9 + 37), "k40": mixed(n=6, n_particles=6 ** 3 * 12 + 5, K=40)}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_sampling_and_sort(name):
+    p = CASES[name]
+    g, o = Pic(p), O.Oracle(p)
+    g.sample_mms(0.2)
+    o.sample(0.2)
+    x, v = g.get_state()
+    xo, vo = o.state()
+    assert dpos(x, xo).max() < 1e-7
+    assert (np.abs(v - vo) / np.maximum(1.0, np.abs(vo))).max() < 1e-6
+    for a, b in zip(g.get_sort(), o.sort()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_field(name):
+    p = CASES[name]
+    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-13))
+    g.sample_mms(0.1)
+    o.sample(0.1)
+    rho, phi, E = g.get_field()
+    ro, po, Eo = o.field()
+    assert np.abs(rho - ro).max() <= 1e-6 * np.abs(ro).max()
+    assert np.abs(phi - po).max() <= 1e-4 * np.abs(po).max()
+    assert np.abs(E - Eo).max() <= 1e-4 * np.abs(Eo).max()
+
+
+@pytest.mark.parametrize("name", ["smallest", "ragged", "k40"])
+def test_mixed_collisions(name):
+    p = CASES[name]
+    g, o = Pic(p), O.Oracle(p)
+    g.sample_mms(0.0)
+    o.sample(0.0)
+    g.reset_stats()
+    o.reset_stats()
+    dv, dvm = g.collide_avg(0)
+    dvo, dvmo = o.collide_avg(0)
+    sg, so = g.stats(), o.stats()
+    assert abs(sg["n_cand"] - so["n_cand"]) <= 2 + 1e-4 * so["n_cand"]
+    assert abs(sg["n_coll"] - so["n_coll"]) <= 2 + 1e-3 * so["n_coll"]
+    assert np.abs(dvm - dvmo).max() <= 1e-5 * max(1.0, np.abs(dvmo).max())
+    bad = (np.abs(dv - dvo) > 2e-5).any(axis=1)
+    assert bad.mean() <= 0.01, bad.mean()
+
+
+@pytest.mark.parametrize("name", ["smallest", "ragged"])
+def test_mixed_steps_track_oracle(name):
+    p = CASES[name]
+    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-12))
+    g.sample_mms(0.0)
+    o.sample(0.0)
+    g.step(10)
+    o.step(10)
+    x, v = g.get_state()
+    xo, vo = o.state()
+    far_x = (dpos(x, xo) > 1e-5).any(axis=1)
+    far_v = (np.abs(v - vo) > 1e-4).any(axis=1)
+    assert far_x.mean() <= 0.01 and far_v.mean() <= 0.02, (far_x.mean(), far_v.mean())
+    eg = g.mms_error()["array"]
+    eo = o.errors()
+    assert np.all(np.abs(eg - eo) <= 0.03 * eo + 1e-7), (eg, eo)
+
+
+def test_mixed_error_floor_matches_fp64_gpu():
+    """32^3, 1M particles, 20 steps: the precision form's MMS error norms
+    match the FP64 path's (the discretisation error floor is unchanged)."""
+    p64 = workloads.refinement_level(2)
+    p32 = workloads.mixed(p64)
+    a, b = Pic(p64), Pic(p32)
+    for s in (a, b):
+        s.sample_mms(0.0)
+        s.step(20)
+    e64 = a.mms_error()["array"]
+    e32 = b.mms_error()["array"]
+    assert np.all(np.abs(e32 - e64) <= 0.03 * e64), (e32, e64)
+
+
+def test_mixed_set_get_state_round_trip_and_determinism():
+    p = CASES["smallest"]
+    x, v = inputs.particles(p["n_particles"], seed=3)
+    a, b = Pic(p), Pic(p)
+    for s in (a, b):
+        s.set_state(x, v)
+    xa, va = a.get_state()
+    assert dpos(xa, x).max() < 1e-7 and np.abs(va - v).max() < 1e-6 * np.abs(v).max()
+    a.step(3)
+    b.step(3)
+    ya, wa = a.get_state()
+    yb, wb = b.get_state()
+    assert np.array_equal(ya, yb) and np.array_equal(wa, wb)
