@@ -23,7 +23,8 @@ inline int blocks_for(int64_t n, int t = kThreads) {
   return (int)(b < 1 ? 1 : b);
 }
 
-// fixed-shape block sum; result valid in every thread
+// fixed-shape block sum (sh holds at least 33 doubles); thread 0 adds the
+// warp totals and the result is broadcast to every thread
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -31,9 +32,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   __syncthreads();
   if (lane == 0) sh[w] = v;
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < nw; ++i) t += sh[i];
-  return t;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += sh[i];
+    sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
 }
 
 struct RhsArgs {
@@ -45,7 +50,7 @@ struct RhsArgs {
 };
 
 __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
-  __shared__ double sh[32];
+  __shared__ double sh[40];
   const Params& P = a.P;
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double bv = 0.0;
@@ -163,6 +168,8 @@ __device__ __forceinline__ Nbr neighbours(int id, int n, int nn) {
 
 __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
   __shared__ double sh[40];
+  __shared__ double scal[2];  // scalars formed once per block by thread 0
+  __shared__ int stop;
   const int n = a.n, nn = a.n * a.n;
   const int m = (int)a.ncell;
   const int stride = gridDim.x * blockDim.x;
@@ -188,11 +195,9 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
   }
   {
     const double s1 = block_sum(rr_loc, sh);
-    const double s2 = block_sum(bb_loc, sh + 8);
-    if (threadIdx.x == 0) {
-      slot(ph)[blockIdx.x] = s1;
-      slot(ph)[G + blockIdx.x] = s2;
-    }
+    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s1;
+    const double s2 = block_sum(bb_loc, sh);
+    if (threadIdx.x == 0) slot(ph)[G + blockIdx.x] = s2;
   }
   if (!grid_barrier(a.bar, a.info, a.flags)) return;
   double rr = grid_total(slot(ph), G, sh);
@@ -203,8 +208,10 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
   double* p = a.p0;
   const double thresh = a.tol * sqrt(bb);
   while (true) {
-    if (bb == 0.0 || sqrt(rr) <= thresh) break;
-    if (it >= a.maxit) { status = 1; break; }
+    if (threadIdx.x == 0) stop = (bb == 0.0 || sqrt(rr) <= thresh) ? 1 : (it >= a.maxit ? 2 : 0);
+    __syncthreads();
+    if (stop == 1) break;
+    if (stop == 2) { status = 1; break; }
     // p = r + beta p
     if (it == 0) {
       for (int id = t0; id < m; id += stride) p[id] = a.r[id];
@@ -229,7 +236,9 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
     if (!grid_barrier(a.bar, a.info, a.flags)) return;
     const double pq = grid_total(slot(ph), G, sh);
     ph ^= 1;
-    const double alpha = rr / pq;
+    if (threadIdx.x == 0) scal[0] = rr / pq;
+    __syncthreads();
+    const double alpha = scal[0];
     double rn_loc = 0.0;
     for (int id = t0; id < m; id += stride) {
       a.x[id] += alpha * p[id];
@@ -245,7 +254,9 @@ __global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
     const double rr_new = grid_total(slot(ph), G, sh);
     ph ^= 1;
     ++it;
-    beta = rr_new / rr;
+    if (threadIdx.x == 0) scal[1] = rr_new / rr;
+    __syncthreads();
+    beta = scal[1];
     rr = rr_new;
   }
   // zero-mean projection
@@ -405,7 +416,7 @@ double* g_noalloc_ptr[64] = {nullptr};
 
 // copy b into the scratch and write per-block partial sums for its mean
 __global__ void __launch_bounds__(kThreads) k_noalloc_prep(const double* b, double* bcopy, double* part, int64_t m) {
-  __shared__ double sh[32];
+  __shared__ double sh[40];
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
   if (id < m) {

@@ -73,28 +73,31 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int off) {
 }
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
-// FP32 x^M: Newton from y = T (within A/(2 pi) of the root); stops when a
-// correction is below 2^-23 (the FP32 resolution of y); returns x^M and
-// sin(2 pi (x^M - c t)).
-__device__ __forceinline__ float xm_solve_f(float A, float A2pi, const TimeTermsF& tt, float xi, float* s_out) {
-  const float T = xi - tt.ct - A2pi * tt.cos2ct;
-  float y = T, s = 0.f, c = 1.f;
-  for (int it = 0; it < 8; ++it) {
-    sincospif(2.f * y, &s, &c);
-    const float dy = (y - A2pi * c - T) / (1.f + A * s);
-    y -= dy;
-    if (fabsf(dy) <= 0x1p-23f) break;
-  }
-  *s_out = sinpif(2.f * y);
-  return y + tt.ct;
+// sin(2 pi (x^M - c t)) in FP32: G^{-1} from the Hermite table, one Newton
+// correction, sine updated to first order.
+__device__ __forceinline__ float xm_sin_f(const ParamsF& P, const TimeTermsF& tt, float xi) {
+  const float T = xi - tt.ct - P.fx_a2pi * tt.cos2ct;
+  const float fl = floorf(T);
+  const float t = (T - fl) * (float)P.ginv_M;
+  int k = (int)t;
+  k = k >= P.ginv_M ? P.ginv_M - 1 : k;
+  const float u = t - (float)k, u2 = u * u, u3 = u2 * u, h = 1.f / (float)P.ginv_M;
+  const float2 q0 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k);
+  const float2 q1 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k + 1);
+  const float y = fl + (2.f * u3 - 3.f * u2 + 1.f) * q0.x + (u3 - 2.f * u2 + u) * h * q0.y +
+                  (3.f * u2 - 2.f * u3) * q1.x + (u3 - u2) * h * q1.y;
+  float s, c;
+  sincospif(2.f * y, &s, &c);
+  const float dy = (y - P.fx_a2pi * c - T) / (1.f + P.fx_amp * s);
+  return s - 6.283185307f * c * dy;
 }
 
-__device__ __forceinline__ float hs_R_f(const Params& P, float a) {
+__device__ __forceinline__ float hs_R_f(const ParamsF& P, float a) {
   const float a2 = a * a;
   if (a < 0.1f) {
-    float acc = (float)P.R_series[4];
+    float acc = P.R_series[4];
 #pragma unroll
-    for (int j = 3; j >= 0; --j) acc = fmaf(acc, a2, (float)P.R_series[j]);
+    for (int j = 3; j >= 0; --j) acc = fmaf(acc, a2, P.R_series[j]);
     return acc;
   }
   const float ia = 1.f / a, ia2 = ia * ia;
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
       x[d] = a.xv[3 * i + d];
       v[d] = a.xv[3 * P.np + 3 * i + d];
     } else {
-      x[d] = wrap_unit(xm_solve(P, a.tt, xi[d], xi[d], &s));
+      x[d] = wrap_unit(xm_solve(P, a.tt, xi[d], &s));
       v[d] = vm[d];
     }
   }
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
 
 // ----------------------------------------------------------- collisions --
 struct Dsmc32Args {
-  Params P;
+  ParamsF P;
   const float *v0, *v1, *v2;
   const int32_t* start;
   uint32_t c0;
@@ -292,12 +295,12 @@ __device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const floa
   }
 }
 
-__device__ void ntc_outcome_f(const Params& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
+__device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
                               const float* v1, const float* v2, uint32_t* bm, float* ov, Counts32& cnt) {
   const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
-  const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * (float)P.pmax;
+  const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
   const int npairs = (int)floorf(base + unif24(u.x));
-  const float gmax = (float)P.gmax;
+  const float gmax = P.gmax;
   for (int s = 0; s < npairs; ++s) {
     const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
@@ -330,7 +333,7 @@ __device__ void ntc_outcome_f(const Params& P, uint32_t c0, uint32_t cell, uint3
     const float ug = unif24(b0.z) * gmax;
     const float ug2 = ug * ug;
     ++cnt.cand;
-    if (g2 > gmax * gmax) ++cnt.gmax;
+    if (g2 > P.gmax2) ++cnt.gmax;
     if (fabsf(ug2 - g2) < 2e-6f * g2) ++cnt.tie;
     if (ug2 < g2) {
       if (!have_b1) b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
@@ -356,9 +359,9 @@ __device__ void ntc_outcome_f(const Params& P, uint32_t c0, uint32_t cell, uint3
 
 constexpr int kDsmcThreads = 128;
 
-__global__ void __launch_bounds__(kDsmcThreads) k_dsmc32(Dsmc32Args a) {
+__global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
   extern __shared__ uint32_t smem[];
-  const Params& P = a.P;
+  const ParamsF& P = a.P;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int64_t gwarp = (int64_t)blockIdx.x * wpb + wib;
@@ -372,8 +375,8 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc32(Dsmc32Args a) {
   Counts32 cnt = {0, 0, 0, 0};
   const bool separate = a.m0 != nullptr;
   const float invK = 1.f / (float)P.K;
-  const float mu0 = (float)P.vmean[0], mu1 = (float)P.vmean[1], mu2 = (float)P.vmean[2];
-  const float vs = (float)P.vsig, ivs = (float)P.inv_vsig, pref = (float)P.src_pref;
+  const float mu0 = P.vmean[0], mu1 = P.vmean[1], mu2 = P.vmean[2];
+  const float vs = P.vsig, ivs = P.inv_vsig, pref = P.src_pref;
 
   for (int64_t grp = gwarp; grp < a.ngroups; grp += nwarps) {
     const int64_t cell0 = grp * a.G;
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc32(Dsmc32Args a) {
 
 // ------------------------------------------------------------ kick/drift --
 struct Kick32Args {
-  Params P;
+  ParamsF P;
   const int32_t* cell;
   float *o0, *o1, *o2, *v0, *v1, *v2;
   const float *m0, *m1, *m2;
@@ -474,9 +477,9 @@ struct Kick32Args {
 
 __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const Params& P = a.P;
+  const ParamsF& P = a.P;
   if (j >= P.np) return;
-  const int n = P.n, nn = n * n;
+  const int n = P.n, nn = P.nn;
   const int c = a.cell[j];
   int ci[3] = {c % n, (c / n) % n, c / nn};
   float o[3] = {a.o0[j], a.o1[j], a.o2[j]};
@@ -502,12 +505,11 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
           e1 = fmaf(w, __ldg(a.E1 + node), e1);
           e2 = fmaf(w, __ldg(a.E2 + node), e2);
         }
-    const float h = (float)P.h;
     float s0, c0, s1, c1, s2, c2;
-    sincospif(2.f * (((float)ci[0] + o[0]) * h - (float)P.phi_shift[0]), &s0, &c0);
-    sincospif(2.f * (((float)ci[1] + o[1]) * h - (float)P.phi_shift[1]), &s1, &c1);
-    sincospif(2.f * (((float)ci[2] + o[2]) * h - (float)P.phi_shift[2]), &s2, &c2);
-    const float amp = a.tE.em_amp, k = (float)(P.dt * P.qm_eff);
+    sincospif(2.f * (((float)ci[0] + o[0]) * P.h - P.phi_shift[0]), &s0, &c0);
+    sincospif(2.f * (((float)ci[1] + o[1]) * P.h - P.phi_shift[1]), &s1, &c1);
+    sincospif(2.f * (((float)ci[2] + o[2]) * P.h - P.phi_shift[2]), &s2, &c2);
+    const float amp = a.tE.em_amp, k = P.dt_qm;
     L[0] = k * (e0 + amp * c0 * s1 * s2);
     L[1] = k * (e1 + amp * s0 * c1 * s2);
     L[2] = k * (e2 + amp * s0 * s1 * c2);
@@ -521,19 +523,17 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, L[d] + dv[d], v[d]);
   a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
   if (!a.drift) return;
-  const uint64_t p = a.pid[j];
-  const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1);
+  const uint32_t p = a.pid[j];
+  const U4 b0 = philox(p, 0u, 0u, 0xFFFFFF00u, P.key0, P.key1);
+  const U4 b1 = philox(p, 0u, 0u, 0xFFFFFF01u, P.key0, P.key1);
   const float xi[3] = {unif24(b0.x), unif24(b0.z), unif24(b1.x)};
   const float vm[3] = {a.m0[j], a.m1[j], a.m2[j]};
-  const float A = (float)P.fx_amp, A2pi = (float)P.fx_amp_over_2pi, Ac = (float)(P.fx_amp * P.fx_speed);
-  const float dtn = (float)(P.dt * (double)n);
   float* op[3] = {a.o0, a.o1, a.o2};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    float s;
-    xm_solve_f(A, A2pi, a.th, xi[d], &s);
-    const float xd = Ac * (s + a.th.sin2ct) / (1.f + A * s);
-    float on = fmaf(dtn, v[d] + xd - vm[d], o[d]);
+    const float s = xm_sin_f(P, a.th, xi[d]);
+    const float xd = P.fx_Ac * (s + a.th.sin2ct) / (1.f + P.fx_amp * s);
+    float on = fmaf(P.dtn, v[d] + xd - vm[d], o[d]);
     const float fl = floorf(on);
     on -= fl;
     int shift = (int)fl;
@@ -599,7 +599,8 @@ __device__ __forceinline__ bool grid_barrier32(unsigned int* bar, int* info, int
   return ok != 0;
 }
 
-// block total of a double-float partial, returned in FP64 to every thread
+// block total of a double-float partial in FP64 (thread 0 only; sh holds
+// at least 32 doubles)
 __device__ __forceinline__ double block_total_df(DF v, double* sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -608,7 +609,8 @@ __device__ __forceinline__ double block_total_df(DF v, double* sh) {
   if (lane == 0) sh[w] = df_to_double(v);
   __syncthreads();
   double t = 0.0;
-  for (int i = 0; i < nw; ++i) t += sh[i];
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) t += sh[i];
   return t;
 }
 
@@ -645,6 +647,8 @@ __device__ __forceinline__ Nbr neighbours(int id, int n, int nn) {
 // per thread, FP64 across blocks; same phases as the FP64 solver.
 __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
   __shared__ double sh[40];
+  __shared__ float fscal[2];  // alpha, beta formed once per block by thread 0
+  __shared__ int stop;
   const int n = a.n, nn = a.n * a.n;
   const int m = (int)a.ncell;
   const int stride = gridDim.x * blockDim.x;
@@ -668,23 +672,22 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
   }
   {
     const double s1 = block_total_df(rr_loc, sh);
-    const double s2 = block_total_df(bb_loc, sh + 8);
-    if (threadIdx.x == 0) {
-      slot(ph)[blockIdx.x] = s1;
-      slot(ph)[G + blockIdx.x] = s2;
-    }
+    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s1;
+    const double s2 = block_total_df(bb_loc, sh);
+    if (threadIdx.x == 0) slot(ph)[G + blockIdx.x] = s2;
   }
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
   double rr = grid_total32(slot(ph), G, sh);
   const double bb = grid_total32(slot(ph) + G, G, sh);
   ph ^= 1;
-  double beta = 0.0;
   int it = 0, status = 0;
   const double thresh = a.tol * sqrt(bb);
   while (true) {
-    if (bb == 0.0 || sqrt(rr) <= thresh) break;
-    if (it >= a.maxit) { status = 1; break; }
-    const float bf = (float)beta;
+    if (threadIdx.x == 0) stop = (bb == 0.0 || sqrt(rr) <= thresh) ? 1 : (it >= a.maxit ? 2 : 0);
+    __syncthreads();
+    if (stop == 1) break;
+    if (stop == 2) { status = 1; break; }
+    const float bf = fscal[1];
     if (it == 0) {
       for (int id = t0; id < m; id += stride) a.p[id] = a.r[id];
     } else {
@@ -708,7 +711,9 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
     if (!grid_barrier32(a.bar, a.info, a.flags)) return;
     const double pq = grid_total32(slot(ph), G, sh);
     ph ^= 1;
-    const float alpha = (float)(rr / pq);
+    if (threadIdx.x == 0) fscal[0] = (float)(rr / pq);
+    __syncthreads();
+    const float alpha = fscal[0];
     DF rn_loc{0.f, 0.f};
     for (int id = t0; id < m; id += stride) {
       a.x[id] = fmaf(alpha, a.p[id], a.x[id]);
@@ -724,7 +729,7 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
     const double rr_new = grid_total32(slot(ph), G, sh);
     ph ^= 1;
     ++it;
-    beta = rr_new / rr;
+    if (threadIdx.x == 0) fscal[1] = (float)(rr_new / rr);
     rr = rr_new;
   }
   DF xs{0.f, 0.f};
@@ -734,7 +739,10 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
     if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
   }
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-  const float mean_x = (float)(grid_total32(slot(ph), G, sh) / (double)m);
+  const double xsum = grid_total32(slot(ph), G, sh);  // every thread calls it: it synchronises the block
+  if (threadIdx.x == 0) fscal[0] = (float)(xsum / (double)m);
+  __syncthreads();
+  const float mean_x = fscal[0];
   ph ^= 1;
   for (int id = t0; id < m; id += stride) a.x[id] -= mean_x;
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
@@ -786,7 +794,7 @@ __global__ void __launch_bounds__(kThreads) k_err_partial32(Err32Args a) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         double s;
-        const double xm = xm_solve(P, a.tt, xi[d], xi[d], &s);
+        const double xm = xm_solve(P, a.tt, xi[d], &s);
         double e = ((double)ci[d] + (double)os[d]) * P.h - xm;
         e -= floor(e + 0.5);
         vals[d] = e * e;
@@ -927,7 +935,7 @@ const void* cg32_kernel_ptr() { return (const void*)k_cg32; }
 
 cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate) {
   Dsmc32Args a;
-  a.P = c->P;
+  a.P = params_f(c->P);
   const int b = c->cur;
   a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
   a.start = c->start;
@@ -953,7 +961,7 @@ cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate) {
 
 cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, double th) {
   Kick32Args a;
-  a.P = c->P;
+  a.P = params_f(c->P);
   const int b = c->cur;
   a.cell = c->cell32[b];
   a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
@@ -1083,4 +1091,37 @@ cudaError_t launch_store_dv32(pic_ctx* c, double* dv, double* dvm) {
   return cudaGetLastError();
 }
 
+}  // namespace pic
+
+namespace pic {
+ParamsF params_f(const Params& P) {
+  ParamsF f;
+  f.n = P.n;
+  f.nn = P.n * P.n;
+  f.K = P.K;
+  f.np = P.np;
+  f.ncell = P.ncell;
+  f.key0 = P.key0;
+  f.key1 = P.key1;
+  f.h = (float)P.h;
+  f.dt_qm = (float)(P.dt * P.qm_eff);
+  f.dtn = (float)(P.dt * (double)P.n);
+  f.fx_amp = (float)P.fx_amp;
+  f.fx_a2pi = (float)P.fx_amp_over_2pi;
+  f.fx_Ac = (float)(P.fx_amp * P.fx_speed);
+  for (int d = 0; d < 3; ++d) {
+    f.vmean[d] = (float)P.vmean[d];
+    f.phi_shift[d] = (float)P.phi_shift[d];
+  }
+  f.vsig = (float)P.vsig;
+  f.inv_vsig = (float)P.inv_vsig;
+  f.src_pref = (float)P.src_pref;
+  f.pmax = (float)P.pmax;
+  f.gmax = (float)P.gmax;
+  f.gmax2 = (float)(P.gmax * P.gmax);
+  for (int j = 0; j < 5; ++j) f.R_series[j] = (float)P.R_series[j];
+  f.ginv_f = P.ginv_f;
+  f.ginv_M = P.ginv_M;
+  return f;
+}
 }  // namespace pic

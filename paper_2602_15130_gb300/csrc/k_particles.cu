@@ -22,7 +22,7 @@ inline int blocks_for(int64_t n, int t = kThreads) {
 struct SampleArgs {
   Params P;
   TimeTerms tt;
-  double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
+  double *x0, *x1, *x2, *v0, *v1, *v2, *vm0, *vm1, *vm2;
   uint32_t* pid;
 };
 
@@ -35,14 +35,13 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a) {
   const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                         unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
   double s;
-  const double X0 = xm_solve(P, a.tt, xi[0], xi[0], &s);
-  const double X1 = xm_solve(P, a.tt, xi[1], xi[1], &s);
-  const double X2 = xm_solve(P, a.tt, xi[2], xi[2], &s);
+  const double X0 = xm_solve(P, a.tt, xi[0], &s);
+  const double X1 = xm_solve(P, a.tt, xi[1], &s);
+  const double X2 = xm_solve(P, a.tt, xi[2], &s);
   const double V0 = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
   const double V1 = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
   const double V2 = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
   a.x0[i] = wrap_unit(X0); a.x1[i] = wrap_unit(X1); a.x2[i] = wrap_unit(X2);
-  a.xm0[i] = X0; a.xm1[i] = X1; a.xm2[i] = X2;
   a.v0[i] = V0; a.v1[i] = V1; a.v2[i] = V2;
   a.vm0[i] = V0; a.vm1[i] = V1; a.vm2[i] = V2;
   a.pid[i] = (uint32_t)i;
@@ -53,7 +52,7 @@ struct LoadArgs {
   Params P;
   TimeTerms tt;
   const double* xv;  // 6 N_p: x AoS then v AoS
-  double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
+  double *x0, *x1, *x2, *v0, *v1, *v2, *vm0, *vm1, *vm2;
   uint32_t* pid;
 };
 
@@ -65,10 +64,6 @@ __global__ void __launch_bounds__(kThreads) k_load_state(LoadArgs a) {
            b2 = sample_block(P, (uint64_t)i, 2);
   const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                         unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
-  double s;
-  a.xm0[i] = xm_solve(P, a.tt, xi[0], xi[0], &s);
-  a.xm1[i] = xm_solve(P, a.tt, xi[1], xi[1], &s);
-  a.xm2[i] = xm_solve(P, a.tt, xi[2], xi[2], &s);
   a.vm0[i] = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
   a.vm1[i] = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
   a.vm2[i] = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
@@ -315,7 +310,7 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
 // --------------------------------------------------------------------------
 struct KickArgs {
   Params P;
-  double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2;
+  double *x0, *x1, *x2, *v0, *v1, *v2;
   const double *vm0, *vm1, *vm2;
   const uint32_t* pid;
   const double *dv0, *dv1, *dv2;
@@ -380,13 +375,11 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
   const uint64_t p = a.pid[j];
   const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1);
   const double xi[3] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y)};
-  double* xmp[3] = {a.xm0, a.xm1, a.xm2};
   const double vm[3] = {a.vm0[j], a.vm1[j], a.vm2[j]};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double s;
-    const double xmv = xm_solve(P, a.th, xi[d], xmp[d][j], &s);
-    xmp[d][j] = xmv;
+    xm_solve(P, a.th, xi[d], &s);
     const double xd = xm_dot(P, a.th, s);
     x[d] = wrap_unit(x[d] + P.dt * (v[d] + xd - vm[d]));
   }
@@ -405,7 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
 struct ErrArgs {
   Params P;
   TimeTerms tt;
-  const double *x0, *x1, *x2, *v0, *v1, *v2, *xm0, *xm1, *xm2, *vm0, *vm1, *vm2;
+  const double *x0, *x1, *x2, *v0, *v1, *v2, *vm0, *vm1, *vm2;
   const uint32_t* pid;
   const double* phi;
   double* part;  // [blocks][14]: 7 sums then 7 maxima
@@ -449,12 +442,11 @@ __global__ void __launch_bounds__(kThreads) k_err_partial(ErrArgs a) {
       const double xi[3] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y)};
       const double xs[3] = {a.x0[j], a.x1[j], a.x2[j]};
       const double vs[3] = {a.v0[j], a.v1[j], a.v2[j]};
-      const double guess[3] = {a.xm0[j], a.xm1[j], a.xm2[j]};
       const double vms[3] = {a.vm0[j], a.vm1[j], a.vm2[j]};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         double s;
-        const double xm = xm_solve(P, a.tt, xi[d], guess[d], &s);
+        const double xm = xm_solve(P, a.tt, xi[d], &s);
         double e = xs[d] - xm;
         e -= floor(e + 0.5);
         vals[d] = e * e;
@@ -523,7 +515,6 @@ cudaError_t launch_sample(pic_ctx* c, double t0) {
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
-  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
   a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
   a.pid = c->pid[b];
   prof_begin(c);
@@ -541,7 +532,6 @@ cudaError_t launch_load_state(pic_ctx* c, const double* xv, double t) {
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
-  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
   a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
   a.pid = c->pid[b];
   prof_begin(c);
@@ -616,7 +606,6 @@ cudaError_t launch_kick(pic_ctx* c, double tE, bool with_coll, bool drift, doubl
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
-  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
   a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
   a.pid = c->pid[b];
   if (with_coll) { a.dv0 = c->dv[0]; a.dv1 = c->dv[1]; a.dv2 = c->dv[2]; }
@@ -647,7 +636,6 @@ cudaError_t launch_errors(pic_ctx* c, double t) {
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
-  a.xm0 = c->xm[b][0]; a.xm1 = c->xm[b][1]; a.xm2 = c->xm[b][2];
   a.vm0 = c->vm[b][0]; a.vm1 = c->vm[b][1]; a.vm2 = c->vm[b][2];
   a.pid = c->pid[b];
   a.phi = c->phi;

@@ -135,8 +135,8 @@ struct GatherArgs {
   int n;
   int64_t ncell;
   const int32_t *start, *perm;
-  const double* in[12];   // x0..2, v0..2, xm0..2, vm0..2
-  double* out[12];
+  const double* in[9];    // x0..2, v0..2, vm0..2
+  double* out[9];
   const uint32_t* pid_in;
   uint32_t* pid_out;
   double* corner;         // [8][ncell]
@@ -144,7 +144,7 @@ struct GatherArgs {
 
 __device__ __forceinline__ void move_particle(const GatherArgs& a, int32_t src, int32_t dst) {
 #pragma unroll
-  for (int q = 0; q < 12; ++q) a.out[q][dst] = a.in[q][src];
+  for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src];
   a.pid_out[dst] = a.pid_in[src];
 }
 
@@ -294,8 +294,8 @@ cudaError_t launch_sort(pic_ctx* c) {
   g.perm = c->perm;
   const int b = c->cur, o = 1 - c->cur;
   for (int d = 0; d < 3; ++d) {
-    g.in[d] = c->x[b][d]; g.in[3 + d] = c->v[b][d]; g.in[6 + d] = c->xm[b][d]; g.in[9 + d] = c->vm[b][d];
-    g.out[d] = c->x[o][d]; g.out[3 + d] = c->v[o][d]; g.out[6 + d] = c->xm[o][d]; g.out[9 + d] = c->vm[o][d];
+    g.in[d] = c->x[b][d]; g.in[3 + d] = c->v[b][d]; g.in[6 + d] = c->vm[b][d];
+    g.out[d] = c->x[o][d]; g.out[3 + d] = c->v[o][d]; g.out[6 + d] = c->vm[o][d];
   }
   g.pid_in = c->pid[b];
   g.pid_out = c->pid[o];

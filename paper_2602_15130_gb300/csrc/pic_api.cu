@@ -72,6 +72,26 @@ using namespace pic;
 
 namespace {
 
+constexpr int kGinvM = 1024;
+
+// Knots of G^{-1}, G(y) = y - a cos(2 pi y), a = A/(2 pi), at T_k = k/M:
+// y_k by Newton in FP64 (converged to |dy| < 1e-16) and the slope
+// dy/dT = 1/G'(y_k) = 1/(1 + A sin(2 pi y_k)).
+void ginv_table(double A, double* out) {
+  const double a = A / (2.0 * kPi);
+  for (int k = 0; k <= kGinvM; ++k) {
+    const double T = (double)k / kGinvM;
+    double y = T;
+    for (int it = 0; it < 100; ++it) {
+      const double dy = (y - a * cos(2.0 * kPi * y) - T) / (1.0 + A * sin(2.0 * kPi * y));
+      y -= dy;
+      if (fabs(dy) < 1e-16) break;
+    }
+    out[2 * k] = y;
+    out[2 * k + 1] = 1.0 / (1.0 + A * sin(2.0 * kPi * y));
+  }
+}
+
 // R(a) small-argument series: R = sqrt(2/pi) sum_j c_j a^{2j},
 // c_j = d_j + d_{j+1} + e_{j-1} + 2 e_j - e_{j+1}, with d_k the Taylor
 // coefficients of e^{-a^2/2} and e_k those of sqrt(pi/2) erf(a/sqrt 2).
@@ -164,7 +184,6 @@ void for_each_buffer(pic_ctx* c, F f) {
       for (int d = 0; d < 3; ++d) {
         f((void**)&c->x[b][d], np * 8);
         f((void**)&c->v[b][d], np * 8);
-        f((void**)&c->xm[b][d], np * 8);
         f((void**)&c->vm[b][d], np * 8);
       }
     for (int d = 0; d < 3; ++d) {
@@ -220,6 +239,8 @@ void for_each_buffer(pic_ctx* c, F f) {
   f((void**)&c->flags, 64);
   f((void**)&c->err_part, (size_t)c->err_blocks * 14 * 8);
   f((void**)&c->err_out, 14 * 8);
+  f((void**)&c->ginv, (size_t)(kGinvM + 1) * 2 * 8);
+  f((void**)&c->ginv_f, (size_t)(kGinvM + 1) * 2 * 4);
   f((void**)&c->stage, 6 * np * 8);
   f((void**)&c->stage_i, (np + 1) * 4);
 }
@@ -428,8 +449,28 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
     pic_destroy(c);
     return PIC_ENOMEM;
   }
-  e = c->mixed ? cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream)
-               : cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream);
+  {
+    double* tab = (double*)malloc((size_t)(kGinvM + 1) * 2 * 8);
+    float* tabf = (float*)malloc((size_t)(kGinvM + 1) * 2 * 4);
+    if (!tab || !tabf) {
+      free(tab);
+      free(tabf);
+      pic_destroy(c);
+      return PIC_ENOMEM;
+    }
+    ginv_table(c->cfg.fx_amp, tab);
+    for (int k = 0; k < 2 * (kGinvM + 1); ++k) tabf[k] = (float)tab[k];
+    e = cudaMemcpy(c->ginv, tab, (size_t)(kGinvM + 1) * 2 * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->ginv_f, tabf, (size_t)(kGinvM + 1) * 2 * 4, cudaMemcpyHostToDevice);
+    free(tab);
+    free(tabf);
+    c->P.ginv = c->ginv;
+    c->P.ginv_f = c->ginv_f;
+    c->P.ginv_M = kGinvM;
+  }
+  if (e == cudaSuccess)
+    e = c->mixed ? cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream)
+                 : cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cg_info, 0, 64, c->stream);

@@ -34,6 +34,28 @@ struct Params {
   double rho_scale;      // q w / h^3
   double src_pref;       // w dt sigma0 / (2 dV): multiplies (c - 1) s R(a) m
   double R_series[kSeriesTerms];  // sqrt(2/pi) c_j, small-a series of R(a)
+  // G^{-1} on T in [0,1], G(y) = y - A/(2 pi) cos(2 pi y): M+1 knots of
+  // (y_k, dy/dT at k) for cubic Hermite interpolation (device arrays)
+  const double* ginv;
+  const float* ginv_f;
+  int ginv_M;
+};
+
+// FP32 copy of the parameters the precision-form kernels use, converted
+// once on the host (FP64 arithmetic in a kernel would run on the slow
+// FP64 pipe).
+struct ParamsF {
+  int n, nn, K;
+  int64_t np, ncell;
+  uint32_t key0, key1;
+  float h, dt_qm, dtn;        // dt q/m, dt n (drift in cell units)
+  float fx_amp, fx_a2pi, fx_Ac;
+  float vmean[3], vsig, inv_vsig;
+  float src_pref, pmax, gmax, gmax2;
+  float phi_shift[3];
+  float R_series[5];
+  const float* ginv_f;
+  int ginv_M;
 };
 
 // ---------------------------------------------------------------------------
@@ -93,20 +115,31 @@ struct TimeTerms {
   double t, ct, cos2ct, sin2ct, em_amp;
 };
 
+// G^{-1}(T) by cubic Hermite interpolation of the knot table (T any real:
+// G^{-1}(T + 1) = G^{-1}(T) + 1).
+__device__ __forceinline__ double ginv_eval(const Params& P, double T) {
+  const double fl = floor(T);
+  const double t = (T - fl) * (double)P.ginv_M;
+  int k = (int)t;
+  k = k >= P.ginv_M ? P.ginv_M - 1 : k;
+  const double u = t - (double)k, u2 = u * u, u3 = u2 * u, h = 1.0 / (double)P.ginv_M;
+  const double* q = P.ginv + 2 * k;
+  return fl + (2.0 * u3 - 3.0 * u2 + 1.0) * q[0] + (u3 - 2.0 * u2 + u) * h * q[1] + (3.0 * u2 - 2.0 * u3) * q[2] +
+         (u3 - u2) * h * q[3];
+}
+
 // x^M(t) with F_x(x^M, t) = xi for f_x = 1 + A sin(2 pi (x - c t)). With
 // y = x - c t the equation is G(y) = y - A/(2 pi) cos(2 pi y) = T, T = xi -
-// c t - A/(2 pi) cos(2 pi c t); G' = 1 + A sin(2 pi y) >= 1 - |A| > 0 and
-// |G''/(2 G')| <= 2 pi |A| / (2 (1 - |A|)) < 1.35. Newton from the guess
-// (clamped into the bracket |y - T| <= A/(2 pi)); once a correction is at
-// most 2^-27 the next one would be below 1.35 * 2^-54, under half an ulp of
-// y = O(1), so the loop stops there and updates sin(2 pi y) to first order
-// (error (2 pi dy)^2 / 2 <= 1e-15 relative to the O(1) terms it enters).
+// c t - A/(2 pi) cos(2 pi c t): time only shifts T, so one table of G^{-1}
+// serves every t. Newton polishes the interpolated start (G' = 1 + A sin
+// >= 1 - |A|, |G''/(2 G')| < 1.35 for |A| = 0.3); once a correction is at
+// most 2^-27 the next one would be below half an ulp of y = O(1), so the
+// loop stops and updates sin(2 pi y) to first order. The Hermite start is
+// within ~1e-11, so one iteration is the rule.
 // Returns x^M and sin(2 pi (x^M - c t)) (for xdot^M).
-__device__ __forceinline__ double xm_solve(const Params& P, const TimeTerms& tt, double xi, double guess,
-                                           double* s_out) {
+__device__ __forceinline__ double xm_solve(const Params& P, const TimeTerms& tt, double xi, double* s_out) {
   const double T = xi - tt.ct - P.fx_amp_over_2pi * tt.cos2ct;
-  const double lo = T - fabs(P.fx_amp_over_2pi), hi = T + fabs(P.fx_amp_over_2pi);
-  double y = fmin(fmax(guess - tt.ct, lo), hi);
+  double y = ginv_eval(P, T);
   for (int it = 0; it < 12; ++it) {
     double s, c;
     sincospi(2.0 * y, &s, &c);
@@ -187,7 +220,6 @@ struct pic_ctx {
   // particles, buffer [b][component]
   double* x[2][3];
   double* v[2][3];
-  double* xm[2][3];  // x^M at the last evaluation (Newton warm start)
   double* vm[2][3];  // v^M (constant for the Gaussian f_v)
   uint32_t* pid[2];
   int cur;
@@ -237,6 +269,10 @@ struct pic_ctx {
   int* cg_info;     // [0] iterations, [1] status (0 ok, 1 noconv, 2 timeout)
   double* cg_res;   // relative residual
   int cg_grid, cg_block;
+
+  // G^{-1} knot tables (FP64 and FP32)
+  double* ginv;
+  float* ginv_f;
 
   // collisions
   double* overlay;  // per-lane working velocities
@@ -292,6 +328,7 @@ cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate_source);
 cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift, double th);
 cudaError_t launch_errors(pic_ctx* c, double t);
 TimeTerms time_terms(const Params& P, double t);
+ParamsF params_f(const Params& P);
 cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E);
 cudaError_t launch_store_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* perm);
 cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm);
