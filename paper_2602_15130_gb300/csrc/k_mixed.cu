@@ -302,14 +302,12 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
   const int npairs = (int)floorf(base + unif24(u.x));
   const float gmax = P.gmax;
   for (int s = 0; s < npairs; ++s) {
+    // both blocks of the candidate up front: two independent Philox chains
     const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
+    const U4 b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
     uint32_t q = draw_index(b0.y, (uint32_t)c);
-    U4 b1;
-    bool have_b1 = false;
     if (q == p) {
-      b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
-      have_b1 = true;
       q = draw_index(b1.y, (uint32_t)c);
       if (q == p) q = draw_index(b1.z, (uint32_t)c);
       if (q == p) q = draw_index(b1.w, (uint32_t)c);
@@ -336,7 +334,6 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
     if (g2 > P.gmax2) ++cnt.gmax;
     if (fabsf(ug2 - g2) < 2e-6f * g2) ++cnt.tie;
     if (ug2 < g2) {
-      if (!have_b1) b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
       float se, ce;
       sincospif(2.f * unif24(b0.w), &se, &ce);
       const float cchi = 1.f - 2.f * unif24(b1.x);
@@ -400,42 +397,55 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
         ntc_outcome_f(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s, bm, ov,
                       cnt);
       __syncwarp();
+      // per cell of the group and per 32-particle word: transpose the
+      // lanes' bitmap words with ballots, so lane b learns which outcomes
+      // touched particle 32 w + b, then add their changes in ascending
+      // outcome order
       const bool last = ch == a.nchunks - 1;
-      for (int32_t j = gs + lane; j < ge; j += 32) {
-        int cl = 0;
-        while (cl + 1 < ncl && a.start[cell0 + cl + 1] <= j) ++cl;
+      for (int cl = 0; cl < ncl; ++cl) {
         const int32_t cs = a.start[cell0 + cl];
         const int cc = a.start[cell0 + cl + 1] - cs;
-        const int jj = j - cs;
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-        if (ch > 0) { acc0 = a.dv0[j]; acc1 = a.dv1[j]; acc2 = a.dv2[j]; }
-        if (cc >= 2 && cc <= a.max_ppc) {
-          const float w0 = a.v0[j], w1 = a.v1[j], w2 = a.v2[j];
-          for (int k = 0; k < a.Kc; ++k) {
-            if (ch * a.Kc + k >= P.K) break;
-            const int L = cl * a.Kc + k;
-            if ((wbm[(size_t)L * a.bm_words + (jj >> 5)] >> (jj & 31)) & 1u) {
-              const float* W = wov + ((size_t)L * a.max_ppc + jj) * 3;
-              acc0 += W[0] - w0;
-              acc1 += W[1] - w1;
-              acc2 += W[2] - w2;
+        const bool coll_ok = cc >= 2 && cc <= a.max_ppc;
+        const int kmax = min(a.Kc, P.K - ch * a.Kc);
+        for (int w = 0; w < (cc + 31) / 32; ++w) {
+          uint32_t mine = 0u;
+          if (coll_ok) {
+            const bool owner = lane >= cl * a.Kc && lane < cl * a.Kc + kmax;
+            const uint32_t word = owner ? bm[w] : 0u;
+#pragma unroll 8
+            for (int b = 0; b < 32; ++b) {
+              const uint32_t m = __ballot_sync(0xffffffffu, (word >> b) & 1u);
+              if (lane == b) mine = m;
             }
           }
-        }
-        if (!last) {
-          a.dv0[j] = acc0; a.dv1[j] = acc1; a.dv2[j] = acc2;
-        } else {
-          const float vx = a.v0[j], vy = a.v1[j], vz = a.v2[j];
-          const float mx = mu0 - vx, my = mu1 - vy, mz = mu2 - vz;
-          const float am = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz))) * ivs;
-          const float f = pref * (float)(cc - 1) * vs * hs_R_f(P, am);
-          if (separate) {
-            a.dv0[j] = acc0 * invK; a.dv1[j] = acc1 * invK; a.dv2[j] = acc2 * invK;
-            a.m0[j] = f * mx; a.m1[j] = f * my; a.m2[j] = f * mz;
+          const int jj = 32 * w + lane;
+          if (jj >= cc) continue;
+          const int32_t j = cs + jj;
+          const float w0 = a.v0[j], w1 = a.v1[j], w2 = a.v2[j];
+          float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+          if (ch > 0) { acc0 = a.dv0[j]; acc1 = a.dv1[j]; acc2 = a.dv2[j]; }
+          while (mine) {
+            const int L = __ffs(mine) - 1;
+            mine &= mine - 1u;
+            const float* W = wov + ((size_t)L * a.max_ppc + jj) * 3;
+            acc0 += W[0] - w0;
+            acc1 += W[1] - w1;
+            acc2 += W[2] - w2;
+          }
+          if (!last) {
+            a.dv0[j] = acc0; a.dv1[j] = acc1; a.dv2[j] = acc2;
           } else {
-            a.dv0[j] = fmaf(acc0, invK, -f * mx);
-            a.dv1[j] = fmaf(acc1, invK, -f * my);
-            a.dv2[j] = fmaf(acc2, invK, -f * mz);
+            const float mx = mu0 - w0, my = mu1 - w1, mz = mu2 - w2;
+            const float am = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz))) * ivs;
+            const float f = pref * (float)(cc - 1) * vs * hs_R_f(P, am);
+            if (separate) {
+              a.dv0[j] = acc0 * invK; a.dv1[j] = acc1 * invK; a.dv2[j] = acc2 * invK;
+              a.m0[j] = f * mx; a.m1[j] = f * my; a.m2[j] = f * mz;
+            } else {
+              a.dv0[j] = fmaf(acc0, invK, -f * mx);
+              a.dv1[j] = fmaf(acc1, invK, -f * my);
+              a.dv2[j] = fmaf(acc2, invK, -f * mz);
+            }
           }
         }
       }
