@@ -211,6 +211,34 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
   for (int64_t cell = gw; cell < a.ncell; cell += nw) {
     const int32_t s = a.start[cell];
     const int32_t cnt = a.start[cell + 1] - s;
+    if (cnt <= 64) {
+      // both 32-element chunks held in registers, ranked in one pass
+      int32_t src0 = 0, src1 = 0;
+      uint32_t p0 = 0xFFFFFFFFu, p1 = 0xFFFFFFFFu;
+      if (lane < cnt) { src0 = a.perm[s + lane]; p0 = a.pid_in[src0]; }
+      if (lane + 32 < cnt) { src1 = a.perm[s + 32 + lane]; p1 = a.pid_in[src1]; }
+      int r0 = 0, r1 = 0;
+      const int lim = min(32, cnt);
+      for (int l = 0; l < lim; ++l) {
+        const uint32_t x0 = __shfl_sync(0xffffffffu, p0, l), x1 = __shfl_sync(0xffffffffu, p1, l);
+        r0 += (x0 < p0) + (x1 < p0);
+        r1 += (x0 < p1) + (x1 < p1);
+      }
+      if (lane < cnt) {
+        const int32_t dst = s + r0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src0];
+        a.pid_out[dst] = p0;
+        a.cell_out[dst] = (int32_t)cell;
+      }
+      if (lane + 32 < cnt) {
+        const int32_t dst = s + r1;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src1];
+        a.pid_out[dst] = p1;
+        a.cell_out[dst] = (int32_t)cell;
+      }
+    } else {
     for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
       const int32_t e = e0 + lane;
       int32_t src = 0;
@@ -232,6 +260,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
         a.pid_out[dst] = mp;
         a.cell_out[dst] = (int32_t)cell;
       }
+    }
     }
     __syncwarp();
     // per-cell CIC weights in sorted order, double-float sums
@@ -485,15 +514,40 @@ struct Kick32Args {
   int32_t *key, *rank, *count;
 };
 
+// cell index -> (i, j, k), by shifts when n is a power of two
+__device__ __forceinline__ void cell_ijk(const ParamsF& P, int c, int* ci) {
+  if (P.log2n >= 0) {
+    const int m = P.n - 1;
+    ci[0] = c & m;
+    ci[1] = (c >> P.log2n) & m;
+    ci[2] = c >> (2 * P.log2n);
+  } else {
+    ci[0] = c % P.n;
+    ci[1] = (c / P.n) % P.n;
+    ci[2] = c / P.nn;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const ParamsF& P = a.P;
   if (j >= P.np) return;
   const int n = P.n, nn = P.nn;
+  // every independent load first (memory-level parallelism), then the
+  // dependent field gather
   const int c = a.cell[j];
-  int ci[3] = {c % n, (c / n) % n, c / nn};
   float o[3] = {a.o0[j], a.o1[j], a.o2[j]};
   float v[3] = {a.v0[j], a.v1[j], a.v2[j]};
+  float dv[3] = {0.f, 0.f, 0.f};
+  if (a.dv0) { dv[0] = a.dv0[j]; dv[1] = a.dv1[j]; dv[2] = a.dv2[j]; }
+  float vm[3] = {0.f, 0.f, 0.f};
+  uint32_t p = 0;
+  if (a.drift) {
+    vm[0] = a.m0[j]; vm[1] = a.m1[j]; vm[2] = a.m2[j];
+    p = a.pid[j];
+  }
+  int ci[3];
+  cell_ijk(P, c, ci);
   float L[3];
   if (a.lor_mode == 2) {
     L[0] = a.L0[j]; L[1] = a.L1[j]; L[2] = a.L2[j];
@@ -527,17 +581,13 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
       a.L0[j] = L[0]; a.L1[j] = L[1]; a.L2[j] = L[2];
     }
   }
-  float dv[3] = {0.f, 0.f, 0.f};
-  if (a.dv0) { dv[0] = a.dv0[j]; dv[1] = a.dv1[j]; dv[2] = a.dv2[j]; }
 #pragma unroll
   for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, L[d] + dv[d], v[d]);
   a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
   if (!a.drift) return;
-  const uint32_t p = a.pid[j];
   const U4 b0 = philox(p, 0u, 0u, 0xFFFFFF00u, P.key0, P.key1);
   const U4 b1 = philox(p, 0u, 0u, 0xFFFFFF01u, P.key0, P.key1);
   const float xi[3] = {unif24(b0.x), unif24(b0.z), unif24(b1.x)};
-  const float vm[3] = {a.m0[j], a.m1[j], a.m2[j]};
   float* op[3] = {a.o0, a.o1, a.o2};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -1108,6 +1158,9 @@ ParamsF params_f(const Params& P) {
   ParamsF f;
   f.n = P.n;
   f.nn = P.n * P.n;
+  f.log2n = -1;
+  for (int b = 0; b < 31; ++b)
+    if ((1 << b) == P.n) f.log2n = b;
   f.K = P.K;
   f.np = P.np;
   f.ncell = P.ncell;

@@ -46,6 +46,7 @@ struct Params {
 // FP64 pipe).
 struct ParamsF {
   int n, nn, K;
+  int log2n;                  // log2(n) when n is a power of two, else -1
   int64_t np, ncell;
   uint32_t key0, key1;
   float h, dt_qm, dtn;        // dt q/m, dt n (drift in cell units)
