@@ -218,6 +218,32 @@ pic_status pic_reset_stats(pic_ctx* ctx);
 pic_status pic_set_profiling(pic_ctx* ctx, int32_t on);
 pic_status pic_get_kernel_times(pic_ctx* ctx, pic_kernel_times* out);
 
+/* ---- Batched form: independent replicates advanced together ----------
+ * pic_create_batch builds one context holding nrep independent replicates
+ * (the refinement-study use of the method: many runs of uneven mesh edge,
+ * particle count and N_avg). cfgs[r] gives replicate r; all must use
+ * PIC_MIXED and share every field except n, n_particles, K, dt, sigma0
+ * and seed (PIC_EINVAL otherwise); 1 <= nrep <= 65534. Replicate r draws
+ * from its own Philox key, local pids and local cell indices, so it
+ * reproduces a single-domain PIC_MIXED run of cfgs[r] (up to the reduction
+ * order of its Poisson solve). pic_sample_mms and pic_step act on every
+ * replicate; replicate r's time is t0 + step * cfgs[r].dt. The
+ * single-domain calls pic_collide_avg, pic_mms_error, pic_get_state,
+ * pic_set_state, pic_get_field and pic_get_sort return PIC_EINVAL on a
+ * batch; use the pic_batch_* calls below. */
+pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* cuda_stream,
+                            const pic_allocator* alloc, pic_ctx** out);
+
+/* Error norms of Sec. 4.3 for every replicate: out[nrep] (host). */
+pic_status pic_batch_mms_error(pic_ctx* ctx, pic_errors* out);
+
+/* State of replicate rep: x, v [n_particles_rep][3], pid indexed, host or device. */
+pic_status pic_batch_get_state(pic_ctx* ctx, int32_t rep, double* x, double* v);
+
+/* Number of replicates, total particles, and (optional, host int[nrep]) the
+ * CG iterations of every replicate's last Poisson solve. */
+pic_status pic_batch_info(pic_ctx* ctx, int32_t* nrep, int64_t* n_particles, int32_t* cg_iters);
+
 void pic_destroy(pic_ctx* ctx);
 const char* pic_status_string(pic_status s);
 

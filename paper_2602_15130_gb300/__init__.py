@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib, workloads
 from ._lib import PicConfig, PicError, check, load
 
-__all__ = ["Pic", "PicConfig", "PicError", "make_config", "workloads", "load"]
+__all__ = ["Pic", "Batch", "PicConfig", "PicError", "make_config", "workloads", "load"]
 
 
 def make_config(p: dict) -> PicConfig:
@@ -194,6 +194,51 @@ class Pic:
         k = _lib.PicKernelTimes()
         check(self.L.pic_get_kernel_times(self.ctx, ctypes.byref(k)), "pic_get_kernel_times")
         return {name: {"ms": k.ms[i], "launches": k.launches[i]} for i, name in enumerate(_lib.KERNEL_CLASSES)}
+
+
+class Batch(Pic):
+    """Independent replicates advanced together (pic_create_batch)."""
+
+    def __init__(self, params_list, stream=None, torch_allocator: bool = True):
+        import torch
+
+        L = load()
+        self.L = L
+        cfgs = (PicConfig * len(params_list))(*[make_config(p) for p in params_list])
+        self.cfgs = cfgs
+        self.nrep = len(params_list)
+        self.np_rep = [int(p["n_particles"]) for p in params_list]
+        self.np = sum(self.np_rep)
+        self.n = None
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        self._alloc = _TorchAllocator() if torch_allocator else None
+        ctx = ctypes.c_void_p()
+        check(L.pic_create_batch(cfgs, len(params_list), ctypes.c_void_p(handle),
+                                 ctypes.byref(self._alloc.struct) if self._alloc else None, ctypes.byref(ctx)),
+              "pic_create_batch")
+        self.ctx = ctx
+
+    def mms_error(self):
+        out = (_lib.PicErrors * self.nrep)()
+        check(self.L.pic_batch_mms_error(self.ctx, out), "pic_batch_mms_error", allow=(_lib.PIC_ENOCONV,))
+        return np.array([list(e.eps2) + list(e.epsinf) for e in out])
+
+    def get_state(self, rep: int, out=None):
+        n = self.np_rep[rep]
+        if out is None:
+            out = (np.zeros((n, 3)), np.zeros((n, 3)))
+        pa, ka = _ptr(out[0])
+        pb, kb = _ptr(out[1])
+        check(self.L.pic_batch_get_state(self.ctx, int(rep), pa, pb), "pic_batch_get_state")
+        return out
+
+    def cg_iters(self):
+        it = (ctypes.c_int32 * self.nrep)()
+        check(self.L.pic_batch_info(self.ctx, None, None, it), "pic_batch_info")
+        return list(it)
 
 
 def derived(params: dict) -> dict:

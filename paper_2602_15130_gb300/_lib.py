@@ -108,6 +108,12 @@ SIGNATURES = {
     "pic_get_kernel_times": (_S, [_V, ctypes.POINTER(PicKernelTimes)]),
     "pic_destroy": (None, [_V]),
     "pic_status_string": (ctypes.c_char_p, [_S]),
+    "pic_create_batch": (_S, [ctypes.POINTER(PicConfig), ctypes.c_int32, _V, ctypes.POINTER(PicAllocator),
+                              ctypes.POINTER(_V)]),
+    "pic_batch_mms_error": (_S, [_V, ctypes.POINTER(PicErrors)]),
+    "pic_batch_get_state": (_S, [_V, ctypes.c_int32, _V, _V]),
+    "pic_batch_info": (_S, [_V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int32)]),
     "pic_poisson_solve_noalloc": (_S, [ctypes.c_int32, _V, _V, _V, ctypes.c_double, ctypes.c_int32, _V,
                                       ctypes.POINTER(ctypes.c_int32), _D]),
 }

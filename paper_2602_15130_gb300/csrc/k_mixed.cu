@@ -8,7 +8,7 @@
 // of two floats, error-free TwoSum / TwoProd of Knuth and Dekker, relative
 // error about 2^-44) on the FP32 pipe and only the few per-block totals are
 // combined in true FP64.
-#include "pic_internal.cuh"
+#include "mixed_common.cuh"
 
 namespace pic {
 namespace {
@@ -18,90 +18,6 @@ constexpr int kThreads = 256;
 inline int blocks_for(int64_t n, int t = kThreads) {
   int64_t b = (n + t - 1) / t;
   return (int)(b < 1 ? 1 : b);
-}
-
-// ---------------------------------------------------------------- helpers --
-struct TimeTermsF {
-  float ct, cos2ct, sin2ct, em_amp;
-};
-
-TimeTermsF to_float(const TimeTerms& t) {
-  TimeTermsF f;
-  f.ct = (float)t.ct;
-  f.cos2ct = (float)t.cos2ct;
-  f.sin2ct = (float)t.sin2ct;
-  f.em_amp = (float)t.em_amp;
-  return f;
-}
-
-// top 24 bits of a Philox word as an FP32 uniform in (0, 1): exact
-__device__ __forceinline__ float unif24(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 0x1p-24f; }
-
-// double-float: hi + lo with |lo| <= ulp(hi)/2
-struct DF {
-  float hi, lo;
-};
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  const float e = (a - (s - bb)) + (b - bb);
-  return DF{s, e};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  DF s = two_sum(a.hi, b.hi);
-  const float lo = s.lo + a.lo + b.lo;
-  const float hi = s.hi + lo;
-  return DF{hi, lo - (hi - s.hi)};
-}
-__device__ __forceinline__ DF df_add_f(DF a, float b) {
-  DF s = two_sum(a.hi, b);
-  const float lo = s.lo + a.lo;
-  const float hi = s.hi + lo;
-  return DF{hi, lo - (hi - s.hi)};
-}
-// a += x y exactly up to the double-float rounding (TwoProd by fma)
-__device__ __forceinline__ DF df_fma(DF a, float x, float y) {
-  const float p = x * y;
-  const float e = fmaf(x, y, -p);
-  DF s = two_sum(a.hi, p);
-  const float lo = s.lo + a.lo + e;
-  const float hi = s.hi + lo;
-  return DF{hi, lo - (hi - s.hi)};
-}
-__device__ __forceinline__ DF df_shfl_xor(DF a, int off) {
-  return DF{__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
-}
-__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
-
-// sin(2 pi (x^M - c t)) in FP32: G^{-1} from the Hermite table, one Newton
-// correction, sine updated to first order.
-__device__ __forceinline__ float xm_sin_f(const ParamsF& P, const TimeTermsF& tt, float xi) {
-  const float T = xi - tt.ct - P.fx_a2pi * tt.cos2ct;
-  const float fl = floorf(T);
-  const float t = (T - fl) * (float)P.ginv_M;
-  int k = (int)t;
-  k = k >= P.ginv_M ? P.ginv_M - 1 : k;
-  const float u = t - (float)k, u2 = u * u, u3 = u2 * u, h = 1.f / (float)P.ginv_M;
-  const float2 q0 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k);
-  const float2 q1 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k + 1);
-  const float y = fl + (2.f * u3 - 3.f * u2 + 1.f) * q0.x + (u3 - 2.f * u2 + u) * h * q0.y +
-                  (3.f * u2 - 2.f * u3) * q1.x + (u3 - u2) * h * q1.y;
-  float s, c;
-  sincospif(2.f * y, &s, &c);
-  const float dy = (y - P.fx_a2pi * c - T) / (1.f + P.fx_amp * s);
-  return s - 6.283185307f * c * dy;
-}
-
-__device__ __forceinline__ float hs_R_f(const ParamsF& P, float a) {
-  const float a2 = a * a;
-  if (a < 0.1f) {
-    float acc = P.R_series[4];
-#pragma unroll
-    for (int j = 3; j >= 0; --j) acc = fmaf(acc, a2, P.R_series[j]);
-    return acc;
-  }
-  const float ia = 1.f / a, ia2 = ia * ia;
-  return 0.7978845608f * (1.f + ia2) * __expf(-0.5f * a2) + (a + 2.f * ia - ia2 * ia) * erff(a * 0.7071067812f);
 }
 
 // --------------------------------------------------------------- sampling --
@@ -167,6 +83,7 @@ struct Store32Args {
   int64_t np;
   int n;
   double h;
+  int64_t cell_base;  // subtracted from the stored cell (batches)
   const int32_t* cell;
   const float *o0, *o1, *o2, *v0, *v1, *v2;
   const uint32_t* pid;
@@ -178,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_store_state32(Store32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.np) return;
   const int64_t p = a.pid[j];
-  const int n = a.n, c = a.cell[j];
+  const int n = a.n, c = (int)(a.cell[j] - a.cell_base);
   if (a.cell_of_pid) a.cell_of_pid[p] = c;
   if (!a.xv) return;
   const int ci = c % n, cj = (c / n) % n, ck = c / (n * n);
@@ -514,20 +431,6 @@ struct Kick32Args {
   int32_t *key, *rank, *count;
 };
 
-// cell index -> (i, j, k), by shifts when n is a power of two
-__device__ __forceinline__ void cell_ijk(const ParamsF& P, int c, int* ci) {
-  if (P.log2n >= 0) {
-    const int m = P.n - 1;
-    ci[0] = c & m;
-    ci[1] = (c >> P.log2n) & m;
-    ci[2] = c >> (2 * P.log2n);
-  } else {
-    ci[0] = c % P.n;
-    ci[1] = (c / P.n) % P.n;
-    ci[2] = c / P.nn;
-  }
-}
-
 __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const ParamsF& P = a.P;
@@ -826,6 +729,7 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
 struct Err32Args {
   Params P;
   TimeTerms tt;
+  int64_t cell_base;  // subtracted from the stored cell (batches)
   const int32_t* cell;
   const float *o0, *o1, *o2, *v0, *v1, *v2;
   const uint32_t* pid;
@@ -847,7 +751,7 @@ __global__ void __launch_bounds__(kThreads) k_err_partial32(Err32Args a) {
       const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1), b2 = sample_block(P, p, 2);
       const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                             unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
-      const int n = P.n, c = a.cell[j];
+      const int n = P.n, c = (int)(a.cell[j] - a.cell_base);
       const int ci[3] = {c % n, (c / n) % n, c / (n * n)};
       const float os[3] = {a.o0[j], a.o1[j], a.o2[j]};
       const float vs[3] = {a.v0[j], a.v1[j], a.v2[j]};
@@ -1087,6 +991,7 @@ cudaError_t launch_errors32(pic_ctx* c, double t) {
   Err32Args a;
   a.P = c->P;
   a.tt = time_terms(c->P, t);
+  a.cell_base = 0;
   const int b = c->cur;
   a.cell = c->cell32[b];
   a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
@@ -1108,6 +1013,7 @@ cudaError_t launch_store_state32(pic_ctx* c, double* xv, int32_t* cell_of_pid) {
   a.np = c->P.np;
   a.n = c->P.n;
   a.h = c->P.h;
+  a.cell_base = 0;
   const int b = c->cur;
   a.cell = c->cell32[b];
   a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
@@ -1117,6 +1023,59 @@ cudaError_t launch_store_state32(pic_ctx* c, double* xv, int32_t* cell_of_pid) {
   a.cell_of_pid = cell_of_pid;
   prof_begin(c);
   k_store_state32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// replicate rep of a batch: the single-domain kernels on its sub-ranges
+cudaError_t launch_batch_errors(pic_ctx* c, int rep, double t) {
+  const Params& P = c->prm_host[rep];
+  const BatchRep& B = c->reps_host[rep];
+  Err32Args a;
+  a.P = P;
+  a.tt = time_terms(P, t);
+  a.cell_base = B.coff;
+  const int b = c->cur;
+  a.cell = c->cell32[b] + B.poff;
+  a.o0 = c->off[b][0] + B.poff; a.o1 = c->off[b][1] + B.poff; a.o2 = c->off[b][2] + B.poff;
+  a.v0 = c->vf[b][0] + B.poff; a.v1 = c->vf[b][1] + B.poff; a.v2 = c->vf[b][2] + B.poff;
+  a.pid = c->pid[b] + B.poff;
+  a.phi = c->phif + B.coff;
+  a.part = c->err_part;
+  a.pblocks = blocks_for(P.np);
+  const int nb = a.pblocks + blocks_for(P.ncell);
+  prof_begin(c);
+  k_err_partial32<<<nb, kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_ERR);
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // final reduction with this replicate's counts
+  const Params saved = c->P;
+  c->P = P;
+  e = launch_err_final(c, nb);
+  c->P = saved;
+  return e;
+}
+
+cudaError_t launch_batch_store_state(pic_ctx* c, int rep, double* xv) {
+  const Params& P = c->prm_host[rep];
+  const BatchRep& B = c->reps_host[rep];
+  Store32Args a;
+  a.np = P.np;
+  a.n = P.n;
+  a.h = P.h;
+  a.cell_base = B.coff;
+  const int b = c->cur;
+  a.cell = c->cell32[b] + B.poff;
+  a.o0 = c->off[b][0] + B.poff; a.o1 = c->off[b][1] + B.poff; a.o2 = c->off[b][2] + B.poff;
+  a.v0 = c->vf[b][0] + B.poff; a.v1 = c->vf[b][1] + B.poff; a.v2 = c->vf[b][2] + B.poff;
+  a.pid = c->pid[b] + B.poff;
+  a.xv = xv;
+  a.cell_of_pid = nullptr;
+  prof_begin(c);
+  k_store_state32<<<blocks_for(a.np), kThreads, 0, c->stream>>>(a);
   prof_end(c, KC_OTHER);
   c->launches++;
   return cudaGetLastError();

@@ -19,6 +19,8 @@ int rhs_blocks_needed(int64_t ncell);
 int err_blocks_needed(int64_t np, int64_t ncell);
 int dsmc32_threads();
 const void* dsmc32_kernel_ptr();
+int batch_dsmc_threads();
+const void* batch_dsmc_kernel_ptr();
 int cg32_threads();
 const void* cg32_kernel_ptr();
 
@@ -286,6 +288,20 @@ pic_status sort_and_field(pic_ctx* c, double t) {
 
 double time_at(const pic_ctx* c, double steps) { return c->t0 + steps * c->cfg.dt; }
 
+// Per-replicate time terms of step n (t_n, t_{n+1/2}, t_{n+1}); every
+// replicate has its own dt.
+pic_status batch_time_terms(pic_ctx* c, int64_t n) {
+  CK(cudaStreamSynchronize(c->stream));  // the pinned buffer may still feed a copy
+  for (int r = 0; r < c->nrep; ++r) {
+    const double dt = c->prm_host[r].dt;
+    c->tt_host[3 * r + 0] = time_terms(c->prm_host[r], c->t0 + (double)n * dt);
+    c->tt_host[3 * r + 1] = time_terms(c->prm_host[r], c->t0 + ((double)n + 0.5) * dt);
+    c->tt_host[3 * r + 2] = time_terms(c->prm_host[r], c->t0 + (double)(n + 1) * dt);
+  }
+  CK(cudaMemcpyAsync(c->tt_dev, c->tt_host, sizeof(TimeTerms) * 3 * c->nrep, cudaMemcpyHostToDevice, c->stream));
+  return PIC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -359,6 +375,12 @@ void pic_destroy(pic_ctx* c) {
     dev_free(c, *p);
     *p = nullptr;
   });
+  void* batch_dev[] = {c->reps_dev, c->prm_dev, c->rep_of_cell, c->poff_dev, c->dsmc_items, c->cg_order,
+                       c->cg_iters_rep, c->cg_res_rep, c->tt_dev};
+  for (void* p : batch_dev) dev_free(c, p);
+  if (c->tt_host) cudaFreeHost(c->tt_host);
+  free(c->reps_host);
+  free(c->prm_host);
   for (int i = 0; i < 2 * c->ev_cap; ++i) cudaEventDestroy(c->ev_pool[i]);
   free(c->ev_pool);
   free(c->ev_class);
@@ -491,6 +513,21 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
   c->t0 = t0;
   c->step = 0;
   c->cur = 0;
+  if (c->nrep > 0) {
+    c->lor_valid = false;
+    CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
+    pic_status s = batch_time_terms(c, 0);
+    if (s != PIC_OK) return s;
+    CK(launch_batch_sample(c, nullptr));
+    CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+    CK(launch_keys32(c));
+    CK(launch_scan_scatter(c));
+    CK(launch_gather32(c));
+    CK(launch_batch_rhs(c, 0));
+    CK(launch_batch_cg(c));
+    c->sampled = true;
+    return check_pending(c);
+  }
   if (c->mixed) {
     CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
     CK(launch_sample32(c, t0, nullptr));
@@ -506,6 +543,7 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
 
 pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0, int64_t step) {
   if (!c || !x || !v || !isfinite(t0) || step < 0) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
   const size_t bytes = (size_t)c->P.np * 3 * 8;
   CK(cudaMemcpyAsync(c->stage, x, bytes, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(c->stage + 3 * c->P.np, v, bytes, cudaMemcpyDefault, c->stream));
@@ -527,7 +565,19 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
   for (int32_t it = 0; it < nsteps; ++it) {
     const int64_t n = c->step;
     const double tn = time_at(c, (double)n), th = time_at(c, (double)n + 0.5), tn1 = time_at(c, (double)(n + 1));
-    if (c->mixed) {
+    if (c->nrep > 0) {
+      pic_status s = batch_time_terms(c, n);
+      if (s != PIC_OK) return s;
+      if (coll) CK(launch_batch_dsmc(c, (uint32_t)(2 * n), 0));
+      CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+      CK(launch_batch_kick(c, coll, true));
+      CK(launch_scan_scatter(c));
+      CK(launch_gather32(c));
+      CK(launch_batch_rhs(c, 2));
+      CK(launch_batch_cg(c));
+      if (coll) CK(launch_batch_dsmc(c, (uint32_t)(2 * n + 1), 1));
+      CK(launch_batch_kick(c, coll, false));
+    } else if (c->mixed) {
       if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n), false));
       CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
       CK(launch_kick32(c, tn, coll, true, th));
@@ -557,6 +607,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
 
 pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
   if (!c || !dv || !dvM || (phase != 0 && phase != 1)) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
   if (!c->sampled) return PIC_ESTATE;
   const size_t bytes = (size_t)c->P.np * 3 * 8;
   if (c->mixed) {
@@ -587,6 +638,7 @@ pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
 
 pic_status pic_mms_error(pic_ctx* c, pic_errors* out) {
   if (!c || !out) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
   if (!c->sampled) return PIC_ESTATE;
   if (c->mixed) {
     CK(launch_errors32(c, time_at(c, (double)c->step)));
@@ -606,6 +658,7 @@ pic_status pic_mms_error(pic_ctx* c, pic_errors* out) {
 
 pic_status pic_get_state(pic_ctx* c, double* x, double* v) {
   if (!c || !x || !v) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
   if (!c->sampled) return PIC_ESTATE;
   const size_t bytes = (size_t)c->P.np * 3 * 8;
   if (c->mixed) CK(launch_store_state32(c, c->stage, nullptr));
@@ -618,6 +671,7 @@ pic_status pic_get_state(pic_ctx* c, double* x, double* v) {
 
 pic_status pic_get_field(pic_ctx* c, double* rho, double* phi, double* E) {
   if (!c) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
   if (!c->sampled) return PIC_ESTATE;
   const size_t nc = (size_t)c->P.ncell;
   double* sphi = c->stage;
@@ -663,6 +717,7 @@ pic_status pic_get_field(pic_ctx* c, double* rho, double* phi, double* E) {
 
 pic_status pic_get_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* count, int32_t* start, int32_t* perm) {
   if (!c) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
   if (!c->sampled) return PIC_ESTATE;
   const size_t np = (size_t)c->P.np, nc = (size_t)c->P.ncell;
   int32_t* scell = (int32_t*)c->stage;            // fits: 6 np doubles = 12 np ints
@@ -726,6 +781,247 @@ pic_status pic_get_kernel_times(pic_ctx* c, pic_kernel_times* out) {
   for (int k = 0; k < PIC_NUM_KERNEL_CLASSES; ++k) {
     out->ms[k] = c->prof_ms[k];
     out->launches[k] = c->prof_launches[k];
+  }
+  return PIC_OK;
+}
+
+pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, const pic_allocator* alloc,
+                            pic_ctx** out) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  if (!cfgs || nrep < 1 || nrep > 65534) return PIC_EINVAL;
+  if (alloc && (!alloc->alloc || !alloc->free)) return PIC_EINVAL;
+  const pic_config& c0 = cfgs[0];
+  int64_t np_tot = 0, nc_tot = 0, items = 0;
+  int max_ppc = c0.max_ppc ? c0.max_ppc : 512;
+  for (int r = 0; r < nrep; ++r) {
+    const pic_config& c = cfgs[r];
+    if (pic_validate_config(&c) != PIC_OK || c.precision != PIC_MIXED) return PIC_EINVAL;
+    // everything but n, n_particles, K, dt, sigma0 and seed is shared
+    if (c.qm != c0.qm || c.q != c0.q || c.eps0 != c0.eps0 || c.n_phys != c0.n_phys || c.g_max != c0.g_max ||
+        c.fx_amp != c0.fx_amp || c.fx_speed != c0.fx_speed || c.v_sigma != c0.v_sigma || c.phi_amp != c0.phi_amp ||
+        c.phi_T != c0.phi_T || c.couple_qm_zero != c0.couple_qm_zero || c.couple_q_zero != c0.couple_q_zero ||
+        c.cg_tol != c0.cg_tol || c.cg_maxit != c0.cg_maxit || (c.max_ppc ? c.max_ppc : 512) != max_ppc)
+      return PIC_EINVAL;
+    for (int d = 0; d < 3; ++d)
+      if (c.v_mean[d] != c0.v_mean[d] || c.phi_shift[d] != c0.phi_shift[d]) return PIC_EINVAL;
+    np_tot += c.n_particles;
+    const int64_t nc = (int64_t)c.n * c.n * c.n;
+    nc_tot += (nc + kBatchTile - 1) / kBatchTile * kBatchTile;
+    if (c.K > 0) {
+      const int G = c.K < 32 ? 32 / c.K : 1;
+      items += (nc + G - 1) / G;
+    }
+  }
+  if (np_tot > 2147483647LL || nc_tot > 2147483647LL) return PIC_EINVAL;
+  pic_ctx* c = new (std::nothrow) pic_ctx();
+  if (!c) return PIC_ENOMEM;
+  memset((void*)c, 0, sizeof(*c));
+  c->cfg = c0;
+  c->cfg.max_ppc = (max_ppc + 31) / 32 * 32;
+  c->cfg.n_particles = np_tot;
+  c->stream = (cudaStream_t)stream;
+  c->mixed = true;
+  c->nrep = nrep;
+  if (alloc) {
+    c->alloc = *alloc;
+    c->have_alloc = true;
+  }
+  derive_params(c->cfg, c->P);
+  c->P.np = np_tot;
+  c->P.ncell = nc_tot;
+  int kmax = 1;
+  for (int r = 0; r < nrep; ++r) kmax = cfgs[r].K > kmax ? cfgs[r].K : kmax;
+  c->cfg.K = kmax;
+  c->P.K = kmax;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return PIC_ECUDA;
+  }
+  c->scan_nblocks = scan_blocks_needed(nc_tot);
+  c->rhs_blocks = 1;
+  int64_t eb = 1;
+  for (int r = 0; r < nrep; ++r) {
+    const int64_t b = err_blocks_needed(cfgs[r].n_particles, (int64_t)cfgs[r].n * cfgs[r].n * cfgs[r].n);
+    eb = b > eb ? b : eb;
+  }
+  c->err_blocks = (int)eb;
+  c->cg_grid = 1;
+  c->bm_words = c->cfg.max_ppc / 32;
+  c->dsmc_block = batch_dsmc_threads();
+  c->dsmc_smem = (size_t)(c->dsmc_block / 32) * 32 * c->bm_words * 4;
+  if (c->dsmc_smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(batch_dsmc_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->dsmc_smem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return PIC_EINVAL;
+    }
+  }
+  int docc = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&docc, batch_dsmc_kernel_ptr(), c->dsmc_block, c->dsmc_smem);
+  if (e != cudaSuccess || docc < 1) {
+    cudaGetLastError();
+    delete c;
+    return PIC_ECUDA;
+  }
+  const int64_t wpb = c->dsmc_block / 32;
+  int64_t dgrid = (items + wpb - 1) / wpb;
+  if (dgrid > (int64_t)docc * c->num_sms) dgrid = (int64_t)docc * c->num_sms;
+  c->dsmc_grid = (int)(dgrid < 1 ? 1 : dgrid);
+  c->n_items = items;
+
+  // host tables
+  c->reps_host = (BatchRep*)calloc((size_t)nrep, sizeof(BatchRep));
+  c->prm_host = (Params*)calloc((size_t)nrep, sizeof(Params));
+  uint16_t* roc = (uint16_t*)malloc((size_t)nc_tot * sizeof(uint16_t));
+  int64_t* poff = (int64_t*)malloc((size_t)(nrep + 1) * sizeof(int64_t));
+  int2* it_h = (int2*)malloc((size_t)(items > 0 ? items : 1) * sizeof(int2));
+  int* order = (int*)malloc((size_t)nrep * sizeof(int));
+  bool ok = c->reps_host && c->prm_host && roc && poff && it_h && order;
+  if (ok) {
+    int64_t p = 0, cc = 0, k = 0;
+    for (int r = 0; r < nrep; ++r) {
+      Params P;
+      derive_params(cfgs[r], P);
+      c->prm_host[r] = P;
+      BatchRep& B = c->reps_host[r];
+      B.poff = p;
+      B.coff = cc;
+      const int K = cfgs[r].K > 0 ? cfgs[r].K : 1;
+      B.Kc = K < 32 ? K : 32;
+      B.G = K < 32 ? 32 / K : 1;
+      B.nchunks = (cfgs[r].K + B.Kc - 1) / B.Kc;
+      poff[r] = p;
+      const int64_t nc = (int64_t)cfgs[r].n * cfgs[r].n * cfgs[r].n;
+      const int64_t ncp = (nc + kBatchTile - 1) / kBatchTile * kBatchTile;
+      for (int64_t i = 0; i < ncp; ++i) roc[cc + i] = i < nc ? (uint16_t)r : (uint16_t)0xFFFF;
+      if (cfgs[r].K > 0)
+        for (int64_t g = 0; g < nc; g += B.G) it_h[k++] = make_int2(r, (int)g);
+      p += cfgs[r].n_particles;
+      cc += ncp;
+      order[r] = r;
+    }
+    poff[nrep] = p;
+    // CG work: largest replicates first
+    for (int i = 1; i < nrep; ++i)
+      for (int j = i; j > 0 && cfgs[order[j]].n > cfgs[order[j - 1]].n; --j) {
+        const int t = order[j];
+        order[j] = order[j - 1];
+        order[j - 1] = t;
+      }
+  }
+  for_each_buffer(c, [&](void** pp, size_t bytes) {
+    if (!ok) return;
+    *pp = dev_alloc(c, bytes);
+    if (!*pp) ok = false;
+  });
+  auto grab = [&](void** pp, size_t bytes) {
+    if (!ok) return;
+    *pp = dev_alloc(c, bytes);
+    if (!*pp) ok = false;
+  };
+  grab((void**)&c->reps_dev, sizeof(BatchRep) * nrep);
+  grab((void**)&c->prm_dev, sizeof(Params) * nrep);
+  grab((void**)&c->rep_of_cell, sizeof(uint16_t) * nc_tot);
+  grab((void**)&c->poff_dev, sizeof(int64_t) * (nrep + 1));
+  grab((void**)&c->dsmc_items, sizeof(int2) * (items > 0 ? items : 1));
+  grab((void**)&c->cg_order, sizeof(int) * nrep);
+  grab((void**)&c->cg_iters_rep, sizeof(int) * nrep);
+  grab((void**)&c->cg_res_rep, sizeof(double) * nrep);
+  grab((void**)&c->tt_dev, sizeof(TimeTerms) * 3 * nrep);
+  if (ok && cudaMallocHost((void**)&c->tt_host, sizeof(TimeTerms) * 3 * nrep) != cudaSuccess) {
+    cudaGetLastError();
+    c->tt_host = nullptr;
+    ok = false;
+  }
+  if (!ok) {
+    free(roc); free(poff); free(it_h); free(order);
+    pic_destroy(c);
+    return PIC_ENOMEM;
+  }
+  // G^{-1} tables (shared manufactured distribution), then per-replicate copies
+  {
+    double* tab = (double*)malloc((size_t)(kGinvM + 1) * 2 * 8);
+    float* tabf = (float*)malloc((size_t)(kGinvM + 1) * 2 * 4);
+    if (tab && tabf) {
+      ginv_table(c0.fx_amp, tab);
+      for (int k = 0; k < 2 * (kGinvM + 1); ++k) tabf[k] = (float)tab[k];
+      e = cudaMemcpy(c->ginv, tab, (size_t)(kGinvM + 1) * 2 * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(c->ginv_f, tabf, (size_t)(kGinvM + 1) * 2 * 4, cudaMemcpyHostToDevice);
+    } else {
+      e = cudaErrorMemoryAllocation;
+    }
+    free(tab);
+    free(tabf);
+  }
+  c->P.ginv = c->ginv;
+  c->P.ginv_f = c->ginv_f;
+  c->P.ginv_M = kGinvM;
+  for (int r = 0; r < nrep; ++r) {
+    c->prm_host[r].ginv = c->ginv;
+    c->prm_host[r].ginv_f = c->ginv_f;
+    c->prm_host[r].ginv_M = kGinvM;
+    c->reps_host[r].f = params_f(c->prm_host[r]);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(c->reps_dev, c->reps_host, sizeof(BatchRep) * nrep, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->prm_dev, c->prm_host, sizeof(Params) * nrep, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->rep_of_cell, roc, sizeof(uint16_t) * nc_tot, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->poff_dev, poff, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && items > 0) e = cudaMemcpy(c->dsmc_items, it_h, sizeof(int2) * items, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->cg_order, order, sizeof(int) * nrep, cudaMemcpyHostToDevice);
+  free(roc); free(poff); free(it_h); free(order);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cg_info, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pic_destroy(c);
+    return cuda_status(e);
+  }
+  *out = c;
+  return PIC_OK;
+}
+
+pic_status pic_batch_mms_error(pic_ctx* c, pic_errors* out) {
+  if (!c || !out || c->nrep < 1) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  for (int r = 0; r < c->nrep; ++r) {
+    const double t = c->t0 + (double)c->step * c->prm_host[r].dt;
+    CK(launch_batch_errors(c, r, t));
+    double h[14];
+    CK(cudaMemcpyAsync(h, c->err_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < 7; ++q) {
+      out[r].eps2[q] = h[q];
+      out[r].epsinf[q] = h[7 + q];
+    }
+  }
+  return check_pending(c);
+}
+
+pic_status pic_batch_get_state(pic_ctx* c, int32_t rep, double* x, double* v) {
+  if (!c || !x || !v || c->nrep < 1 || rep < 0 || rep >= c->nrep) return PIC_EINVAL;
+  if (!c->sampled) return PIC_ESTATE;
+  const size_t bytes = (size_t)c->prm_host[rep].np * 3 * 8;
+  CK(launch_batch_store_state(c, rep, c->stage));
+  CK(cudaMemcpyAsync(x, c->stage, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(v, c->stage + 3 * c->prm_host[rep].np, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_batch_info(pic_ctx* c, int32_t* nrep, int64_t* n_particles, int32_t* cg_iters) {
+  if (!c) return PIC_EINVAL;
+  if (nrep) *nrep = c->nrep;
+  if (n_particles) *n_particles = c->P.np;
+  if (cg_iters && c->nrep > 0) {
+    CK(cudaMemcpyAsync(cg_iters, c->cg_iters_rep, sizeof(int) * c->nrep, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
   }
   return PIC_OK;
 }

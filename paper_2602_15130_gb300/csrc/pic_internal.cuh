@@ -41,6 +41,7 @@ struct Params {
   int ginv_M;
 };
 
+
 // FP32 copy of the parameters the precision-form kernels use, converted
 // once on the host (FP64 arithmetic in a kernel would run on the slow
 // FP64 pipe).
@@ -58,6 +59,15 @@ struct ParamsF {
   const float* ginv_f;
   int ginv_M;
 };
+
+// Per-replicate data of a batch (device copy).
+struct BatchRep {
+  ParamsF f;
+  int64_t poff, coff;  // first particle, first cell/node
+  int Kc, G, nchunks;
+};
+constexpr int kBatchTile = 256;
+
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11). Round: two 32x32 -> 64 products with
@@ -301,6 +311,26 @@ struct pic_ctx {
   double cg_res_last;
   pic_status pending;  // sticky status from asynchronous checks
 
+  // batch of independent replicates (0 = single domain). Arrays above hold
+  // all replicates back to back: particles at poff[r], cells and nodes at
+  // coff[r] (padded to a multiple of 256).
+  int nrep;
+  pic::BatchRep* reps_dev;       // [nrep] per-replicate parameters
+  pic::BatchRep* reps_host;
+  pic::Params* prm_dev;          // [nrep] FP64 parameters
+  pic::Params* prm_host;
+  uint16_t* rep_of_cell;         // [ncell total] replicate of each cell/node, 0xFFFF = padding
+  int64_t* poff_dev;             // [nrep + 1]
+  int2* dsmc_items;              // (replicate, first local cell) per warp work item
+  int64_t n_items;
+  int* cg_order;                 // replicates by decreasing size
+  int* cg_iters_rep;             // [nrep]
+  double* cg_res_rep;            // [nrep]
+  pic::TimeTerms* tt_dev;        // [nrep][3]: t_n, t_{n+1/2}, t_{n+1}
+  pic::TimeTerms* tt_host;       // pinned
+  int kick_block, gather_block;  // autotuned block sizes
+  int tune_step;
+
   // profiling: pairs of events recorded on the stream, resolved lazily
   bool profiling;
   cudaEvent_t* ev_pool;
@@ -330,6 +360,15 @@ cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift,
 cudaError_t launch_errors(pic_ctx* c, double t);
 TimeTerms time_terms(const Params& P, double t);
 ParamsF params_f(const Params& P);
+
+// batched kernels (k_batch.cu)
+cudaError_t launch_batch_sample(pic_ctx* c, const double* xv);
+cudaError_t launch_batch_rhs(pic_ctx* c, int slot);
+cudaError_t launch_batch_cg(pic_ctx* c);
+cudaError_t launch_batch_dsmc(pic_ctx* c, uint32_t c0, int slot);
+cudaError_t launch_batch_kick(pic_ctx* c, bool with_collisions, bool drift);
+cudaError_t launch_batch_errors(pic_ctx* c, int rep, double t);
+cudaError_t launch_batch_store_state(pic_ctx* c, int rep, double* xv);
 cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E);
 cudaError_t launch_store_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* perm);
 cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm);
