@@ -42,6 +42,8 @@ def workload(name: str) -> dict:
 
     if name == "precision":
         return W.precision_form()
+    if name == "batched":
+        return {"batch": W.batched(256)}
     if name == "refine4":
         return W.refinement_level(4)
     if name.startswith("refine"):
@@ -274,6 +276,64 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
     }
 
 
+# --------------------------------------------------------------- batches ---
+def run_batched(args, rank: int, world: int) -> dict | None:
+    """256 uneven replicates advanced together (pic_create_batch)."""
+    import torch
+
+    from paper_2602_15130_gb300 import Batch
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    cfgs = [replica_params(p, rank * 100000) for p in workload("batched")["batch"]]
+    npart = sum(p["n_particles"] for p in cfgs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = Batch(cfgs, stream=stream)
+        b.sample_mms(0.0)
+        b.step(max(args.warmup, 4))  # 3 autotuning steps, then graph capture
+        torch.cuda.synchronize()
+        b.reset_stats()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            time.sleep(0.3)
+            ev0.record(stream)
+            b.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = max_over_ranks(ev0.elapsed_time(ev1), "cuda")
+        st = b.stats()
+        # per-kernel times from a profiled pass (direct launches)
+        b.set_profiling(True)
+        b.step(1)
+        kt = b.kernel_times()
+        b.set_profiling(False)
+        errs = b.mms_error()
+        iters = b.cg_iters()
+        b.close()
+    if rank != 0:
+        return None
+    ns = sorted({p["n"] for p in cfgs})
+    return {
+        "metric": METRIC, "value": aggregate_value(npart, args.steps, world, ms), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 4), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic manufactured-solution workload",
+        "config": {"workload": "batched: %d replicates, n in %s, %d particles in total, K in [%d, %d], dt = 0.005, "
+                               "precision form" % (len(cfgs), ns, npart, min(p["K"] for p in cfgs),
+                                                   max(p["K"] for p in cfgs)),
+                   "n_particles": npart, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2"},
+        "e2e": None, "e2e_note": "batches have no host-buffer input path (states are sampled on the device)",
+        "gpu_launches": int(st["kernel_launches"]), "graph_replays": int(st["graph_replays"]),
+        "tuned_kick_block": int(st["tuned_kick_block"]),
+        "kernel_ms_one_profiled_step": {k: round(v["ms"], 3) for k, v in kt.items()},
+        "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
+                  "cg_iters_max": st["cg_iters_max"], "cg_iters_median": sorted(iters)[len(iters) // 2]},
+        "mms_error_eps2_x_median": float(sorted(e[0] for e in errs)[len(errs) // 2]),
+        "clocks": clk.summary(),
+    }
+
+
 # ------------------------------------------------------------ CPU oracle ----
 def oracle_sample_params(args) -> tuple[dict, str]:
     from paper_2602_15130_gb300 import workloads as W
@@ -354,6 +414,15 @@ def main():
         import torch.distributed as td
 
         td.barrier()
+    if args.workload == "batched":
+        out = run_batched(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        if world > 1:
+            import torch.distributed as td
+
+            td.destroy_process_group()
+        return
     out = run_gpu(args, rank, world, args.form)
     beside = None
     if args.form == "mixed" and not args.no_fp64_beside:

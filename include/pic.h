@@ -122,6 +122,9 @@ typedef struct {
   int32_t cg_iters_last;  /* iterations of the last Poisson solve           */
   int32_t cg_iters_max;
   double cg_res_last;     /* last relative residual ||r|| / ||b||           */
+  int64_t graph_replays;  /* batched steps replayed from a captured CUDA graph */
+  int32_t tuned_kick_block; /* block size the batch autotuner chose (0: none) */
+  int32_t reserved;
 } pic_stats;
 
 /* Optional device allocator (e.g. a framework's caching allocator). Both

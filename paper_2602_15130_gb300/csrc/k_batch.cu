@@ -286,7 +286,8 @@ struct BDsmcArgs {
   const BatchRep* reps;
   const float *v0, *v1, *v2;
   const int32_t* start;
-  uint32_t c0;
+  const int64_t* step;  // device-side step counter (graph replays change no argument)
+  int phase;
   const int2* items;
   int64_t n_items;
   float *dv0, *dv1, *dv2;
@@ -380,6 +381,7 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) kb_dsmc(BDsmcArgs a) {
   for (int i = 0; i < a.bm_words; ++i) bm[i] = 0u;
   __syncwarp();
   CountsB cnt = {0, 0, 0, 0};
+  const uint32_t c0 = (uint32_t)(2 * (*a.step) + a.phase);
   for (int64_t it = gwarp; it < a.n_items; it += nwarps) {
     const int2 item = a.items[it];
     const BatchRep& B = a.reps[item.x];
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) kb_dsmc(BDsmcArgs a) {
         run = false;
       }
       if (run)
-        ntc_outcome_b(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s, bm, ov,
+        ntc_outcome_b(P, c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s, bm, ov,
                       cnt);
       __syncwarp();
       const bool last = ch == nchunks - 1;
@@ -640,13 +642,14 @@ cudaError_t launch_batch_cg(pic_ctx* c) {
 int batch_dsmc_threads() { return kDsmcThreads; }
 const void* batch_dsmc_kernel_ptr() { return (const void*)kb_dsmc; }
 
-cudaError_t launch_batch_dsmc(pic_ctx* c, uint32_t c0, int /*slot*/) {
+cudaError_t launch_batch_dsmc(pic_ctx* c, int phase) {
   BDsmcArgs a;
   a.reps = c->reps_dev;
   const int b = c->cur;
   a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
   a.start = c->start;
-  a.c0 = c0;
+  a.step = reinterpret_cast<const int64_t*>(c->tt_dev + 3 * c->nrep);
+  a.phase = phase;
   a.items = c->dsmc_items;
   a.n_items = c->n_items;
   a.dv0 = c->dvf[0]; a.dv1 = c->dvf[1]; a.dv2 = c->dvf[2];

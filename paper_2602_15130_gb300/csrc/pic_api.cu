@@ -213,7 +213,7 @@ void for_each_buffer(pic_ctx* c, F f) {
     for (int d = 0; d < 3; ++d) {
       f((void**)&c->lorf[d], np * 4);
       f((void**)&c->dvf[d], np * 4);
-      f((void**)&c->dvmf[d], np * 4);
+      if (c->nrep == 0) f((void**)&c->dvmf[d], np * 4);  // pic_collide_avg only
       f((void**)&c->Ef[d], nc * 4);
     }
     f((void**)&c->bf, nc * 4);
@@ -243,8 +243,15 @@ void for_each_buffer(pic_ctx* c, F f) {
   f((void**)&c->err_out, 14 * 8);
   f((void**)&c->ginv, (size_t)(kGinvM + 1) * 2 * 8);
   f((void**)&c->ginv_f, (size_t)(kGinvM + 1) * 2 * 4);
-  f((void**)&c->stage, 6 * np * 8);
-  f((void**)&c->stage_i, (np + 1) * 4);
+  // host-boundary staging: the largest replicate of a batch, else everything
+  size_t stage_np = np;
+  if (c->nrep > 0) {
+    stage_np = 1;
+    for (int r = 0; r < c->nrep; ++r)
+      stage_np = (size_t)c->prm_host[r].np > stage_np ? (size_t)c->prm_host[r].np : stage_np;
+  }
+  f((void**)&c->stage, 6 * stage_np * 8);
+  f((void**)&c->stage_i, (stage_np + 1) * 4);
 }
 
 // Read and clear the sticky device flags of the work enqueued so far
@@ -288,17 +295,117 @@ pic_status sort_and_field(pic_ctx* c, double t) {
 
 double time_at(const pic_ctx* c, double steps) { return c->t0 + steps * c->cfg.dt; }
 
-// Per-replicate time terms of step n (t_n, t_{n+1/2}, t_{n+1}); every
-// replicate has its own dt.
+// Per-replicate time terms of step n (t_n, t_{n+1/2}, t_{n+1}) and the step
+// number into the pinned mirror (every replicate has its own dt); the copy
+// to the device is enqueued by batch_enqueue_times (and captured in graphs).
 pic_status batch_time_terms(pic_ctx* c, int64_t n) {
-  CK(cudaStreamSynchronize(c->stream));  // the pinned buffer may still feed a copy
+  CK(cudaStreamSynchronize(c->stream));  // the pinned mirror may still feed a copy
   for (int r = 0; r < c->nrep; ++r) {
     const double dt = c->prm_host[r].dt;
     c->tt_host[3 * r + 0] = time_terms(c->prm_host[r], c->t0 + (double)n * dt);
     c->tt_host[3 * r + 1] = time_terms(c->prm_host[r], c->t0 + ((double)n + 0.5) * dt);
     c->tt_host[3 * r + 2] = time_terms(c->prm_host[r], c->t0 + (double)(n + 1) * dt);
   }
-  CK(cudaMemcpyAsync(c->tt_dev, c->tt_host, sizeof(TimeTerms) * 3 * c->nrep, cudaMemcpyHostToDevice, c->stream));
+  memset((void*)(c->tt_host + 3 * c->nrep), 0, sizeof(TimeTerms));
+  *reinterpret_cast<int64_t*>(c->tt_host + 3 * c->nrep) = n;
+  return PIC_OK;
+}
+
+cudaError_t batch_enqueue_times(pic_ctx* c) {
+  return cudaMemcpyAsync(c->tt_dev, c->tt_host, sizeof(TimeTerms) * (3 * c->nrep + 1), cudaMemcpyHostToDevice,
+                         c->stream);
+}
+
+// One step of every replicate, enqueued without host synchronisation (so it
+// can be captured into a graph).
+cudaError_t batch_enqueue_step(pic_ctx* c, bool coll) {
+  cudaError_t e = batch_enqueue_times(c);
+  if (e == cudaSuccess && coll) e = launch_batch_dsmc(c, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream);
+  if (e == cudaSuccess) e = launch_batch_kick(c, coll, true);
+  if (e == cudaSuccess) e = launch_scan_scatter(c);
+  if (e == cudaSuccess) e = launch_gather32(c);
+  if (e == cudaSuccess) e = launch_batch_rhs(c, 2);
+  if (e == cudaSuccess) e = launch_batch_cg(c);
+  if (e == cudaSuccess && coll) e = launch_batch_dsmc(c, 1);
+  if (e == cudaSuccess) e = launch_batch_kick(c, coll, false);
+  return e;
+}
+
+constexpr int kTuneCandidates = 3;
+const int kKickBlocks[kTuneCandidates] = {128, 256, 512};
+
+// One batched step: the first steps time the candidate kick block sizes
+// (the result does not depend on the block size), later steady-state steps
+// replay a captured graph per buffer parity.
+pic_status batch_step(pic_ctx* c, int64_t n, bool coll) {
+  pic_status s = batch_time_terms(c, n);
+  if (s != PIC_OK) return s;
+  if (c->tune_step < kTuneCandidates) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    c->kick_block = kKickBlocks[c->tune_step];
+    CK(batch_enqueue_times(c));
+    if (coll) CK(launch_batch_dsmc(c, 0));
+    CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+    CK(cudaEventRecord(e0, c->stream));
+    CK(launch_batch_kick(c, coll, true));
+    CK(cudaEventRecord(e1, c->stream));
+    CK(launch_scan_scatter(c));
+    CK(launch_gather32(c));
+    CK(launch_batch_rhs(c, 2));
+    CK(launch_batch_cg(c));
+    if (coll) CK(launch_batch_dsmc(c, 1));
+    CK(launch_batch_kick(c, coll, false));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune_ms[c->tune_step] = ms;
+    if (++c->tune_step == kTuneCandidates) {
+      int best = 0;
+      for (int k = 1; k < kTuneCandidates; ++k)
+        if (c->tune_ms[k] < c->tune_ms[best]) best = k;
+      c->kick_block = kKickBlocks[best];
+    }
+    return PIC_OK;
+  }
+  if (!c->use_graphs || c->profiling || !c->lor_valid) {
+    CK(batch_enqueue_step(c, coll));
+    return PIC_OK;
+  }
+  const int parity = c->cur;
+  if (!c->graph[parity]) {
+    const int64_t l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = batch_enqueue_step(c, coll);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return PIC_ECUDA;
+    }
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->graph[parity] = nullptr;
+      return PIC_ECUDA;
+    }
+    // the capture advanced the host state (buffer parity, Lorentz flag) as a
+    // step would; restore it, then replay
+    c->cur = parity;
+  }
+  CK(cudaGraphLaunch(c->graph[parity], c->stream));
+  c->graph_replays++;
+  c->cur = 1 - parity;
+  c->lor_valid = true;
+  c->launches += c->graph_launches;
   return PIC_OK;
 }
 
@@ -379,6 +486,8 @@ void pic_destroy(pic_ctx* c) {
                        c->cg_iters_rep, c->cg_res_rep, c->tt_dev};
   for (void* p : batch_dev) dev_free(c, p);
   if (c->tt_host) cudaFreeHost(c->tt_host);
+  for (int k = 0; k < 2; ++k)
+    if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
   free(c->reps_host);
   free(c->prm_host);
   for (int i = 0; i < 2 * c->ev_cap; ++i) cudaEventDestroy(c->ev_pool[i]);
@@ -518,6 +627,7 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
     CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
     pic_status s = batch_time_terms(c, 0);
     if (s != PIC_OK) return s;
+    CK(batch_enqueue_times(c));
     CK(launch_batch_sample(c, nullptr));
     CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
     CK(launch_keys32(c));
@@ -566,17 +676,8 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     const int64_t n = c->step;
     const double tn = time_at(c, (double)n), th = time_at(c, (double)n + 0.5), tn1 = time_at(c, (double)(n + 1));
     if (c->nrep > 0) {
-      pic_status s = batch_time_terms(c, n);
+      pic_status s = batch_step(c, n, coll);
       if (s != PIC_OK) return s;
-      if (coll) CK(launch_batch_dsmc(c, (uint32_t)(2 * n), 0));
-      CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-      CK(launch_batch_kick(c, coll, true));
-      CK(launch_scan_scatter(c));
-      CK(launch_gather32(c));
-      CK(launch_batch_rhs(c, 2));
-      CK(launch_batch_cg(c));
-      if (coll) CK(launch_batch_dsmc(c, (uint32_t)(2 * n + 1), 1));
-      CK(launch_batch_kick(c, coll, false));
     } else if (c->mixed) {
       if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n), false));
       CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
@@ -753,6 +854,8 @@ pic_status pic_get_stats(pic_ctx* c, pic_stats* out) {
   out->cg_iters_last = c->cg_iters_last;
   out->cg_iters_max = c->cg_iters_max;
   out->cg_res_last = c->cg_res_last;
+  out->graph_replays = c->graph_replays;
+  out->tuned_kick_block = c->kick_block;
   return s;
 }
 
@@ -932,8 +1035,8 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   grab((void**)&c->cg_order, sizeof(int) * nrep);
   grab((void**)&c->cg_iters_rep, sizeof(int) * nrep);
   grab((void**)&c->cg_res_rep, sizeof(double) * nrep);
-  grab((void**)&c->tt_dev, sizeof(TimeTerms) * 3 * nrep);
-  if (ok && cudaMallocHost((void**)&c->tt_host, sizeof(TimeTerms) * 3 * nrep) != cudaSuccess) {
+  grab((void**)&c->tt_dev, sizeof(TimeTerms) * (3 * nrep + 1));
+  if (ok && cudaMallocHost((void**)&c->tt_host, sizeof(TimeTerms) * (3 * nrep + 1)) != cudaSuccess) {
     cudaGetLastError();
     c->tt_host = nullptr;
     ok = false;
@@ -983,6 +1086,8 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
     pic_destroy(c);
     return cuda_status(e);
   }
+  // graphs cannot capture the legacy default stream
+  c->use_graphs = c->stream != nullptr;
   *out = c;
   return PIC_OK;
 }

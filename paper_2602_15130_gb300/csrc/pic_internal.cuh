@@ -326,10 +326,15 @@ struct pic_ctx {
   int* cg_order;                 // replicates by decreasing size
   int* cg_iters_rep;             // [nrep]
   double* cg_res_rep;            // [nrep]
-  pic::TimeTerms* tt_dev;        // [nrep][3]: t_n, t_{n+1/2}, t_{n+1}
-  pic::TimeTerms* tt_host;       // pinned
-  int kick_block, gather_block;  // autotuned block sizes
+  pic::TimeTerms* tt_dev;        // [nrep][3]: t_n, t_{n+1/2}, t_{n+1}, then the step (int64)
+  pic::TimeTerms* tt_host;       // pinned mirror
+  int kick_block;                // autotuned block size of the batched kick
   int tune_step;
+  float tune_ms[4];
+  cudaGraphExec_t graph[2];      // steady-state step, by buffer parity
+  int64_t graph_launches;        // kernels per captured step
+  int64_t graph_replays;
+  bool use_graphs;
 
   // profiling: pairs of events recorded on the stream, resolved lazily
   bool profiling;
@@ -365,7 +370,7 @@ ParamsF params_f(const Params& P);
 cudaError_t launch_batch_sample(pic_ctx* c, const double* xv);
 cudaError_t launch_batch_rhs(pic_ctx* c, int slot);
 cudaError_t launch_batch_cg(pic_ctx* c);
-cudaError_t launch_batch_dsmc(pic_ctx* c, uint32_t c0, int slot);
+cudaError_t launch_batch_dsmc(pic_ctx* c, int phase);
 cudaError_t launch_batch_kick(pic_ctx* c, bool with_collisions, bool drift);
 cudaError_t launch_batch_errors(pic_ctx* c, int rep, double t);
 cudaError_t launch_batch_store_state(pic_ctx* c, int rep, double* xv);

@@ -101,3 +101,26 @@ def test_batched_workload_recipe_small():
     assert np.all(np.isfinite(e)) and e.shape == (12, 14)
     st = b.stats()
     assert st["n_coll"] > 0 and st["n_near_ties"] >= 0
+
+
+def test_graph_replayed_steps_are_bit_identical_and_tuned():
+    """After the autotuning steps a batch on a real stream replays captured
+    graphs; its state must equal a batch on the legacy stream (no graphs)."""
+    import torch
+
+    cf = configs()[:3]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a = Batch(cf, stream=stream)
+        a.sample_mms(0.0)
+        a.step(8)
+        sa = a.stats()
+    b = Batch(cf, stream=0)
+    b.sample_mms(0.0)
+    b.step(8)
+    assert sa["graph_replays"] >= 4 and b.stats()["graph_replays"] == 0
+    assert sa["tuned_kick_block"] in (128, 256, 512)
+    for r in range(3):
+        xa, va = a.get_state(r)
+        xb, vb = b.get_state(r)
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb), r
