@@ -59,7 +59,16 @@ class OrcCfg(ctypes.Structure):
         ("phi_T", ctypes.c_double),
         ("phi_shift", ctypes.c_double * 3),
         ("cg_tol", ctypes.c_double),
+        ("verify", ctypes.c_int64),
     ]
+
+
+# verification switches (bit flags of ``verify``), Sec. 5.4
+ISOLATE = 1
+ERROR1 = 2
+ERROR2 = 4
+ANGLES = 8
+ANISO = 16
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -120,6 +129,10 @@ def lib():
             "orc_set_phi": (None, [ctypes.c_void_p, _D]),
             "orc_ntc_cell": (ctypes.c_int64, [_CFG, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                               ctypes.c_int64, _D]),
+            "orc_angle_count": (ctypes.c_int64, [ctypes.c_void_p]),
+            "orc_aniso_F": (ctypes.c_double, [ctypes.c_double]),
+            "orc_aniso_u": (ctypes.c_double, [ctypes.c_double]),
+            "orc_get_angles": (None, [ctypes.c_void_p, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -166,6 +179,7 @@ def make_cfg(p: dict) -> OrcCfg:
     c.phi_amp = float(p.get("phi_amp", 0.1))
     c.phi_T = float(p.get("phi_T", 1.0))
     c.cg_tol = float(p.get("cg_tol", 1e-13))
+    c.verify = int(p.get("verify", 0))
     return c
 
 
@@ -262,6 +276,14 @@ class Oracle:
 
     def reset_stats(self):
         self.L.orc_reset_stats(self.h)
+
+    def angles(self) -> np.ndarray:
+        """(chi, eps) of every recorded collision, ``[N_coll, 2]``."""
+        n = int(self.L.orc_angle_count(self.h))
+        out = np.zeros((n, 2))
+        if n:
+            self.L.orc_get_angles(self.h, _dp(out))
+        return out
 
 
 # ---- scalar helpers used by the pins ---------------------------------------
@@ -364,6 +386,38 @@ def ntc_cell(cfg, c0, cell, outcome, v):
     vv = np.ascontiguousarray(v, dtype=np.float64).copy()
     ncoll = lib().orc_ntc_cell(ctypes.byref(cfg), c0, cell, outcome, vv.shape[0], _dp(vv))
     return vv, ncoll
+
+
+def F_chi_iso(chi):
+    """Analytic CDF of the isotropic polar angle, (1 - cos chi)/2 (Eq. Fp_chi
+    with the isotropic p(chi) = sin(chi)/2)."""
+    return 0.5 * (1.0 - np.cos(chi))
+
+
+def F_chi_aniso(chi):
+    """Analytic CDF of the manufactured anisotropic polar angle (Sec. 5.1):
+    sin^2(chi/2) - (3 + 5 cos 2 chi) sin^2(chi) / 58."""
+    chi = np.asarray(chi)
+    return np.sin(chi / 2) ** 2 - (3.0 + 5.0 * np.cos(2 * chi)) * np.sin(chi) ** 2 / 58.0
+
+
+def F_eps(eps):
+    """Analytic CDF of the azimuth, eps/(2 pi) (Eq. Fp_eps)."""
+    return np.asarray(eps) / (2.0 * np.pi)
+
+
+def angle_cdf_errors(alpha: np.ndarray, F) -> tuple[float, float]:
+    """Sec. 4.4: e_r = F_emp(alpha_r) - F^M(alpha_r) for every recorded angle,
+    with the empirical CDF F_emp(a) = (1/N) sum_s theta(a - alpha_s) and
+    theta(0) = 1 (the CDF is right-continuous). Returns (eps_2, eps_inf)."""
+    a = np.asarray(alpha, dtype=np.float64)
+    N = a.size
+    if N == 0:
+        return 0.0, 0.0
+    srt = np.sort(a)
+    Femp = np.searchsorted(srt, a, side="right") / N
+    e = Femp - F(a)
+    return float(np.sqrt(np.mean(e * e))), float(np.max(np.abs(e)))
 
 
 def wrap(x):

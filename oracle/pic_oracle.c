@@ -47,7 +47,25 @@ typedef struct {
   double phi_amp, phi_T;
   double phi_shift[3];
   double cg_tol;
+  int64_t verify;  /* verification switches, bit flags (Sec. 5.4):
+                    *   1  isolated-collision mode: the drift moves x by the
+                    *      exact manufactured increment x^M(t_{n+1}) - x^M(t_n)
+                    *      in place of dt xdot^M(t_{n+1/2}) (v^M is constant,
+                    *      so the kicks' vdot^M terms are zero either way)
+                    *   2  injected Error 1: v_cm = (v_p - v_q)/2
+                    *   4  injected Error 2: velocities swapped with
+                    *      probability 1/2, else left unchanged
+                    *   8  record (chi, eps) of every collision (Sec. 4.4)
+                    *  16  manufactured anisotropic scattering (Sec. 5.1):
+                    *      p_chi = (29/2 + 12 cos chi - 20 cos^3 chi)
+                    *      sin chi / 29 in place of sin chi / 2           */
 } orc_cfg;
+
+#define ORC_ISOLATE 1
+#define ORC_ERROR1 2
+#define ORC_ERROR2 4
+#define ORC_ANGLES 8
+#define ORC_ANISO 16
 
 /* ------------------------------------------------------------------------
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -259,6 +277,8 @@ typedef struct {
   int64_t n_cand, n_coll, n_gmax, n_tie;
   int64_t cg_iters;
   double cg_res;
+  double* ang;          /* [n_ang][2]: (chi, eps) of recorded collisions  */
+  int64_t n_ang, cap_ang;
 } orc_state;
 
 static int64_t ncell(const orc_cfg* c) { return c->n * c->n * c->n; }
@@ -301,6 +321,7 @@ void orc_destroy(orc_state* s) {
   if (!s) return;
   free(s->xi); free(s->x); free(s->v); free(s->rho); free(s->phi); free(s->E);
   free(s->cell); free(s->count); free(s->start); free(s->perm);
+  free(s->ang);
   free(s);
 }
 
@@ -524,8 +545,50 @@ int64_t orc_field(orc_state* s, double t) {
  *             Philox(c0, k, s, o<<8 | b), b >= 2: four more q redraws each
  * ---------------------------------------------------------------------- */
 typedef struct {
+  double* a;  /* [n][2] (chi, eps) */
+  int64_t n, cap;
+} orc_angles;
+
+typedef struct {
   int64_t n_cand, n_coll, n_gmax, n_tie;
+  orc_angles* rec;  /* NULL: angles not recorded */
 } orc_dsmc_stats;
+
+/* Manufactured anisotropy (Sec. 5.1): with u = sin^2(chi/2) the CDF of chi
+ * is F(u) = (13 u + 96 u^2 - 160 u^3 + 80 u^4)/29, increasing on [0, 1]
+ * (p_chi > 0). chi = F^{-1}(xi) by bisection on u to the last bit; the
+ * isotropic kernel is F(u) = u.                                            */
+double orc_aniso_F(double u) {
+  return (13.0 * u + 96.0 * u * u - 160.0 * u * u * u + 80.0 * u * u * u * u) / 29.0;
+}
+
+double orc_aniso_u(double xi) {
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (orc_aniso_F(mid) < xi) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* Sec. 4.4, Eq. angle_recovery: chi = acos(g'_z / g) with the PRE-collision
+ * relative speed g, eps = atan2(g'_y, g'_x) taken into [0, 2 pi).          */
+static void record_angles(orc_angles* r, double g, const double gp[3]) {
+  if (r->n == r->cap) {
+    r->cap = r->cap ? 2 * r->cap : 1024;
+    r->a = (double*)realloc(r->a, (size_t)(2 * r->cap) * sizeof(double));
+  }
+  double cz = gp[2] / g;
+  if (cz > 1.0) cz = 1.0;
+  if (cz < -1.0) cz = -1.0;
+  double eps = atan2(gp[1], gp[0]);
+  if (eps < 0.0) eps += 2.0 * ORC_PI;
+  r->a[2 * r->n] = acos(cz);
+  r->a[2 * r->n + 1] = eps;
+  r->n++;
+}
 
 /* P_coll,max = (sigma g)_max w dt / dV (Algorithm 1; Eq. p_coll at g where
  * sigma g peaks). For hard spheres (sigma g)_max = sigma0 g_max.          */
@@ -576,18 +639,37 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
     if (g > cf->gmax) st->n_gmax++;
     if (fabs(U - ratio) < 1e-12) st->n_tie++;
     if (U < ratio) {
-      double eps = 2.0 * ORC_PI * orc_u32(b0[3]);     /* epsilon = 2 pi U        */
-      double cchi = 1.0 - 2.0 * orc_u32(b1[0]);       /* chi = acos(1 - 2U)      */
-      double schi = sqrt(1.0 - cchi * cchi);
-      double n[3] = {cos(eps) * schi, sin(eps) * schi, cchi}; /* Eq. n (lab frame) */
-      double gp[3], vcm[3];
-      for (int d = 0; d < 3; d++) {
-        gp[d] = g * n[d];
-        vcm[d] = (vp[d] + vq[d]) / 2.0;
+      if (cf->verify & ORC_ERROR2) {
+        /* injected Error 2 (Sec. 5.4): swap with probability beta = 1/2,
+         * the coin being the chi word of block 1                          */
+        if (orc_u32(b1[0]) < 0.5) {
+          for (int d = 0; d < 3; d++) {
+            double tmp = vp[d];
+            vp[d] = vq[d];
+            vq[d] = tmp;
+          }
+        }
+      } else {
+        double eps = 2.0 * ORC_PI * orc_u32(b0[3]);     /* epsilon = 2 pi U        */
+        /* chi = F^{-1}(U) (Eq. chi): cos chi = 1 - 2U isotropic, 1 - 2u(U) anisotropic */
+        double uchi = (cf->verify & ORC_ANISO) ? orc_aniso_u(orc_u32(b1[0])) : orc_u32(b1[0]);
+        double cchi = 1.0 - 2.0 * uchi;
+        double schi = sqrt(1.0 - cchi * cchi);
+        double n[3] = {cos(eps) * schi, sin(eps) * schi, cchi}; /* Eq. n (lab frame) */
+        double gp[3], vcm[3];
+        for (int d = 0; d < 3; d++) {
+          gp[d] = g * n[d];
+          /* Eq. v_cm; injected Error 1 flips the sign of v_q             */
+          vcm[d] = (cf->verify & ORC_ERROR1) ? (vp[d] - vq[d]) / 2.0 : (vp[d] + vq[d]) / 2.0;
+        }
+        for (int d = 0; d < 3; d++) {
+          vp[d] = vcm[d] + gp[d] / 2.0;
+          vq[d] = vcm[d] - gp[d] / 2.0;
+        }
       }
-      for (int d = 0; d < 3; d++) {
-        vp[d] = vcm[d] + gp[d] / 2.0;
-        vq[d] = vcm[d] - gp[d] / 2.0;
+      if (st->rec) {
+        double gpost[3] = {vp[0] - vq[0], vp[1] - vq[1], vp[2] - vq[2]};
+        record_angles(st->rec, g, gpost);
       }
       st->n_coll++;
     }
@@ -599,7 +681,8 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
 void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
   const orc_cfg* cf = &s->c;
   int64_t nc = ncell(cf);
-  orc_dsmc_stats st = {0, 0, 0, 0};
+  orc_angles rec = {s->ang, s->n_ang, s->cap_ang};
+  orc_dsmc_stats st = {0, 0, 0, 0, (cf->verify & ORC_ANGLES) ? &rec : NULL};
   for (int64_t p = 0; p < 3 * cf->np; p++) dv[p] = 0.0;
   if (cf->K <= 0) return;
   double* v0 = NULL;
@@ -633,6 +716,9 @@ void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
     }
   }
   free(v0); free(vloc); free(acc);
+  s->ang = rec.a;
+  s->n_ang = rec.n;
+  s->cap_ang = rec.cap;
   s->n_cand += st.n_cand;
   s->n_coll += st.n_coll;
   s->n_gmax += st.n_gmax;
@@ -658,6 +744,7 @@ void orc_sample(orc_state* s, double t0) {
   const orc_cfg* cf = &s->c;
   s->t0 = t0;
   s->step = 0;
+  s->n_ang = 0;
   for (int64_t p = 0; p < cf->np; p++) {
     for (int d = 0; d < 3; d++) {
       s->x[3 * p + d] = orc_xM(cf, s->xi[6 * p + d], t0);
@@ -716,13 +803,20 @@ void orc_step(orc_state* s, int64_t nsteps) {
     orc_source_all(s, s->v, dvM);
     for (int64_t j = 0; j < 3 * np; j++)
       vh[j] = s->v[j] + 0.5 * (L[j] + dv[j] - dvM[j] + cf->dt * vdotM);
-    /* x^{n+1} = x^n + dt (v + xdot^M - v^M)^{n+1/2}, wrapped              */
+    /* x^{n+1} = x^n + dt (v + xdot^M - v^M)^{n+1/2}, wrapped; in the
+     * isolated-collision mode dt xdot^M(t_{n+1/2}) becomes the exact
+     * increment x^M(t_{n+1}) - x^M(t_n) (Sec. 5.4)                       */
     for (int64_t p = 0; p < np; p++) {
       for (int d = 0; d < 3; d++) {
-        double xm = orc_xM(cf, s->xi[6 * p + d], th);
-        double xmd = orc_xMdot(cf, xm, th);
         double vm = orc_vM(cf, d, s->xi[6 * p + 3 + d]);
-        s->x[3 * p + d] = orc_wrap(s->x[3 * p + d] + cf->dt * (vh[3 * p + d] + xmd - vm));
+        if (cf->verify & ORC_ISOLATE) {
+          double dxm = orc_xM(cf, s->xi[6 * p + d], tn1) - orc_xM(cf, s->xi[6 * p + d], tn);
+          s->x[3 * p + d] = orc_wrap(s->x[3 * p + d] + (cf->dt * (vh[3 * p + d] - vm) + dxm));
+        } else {
+          double xm = orc_xM(cf, s->xi[6 * p + d], th);
+          double xmd = orc_xMdot(cf, xm, th);
+          s->x[3 * p + d] = orc_wrap(s->x[3 * p + d] + cf->dt * (vh[3 * p + d] + xmd - vm));
+        }
       }
     }
     /* field at t^{n+1} from x^{n+1}                                       */
@@ -810,7 +904,10 @@ void orc_get_stats(const orc_state* s, int64_t out[6], double* cg_res) {
   out[4] = s->cg_iters; out[5] = s->step;
   if (cg_res) *cg_res = s->cg_res;
 }
-void orc_reset_stats(orc_state* s) { s->n_cand = s->n_coll = s->n_gmax = s->n_tie = 0; }
+void orc_reset_stats(orc_state* s) {
+  s->n_cand = s->n_coll = s->n_gmax = s->n_tie = 0;
+  s->n_ang = 0;
+}
 void orc_set_phi(orc_state* s, const double* phi) {
   memcpy(s->phi, phi, (size_t)ncell(&s->c) * sizeof(double));
 }
@@ -818,7 +915,15 @@ void orc_set_phi(orc_state* s, const double* phi) {
  * in place, returns the number of collisions.                            */
 int64_t orc_ntc_cell(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint32_t o, int64_t c,
                      double* v) {
-  orc_dsmc_stats st = {0, 0, 0, 0};
+  orc_dsmc_stats st = {0, 0, 0, 0, NULL};
   ntc_one_outcome(cf, c0, cellk, o, c, v, &st);
   return st.n_coll;
+}
+
+/* Recorded (chi, eps) pairs of every collision since sampling or the last
+ * orc_reset_stats, in the order the oracle ran them.                      */
+int64_t orc_angle_count(const orc_state* s) { return s->n_ang; }
+
+void orc_get_angles(const orc_state* s, double* out) {
+  if (s->n_ang) memcpy(out, s->ang, (size_t)(2 * s->n_ang) * sizeof(double));
 }
