@@ -52,6 +52,36 @@ typedef enum {
 
 enum { PIC_FP64 = 0, PIC_MIXED = 1 };
 
+/* Verification switches of pic_config.verify (bit flags, Sec. 5.4 and 5.1):
+ *  PIC_VERIFY_ISOLATE  isolated-collision mode: the drift moves x by the
+ *                      exact manufactured increment x^M(t_{n+1}) - x^M(t_n)
+ *                      instead of dt xdot^M(t_{n+1/2}); with q/m = 0
+ *                      (couple_qm_zero) the particle error is then the
+ *                      collision error alone. v^M does not depend on t, so
+ *                      the kicks' vdot^M terms are zero in both modes.
+ *  PIC_VERIFY_ERROR1   injected coding error 1: v_cm = (v_p - v_q)/2.
+ *  PIC_VERIFY_ERROR2   injected coding error 2: an accepted pair swaps its
+ *                      velocities with probability 1/2 (the coin is the
+ *                      chi draw, U < 1/2) or keeps them. Exclusive with 1.
+ *  PIC_VERIFY_ANGLES   record the scattering angles of every collision for
+ *                      pic_get_angle_stats (Sec. 4.4).
+ *  PIC_VERIFY_ANISO    manufactured anisotropic scattering (Sec. 5.1):
+ *                      p_chi = (29/2 + 12 cos chi - 20 cos^3 chi) sin chi
+ *                      / 29, drawn by the closed-form quartic inverse; its
+ *                      mean cos chi is 0, so the hard-sphere source term
+ *                      is unchanged.
+ * Only single contexts accept them (pic_create_batch rejects any bit). */
+enum {
+  PIC_VERIFY_ISOLATE = 1,
+  PIC_VERIFY_ERROR1 = 2,
+  PIC_VERIFY_ERROR2 = 4,
+  PIC_VERIFY_ANGLES = 8,
+  PIC_VERIFY_ANISO = 16
+};
+
+/* Bins per angle of the recorded-angle histograms. */
+#define PIC_ANGLE_BINS 4194304
+
 /* Problem statement (unit cube [0,1)^3, periodic). Field meanings:
  *  n             cells = nodes per axis (2 .. 1024); cell (i,j,k) spans
  *                [i h,(i+1) h) x ...; node (i,j,k) sits at (i h, j h, k h).
@@ -81,7 +111,8 @@ enum { PIC_FP64 = 0, PIC_MIXED = 1 };
  *  max_ppc       most particles one cell may hold during collisions (working
  *                set of the collision kernel); 0 selects 512.
  *  seed          Philox4x32-10 key (low word, high word).
- *  cg_tol, cg_maxit  CG stops at ||r||_2 <= cg_tol ||b||_2 or cg_maxit. */
+ *  cg_tol, cg_maxit  CG stops at ||r||_2 <= cg_tol ||b||_2 or cg_maxit.
+ *  verify        PIC_VERIFY_* bit flags (0: the method as stated). */
 typedef struct {
   int32_t n;
   int32_t K;
@@ -100,7 +131,7 @@ typedef struct {
   uint64_t seed;
   double cg_tol;
   int32_t cg_maxit;
-  int32_t reserved;
+  int32_t verify;
 } pic_config;
 
 /* Error norms of Sec. 4.3 at the context's current time: index 0..5 =
@@ -126,6 +157,24 @@ typedef struct {
   int32_t tuned_kick_block; /* block size the batch autotuner chose (0: none) */
   int32_t reserved;
 } pic_stats;
+
+/* Scattering-angle CDF errors of Sec. 4.4 over every collision recorded
+ * since sampling or pic_reset_stats (PIC_VERIFY_ANGLES): for alpha in
+ * {chi, eps}, e_r = F_emp(alpha_r) - F^M(alpha_r), eps_2 = sqrt(mean e^2),
+ * eps_inf = max |e|. chi = acos(g'_z / g) with the pre-collision g and
+ * eps = atan2(g'_y, g'_x) in [0, 2 pi) (Eq. angle_recovery); F^M is the
+ * isotropic or the manufactured anisotropic CDF (Eqs. Fp_chi, Fp_eps).
+ * The device keeps u = F^M(alpha) in PIC_ANGLE_BINS equal bins and puts each
+ * sample at its bin's centre with its rank inside the bin, so each e_r is
+ * within 1/(2 PIC_ANGLE_BINS) of the exact value of a sample that fell in
+ * that bin; max_bin is the largest bin count (ties inside a bin can move
+ * the exact empirical CDF by up to max_bin / n_coll). */
+typedef struct {
+  int64_t n_coll;         /* recorded collisions N_coll                      */
+  int64_t max_bin[2];     /* largest bin count, chi and eps                  */
+  double eps2_chi, epsinf_chi;
+  double eps2_eps, epsinf_eps;
+} pic_angle_stats;
 
 /* Optional device allocator (e.g. a framework's caching allocator). Both
  * callbacks are called on the creating thread; alloc returns NULL on
@@ -214,7 +263,13 @@ pic_status pic_get_sort(pic_ctx* ctx, int32_t* cell_of_pid, int32_t* count, int3
                         int32_t* perm);
 
 pic_status pic_get_stats(pic_ctx* ctx, pic_stats* out);
+/* Zero the counters of pic_stats and the recorded scattering angles. */
 pic_status pic_reset_stats(pic_ctx* ctx);
+
+/* Angle CDF errors (pic_angle_stats) of the recorded collisions; computed by
+ * kernels on the context stream, then synchronised. PIC_ESTATE when the
+ * context was created without PIC_VERIFY_ANGLES. */
+pic_status pic_get_angle_stats(pic_ctx* ctx, pic_angle_stats* out);
 
 /* Per-kernel CUDA-event timing on the context stream (off by default).
  * Turning it on or off clears the accumulated times. */

@@ -45,6 +45,7 @@ def make_config(p: dict) -> PicConfig:
     c.precision = int(p.get("precision", 0))
     c.seed = int(p.get("seed", 0))
     c.cg_maxit = int(p.get("cg_maxit", c.cg_maxit))
+    c.verify = int(p.get("verify", 0))
     return c
 
 
@@ -186,6 +187,14 @@ class Pic:
 
     def reset_stats(self):
         check(self.L.pic_reset_stats(self.ctx), "pic_reset_stats")
+
+    def angle_stats(self) -> dict:
+        """Scattering-angle CDF errors of the recorded collisions (needs
+        ``verify`` with PIC_VERIFY_ANGLES)."""
+        a = _lib.PicAngleStats()
+        check(self.L.pic_get_angle_stats(self.ctx, ctypes.byref(a)), "pic_get_angle_stats")
+        return {"n_coll": a.n_coll, "max_bin": (a.max_bin[0], a.max_bin[1]), "eps2_chi": a.eps2_chi,
+                "epsinf_chi": a.epsinf_chi, "eps2_eps": a.eps2_eps, "epsinf_eps": a.epsinf_eps}
 
     def set_profiling(self, on: bool):
         check(self.L.pic_set_profiling(self.ctx, 1 if on else 0), "pic_set_profiling")

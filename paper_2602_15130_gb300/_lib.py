@@ -20,6 +20,10 @@ STATUS = {
 }
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENOCONV, PIC_ETIMEOUT, PIC_ESTATE, PIC_ECAPACITY = range(8)
 PIC_FP64 = 0
+PIC_MIXED = 1
+# verification switches (pic_config.verify bits)
+PIC_VERIFY_ISOLATE, PIC_VERIFY_ERROR1, PIC_VERIFY_ERROR2, PIC_VERIFY_ANGLES, PIC_VERIFY_ANISO = 1, 2, 4, 8, 16
+PIC_ANGLE_BINS = 4194304
 NUM_KERNEL_CLASSES = 9
 KERNEL_CLASSES = ["sample", "sort", "sort_gather_deposit", "rhs", "cg_efield", "dsmc", "kick_drift",
                   "error_norms", "other"]
@@ -51,7 +55,7 @@ class PicConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("cg_tol", ctypes.c_double),
         ("cg_maxit", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("verify", ctypes.c_int32),
     ]
 
 
@@ -85,6 +89,17 @@ class PicAllocator(ctypes.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
 
 
+class PicAngleStats(ctypes.Structure):
+    _fields_ = [
+        ("n_coll", ctypes.c_int64),
+        ("max_bin", ctypes.c_int64 * 2),
+        ("eps2_chi", ctypes.c_double),
+        ("epsinf_chi", ctypes.c_double),
+        ("eps2_eps", ctypes.c_double),
+        ("epsinf_eps", ctypes.c_double),
+    ]
+
+
 class PicKernelTimes(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * NUM_KERNEL_CLASSES), ("launches", ctypes.c_int64 * NUM_KERNEL_CLASSES)]
 
@@ -107,6 +122,7 @@ SIGNATURES = {
     "pic_get_sort": (_S, [_V, _V, _V, _V, _V]),
     "pic_get_stats": (_S, [_V, ctypes.POINTER(PicStats)]),
     "pic_reset_stats": (_S, [_V]),
+    "pic_get_angle_stats": (_S, [_V, ctypes.POINTER(PicAngleStats)]),
     "pic_set_profiling": (_S, [_V, ctypes.c_int32]),
     "pic_get_kernel_times": (_S, [_V, ctypes.POINTER(PicKernelTimes)]),
     "pic_destroy": (None, [_V]),

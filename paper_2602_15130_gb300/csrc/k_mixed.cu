@@ -117,6 +117,7 @@ struct Gather32Args {
   uint32_t* pid_out;
   int32_t* cell_out;
   double* corner;       // [8][ncell]
+  int big_lo;             // cells above this count go to the block sort
 };
 
 constexpr int kGatherThreads = 256;
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
   for (int64_t cell = gw; cell < a.ncell; cell += nw) {
     const int32_t s = a.start[cell];
     const int32_t cnt = a.start[cell + 1] - s;
+    if (cnt > a.big_lo && cnt <= kMaxBlockSort) continue;  // k_sort_big32
     if (cnt <= 64) {
       // both 32-element chunks held in registers, ranked in one pass
       int32_t src0 = 0, src1 = 0;
@@ -213,6 +215,74 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
   }
 }
 
+// Cells of kBigCell < count <= kMaxBlockSort particles: one block per cell,
+// shared-memory bitonic sort by pid, double-float CIC partials reduced in a
+// fixed block order.
+constexpr int kBigThreads = 512;
+
+__global__ void __launch_bounds__(kBigThreads) k_sort_big32(Gather32Args a) {
+  extern __shared__ uint32_t shm[];
+  uint32_t* key = shm;
+  int32_t* val = reinterpret_cast<int32_t*>(shm + kMaxBlockSort);
+  __shared__ double red[kBigThreads / 32][8];
+  for (int64_t cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
+    const int32_t s = a.start[cell];
+    const int32_t cnt = a.start[cell + 1] - s;
+    if (cnt <= a.big_lo || cnt > kMaxBlockSort) continue;  // uniform per block
+    int np2 = 1;
+    while (np2 < cnt) np2 <<= 1;
+    for (int e = threadIdx.x; e < np2; e += blockDim.x) {
+      if (e < cnt) {
+        const int32_t src = a.perm[s + e];
+        key[e] = a.pid_in[src];
+        val[e] = src;
+      } else {
+        key[e] = 0xFFFFFFFFu;
+        val[e] = -1;
+      }
+    }
+    __syncthreads();
+    block_bitonic_sort(key, val, np2);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int32_t src = val[e], dst = s + e;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src];
+      a.pid_out[dst] = key[e];
+      a.cell_out[dst] = (int32_t)cell;
+    }
+    __syncthreads();
+    DF acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = DF{0.f, 0.f};
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const float ox = a.out[0][s + e], oy = a.out[1][s + e], oz = a.out[2][s + e];
+      const float wx[2] = {1.f - ox, ox}, wy[2] = {1.f - oy, oy}, wz[2] = {1.f - oz, oz};
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const float wyz = wy[b] * wz[c];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) acc[q + 2 * b + 4 * c] = df_fma(acc[q + 2 * b + 4 * c], wx[q], wyz);
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[q] = df_add(acc[q], df_shfl_xor(acc[q], off));
+      if (lane == 0) red[w][q] = df_to_double(acc[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
+      a.corner[(int64_t)threadIdx.x * a.ncell + cell] = t;
+    }
+    __syncthreads();
+  }
+}
+
 // ----------------------------------------------------------- collisions --
 struct Dsmc32Args {
   ParamsF P;
@@ -241,6 +311,7 @@ __device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const floa
   }
 }
 
+template <bool kVerify>
 __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
                               const float* v1, const float* v2, uint32_t* bm, float* ov, Counts32& cnt) {
   const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
@@ -280,19 +351,36 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
     if (g2 > P.gmax2) ++cnt.gmax;
     if (fabsf(ug2 - g2) < 2e-6f * g2) ++cnt.tie;
     if (ug2 < g2) {
-      float se, ce;
-      sincospif(2.f * unif24(b0.w), &se, &ce);
-      const float cchi = 1.f - 2.f * unif24(b1.x);
-      const float schi = sqrtf(fmaxf(0.f, 1.f - cchi * cchi));
       const float g = sqrtf(g2);
-      const float nv[3] = {ce * schi, se * schi, cchi};
+      if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
+        // injected Error 2: swap with probability 1/2 (coin = chi draw)
+        const bool swap = unif24(b1.x) < 0.5f;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float cm = 0.5f * (vp[d] + vq[d]);
-        const float hg = 0.5f * g * nv[d];
-        ov[3 * p + d] = cm + hg;
-        ov[3 * q + d] = cm - hg;
+        for (int d = 0; d < 3; ++d) {
+          ov[3 * p + d] = swap ? vq[d] : vp[d];
+          ov[3 * q + d] = swap ? vp[d] : vq[d];
+        }
+      } else {
+        float se, ce;
+        sincospif(2.f * unif24(b0.w), &se, &ce);
+        float uchi = unif24(b1.x);
+        if (kVerify && (P.verify & PIC_VERIFY_ANISO)) uchi = aniso_u_f(uchi);
+        const float cchi = 1.f - 2.f * uchi;
+        const float schi = sqrtf(fmaxf(0.f, 1.f - cchi * cchi));
+        const float nv[3] = {ce * schi, se * schi, cchi};
+        const bool err1 = kVerify && (P.verify & PIC_VERIFY_ERROR1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          // Eq. v_cm; injected Error 1 flips the sign of v_q
+          const float cm = 0.5f * (err1 ? vp[d] - vq[d] : vp[d] + vq[d]);
+          const float hg = 0.5f * g * nv[d];
+          ov[3 * p + d] = cm + hg;
+          ov[3 * q + d] = cm - hg;
+        }
       }
+      if (kVerify && P.ang_hist)
+        record_angles_f(P.ang_hist, (P.verify & PIC_VERIFY_ANISO) != 0, g, ov[3 * p] - ov[3 * q],
+                        ov[3 * p + 1] - ov[3 * q + 1], ov[3 * p + 2] - ov[3 * q + 2]);
       bm[p >> 5] |= 1u << (p & 31);
       bm[q >> 5] |= 1u << (q & 31);
       ++cnt.coll;
@@ -302,6 +390,7 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
 
 constexpr int kDsmcThreads = 128;
 
+template <bool kVerify>
 __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
   extern __shared__ uint32_t smem[];
   const ParamsF& P = a.P;
@@ -340,8 +429,8 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
         run = false;
       }
       if (run)
-        ntc_outcome_f(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s, bm, ov,
-                      cnt);
+        ntc_outcome_f<kVerify>(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s,
+                               bm, ov, cnt);
       __syncwarp();
       // per cell of the group and per 32-particle word: transpose the
       // lanes' bitmap words with ballots, so lane b learns which outcomes
@@ -427,10 +516,14 @@ struct Kick32Args {
   float *L0, *L1, *L2;
   int lor_mode;  // 0: compute, 1: compute and store, 2: load
   TimeTermsF tE, th;
+  TimeTermsF t0, t1;  // t_n, t_{n+1} for the isolated-collision drift
   int drift;
   int32_t *key, *rank, *count;
 };
 
+// kIsolate: the isolated-collision drift of Sec. 5.4 (kept out of the
+// plain kernel, whose register budget it would raise)
+template <bool kIsolate>
 __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const ParamsF& P = a.P;
@@ -494,9 +587,16 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   float* op[3] = {a.o0, a.o1, a.o2};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float s = xm_sin_f(P, a.th, xi[d]);
-    const float xd = P.fx_Ac * (s + a.th.sin2ct) / (1.f + P.fx_amp * s);
-    float on = fmaf(P.dtn, v[d] + xd - vm[d], o[d]);
+    float on;
+    if (kIsolate) {
+      // exact manufactured increment y(t_{n+1}) - y(t_n) + c dt (Sec. 5.4)
+      const float dy = xm_y_f(P, a.t1, xi[d]) - xm_y_f(P, a.t0, xi[d]);
+      on = fmaf(P.dtn, v[d] - vm[d], o[d]) + P.nf * (dy + P.cdt);
+    } else {
+      const float s = xm_sin_f(P, a.th, xi[d]);
+      const float xd = P.fx_Ac * (s + a.th.sin2ct) / (1.f + P.fx_amp * s);
+      on = fmaf(P.dtn, v[d] + xd - vm[d], o[d]);
+    }
     const float fl = floorf(on);
     on -= fl;
     int shift = (int)fl;
@@ -881,19 +981,27 @@ cudaError_t launch_gather32(pic_ctx* c) {
   g.pid_out = c->pid[o];
   g.cell_out = c->cell32[o];
   g.corner = c->corner;
+  g.big_lo = big_cell_threshold(g.ncell, c->P.np);
   int64_t blocks = (c->P.ncell * 32 + kGatherThreads - 1) / kGatherThreads;
   const int64_t cap = (int64_t)c->num_sms * 16;
   if (blocks > cap) blocks = cap;
   prof_begin(c);
   k_sort_gather32<<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
+  if (g.big_lo < INT_MAX) {
+    k_sort_big32<<<2 * c->num_sms, kBigThreads, (size_t)kMaxBlockSort * 8, c->stream>>>(g);
+    c->launches++;
+  }
   prof_end(c, KC_GATHER);
   c->launches++;
   c->cur = o;
   return cudaGetLastError();
 }
 
+const void* sort_big32_kernel_ptr() { return (const void*)k_sort_big32; }
 int dsmc32_threads() { return kDsmcThreads; }
-const void* dsmc32_kernel_ptr() { return (const void*)k_dsmc32; }
+const void* dsmc32_kernel_ptr(bool verify) {
+  return verify ? (const void*)k_dsmc32<true> : (const void*)k_dsmc32<false>;
+}
 int cg32_threads() { return kThreads; }
 const void* cg32_kernel_ptr() { return (const void*)k_cg32; }
 
@@ -917,13 +1025,16 @@ cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate) {
   a.counters = c->counters;
   a.flags = c->flags;
   prof_begin(c);
-  k_dsmc32<<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
+  if (c->P.verify)
+    k_dsmc32<true><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
+  else
+    k_dsmc32<false><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
   prof_end(c, KC_DSMC);
   c->launches++;
   return cudaGetLastError();
 }
 
-cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, double th) {
+cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, double th, double tn1) {
   Kick32Args a;
   a.P = params_f(c->P);
   const int b = c->cur;
@@ -939,12 +1050,17 @@ cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, dou
   a.lor_mode = drift ? (c->lor_valid ? 2 : 0) : 1;
   a.tE = to_float(time_terms(c->P, tE));
   a.th = to_float(time_terms(c->P, th));
+  a.t0 = to_float(time_terms(c->P, tE));
+  a.t1 = to_float(time_terms(c->P, tn1));
   a.drift = drift ? 1 : 0;
   a.key = c->key;
   a.rank = c->rank;
   a.count = c->count;
   prof_begin(c);
-  k_kick32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  if (c->P.verify & PIC_VERIFY_ISOLATE)
+    k_kick32<true><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  else
+    k_kick32<false><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
   prof_end(c, KC_KICK);
   c->launches++;
   c->lor_valid = !drift;
@@ -1144,6 +1260,10 @@ ParamsF params_f(const Params& P) {
   for (int j = 0; j < 5; ++j) f.R_series[j] = (float)P.R_series[j];
   f.ginv_f = P.ginv_f;
   f.ginv_M = P.ginv_M;
+  f.verify = P.verify;
+  f.nf = (float)P.n;
+  f.cdt = (float)(P.fx_speed * P.dt);
+  f.ang_hist = P.ang_hist;
   return f;
 }
 }  // namespace pic

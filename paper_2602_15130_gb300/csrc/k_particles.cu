@@ -142,6 +142,9 @@ __device__ __forceinline__ void load_vel(int p, const uint32_t* bm, const double
   }
 }
 
+// kVerify: the verification switches of Sec. 5.4 (injected Errors 1 and 2,
+// manufactured anisotropy, angle recording) are compiled in.
+template <bool kVerify>
 __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_t o, int c,
                             const double* v0, const double* v1, const double* v2, uint32_t* bm,
                             double* ov, LaneCounts& cnt) {
@@ -183,19 +186,36 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
     if (fabs(U - ratio) < 1e-12) ++cnt.tie;
     if (U < ratio) {
       if (!have_b1) b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
-      const double eps = __dmul_rn(kTwoPi, unif32(b0.w));
-      double se, ce;
-      sincos(eps, &se, &ce);
-      const double cchi = __dsub_rn(1.0, __dmul_rn(2.0, unif32(b1.x)));
-      const double schi = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(cchi, cchi)));
-      const double nv[3] = {__dmul_rn(ce, schi), __dmul_rn(se, schi), cchi};
+      if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
+        // injected Error 2: swap with probability 1/2 (coin = chi draw)
+        const bool swap = unif32(b1.x) < 0.5;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const double gp = __dmul_rn(g, nv[d]);
-        const double cm = __dmul_rn(__dadd_rn(vp[d], vq[d]), 0.5);
-        ov[3 * p + d] = __dadd_rn(cm, __dmul_rn(gp, 0.5));
-        ov[3 * q + d] = __dsub_rn(cm, __dmul_rn(gp, 0.5));
+        for (int d = 0; d < 3; ++d) {
+          ov[3 * p + d] = swap ? vq[d] : vp[d];
+          ov[3 * q + d] = swap ? vp[d] : vq[d];
+        }
+      } else {
+        const double eps = __dmul_rn(kTwoPi, unif32(b0.w));
+        double se, ce;
+        sincos(eps, &se, &ce);
+        double uchi = unif32(b1.x);
+        if (kVerify && (P.verify & PIC_VERIFY_ANISO)) uchi = aniso_u(uchi);
+        const double cchi = __dsub_rn(1.0, __dmul_rn(2.0, uchi));
+        const double schi = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(cchi, cchi)));
+        const double nv[3] = {__dmul_rn(ce, schi), __dmul_rn(se, schi), cchi};
+        const bool err1 = kVerify && (P.verify & PIC_VERIFY_ERROR1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const double gp = __dmul_rn(g, nv[d]);
+          // Eq. v_cm; injected Error 1 flips the sign of v_q
+          const double cm = __dmul_rn(err1 ? __dsub_rn(vp[d], vq[d]) : __dadd_rn(vp[d], vq[d]), 0.5);
+          ov[3 * p + d] = __dadd_rn(cm, __dmul_rn(gp, 0.5));
+          ov[3 * q + d] = __dsub_rn(cm, __dmul_rn(gp, 0.5));
+        }
       }
+      if (kVerify && P.ang_hist)
+        record_angles(P.ang_hist, (P.verify & PIC_VERIFY_ANISO) != 0, g, __dsub_rn(ov[3 * p], ov[3 * q]),
+                      __dsub_rn(ov[3 * p + 1], ov[3 * q + 1]), __dsub_rn(ov[3 * p + 2], ov[3 * q + 2]));
       bm[p >> 5] |= 1u << (p & 31);
       bm[q >> 5] |= 1u << (q & 31);
       ++cnt.coll;
@@ -205,6 +225,7 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
 
 constexpr int kDsmcThreads = 128;
 
+template <bool kVerify>
 __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
   extern __shared__ uint32_t smem[];
   const Params& P = a.P;
@@ -240,8 +261,8 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
         run = false;
       }
       if (run)
-        ntc_outcome(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s, bm,
-                    ov, cnt);
+        ntc_outcome<kVerify>(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s,
+                             bm, ov, cnt);
       __syncwarp();
       // sum this chunk's changes per particle in ascending outcome order
       const bool last = ch == a.nchunks - 1;
@@ -318,6 +339,7 @@ struct KickArgs {
   double *L0, *L1, *L2;  // Lorentz term dt q/m (E_p - E^M_p)
   int lor_mode;          // 0: compute, 1: compute and store, 2: load
   TimeTerms tE, th;
+  TimeTerms t0, t1;      // t_n, t_{n+1} for the isolated-collision drift
   int drift;
   int32_t *key, *rank, *count;
 };
@@ -379,9 +401,15 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double s;
-    xm_solve(P, a.th, xi[d], &s);
-    const double xd = xm_dot(P, a.th, s);
-    x[d] = wrap_unit(x[d] + P.dt * (v[d] + xd - vm[d]));
+    if (P.verify & PIC_VERIFY_ISOLATE) {
+      // exact manufactured increment x^M(t_{n+1}) - x^M(t_n) (Sec. 5.4)
+      const double dxm = xm_solve(P, a.t1, xi[d], &s) - xm_solve(P, a.t0, xi[d], &s);
+      x[d] = wrap_unit(x[d] + (P.dt * (v[d] - vm[d]) + dxm));
+    } else {
+      xm_solve(P, a.th, xi[d], &s);
+      const double xd = xm_dot(P, a.th, s);
+      x[d] = wrap_unit(x[d] + P.dt * (v[d] + xd - vm[d]));
+    }
   }
   a.x0[j] = x[0]; a.x1[j] = x[1]; a.x2[j] = x[2];
   const int n = P.n;
@@ -591,16 +619,21 @@ cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate) {
   a.counters = c->counters;
   a.flags = c->flags;
   prof_begin(c);
-  k_dsmc<<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
+  if (c->P.verify)
+    k_dsmc<true><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
+  else
+    k_dsmc<false><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
   prof_end(c, KC_DSMC);
   c->launches++;
   return cudaGetLastError();
 }
 
 int dsmc_threads() { return kDsmcThreads; }
-const void* dsmc_kernel_ptr() { return (const void*)k_dsmc; }
+const void* dsmc_kernel_ptr(bool verify) {
+  return verify ? (const void*)k_dsmc<true> : (const void*)k_dsmc<false>;
+}
 
-cudaError_t launch_kick(pic_ctx* c, double tE, bool with_coll, bool drift, double th) {
+cudaError_t launch_kick(pic_ctx* c, double tE, bool with_coll, bool drift, double th, double tn1) {
   KickArgs a;
   a.P = c->P;
   const int b = c->cur;
@@ -617,6 +650,8 @@ cudaError_t launch_kick(pic_ctx* c, double tE, bool with_coll, bool drift, doubl
   a.lor_mode = drift ? (c->lor_valid ? 2 : 0) : 1;
   a.tE = time_terms(c->P, tE);
   a.th = time_terms(c->P, th);
+  a.t0 = time_terms(c->P, tE);
+  a.t1 = time_terms(c->P, tn1);
   a.drift = drift ? 1 : 0;
   a.key = c->key;
   a.rank = c->rank;

@@ -140,6 +140,7 @@ struct GatherArgs {
   const uint32_t* pid_in;
   uint32_t* pid_out;
   double* corner;         // [8][ncell]
+  int big_lo;             // cells above this count go to the block sort
 };
 
 __device__ __forceinline__ void move_particle(const GatherArgs& a, int32_t src, int32_t dst) {
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather(GatherArgs a) {
   for (int64_t cell = gw; cell < a.ncell; cell += nw) {
     const int32_t s = a.start[cell];
     const int32_t cnt = a.start[cell + 1] - s;
+    if (cnt > a.big_lo && cnt <= kMaxBlockSort) continue;  // k_sort_big
     const int ci = (int)(cell % n), cj = (int)((cell / n) % n), ck = (int)(cell / ((int64_t)n * n));
     double acc[8];
 #pragma unroll
@@ -243,7 +245,63 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather(GatherArgs a) {
   }
 }
 
+// Cells of kBigCell < count <= kMaxBlockSort particles: one block per cell,
+// (pid, source) pairs sorted in shared memory, particles moved in pid order,
+// CIC corner partials summed with a fixed-shape block reduction.
+constexpr int kBigThreads = 512;
+
+__global__ void __launch_bounds__(kBigThreads) k_sort_big(GatherArgs a) {
+  extern __shared__ uint32_t shm[];
+  uint32_t* key = shm;
+  int32_t* val = reinterpret_cast<int32_t*>(shm + kMaxBlockSort);
+  __shared__ double red[kBigThreads / 32][8];
+  const int n = a.n;
+  for (int64_t cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
+    const int32_t s = a.start[cell];
+    const int32_t cnt = a.start[cell + 1] - s;
+    if (cnt <= a.big_lo || cnt > kMaxBlockSort) continue;  // uniform per block
+    int np2 = 1;
+    while (np2 < cnt) np2 <<= 1;
+    for (int e = threadIdx.x; e < np2; e += blockDim.x) {
+      if (e < cnt) {
+        const int32_t src = a.perm[s + e];
+        key[e] = a.pid_in[src];
+        val[e] = src;
+      } else {
+        key[e] = 0xFFFFFFFFu;
+        val[e] = -1;
+      }
+    }
+    __syncthreads();
+    block_bitonic_sort(key, val, np2);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) move_particle(a, val[e], s + e);
+    __syncthreads();
+    const int ci = (int)(cell % n), cj = (int)((cell / n) % n), ck = (int)(cell / ((int64_t)n * n));
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) add_cic(a, s + e, ci, cj, ck, acc);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+      if (lane == 0) red[w][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
+      a.corner[(int64_t)threadIdx.x * a.ncell + cell] = t;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+size_t big_sort_smem() { return (size_t)kMaxBlockSort * 8; }
+const void* sort_big_kernel_ptr() { return (const void*)k_sort_big; }
 
 cudaError_t launch_keys(pic_ctx* c) {
   KeysArgs a;
@@ -300,12 +358,17 @@ cudaError_t launch_sort(pic_ctx* c) {
   g.pid_in = c->pid[b];
   g.pid_out = c->pid[o];
   g.corner = c->corner;
+  g.big_lo = big_cell_threshold(m, c->P.np);
   const int64_t warps = m;
   int64_t blocks = (warps * 32 + kGatherThreads - 1) / kGatherThreads;
   const int64_t cap = (int64_t)c->num_sms * 16;
   if (blocks > cap) blocks = cap;
   prof_begin(c);
   k_sort_gather<<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
+  if (g.big_lo < INT_MAX) {
+    k_sort_big<<<2 * c->num_sms, kBigThreads, big_sort_smem(), c->stream>>>(g);
+    c->launches++;
+  }
   prof_end(c, KC_GATHER);
   c->launches++;
   c->cur = o;

@@ -81,6 +81,38 @@ __device__ __forceinline__ float xm_sin_f(const ParamsF& P, const TimeTermsF& tt
   return s - 6.283185307f * c * dy;
 }
 
+// y = x^M - c t in FP32 (G^{-1} from the Hermite table, one Newton step):
+// the isolated-collision drift moves by y(t_{n+1}) - y(t_n) + c dt.
+__device__ __forceinline__ float xm_y_f(const ParamsF& P, const TimeTermsF& tt, float xi) {
+  const float T = xi - tt.ct - P.fx_a2pi * tt.cos2ct;
+  const float fl = floorf(T);
+  const float t = (T - fl) * (float)P.ginv_M;
+  int k = (int)t;
+  k = k >= P.ginv_M ? P.ginv_M - 1 : k;
+  const float u = t - (float)k, u2 = u * u, u3 = u2 * u, h = 1.f / (float)P.ginv_M;
+  const float2 q0 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k);
+  const float2 q1 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k + 1);
+  const float y = fl + (2.f * u3 - 3.f * u2 + 1.f) * q0.x + (u3 - 2.f * u2 + u) * h * q0.y +
+                  (3.f * u2 - 2.f * u3) * q1.x + (u3 - u2) * h * q1.y;
+  float s, c;
+  sincospif(2.f * y, &s, &c);
+  return y - (y - P.fx_a2pi * c - T) / (1.f + P.fx_amp * s);
+}
+
+// FP32 form of record_angles (Sec. 4.4)
+__device__ __forceinline__ void record_angles_f(unsigned long long* hist, bool aniso, float g, float gx, float gy,
+                                                float gz) {
+  const float cz = fminf(1.f, fmaxf(-1.f, gz / g));
+  const float u = 0.5f * (1.f - cz);
+  const float uc = aniso ? u * (13.f + u * (96.f + u * (-160.f + 80.f * u))) * (1.f / 29.f) : u;
+  float e = atan2f(gy, gx);
+  if (e < 0.f) e += 6.283185307f;
+  const int bc = min(PIC_ANGLE_BINS - 1, max(0, (int)(uc * (float)PIC_ANGLE_BINS)));
+  const int be = min(PIC_ANGLE_BINS - 1, max(0, (int)(e * (0.1591549431f * (float)PIC_ANGLE_BINS))));
+  atomicAdd(hist + bc, 1ull);
+  atomicAdd(hist + PIC_ANGLE_BINS + be, 1ull);
+}
+
 __device__ __forceinline__ float hs_R_f(const ParamsF& P, float a) {
   const float a2 = a * a;
   if (a < 0.1f) {

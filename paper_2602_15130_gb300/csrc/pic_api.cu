@@ -11,16 +11,27 @@
 
 namespace pic {
 int dsmc_threads();
-const void* dsmc_kernel_ptr();
+const void* dsmc_kernel_ptr(bool verify);
 int cg_threads();
 const void* cg_kernel_ptr();
 int64_t scan_blocks_needed(int64_t ncell);
 int rhs_blocks_needed(int64_t ncell);
 int err_blocks_needed(int64_t np, int64_t ncell);
 int dsmc32_threads();
-const void* dsmc32_kernel_ptr();
+const void* dsmc32_kernel_ptr(bool verify);
 int batch_dsmc_threads();
 const void* batch_dsmc_kernel_ptr();
+const void* sort_big_kernel_ptr();
+const void* sort_big32_kernel_ptr();
+
+// the big-cell sorts keep kMaxBlockSort (pid, source) pairs in shared memory
+cudaError_t allow_big_sort_smem() {
+  const int bytes = kMaxBlockSort * 8;
+  cudaError_t e = cudaFuncSetAttribute(sort_big_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sort_big32_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
 int cg32_threads();
 const void* cg32_kernel_ptr();
 
@@ -145,6 +156,8 @@ void derive_params(const pic_config& c, Params& P) {
   P.rho_scale = P.q_eff * P.w / P.dV;
   P.src_pref = P.w * c.dt * c.sigma0 / (2.0 * P.dV);
   series_coefficients(P.R_series);
+  P.verify = c.verify;
+  P.ang_hist = nullptr;
 }
 
 pic_status cuda_status(cudaError_t e) {
@@ -243,6 +256,12 @@ void for_each_buffer(pic_ctx* c, F f) {
   f((void**)&c->err_out, 14 * 8);
   f((void**)&c->ginv, (size_t)(kGinvM + 1) * 2 * 8);
   f((void**)&c->ginv_f, (size_t)(kGinvM + 1) * 2 * 4);
+  if (c->nrep == 0 && (c->cfg.verify & PIC_VERIFY_ANGLES)) {
+    f((void**)&c->ang_hist, (size_t)2 * PIC_ANGLE_BINS * 8);
+    f((void**)&c->ang_bsum, (size_t)4 * kAngleBlocks * 8);
+    f((void**)&c->ang_part, (size_t)4 * kAngleBlocks * 8);
+    f((void**)&c->ang_out, 8 * 8);
+  }
   // host-boundary staging: the largest replicate of a batch, else everything
   size_t stage_np = np;
   if (c->nrep > 0) {
@@ -457,6 +476,8 @@ pic_status pic_validate_config(const pic_config* c) {
   if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return PIC_EINVAL;
   if (c->max_ppc < 0 || c->max_ppc > 65536) return PIC_EINVAL;
   if (!(c->cg_tol > 0.0) || c->cg_maxit < 1) return PIC_EINVAL;
+  if (c->verify & ~31) return PIC_EINVAL;
+  if ((c->verify & PIC_VERIFY_ERROR1) && (c->verify & PIC_VERIFY_ERROR2)) return PIC_EINVAL;
   const int64_t ncell = (int64_t)c->n * c->n * c->n;
   if (ncell > 2147483647LL) return PIC_EINVAL;
   return PIC_OK;
@@ -519,6 +540,7 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   int coop = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+  if (e == cudaSuccess) e = allow_big_sort_smem();
   if (e != cudaSuccess || !coop) {
     cudaGetLastError();
     delete c;
@@ -547,7 +569,7 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   c->dsmc_groups = (c->P.ncell + c->dsmc_G - 1) / c->dsmc_G;
   c->bm_words = c->cfg.max_ppc / 32;
   c->dsmc_block = c->mixed ? dsmc32_threads() : dsmc_threads();
-  const void* dsmc_fn = c->mixed ? dsmc32_kernel_ptr() : dsmc_kernel_ptr();
+  const void* dsmc_fn = c->mixed ? dsmc32_kernel_ptr(c->P.verify != 0) : dsmc_kernel_ptr(c->P.verify != 0);
   c->dsmc_smem = (size_t)(c->dsmc_block / 32) * 32 * c->bm_words * 4;
   if (c->dsmc_smem > 48 * 1024) {
     e = cudaFuncSetAttribute(dsmc_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->dsmc_smem);
@@ -598,7 +620,10 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
     c->P.ginv = c->ginv;
     c->P.ginv_f = c->ginv_f;
     c->P.ginv_M = kGinvM;
+    c->P.ang_hist = c->ang_hist;
   }
+  if (e == cudaSuccess && c->ang_hist)
+    e = cudaMemsetAsync(c->ang_hist, 0, (size_t)2 * PIC_ANGLE_BINS * 8, c->stream);
   if (e == cudaSuccess)
     e = c->mixed ? cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream)
                  : cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream);
@@ -638,6 +663,7 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
     c->sampled = true;
     return check_pending(c);
   }
+  if (c->ang_hist) CK(cudaMemsetAsync(c->ang_hist, 0, (size_t)2 * PIC_ANGLE_BINS * 8, c->stream));
   if (c->mixed) {
     CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
     CK(launch_sample32(c, t0, nullptr));
@@ -681,25 +707,25 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     } else if (c->mixed) {
       if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n), false));
       CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-      CK(launch_kick32(c, tn, coll, true, th));
+      CK(launch_kick32(c, tn, coll, true, th, tn1));
       CK(launch_scan_scatter(c));
       CK(launch_gather32(c));
       CK(launch_rhs(c, tn1));
       CK(launch_cg32(c));
       if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n + 1), false));
-      CK(launch_kick32(c, tn1, coll, false, 0.0));
+      CK(launch_kick32(c, tn1, coll, false, 0.0, 0.0));
     } else {
       // v^{n+1/2} and x^{n+1}: collision call A at (x^n, v^n)
       if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n), false));
       CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-      CK(launch_kick(c, tn, coll, true, th));
+      CK(launch_kick(c, tn, coll, true, th, tn1));
       // cells of x^{n+1}, field at t^{n+1}
       CK(launch_sort(c));
       CK(launch_rhs(c, tn1));
       CK(launch_cg(c));
       // v^{n+1}: collision call B at (x^{n+1}, v^{n+1/2})
       if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n + 1), false));
-      CK(launch_kick(c, tn1, coll, false, 0.0));
+      CK(launch_kick(c, tn1, coll, false, 0.0, 0.0));
     }
     c->step = n + 1;
   }
@@ -863,9 +889,17 @@ pic_status pic_reset_stats(pic_ctx* c) {
   if (!c) return PIC_EINVAL;
   CK(cudaMemsetAsync(c->counters, 0, 64, c->stream));
   CK(cudaMemsetAsync(c->flags, 0, 64, c->stream));
+  if (c->ang_hist) CK(cudaMemsetAsync(c->ang_hist, 0, (size_t)2 * PIC_ANGLE_BINS * 8, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->launches = 0;
   c->cg_iters_max = 0;
+  return PIC_OK;
+}
+
+pic_status pic_get_angle_stats(pic_ctx* c, pic_angle_stats* out) {
+  if (!c || !out) return PIC_EINVAL;
+  if (!c->ang_hist) return PIC_ESTATE;
+  CK(launch_angle_stats(c, out));
   return PIC_OK;
 }
 
@@ -899,7 +933,7 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   int max_ppc = c0.max_ppc ? c0.max_ppc : 512;
   for (int r = 0; r < nrep; ++r) {
     const pic_config& c = cfgs[r];
-    if (pic_validate_config(&c) != PIC_OK || c.precision != PIC_MIXED) return PIC_EINVAL;
+    if (pic_validate_config(&c) != PIC_OK || c.precision != PIC_MIXED || c.verify != 0) return PIC_EINVAL;
     // everything but n, n_particles, K, dt, sigma0 and seed is shared
     if (c.qm != c0.qm || c.q != c0.q || c.eps0 != c0.eps0 || c.n_phys != c0.n_phys || c.g_max != c0.g_max ||
         c.fx_amp != c0.fx_amp || c.fx_speed != c0.fx_speed || c.v_sigma != c0.v_sigma || c.phi_amp != c0.phi_amp ||
@@ -939,6 +973,7 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   c->P.K = kmax;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = allow_big_sort_smem();
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete c;

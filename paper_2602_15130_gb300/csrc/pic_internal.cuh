@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <climits>
 #include <stdint.h>
 
 #include "../../include/pic.h"
@@ -39,6 +40,8 @@ struct Params {
   const double* ginv;
   const float* ginv_f;
   int ginv_M;
+  int verify;                      // PIC_VERIFY_* bits
+  unsigned long long* ang_hist;    // [2][PIC_ANGLE_BINS] when recording angles
 };
 
 
@@ -58,6 +61,9 @@ struct ParamsF {
   float R_series[5];
   const float* ginv_f;
   int ginv_M;
+  int verify;                      // PIC_VERIFY_* bits
+  float nf, cdt;                   // n, and c dt of the manufactured drift
+  unsigned long long* ang_hist;    // [2][PIC_ANGLE_BINS] when recording angles
 };
 
 // Per-replicate data of a batch (device copy).
@@ -207,6 +213,90 @@ __device__ __forceinline__ void hs_source(const Params& P, double vx, double vy,
   *sz = f * mz;
 }
 
+// Cells above kBigCell particles are ranked by a block-level bitonic sort
+// in shared memory (up to kMaxBlockSort particles); smaller and larger ones
+// by the warp's pairwise count.
+// blocks of the angle-histogram reduction (PIC_ANGLE_BINS / kAngleBlocks
+// bins each)
+constexpr int kAngleBlocks = 1024;
+
+constexpr int kBigCell = 256;
+constexpr int kMaxBlockSort = 16384;
+
+// The block sort is launched only when the mean occupancy is high enough for
+// big cells to be common; otherwise the warp pass takes every cell.
+inline int big_cell_threshold(int64_t ncell, int64_t np) {
+  return (ncell > 0 && np >= 128 * ncell) ? kBigCell : INT_MAX;
+}
+
+// Ascending bitonic sort of n (a power of two) (key, val) pairs in shared
+// memory by the whole block; returns after a __syncthreads.
+__device__ __forceinline__ void block_bitonic_sort(uint32_t* key, int32_t* val, int n) {
+  for (int k = 2; k <= n; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const uint32_t a = key[i], b = key[ixj];
+          if ((a > b) == up) {
+            key[i] = b;
+            key[ixj] = a;
+            const int32_t t = val[i];
+            val[i] = val[ixj];
+            val[ixj] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Manufactured anisotropic scattering (Sec. 5.1): with u = sin^2(chi/2) the
+// CDF of chi is F(u) = (13 u + 96 u^2 - 160 u^3 + 80 u^4)/29; u(xi) is the
+// root of the quartic F(u) = xi in [0, 1] by its closed form (a resolvent
+// cube root, then two square roots).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double aniso_u(double xi) {
+  const double r = sqrt(298924665.0 + 55680.0 * xi * (376377.0 + 2320.0 * xi * (-429.0 + 290.0 * xi)));
+  const double a = cbrt(81909.0 - 83520.0 * xi + r) / 83.20335292207616;  // 40 3^{2/3}
+  const double b = 0.2 + a + (161.0 - 290.0 * xi) / (600.0 * a);
+  const double sb = sqrt(b);
+  const double u = 0.5 * (1.0 - sb + sqrt(0.6 - b + 29.0 / (40.0 * sb)));
+  return u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+}
+__device__ __forceinline__ float aniso_u_f(float xi) {
+  const float r = sqrtf(298924665.f + 55680.f * xi * (376377.f + 2320.f * xi * (-429.f + 290.f * xi)));
+  const float a = cbrtf(81909.f - 83520.f * xi + r) / 83.2033529f;
+  const float b = 0.2f + a + (161.f - 290.f * xi) / (600.f * a);
+  const float sb = sqrtf(b);
+  const float u = 0.5f * (1.f - sb + sqrtf(fmaxf(0.f, 0.6f - b + 29.f / (40.f * sb))));
+  return fminf(fmaxf(u, 0.f), 1.f);
+}
+__host__ __device__ __forceinline__ double aniso_F(double u) {
+  return u * (13.0 + u * (96.0 + u * (-160.0 + 80.0 * u))) / 29.0;
+}
+
+// One recorded collision (Sec. 4.4): u_chi = F^M(chi) with cos chi =
+// g'_z / g (g the pre-collision speed), u_eps = eps / (2 pi) with eps =
+// atan2(g'_y, g'_x) in [0, 2 pi); each goes into its bin of PIC_ANGLE_BINS.
+__device__ __forceinline__ int angle_bin(double u) {
+  int b = (int)(u * (double)PIC_ANGLE_BINS);
+  return b < 0 ? 0 : (b >= PIC_ANGLE_BINS ? PIC_ANGLE_BINS - 1 : b);
+}
+__device__ __forceinline__ void record_angles(unsigned long long* hist, bool aniso, double g, double gx, double gy,
+                                              double gz) {
+  double cz = gz / g;
+  cz = cz > 1.0 ? 1.0 : (cz < -1.0 ? -1.0 : cz);
+  const double u = 0.5 * (1.0 - cz);
+  const double uc = aniso ? aniso_F(u) : u;
+  double e = atan2(gy, gx);
+  if (e < 0.0) e += kTwoPi;
+  atomicAdd(hist + angle_bin(uc), 1ull);
+  atomicAdd(hist + PIC_ANGLE_BINS + angle_bin(e / kTwoPi), 1ull);
+}
+
 __device__ __forceinline__ double wrap_unit(double x) {
   double y = x - floor(x);
   return y >= 1.0 ? 0.0 : y;
@@ -291,6 +381,12 @@ struct pic_ctx {
   int64_t dsmc_groups;
   size_t dsmc_smem;
   unsigned long long* counters;  // n_cand, n_coll, n_gmax, n_tie
+  // recorded scattering angles (PIC_VERIFY_ANGLES): histograms of F^M(chi)
+  // and eps/(2 pi), and the scratch of their CDF-error reduction
+  unsigned long long* ang_hist;  // [2][PIC_ANGLE_BINS]
+  unsigned long long* ang_bsum;  // [2][kAngleBlocks] counts, then [2][kAngleBlocks] maxima
+  double* ang_part;              // [2][kAngleBlocks][2] (sum of e^2, max |e|)
+  double* ang_out;               // [8]
   int* flags;       // sticky: [0] bits 1 capacity, 2 no convergence, 4 timeout; [1] max CG iterations
 
   // error norms
@@ -361,7 +457,7 @@ cudaError_t launch_rhs(pic_ctx* c, double t);
 cudaError_t launch_cg(pic_ctx* c);             // CG + zero-mean + E
 cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate_source);
 // kick at time tE; drift to th if drift. Reuses / refreshes c->lor.
-cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift, double th);
+cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift, double th, double tn1);
 cudaError_t launch_errors(pic_ctx* c, double t);
 TimeTerms time_terms(const Params& P, double t);
 ParamsF params_f(const Params& P);
@@ -384,7 +480,9 @@ cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv_dev);
 cudaError_t launch_keys32(pic_ctx* c);
 cudaError_t launch_gather32(pic_ctx* c);
 cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate_source);
-cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_collisions, bool drift, double th);
+cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_collisions, bool drift, double th, double tn1);
+// angle CDF errors of the recorded collisions into out (synchronises)
+cudaError_t launch_angle_stats(pic_ctx* c, pic_angle_stats* out);
 cudaError_t launch_cg32(pic_ctx* c);
 cudaError_t launch_errors32(pic_ctx* c, double t);
 cudaError_t launch_store_state32(pic_ctx* c, double* xv_dev, int32_t* cell_of_pid);

@@ -68,6 +68,41 @@ def refinement_level(level: int, collisions: bool = True, **kw) -> dict:
     return p
 
 
+# Table 1 of the paper: five discretizations with T/dt = n = 8, 12, 16, 20,
+# 24, N_p = 10240 (n/8)^7 and N_avg = 32 (n/8)^5 (collisional, Eq.
+# refinements with s = 7, r = 5) or N_p = 10240 (n/8)^5 (collisionless,
+# s = 5), and 1/P_coll,max = 108.28 at the first level.
+TABLE1_N = (8, 12, 16, 20, 24)
+TABLE1_INV_PMAX_L1 = 108.28
+TABLE1_T = 0.1   # T = L / (10 vbar) with L = 1 and vbar = sigma_v = 1 (Sec. 5.2)
+
+
+def table1_sigma0(g_max: float = G_MAX) -> float:
+    """Hard-sphere sigma0 giving Table 1's P_coll,max at its first level
+    (P_max = sigma0 g_max w dt / dV with w = 1/10240, dt = T/8, dV = 8^-3);
+    P_max then follows Table 1 at every level (P_max ~ h^5)."""
+    n, npart = TABLE1_N[0], 10240
+    dt = TABLE1_T / n
+    return (1.0 / TABLE1_INV_PMAX_L1) * (1.0 / n ** 3) / (g_max * (1.0 / npart) * dt)
+
+
+def table1_level(level: int, collisions: bool = True, **kw) -> dict:
+    """Level l = 0..4 of Table 1 on the unit cube: n = 8 + 4 l cells per
+    axis, dt = T/n, n steps to T = 0.1; collisional: N_p = 10240 (n/8)^7,
+    K = 32 (n/8)^5; collisionless: N_p = 10240 (n/8)^5, K = 0. max_ppc
+    covers the densest cell ((1 + 0.3)^3 times the mean) with margin."""
+    n = TABLE1_N[level]
+    r = n / 8
+    npart = int(round(10240 * r ** (7 if collisions else 5)))
+    K = int(round(32 * r ** 5)) if collisions else 0
+    dt = TABLE1_T / n
+    ppc = npart / n ** 3
+    max_ppc = int(math.ceil((ppc * 1.3 ** 3 * 1.15 + 64) / 32.0)) * 32
+    p = base(n, npart, dt, K, table1_sigma0(), steps=n, max_ppc=max_ppc)
+    p.update(kw)
+    return p
+
+
 PRECISION_CG_TOL = 1e-6
 
 

@@ -30,6 +30,7 @@ def test_struct_layout_matches_header(L):
     # pic_config: 2 int32, int64, 13 doubles incl. arrays..., checked by size
     assert ctypes.sizeof(_lib.PicConfig) == 4 + 4 + 8 + 8 * 5 + 8 * 2 + 8 * 2 + 24 + 8 + 8 * 2 + 24 + 4 * 4 + 8 + 8 + 4 + 4
     assert ctypes.sizeof(_lib.PicErrors) == 14 * 8
+    assert ctypes.sizeof(_lib.PicAngleStats) == 8 + 16 + 4 * 8
 
 
 def test_default_config_is_valid_and_is_the_smallest_workload(L):
@@ -44,7 +45,7 @@ def test_default_config_is_valid_and_is_the_smallest_workload(L):
 @pytest.mark.parametrize("field,value", [
     ("n", 1), ("n", 2048), ("n_particles", 0), ("K", -1), ("dt", 0.0), ("dt", float("nan")),
     ("fx_amp", 1.0), ("v_sigma", 0.0), ("eps0", 0.0), ("cg_tol", 0.0), ("cg_maxit", 0), ("precision", 7),
-    ("max_ppc", -5), ("phi_T", 0.0),
+    ("max_ppc", -5), ("phi_T", 0.0), ("verify", 32), ("verify", 2 | 4), ("verify", -1),
 ])
 def test_invalid_configs_are_rejected(L, field, value):
     c = make_config(workloads.smallest())
@@ -62,6 +63,28 @@ def test_null_arguments(L):
     assert L.pic_step(None, 1) == _lib.PIC_EINVAL
     assert L.pic_sample_mms(None, 0.0) == _lib.PIC_EINVAL
     L.pic_destroy(None)  # no-op
+
+
+def test_verification_switches_validate(L):
+    for bits in (0, 1, 2, 4, 8, 16, 1 | 2 | 8 | 16, 1 | 4 | 8 | 16):
+        c = make_config(dict(workloads.smallest(), verify=bits))
+        assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_OK
+    assert L.pic_get_angle_stats(None, None) == _lib.PIC_EINVAL
+    # header constants agree with the binding
+    text = _lib.HEADER.read_text()
+    for name in ("PIC_VERIFY_ISOLATE", "PIC_VERIFY_ERROR1", "PIC_VERIFY_ERROR2", "PIC_VERIFY_ANGLES",
+                 "PIC_VERIFY_ANISO"):
+        import re
+        m = re.search(name + r" = (\d+)", text)
+        assert m and int(m.group(1)) == getattr(_lib, name)
+    assert f"#define PIC_ANGLE_BINS {_lib.PIC_ANGLE_BINS}" in text
+
+
+def test_batch_rejects_verification_switches(L):
+    cfgs = (_lib.PicConfig * 2)(*[make_config(dict(p, verify=1)) for p in workloads.batched(n_rep=2)])
+    out = ctypes.c_void_p(5)
+    assert L.pic_create_batch(cfgs, 2, None, None, ctypes.byref(out)) == _lib.PIC_EINVAL
+    assert not out.value
 
 
 def test_status_strings(L):

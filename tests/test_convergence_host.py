@@ -1,0 +1,61 @@
+"""Host logic of the refinement studies (no GPU): the Table 1 schedule
+recipe against the paper's printed table, and the rate fit against exact
+power laws."""
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_2602_15130_gb300 import convergence as C
+from paper_2602_15130_gb300 import derived, workloads as W
+
+GOLDEN = Path(__file__).parent / "golden"
+
+
+def _table1():
+    return [list(map(float, l.split())) for l in (GOLDEN / "paper_table1_discretizations.txt").read_text().splitlines()
+            if l.strip() and not l.startswith("#")]
+
+
+def test_table1_recipe_reproduces_the_paper_table():
+    for lvl, steps, nax, ncell, navg, inv_p, np_coll, np_free in _table1():
+        l = int(lvl) - 1
+        p = W.table1_level(l, collisions=True)
+        q = W.table1_level(l, collisions=False)
+        assert p["n"] == nax and p["steps"] == steps and abs(p["dt"] * steps - W.TABLE1_T) < 1e-15
+        assert p["n_particles"] == np_coll and p["K"] == navg
+        assert q["n_particles"] == np_free and q["K"] == 0
+        # 1/P_coll,max of the table, to its printed rounding
+        assert abs(1.0 / derived(p)["pmax"] / inv_p - 1.0) < 2e-4
+        # the densest cell of (1 + 0.3)^3 times the mean fits max_ppc
+        assert p["max_ppc"] >= 1.3 ** 3 * np_coll / ncell + 64 and p["max_ppc"] % 32 == 0
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, 2.5])
+def test_rate_fit_recovers_power_laws(p):
+    h = [1 / 8, 1 / 12, 1 / 16, 1 / 20, 1 / 24]
+    e = [3.0 * x ** p for x in h]
+    r = C.observed_rates(h, e)
+    assert all(abs(x - p) < 1e-12 for x in r["pairwise"])
+    assert abs(r["fit"] - p) < 1e-12
+
+
+def test_group_errors():
+    rec = {"eps2": dict(x=3.0, y=4.0, z=0.0, u=1.0, v=1.0, w=1.0, phi=0.5),
+           "epsinf": dict(x=1.0, y=5.0, z=2.0, u=0.1, v=0.3, w=0.2, phi=0.25)}
+    assert C.group_error(rec, "epsinf", "x") == 5.0
+    assert C.group_error(rec, "epsinf", "v") == 0.3
+    assert abs(C.group_error(rec, "eps2", "x") - math.sqrt(25.0 / 3)) < 1e-15
+    assert C.group_error(rec, "eps2", "phi") == 0.5
+
+
+def test_study_tables_are_consistent():
+    for table in (C.TABLE1_COLLISIONAL, C.TABLE1_COLLISIONLESS, C.REFINE):
+        for name, (over, pred) in table.items():
+            assert set(pred) <= {"x", "v", "phi", "x2", "v2"}
+            assert set(over) <= {"verify", "couple_qm_zero", "couple_q_zero", "K"}
+    # the isolated-collision variants switch the field off the particles
+    for name, (over, _) in C.TABLE1_COLLISIONAL.items():
+        if name.startswith("isolated"):
+            assert over["couple_qm_zero"] == 1 and over["verify"] & C.ISO

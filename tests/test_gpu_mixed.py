@@ -60,6 +60,26 @@ def test_mixed_sampling_and_sort(name):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("npart,clustered", [(4 * 4 * 4 * 300, 0), (26000, 3)])
+def test_mixed_sort_big_cells(npart, clustered):
+    """Block sort of cells above 256 particles (mean occupancy >= 128)."""
+    p = workloads.mixed(workloads.smallest(n=4, n_particles=npart))
+    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-12))
+    x, v = inputs.particles(npart, seed=21 + clustered, clustered_cells=clustered, n=4)
+    g.set_state(x, v)
+    o.set_state(x, v)
+    srt = o.sort()
+    assert (srt[1] > 256).any()
+    for a, b in zip(g.get_sort(), srt):
+        assert np.array_equal(a, b)
+    xg, vg = g.get_state()
+    xo, vo = o.state()
+    assert dpos(xg, xo).max() <= 1e-7 and np.abs(vg - vo).max() <= 1e-6 * np.abs(vo).max()
+    rho, _, _ = g.get_field()
+    ro, _, _ = o.field()
+    assert np.abs(rho - ro).max() <= 1e-6 * np.abs(ro).max()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_field(name):
     p = CASES[name]

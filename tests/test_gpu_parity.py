@@ -94,6 +94,31 @@ def test_sort_crowded_cells_and_empty_cells():
     assert close(rho, ro)[0] and close(phi, po)[0] and close(E, Eo)[0]
 
 
+@pytest.mark.parametrize("npart,clustered", [(4 * 4 * 4 * 300, 0), (20000, 1), (26000, 3)])
+def test_sort_big_cells(npart, clustered):
+    """Mean occupancy >= 128 switches on the block sort for cells of 257 to
+    16384 particles; smaller and larger cells stay on the warp pass."""
+    p = workloads.smallest(n=4, n_particles=npart, cg_tol=1e-13)
+    g, o = pair(p)
+    x, v = inputs.particles(npart, seed=11 + clustered, clustered_cells=clustered, n=4)
+    g.set_state(x, v)
+    o.set_state(x, v)
+    srt = o.sort()
+    counts = srt[1]
+    if clustered == 0:
+        assert ((counts > 256) & (counts <= 16384)).any() and (counts <= 256).any()
+    else:
+        assert (counts > 16384).any() or ((counts > 256) & (counts <= 16384)).any()
+    for a, b in zip(g.get_sort(), srt):
+        assert np.array_equal(a, b)
+    xg, vg = g.get_state()
+    xo, vo = o.state()
+    assert pos_close(xg, xo)[0] and close(vg, vo)[0]
+    rho, phi, E = g.get_field()
+    ro, po, Eo = o.field()
+    assert close(rho, ro, scale=np.abs(ro).max())[0] and close(phi, po, scale=np.abs(po).max())[0]
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_field_matches_oracle(name):
     p = CASES[name]

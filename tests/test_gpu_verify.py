@@ -1,0 +1,175 @@
+"""Verification switches (Sec. 5.4, 5.1) and the angle CDF metric (Sec. 4.4)
+on the GPU against the oracle, through the C ABI.
+
+FP64 form: positions and velocities within 1e-10, collision counts equal,
+as for the plain method. Angle metric: the device's binned closed form is
+within 2/PIC_ANGLE_BINS of the oracle's exact sort-based value on the same
+collisions (each sample sits within half a bin of its bin centre, plus one
+bin where rounding moves a sample across an edge). Precision form: the
+isolated collisionless drift reproduces x^M to FP32 rounding, and the angle
+metric tracks the oracle's within a few samples' worth (5/N).
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import oracle as O
+from paper_2602_15130_gb300 import Pic, workloads
+from paper_2602_15130_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+ISO, E1, E2, ANG, ANI = (_lib.PIC_VERIFY_ISOLATE, _lib.PIC_VERIFY_ERROR1, _lib.PIC_VERIFY_ERROR2,
+                         _lib.PIC_VERIFY_ANGLES, _lib.PIC_VERIFY_ANISO)
+BIN_TOL = 2.0 / _lib.PIC_ANGLE_BINS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+def dpos(a, b):
+    d = np.abs(a - b)
+    return np.minimum(d, 1.0 - d)
+
+
+SWITCHES = {
+    "isolate": dict(verify=ISO, couple_qm_zero=1),
+    "isolate_coupled": dict(verify=ISO),
+    "error1": dict(verify=E1),
+    "error2": dict(verify=E2),
+    "aniso": dict(verify=ANI),
+    "aniso_error2_angles": dict(verify=ANI | E2 | ANG),
+}
+
+
+@pytest.mark.parametrize("name", list(SWITCHES))
+def test_switch_steps_match_oracle_fp64(name):
+    p = workloads.smallest(n=8, n_particles=4096, cg_tol=1e-13, **SWITCHES[name])
+    g, o = Pic(p), O.Oracle(p)
+    g.sample_mms(0.0)
+    o.sample(0.0)
+    g.step(4)
+    o.step(4)
+    x, v = g.get_state()
+    xo, vo = o.state()
+    assert dpos(x, xo).max() <= TOL
+    assert np.abs(v - vo).max() <= TOL * max(1.0, np.abs(vo).max())
+    sg, so = g.stats(), o.stats()
+    assert sg["n_coll"] == so["n_coll"] > 0 and sg["n_cand"] == so["n_cand"]
+    eg, eo = g.mms_error()["array"], o.errors()
+    assert np.all(np.abs(eg - eo) <= TOL * np.abs(eo).max())
+
+
+def test_isolated_collisionless_reproduces_manufactured_solution():
+    """q/m = 0, K = 0: x^n = x^M(t_n) to rounding in both forms; v never
+    changes."""
+    p = workloads.smallest(K=0, couple_qm_zero=1, verify=ISO, cg_tol=1e-12)
+    for params, xtol in ((p, 1e-13), (workloads.mixed(p), 4e-6)):
+        g = Pic(params)
+        g.sample_mms(0.0)
+        e0 = g.mms_error()
+        g.step(20)
+        e = g.mms_error()
+        assert max(e["epsinf"][k] for k in "xyz") <= xtol, e["epsinf"]
+        # velocities keep their sampled values (FP32 sampling error only)
+        for k in "uvw":
+            assert e["epsinf"][k] == e0["epsinf"][k] and e["eps2"][k] == e0["eps2"][k]
+    assert e0["epsinf"]["u"] <= 1e-6
+    # the plain drift carries the midpoint-rule error of xdot^M
+    q = dict(p, verify=0)
+    g = Pic(q)
+    g.sample_mms(0.0)
+    g.step(20)
+    assert max(g.mms_error()["epsinf"][k] for k in "xyz") > 1e-9
+
+
+def test_isolated_mixed_tracks_oracle():
+    p = workloads.mixed(workloads.smallest(verify=ISO, couple_qm_zero=1))
+    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-12))
+    g.sample_mms(0.0)
+    o.sample(0.0)
+    g.step(10)
+    o.step(10)
+    x, v = g.get_state()
+    xo, vo = o.state()
+    far_x = (dpos(x, xo) > 1e-5).any(axis=1)
+    far_v = (np.abs(v - vo) > 1e-4).any(axis=1)
+    assert far_x.mean() <= 0.01 and far_v.mean() <= 0.02, (far_x.mean(), far_v.mean())
+    eg, eo = g.mms_error()["array"], o.errors()
+    assert np.all(np.abs(eg - eo) <= 0.03 * eo + 1e-7), (eg, eo)
+
+
+def _oracle_angle_errors(o, aniso):
+    ang = o.angles()
+    Fchi = O.F_chi_aniso if aniso else O.F_chi_iso
+    return len(ang), O.angle_cdf_errors(ang[:, 0], Fchi), O.angle_cdf_errors(ang[:, 1], O.F_eps)
+
+
+@pytest.mark.parametrize("verify", [ANG, ANG | ANI, ANG | ANI | E2, ANG | E1, ANG | E2])
+def test_angle_metric_matches_oracle_fp64(verify):
+    p = workloads.smallest(cg_tol=1e-13, verify=verify)
+    g, o = Pic(p), O.Oracle(p)
+    g.sample_mms(0.0)
+    o.sample(0.0)
+    g.step(3)
+    o.step(3)
+    a = g.angle_stats()
+    N, (e2c, eic), (e2e, eie) = _oracle_angle_errors(o, verify & ANI)
+    assert a["n_coll"] == N == o.stats()["n_coll"] > 5000
+    assert abs(a["eps2_chi"] - e2c) <= BIN_TOL, (a, e2c)
+    assert abs(a["epsinf_chi"] - eic) <= BIN_TOL, (a, eic)
+    assert abs(a["eps2_eps"] - e2e) <= BIN_TOL, (a, e2e)
+    assert abs(a["epsinf_eps"] - eie) <= BIN_TOL, (a, eie)
+
+
+def test_angle_metric_detects_error2_only_with_anisotropy():
+    out = {}
+    for verify in (ANG | ANI, ANG | ANI | E2, ANG | E2):
+        g = Pic(workloads.smallest(cg_tol=1e-12, verify=verify))
+        g.sample_mms(0.0)
+        g.step(6)
+        out[verify] = g.angle_stats()
+    N = out[ANG | ANI]["n_coll"]
+    assert out[ANG | ANI]["epsinf_chi"] * np.sqrt(N) < 2.0
+    assert 0.025 < out[ANG | ANI | E2]["epsinf_chi"] < 0.045
+    assert out[ANG | E2]["epsinf_chi"] * np.sqrt(out[ANG | E2]["n_coll"]) < 2.0
+
+
+def test_angle_metric_mixed_tracks_oracle():
+    p = workloads.mixed(workloads.smallest(verify=ANG | ANI))
+    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-12))
+    g.sample_mms(0.0)
+    o.sample(0.0)
+    g.step(3)
+    o.step(3)
+    a = g.angle_stats()
+    N, (e2c, eic), (e2e, eie) = _oracle_angle_errors(o, True)
+    assert abs(a["n_coll"] - N) <= 0.002 * N
+    tol = 5.0 / N + BIN_TOL
+    for got, want in ((a["eps2_chi"], e2c), (a["epsinf_chi"], eic), (a["eps2_eps"], e2e), (a["epsinf_eps"], eie)):
+        assert abs(got - want) <= tol, (got, want, tol)
+
+
+def test_angle_stats_state_and_reset():
+    g = Pic(workloads.smallest())
+    g.sample_mms(0.0)
+    with pytest.raises(_lib.PicError) as ei:
+        g.angle_stats()
+    assert ei.value.status == _lib.PIC_ESTATE
+    g = Pic(workloads.smallest(verify=ANG))
+    g.sample_mms(0.0)
+    assert g.angle_stats()["n_coll"] == 0
+    g.step(2)
+    assert g.angle_stats()["n_coll"] == g.stats()["n_coll"] > 0
+    g.reset_stats()
+    a = g.angle_stats()
+    assert a["n_coll"] == 0 and a["epsinf_chi"] == 0.0 and a["eps2_eps"] == 0.0
