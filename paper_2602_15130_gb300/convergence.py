@@ -81,12 +81,18 @@ def run_one(p: dict, precision: str) -> dict:
     t0 = time.perf_counter()
     sim = Pic(p)
     sim.sample_mms(0.0)
-    sim.step(int(p["steps"]))
+    sim.set_profiling(True)
+    # a diverging run (velocities past g_max run away; see the refine study)
+    # ends in a non-finite field: record it instead of stopping the study
+    status = sim.step(int(p["steps"]), allow=(_lib.PIC_ENOCONV,))
+    kt = sim.kernel_times()
     err = sim.mms_error()
     st = sim.stats()
     out = {"n": p["n"], "h": 1.0 / p["n"], "n_particles": p["n_particles"], "K": p["K"], "dt": p["dt"],
            "steps": p["steps"], "eps2": err["eps2"], "epsinf": err["epsinf"], "n_coll": st["n_coll"],
-           "n_cand": st["n_cand"], "cg_iters_max": st["cg_iters_max"]}
+           "n_cand": st["n_cand"], "cg_iters_max": st["cg_iters_max"],
+           "step_kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items() if v["launches"]},
+           "n_gmax_exceed": st["n_gmax_exceed"], "status": _lib.STATUS[status]}
     if p.get("verify", 0) & ANG:
         out["angles"] = sim.angle_stats()
     out["seconds"] = time.perf_counter() - t0
@@ -112,7 +118,8 @@ def group_error(rec: dict, norm: str, group: str) -> float:
     return e["phi"]
 
 
-def run_study(study: str, levels: list[int], precision: str, variants: list[str] | None = None, log=print) -> dict:
+def run_study(study: str, levels: list[int], precision: str, variants: list[str] | None = None, log=print,
+              save=None) -> dict:
     table = {"table1-collisional": TABLE1_COLLISIONAL, "table1-collisionless": TABLE1_COLLISIONLESS,
              "refine": REFINE}[study]
     result = {"study": study, "precision": precision, "levels": levels, "variants": {}}
@@ -123,9 +130,13 @@ def run_study(study: str, levels: list[int], precision: str, variants: list[str]
         for l in levels:
             rec = run_one(levels_params(study, l, over), precision)
             recs.append(rec)
+            result["variants"][name] = {"records": recs, "rates": {}}
+            if save:
+                save(result)
             log(f"[{study}/{name}] n={rec['n']} Np={rec['n_particles']} K={rec['K']} steps={rec['steps']} "
                 f"eps_inf(x,v,phi)=({group_error(rec, 'epsinf', 'x'):.3e}, {group_error(rec, 'epsinf', 'v'):.3e}, "
-                f"{rec['epsinf']['phi']:.3e}) {rec['seconds']:.1f}s")
+                f"{rec['epsinf']['phi']:.3e}) {rec['seconds']:.1f}s "
+                f"(dsmc {rec['step_kernel_ms'].get('dsmc', 0.0) / 1e3:.1f}s)")
         h = [r["h"] for r in recs]
         rates = {}
         for group in ("x", "v", "phi"):
@@ -141,6 +152,8 @@ def run_study(study: str, levels: list[int], precision: str, variants: list[str]
                 slope = float(np.polyfit(np.log(ncoll), np.log(e), 1)[0]) if all(x > 0 for x in e) else None
                 rates[f"angle_{k}"] = {"errors": e, "n_coll": ncoll, "slope_vs_ncoll": slope, "predicted": -0.5}
         result["variants"][name] = {"records": recs, "rates": rates}
+        if save:
+            save(result)
     return result
 
 
@@ -168,11 +181,13 @@ def main(argv=None) -> int:
     ap.add_argument("--variants", nargs="*", default=None)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
-    res = run_study(a.study, a.levels, a.precision, a.variants, log=lambda s: print(s, flush=True))
+    def save(res):
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(res, f, indent=1)
+
+    res = run_study(a.study, a.levels, a.precision, a.variants, log=lambda s: print(s, flush=True), save=save)
     print(format_report(res), flush=True)
-    if a.out:
-        with open(a.out, "w") as f:
-            json.dump(res, f, indent=1)
     return 0
 
 

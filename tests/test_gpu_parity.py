@@ -94,7 +94,7 @@ def test_sort_crowded_cells_and_empty_cells():
     assert close(rho, ro)[0] and close(phi, po)[0] and close(E, Eo)[0]
 
 
-@pytest.mark.parametrize("npart,clustered", [(4 * 4 * 4 * 300, 0), (20000, 1), (26000, 3)])
+@pytest.mark.parametrize("npart,clustered", [(4 * 4 * 4 * 260, 0), (20000, 1), (26000, 3)])
 def test_sort_big_cells(npart, clustered):
     """Mean occupancy >= 128 switches on the block sort for cells of 257 to
     16384 particles; smaller and larger cells stay on the warp pass."""

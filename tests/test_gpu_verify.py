@@ -5,7 +5,8 @@ FP64 form: positions and velocities within 1e-10, collision counts equal,
 as for the plain method. Angle metric: the device's binned closed form is
 within 2/PIC_ANGLE_BINS of the oracle's exact sort-based value on the same
 collisions (each sample sits within half a bin of its bin centre, plus one
-bin where rounding moves a sample across an edge). Precision form: the
+bin where rounding moves a sample across an edge), widened by the bin
+count over N where Error 2 makes exact ties. Precision form: the
 isolated collisionless drift reproduces x^M to FP32 rounding, and the angle
 metric tracks the oracle's within a few samples' worth (5/N).
 """
@@ -125,10 +126,15 @@ def test_angle_metric_matches_oracle_fp64(verify):
     a = g.angle_stats()
     N, (e2c, eic), (e2e, eie) = _oracle_angle_errors(o, verify & ANI)
     assert a["n_coll"] == N == o.stats()["n_coll"] > 5000
-    assert abs(a["eps2_chi"] - e2c) <= BIN_TOL, (a, e2c)
-    assert abs(a["epsinf_chi"] - eic) <= BIN_TOL, (a, eic)
-    assert abs(a["eps2_eps"] - e2e) <= BIN_TOL, (a, e2e)
-    assert abs(a["epsinf_eps"] - eie) <= BIN_TOL, (a, eie)
+    # Error 2 repeats g' = +-(v_p - v_q) whenever the same untouched pair
+    # collides in several outcomes: exact ties, which the right-continuous
+    # empirical CDF ranks together (up to max_bin - 1 ranks apart from the
+    # device's spread); scattered angles never tie
+    tie = [(m - 1) / N if verify & E2 else 0.0 for m in a["max_bin"]]
+    assert abs(a["eps2_chi"] - e2c) <= BIN_TOL + tie[0], (a, e2c)
+    assert abs(a["epsinf_chi"] - eic) <= BIN_TOL + tie[0], (a, eic)
+    assert abs(a["eps2_eps"] - e2e) <= BIN_TOL + tie[1], (a, e2e)
+    assert abs(a["epsinf_eps"] - eie) <= BIN_TOL + tie[1], (a, eie)
 
 
 def test_angle_metric_detects_error2_only_with_anisotropy():
