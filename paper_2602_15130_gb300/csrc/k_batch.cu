@@ -419,12 +419,7 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) kb_dsmc(BDsmcArgs a) {
           uint32_t mine = 0u;
           if (coll_ok) {
             const bool owner = lane >= cl * Kc && lane < cl * Kc + kmax;
-            const uint32_t word = owner ? bm[w] : 0u;
-#pragma unroll 8
-            for (int b = 0; b < 32; ++b) {
-              const uint32_t m = __ballot_sync(0xffffffffu, (word >> b) & 1u);
-              if (lane == b) mine = m;
-            }
+            mine = warp_transpose32(owner ? bm[w] : 0u, lane);
           }
           const int jj = 32 * w + lane;
           if (jj >= cc) continue;
@@ -567,7 +562,7 @@ __global__ void __launch_bounds__(512) kb_kick(BKickArgs a) {
   }
   const int32_t k = (int32_t)(base + ci[0] + n * (ci[1] + n * ci[2]));
   a.key[j] = k;
-  a.rank[j] = atomicAdd(a.count + k, 1);
+  a.rank[j] = cell_slot(a.count, k);
 }
 
 }  // namespace

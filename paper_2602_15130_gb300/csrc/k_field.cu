@@ -84,6 +84,48 @@ __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
   if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
 }
 
+// Precision form: the same RHS with the manufactured terms in FP32 (the
+// FP64 pipe is slow on this part); the corner sums, rho and the block
+// partial of the mean stay FP64.
+struct Rhs32Consts {
+  float h, two_pi_over, lap_scale;   // h, phi^M amplitude / (2 pi) * e^{t/2T}, -3 (2 pi)^2
+  float shift[3], ct, fx_amp;
+  float rhoM_scale, inv_eps0;         // q N, 1/eps0
+};
+
+__global__ void __launch_bounds__(kThreads) k_rhs32(RhsArgs a, Rhs32Consts k) {
+  __shared__ double sh[40];
+  const Params& P = a.P;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double bsum = 0.0;
+  if (id < P.ncell) {
+    const int n = P.n;
+    const int i = (int)(id % n), j = (int)((id / n) % n), kk0 = (int)(id / ((int64_t)n * n));
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int ii = i - q < 0 ? n - 1 : i - q, jj = j - b < 0 ? n - 1 : j - b, kk = kk0 - c < 0 ? n - 1 : kk0 - c;
+          s += a.corner[(int64_t)(q + 2 * b + 4 * c) * P.ncell + ii + (int64_t)n * (jj + (int64_t)n * kk)];
+        }
+    const double rho = P.rho_scale * s;
+    const float X = (float)i * k.h, Y = (float)j * k.h, Z = (float)kk0 * k.h;
+    const float phiM = k.two_pi_over * sinpif(2.f * (X - k.shift[0])) * sinpif(2.f * (Y - k.shift[1])) *
+                       sinpif(2.f * (Z - k.shift[2]));
+    const float rhoM = k.rhoM_scale * (1.f + k.fx_amp * sinpif(2.f * (X - k.ct))) *
+                       (1.f + k.fx_amp * sinpif(2.f * (Y - k.ct))) * (1.f + k.fx_amp * sinpif(2.f * (Z - k.ct)));
+    const float bv = (float)(rho * (double)k.inv_eps0) - k.lap_scale * phiM - rhoM * k.inv_eps0;
+    a.rho[id] = rho;
+    a.b32[id] = bv;
+    bsum = (double)bv;
+  }
+  const double tot = block_sum(bsum, sh);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+}
+
 struct CgArgs {
   int n;
   int64_t ncell;
@@ -166,7 +208,11 @@ __device__ __forceinline__ Nbr neighbours(int id, int n, int nn) {
   return b;
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg(CgArgs a) {
+// One block per SM of 1024 threads keeps the grid barriers and the
+// per-block partial sums short.
+constexpr int kCgThreads = 1024;
+
+__global__ void __launch_bounds__(kCgThreads) k_cg(CgArgs a) {
   __shared__ double sh[40];
   __shared__ double scal[2];  // scalars formed once per block by thread 0
   __shared__ int stop;
@@ -320,13 +366,26 @@ cudaError_t launch_rhs(pic_ctx* c, double t) {
   a.b32 = c->mixed ? c->bf : nullptr;
   a.part = c->rhs_part;
   prof_begin(c);
-  k_rhs<<<(int)c->rhs_blocks, kThreads, 0, c->stream>>>(a);
+  if (c->mixed) {
+    Rhs32Consts k;
+    k.h = (float)c->P.h;
+    k.two_pi_over = (float)(a.tt.em_amp / kTwoPi);
+    k.lap_scale = (float)(-3.0 * kTwoPi * kTwoPi);
+    for (int d = 0; d < 3; ++d) k.shift[d] = (float)c->P.phi_shift[d];
+    k.ct = (float)(a.tt.ct - floor(a.tt.ct));
+    k.fx_amp = (float)c->P.fx_amp;
+    k.rhoM_scale = (float)(c->P.q_eff * c->P.nphys);
+    k.inv_eps0 = (float)(1.0 / c->P.eps0);
+    k_rhs32<<<(int)c->rhs_blocks, kThreads, 0, c->stream>>>(a, k);
+  } else {
+    k_rhs<<<(int)c->rhs_blocks, kThreads, 0, c->stream>>>(a);
+  }
   prof_end(c, KC_RHS);
   c->launches++;
   return cudaGetLastError();
 }
 
-int cg_threads() { return kThreads; }
+int cg_threads() { return kCgThreads; }
 const void* cg_kernel_ptr() { return (const void*)k_cg; }
 
 cudaError_t launch_cg(pic_ctx* c) {
@@ -359,7 +418,7 @@ cudaError_t launch_cg(pic_ctx* c) {
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
   prof_begin(c);
-  e = cudaLaunchCooperativeKernel((const void*)k_cg, dim3(c->cg_grid), dim3(kThreads), args, 0, c->stream);
+  e = cudaLaunchCooperativeKernel((const void*)k_cg, dim3(c->cg_grid), dim3(kCgThreads), args, 0, c->stream);
   prof_end(c, KC_CG);
   c->launches++;
   if (e != cudaSuccess) return e;

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_keys32(Keys32Args a) {
   if (j >= a.np) return;
   const int32_t k = a.cell[j];
   a.key[j] = k;
-  a.rank[j] = atomicAdd(a.count + k, 1);
+  a.rank[j] = cell_slot(a.count, k);
 }
 
 struct Store32Args {
@@ -122,6 +122,68 @@ struct Gather32Args {
 
 constexpr int kGatherThreads = 256;
 
+// CIC corner weights of one particle (offsets in cell units) in 64-bit fixed
+// point: integer sums are exact in any order, so a cell's corner partials do
+// not depend on the order its particles are visited in. The conversion
+// rounds with FP32 arithmetic only (64-bit float-to-integer conversions run
+// on the slow FP64 pipe): adding 1.5 2^23 rounds w 2^22 to an integer held
+// in the low mantissa bits, an FMA recovers the remainder exactly, and the
+// remainder is rounded the same way to lo_bits more bits. Resolution 2^-40
+// (error <= 2^-41 per weight) below 2^23 particles per cell, 2^-30 above, so
+// a corner sum never leaves int64.
+struct CicFixed {
+  float lo_scale;  // 2^lo_bits
+  int lo_bits;     // 18 or 8
+  double inv;      // 2^-(22 + lo_bits)
+};
+__device__ __forceinline__ CicFixed cic_fixed_for(int32_t cnt) {
+  return cnt < (1 << 23) ? CicFixed{262144.f, 18, 1.0 / 1099511627776.0} : CicFixed{256.f, 8, 1.0 / 1073741824.0};
+}
+__device__ __forceinline__ long long to_fixed(float w, const CicFixed& f) {
+  constexpr float M = 12582912.f;  // 1.5 2^23
+  const float hs = fmaf(w, 4194304.f, M);
+  const int hi = __float_as_int(hs) - 0x4B400000;
+  const float rem = fmaf(w, 4194304.f, -(hs - M));
+  const int lo = __float_as_int(fmaf(rem, f.lo_scale, M)) - 0x4B400000;
+  return ((long long)hi << f.lo_bits) + lo;
+}
+
+__device__ __forceinline__ void cic_add_fixed(long long* acc, float ox, float oy, float oz, const CicFixed& f) {
+  const float wx[2] = {1.f - ox, ox}, wy[2] = {1.f - oy, oy}, wz[2] = {1.f - oz, oz};
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float wyz = wy[b] * wz[c];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) acc[q + 2 * b + 4 * c] += to_fixed(wx[q] * wyz, f);
+    }
+}
+
+__device__ __forceinline__ long long shfl_xor_ll(long long v, int off) {
+  return (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, off);
+}
+
+// warp sum of 8 fixed-point corner partials: each xor level halves the
+// values a lane keeps; lane l then holds corner 4 [l & 16] + 2 [l & 8] + [l & 4]
+__device__ __forceinline__ void store_corners_fixed(const long long* acc, int lane, double* corner, int64_t ncell,
+                                                    int64_t cell, double inv) {
+  const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+  long long a4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a4[i] = (u16 ? acc[4 + i] : acc[i]) + shfl_xor_ll(u16 ? acc[i] : acc[4 + i], 16);
+  long long a2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) a2[i] = (u8 ? a4[2 + i] : a4[i]) + shfl_xor_ll(u8 ? a4[i] : a4[2 + i], 8);
+  long long a1 = (u4 ? a2[1] : a2[0]) + shfl_xor_ll(u4 ? a2[0] : a2[1], 4);
+  a1 += shfl_xor_ll(a1, 2);
+  a1 += shfl_xor_ll(a1, 1);
+  if ((lane & 3) == 0) {
+    const int c = (u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0);
+    corner[(int64_t)c * ncell + cell] = (double)a1 * inv;
+  }
+}
+
 __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -130,12 +192,29 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
     const int32_t s = a.start[cell];
     const int32_t cnt = a.start[cell + 1] - s;
     if (cnt > a.big_lo && cnt <= kMaxBlockSort) continue;  // k_sort_big32
+    const CicFixed fx = cic_fixed_for(cnt);
+    long long acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0;
     if (cnt <= 64) {
-      // both 32-element chunks held in registers, ranked in one pass
+      // both 32-element chunks in registers; the particle data is loaded
+      // with the pids (one memory round trip), then ranked in one pass
       int32_t src0 = 0, src1 = 0;
       uint32_t p0 = 0xFFFFFFFFu, p1 = 0xFFFFFFFFu;
-      if (lane < cnt) { src0 = a.perm[s + lane]; p0 = a.pid_in[src0]; }
-      if (lane + 32 < cnt) { src1 = a.perm[s + 32 + lane]; p1 = a.pid_in[src1]; }
+      float d0[9], d1[9];
+      const bool h0 = lane < cnt, h1 = lane + 32 < cnt;
+      if (h0) src0 = a.perm[s + lane];
+      if (h1) src1 = a.perm[s + 32 + lane];
+      if (h0) {
+        p0 = a.pid_in[src0];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d0[q] = a.in[q][src0];
+      }
+      if (h1) {
+        p1 = a.pid_in[src1];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d1[q] = a.in[q][src1];
+      }
       int r0 = 0, r1 = 0;
       const int lim = min(32, cnt);
       for (int l = 0; l < lim; ++l) {
@@ -143,75 +222,51 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
         r0 += (x0 < p0) + (x1 < p0);
         r1 += (x0 < p1) + (x1 < p1);
       }
-      if (lane < cnt) {
+      if (h0) {
         const int32_t dst = s + r0;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src0];
+        for (int q = 0; q < 9; ++q) a.out[q][dst] = d0[q];
         a.pid_out[dst] = p0;
         a.cell_out[dst] = (int32_t)cell;
+        cic_add_fixed(acc, d0[0], d0[1], d0[2], fx);
       }
-      if (lane + 32 < cnt) {
+      if (h1) {
         const int32_t dst = s + r1;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src1];
+        for (int q = 0; q < 9; ++q) a.out[q][dst] = d1[q];
         a.pid_out[dst] = p1;
         a.cell_out[dst] = (int32_t)cell;
+        cic_add_fixed(acc, d1[0], d1[1], d1[2], fx);
       }
     } else {
-    for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
-      const int32_t e = e0 + lane;
-      int32_t src = 0;
-      uint32_t mp = 0xFFFFFFFFu;
-      if (e < cnt) {
-        src = a.perm[s + e];
-        mp = a.pid_in[src];
-      }
-      int32_t r = 0;
-      for (int32_t f0 = 0; f0 < cnt; f0 += 32) {
-        const uint32_t other = f0 == e0 ? mp : ((f0 + lane < cnt) ? a.pid_in[a.perm[s + f0 + lane]] : 0xFFFFFFFFu);
-        const int lim = min(32, cnt - f0);
-        for (int l = 0; l < lim; ++l) r += __shfl_sync(0xffffffffu, other, l) < mp ? 1 : 0;
-      }
-      if (e < cnt) {
-        const int32_t dst = s + r;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src];
-        a.pid_out[dst] = mp;
-        a.cell_out[dst] = (int32_t)cell;
-      }
-    }
-    }
-    __syncwarp();
-    // per-cell CIC weights in sorted order, double-float sums
-    DF acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = DF{0.f, 0.f};
-    for (int32_t e = lane; e < cnt; e += 32) {
-      const float ox = a.out[0][s + e], oy = a.out[1][s + e], oz = a.out[2][s + e];
-      const float wx[2] = {1.f - ox, ox}, wy[2] = {1.f - oy, oy}, wz[2] = {1.f - oz, oz};
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          const float wyz = wy[b] * wz[c];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) acc[q + 2 * b + 4 * c] = df_fma(acc[q + 2 * b + 4 * c], wx[q], wyz);
+      for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
+        const int32_t e = e0 + lane;
+        int32_t src = 0;
+        uint32_t mp = 0xFFFFFFFFu;
+        if (e < cnt) {
+          src = a.perm[s + e];
+          mp = a.pid_in[src];
         }
-    }
-    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
-    DF a4[4];
+        int32_t r = 0;
+        for (int32_t f0 = 0; f0 < cnt; f0 += 32) {
+          const uint32_t other = f0 == e0 ? mp : ((f0 + lane < cnt) ? a.pid_in[a.perm[s + f0 + lane]] : 0xFFFFFFFFu);
+          const int lim = min(32, cnt - f0);
+          for (int l = 0; l < lim; ++l) r += __shfl_sync(0xffffffffu, other, l) < mp ? 1 : 0;
+        }
+        if (e < cnt) {
+          const int32_t dst = s + r;
+          float d[9];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a4[i] = df_add(u16 ? acc[4 + i] : acc[i], df_shfl_xor(u16 ? acc[i] : acc[4 + i], 16));
-    DF a2[2];
+          for (int q = 0; q < 9; ++q) d[q] = a.in[q][src];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) a2[i] = df_add(u8 ? a4[2 + i] : a4[i], df_shfl_xor(u8 ? a4[i] : a4[2 + i], 8));
-    DF a1 = df_add(u4 ? a2[1] : a2[0], df_shfl_xor(u4 ? a2[0] : a2[1], 4));
-    a1 = df_add(a1, df_shfl_xor(a1, 2));
-    a1 = df_add(a1, df_shfl_xor(a1, 1));
-    if ((lane & 3) == 0) {
-      const int corner = (u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0);
-      a.corner[(int64_t)corner * a.ncell + cell] = df_to_double(a1);
+          for (int q = 0; q < 9; ++q) a.out[q][dst] = d[q];
+          a.pid_out[dst] = mp;
+          a.cell_out[dst] = (int32_t)cell;
+          cic_add_fixed(acc, d[0], d[1], d[2], fx);
+        }
+      }
     }
+    store_corners_fixed(acc, lane, a.corner, a.ncell, cell, fx.inv);
   }
 }
 
@@ -224,7 +279,7 @@ __global__ void __launch_bounds__(kBigThreads) k_sort_big32(Gather32Args a) {
   extern __shared__ uint32_t shm[];
   uint32_t* key = shm;
   int32_t* val = reinterpret_cast<int32_t*>(shm + kMaxBlockSort);
-  __shared__ double red[kBigThreads / 32][8];
+  __shared__ long long red[kBigThreads / 32][8];
   for (int64_t cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
     const int32_t s = a.start[cell];
     const int32_t cnt = a.start[cell + 1] - s;
@@ -251,33 +306,24 @@ __global__ void __launch_bounds__(kBigThreads) k_sort_big32(Gather32Args a) {
       a.cell_out[dst] = (int32_t)cell;
     }
     __syncthreads();
-    DF acc[8];
+    long long acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = DF{0.f, 0.f};
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const float ox = a.out[0][s + e], oy = a.out[1][s + e], oz = a.out[2][s + e];
-      const float wx[2] = {1.f - ox, ox}, wy[2] = {1.f - oy, oy}, wz[2] = {1.f - oz, oz};
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          const float wyz = wy[b] * wz[c];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) acc[q + 2 * b + 4 * c] = df_fma(acc[q + 2 * b + 4 * c], wx[q], wyz);
-        }
-    }
+    for (int q = 0; q < 8; ++q) acc[q] = 0;
+    const CicFixed fx = cic_fixed_for(cnt);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+      cic_add_fixed(acc, a.out[0][s + e], a.out[1][s + e], a.out[2][s + e], fx);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[q] = df_add(acc[q], df_shfl_xor(acc[q], off));
-      if (lane == 0) red[w][q] = df_to_double(acc[q]);
+      for (int off = 16; off > 0; off >>= 1) acc[q] += shfl_xor_ll(acc[q], off);
+      if (lane == 0) red[w][q] = acc[q];
     }
     __syncthreads();
     if (threadIdx.x < 8) {
-      double t = 0.0;
+      long long t = 0;
       for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
-      a.corner[(int64_t)threadIdx.x * a.ncell + cell] = t;
+      a.corner[(int64_t)threadIdx.x * a.ncell + cell] = (double)t * fx.inv;
     }
     __syncthreads();
   }
@@ -433,9 +479,9 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
                                bm, ov, cnt);
       __syncwarp();
       // per cell of the group and per 32-particle word: transpose the
-      // lanes' bitmap words with ballots, so lane b learns which outcomes
-      // touched particle 32 w + b, then add their changes in ascending
-      // outcome order
+      // lanes' bitmap words across the warp, so lane b learns which
+      // outcomes touched particle 32 w + b, then add their changes in
+      // ascending outcome order
       const bool last = ch == a.nchunks - 1;
       for (int cl = 0; cl < ncl; ++cl) {
         const int32_t cs = a.start[cell0 + cl];
@@ -446,12 +492,7 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
           uint32_t mine = 0u;
           if (coll_ok) {
             const bool owner = lane >= cl * a.Kc && lane < cl * a.Kc + kmax;
-            const uint32_t word = owner ? bm[w] : 0u;
-#pragma unroll 8
-            for (int b = 0; b < 32; ++b) {
-              const uint32_t m = __ballot_sync(0xffffffffu, (word >> b) & 1u);
-              if (lane == b) mine = m;
-            }
+            mine = warp_transpose32(owner ? bm[w] : 0u, lane);
           }
           const int jj = 32 * w + lane;
           if (jj >= cc) continue;
@@ -607,7 +648,7 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   }
   const int32_t k = ci[0] + n * (ci[1] + n * ci[2]);
   a.key[j] = k;
-  a.rank[j] = atomicAdd(a.count + k, 1);
+  a.rank[j] = cell_slot(a.count, k);
 }
 
 // ---------------------------------------------------------------- CG32 --
@@ -677,6 +718,57 @@ __device__ __forceinline__ double block_total_df(DF v, double* sh) {
   return t;
 }
 
+// two block totals at once (thread 0 only; sh holds at least 64 doubles)
+__device__ __forceinline__ void block_total_df2(DF u, DF v, double* sh, double* tu, double* tv) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    u = df_add(u, df_shfl_xor(u, off));
+    v = df_add(v, df_shfl_xor(v, off));
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[w] = df_to_double(u);
+    sh[32 + w] = df_to_double(v);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      a += sh[i];
+      b += sh[32 + i];
+    }
+    *tu = a;
+    *tv = b;
+  }
+}
+
+// totals of two partial arrays in one pass, in every thread
+__device__ __forceinline__ void grid_total32x2(const double* pa, const double* pb, int m, double* sh, double* ta,
+                                               double* tb) {
+  const int lane = threadIdx.x & 31;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      a += ((volatile const double*)pa)[i];
+      b += ((volatile const double*)pb)[i];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, off);
+      b += __shfl_xor_sync(0xffffffffu, b, off);
+    }
+    if (lane == 0) {
+      sh[0] = a;
+      sh[1] = b;
+    }
+  }
+  __syncthreads();
+  *ta = sh[0];
+  *tb = sh[1];
+}
+
 __device__ __forceinline__ double grid_total32(const double* part, int m, double* sh) {
   const int lane = threadIdx.x & 31;
   __syncthreads();
@@ -707,9 +799,16 @@ __device__ __forceinline__ Nbr neighbours(int id, int n, int nn) {
 }
 
 // FP32 vectors and stencil; inner products and the residual in double-float
-// per thread, FP64 across blocks; same phases as the FP64 solver.
-__global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
-  __shared__ double sh[40];
+// per thread, FP64 across blocks. Chronopoulos-Gear form of CG: with
+// w = A r and s = A p carried by recurrence, (r, r) and (r, w) come from one
+// reduction, so an iteration needs two grid barriers (r complete before
+// the stencil; the partial sums published) instead of three. The iterates
+// are those of standard CG in exact arithmetic. b's storage holds w once
+// the initial residual has been formed.
+constexpr int kCgThreads = 1024;
+
+__global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
+  __shared__ double sh[72];
   __shared__ float fscal[2];  // alpha, beta formed once per block by thread 0
   __shared__ int stop;
   const int n = a.n, nn = a.n * a.n;
@@ -719,13 +818,14 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
   const int G = gridDim.x;
   int ph = 0;
   auto slot = [&](int q) { return a.red + (size_t)q * 2 * G; };
+  float* const w = a.b;  // reused after the initial residual
+  float* const s = a.q;
 
   const float mean_b = (float)(grid_total32(a.rhs_part, a.rhs_blocks, sh) / (double)m);
   DF rr_loc{0.f, 0.f}, bb_loc{0.f, 0.f};
   for (int id = t0; id < m; id += stride) {
     const Nbr q = neighbours(id, n, nn);
     const float bv = a.b[id] - mean_b;
-    a.b[id] = bv;
     const float* x = a.x;
     const float nb = x[q.xp] + x[q.xm] + x[q.yp] + x[q.ym] + x[q.zp] + x[q.zm];
     const float rv = bv - (6.f * x[id] - nb) * a.inv_h2;
@@ -740,66 +840,94 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
     if (threadIdx.x == 0) slot(ph)[G + blockIdx.x] = s2;
   }
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-  double rr = grid_total32(slot(ph), G, sh);
+  double gamma = grid_total32(slot(ph), G, sh);
   const double bb = grid_total32(slot(ph) + G, G, sh);
   ph ^= 1;
-  int it = 0, status = 0;
   const double thresh = a.tol * sqrt(bb);
+  int it = 0, status = 0;
+  double alpha = 0.0;
+  // w = A r and delta = (r, w) for the first step
+  {
+    DF rw_loc{0.f, 0.f};
+    for (int id = t0; id < m; id += stride) {
+      const Nbr q = neighbours(id, n, nn);
+      const float* r = a.r;
+      const float rc = r[id];
+      const float wv = (6.f * rc - (r[q.xp] + r[q.xm] + r[q.yp] + r[q.ym] + r[q.zp] + r[q.zm])) * a.inv_h2;
+      w[id] = wv;
+      rw_loc = df_fma(rw_loc, rc, wv);
+    }
+    const double s1 = block_total_df(rw_loc, sh);
+    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s1;
+  }
+  if (!grid_barrier32(a.bar, a.info, a.flags)) return;
+  double delta = grid_total32(slot(ph), G, sh);
+  ph ^= 1;
+  double beta = 0.0;
   while (true) {
-    if (threadIdx.x == 0) stop = (bb == 0.0 || sqrt(rr) <= thresh) ? 1 : (it >= a.maxit ? 2 : 0);
+    if (threadIdx.x == 0) {
+      stop = (bb == 0.0 || sqrt(gamma) <= thresh) ? 1 : (it >= a.maxit ? 2 : 0);
+      if (!stop) {
+        const double den = it == 0 ? delta : delta - beta * gamma / alpha;
+        alpha = gamma / den;
+        fscal[0] = (float)alpha;
+        fscal[1] = (float)beta;
+      }
+    }
     __syncthreads();
     if (stop == 1) break;
     if (stop == 2) { status = 1; break; }
-    const float bf = fscal[1];
+    const float al = fscal[0], be = fscal[1];
     if (it == 0) {
-      for (int id = t0; id < m; id += stride) a.p[id] = a.r[id];
+      for (int id = t0; id < m; id += stride) {
+        const float pv = a.r[id], sv = w[id];
+        a.p[id] = pv;
+        s[id] = sv;
+        a.x[id] = fmaf(al, pv, a.x[id]);
+        a.r[id] = fmaf(-al, sv, pv);
+      }
     } else {
-      for (int id = t0; id < m; id += stride) a.p[id] = fmaf(bf, a.p[id], a.r[id]);
+      for (int id = t0; id < m; id += stride) {
+        const float pv = fmaf(be, a.p[id], a.r[id]);
+        const float sv = fmaf(be, s[id], w[id]);
+        a.p[id] = pv;
+        s[id] = sv;
+        a.x[id] = fmaf(al, pv, a.x[id]);
+        a.r[id] = fmaf(-al, sv, a.r[id]);
+      }
     }
     if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-    DF pq_loc{0.f, 0.f};
+    DF rr_l{0.f, 0.f}, rw_l{0.f, 0.f};
     for (int id = t0; id < m; id += stride) {
       const Nbr q = neighbours(id, n, nn);
-      const float* p = a.p;
-      const float nb = p[q.xp] + p[q.xm] + p[q.yp] + p[q.ym] + p[q.zp] + p[q.zm];
-      const float pc = p[id];
-      const float qv = (6.f * pc - nb) * a.inv_h2;
-      a.q[id] = qv;
-      pq_loc = df_fma(pq_loc, pc, qv);
+      const float* r = a.r;
+      const float rc = r[id];
+      const float wv = (6.f * rc - (r[q.xp] + r[q.xm] + r[q.yp] + r[q.ym] + r[q.zp] + r[q.zm])) * a.inv_h2;
+      w[id] = wv;
+      rr_l = df_fma(rr_l, rc, rc);
+      rw_l = df_fma(rw_l, rc, wv);
     }
     {
-      const double s = block_total_df(pq_loc, sh);
-      if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+      double s1 = 0.0, s2 = 0.0;
+      block_total_df2(rr_l, rw_l, sh, &s1, &s2);
+      if (threadIdx.x == 0) {
+        slot(ph)[blockIdx.x] = s1;
+        slot(ph)[G + blockIdx.x] = s2;
+      }
     }
     if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-    const double pq = grid_total32(slot(ph), G, sh);
-    ph ^= 1;
-    if (threadIdx.x == 0) fscal[0] = (float)(rr / pq);
-    __syncthreads();
-    const float alpha = fscal[0];
-    DF rn_loc{0.f, 0.f};
-    for (int id = t0; id < m; id += stride) {
-      a.x[id] = fmaf(alpha, a.p[id], a.x[id]);
-      const float rv = fmaf(-alpha, a.q[id], a.r[id]);
-      a.r[id] = rv;
-      rn_loc = df_fma(rn_loc, rv, rv);
-    }
-    {
-      const double s = block_total_df(rn_loc, sh);
-      if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
-    }
-    if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-    const double rr_new = grid_total32(slot(ph), G, sh);
+    double gamma_new;
+    grid_total32x2(slot(ph), slot(ph) + G, G, sh, &gamma_new, &delta);
     ph ^= 1;
     ++it;
-    if (threadIdx.x == 0) fscal[1] = (float)(rr_new / rr);
-    rr = rr_new;
+    beta = gamma_new / gamma;
+    gamma = gamma_new;
   }
   DF xs{0.f, 0.f};
   for (int id = t0; id < m; id += stride) xs = df_add_f(xs, a.x[id]);
   {
-    const double s = block_total_df(xs, sh);
-    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s;
+    const double s1 = block_total_df(xs, sh);
+    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s1;
   }
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
   const double xsum = grid_total32(slot(ph), G, sh);  // every thread calls it: it synchronises the block
@@ -819,7 +947,7 @@ __global__ void __launch_bounds__(kThreads) k_cg32(Cg32Args a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[0] = it;
     a.info[1] = status;
-    a.res[0] = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
+    a.res[0] = bb > 0.0 ? sqrt(gamma) / sqrt(bb) : 0.0;
     if (status) atomicOr(a.flags, 2);
     atomicMax(a.flags + 1, it);
   }
@@ -1002,7 +1130,7 @@ int dsmc32_threads() { return kDsmcThreads; }
 const void* dsmc32_kernel_ptr(bool verify) {
   return verify ? (const void*)k_dsmc32<true> : (const void*)k_dsmc32<false>;
 }
-int cg32_threads() { return kThreads; }
+int cg32_threads() { return kCgThreads; }
 const void* cg32_kernel_ptr() { return (const void*)k_cg32; }
 
 cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate) {
@@ -1096,7 +1224,7 @@ cudaError_t launch_cg32(pic_ctx* c) {
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
   prof_begin(c);
-  e = cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(c->cg_grid), dim3(kThreads), args, 0, c->stream);
+  e = cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(c->cg_grid), dim3(kCgThreads), args, 0, c->stream);
   prof_end(c, KC_CG);
   c->launches++;
   if (e != cudaSuccess) return e;

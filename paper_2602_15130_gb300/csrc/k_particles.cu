@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
   const int n = P.n;
   const int32_t k = cell_coord(x[0], n) + n * (cell_coord(x[1], n) + n * cell_coord(x[2], n));
   a.key[j] = k;
-  a.rank[j] = atomicAdd(a.count + k, 1);
+  a.rank[j] = cell_slot(a.count, k);
 }
 
 // --------------------------------------------------------------------------

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_keys(KeysArgs a) {
   const int n = a.n;
   const int32_t k = cell_coord(a.x0[j], n) + n * (cell_coord(a.x1[j], n) + n * cell_coord(a.x2[j], n));
   a.key[j] = k;
-  a.rank[j] = atomicAdd(a.count + k, 1);
+  a.rank[j] = cell_slot(a.count, k);
 }
 
 // block-wide exclusive scan of one int per thread; returns the block total

@@ -99,6 +99,19 @@ __device__ __forceinline__ float xm_y_f(const ParamsF& P, const TimeTermsF& tt, 
   return y - (y - P.fx_a2pi * c - T) / (1.f + P.fx_amp * s);
 }
 
+// 32 x 32 bit-matrix transpose across a warp: lane r holds row r on entry
+// and column r on return (bit c of row r becomes bit r of column c). Five
+// exchange stages swap the off-diagonal blocks of size 16, 8, 4, 2, 1.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  uint32_t m = 0x0000FFFFu;
+#pragma unroll
+  for (int j = 16; j != 0; j >>= 1, m ^= m << j) {
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+  }
+  return x;
+}
+
 // FP32 form of record_angles (Sec. 4.4)
 __device__ __forceinline__ void record_angles_f(unsigned long long* hist, bool aniso, float g, float gx, float gy,
                                                 float gz) {

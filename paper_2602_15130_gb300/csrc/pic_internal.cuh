@@ -297,6 +297,21 @@ __device__ __forceinline__ void record_angles(unsigned long long* hist, bool ani
   atomicAdd(hist + PIC_ANGLE_BINS + angle_bin(e / kTwoPi), 1ull);
 }
 
+// Slot of one particle in its cell's count: lanes of a warp with the same
+// key share one atomic (particles arrive sorted by cell, so a warp covers
+// one or two cells); the ranks inside a cell are a permutation of
+// 0..count-1 in any order (the in-cell pid sort fixes the final order).
+__device__ __forceinline__ int32_t cell_slot(int32_t* count, int32_t key) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int32_t base = 0;
+  if (lane == leader) base = atomicAdd(count + key, __popc(peers));
+  base = __shfl_sync(act, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 __device__ __forceinline__ double wrap_unit(double x) {
   double y = x - floor(x);
   return y >= 1.0 ? 0.0 : y;
