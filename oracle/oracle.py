@@ -60,6 +60,7 @@ class OrcCfg(ctypes.Structure):
         ("phi_shift", ctypes.c_double * 3),
         ("cg_tol", ctypes.c_double),
         ("verify", ctypes.c_int64),
+        ("E_app", ctypes.c_double * 3),
     ]
 
 
@@ -131,6 +132,7 @@ def lib():
                                               ctypes.c_int64, _D]),
             "orc_angle_count": (ctypes.c_int64, [ctypes.c_void_p]),
             "orc_aniso_F": (ctypes.c_double, [ctypes.c_double]),
+            "orc_objective": (None, [ctypes.c_void_p, _D]),
             "orc_aniso_u": (ctypes.c_double, [ctypes.c_double]),
             "orc_get_angles": (None, [ctypes.c_void_p, _D]),
         }
@@ -180,6 +182,8 @@ def make_cfg(p: dict) -> OrcCfg:
     c.phi_T = float(p.get("phi_T", 1.0))
     c.cg_tol = float(p.get("cg_tol", 1e-13))
     c.verify = int(p.get("verify", 0))
+    for d in range(3):
+        c.E_app[d] = float(p.get("E_app", (0.0, 0.0, 0.0))[d])
     return c
 
 
@@ -276,6 +280,12 @@ class Oracle:
 
     def reset_stats(self):
         self.L.orc_reset_stats(self.h)
+
+    def objective(self) -> np.ndarray:
+        """(J, J_field, J_vel) at the current state."""
+        out = np.zeros(3)
+        self.L.orc_objective(self.h, _dp(out))
+        return out
 
     def angles(self) -> np.ndarray:
         """(chi, eps) of every recorded collision, ``[N_coll, 2]``."""

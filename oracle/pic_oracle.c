@@ -59,6 +59,7 @@ typedef struct {
                     *  16  manufactured anisotropic scattering (Sec. 5.1):
                     *      p_chi = (29/2 + 12 cos chi - 20 cos^3 chi)
                     *      sin chi / 29 in place of sin chi / 2           */
+  double E_app[3];   /* uniform applied field added to E_p in the push      */
 } orc_cfg;
 
 #define ORC_ISOLATE 1
@@ -780,7 +781,7 @@ static void lorentz_term(orc_state* s, double t, double* out) {
     double Ep[3], EMp[3];
     orc_gather(cf, s->E, s->x + 3 * p, Ep);
     orc_EM(cf, s->x + 3 * p, t, EMp);
-    for (int d = 0; d < 3; d++) out[3 * p + d] = cf->dt * qm * (Ep[d] - EMp[d]);
+    for (int d = 0; d < 3; d++) out[3 * p + d] = cf->dt * qm * (Ep[d] + cf->E_app[d] - EMp[d]);
   }
 }
 
@@ -873,6 +874,23 @@ void orc_errors(const orc_state* s, double out[14]) {
   for (int a = 0; a < 6; a++) out[a] = sqrt(s2[a] / (double)cf->np);
   out[6] = sqrt(s2[6] / (double)(n * n * n));
   for (int a = 0; a < 7; a++) out[7 + a] = mx[a];
+}
+
+/* Objective of the pathwise-gradient study: out[1] = field energy
+ * (eps0/2) h^3 sum_nodes |E|^2, out[2] = mean-square velocity error
+ * (1/N_p) sum_p |v_p - v_p^M|^2, out[0] = their sum.                      */
+void orc_objective(const orc_state* s, double out[3]) {
+  const orc_cfg* cf = &s->c;
+  double h = 1.0 / (double)cf->n, ef = 0.0, ev = 0.0;
+  for (int64_t i = 0; i < 3 * ncell(cf); i++) ef += s->E[i] * s->E[i];
+  for (int64_t p = 0; p < cf->np; p++)
+    for (int d = 0; d < 3; d++) {
+      double e = s->v[3 * p + d] - orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+      ev += e * e;
+    }
+  out[1] = 0.5 * cf->eps0 * h * h * h * ef;
+  out[2] = ev / (double)cf->np;
+  out[0] = out[1] + out[2];
 }
 
 /* ------------------------------------------------------------------------

@@ -280,3 +280,36 @@ def test_aniso_angles_converge_and_error2_does_not():
     assert 0.025 < einf2 < 0.045
     _, e_eps = O.angle_cdf_errors(ang2[:, 1], O.F_eps)
     assert e_eps * math.sqrt(len(ang2)) < 2.0
+
+
+# --------------------------------------------------------------- objective --
+def test_objective_is_field_energy_plus_velocity_error():
+    """J_field = (eps0/2) h^3 sum |E|^2 over the nodes and J_vel = sum of the
+    squared eps_2 of u, v, w (Sec. 4.3 norms), after a few steps with an
+    applied field."""
+    p = dict(W.smallest(), E_app=(0.1, -0.2, 0.05))
+    o = O.Oracle(p)
+    o.sample()
+    o.step(3)
+    J = o.objective()
+    _, _, E = o.field()
+    h = 1.0 / p["n"]
+    assert abs(J[1] - 0.5 * h ** 3 * (E ** 2).sum()) <= 1e-14 * J[1]
+    e = o.errors()
+    assert abs(J[2] - (e[3:6] ** 2).sum()) <= 1e-12 * J[2]
+    assert J[0] == J[1] + J[2]
+
+
+def test_applied_field_enters_the_push():
+    """With q/m = 1 a uniform E_app changes every velocity after one step
+    by dt E_app (two half kicks); the shifted drift moves x by dt^2 E_app/2,
+    which changes the gathered fields at second order only."""
+    base = W.smallest(K=0, couple_q_zero=1)
+    a, b = O.Oracle(base), O.Oracle(dict(base, E_app=(0.3, 0.0, -0.1)))
+    for o in (a, b):
+        o.sample()
+        o.step(1)
+    _, va = a.state()
+    _, vb = b.state()
+    shift = np.array([0.3, 0.0, -0.1]) * base["dt"]
+    assert np.abs(vb - va - shift).max() < 1e-6 < np.abs(shift).max()
