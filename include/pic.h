@@ -266,6 +266,31 @@ pic_status pic_get_stats(pic_ctx* ctx, pic_stats* out);
 /* Zero the counters of pic_stats and the recorded scattering angles. */
 pic_status pic_reset_stats(pic_ctx* ctx);
 
+/* Pathwise gradient (an extension of the method; the paper has no adjoint):
+ * runs nsteps FP64 steps from x^M(0) and the velocities v0 with a uniform
+ * applied field E_app in the push, L = dt q/m (E_p + E_app - E^M_p), and
+ * returns at t_N
+ *   J[1] = (eps0/2) h^3 sum_nodes |E|^2,  J[2] = (1/N_p) sum_p |v_p - v_p^M|^2,
+ *   J[0] = J[1] + J[2];
+ * when dJ_dEapp or dJ_dv0 is non-NULL, also the gradient of J[0] by a
+ * hand-written adjoint of gather, push, CIC deposit, the Poisson solve and
+ * the K-averaged collisions with candidate pairs, accept decisions and
+ * scattering directions frozen at their sampled values (a pathwise
+ * derivative). Checkpoints (x, v, phi, E) every `every` steps; each segment
+ * is recomputed bit-identically and swept in reverse, so the result does not
+ * depend on `every`. Arguments: ctx an FP64 single context (PIC_EINVAL for
+ * the precision form, a batch, or the injected-error switches); E_app 3
+ * doubles, host (NULL = 0); v0 [N_p][3] in pid order, host or device (NULL =
+ * v^M(0)); J 3 doubles, host; dJ_dEapp 3 doubles, host, or NULL; dJ_dv0
+ * [N_p][3], host or device, or NULL. The working set (about 24 N_p bytes x
+ * (3 every + 2 ceil(nsteps/every) + 6), plus collision overlays) comes from
+ * the context's allocator on first use and is kept. With a gradient the
+ * context's particle state afterwards is unspecified (pic_step returns
+ * PIC_ESTATE until pic_sample_mms or pic_set_state); without one it holds
+ * t_N. PIC_ECAPACITY if an outcome recorded more than 64 accepted pairs. */
+pic_status pic_adjoint_gradient(pic_ctx* ctx, int32_t nsteps, int32_t every, const double E_app[3],
+                                const double* v0, double J[3], double dJ_dEapp[3], double* dJ_dv0);
+
 /* Angle CDF errors (pic_angle_stats) of the recorded collisions; computed by
  * kernels on the context stream, then synchronised. PIC_ESTATE when the
  * context was created without PIC_VERIFY_ANGLES. */

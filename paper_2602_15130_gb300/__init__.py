@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib, workloads
 from ._lib import PicConfig, PicError, check, load
 
-__all__ = ["Pic", "Batch", "PicConfig", "PicError", "make_config", "workloads", "load"]
+__all__ = ["Pic", "Batch", "PicConfig", "PicError", "PicObjective", "make_config", "workloads", "load"]
 
 
 def make_config(p: dict) -> PicConfig:
@@ -188,6 +188,27 @@ class Pic:
     def reset_stats(self):
         check(self.L.pic_reset_stats(self.ctx), "pic_reset_stats")
 
+    def adjoint_gradient(self, nsteps: int, every: int = 20, E_app=(0.1, 0.1, 0.1), v0=None, grad: bool = True):
+        """Objective J = J_field + J_vel at t_N and, with ``grad``, its
+        pathwise gradient (dJ/dE_app [3], dJ/dv0 [N_p, 3]) by the library's
+        adjoint (pic_adjoint_gradient). v0: [N_p, 3] pid order (numpy or a
+        CUDA tensor), None for v^M(0)."""
+        J = (ctypes.c_double * 3)()
+        ea = (ctypes.c_double * 3)(*[float(x) for x in E_app])
+        dE = (ctypes.c_double * 3)() if grad else None
+        dv = np.zeros((self.np, 3)) if grad else None
+        if v0 is not None and isinstance(v0, np.ndarray):
+            v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        pv, kv = _ptr(v0)
+        pd, kd = _ptr(dv)
+        check(self.L.pic_adjoint_gradient(self.ctx, int(nsteps), int(every), ea, pv, J, dE, pd),
+              "pic_adjoint_gradient")
+        out = {"J": J[0], "J_field": J[1], "J_vel": J[2]}
+        if grad:
+            out["dJ_dEapp"] = np.array(list(dE))
+            out["dJ_dv0"] = dv
+        return out
+
     def angle_stats(self) -> dict:
         """Scattering-angle CDF errors of the recorded collisions (needs
         ``verify`` with PIC_VERIFY_ANGLES)."""
@@ -257,3 +278,34 @@ def derived(params: dict) -> dict:
     out = (ctypes.c_double * 5)()
     check(L.pic_derived(ctypes.byref(c), out), "pic_derived")
     return {"w": out[0], "dV": out[1], "pmax": out[2], "ppc": out[3], "inv_pmax": out[4]}
+
+
+
+try:
+    import torch as _torch
+except ImportError:  # pragma: no cover - the library needs torch for its allocator
+    _torch = None
+
+if _torch is not None:
+
+    class PicObjective(_torch.autograd.Function):
+        """J(E_app, v0) of ``Pic.adjoint_gradient`` as an autograd function:
+        forward runs the library's simulation with checkpoints and its
+        hand-written pathwise adjoint; backward scales the stored gradient.
+        Call as ``PicObjective.apply(E_app, v0, sim, nsteps, every)``."""
+
+        @staticmethod
+        def forward(ctx, E_app, v0, sim, nsteps, every):
+            e = [float(x) for x in E_app.detach().cpu().tolist()]
+            v = v0.detach().to(_torch.float64).contiguous()
+            r = sim.adjoint_gradient(nsteps, every, e, v if v.is_cuda else v.numpy(), grad=True)
+            ctx.save_for_backward(_torch.as_tensor(r["dJ_dEapp"], dtype=E_app.dtype, device=E_app.device),
+                                  _torch.as_tensor(r["dJ_dv0"], dtype=v0.dtype, device=v0.device))
+            return _torch.tensor(r["J"], dtype=_torch.float64, device=E_app.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            dE, dv = ctx.saved_tensors
+            return g * dE, g * dv, None, None, None
+else:  # pragma: no cover
+    PicObjective = None

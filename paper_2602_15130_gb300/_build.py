@@ -15,7 +15,7 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build_objs"
 LIB = PKG / "libpic_gb300.so"
-SOURCES = ["pic_api.cu", "k_particles.cu", "k_sort.cu", "k_field.cu", "k_mixed.cu", "k_batch.cu", "k_angles.cu"]
+SOURCES = ["pic_api.cu", "k_particles.cu", "k_sort.cu", "k_field.cu", "k_mixed.cu", "k_batch.cu", "k_angles.cu", "k_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = [
     "-O3", "-std=c++17", "-lineinfo", *ARCH,
@@ -40,7 +40,7 @@ def _stale(target: Path, deps) -> bool:
 
 def build_library(force: bool = False, verbose: bool = False) -> Path:
     BUILD.mkdir(exist_ok=True)
-    headers = [CSRC / "pic_internal.cuh", CSRC / "mixed_common.cuh", PKG.parent / "include" / "pic.h"]
+    headers = [CSRC / "pic_internal.cuh", CSRC / "mixed_common.cuh", CSRC / "ntc_fp64.cuh", PKG.parent / "include" / "pic.h"]
     cc = nvcc()
     jobs = []
     for src in SOURCES:

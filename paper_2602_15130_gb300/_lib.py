@@ -123,6 +123,7 @@ SIGNATURES = {
     "pic_get_stats": (_S, [_V, ctypes.POINTER(PicStats)]),
     "pic_reset_stats": (_S, [_V]),
     "pic_get_angle_stats": (_S, [_V, ctypes.POINTER(PicAngleStats)]),
+    "pic_adjoint_gradient": (_S, [_V, ctypes.c_int32, ctypes.c_int32, _D, _V, _D, _D, _V]),
     "pic_set_profiling": (_S, [_V, ctypes.c_int32]),
     "pic_get_kernel_times": (_S, [_V, ctypes.POINTER(PicKernelTimes)]),
     "pic_destroy": (None, [_V]),

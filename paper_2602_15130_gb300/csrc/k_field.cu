@@ -388,20 +388,21 @@ cudaError_t launch_rhs(pic_ctx* c, double t) {
 int cg_threads() { return kCgThreads; }
 const void* cg_kernel_ptr() { return (const void*)k_cg; }
 
-cudaError_t launch_cg(pic_ctx* c) {
+cudaError_t launch_cg_on(pic_ctx* c, double* b, double* x, const double* rhs_part, int rhs_blocks, double* E0,
+                         double* E1, double* E2) {
   CgArgs a;
   a.n = c->P.n;
   a.ncell = c->P.ncell;
   a.inv_h2 = (double)c->P.n * (double)c->P.n;
   a.two_h = 2.0 * c->P.h;
-  a.b = c->b;
-  a.x = c->phi;
+  a.b = b;
+  a.x = x;
   a.r = c->cg_r;
   a.p0 = c->cg_p[0];
   a.p1 = c->cg_p[1];
   a.q = c->cg_q;
-  a.rhs_part = c->rhs_part;
-  a.rhs_blocks = (int)c->rhs_blocks;
+  a.rhs_part = rhs_part;
+  a.rhs_blocks = rhs_blocks;
   a.red = c->cg_red;
   a.bar = c->cg_bar;
   a.info = c->cg_info;
@@ -409,9 +410,9 @@ cudaError_t launch_cg(pic_ctx* c) {
   a.res = c->cg_res;
   a.tol = c->cfg.cg_tol;
   a.maxit = c->cfg.cg_maxit;
-  a.E0 = c->E[0];
-  a.E1 = c->E[1];
-  a.E2 = c->E[2];
+  a.E0 = E0;
+  a.E1 = E1;
+  a.E2 = E2;
   cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c->cg_info, 0, 3 * sizeof(int), c->stream);
@@ -423,6 +424,10 @@ cudaError_t launch_cg(pic_ctx* c) {
   c->launches++;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+cudaError_t launch_cg(pic_ctx* c) {
+  return launch_cg_on(c, c->b, c->phi, c->rhs_part, (int)c->rhs_blocks, c->E[0], c->E[1], c->E[2]);
 }
 
 cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E) {

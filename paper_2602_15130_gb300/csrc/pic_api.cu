@@ -430,6 +430,36 @@ pic_status batch_step(pic_ctx* c, int64_t n, bool coll) {
 
 }  // namespace
 
+namespace pic {
+
+void* ctx_alloc(pic_ctx* c, size_t bytes) { return dev_alloc(c, bytes); }
+void ctx_free(pic_ctx* c, void* p) { dev_free(c, p); }
+
+// One FP64 step of Eq. velocity_verlet. hook(where), if given, runs at
+// 0: the start (x^n, v^n in the current buffers), 1: after the drift and the
+// sort (x^{n+1}, v^{n+1/2}), 2: after the field solve (E^{n+1}).
+cudaError_t step_fp64(pic_ctx* c, int64_t n, const StepHook* hook) {
+  const bool coll = c->cfg.K > 0;
+  const double tn = time_at(c, (double)n), th = time_at(c, (double)n + 0.5), tn1 = time_at(c, (double)(n + 1));
+  cudaError_t e;
+  if (hook && (e = (*hook)(0)) != cudaSuccess) return e;
+  // v^{n+1/2} and x^{n+1}: collision call A at (x^n, v^n)
+  if (coll && (e = launch_dsmc(c, (uint32_t)(2 * n), false)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream)) != cudaSuccess) return e;
+  if ((e = launch_kick(c, tn, coll, true, th, tn1)) != cudaSuccess) return e;
+  // cells of x^{n+1}, field at t^{n+1}
+  if ((e = launch_sort(c)) != cudaSuccess) return e;
+  if (hook && (e = (*hook)(1)) != cudaSuccess) return e;
+  if ((e = launch_rhs(c, tn1)) != cudaSuccess) return e;
+  if ((e = launch_cg(c)) != cudaSuccess) return e;
+  if (hook && (e = (*hook)(2)) != cudaSuccess) return e;
+  // v^{n+1}: collision call B at (x^{n+1}, v^{n+1/2})
+  if (coll && (e = launch_dsmc(c, (uint32_t)(2 * n + 1), false)) != cudaSuccess) return e;
+  return launch_kick(c, tn1, coll, false, 0.0, 0.0);
+}
+
+}  // namespace pic
+
 extern "C" {
 
 pic_status pic_config_default(pic_config* cfg) {
@@ -499,6 +529,7 @@ pic_status pic_derived(const pic_config* cfg, double out[5]) {
 
 void pic_destroy(pic_ctx* c) {
   if (!c) return;
+  adjoint_free(c);
   for_each_buffer(c, [&](void** p, size_t) {
     dev_free(c, *p);
     *p = nullptr;
@@ -715,17 +746,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
       if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n + 1), false));
       CK(launch_kick32(c, tn1, coll, false, 0.0, 0.0));
     } else {
-      // v^{n+1/2} and x^{n+1}: collision call A at (x^n, v^n)
-      if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n), false));
-      CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-      CK(launch_kick(c, tn, coll, true, th, tn1));
-      // cells of x^{n+1}, field at t^{n+1}
-      CK(launch_sort(c));
-      CK(launch_rhs(c, tn1));
-      CK(launch_cg(c));
-      // v^{n+1}: collision call B at (x^{n+1}, v^{n+1/2})
-      if (coll) CK(launch_dsmc(c, (uint32_t)(2 * n + 1), false));
-      CK(launch_kick(c, tn1, coll, false, 0.0, 0.0));
+      CK(step_fp64(c, n, nullptr));
     }
     c->step = n + 1;
   }

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <climits>
+#include <functional>
 #include <stdint.h>
 
 #include "../../include/pic.h"
@@ -42,6 +43,7 @@ struct Params {
   int ginv_M;
   int verify;                      // PIC_VERIFY_* bits
   unsigned long long* ang_hist;    // [2][PIC_ANGLE_BINS] when recording angles
+  double E_app[3];                 // uniform applied field in the push (adjoint parameter; 0 otherwise)
 };
 
 
@@ -323,6 +325,10 @@ __device__ __forceinline__ double wrap_unit(double x) {
 // Context (host side). Device arrays are structure-of-arrays, sorted by
 // (cell, pid); two copies of every per-particle array for the sort.
 // ---------------------------------------------------------------------------
+namespace pic {
+struct AdjointBuffers;
+}
+
 struct pic_ctx {
   pic_config cfg;
   pic::Params P;
@@ -395,6 +401,7 @@ struct pic_ctx {
   int dsmc_grid, dsmc_block, dsmc_G, dsmc_Kc, bm_words;
   int64_t dsmc_groups;
   size_t dsmc_smem;
+  pic::AdjointBuffers* adj;      // pathwise-adjoint working set, allocated on first use
   unsigned long long* counters;  // n_cand, n_coll, n_gmax, n_tie
   // recorded scattering angles (PIC_VERIFY_ANGLES): histograms of F^M(chi)
   // and eps/(2 pi), and the scratch of their CDF-error reduction
@@ -470,6 +477,12 @@ cudaError_t launch_keys(pic_ctx* c);
 cudaError_t launch_sort(pic_ctx* c);            // scan + scatter + in-cell sort + gather + CIC
 cudaError_t launch_rhs(pic_ctx* c, double t);
 cudaError_t launch_cg(pic_ctx* c);             // CG + zero-mean + E
+// the FP64 CG on caller buffers: solves -Lap_h x = b - mean(b) (warm start
+// from x, mean removed from x) and writes E = -grad_h x
+cudaError_t launch_cg_on(pic_ctx* c, double* b, double* x, const double* rhs_part, int rhs_blocks, double* E0,
+                         double* E1, double* E2);
+using StepHook = std::function<cudaError_t(int)>;
+cudaError_t step_fp64(pic_ctx* c, int64_t n, const StepHook* hook);
 cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate_source);
 // kick at time tE; drift to th if drift. Reuses / refreshes c->lor.
 cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift, double th, double tn1);
@@ -498,6 +511,10 @@ cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate_source);
 cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_collisions, bool drift, double th, double tn1);
 // angle CDF errors of the recorded collisions into out (synchronises)
 cudaError_t launch_angle_stats(pic_ctx* c, pic_angle_stats* out);
+// device memory through the context's allocator; adjoint buffers (k_adjoint.cu)
+void* ctx_alloc(pic_ctx* c, size_t bytes);
+void ctx_free(pic_ctx* c, void* p);
+void adjoint_free(pic_ctx* c);
 cudaError_t launch_cg32(pic_ctx* c);
 cudaError_t launch_errors32(pic_ctx* c, double t);
 cudaError_t launch_store_state32(pic_ctx* c, double* xv_dev, int32_t* cell_of_pid);

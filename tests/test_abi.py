@@ -70,6 +70,8 @@ def test_verification_switches_validate(L):
         c = make_config(dict(workloads.smallest(), verify=bits))
         assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_OK
     assert L.pic_get_angle_stats(None, None) == _lib.PIC_EINVAL
+    J = (ctypes.c_double * 3)()
+    assert L.pic_adjoint_gradient(None, 1, 1, None, None, J, None, None) == _lib.PIC_EINVAL
     # header constants agree with the binding
     text = _lib.HEADER.read_text()
     for name in ("PIC_VERIFY_ISOLATE", "PIC_VERIFY_ERROR1", "PIC_VERIFY_ERROR2", "PIC_VERIFY_ANGLES",
