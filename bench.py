@@ -50,6 +50,8 @@ def workload(name: str) -> dict:
         return W.refinement_level(int(name[6:]))
     if name == "smallest":
         return W.smallest()
+    if name == "adjoint":
+        return W.differentiation()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -334,6 +336,70 @@ def run_batched(args, rank: int, world: int) -> dict | None:
     }
 
 
+def run_adjoint(args) -> dict:
+    """One pathwise gradient of J (field energy + velocity error at t_N)
+    with respect to E_app and v0 on the differentiation workload (collisions
+    on, pairs frozen), timed with CUDA events after a warm-up gradient. With
+    collisions, J is discontinuous in E_app at this size (a 1e-6 change
+    moves cell memberships and with them whole cells' pair draws), so the
+    central-difference check (h = 1e-6) of dJ/dE_app runs on the same
+    workload without collisions, where J is smooth."""
+    import numpy as np
+    import torch
+
+    from paper_2602_15130_gb300 import Pic
+
+    torch.cuda.set_device(0)
+    p = workload("adjoint")
+    steps, every, E = p["steps"], p["checkpoint_every"], tuple(p["E_app"])
+    sim = Pic(p)
+    sim.adjoint_gradient(steps, every, E)  # warm-up: allocates the working set
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record()
+        r = sim.adjoint_gradient(steps, every, E)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ev0.record()
+    sim.adjoint_gradient(steps, every, E, grad=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_fwd = ev0.elapsed_time(ev1)
+    st = sim.stats()
+    sim.close()
+    del sim
+    # central differences without collisions
+    p0 = dict(p, K=0)
+    s0 = Pic(p0)
+    r0 = s0.adjoint_gradient(steps, every, E)
+    fd = []
+    for d in range(3):
+        ep, em = list(E), list(E)
+        ep[d] += 1e-6
+        em[d] -= 1e-6
+        jp = s0.adjoint_gradient(steps, every, ep, grad=False)["J"]
+        jm = s0.adjoint_gradient(steps, every, em, grad=False)["J"]
+        fd.append((jp - jm) / 2e-6)
+    g0 = r0["dJ_dEapp"]
+    return {
+        "metric": "pathwise gradient of J(E_app, v0): particle-steps/s (forward with checkpoints + adjoint)",
+        "value": p["n_particles"] * steps / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1,
+        "steps": steps, "warmup": 1, "ms_per_gradient": ms, "ms_forward_only": ms_fwd,
+        "gradient_over_forward": ms / ms_fwd, "higher_is_better": True, "dtype": "f64",
+        "data": "synthetic manufactured-solution workload",
+        "config": {"workload": describe("adjoint", p), "n": p["n"], "n_particles": p["n_particles"], "K": p["K"],
+                   "dt": p["dt"], "steps": steps, "checkpoint_every": every, "E_app": list(E)},
+        "J": r["J"], "J_field": r["J_field"], "J_vel": r["J_vel"], "dJ_dEapp": [float(x) for x in r["dJ_dEapp"]],
+        "dJ_dv0_rms": float(np.sqrt(np.mean(r["dJ_dv0"] ** 2))),
+        "stats": {"n_coll": st["n_coll"], "n_gmax_exceed": st["n_gmax_exceed"], "cg_iters_max": st["cg_iters_max"]},
+        "fd_check_collisionless": {"J": r0["J"], "dJ_dEapp": [float(x) for x in g0], "fd": fd,
+                                   "rel_err": [abs(g0[d] - fd[d]) / max(abs(fd[d]), 1e-300) for d in range(3)]},
+        "clocks": clk.summary(),
+    }
+
+
 # ------------------------------------------------------------ CPU oracle ----
 def oracle_sample_params(args) -> tuple[dict, str]:
     from paper_2602_15130_gb300 import workloads as W
@@ -414,6 +480,10 @@ def main():
         import torch.distributed as td
 
         td.barrier()
+    if args.workload == "adjoint":
+        if rank == 0:
+            print(json.dumps(run_adjoint(args)), flush=True)
+        return
     if args.workload == "batched":
         out = run_batched(args, rank, world)
         if out is not None:

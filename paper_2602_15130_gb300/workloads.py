@@ -118,6 +118,24 @@ def precision_form(**kw) -> dict:
     return p
 
 
+DIFF_COLL_PER_CALL = 0.005
+
+
+def differentiation(**kw) -> dict:
+    """Pathwise-gradient study: 64^3 cells, 64 particles per cell
+    (16,777,216), 200 steps of dt = 0.005, K = 8, FP64, applied field
+    E_app = (0.1, 0.1, 0.1), checkpoints every 20 steps. sigma0 gives 0.005
+    expected collisions per particle per call: at 0.02 and above, K = 8
+    leaves a collision error that grows until velocities pass g_max and run
+    away within the 200 steps (the saturated-NTC runaway of the fixed-ppc
+    sweep). CG is capped at 2000 iterations so a diverging run stops."""
+    n, ppc, dt = 64, 64, 0.005
+    p = base(n, ppc * n ** 3, dt, 8, hard_sphere_sigma0(ppc, dt, DIFF_COLL_PER_CALL), steps=200,
+             E_app=(0.1, 0.1, 0.1), checkpoint_every=20, cg_maxit=2000)
+    p.update(kw)
+    return p
+
+
 def mixed(p: dict) -> dict:
     """The same workload in the precision form."""
     q = dict(p)
