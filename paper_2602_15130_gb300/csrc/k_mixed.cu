@@ -216,11 +216,14 @@ __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a
         for (int q = 0; q < 9; ++q) d1[q] = a.in[q][src1];
       }
       int r0 = 0, r1 = 0;
-      const int lim = min(32, cnt);
-      for (int l = 0; l < lim; ++l) {
-        const uint32_t x0 = __shfl_sync(0xffffffffu, p0, l), x1 = __shfl_sync(0xffffffffu, p1, l);
-        r0 += (x0 < p0) + (x1 < p0);
-        r1 += (x0 < p1) + (x1 < p1);
+      if (cnt <= 32) {
+        for (int l = 0; l < cnt; ++l) r0 += __shfl_sync(0xffffffffu, p0, l) < p0 ? 1 : 0;
+      } else {
+        for (int l = 0; l < 32; ++l) {
+          const uint32_t x0 = __shfl_sync(0xffffffffu, p0, l), x1 = __shfl_sync(0xffffffffu, p1, l);
+          r0 += (x0 < p0) + (x1 < p0);
+          r1 += (x0 < p1) + (x1 < p1);
+        }
       }
       if (h0) {
         const int32_t dst = s + r0;
@@ -437,7 +440,7 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
 constexpr int kDsmcThreads = 128;
 
 template <bool kVerify>
-__global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
+__global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
   extern __shared__ uint32_t smem[];
   const ParamsF& P = a.P;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
