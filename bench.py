@@ -120,6 +120,15 @@ def measured_peaks() -> dict:
 # Algorithmic HBM bytes per unit for each kernel class of one step. Units:
 # particles for the particle kernels, nodes x CG iterations for the CG. The
 # derivations are listed in the design doc (data layout and roofline section).
+# Philox4x32-10: 10 rounds of two 32x32->64 products (4 ops), four xors and
+# two key additions; GB300 issues 64 INT32 lanes per SM per clock.
+INT_OPS_PER_PHILOX = 100
+INT32_LANES_PER_SM = 64
+# DRAM bytes per particle of one k_dsmc32 launch (read 204 MB + write 124 MB
+# for 8,388,608 particles at 32 per cell, K = 16), from the capture summarised
+# in profiles/ncu_full_mixed_refine3.md; valid while that kernel is unchanged
+NCU_DSMC32_DRAM_BYTES_PER_PARTICLE = (204e6 + 124e6) / 8388608
+
 BYTES_PER_UNIT = {
     "fp64": {
         "kick_drift": (228 + 120) / 2.0,   # mean of the drift (228 B) and closing (120 B) kick launches
@@ -248,6 +257,30 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
     # dominant kernel class by device time inside the timed region
     dom = max(kt, key=lambda k: kt[k]["ms"])
     achieved = hbm_gbs(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+            "bytes_per_unit": bpu.get(dom), "units_per_launch": units_of(dom)}
+    if dom == "dsmc":
+        # integer-ALU bound: the Philox4x32-10 blocks the method draws per
+        # launch (one per (cell, outcome) lane for N_pairs, one per candidate
+        # pair, one more per accepted pair) at INT_OPS_PER_PHILOX each,
+        # against INT32_LANES_PER_SM x SMs x the sampled maximum SM clock
+        nl = max(1, kt["dsmc"]["launches"])
+        blocks = p["n"] ** 3 * p["K"] + (st["n_cand"] + st["n_coll"]) / nl
+        ops = blocks * INT_OPS_PER_PHILOX
+        per_launch_s = kt["dsmc"]["ms"] / nl / 1000.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.summary().get("sm_max_mhz") or 2070.0
+        peak = INT32_LANES_PER_SM * sms * mhz * 1e6
+        traffic = (NCU_DSMC32_DRAM_BYTES_PER_PARTICLE * npart
+                   if form == "mixed" and (p["n"], p["K"]) == (128, 16) else None)
+        roof = {"bound": "alu", "kernel": "dsmc", "achieved": ops / per_launch_s / 1e12, "peak": peak / 1e12,
+                "unit": "Tops/s (INT32)", "frac": ops / per_launch_s / peak, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read+write of k_dsmc32 at 64^3 (8.4M particles, K=16), "
+                                  "scaled by particles; profiles/ncu_full_mixed_refine3.md",
+                "peak_source": "derived: %d INT32 lanes/SM x %d SMs x %.0f MHz" % (INT32_LANES_PER_SM, sms, mhz),
+                "ops_per_launch": ops, "philox_blocks_per_launch": blocks,
+                "hbm_frac_of_measured": round(achieved / peaks["hbm_gbs"], 4)}
     step_kernels = {k: {"ms_per_launch": round(kt[k]["ms"] / max(1, kt[k]["launches"]), 4),
                         "bytes_per_unit": bpu[k], "achieved_gbs": round(hbm_gbs(k), 1),
                         "frac_of_measured_hbm": round(hbm_gbs(k) / peaks["hbm_gbs"], 4)}
@@ -265,9 +298,7 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
                 "h2d_bytes_per_step": npart * 48, "d2h_bytes_per_step": npart * 48,
                 "path": "pic_set_state(host) + pic_step(1) + pic_get_state(host), pinned buffers"},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "peak_source": peaks["source"], "bytes_per_unit": bpu.get(dom), "units_per_launch": units_of(dom)},
+        "roofline": roof,
         "step_kernels_hbm": step_kernels,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items()},
         "kernel_launches_by_class": {k: v["launches"] for k, v in kt.items()},
