@@ -143,30 +143,25 @@ struct CgArgs {
   double *E0, *E1, *E2;
 };
 
-// Sense-free generation barrier for a cooperative grid, bounded in time.
+// Grid barrier for a cooperative grid, bounded in time.
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* info, int* flags) {
+  // monotonic arrival counter (zero at launch): the k-th barrier of the
+  // launch is passed once the counter reaches k gridDim.x; the wait is
+  // bounded, after which the timeout flag is set and every block returns
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = bar + 1;
-    const unsigned int g = *gen;
     __threadfence();
     const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+    const unsigned int target = (arrived + gridDim.x - 1u) / gridDim.x * gridDim.x;
     ok = 1;
-    if (arrived == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g) {
-        if (clock64() - t0 > kBarrierCycles) {
-          atomicOr(info + 2, 1);
-          atomicOr(flags, 4);
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
+    const long long t0 = clock64();
+    while (*(volatile unsigned int*)bar < target) {
+      if (clock64() - t0 > kBarrierCycles) {
+        atomicOr(info + 2, 1);
+        atomicOr(flags, 4);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
