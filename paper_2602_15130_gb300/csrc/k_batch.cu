@@ -369,7 +369,7 @@ __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint
 
 constexpr int kDsmcThreads = 128;
 
-__global__ void __launch_bounds__(kDsmcThreads, 6) kb_dsmc(BDsmcArgs a) {
+__global__ void __launch_bounds__(kDsmcThreads, 7) kb_dsmc(BDsmcArgs a) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
