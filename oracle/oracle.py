@@ -61,6 +61,11 @@ class OrcCfg(ctypes.Structure):
         ("cg_tol", ctypes.c_double),
         ("verify", ctypes.c_int64),
         ("E_app", ctypes.c_double * 3),
+        ("dist", ctypes.c_int64),
+        ("n_sigma", ctypes.c_int64),
+        ("sigma_n", ctypes.c_double * 3),
+        ("vbar", ctypes.c_double),
+        ("t_ref", ctypes.c_double),
     ]
 
 
@@ -70,6 +75,10 @@ ERROR1 = 2
 ERROR2 = 4
 ANGLES = 8
 ANISO = 16
+
+# manufactured-distribution forms (``dist``)
+DIST_CONFIG = 0   # travelling-wave f_x, Gaussian f_v
+DIST_PAPER = 1    # the paper's own problem of Sec. 5.2 on the unit cube
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -135,6 +144,20 @@ def lib():
             "orc_objective": (None, [ctypes.c_void_p, _D]),
             "orc_aniso_u": (ctypes.c_double, [ctypes.c_double]),
             "orc_get_angles": (None, [ctypes.c_void_p, _D]),
+            "orc_fx_terms": (None, [_CFG, ctypes.c_int, ctypes.c_double, _D]),
+            "orc_fx": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_Fx": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_xM_d": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_xMdot_d": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_vhat": (None, [_CFG, ctypes.c_double, _D, _D]),
+            "orc_fv_paper": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_Fv_paper": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_vM_t": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_vMdot": (ctypes.c_double, [_CFG, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+            "orc_fn": (None, [_CFG, ctypes.c_int, _D, ctypes.c_double, _D]),
+            "orc_sigma_g": (ctypes.c_double, [_CFG, ctypes.c_double]),
+            "orc_sg_max": (ctypes.c_double, [_CFG]),
+            "orc_odd_source": (None, [_CFG, _D, ctypes.c_int64, ctypes.c_double, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -184,6 +207,12 @@ def make_cfg(p: dict) -> OrcCfg:
     c.verify = int(p.get("verify", 0))
     for d in range(3):
         c.E_app[d] = float(p.get("E_app", (0.0, 0.0, 0.0))[d])
+    c.dist = int(p.get("dist", DIST_CONFIG))
+    c.n_sigma = int(p.get("n_sigma", 0))
+    for k in range(3):
+        c.sigma_n[k] = float(p.get("sigma_n", (0.0, 0.0, 0.0))[k])
+    c.vbar = float(p.get("v_bar", 0.0))
+    c.t_ref = float(p.get("t_ref", 1.0))
     return c
 
 
@@ -315,6 +344,72 @@ def xMdot(cfg, xm, t):
 
 def vM(cfg, d, xi):
     return lib().orc_vM(ctypes.byref(cfg), d, xi)
+
+
+def fx_terms(cfg, d, t):
+    out = np.zeros(4)
+    lib().orc_fx_terms(ctypes.byref(cfg), d, t, _dp(out))
+    return out
+
+
+def fx(cfg, d, x, t):
+    return lib().orc_fx(ctypes.byref(cfg), d, x, t)
+
+
+def Fx(cfg, d, x, t):
+    return lib().orc_Fx(ctypes.byref(cfg), d, x, t)
+
+
+def xM_d(cfg, d, xi, t):
+    return lib().orc_xM_d(ctypes.byref(cfg), d, xi, t)
+
+
+def xMdot_d(cfg, d, xm, t):
+    return lib().orc_xMdot_d(ctypes.byref(cfg), d, xm, t)
+
+
+def vhat(cfg, t):
+    vh, dvh = np.zeros(3), np.zeros(3)
+    lib().orc_vhat(ctypes.byref(cfg), t, _dp(vh), _dp(dvh))
+    return vh, dvh
+
+
+def fv_paper(cfg, d, v, t):
+    return lib().orc_fv_paper(ctypes.byref(cfg), d, v, t)
+
+
+def Fv_paper(cfg, d, v, t):
+    return lib().orc_Fv_paper(ctypes.byref(cfg), d, v, t)
+
+
+def vM_t(cfg, d, xi, t):
+    return lib().orc_vM_t(ctypes.byref(cfg), d, xi, t)
+
+
+def vMdot(cfg, d, vm, t):
+    return lib().orc_vMdot(ctypes.byref(cfg), d, vm, t)
+
+
+def fn(cfg, k, vp, t):
+    a = np.ascontiguousarray(vp, dtype=np.float64)
+    out = np.zeros(3)
+    lib().orc_fn(ctypes.byref(cfg), k, _dp(a), t, _dp(out))
+    return out
+
+
+def sigma_g(cfg, g2):
+    return lib().orc_sigma_g(ctypes.byref(cfg), g2)
+
+
+def sg_max(cfg):
+    return lib().orc_sg_max(ctypes.byref(cfg))
+
+
+def odd_source(cfg, vp, ccell, t):
+    a = np.ascontiguousarray(vp, dtype=np.float64)
+    out = np.zeros(3)
+    lib().orc_odd_source(ctypes.byref(cfg), _dp(a), ccell, t, _dp(out))
+    return out
 
 
 def phiM(cfg, x, t):

@@ -13,12 +13,22 @@
  * states. It must be compiled with -ffp-contract=off so that x86 and Arm
  * builds give the same bits.
  *
- * Workload (the paper's Sec. 3 machinery applied to a simpler distribution):
- *   periodic unit cube [0,1)^3, n^3 cells of size h = 1/n, node i at x = i h;
+ * Workloads, on the periodic unit cube [0,1)^3 with n^3 cells of size
+ * h = 1/n and node i at x = i h:
+ *  dist = 0 (the paper's Sec. 3 machinery applied to a simpler distribution)
  *   f_x(x,t) = N prod_d (1 + A sin(2 pi (x_d - c t)))                 (Eq. fx)
  *   f_v(v,t) = prod_d Normal(v_d; mu_d, s^2), constant in time         (Eq. fv)
+ *  dist = 1 (the paper's own problem of Sec. 5.2, lengths in units of L,
+ *  times in units of T = t_ref):
+ *   f_x(x,t) = N prod_d (1 + A_d(t) sin(2 pi (x_d - s_d(t)))) with
+ *     A = (e^{t/T}/5, 1/5, -e^{t/T}/6), s = (0, 3 e^{t/T}/20, -e^{t/T}/15)
+ *   f_v(v,t) = prod_d (2/sqrt pi) v_d^2 / vh_d^3 e^{-v_d^2/vh_d^2}     (Eq. fv)
+ *     vh = vbar (1 + sin(pi t/(2T))/5, 1 + cos(pi t/T)/5, 1 + sin(3 pi t/(2T))/5)
+ *  both:
  *   phi^M(x,t) = phibar e^{t/(2T)} prod_d sin(2 pi (x_d - s_d))        (Sec. 5.2)
- *   hard-sphere cross section sigma(g) = sigma0, isotropic scattering  (Eq. chi_iso)
+ *   cross section: n_sigma = 0 hard sphere sigma(g) = sigma0; n_sigma > 0
+ *   sigma(g) = sum_{k<n_sigma} sigma_k g^{2k-1} (Eq. sigma_ms) with its
+ *   exact source (Eqs. vel_change_3, fn); isotropic scattering (Eq. chi_iso)
  *
  * Parity status of each function is given beside it; every function here is
  * pinned by tests in tests/test_oracle_pins.py (closed forms, invariants,
@@ -60,6 +70,11 @@ typedef struct {
                     *      p_chi = (29/2 + 12 cos chi - 20 cos^3 chi)
                     *      sin chi / 29 in place of sin chi / 2           */
   double E_app[3];   /* uniform applied field added to E_p in the push      */
+  int64_t dist;      /* 0: travelling-wave f_x and Gaussian f_v; 1: Sec. 5.2 */
+  int64_t n_sigma;   /* 0: hard sphere sigma0; 1..3: odd-power sigma_k      */
+  double sigma_n[3]; /* sigma_k of Eq. sigma_ms (k < n_sigma)               */
+  double vbar;       /* dist 1: vbar of vh_d(t)                             */
+  double t_ref;      /* dist 1: T of A_d(t), s_d(t), vh_d(t)                */
 } orc_cfg;
 
 #define ORC_ISOLATE 1
@@ -124,11 +139,59 @@ double orc_fxd(const orc_cfg* cf, double x, double t) {
   return 1.0 + cf->fx_amp * sin(2.0 * ORC_PI * (x - cf->fx_speed * t));
 }
 
+/* Amplitude A_d(t) and phase s_d(t) of the paper's f_{x_d} = 1 + A_d
+ * sin(2 pi (x - s_d)) on the unit cube (Sec. 5.2), with their time
+ * derivatives. dist = 0 reads A_d = A, s_d = c t.                         */
+void orc_fx_terms(const orc_cfg* cf, int d, double t, double out[4]) {
+  if (cf->dist == 0) {
+    out[0] = cf->fx_amp; out[1] = cf->fx_speed * t;
+    out[2] = 0.0;        out[3] = cf->fx_speed;
+    return;
+  }
+  double T = cf->t_ref, e = exp(t / T);
+  if (d == 0)      { out[0] = e / 5.0;  out[1] = 0.0; }
+  else if (d == 1) { out[0] = 1.0 / 5.0; out[1] = 3.0 * e / 20.0; }
+  else             { out[0] = -e / 6.0; out[1] = -e / 15.0; }
+  /* d/dt e^{t/T} = e^{t/T} / T; the constant amplitude has derivative 0 */
+  out[2] = (d == 1) ? 0.0 : out[0] / T;
+  out[3] = out[1] / T;
+}
+
+/* f_{x_d}(x,t) of either form (unit integral over [0,1)).                */
+double orc_fx(const orc_cfg* cf, int d, double x, double t) {
+  if (cf->dist == 0) return orc_fxd(cf, x, t);
+  double a[4];
+  orc_fx_terms(cf, d, t, a);
+  return 1.0 + a[0] * sin(2.0 * ORC_PI * (x - a[1]));
+}
+
 /* F_{x_d}(x,t) = int_0^x f_{x_d}(x',t) dx' in closed form (Sec. 3.1).   */
 double orc_Fxd(const orc_cfg* cf, double x, double t) {
   double A = cf->fx_amp, c = cf->fx_speed;
   return x + A / (2.0 * ORC_PI) *
                  (cos(2.0 * ORC_PI * (0.0 - c * t)) - cos(2.0 * ORC_PI * (x - c * t)));
+}
+
+/* F_{x_d}(x,t) of either form: x + A_d/(2 pi) [cos(2 pi (0 - s_d)) -
+ * cos(2 pi (x - s_d))].                                                   */
+double orc_Fx(const orc_cfg* cf, int d, double x, double t) {
+  if (cf->dist == 0) return orc_Fxd(cf, x, t);
+  double a[4];
+  orc_fx_terms(cf, d, t, a);
+  return x + a[0] / (2.0 * ORC_PI) *
+                 (cos(2.0 * ORC_PI * (0.0 - a[1])) - cos(2.0 * ORC_PI * (x - a[1])));
+}
+
+/* x_d^M(t) solves F_{x_d}(x^M, t) = xi on [0,1] (Eq. mms_sol), bisection. */
+double orc_xM_d(const orc_cfg* cf, int d, double xi, double t) {
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (orc_Fx(cf, d, mid, t) < xi) lo = mid; else hi = mid;
+  }
+  double rl = fabs(orc_Fx(cf, d, lo, t) - xi), rh = fabs(orc_Fx(cf, d, hi, t) - xi);
+  return rl <= rh ? lo : hi;
 }
 
 /* x^M(t) solves F_x(x^M, t) = xi on [0,1] (Eq. mms_sol). F is increasing,
@@ -155,6 +218,20 @@ double orc_xMdot(const orc_cfg* cf, double xM, double t) {
   return -integral / orc_fxd(cf, xM, t);
 }
 
+/* xdot_d^M of either form (Sec. 3.2): with d/dt f = A' sin(2 pi (x - s))
+ * - 2 pi A s' cos(2 pi (x - s)), the integral from 0 to x^M is
+ * A'/(2 pi) [cos(2 pi (0 - s)) - cos(2 pi (x^M - s))]
+ * - A s' [sin(2 pi (x^M - s)) - sin(2 pi (0 - s))].                        */
+double orc_xMdot_d(const orc_cfg* cf, int d, double xM, double t) {
+  if (cf->dist == 0) return orc_xMdot(cf, xM, t);
+  double a[4];
+  orc_fx_terms(cf, d, t, a);
+  double A = a[0], s = a[1], dA = a[2], ds = a[3];
+  double integral = dA / (2.0 * ORC_PI) * (cos(2.0 * ORC_PI * (0.0 - s)) - cos(2.0 * ORC_PI * (xM - s))) -
+                    A * ds * (sin(2.0 * ORC_PI * (xM - s)) - sin(2.0 * ORC_PI * (0.0 - s)));
+  return -integral / orc_fx(cf, d, xM, t);
+}
+
 /* Standard normal CDF Phi(z) = erfc(-z/sqrt 2)/2.                        */
 static double orc_Phi(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
 
@@ -174,6 +251,61 @@ static double orc_Phi_inv(double xi) {
 }
 double orc_vM(const orc_cfg* cf, int d, double xi) {
   return cf->vmean[d] + cf->vsig * orc_Phi_inv(xi);
+}
+
+/* The paper's velocity scales vh_d(t) (Sec. 5.2) and their derivatives.  */
+void orc_vhat(const orc_cfg* cf, double t, double vh[3], double dvh[3]) {
+  double T = cf->t_ref, vb = cf->vbar;
+  vh[0] = vb * (1.0 + sin(ORC_PI * t / (2.0 * T)) / 5.0);
+  vh[1] = vb * (1.0 + cos(ORC_PI * t / T) / 5.0);
+  vh[2] = vb * (1.0 + sin(3.0 * ORC_PI * t / (2.0 * T)) / 5.0);
+  dvh[0] = vb * (ORC_PI / (2.0 * T)) * cos(ORC_PI * t / (2.0 * T)) / 5.0;
+  dvh[1] = -vb * (ORC_PI / T) * sin(ORC_PI * t / T) / 5.0;
+  dvh[2] = vb * (3.0 * ORC_PI / (2.0 * T)) * cos(3.0 * ORC_PI * t / (2.0 * T)) / 5.0;
+}
+
+/* The paper's f_{v_d}(v,t) = (2/sqrt pi) v^2/vh^3 e^{-v^2/vh^2} (Eq. fv)
+ * and its CDF F_{v_d}(v,t) = (1 + erf(v/vh))/2 - (v/vh) e^{-v^2/vh^2}/sqrt pi
+ * (the antiderivative, zero at -infinity).                                */
+double orc_fv_paper(const orc_cfg* cf, int d, double v, double t) {
+  double vh[3], dvh[3];
+  orc_vhat(cf, t, vh, dvh);
+  double z = v / vh[d];
+  return 2.0 / sqrt(ORC_PI) * z * z / vh[d] * exp(-z * z);
+}
+double orc_Fv_paper(const orc_cfg* cf, int d, double v, double t) {
+  double vh[3], dvh[3];
+  orc_vhat(cf, t, vh, dvh);
+  double z = v / vh[d];
+  return 0.5 * (1.0 + erf(z)) - z * exp(-z * z) / sqrt(ORC_PI);
+}
+
+/* v_d^M(t) solves F_{v_d}(v^M, t) = xi (Eq. mms_sol). Gaussian form: the
+ * constant orc_vM. Paper form: bisection on F_v at time t; f_v is even in
+ * v, so for xi > 1/2 the root is minus the root for 1 - xi (exact there). */
+double orc_vM_t(const orc_cfg* cf, int d, double xi, double t) {
+  if (cf->dist == 0) return orc_vM(cf, d, xi);
+  if (xi > 0.5) return -orc_vM_t(cf, d, 1.0 - xi, t);
+  double vh[3], dvh[3];
+  orc_vhat(cf, t, vh, dvh);
+  double lo = -40.0 * vh[d], hi = 0.0;
+  for (int it = 0; it < 400; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (orc_Fv_paper(cf, d, mid, t) < xi) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* vdot_d^M = -(1/f_v(v^M,t)) int_{-inf}^{v^M} d/dt f_v dv' (Sec. 3.2). The
+ * integral is d/dt F_v(v^M,t) = f_v(v^M,t) (-v^M vh'/vh) by the chain rule
+ * on F_v(v,t) = G(v/vh(t)). Zero for the Gaussian form.                  */
+double orc_vMdot(const orc_cfg* cf, int d, double vM, double t) {
+  if (cf->dist == 0) return 0.0;
+  double vh[3], dvh[3];
+  orc_vhat(cf, t, vh, dvh);
+  double integral = orc_fv_paper(cf, d, vM, t) * (-vM * dvh[d] / vh[d]);
+  return -integral / orc_fv_paper(cf, d, vM, t);
 }
 
 /* phi^M and its derivatives (Sec. 5.2 form on the unit cube).            */
@@ -201,7 +333,7 @@ double orc_lap_phiM(const orc_cfg* cf, const double x[3], double t) {
 /* rho^M = q f_x (Sec. 3.4).                                              */
 double orc_rhoM(const orc_cfg* cf, double q, const double x[3], double t) {
   double f = cf->nphys;
-  for (int d = 0; d < 3; d++) f *= orc_fxd(cf, x[d], t);
+  for (int d = 0; d < 3; d++) f *= orc_fx(cf, d, x[d], t);
   return q * f;
 }
 
@@ -256,6 +388,107 @@ void orc_hs_source(const orc_cfg* cf, const double vp[3], int64_t ccell, double 
   double a = sqrt(a2) / cf->vsig;
   double R = orc_hs_R(a);
   for (int d = 0; d < 3; d++) out[d] = pref * cf->vsig * R * m[d];
+}
+
+/* ------------------------------------------------------------------------
+ * Manufactured cross section sigma(g) = sum_k sigma_k g^{2k-1} (Eq.
+ * sigma_ms), so sigma(g) g = sum_k sigma_k g^{2k}, and its source (Eq.
+ * vel_change_3): <Delta v_p^M> = w dt (c - 1)/(2 dV) sum_k sigma_k f_k with
+ * f_k = E_{v_q ~ f_v}[ g^{2k} (v_q - v_p) ] (Eq. fn).
+ *
+ * f_k is evaluated from its definition by expanding the polynomial: with
+ * X = v_q - v_p, |X|^{2k} X_i = sum_{a+b+c=k} k!/(a! b! c!) X_1^{2a} X_2^{2b}
+ * X_3^{2c} X_i, the components of v_q are independent, and
+ * E[X_j^m] = sum_l C(m,l) E[V_j^l] (-v_pj)^{m-l} with the raw moments of
+ * f_{v_j}: Gaussian E[V^l] = sum_{r even} C(l,r) mu^{l-r} s^r (r-1)!!;
+ * paper form E[V^l] = vh^l (l+1)!!/2^{l/2} for even l, 0 for odd l.
+ * ---------------------------------------------------------------------- */
+static double binom(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; i++) r = r * (double)(n - k + i) / (double)i;
+  return r;
+}
+static double dfact(int m) { /* m!! for m >= -1 */
+  double r = 1.0;
+  for (int i = m; i > 1; i -= 2) r *= (double)i;
+  return r;
+}
+/* raw moment E[V_d^l] of f_{v_d} at time t                                */
+static double vmoment(const orc_cfg* cf, int d, int l, double t) {
+  if (cf->dist == 0) {
+    double mu = cf->vmean[d], sg = cf->vsig, acc = 0.0;
+    for (int r = 0; r <= l; r += 2) acc += binom(l, r) * pow(mu, l - r) * pow(sg, r) * dfact(r - 1);
+    return acc;
+  }
+  if (l % 2) return 0.0;
+  double vh[3], dvh[3];
+  orc_vhat(cf, t, vh, dvh);
+  return pow(vh[d], l) * dfact(l + 1) / pow(2.0, l / 2);
+}
+/* E[X_d^m], X_d = V_d - v_pd                                              */
+static double xmoment(const orc_cfg* cf, int d, int m, double vpd, double t) {
+  double acc = 0.0;
+  for (int l = 0; l <= m; l++) acc += binom(m, l) * vmoment(cf, d, l, t) * pow(-vpd, m - l);
+  return acc;
+}
+/* f_k (Eq. fn) at v_p and time t                                          */
+void orc_fn(const orc_cfg* cf, int k, const double vp[3], double t, double out[3]) {
+  for (int i = 0; i < 3; i++) {
+    double acc = 0.0;
+    for (int a = 0; a <= k; a++)
+      for (int b = 0; a + b <= k; b++) {
+        int c = k - a - b;
+        int e[3] = {2 * a, 2 * b, 2 * c};
+        e[i] += 1;
+        double coef = binom(k, a) * binom(k - a, b);   /* k!/(a! b! c!) */
+        acc += coef * xmoment(cf, 0, e[0], vp[0], t) * xmoment(cf, 1, e[1], vp[1], t) *
+               xmoment(cf, 2, e[2], vp[2], t);
+      }
+    out[i] = acc;
+  }
+}
+
+/* sigma(g) g = sum_{k < n_sigma} sigma_k (g^2)^k, summed in ascending k.  */
+double orc_sigma_g(const orc_cfg* cf, double g2) {
+  double sum = 0.0, g2k = 1.0;
+  for (int k = 0; k < cf->n_sigma; k++) {
+    sum += cf->sigma_n[k] * g2k;
+    g2k *= g2;
+  }
+  return sum;
+}
+
+/* (sigma g)_max over g in [0, g_max] (Sec. 5.2): hard sphere sigma0 g_max;
+ * odd power: the largest of the polynomial in u = g^2 at u = 0, at
+ * u = g_max^2 and at its interior stationary point.                       */
+double orc_sg_max(const orc_cfg* cf) {
+  if (cf->n_sigma == 0) return cf->sigma0 * cf->gmax;
+  double u1 = cf->gmax * cf->gmax;
+  double best = orc_sigma_g(cf, 0.0), e = orc_sigma_g(cf, u1);
+  if (e > best) best = e;
+  if (cf->n_sigma == 3 && cf->sigma_n[2] != 0.0) {
+    double us = -cf->sigma_n[1] / (2.0 * cf->sigma_n[2]);
+    if (us > 0.0 && us < u1) {
+      double m = orc_sigma_g(cf, us);
+      if (m > best) best = m;
+    }
+  }
+  return best;
+}
+
+/* <Delta v_p^M>_coll of Eq. vel_change_3 for the odd-power sigma.        */
+void orc_odd_source(const orc_cfg* cf, const double vp[3], int64_t ccell, double t, double out[3]) {
+  double h = 1.0 / (double)cf->n;
+  double dV = h * h * h;
+  double w = cf->nphys / (double)cf->np;
+  double pref = w * cf->dt * (double)(ccell - 1) / (2.0 * dV);
+  out[0] = out[1] = out[2] = 0.0;
+  for (int k = 0; k < cf->n_sigma; k++) {
+    double f[3];
+    orc_fn(cf, k, vp, t, f);
+    for (int d = 0; d < 3; d++) out[d] += cf->sigma_n[k] * f[d];
+  }
+  for (int d = 0; d < 3; d++) out[d] *= pref;
 }
 
 /* ------------------------------------------------------------------------
@@ -597,14 +830,14 @@ double orc_pmax(const orc_cfg* cf) {
   double h = 1.0 / (double)cf->n;
   double dV = h * h * h;
   double w = cf->nphys / (double)cf->np;
-  double sg_max = cf->sigma0 * cf->gmax;
+  double sg_max = orc_sg_max(cf);
   return sg_max * w * cf->dt / dV;
 }
 
 static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint32_t o,
                             int64_t c, double* vloc /* [c][3], updated in place */,
                             orc_dsmc_stats* st) {
-  double sg_max = cf->sigma0 * cf->gmax;              /* (sigma g)_max, hard sphere */
+  double sg_max = orc_sg_max(cf);                     /* (sigma g)_max              */
   double Pmax = orc_pmax(cf);
   uint32_t u[4];
   philox4(c0, cellk, 0xFFFFFFFFu, o << 8, cf->seed, u);
@@ -634,8 +867,10 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
     double* vp = vloc + 3 * p;
     double* vq = vloc + 3 * q;
     double dx = vp[0] - vq[0], dy = vp[1] - vq[1], dz = vp[2] - vq[2];
-    double g = sqrt(dx * dx + dy * dy + dz * dz);
-    double ratio = (cf->sigma0 * g) / sg_max;         /* sigma(g) g / (sigma g)_max */
+    double g2 = dx * dx + dy * dy + dz * dz;
+    double g = sqrt(g2);
+    /* sigma(g) g / (sigma g)_max                                         */
+    double ratio = cf->n_sigma == 0 ? (cf->sigma0 * g) / sg_max : orc_sigma_g(cf, g2) / sg_max;
     double U = orc_u32(b0[2]);
     if (g > cf->gmax) st->n_gmax++;
     if (fabs(U - ratio) < 1e-12) st->n_tie++;
@@ -726,15 +961,19 @@ void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
   s->n_tie += st.n_tie;
 }
 
-/* Analytic source for every particle, using its cell's count.            */
-void orc_source_all(orc_state* s, const double* v, double* dvM) {
+/* Analytic source for every particle, using its cell's count and f_v at
+ * the call's time t.                                                     */
+void orc_source_all(orc_state* s, const double* v, double t, double* dvM) {
   const orc_cfg* cf = &s->c;
   for (int64_t p = 0; p < cf->np; p++) {
     if (cf->K <= 0) {
       dvM[3 * p] = dvM[3 * p + 1] = dvM[3 * p + 2] = 0.0;
       continue;
     }
-    orc_hs_source(cf, v + 3 * p, s->count[s->cell[p]], dvM + 3 * p);
+    if (cf->n_sigma == 0)
+      orc_hs_source(cf, v + 3 * p, s->count[s->cell[p]], dvM + 3 * p);
+    else
+      orc_odd_source(cf, v + 3 * p, s->count[s->cell[p]], t, dvM + 3 * p);
   }
 }
 
@@ -748,8 +987,8 @@ void orc_sample(orc_state* s, double t0) {
   s->n_ang = 0;
   for (int64_t p = 0; p < cf->np; p++) {
     for (int d = 0; d < 3; d++) {
-      s->x[3 * p + d] = orc_xM(cf, s->xi[6 * p + d], t0);
-      s->v[3 * p + d] = orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+      s->x[3 * p + d] = orc_xM_d(cf, d, s->xi[6 * p + d], t0);
+      s->v[3 * p + d] = orc_vM_t(cf, d, s->xi[6 * p + 3 + d], t0);
     }
   }
   for (int64_t i = 0; i < ncell(cf); i++) s->phi[i] = 0.0;
@@ -792,7 +1031,6 @@ void orc_step(orc_state* s, int64_t nsteps) {
   double* dv = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
   double* dvM = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
   double* vh = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
-  const double vdotM = 0.0; /* the Gaussian f_v does not depend on t */
   for (int64_t it = 0; it < nsteps; it++) {
     int64_t n = s->step;
     double tn = time_at(s, (double)n);
@@ -801,21 +1039,26 @@ void orc_step(orc_state* s, int64_t nsteps) {
     /* v^{n+1/2}: Lorentz term, collision call A at (x^n, v^n)             */
     lorentz_term(s, tn, L);
     orc_dsmc_avg(s, s->v, (uint32_t)(2 * n + 0), dv);
-    orc_source_all(s, s->v, dvM);
-    for (int64_t j = 0; j < 3 * np; j++)
-      vh[j] = s->v[j] + 0.5 * (L[j] + dv[j] - dvM[j] + cf->dt * vdotM);
+    orc_source_all(s, s->v, tn, dvM);
+    for (int64_t p = 0; p < np; p++)
+      for (int d = 0; d < 3; d++) {
+        int64_t j = 3 * p + d;
+        /* vdot^M is zero for the constant Gaussian f_v */
+        double vdotM = cf->dist == 0 ? 0.0 : orc_vMdot(cf, d, orc_vM_t(cf, d, s->xi[6 * p + 3 + d], tn), tn);
+        vh[j] = s->v[j] + 0.5 * (L[j] + dv[j] - dvM[j] + cf->dt * vdotM);
+      }
     /* x^{n+1} = x^n + dt (v + xdot^M - v^M)^{n+1/2}, wrapped; in the
      * isolated-collision mode dt xdot^M(t_{n+1/2}) becomes the exact
      * increment x^M(t_{n+1}) - x^M(t_n) (Sec. 5.4)                       */
     for (int64_t p = 0; p < np; p++) {
       for (int d = 0; d < 3; d++) {
-        double vm = orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+        double vm = orc_vM_t(cf, d, s->xi[6 * p + 3 + d], th);
         if (cf->verify & ORC_ISOLATE) {
           double dxm = orc_xM(cf, s->xi[6 * p + d], tn1) - orc_xM(cf, s->xi[6 * p + d], tn);
           s->x[3 * p + d] = orc_wrap(s->x[3 * p + d] + (cf->dt * (vh[3 * p + d] - vm) + dxm));
         } else {
-          double xm = orc_xM(cf, s->xi[6 * p + d], th);
-          double xmd = orc_xMdot(cf, xm, th);
+          double xm = orc_xM_d(cf, d, s->xi[6 * p + d], th);
+          double xmd = orc_xMdot_d(cf, d, xm, th);
           s->x[3 * p + d] = orc_wrap(s->x[3 * p + d] + cf->dt * (vh[3 * p + d] + xmd - vm));
         }
       }
@@ -826,19 +1069,25 @@ void orc_step(orc_state* s, int64_t nsteps) {
     /* v^{n+1}: Lorentz term at x^{n+1}, collision call B at (x^{n+1}, v^{n+1/2}) */
     lorentz_term(s, tn1, L);
     orc_dsmc_avg(s, vh, (uint32_t)(2 * n + 1), dv);
-    orc_source_all(s, vh, dvM);
-    for (int64_t j = 0; j < 3 * np; j++)
-      s->v[j] = vh[j] + 0.5 * (L[j] + dv[j] - dvM[j] + cf->dt * vdotM);
+    orc_source_all(s, vh, th, dvM);
+    for (int64_t p = 0; p < np; p++)
+      for (int d = 0; d < 3; d++) {
+        int64_t j = 3 * p + d;
+        /* vdot^M is zero for the constant Gaussian f_v */
+        double vdotM = cf->dist == 0 ? 0.0 : orc_vMdot(cf, d, orc_vM_t(cf, d, s->xi[6 * p + 3 + d], tn1), tn1);
+        s->v[j] = vh[j] + 0.5 * (L[j] + dv[j] - dvM[j] + cf->dt * vdotM);
+      }
     s->step = n + 1;
   }
   free(L); free(dv); free(dvM); free(vh);
 }
 
 /* One K-averaged collision call on the current state (cells of x, v); the
- * phase selects the counter 2 step + phase; the source uses f_v (constant). */
+ * phase selects the counter 2 step + phase; the source uses f_v at the
+ * state's time.                                                          */
 void orc_collide_avg(orc_state* s, int64_t phase, double* dv, double* dvM) {
   orc_dsmc_avg(s, s->v, (uint32_t)(2 * s->step + phase), dv);
-  orc_source_all(s, s->v, dvM);
+  orc_source_all(s, s->v, time_at(s, (double)s->step), dvM);
 }
 
 /* ------------------------------------------------------------------------
@@ -852,11 +1101,11 @@ void orc_errors(const orc_state* s, double out[14]) {
   double s2[7] = {0}, mx[7] = {0};
   for (int64_t p = 0; p < cf->np; p++) {
     for (int d = 0; d < 3; d++) {
-      double e = s->x[3 * p + d] - orc_xM(cf, s->xi[6 * p + d], t);
+      double e = s->x[3 * p + d] - orc_xM_d(cf, d, s->xi[6 * p + d], t);
       e -= floor(e + 0.5);
       s2[d] += e * e;
       if (fabs(e) > mx[d]) mx[d] = fabs(e);
-      double ev = s->v[3 * p + d] - orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+      double ev = s->v[3 * p + d] - orc_vM_t(cf, d, s->xi[6 * p + 3 + d], t);
       s2[3 + d] += ev * ev;
       if (fabs(ev) > mx[3 + d]) mx[3 + d] = fabs(ev);
     }
@@ -882,10 +1131,11 @@ void orc_errors(const orc_state* s, double out[14]) {
 void orc_objective(const orc_state* s, double out[3]) {
   const orc_cfg* cf = &s->c;
   double h = 1.0 / (double)cf->n, ef = 0.0, ev = 0.0;
+  double t = time_at(s, (double)s->step);
   for (int64_t i = 0; i < 3 * ncell(cf); i++) ef += s->E[i] * s->E[i];
   for (int64_t p = 0; p < cf->np; p++)
     for (int d = 0; d < 3; d++) {
-      double e = s->v[3 * p + d] - orc_vM(cf, d, s->xi[6 * p + 3 + d]);
+      double e = s->v[3 * p + d] - orc_vM_t(cf, d, s->xi[6 * p + 3 + d], t);
       ev += e * e;
     }
   out[1] = 0.5 * cf->eps0 * h * h * h * ef;
