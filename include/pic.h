@@ -79,6 +79,24 @@ enum {
   PIC_VERIFY_ANISO = 16
 };
 
+/* Manufactured-distribution forms of pic_config.dist:
+ *  PIC_DIST_CONFIG  f_{x_d} = 1 + fx_amp sin(2 pi (x - fx_speed t)) and a
+ *                   Gaussian f_v (mean v_mean, width v_sigma), constant in t.
+ *  PIC_DIST_PAPER   the paper's own problem of Sec. 5.2 on the unit cube
+ *                   (lengths in units of the box edge L, times in units of
+ *                   t_ref = T): f_{x_d} = 1 + A_d(t) sin(2 pi (x - s_d(t)))
+ *                   with A = (e^{t/T}/5, 1/5, -e^{t/T}/6) and
+ *                   s = (0, 3 e^{t/T}/20, -e^{t/T}/15); the non-Maxwellian
+ *                   f_{v_d} = (2/sqrt pi) v^2/vh_d^3 e^{-v^2/vh_d^2} of Eq. fv
+ *                   with vh = v_bar (1 + sin(pi t/(2T))/5, 1 + cos(pi t/T)/5,
+ *                   1 + sin(3 pi t/(2T))/5). v^M(t) = vh(t) tau(xi) and
+ *                   vdot^M = vh'(t) tau(xi) enter the kicks (Eq.
+ *                   velocity_verlet). FP64 single contexts only; collisions
+ *                   need the odd-power cross section (n_sigma >= 1), whose
+ *                   source is closed-form for this f_v (Eq. fn); the
+ *                   isolated-collision switch is not available. */
+enum { PIC_DIST_CONFIG = 0, PIC_DIST_PAPER = 1 };
+
 /* Bins per angle of the recorded-angle histograms. */
 #define PIC_ANGLE_BINS 4194304
 
@@ -112,7 +130,14 @@ enum {
  *                set of the collision kernel); 0 selects 512.
  *  seed          Philox4x32-10 key (low word, high word).
  *  cg_tol, cg_maxit  CG stops at ||r||_2 <= cg_tol ||b||_2 or cg_maxit.
- *  verify        PIC_VERIFY_* bit flags (0: the method as stated). */
+ *  verify        PIC_VERIFY_* bit flags (0: the method as stated).
+ *  dist          PIC_DIST_* (0: the fields fx_*, v_mean, v_sigma above).
+ *  n_sigma       0: hard spheres (sigma0). 1..3: the manufactured cross
+ *                section sigma(g) = sum_{k<n_sigma} sigma_n[k] g^{2k-1} of
+ *                Eq. sigma_ms with the source of Eqs. vel_change_3 and fn;
+ *                (sigma g)_max is its maximum over [0, g_max] (Sec. 5.2),
+ *                and sigma(g) g must be >= 0 there. FP64 contexts only.
+ *  v_bar, t_ref  PIC_DIST_PAPER: vbar and T of the manufactured solution. */
 typedef struct {
   int32_t n;
   int32_t K;
@@ -132,6 +157,10 @@ typedef struct {
   double cg_tol;
   int32_t cg_maxit;
   int32_t verify;
+  int32_t dist;
+  int32_t n_sigma;
+  double sigma_n[3];
+  double v_bar, t_ref;
 } pic_config;
 
 /* Error norms of Sec. 4.3 at the context's current time: index 0..5 =

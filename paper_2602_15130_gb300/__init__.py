@@ -46,6 +46,12 @@ def make_config(p: dict) -> PicConfig:
     c.seed = int(p.get("seed", 0))
     c.cg_maxit = int(p.get("cg_maxit", c.cg_maxit))
     c.verify = int(p.get("verify", 0))
+    c.dist = int(p.get("dist", _lib.PIC_DIST_CONFIG))
+    c.n_sigma = int(p.get("n_sigma", 0))
+    for k in range(3):
+        c.sigma_n[k] = float(p.get("sigma_n", (0.0, 0.0, 0.0))[k])
+    c.v_bar = float(p.get("v_bar", 0.0))
+    c.t_ref = float(p.get("t_ref", 1.0))
     return c
 
 

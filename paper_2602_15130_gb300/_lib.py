@@ -24,6 +24,7 @@ PIC_MIXED = 1
 # verification switches (pic_config.verify bits)
 PIC_VERIFY_ISOLATE, PIC_VERIFY_ERROR1, PIC_VERIFY_ERROR2, PIC_VERIFY_ANGLES, PIC_VERIFY_ANISO = 1, 2, 4, 8, 16
 PIC_ANGLE_BINS = 4194304
+PIC_DIST_CONFIG, PIC_DIST_PAPER = 0, 1
 NUM_KERNEL_CLASSES = 9
 KERNEL_CLASSES = ["sample", "sort", "sort_gather_deposit", "rhs", "cg_efield", "dsmc", "kick_drift",
                   "error_norms", "other"]
@@ -56,6 +57,11 @@ class PicConfig(ctypes.Structure):
         ("cg_tol", ctypes.c_double),
         ("cg_maxit", ctypes.c_int32),
         ("verify", ctypes.c_int32),
+        ("dist", ctypes.c_int32),
+        ("n_sigma", ctypes.c_int32),
+        ("sigma_n", ctypes.c_double * 3),
+        ("v_bar", ctypes.c_double),
+        ("t_ref", ctypes.c_double),
     ]
 
 

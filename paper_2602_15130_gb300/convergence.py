@@ -12,6 +12,11 @@ Studies:
                         both one-way couplings and the coupled case, with
                         the manufactured anisotropic scattering of Sec. 5.1.
   table1-collisionless  Table 1, s = 5: both one-way couplings, coupled.
+  paper-collisional     the paper's own problem of Sec. 5.2 (non-Maxwellian
+                        f_v with vh(t), per-axis f_x, odd-power sigma with
+                        its exact source) on the Table 1 schedule, s = 7,
+                        r = 5, FP64: uncoupled, one-way and coupled.
+  paper-collisionless   the same problem without collisions, s = 5.
   refine                the fixed-32-particles-per-cell sweep (n = 8..128,
                         dt = 0.02 / 2^l, T = 0.5): s = 3 and r = 0, so the
                         coupled collisionless rate is 1 and the collisional
@@ -55,6 +60,15 @@ TABLE1_COLLISIONLESS = {
     "oneway_q0": (dict(couple_q_zero=1), {"x": 2, "v": 2}),
     "coupled": (dict(), {"x": 2, "v": 2, "phi": 2}),
 }
+PAPER_COLLISIONAL = {
+    "uncoupled": (dict(couple_qm_zero=1, couple_q_zero=1), {"x": 2, "v": 2, "phi": 2}),
+    "oneway_q0": (dict(couple_q_zero=1), {"x": 2, "v": 2}),
+    "coupled": (dict(), {"x": 2, "v": 2, "phi": 2}),
+}
+PAPER_COLLISIONLESS = {
+    "oneway_qm0": (dict(couple_qm_zero=1), {"phi": 2}),
+    "coupled": (dict(), {"x": 2, "v": 2, "phi": 2}),
+}
 REFINE = {
     "collisionless_uncoupled": (dict(K=0, couple_qm_zero=1, couple_q_zero=1), {"x": 2, "phi": 2}),
     "collisionless_coupled": (dict(K=0), {"x": 1, "v": 1, "phi": 1}),
@@ -67,6 +81,10 @@ def levels_params(study: str, level: int, overrides: dict) -> dict:
         p = workloads.table1_level(level, collisions=True)
     elif study == "table1-collisionless":
         p = workloads.table1_level(level, collisions=False)
+    elif study == "paper-collisional":
+        p = workloads.paper_table1_level(level, collisions=True)
+    elif study == "paper-collisionless":
+        p = workloads.paper_table1_level(level, collisions=False)
     elif study == "refine":
         p = workloads.refinement_level(level)
     else:
@@ -121,6 +139,7 @@ def group_error(rec: dict, norm: str, group: str) -> float:
 def run_study(study: str, levels: list[int], precision: str, variants: list[str] | None = None, log=print,
               save=None) -> dict:
     table = {"table1-collisional": TABLE1_COLLISIONAL, "table1-collisionless": TABLE1_COLLISIONLESS,
+             "paper-collisional": PAPER_COLLISIONAL, "paper-collisionless": PAPER_COLLISIONLESS,
              "refine": REFINE}[study]
     result = {"study": study, "precision": precision, "levels": levels, "variants": {}}
     for name, (over, pred) in table.items():
@@ -175,7 +194,8 @@ def format_report(res: dict) -> str:
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--study", required=True, choices=["table1-collisional", "table1-collisionless", "refine"])
+    ap.add_argument("--study", required=True, choices=["table1-collisional", "table1-collisionless",
+                                                          "paper-collisional", "paper-collisionless", "refine"])
     ap.add_argument("--levels", type=int, nargs="+", default=[0, 1, 2, 3, 4])
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--variants", nargs="*", default=None)

@@ -703,6 +703,7 @@ extern "C" pic_status pic_adjoint_gradient(pic_ctx* c, int32_t nsteps, int32_t e
   if (!c || nsteps < 0 || every < 1 || !J) return PIC_EINVAL;
   if (c->mixed || c->nrep > 0) return PIC_EINVAL;
   if (c->cfg.verify & (PIC_VERIFY_ERROR1 | PIC_VERIFY_ERROR2)) return PIC_EINVAL;
+  if (c->cfg.dist != PIC_DIST_CONFIG || c->cfg.n_sigma != 0) return PIC_EINVAL;
   const bool grad = dJ_dEapp || dJ_dv0;
   const int seg = grad ? (nsteps < every ? (nsteps > 0 ? nsteps : 1) : every) : 1;
   const int ncp = grad ? (nsteps + every - 1) / every : 0;

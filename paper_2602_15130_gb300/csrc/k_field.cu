@@ -73,8 +73,12 @@ __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
     const double phiM = a.tt.em_amp / kTwoPi * sinpi(2.0 * (X - P.phi_shift[0])) *
                         sinpi(2.0 * (Y - P.phi_shift[1])) * sinpi(2.0 * (Z - P.phi_shift[2]));
     const double lap_phiM = -3.0 * kTwoPi * kTwoPi * phiM;
-    const double rhoM = P.q_eff * P.nphys * (1.0 + P.fx_amp * sinpi(2.0 * (X - ct))) *
-                        (1.0 + P.fx_amp * sinpi(2.0 * (Y - ct))) * (1.0 + P.fx_amp * sinpi(2.0 * (Z - ct)));
+    const double rhoM =
+        P.dist == PIC_DIST_PAPER
+            ? P.q_eff * P.nphys * (1.0 + a.tt.fA[0] * sinpi(2.0 * (X - a.tt.fs[0]))) *
+                  (1.0 + a.tt.fA[1] * sinpi(2.0 * (Y - a.tt.fs[1]))) * (1.0 + a.tt.fA[2] * sinpi(2.0 * (Z - a.tt.fs[2])))
+            : P.q_eff * P.nphys * (1.0 + P.fx_amp * sinpi(2.0 * (X - ct))) * (1.0 + P.fx_amp * sinpi(2.0 * (Y - ct))) *
+                  (1.0 + P.fx_amp * sinpi(2.0 * (Z - ct)));
     bv = rho / P.eps0 - lap_phiM - rhoM / P.eps0;
     a.rho[id] = rho;
     if (a.b) a.b[id] = bv;

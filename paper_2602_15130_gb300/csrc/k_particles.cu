@@ -36,6 +36,18 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a) {
   const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                         unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
   double s;
+  if (P.dist == PIC_DIST_PAPER) {
+    // x^M(t0) per axis; v^M(t0) = vh(t0) tau(xi), tau kept in the v^M arrays
+    double c;
+    a.x0[i] = wrap_unit(xm_solve_gen(a.tt, 0, xi[0], &s, &c));
+    a.x1[i] = wrap_unit(xm_solve_gen(a.tt, 1, xi[1], &s, &c));
+    a.x2[i] = wrap_unit(xm_solve_gen(a.tt, 2, xi[2], &s, &c));
+    const double t0 = tau_inv(xi[3]), t1 = tau_inv(xi[4]), t2 = tau_inv(xi[5]);
+    a.v0[i] = t0 * a.tt.vh[0]; a.v1[i] = t1 * a.tt.vh[1]; a.v2[i] = t2 * a.tt.vh[2];
+    a.vm0[i] = t0; a.vm1[i] = t1; a.vm2[i] = t2;
+    a.pid[i] = (uint32_t)i;
+    return;
+  }
   const double X0 = xm_solve(P, a.tt, xi[0], &s);
   const double X1 = xm_solve(P, a.tt, xi[1], &s);
   const double X2 = xm_solve(P, a.tt, xi[2], &s);
@@ -65,9 +77,13 @@ __global__ void __launch_bounds__(kThreads) k_load_state(LoadArgs a) {
            b2 = sample_block(P, (uint64_t)i, 2);
   const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                         unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
-  a.vm0[i] = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
-  a.vm1[i] = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
-  a.vm2[i] = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
+  if (P.dist == PIC_DIST_PAPER) {
+    a.vm0[i] = tau_inv(xi[3]); a.vm1[i] = tau_inv(xi[4]); a.vm2[i] = tau_inv(xi[5]);
+  } else {
+    a.vm0[i] = P.vmean[0] + P.vsig * normcdfinv(xi[3]);
+    a.vm1[i] = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
+    a.vm2[i] = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
+  }
   const double* xs = a.xv;
   const double* vs = a.xv + 3 * P.np;
   a.x0[i] = xs[3 * i]; a.x1[i] = xs[3 * i + 1]; a.x2[i] = xs[3 * i + 2];
@@ -128,6 +144,7 @@ struct DsmcArgs {
   int64_t ngroups;
   unsigned long long* counters;
   int* flags;
+  double vh[3];             // PIC_DIST_PAPER: f_v scales at the call's time
 };
 
 constexpr int kDsmcThreads = 128;
@@ -204,7 +221,13 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
           const double m0 = acc0 != 0.0 ? acc0 / K : 0.0, m1 = acc1 != 0.0 ? acc1 / K : 0.0,
                        m2 = acc2 != 0.0 ? acc2 / K : 0.0;
           double s0, s1, s2;
-          hs_source(P, a.v0[j], a.v1[j], a.v2[j], cc, &s0, &s1, &s2);
+          if (P.n_sigma == 0) {
+            hs_source(P, a.v0[j], a.v1[j], a.v2[j], cc, &s0, &s1, &s2);
+          } else {
+            double so[3];
+            odd_source(P, a.vh, a.v0[j], a.v1[j], a.v2[j], cc, so);
+            s0 = so[0]; s1 = so[1]; s2 = so[2];
+          }
           if (separate) {
             a.dv0[j] = m0; a.dv1[j] = m1; a.dv2[j] = m2;
             a.m0[j] = s0; a.m1[j] = s1; a.m2[j] = s2;
@@ -300,18 +323,31 @@ __global__ void __launch_bounds__(kThreads) k_kick(KickArgs a) {
   }
   double dv[3] = {0.0, 0.0, 0.0};
   if (a.dv0) { dv[0] = a.dv0[j]; dv[1] = a.dv1[j]; dv[2] = a.dv2[j]; }
+  const bool paper = P.dist == PIC_DIST_PAPER;
+  double vm[3] = {0.0, 0.0, 0.0};
+  if (a.drift || paper) { vm[0] = a.vm0[j]; vm[1] = a.vm1[j]; vm[2] = a.vm2[j]; }
+  if (paper) {
+    // v^M arrays hold tau: vdot^M(t) = vh'(t) tau (Eq. velocity_verlet)
 #pragma unroll
-  for (int d = 0; d < 3; ++d) v[d] = v[d] + 0.5 * (L[d] + dv[d]);
+    for (int d = 0; d < 3; ++d) v[d] = v[d] + 0.5 * ((L[d] + dv[d]) + P.dt * (vm[d] * a.tE.dvh[d]));
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] = v[d] + 0.5 * (L[d] + dv[d]);
+  }
   a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
   if (!a.drift) return;
   const uint64_t p = a.pid[j];
   const U4 b0 = sample_block(P, p, 0), b1 = sample_block(P, p, 1);
   const double xi[3] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y)};
-  const double vm[3] = {a.vm0[j], a.vm1[j], a.vm2[j]};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double s;
-    if (P.verify & PIC_VERIFY_ISOLATE) {
+    if (paper) {
+      double c;
+      xm_solve_gen(a.th, d, xi[d], &s, &c);
+      const double xd = xm_dot_gen(a.th, d, s, c);
+      x[d] = wrap_unit(x[d] + P.dt * (v[d] + xd - vm[d] * a.th.vh[d]));
+    } else if (P.verify & PIC_VERIFY_ISOLATE) {
       // exact manufactured increment x^M(t_{n+1}) - x^M(t_n) (Sec. 5.4)
       const double dxm = xm_solve(P, a.t1, xi[d], &s) - xm_solve(P, a.t0, xi[d], &s);
       x[d] = wrap_unit(x[d] + (P.dt * (v[d] - vm[d]) + dxm));
@@ -383,13 +419,14 @@ __global__ void __launch_bounds__(kThreads) k_err_partial(ErrArgs a) {
       const double vms[3] = {a.vm0[j], a.vm1[j], a.vm2[j]};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        double s;
-        const double xm = xm_solve(P, a.tt, xi[d], &s);
+        double s, c;
+        const bool paper = P.dist == PIC_DIST_PAPER;
+        const double xm = paper ? xm_solve_gen(a.tt, d, xi[d], &s, &c) : xm_solve(P, a.tt, xi[d], &s);
         double e = xs[d] - xm;
         e -= floor(e + 0.5);
         vals[d] = e * e;
         vals[7 + d] = fabs(e);
-        const double ev = vs[d] - vms[d];
+        const double ev = vs[d] - (paper ? vms[d] * a.tt.vh[d] : vms[d]);
         vals[3 + d] = ev * ev;
         vals[10 + d] = fabs(ev);
       }
@@ -509,9 +546,11 @@ cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate) {
+cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate, double t_src) {
   DsmcArgs a;
   a.P = c->P;
+  const TimeTerms ts = time_terms(c->P, t_src);
+  for (int d = 0; d < 3; ++d) a.vh[d] = ts.vh[d];
   const int b = c->cur;
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];
   a.start = c->start;
@@ -618,6 +657,30 @@ TimeTerms time_terms(const Params& P, double t) {
   tt.cos2ct = cos(kTwoPi * tt.ct);
   tt.sin2ct = sin(kTwoPi * tt.ct);
   tt.em_amp = kTwoPi * P.phi_amp * exp(t / (2.0 * P.phi_T));
+  for (int d = 0; d < 3; ++d) {
+    tt.fA[d] = tt.fs[d] = tt.fdA[d] = tt.fds[d] = tt.fsn[d] = 0.0;
+    tt.fcs[d] = 1.0;
+    tt.vh[d] = tt.dvh[d] = 0.0;
+  }
+  if (P.dist == PIC_DIST_PAPER) {
+    // Sec. 5.2 on the unit cube, T = t_ref
+    const double T = P.t_ref, e = exp(t / T), vb = P.vbar;
+    tt.fA[0] = e / 5.0;  tt.fs[0] = 0.0;
+    tt.fA[1] = 1.0 / 5.0; tt.fs[1] = 3.0 * e / 20.0;
+    tt.fA[2] = -e / 6.0; tt.fs[2] = -e / 15.0;
+    for (int d = 0; d < 3; ++d) {
+      tt.fdA[d] = d == 1 ? 0.0 : tt.fA[d] / T;
+      tt.fds[d] = tt.fs[d] / T;
+      tt.fcs[d] = cos(kTwoPi * tt.fs[d]);
+      tt.fsn[d] = sin(kTwoPi * tt.fs[d]);
+    }
+    tt.vh[0] = vb * (1.0 + sin(kPi * t / (2.0 * T)) / 5.0);
+    tt.vh[1] = vb * (1.0 + cos(kPi * t / T) / 5.0);
+    tt.vh[2] = vb * (1.0 + sin(3.0 * kPi * t / (2.0 * T)) / 5.0);
+    tt.dvh[0] = vb * (kPi / (2.0 * T)) * cos(kPi * t / (2.0 * T)) / 5.0;
+    tt.dvh[1] = -vb * (kPi / T) * sin(kPi * t / T) / 5.0;
+    tt.dvh[2] = vb * (3.0 * kPi / (2.0 * T)) * cos(3.0 * kPi * t / (2.0 * T)) / 5.0;
+  }
   return tt;
 }
 }  // namespace pic

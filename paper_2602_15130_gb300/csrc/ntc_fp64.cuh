@@ -65,8 +65,11 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
     load_vel((int)p, bm, ov, v0, v1, v2, vp);
     load_vel((int)q, bm, ov, v0, v1, v2, vq);
     const double dx = __dsub_rn(vp[0], vq[0]), dy = __dsub_rn(vp[1], vq[1]), dz = __dsub_rn(vp[2], vq[2]);
-    const double g = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-    const double ratio = __ddiv_rn(__dmul_rn(P.sigma0, g), P.sg_max);
+    const double g2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double g = __dsqrt_rn(g2);
+    // sigma(g) g / (sigma g)_max: hard sphere, or the odd-power sigma of Eq. sigma_ms
+    const double ratio = P.n_sigma == 0 ? __ddiv_rn(__dmul_rn(P.sigma0, g), P.sg_max)
+                                        : __ddiv_rn(sigma_g(P, g2), P.sg_max);
     const double U = unif32(b0.z);
     ++cnt.cand;
     if (g > P.gmax) ++cnt.gmax;

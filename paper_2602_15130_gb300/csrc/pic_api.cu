@@ -122,6 +122,48 @@ void series_coefficients(double* out) {
     out[j] = s * (d[j] + d[j + 1] + (j > 0 ? e[j - 1] : 0.0) + 2.0 * e[j] - e[j + 1]);
 }
 
+// (sigma g)_max over g in [0, g_max] (Sec. 5.2). Odd-power sigma: sigma(g)
+// g = sum_k sigma_k u^k with u = g^2 is a polynomial of degree < 3 in u, so
+// its maximum is at u = 0, u = g_max^2 or the stationary point.
+double poly_sg(const pic_config& c, double u) {
+  double sum = 0.0, uk = 1.0;
+  for (int k = 0; k < c.n_sigma; ++k) {
+    sum += c.sigma_n[k] * uk;
+    uk *= u;
+  }
+  return sum;
+}
+double sg_max_of(const pic_config& c) {
+  if (c.n_sigma == 0) return c.sigma0 * c.g_max;
+  const double u1 = c.g_max * c.g_max;
+  double best = poly_sg(c, 0.0);
+  const double e = poly_sg(c, u1);
+  if (e > best) best = e;
+  if (c.n_sigma == 3 && c.sigma_n[2] != 0.0) {
+    const double us = -c.sigma_n[1] / (2.0 * c.sigma_n[2]);
+    if (us > 0.0 && us < u1) {
+      const double m = poly_sg(c, us);
+      if (m > best) best = m;
+    }
+  }
+  return best;
+}
+// smallest sigma(g) g on [0, g_max] (the same candidates)
+double sg_min_of(const pic_config& c) {
+  const double u1 = c.g_max * c.g_max;
+  double lo = poly_sg(c, 0.0);
+  const double e = poly_sg(c, u1);
+  if (e < lo) lo = e;
+  if (c.n_sigma == 3 && c.sigma_n[2] != 0.0) {
+    const double us = -c.sigma_n[1] / (2.0 * c.sigma_n[2]);
+    if (us > 0.0 && us < u1) {
+      const double m = poly_sg(c, us);
+      if (m < lo) lo = m;
+    }
+  }
+  return lo;
+}
+
 void derive_params(const pic_config& c, Params& P) {
   memset(&P, 0, sizeof(P));
   P.n = c.n;
@@ -151,8 +193,14 @@ void derive_params(const pic_config& c, Params& P) {
   P.h = 1.0 / (double)c.n;
   P.dV = P.h * P.h * P.h;
   P.w = c.n_phys / (double)c.n_particles;
-  P.sg_max = c.sigma0 * c.g_max;
+  P.sg_max = sg_max_of(c);
   P.pmax = P.sg_max * P.w * c.dt / P.dV;
+  P.dist = c.dist;
+  P.n_sigma = c.n_sigma;
+  for (int k = 0; k < 3; ++k) P.sigma_n[k] = k < c.n_sigma ? c.sigma_n[k] : 0.0;
+  P.src_pref_n = P.w * c.dt / (2.0 * P.dV);
+  P.vbar = c.v_bar;
+  P.t_ref = c.t_ref;
   P.rho_scale = P.q_eff * P.w / P.dV;
   P.src_pref = P.w * c.dt * c.sigma0 / (2.0 * P.dV);
   series_coefficients(P.R_series);
@@ -444,7 +492,7 @@ cudaError_t step_fp64(pic_ctx* c, int64_t n, const StepHook* hook) {
   cudaError_t e;
   if (hook && (e = (*hook)(0)) != cudaSuccess) return e;
   // v^{n+1/2} and x^{n+1}: collision call A at (x^n, v^n)
-  if (coll && (e = launch_dsmc(c, (uint32_t)(2 * n), false)) != cudaSuccess) return e;
+  if (coll && (e = launch_dsmc(c, (uint32_t)(2 * n), false, tn)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream)) != cudaSuccess) return e;
   if ((e = launch_kick(c, tn, coll, true, th, tn1)) != cudaSuccess) return e;
   // cells of x^{n+1}, field at t^{n+1}
@@ -454,7 +502,7 @@ cudaError_t step_fp64(pic_ctx* c, int64_t n, const StepHook* hook) {
   if ((e = launch_cg(c)) != cudaSuccess) return e;
   if (hook && (e = (*hook)(2)) != cudaSuccess) return e;
   // v^{n+1}: collision call B at (x^{n+1}, v^{n+1/2})
-  if (coll && (e = launch_dsmc(c, (uint32_t)(2 * n + 1), false)) != cudaSuccess) return e;
+  if (coll && (e = launch_dsmc(c, (uint32_t)(2 * n + 1), false, th)) != cudaSuccess) return e;
   return launch_kick(c, tn1, coll, false, 0.0, 0.0);
 }
 
@@ -508,6 +556,20 @@ pic_status pic_validate_config(const pic_config* c) {
   if (!(c->cg_tol > 0.0) || c->cg_maxit < 1) return PIC_EINVAL;
   if (c->verify & ~31) return PIC_EINVAL;
   if ((c->verify & PIC_VERIFY_ERROR1) && (c->verify & PIC_VERIFY_ERROR2)) return PIC_EINVAL;
+  // the paper's problem and the odd-power cross section: FP64 form only
+  if (c->dist != PIC_DIST_CONFIG && c->dist != PIC_DIST_PAPER) return PIC_EINVAL;
+  if (c->n_sigma < 0 || c->n_sigma > 3) return PIC_EINVAL;
+  if ((c->dist != PIC_DIST_CONFIG || c->n_sigma > 0) && c->precision != PIC_FP64) return PIC_EINVAL;
+  if (c->dist == PIC_DIST_PAPER) {
+    if (!(c->v_bar > 0.0) || !isfinite(c->v_bar) || !(c->t_ref > 0.0) || !isfinite(c->t_ref)) return PIC_EINVAL;
+    if (c->verify & PIC_VERIFY_ISOLATE) return PIC_EINVAL;
+    if (c->K > 0 && c->n_sigma == 0) return PIC_EINVAL;  // no closed-form hard-sphere source for this f_v
+  }
+  if (c->n_sigma > 0) {
+    for (int k = 0; k < c->n_sigma; ++k)
+      if (!isfinite(c->sigma_n[k])) return PIC_EINVAL;
+    if (c->K > 0 && (!(sg_max_of(*c) > 0.0) || !(sg_min_of(*c) >= 0.0))) return PIC_EINVAL;
+  }
   const int64_t ncell = (int64_t)c->n * c->n * c->n;
   if (ncell > 2147483647LL) return PIC_EINVAL;
   return PIC_OK;
@@ -770,7 +832,7 @@ pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
     CK(launch_store_dv32(c, c->stage, c->stage + 3 * c->P.np));
   } else {
     if (c->cfg.K > 0) {
-      CK(launch_dsmc(c, (uint32_t)(2 * c->step + phase), true));
+      CK(launch_dsmc(c, (uint32_t)(2 * c->step + phase), true, time_at(c, (double)c->step)));
     } else {
       for (int d = 0; d < 3; ++d) {
         CK(cudaMemsetAsync(c->dv[d], 0, (size_t)c->P.np * 8, c->stream));

@@ -44,6 +44,11 @@ struct Params {
   int verify;                      // PIC_VERIFY_* bits
   unsigned long long* ang_hist;    // [2][PIC_ANGLE_BINS] when recording angles
   double E_app[3];                 // uniform applied field in the push (adjoint parameter; 0 otherwise)
+  int dist;                        // PIC_DIST_*
+  int n_sigma;                     // 0: hard sphere; 1..3: odd-power sigma(g)
+  double sigma_n[3];               // sigma_k (zero beyond n_sigma)
+  double src_pref_n;               // w dt / (2 dV): multiplies (c - 1) sum_k sigma_k f_k
+  double vbar, t_ref;              // PIC_DIST_PAPER
 };
 
 
@@ -132,6 +137,10 @@ __device__ __forceinline__ int cell_coord(double x, int n) {
 // 2 pi phibar e^{t/(2T)} of grad phi^M.
 struct TimeTerms {
   double t, ct, cos2ct, sin2ct, em_amp;
+  // PIC_DIST_PAPER: per axis A_d, s_d of f_{x_d} = 1 + A_d sin(2 pi (x - s_d)),
+  // their time derivatives, cos and sin of 2 pi s_d, and vh_d, vh_d'
+  double fA[3], fs[3], fdA[3], fds[3], fcs[3], fsn[3];
+  double vh[3], dvh[3];
 };
 
 // G^{-1}(T) by cubic Hermite interpolation of the knot table (T any real:
@@ -176,6 +185,145 @@ __device__ __forceinline__ double xm_solve(const Params& P, const TimeTerms& tt,
 // xdot^M = A c [sin(2 pi (x^M - c t)) + sin(2 pi c t)] / (1 + A sin(2 pi (x^M - c t)))
 __device__ __forceinline__ double xm_dot(const Params& P, const TimeTerms& tt, double s) {
   return P.fx_amp * P.fx_speed * (s + tt.sin2ct) / (1.0 + P.fx_amp * s);
+}
+
+// PIC_DIST_PAPER: x_d^M(t) solves F_{x_d}(x, t) = xi for f_{x_d} = 1 + A
+// sin(2 pi (x - s)), A and s varying in time. With y = x - s the equation
+// is G(y) = y - A/(2 pi) cos(2 pi y) = T, T = xi - s - A/(2 pi) cos(2 pi s)
+// (G' = 1 + A sin >= 1 - |A| > 0, root within |A|/(2 pi) of T): Newton from
+// y = T, kept inside a bracket that every step narrows (bisection where a
+// step leaves it). Returns x^M = y + s, with sin and cos of 2 pi y.
+__device__ __forceinline__ double xm_solve_gen(const TimeTerms& tt, int d, double xi, double* sy, double* cy) {
+  const double A = tt.fA[d], a2p = A / kTwoPi;
+  const double T = xi - tt.fs[d] - a2p * tt.fcs[d];
+  const double r = fabs(a2p);
+  double lo = T - r, hi = T + r, y = T;
+  for (int it = 0; it < 64; ++it) {
+    double s, c;
+    sincospi(2.0 * y, &s, &c);
+    const double G = y - a2p * c - T;
+    if (G == 0.0) break;
+    if (G < 0.0) lo = y; else hi = y;
+    double yn = y - G / (1.0 + A * s);
+    if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+    const bool done = fabs(yn - y) <= 0x1p-52;
+    y = yn;
+    if (done) break;
+  }
+  sincospi(2.0 * y, sy, cy);
+  return y + tt.fs[d];
+}
+
+// xdot^M = -(1/f) int_0^{x^M} d/dt f = [A s' (sin 2 pi y + sin 2 pi s) -
+// A'/(2 pi) (cos 2 pi s - cos 2 pi y)] / (1 + A sin 2 pi y), y = x^M - s.
+__device__ __forceinline__ double xm_dot_gen(const TimeTerms& tt, int d, double sy, double cy) {
+  const double A = tt.fA[d];
+  return (A * tt.fds[d] * (sy + tt.fsn[d]) - tt.fdA[d] / kTwoPi * (tt.fcs[d] - cy)) / (1.0 + A * sy);
+}
+
+// PIC_DIST_PAPER: tau(xi) with G(tau) = (1 + erf tau)/2 - tau e^{-tau^2}/sqrt pi
+// = xi, the quantile of the standardised f_v (v^M = vh(t) tau). G is odd
+// about 1/2, so |tau| solves P(|tau|) = |2 xi - 1| with P(t) = erf t -
+// (2/sqrt pi) t e^{-t^2}; below P = 1/2 by Newton on P^{1/3} (P ~ 4 t^3 /
+// (3 sqrt pi) near 0, summed as its alternating series there), above it by
+// Newton on log Q, Q = 1 - P = erfc t + (2/sqrt pi) t e^{-t^2} = 2 min(xi,
+// 1 - xi) (exact), each inside a bracket with bisection as the fallback.
+__device__ __forceinline__ double tau_P(double t) {
+  const double two_sqpi = 1.1283791670955126;  // 2/sqrt(pi)
+  if (t < 0.5) {
+    // (2/sqrt pi) sum_{k>=1} (-1)^{k+1} 2k/(2k+1) t^{2k+1}/k!
+    const double t2 = t * t;
+    double term = t, acc = 0.0;
+    for (int k = 1; k <= 24; ++k) {
+      term *= t2 / (double)k;   // t^{2k+1}/k!
+      const double c = (2.0 * k) / (2.0 * k + 1.0) * term;
+      acc += (k & 1) ? c : -c;
+    }
+    return two_sqpi * acc;
+  }
+  return erf(t) - two_sqpi * t * exp(-t * t);
+}
+__device__ __forceinline__ double tau_inv(double xi) {
+  const double two_sqpi = 1.1283791670955126, four_sqpi = 2.2567583341910252;
+  const bool neg = xi < 0.5;
+  const double q = neg ? 2.0 * xi : 2.0 * (1.0 - xi);   // Q(|tau|), exact
+  double t;
+  if (q >= 0.5) {
+    const double r = 1.0 - q;                           // P(|tau|), exact
+    if (r <= 0.0) return 0.0;
+    const double r3 = cbrt(r);
+    double lo = 0.0, hi = 1.2;
+    t = cbrt(0.75 * 1.7724538509055160 * r);            // P ~ 4 t^3/(3 sqrt pi)
+    if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+    for (int it = 0; it < 80; ++it) {
+      const double P = tau_P(t);
+      const double h = cbrt(P) - r3;
+      if (h == 0.0) break;
+      if (h < 0.0) lo = t; else hi = t;
+      const double dP = four_sqpi * t * t * exp(-t * t);
+      double tn = t - h * 3.0 * cbrt(P) * cbrt(P) / dP;
+      if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+      const bool done = fabs(tn - t) <= 0x1p-53 * t;
+      t = tn;
+      if (done) break;
+    }
+  } else {
+    const double lq = log(q);
+    double lo = 0.8, hi = 7.0;
+    t = sqrt(-log(q * 0.88622692545275801));            // Q ~ (2/sqrt pi) t e^{-t^2}
+    if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+    for (int it = 0; it < 80; ++it) {
+      const double e = exp(-t * t);
+      const double Q = erfc(t) + two_sqpi * t * e;
+      const double h = log(Q) - lq;                     // decreasing in t
+      if (h == 0.0) break;
+      if (h > 0.0) lo = t; else hi = t;
+      const double dlogQ = -four_sqpi * t * t * e / Q;
+      double tn = t - h / dlogQ;
+      if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+      const bool done = fabs(tn - t) <= 0x1p-53 * t;
+      t = tn;
+      if (done) break;
+    }
+  }
+  return neg ? -t : t;
+}
+
+// <Delta v^M> of Eq. vel_change_3 for sigma(g) = sum_k sigma_k g^{2k-1}
+// (k < 3): src_pref_n (c - 1) sum_k sigma_k f_k with f_k = E[g^{2k} (v_q -
+// v_p)] (Eq. fn) in closed form. Gaussian f_v (mean mu, width s), M = mu - v:
+// f_0 = M, f_1 = (|M|^2 + 5 s^2) M, f_2 = (|M|^4 + 14 s^2 |M|^2 + 35 s^4) M.
+// The paper's f_v (scales vh at the call's time): the f_0, f_1, f_2 of
+// Sec. 3.3.
+__device__ __forceinline__ void odd_source(const Params& P, const double* vh, double vx, double vy, double vz,
+                                           int c, double* out) {
+  const double pref = P.src_pref_n * (double)(c - 1);
+  const double s0 = P.sigma_n[0], s1 = P.sigma_n[1], s2 = P.sigma_n[2];
+  if (P.dist == PIC_DIST_CONFIG) {
+    const double mx = P.vmean[0] - vx, my = P.vmean[1] - vy, mz = P.vmean[2] - vz;
+    const double m2 = mx * mx + my * my + mz * mz, q2 = P.vsig * P.vsig;
+    const double k = pref * (s0 + s1 * (m2 + 5.0 * q2) + s2 * (m2 * m2 + 14.0 * q2 * m2 + 35.0 * q2 * q2));
+    out[0] = k * mx; out[1] = k * my; out[2] = k * mz;
+    return;
+  }
+  const double v[3] = {vx, vy, vz};
+  const double a2[3] = {vh[0] * vh[0], vh[1] * vh[1], vh[2] * vh[2]};
+  const double vh2 = a2[0] + a2[1] + a2[2], vp2 = vx * vx + vy * vy + vz * vz;
+  const double cross = a2[0] * vx * vx + a2[1] * vy * vy + a2[2] * vz * vz;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double others = a2[(i + 1) % 3] * a2[(i + 2) % 3];
+    const double f1 = -0.5 * (3.0 * vh2 + 6.0 * a2[i] + 2.0 * vp2);
+    const double f2 = -0.25 * (15.0 * vh2 * vh2 + 36.0 * a2[i] * a2[i] + 24.0 * vp2 * a2[i] + 4.0 * vp2 * vp2 +
+                               24.0 * a2[i] * vh2 + 12.0 * vp2 * vh2 + 24.0 * cross - 12.0 * others);
+    out[i] = pref * (-s0 + s1 * f1 + s2 * f2) * v[i];
+  }
+}
+
+// sigma(g) g = sigma_0 + sigma_1 g^2 + sigma_2 g^4 (zero coefficients beyond
+// n_sigma), summed in ascending order without contraction.
+__device__ __forceinline__ double sigma_g(const Params& P, double g2) {
+  return __dadd_rn(__dadd_rn(P.sigma_n[0], __dmul_rn(P.sigma_n[1], g2)), __dmul_rn(P.sigma_n[2], __dmul_rn(g2, g2)));
 }
 
 // E^M = -grad phi^M at x (time terms in tt).
@@ -483,7 +631,7 @@ cudaError_t launch_cg_on(pic_ctx* c, double* b, double* x, const double* rhs_par
                          double* E1, double* E2);
 using StepHook = std::function<cudaError_t(int)>;
 cudaError_t step_fp64(pic_ctx* c, int64_t n, const StepHook* hook);
-cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate_source);
+cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate_source, double t_src);
 // kick at time tE; drift to th if drift. Reuses / refreshes c->lor.
 cudaError_t launch_kick(pic_ctx* c, double tE, bool with_collisions, bool drift, double th, double tn1);
 cudaError_t launch_errors(pic_ctx* c, double t);

@@ -28,7 +28,8 @@ def test_exports_every_declared_symbol(L):
 
 def test_struct_layout_matches_header(L):
     # pic_config: 2 int32, int64, 13 doubles incl. arrays..., checked by size
-    assert ctypes.sizeof(_lib.PicConfig) == 4 + 4 + 8 + 8 * 5 + 8 * 2 + 8 * 2 + 24 + 8 + 8 * 2 + 24 + 4 * 4 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(_lib.PicConfig) == (4 + 4 + 8 + 8 * 5 + 8 * 2 + 8 * 2 + 24 + 8 + 8 * 2 + 24 + 4 * 4 + 8 + 8
+                                             + 4 + 4 + 4 + 4 + 24 + 8 + 8)
     assert ctypes.sizeof(_lib.PicErrors) == 14 * 8
     assert ctypes.sizeof(_lib.PicAngleStats) == 8 + 16 + 4 * 8
 
@@ -117,3 +118,39 @@ def test_workload_recipes():
         assert math.isclose(q["dt"] * q["steps"], 0.5)
         assert q["sigma0"] == workloads.refinement_level(0)["sigma0"]
     assert workloads.precision_form()["n_particles"] == 134217728
+
+
+@pytest.mark.parametrize("over", [
+    dict(dist=2), dict(n_sigma=4), dict(n_sigma=-1),
+    dict(precision=1),                       # the paper's problem is FP64-only
+    dict(n_sigma=0),                         # collisions need the odd-power source there
+    dict(verify=_lib.PIC_VERIFY_ISOLATE),
+    dict(v_bar=0.0), dict(t_ref=-1.0),
+    dict(sigma_n=(1.0, -1.0, 0.0)),          # sigma g negative inside [0, g_max]
+    dict(sigma_n=(0.0, 0.0, 0.0)),           # (sigma g)_max = 0
+    dict(sigma_n=(float("nan"), 0.0, 0.0)),
+])
+def test_paper_problem_configs_validate(L, over):
+    good = make_config(workloads.paper_small())
+    assert L.pic_validate_config(ctypes.byref(good)) == _lib.PIC_OK
+    c = make_config(dict(workloads.paper_small(), **over))
+    assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_EINVAL
+    # the odd-power cross section with the Gaussian form: FP64 only
+    g = make_config(dict(workloads.smallest(), n_sigma=2, sigma_n=(1.0, 0.5, 0.0)))
+    assert L.pic_validate_config(ctypes.byref(g)) == _lib.PIC_OK
+    g = make_config(dict(workloads.smallest(), n_sigma=2, sigma_n=(1.0, 0.5, 0.0), precision=1))
+    assert L.pic_validate_config(ctypes.byref(g)) == _lib.PIC_EINVAL
+    # collisionless paper problem needs no cross section
+    q = make_config(workloads.paper_table1_level(0, collisions=False))
+    assert L.pic_validate_config(ctypes.byref(q)) == _lib.PIC_OK
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_paper_problem_pmax_matches_oracle(L, level):
+    """P_coll,max of the odd-power cross section: the host's maximum of
+    sigma(g) g over [0, g_max] gives the oracle's value to the last bit, and
+    Table 1's 1/P_coll,max at the first level."""
+    p = workloads.paper_table1_level(level)
+    assert derived(p)["pmax"] == O.pmax(O.make_cfg(p))
+    if level == 0:
+        assert abs(derived(p)["inv_pmax"] - workloads.TABLE1_INV_PMAX_L1) < 1e-10

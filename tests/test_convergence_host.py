@@ -51,7 +51,8 @@ def test_group_errors():
 
 
 def test_study_tables_are_consistent():
-    for table in (C.TABLE1_COLLISIONAL, C.TABLE1_COLLISIONLESS, C.REFINE):
+    for table in (C.TABLE1_COLLISIONAL, C.TABLE1_COLLISIONLESS, C.PAPER_COLLISIONAL, C.PAPER_COLLISIONLESS,
+                  C.REFINE):
         for name, (over, pred) in table.items():
             assert set(pred) <= {"x", "v", "phi", "x2", "v2"}
             assert set(over) <= {"verify", "couple_qm_zero", "couple_q_zero", "K"}
@@ -59,3 +60,14 @@ def test_study_tables_are_consistent():
     for name, (over, _) in C.TABLE1_COLLISIONAL.items():
         if name.startswith("isolated"):
             assert over["couple_qm_zero"] == 1 and over["verify"] & C.ISO
+
+
+def test_paper_table1_schedule():
+    for lvl, steps, nax, ncell, navg, inv_p, np_coll, np_free in _table1():
+        l = int(lvl) - 1
+        p = W.paper_table1_level(l, collisions=True)
+        q = W.paper_table1_level(l, collisions=False)
+        assert p["n"] == nax and p["steps"] == steps and abs(p["dt"] * steps - 1.0) < 1e-15
+        assert p["n_particles"] == np_coll and p["K"] == navg and q["n_particles"] == np_free and q["K"] == 0
+        assert abs(1.0 / derived(p)["pmax"] / inv_p - 1.0) < 2e-4
+        assert p["dist"] == 1 and p["n_sigma"] == 3 and q["n_sigma"] == 0
