@@ -265,9 +265,11 @@ pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
 
 /* One K-averaged collision call (Eq. avg_outcome, Algorithm 1) on the
  * current state: counter word 2 step + phase (phase 0 or 1). Writes
- * <Delta v_p>_coll to dv and the analytic <Delta v_p^M>_coll of Eq.
- * vel_change_1c (hard spheres, Gaussian f_v) to dvM, both [N_p][3], pid
- * indexed, host or device. Does not change the state. */
+ * <Delta v_p>_coll to dv and the analytic <Delta v_p^M>_coll to dvM (Eq.
+ * vel_change_1c for hard spheres with the Gaussian f_v, Eqs. vel_change_3
+ * and fn for the odd-power cross section, f_v at the context's current
+ * time), both [N_p][3], pid indexed, host or device. Does not change the
+ * state. */
 pic_status pic_collide_avg(pic_ctx* ctx, int32_t phase, double* dv, double* dvM);
 
 /* Error norms of Sec. 4.3 at the current time into *out (host). */
