@@ -95,6 +95,8 @@ struct Rhs32Consts {
   float h, two_pi_over, lap_scale;   // h, phi^M amplitude / (2 pi) * e^{t/2T}, -3 (2 pi)^2
   float shift[3], ct, fx_amp;
   float rhoM_scale, inv_eps0;         // q N, 1/eps0
+  int paper;                          // PIC_DIST_PAPER: per-axis amplitude fA and phase fs
+  float fA[3], fs[3];
 };
 
 __global__ void __launch_bounds__(kThreads) k_rhs32(RhsArgs a, Rhs32Consts k) {
@@ -119,8 +121,11 @@ __global__ void __launch_bounds__(kThreads) k_rhs32(RhsArgs a, Rhs32Consts k) {
     const float X = (float)i * k.h, Y = (float)j * k.h, Z = (float)kk0 * k.h;
     const float phiM = k.two_pi_over * sinpif(2.f * (X - k.shift[0])) * sinpif(2.f * (Y - k.shift[1])) *
                        sinpif(2.f * (Z - k.shift[2]));
-    const float rhoM = k.rhoM_scale * (1.f + k.fx_amp * sinpif(2.f * (X - k.ct))) *
-                       (1.f + k.fx_amp * sinpif(2.f * (Y - k.ct))) * (1.f + k.fx_amp * sinpif(2.f * (Z - k.ct)));
+    const float rhoM =
+        k.paper ? k.rhoM_scale * (1.f + k.fA[0] * sinpif(2.f * (X - k.fs[0]))) *
+                      (1.f + k.fA[1] * sinpif(2.f * (Y - k.fs[1]))) * (1.f + k.fA[2] * sinpif(2.f * (Z - k.fs[2])))
+                : k.rhoM_scale * (1.f + k.fx_amp * sinpif(2.f * (X - k.ct))) *
+                      (1.f + k.fx_amp * sinpif(2.f * (Y - k.ct))) * (1.f + k.fx_amp * sinpif(2.f * (Z - k.ct)));
     const float bv = (float)(rho * (double)k.inv_eps0) - k.lap_scale * phiM - rhoM * k.inv_eps0;
     a.rho[id] = rho;
     a.b32[id] = bv;
@@ -375,6 +380,11 @@ cudaError_t launch_rhs(pic_ctx* c, double t) {
     k.fx_amp = (float)c->P.fx_amp;
     k.rhoM_scale = (float)(c->P.q_eff * c->P.nphys);
     k.inv_eps0 = (float)(1.0 / c->P.eps0);
+    k.paper = c->P.dist == PIC_DIST_PAPER;
+    for (int d = 0; d < 3; ++d) {
+      k.fA[d] = (float)a.tt.fA[d];
+      k.fs[d] = (float)(a.tt.fs[d] - floor(a.tt.fs[d]));
+    }
     k_rhs32<<<(int)c->rhs_blocks, kThreads, 0, c->stream>>>(a, k);
   } else {
     k_rhs<<<(int)c->rhs_blocks, kThreads, 0, c->stream>>>(a);

@@ -39,12 +39,17 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
   const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
                         unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
   double x[3], v[3], vm[3];
+  const bool paper = P.dist == PIC_DIST_PAPER;
   for (int d = 0; d < 3; ++d) {
-    double s;
-    vm[d] = P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
+    double s, cc;
+    // the paper's f_v: the v^M array holds tau, v^M(t) = vh(t) tau
+    vm[d] = paper ? tau_inv(xi[3 + d]) : P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
     if (a.xv) {
       x[d] = a.xv[3 * i + d];
       v[d] = a.xv[3 * P.np + 3 * i + d];
+    } else if (paper) {
+      x[d] = wrap_unit(xm_solve_gen(a.tt, d, xi[d], &s, &cc));
+      v[d] = vm[d] * a.tt.vh[d];
     } else {
       x[d] = wrap_unit(xm_solve(P, a.tt, xi[d], &s));
       v[d] = vm[d];
@@ -345,6 +350,7 @@ struct Dsmc32Args {
   int64_t ngroups;
   unsigned long long* counters;
   int* flags;
+  float vh[3];             // PIC_DIST_PAPER: f_v scales at the call's time
 };
 
 struct Counts32 {
@@ -393,13 +399,21 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
     load_vel_f((int)q, bm, ov, v0, v1, v2, vq);
     const float dx = vp[0] - vq[0], dy = vp[1] - vq[1], dz = vp[2] - vq[2];
     const float g2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    // accept if U < sigma g / (sigma g)_max = g / g_max, i.e. (U g_max)^2 < g^2
-    const float ug = unif24(b0.z) * gmax;
-    const float ug2 = ug * ug;
+    // accept if U < sigma g / (sigma g)_max: hard spheres g / g_max, i.e.
+    // (U g_max)^2 < g^2; odd-power sigma U (sigma g)_max < sum_k sigma_k g^2k
+    float lhs, rhs;
+    if (P.n_sigma == 0) {
+      const float ug = unif24(b0.z) * gmax;
+      lhs = ug * ug;
+      rhs = g2;
+    } else {
+      lhs = unif24(b0.z) * P.sgmax;
+      rhs = fmaf(fmaf(P.sigma_n[2], g2, P.sigma_n[1]), g2, P.sigma_n[0]);
+    }
     ++cnt.cand;
     if (g2 > P.gmax2) ++cnt.gmax;
-    if (fabsf(ug2 - g2) < 2e-6f * g2) ++cnt.tie;
-    if (ug2 < g2) {
+    if (fabsf(lhs - rhs) < 2e-6f * fabsf(rhs)) ++cnt.tie;
+    if (lhs < rhs) {
       const float g = sqrtf(g2);
       if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
         // injected Error 2: swap with probability 1/2 (coin = chi draw)
@@ -514,16 +528,23 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
           if (!last) {
             a.dv0[j] = acc0; a.dv1[j] = acc1; a.dv2[j] = acc2;
           } else {
-            const float mx = mu0 - w0, my = mu1 - w1, mz = mu2 - w2;
-            const float am = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz))) * ivs;
-            const float f = pref * (float)(cc - 1) * vs * hs_R_f(P, am);
+            // analytic <Delta v^M> (hard spheres: f m with m = mu - v)
+            float sm[3];
+            if (P.n_sigma == 0) {
+              const float mx = mu0 - w0, my = mu1 - w1, mz = mu2 - w2;
+              const float am = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz))) * ivs;
+              const float f = pref * (float)(cc - 1) * vs * hs_R_f(P, am);
+              sm[0] = f * mx; sm[1] = f * my; sm[2] = f * mz;
+            } else {
+              odd_source_f(P, a.vh, w0, w1, w2, cc, sm);
+            }
             if (separate) {
               a.dv0[j] = acc0 * invK; a.dv1[j] = acc1 * invK; a.dv2[j] = acc2 * invK;
-              a.m0[j] = f * mx; a.m1[j] = f * my; a.m2[j] = f * mz;
+              a.m0[j] = sm[0]; a.m1[j] = sm[1]; a.m2[j] = sm[2];
             } else {
-              a.dv0[j] = fmaf(acc0, invK, -f * mx);
-              a.dv1[j] = fmaf(acc1, invK, -f * my);
-              a.dv2[j] = fmaf(acc2, invK, -f * mz);
+              a.dv0[j] = fmaf(acc0, invK, -sm[0]);
+              a.dv1[j] = fmaf(acc1, invK, -sm[1]);
+              a.dv2[j] = fmaf(acc2, invK, -sm[2]);
             }
           }
         }
@@ -565,9 +586,10 @@ struct Kick32Args {
   int32_t *key, *rank, *count;
 };
 
-// kIsolate: the isolated-collision drift of Sec. 5.4 (kept out of the
-// plain kernel, whose register budget it would raise)
-template <bool kIsolate>
+// kMode 0: the plain step; 1: the isolated-collision drift of Sec. 5.4;
+// 2: the paper's problem (per-axis x^M solve, vdot^M). Kept apart so that
+// the plain kernel keeps its register budget.
+template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const ParamsF& P = a.P;
@@ -582,10 +604,9 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   if (a.dv0) { dv[0] = a.dv0[j]; dv[1] = a.dv1[j]; dv[2] = a.dv2[j]; }
   float vm[3] = {0.f, 0.f, 0.f};
   uint32_t p = 0;
-  if (a.drift) {
-    vm[0] = a.m0[j]; vm[1] = a.m1[j]; vm[2] = a.m2[j];
-    p = a.pid[j];
-  }
+  constexpr bool paper = kMode == 2, kIsolate = kMode == 1;
+  if (a.drift || paper) { vm[0] = a.m0[j]; vm[1] = a.m1[j]; vm[2] = a.m2[j]; }
+  if (a.drift) p = a.pid[j];
   int ci[3];
   cell_ijk(P, c, ci);
   float L[3];
@@ -621,8 +642,14 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
       a.L0[j] = L[0]; a.L1[j] = L[1]; a.L2[j] = L[2];
     }
   }
+  if (paper) {
+    // v^M arrays hold tau: vdot^M(t) = vh'(t) tau (Eq. velocity_verlet)
 #pragma unroll
-  for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, L[d] + dv[d], v[d]);
+    for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, (L[d] + dv[d]) + P.dt * (vm[d] * a.tE.dvh[d]), v[d]);
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, L[d] + dv[d], v[d]);
+  }
   a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
   if (!a.drift) return;
   const U4 b0 = philox(p, 0u, 0u, 0xFFFFFF00u, P.key0, P.key1);
@@ -632,7 +659,11 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     float on;
-    if (kIsolate) {
+    if (paper) {
+      float sy, cy;
+      xm_sc_gen_f(a.th, d, xi[d], &sy, &cy);
+      on = fmaf(P.dtn, v[d] + xm_dot_gen_f(a.th, d, sy, cy) - vm[d] * a.th.vh[d], o[d]);
+    } else if (kIsolate) {
       // exact manufactured increment y(t_{n+1}) - y(t_n) + c dt (Sec. 5.4)
       const float dy = xm_y_f(P, a.t1, xi[d]) - xm_y_f(P, a.t0, xi[d]);
       on = fmaf(P.dtn, v[d] - vm[d], o[d]) + P.nf * (dy + P.cdt);
@@ -981,15 +1012,17 @@ __global__ void __launch_bounds__(kThreads) k_err_partial32(Err32Args a) {
       const int ci[3] = {c % n, (c / n) % n, c / (n * n)};
       const float os[3] = {a.o0[j], a.o1[j], a.o2[j]};
       const float vs[3] = {a.v0[j], a.v1[j], a.v2[j]};
+      const bool paper = P.dist == PIC_DIST_PAPER;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        double s;
-        const double xm = xm_solve(P, a.tt, xi[d], &s);
+        double s, cc;
+        const double xm = paper ? xm_solve_gen(a.tt, d, xi[d], &s, &cc) : xm_solve(P, a.tt, xi[d], &s);
         double e = ((double)ci[d] + (double)os[d]) * P.h - xm;
         e -= floor(e + 0.5);
         vals[d] = e * e;
         vals[7 + d] = fabs(e);
-        const double ev = (double)vs[d] - (P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]));
+        const double vmd = paper ? tau_inv(xi[3 + d]) * a.tt.vh[d] : P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
+        const double ev = (double)vs[d] - vmd;
         vals[3 + d] = ev * ev;
         vals[10 + d] = fabs(ev);
       }
@@ -1131,9 +1164,11 @@ const void* dsmc32_kernel_ptr(bool verify) {
 int cg32_threads() { return kCgThreads; }
 const void* cg32_kernel_ptr() { return (const void*)k_cg32; }
 
-cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate) {
+cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate, double t_src) {
   Dsmc32Args a;
   a.P = params_f(c->P);
+  const TimeTermsF ts = to_float(time_terms(c->P, t_src));
+  for (int d = 0; d < 3; ++d) a.vh[d] = ts.vh[d];
   const int b = c->cur;
   a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
   a.start = c->start;
@@ -1183,10 +1218,12 @@ cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, dou
   a.rank = c->rank;
   a.count = c->count;
   prof_begin(c);
-  if (c->P.verify & PIC_VERIFY_ISOLATE)
-    k_kick32<true><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  if (c->P.dist == PIC_DIST_PAPER)
+    k_kick32<2><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  else if (c->P.verify & PIC_VERIFY_ISOLATE)
+    k_kick32<1><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
   else
-    k_kick32<false><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+    k_kick32<0><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
   prof_end(c, KC_KICK);
   c->launches++;
   c->lor_valid = !drift;
@@ -1390,6 +1427,12 @@ ParamsF params_f(const Params& P) {
   f.nf = (float)P.n;
   f.cdt = (float)(P.fx_speed * P.dt);
   f.ang_hist = P.ang_hist;
+  f.dist = P.dist;
+  f.n_sigma = P.n_sigma;
+  for (int k = 0; k < 3; ++k) f.sigma_n[k] = (float)P.sigma_n[k];
+  f.sgmax = (float)P.sg_max;
+  f.src_pref_n = (float)P.src_pref_n;
+  f.dt = (float)P.dt;
   return f;
 }
 }  // namespace pic

@@ -10,6 +10,8 @@ namespace pic {
 // ---------------------------------------------------------------- helpers --
 struct TimeTermsF {
   float ct, cos2ct, sin2ct, em_amp;
+  // PIC_DIST_PAPER: the per-axis terms of TimeTerms in FP32
+  float fA[3], fs[3], fdA[3], fds[3], fcs[3], fsn[3], vh[3], dvh[3];
 };
 
 __host__ __device__ inline TimeTermsF to_float(const TimeTerms& t) {
@@ -18,6 +20,17 @@ __host__ __device__ inline TimeTermsF to_float(const TimeTerms& t) {
   f.cos2ct = (float)t.cos2ct;
   f.sin2ct = (float)t.sin2ct;
   f.em_amp = (float)t.em_amp;
+  for (int d = 0; d < 3; ++d) {
+    // the phase enters only through sin/cos(2 pi (x - s)): reduce it mod 1
+    f.fA[d] = (float)t.fA[d];
+    f.fs[d] = (float)(t.fs[d] - floor(t.fs[d]));
+    f.fdA[d] = (float)t.fdA[d];
+    f.fds[d] = (float)t.fds[d];
+    f.fcs[d] = (float)t.fcs[d];
+    f.fsn[d] = (float)t.fsn[d];
+    f.vh[d] = (float)t.vh[d];
+    f.dvh[d] = (float)t.dvh[d];
+  }
   return f;
 }
 
@@ -97,6 +110,60 @@ __device__ __forceinline__ float xm_y_f(const ParamsF& P, const TimeTermsF& tt, 
   float s, c;
   sincospif(2.f * y, &s, &c);
   return y - (y - P.fx_a2pi * c - T) / (1.f + P.fx_amp * s);
+}
+
+// PIC_DIST_PAPER in FP32: sin and cos of 2 pi y, y = x_d^M - s_d, for the
+// drift's xdot^M. G(y) = y - A/(2 pi) cos(2 pi y) = T (the FP64 xm_solve_gen
+// equation) by Newton from y = T inside the bracket |y - T| <= |A|/(2 pi);
+// the iteration stops once a step is below 2^-22 (FP32 resolution of y).
+__device__ __forceinline__ void xm_sc_gen_f(const TimeTermsF& tt, int d, float xi, float* sy, float* cy) {
+  const float A = tt.fA[d], a2p = A * 0.15915494309f;
+  const float T = xi - tt.fs[d] - a2p * tt.fcs[d];
+  const float r = fabsf(a2p);
+  float lo = T - r, hi = T + r, y = T, s, c;
+  for (int it = 0; it < 12; ++it) {
+    sincospif(2.f * y, &s, &c);
+    const float G = y - a2p * c - T;
+    if (G == 0.f) break;
+    if (G < 0.f) lo = y; else hi = y;
+    float yn = y - G / (1.f + A * s);
+    if (!(yn > lo && yn < hi)) yn = 0.5f * (lo + hi);
+    const bool done = fabsf(yn - y) <= 0x1p-22f;
+    y = yn;
+    if (done) break;
+  }
+  sincospif(2.f * y, sy, cy);
+}
+__device__ __forceinline__ float xm_dot_gen_f(const TimeTermsF& tt, int d, float sy, float cy) {
+  const float A = tt.fA[d];
+  return (A * tt.fds[d] * (sy + tt.fsn[d]) - tt.fdA[d] * 0.15915494309f * (tt.fcs[d] - cy)) / (1.f + A * sy);
+}
+
+// Odd-power source of Eq. vel_change_3 in FP32 (the closed forms of
+// odd_source): Gaussian f_v or the paper's f_v with scales vh.
+__device__ __forceinline__ void odd_source_f(const ParamsF& P, const float* vh, float vx, float vy, float vz, int c,
+                                             float* out) {
+  const float pref = P.src_pref_n * (float)(c - 1);
+  const float s0 = P.sigma_n[0], s1 = P.sigma_n[1], s2 = P.sigma_n[2];
+  if (P.dist == PIC_DIST_CONFIG) {
+    const float mx = P.vmean[0] - vx, my = P.vmean[1] - vy, mz = P.vmean[2] - vz;
+    const float m2 = mx * mx + my * my + mz * mz, q2 = P.vsig * P.vsig;
+    const float k = pref * (s0 + s1 * (m2 + 5.f * q2) + s2 * (m2 * m2 + 14.f * q2 * m2 + 35.f * q2 * q2));
+    out[0] = k * mx; out[1] = k * my; out[2] = k * mz;
+    return;
+  }
+  const float v[3] = {vx, vy, vz};
+  const float a2[3] = {vh[0] * vh[0], vh[1] * vh[1], vh[2] * vh[2]};
+  const float vh2 = a2[0] + a2[1] + a2[2], vp2 = vx * vx + vy * vy + vz * vz;
+  const float cross = a2[0] * vx * vx + a2[1] * vy * vy + a2[2] * vz * vz;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float others = a2[(i + 1) % 3] * a2[(i + 2) % 3];
+    const float f1 = -0.5f * (3.f * vh2 + 6.f * a2[i] + 2.f * vp2);
+    const float f2 = -0.25f * (15.f * vh2 * vh2 + 36.f * a2[i] * a2[i] + 24.f * vp2 * a2[i] + 4.f * vp2 * vp2 +
+                               24.f * a2[i] * vh2 + 12.f * vp2 * vh2 + 24.f * cross - 12.f * others);
+    out[i] = pref * (-s0 + s1 * f1 + s2 * f2) * v[i];
+  }
 }
 
 // 32 x 32 bit-matrix transpose across a warp: lane r holds row r on entry

@@ -556,10 +556,9 @@ pic_status pic_validate_config(const pic_config* c) {
   if (!(c->cg_tol > 0.0) || c->cg_maxit < 1) return PIC_EINVAL;
   if (c->verify & ~31) return PIC_EINVAL;
   if ((c->verify & PIC_VERIFY_ERROR1) && (c->verify & PIC_VERIFY_ERROR2)) return PIC_EINVAL;
-  // the paper's problem and the odd-power cross section: FP64 form only
+  // the paper's problem and the odd-power cross section (single contexts)
   if (c->dist != PIC_DIST_CONFIG && c->dist != PIC_DIST_PAPER) return PIC_EINVAL;
   if (c->n_sigma < 0 || c->n_sigma > 3) return PIC_EINVAL;
-  if ((c->dist != PIC_DIST_CONFIG || c->n_sigma > 0) && c->precision != PIC_FP64) return PIC_EINVAL;
   if (c->dist == PIC_DIST_PAPER) {
     if (!(c->v_bar > 0.0) || !isfinite(c->v_bar) || !(c->t_ref > 0.0) || !isfinite(c->t_ref)) return PIC_EINVAL;
     if (c->verify & PIC_VERIFY_ISOLATE) return PIC_EINVAL;
@@ -798,14 +797,14 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
       pic_status s = batch_step(c, n, coll);
       if (s != PIC_OK) return s;
     } else if (c->mixed) {
-      if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n), false));
+      if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n), false, tn));
       CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
       CK(launch_kick32(c, tn, coll, true, th, tn1));
       CK(launch_scan_scatter(c));
       CK(launch_gather32(c));
       CK(launch_rhs(c, tn1));
       CK(launch_cg32(c));
-      if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n + 1), false));
+      if (coll) CK(launch_dsmc32(c, (uint32_t)(2 * n + 1), false, th));
       CK(launch_kick32(c, tn1, coll, false, 0.0, 0.0));
     } else {
       CK(step_fp64(c, n, nullptr));
@@ -822,7 +821,7 @@ pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
   const size_t bytes = (size_t)c->P.np * 3 * 8;
   if (c->mixed) {
     if (c->cfg.K > 0) {
-      CK(launch_dsmc32(c, (uint32_t)(2 * c->step + phase), true));
+      CK(launch_dsmc32(c, (uint32_t)(2 * c->step + phase), true, time_at(c, (double)c->step)));
     } else {
       for (int d = 0; d < 3; ++d) {
         CK(cudaMemsetAsync(c->dvf[d], 0, (size_t)c->P.np * 4, c->stream));
@@ -1017,6 +1016,7 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   for (int r = 0; r < nrep; ++r) {
     const pic_config& c = cfgs[r];
     if (pic_validate_config(&c) != PIC_OK || c.precision != PIC_MIXED || c.verify != 0) return PIC_EINVAL;
+    if (c.dist != PIC_DIST_CONFIG || c.n_sigma != 0) return PIC_EINVAL;  // single contexts only
     // everything but n, n_particles, K, dt, sigma0 and seed is shared
     if (c.qm != c0.qm || c.q != c0.q || c.eps0 != c0.eps0 || c.n_phys != c0.n_phys || c.g_max != c0.g_max ||
         c.fx_amp != c0.fx_amp || c.fx_speed != c0.fx_speed || c.v_sigma != c0.v_sigma || c.phi_amp != c0.phi_amp ||

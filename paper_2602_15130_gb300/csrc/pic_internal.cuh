@@ -71,6 +71,8 @@ struct ParamsF {
   int verify;                      // PIC_VERIFY_* bits
   float nf, cdt;                   // n, and c dt of the manufactured drift
   unsigned long long* ang_hist;    // [2][PIC_ANGLE_BINS] when recording angles
+  int dist, n_sigma;               // PIC_DIST_*, odd-power cross section terms (0: hard sphere)
+  float sigma_n[3], sgmax, src_pref_n, dt;
 };
 
 // Per-replicate data of a batch (device copy).
@@ -655,7 +657,7 @@ cudaError_t launch_err_final(pic_ctx* c, int nblocks);
 cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv_dev);
 cudaError_t launch_keys32(pic_ctx* c);
 cudaError_t launch_gather32(pic_ctx* c);
-cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate_source);
+cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate_source, double t_src);
 cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_collisions, bool drift, double th, double tn1);
 // angle CDF errors of the recorded collisions into out (synchronises)
 cudaError_t launch_angle_stats(pic_ctx* c, pic_angle_stats* out);

@@ -122,7 +122,6 @@ def test_workload_recipes():
 
 @pytest.mark.parametrize("over", [
     dict(dist=2), dict(n_sigma=4), dict(n_sigma=-1),
-    dict(precision=1),                       # the paper's problem is FP64-only
     dict(n_sigma=0),                         # collisions need the odd-power source there
     dict(verify=_lib.PIC_VERIFY_ISOLATE),
     dict(v_bar=0.0), dict(t_ref=-1.0),
@@ -135,11 +134,12 @@ def test_paper_problem_configs_validate(L, over):
     assert L.pic_validate_config(ctypes.byref(good)) == _lib.PIC_OK
     c = make_config(dict(workloads.paper_small(), **over))
     assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_EINVAL
-    # the odd-power cross section with the Gaussian form: FP64 only
-    g = make_config(dict(workloads.smallest(), n_sigma=2, sigma_n=(1.0, 0.5, 0.0)))
-    assert L.pic_validate_config(ctypes.byref(g)) == _lib.PIC_OK
-    g = make_config(dict(workloads.smallest(), n_sigma=2, sigma_n=(1.0, 0.5, 0.0), precision=1))
-    assert L.pic_validate_config(ctypes.byref(g)) == _lib.PIC_EINVAL
+    # both forms take the paper's problem and the odd-power cross section
+    for prec in (0, 1):
+        g = make_config(dict(workloads.smallest(), n_sigma=2, sigma_n=(1.0, 0.5, 0.0), precision=prec))
+        assert L.pic_validate_config(ctypes.byref(g)) == _lib.PIC_OK
+        g = make_config(dict(workloads.paper_small(), precision=prec))
+        assert L.pic_validate_config(ctypes.byref(g)) == _lib.PIC_OK
     # collisionless paper problem needs no cross section
     q = make_config(workloads.paper_table1_level(0, collisions=False))
     assert L.pic_validate_config(ctypes.byref(q)) == _lib.PIC_OK
@@ -154,3 +154,11 @@ def test_paper_problem_pmax_matches_oracle(L, level):
     assert derived(p)["pmax"] == O.pmax(O.make_cfg(p))
     if level == 0:
         assert abs(derived(p)["inv_pmax"] - workloads.TABLE1_INV_PMAX_L1) < 1e-10
+
+
+def test_batch_rejects_the_paper_problem(L):
+    for over in (dict(dist=1, v_bar=0.1, t_ref=1.0, n_sigma=1, sigma_n=(1.0, 0.0, 0.0)),
+                 dict(n_sigma=1, sigma_n=(1.0, 0.0, 0.0))):
+        cfgs = (_lib.PicConfig * 2)(*[make_config(dict(p, **over)) for p in workloads.batched(n_rep=2)])
+        ctx = ctypes.c_void_p()
+        assert L.pic_create_batch(cfgs, 2, None, None, ctypes.byref(ctx)) == _lib.PIC_EINVAL
