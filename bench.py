@@ -42,8 +42,9 @@ def workload(name: str) -> dict:
 
     if name == "precision":
         return W.precision_form()
-    if name == "batched":
-        return {"batch": W.batched(256)}
+    if name.startswith("batched"):
+        # "batched": the 256-replicate study; "batchedN": its first N replicates
+        return {"batch": W.batched(int(name[7:]) if name[7:] else 256)}
     if name == "refine4":
         return W.refinement_level(4)
     if name.startswith("refine"):
@@ -319,7 +320,7 @@ def run_batched(args, rank: int, world: int) -> dict | None:
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    cfgs = [replica_params(p, rank * 100000) for p in workload("batched")["batch"]]
+    cfgs = [replica_params(p, rank * 100000) for p in workload(args.workload)["batch"]]
     npart = sum(p["n_particles"] for p in cfgs)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -516,7 +517,7 @@ def main():
         if rank == 0:
             print(json.dumps(run_adjoint(args)), flush=True)
         return
-    if args.workload == "batched":
+    if args.workload.startswith("batched"):
         out = run_batched(args, rank, world)
         if out is not None:
             print(json.dumps(out), flush=True)
