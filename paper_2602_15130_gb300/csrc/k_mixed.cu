@@ -369,14 +369,14 @@ __device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const floa
 template <bool kVerify>
 __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
                               const float* v1, const float* v2, uint32_t* bm, float* ov, Counts32& cnt) {
-  const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
+  const U4 u = philox_rk<true>(c0, cell, 0xFFFFFFFFu, o << 8, P.rk);
   const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
   const int npairs = (int)floorf(base + unif24(u.x));
   const float gmax = P.gmax;
   for (int s = 0; s < npairs; ++s) {
     // both blocks of the candidate up front: two independent Philox chains
-    const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
-    const U4 b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+    const U4 b0 = philox_rk<true>(c0, cell, (uint32_t)s, o << 8, P.rk);
+    const U4 b1 = philox_rk<true>(c0, cell, (uint32_t)s, (o << 8) | 1u, P.rk);
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
     uint32_t q = draw_index(b0.y, (uint32_t)c);
     if (q == p) {
@@ -386,7 +386,7 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
       uint32_t blk = 2;
       while (q == p) {
         if (blk > 255u) { q = (p + 1u) % (uint32_t)c; break; }
-        const U4 bb = philox(c0, cell, (uint32_t)s, (o << 8) | blk, P.key0, P.key1);
+        const U4 bb = philox_rk<true>(c0, cell, (uint32_t)s, (o << 8) | blk, P.rk);
         q = draw_index(bb.x, (uint32_t)c);
         if (q == p) q = draw_index(bb.y, (uint32_t)c);
         if (q == p) q = draw_index(bb.z, (uint32_t)c);
@@ -652,8 +652,8 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   }
   a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
   if (!a.drift) return;
-  const U4 b0 = philox(p, 0u, 0u, 0xFFFFFF00u, P.key0, P.key1);
-  const U4 b1 = philox(p, 0u, 0u, 0xFFFFFF01u, P.key0, P.key1);
+  const U4 b0 = philox_rk(p, 0u, 0u, 0xFFFFFF00u, P.rk);
+  const U4 b1 = philox_rk(p, 0u, 0u, 0xFFFFFF01u, P.rk);
   const float xi[3] = {unif24(b0.x), unif24(b0.z), unif24(b1.x)};
   float* op[3] = {a.o0, a.o1, a.o2};
 #pragma unroll
@@ -1404,6 +1404,10 @@ ParamsF params_f(const Params& P) {
   f.ncell = P.ncell;
   f.key0 = P.key0;
   f.key1 = P.key1;
+  for (int r = 0; r < 10; ++r) {
+    f.rk[0][r] = P.key0 + (uint32_t)r * 0x9E3779B9u;
+    f.rk[1][r] = P.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   f.h = (float)P.h;
   f.dt_qm = (float)(P.dt * P.qm_eff);
   f.dtn = (float)(P.dt * (double)P.n);

@@ -60,6 +60,7 @@ struct ParamsF {
   int log2n;                  // log2(n) when n is a power of two, else -1
   int64_t np, ncell;
   uint32_t key0, key1;
+  uint32_t rk[2][10];          // Philox round keys: key + r (Weyl constants), r = 0..9
   float h, dt_qm, dtn;        // dt q/m, dt n (drift in cell units)
   float fx_amp, fx_a2pi, fx_Ac;
   float vmean[3], vsig, inv_vsig;
@@ -105,6 +106,37 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
     c3 = lo0;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// The same generator with its ten round keys given (key0 + r 0x9E3779B9,
+// key1 + r 0xBB67AE85): where they sit in the kernel parameters, each round
+// takes them as constant operands instead of bumping the key in registers.
+// kWide forms each product as one 32 x 32 -> 64 multiply instead of separate
+// high and low halves: the same bits; measured faster in the collision
+// kernel (1.90 -> 1.87 ms per launch at 128^3) and slower in the kick (1.52
+// -> 1.56 ms), so each kernel takes the form that suits it.
+template <bool kWide = false>
+__device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        const uint32_t (&rk)[2][10]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0, lo0, hi1, lo1;
+    if (kWide) {
+      const unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53ull;
+      const unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57ull;
+      hi0 = (uint32_t)(p0 >> 32); lo0 = (uint32_t)p0;
+      hi1 = (uint32_t)(p1 >> 32); lo1 = (uint32_t)p1;
+    } else {
+      hi0 = __umulhi(0xD2511F53u, c0); lo0 = 0xD2511F53u * c0;
+      hi1 = __umulhi(0xCD9E8D57u, c2); lo1 = 0xCD9E8D57u * c2;
+    }
+    const uint32_t n0 = hi1 ^ c1 ^ rk[0][r], n2 = hi0 ^ c3 ^ rk[1][r];
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
   }
   return U4{c0, c1, c2, c3};
 }
