@@ -75,23 +75,20 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int off) {
 }
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
-// sin(2 pi (x^M - c t)) in FP32: G^{-1} from the Hermite table, one Newton
-// correction, sine updated to first order.
+// sin(2 pi (x^M - c t)) in FP32 by cubic Hermite interpolation of the
+// tabulated s(T) = sin(2 pi G^{-1}(T)) (knots behind the G^{-1} knots, exact
+// slopes): the argument T = xi - c t - A/(2 pi) cos(2 pi c t) is that of
+// xm_solve, and s has period 1 in T.
 __device__ __forceinline__ float xm_sin_f(const ParamsF& P, const TimeTermsF& tt, float xi) {
   const float T = xi - tt.ct - P.fx_a2pi * tt.cos2ct;
-  const float fl = floorf(T);
-  const float t = (T - fl) * (float)P.ginv_M;
+  const float t = (T - floorf(T)) * (float)P.ginv_M;
   int k = (int)t;
   k = k >= P.ginv_M ? P.ginv_M - 1 : k;
   const float u = t - (float)k, u2 = u * u, u3 = u2 * u, h = 1.f / (float)P.ginv_M;
-  const float2 q0 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k);
-  const float2 q1 = __ldg(reinterpret_cast<const float2*>(P.ginv_f) + k + 1);
-  const float y = fl + (2.f * u3 - 3.f * u2 + 1.f) * q0.x + (u3 - 2.f * u2 + u) * h * q0.y +
-                  (3.f * u2 - 2.f * u3) * q1.x + (u3 - u2) * h * q1.y;
-  float s, c;
-  sincospif(2.f * y, &s, &c);
-  const float dy = (y - P.fx_a2pi * c - T) / (1.f + P.fx_amp * s);
-  return s - 6.283185307f * c * dy;
+  const float2* st = reinterpret_cast<const float2*>(P.ginv_f) + (P.ginv_M + 1);
+  const float2 q0 = __ldg(st + k), q1 = __ldg(st + k + 1);
+  return (2.f * u3 - 3.f * u2 + 1.f) * q0.x + (u3 - 2.f * u2 + u) * h * q0.y + (3.f * u2 - 2.f * u3) * q1.x +
+         (u3 - u2) * h * q1.y;
 }
 
 // y = x^M - c t in FP32 (G^{-1} from the Hermite table, one Newton step):
