@@ -191,15 +191,21 @@ __device__ __forceinline__ void record_angles_f(unsigned long long* hist, bool a
 }
 
 __device__ __forceinline__ float hs_R_f(const ParamsF& P, float a) {
-  const float a2 = a * a;
-  if (a < 0.1f) {
-    float acc = P.R_series[4];
-#pragma unroll
-    for (int j = 3; j >= 0; --j) acc = fmaf(acc, a2, P.R_series[j]);
-    return acc;
+  // cubic Hermite interpolation of the tabulated R (interpolation error
+  // below 1e-10); beyond the table erf(a/sqrt 2) = 1 and e^{-a^2/2} = 0 to
+  // FP32 precision, which leaves a + 2/a - 1/a^3
+  if (a >= kRTabAmax) {
+    const float ia = 1.f / a;
+    return a + 2.f * ia - ia * ia * ia;
   }
-  const float ia = 1.f / a, ia2 = ia * ia;
-  return 0.7978845608f * (1.f + ia2) * __expf(-0.5f * a2) + (a + 2.f * ia - ia2 * ia) * erff(a * 0.7071067812f);
+  const float2* rt = reinterpret_cast<const float2*>(P.ginv_f + 4 * (P.ginv_M + 1));
+  const float t = a * ((float)kRTabM / kRTabAmax);
+  int k = (int)t;
+  k = k >= kRTabM ? kRTabM - 1 : k;
+  const float u = t - (float)k, u2 = u * u, u3 = u2 * u, h = kRTabAmax / (float)kRTabM;
+  const float2 q0 = __ldg(rt + k), q1 = __ldg(rt + k + 1);
+  return (2.f * u3 - 3.f * u2 + 1.f) * q0.x + (u3 - 2.f * u2 + u) * h * q0.y + (3.f * u2 - 2.f * u3) * q1.x +
+         (u3 - u2) * h * q1.y;
 }
 
 // cell index -> (i, j, k), by shifts when n is a power of two

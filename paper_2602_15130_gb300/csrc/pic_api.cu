@@ -105,6 +105,24 @@ void ginv_table(double A, double* out) {
   }
 }
 
+void series_coefficients(double* out);
+
+// R(a) and R'(a) in FP64: the even series sqrt(2/pi) sum_j c_j a^{2j} below
+// a = 1/2, the closed form above (see hs_R).
+void hs_R_host(double a, const double* ser, double* R, double* dR) {
+  if (a < 0.5) {
+    double r = 0.0, d = 0.0;
+    for (int j = kSeriesTerms - 1; j >= 0; --j) r = r * a * a + ser[j];
+    for (int j = kSeriesTerms - 1; j >= 1; --j) d = d * a * a + 2.0 * j * ser[j];
+    *R = r;
+    *dR = d * a;
+    return;
+  }
+  const double s = sqrt(2.0 / kPi), e = exp(-0.5 * a * a), f = erf(a / sqrt(2.0));
+  *R = s * (1.0 + 1.0 / (a * a)) * e + (a + 2.0 / a - 1.0 / (a * a * a)) * f;
+  *dR = s * e * (1.0 / a - 3.0 / (a * a * a)) + (1.0 - 2.0 / (a * a) + 3.0 / (a * a * a * a)) * f;
+}
+
 // FP32 tables of the precision form: the knots of G^{-1} (y_k, dy/dT) and
 // behind them those of s(T) = sin(2 pi G^{-1}(T)), the one quantity the
 // drift's xdot^M needs, with its exact slope ds/dT = 2 pi cos(2 pi y_k)
@@ -116,6 +134,16 @@ void ginv_table_f(const double* tab, float* tabf) {
     const double y = tab[2 * k], dy = tab[2 * k + 1];
     st[2 * k] = (float)sin(2.0 * kPi * y);
     st[2 * k + 1] = (float)(2.0 * kPi * cos(2.0 * kPi * y) * dy);
+  }
+  // then the knots (R, dR/da) of the hard-sphere moment on [0, kRTabAmax]
+  double ser[kSeriesTerms];
+  series_coefficients(ser);
+  float* rt = tabf + 4 * (kGinvM + 1);
+  for (int k = 0; k <= kRTabM; ++k) {
+    double R, dR;
+    hs_R_host((double)k * (double)kRTabAmax / kRTabM, ser, &R, &dR);
+    rt[2 * k] = (float)R;
+    rt[2 * k + 1] = (float)dR;
   }
 }
 
@@ -317,7 +345,7 @@ void for_each_buffer(pic_ctx* c, F f) {
   f((void**)&c->err_part, (size_t)c->err_blocks * 14 * 8);
   f((void**)&c->err_out, 14 * 8);
   f((void**)&c->ginv, (size_t)(kGinvM + 1) * 2 * 8);
-  f((void**)&c->ginv_f, (size_t)(kGinvM + 1) * 4 * 4);
+  f((void**)&c->ginv_f, (size_t)(kGinvM + 1) * 4 * 4 + (size_t)(kRTabM + 1) * 2 * 4);
   if (c->nrep == 0 && (c->cfg.verify & PIC_VERIFY_ANGLES)) {
     f((void**)&c->ang_hist, (size_t)2 * PIC_ANGLE_BINS * 8);
     f((void**)&c->ang_bsum, (size_t)4 * kAngleBlocks * 8);
@@ -710,7 +738,7 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   }
   {
     double* tab = (double*)malloc((size_t)(kGinvM + 1) * 2 * 8);
-    float* tabf = (float*)malloc((size_t)(kGinvM + 1) * 4 * 4);
+    float* tabf = (float*)malloc((size_t)(kGinvM + 1) * 4 * 4 + (size_t)(kRTabM + 1) * 2 * 4);
     if (!tab || !tabf) {
       free(tab);
       free(tabf);
@@ -720,7 +748,8 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
     ginv_table(c->cfg.fx_amp, tab);
     ginv_table_f(tab, tabf);
     e = cudaMemcpy(c->ginv, tab, (size_t)(kGinvM + 1) * 2 * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->ginv_f, tabf, (size_t)(kGinvM + 1) * 4 * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->ginv_f, tabf, (size_t)(kGinvM + 1) * 4 * 4 + (size_t)(kRTabM + 1) * 2 * 4,
+                                         cudaMemcpyHostToDevice);
     free(tab);
     free(tabf);
     c->P.ginv = c->ginv;
@@ -1181,12 +1210,13 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   // G^{-1} tables (shared manufactured distribution), then per-replicate copies
   {
     double* tab = (double*)malloc((size_t)(kGinvM + 1) * 2 * 8);
-    float* tabf = (float*)malloc((size_t)(kGinvM + 1) * 4 * 4);
+    float* tabf = (float*)malloc((size_t)(kGinvM + 1) * 4 * 4 + (size_t)(kRTabM + 1) * 2 * 4);
     if (tab && tabf) {
       ginv_table(c0.fx_amp, tab);
       ginv_table_f(tab, tabf);
       e = cudaMemcpy(c->ginv, tab, (size_t)(kGinvM + 1) * 2 * 8, cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(c->ginv_f, tabf, (size_t)(kGinvM + 1) * 4 * 4, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(c->ginv_f, tabf, (size_t)(kGinvM + 1) * 4 * 4 + (size_t)(kRTabM + 1) * 2 * 4,
+                                         cudaMemcpyHostToDevice);
     } else {
       e = cudaErrorMemoryAllocation;
     }

@@ -14,6 +14,11 @@ namespace pic {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
 constexpr int kSeriesTerms = 10;
+// FP32 table of the hard-sphere moment R(a) on [0, kRTabAmax]: kRTabM
+// intervals of cubic Hermite knots (R, dR/da), stored after the two G^{-1}
+// tables of the precision form
+constexpr int kRTabM = 512;
+constexpr float kRTabAmax = 8.f;
 
 // ---------------------------------------------------------------------------
 // Everything a kernel needs to know about the problem, passed by value.
