@@ -495,24 +495,24 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
         ntc_outcome_f<kVerify>(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s,
                                bm, ov, cnt);
       __syncwarp();
-      // per cell of the group and per 32-particle word: transpose the
-      // lanes' bitmap words across the warp, so lane b learns which
-      // outcomes touched particle 32 w + b, then add their changes in
-      // ascending outcome order
+      // per 32-particle word: one transpose of the lanes' bitmap words across
+      // the warp serves every cell of the group, since lane l holds outcome
+      // l % Kc of cell l / Kc: lane b receives, in the Kc-bit segment of cell
+      // cl, the outcomes that touched particle 32 w + b of that cell; their
+      // changes are then added in ascending outcome order
       const bool last = ch == a.nchunks - 1;
-      for (int cl = 0; cl < ncl; ++cl) {
-        const int32_t cs = a.start[cell0 + cl];
-        const int cc = a.start[cell0 + cl + 1] - cs;
-        const bool coll_ok = cc >= 2 && cc <= a.max_ppc;
-        const int kmax = min(a.Kc, P.K - ch * a.Kc);
-        for (int w = 0; w < (cc + 31) / 32; ++w) {
-          uint32_t mine = 0u;
-          if (coll_ok) {
-            const bool owner = lane >= cl * a.Kc && lane < cl * a.Kc + kmax;
-            mine = warp_transpose32(owner ? bm[w] : 0u, lane);
-          }
-          const int jj = 32 * w + lane;
+      const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)((c + 31) / 32));
+      const uint32_t kseg = a.Kc == 32 ? 0xffffffffu : ((1u << a.Kc) - 1u);
+      for (int w = 0; w < wmax; ++w) {
+        // lanes without collisions in this word (no cell, outcome beyond K,
+        // cell outside 2..max_ppc) hold zero words
+        const uint32_t tw = warp_transpose32(w < a.bm_words ? bm[w] : 0u, lane);
+        const int jj = 32 * w + lane;
+        for (int cl = 0; cl < ncl; ++cl) {
+          const int32_t cs = __shfl_sync(0xffffffffu, s, cl * a.Kc);
+          const int cc = __shfl_sync(0xffffffffu, c, cl * a.Kc);
           if (jj >= cc) continue;
+          uint32_t mine = tw & (kseg << (cl * a.Kc));
           const int32_t j = cs + jj;
           const float w0 = a.v0[j], w1 = a.v1[j], w2 = a.v2[j];
           float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
