@@ -313,12 +313,12 @@ struct CountsB {
 // Algorithm 1 for one (cell, outcome), as in the single-domain FP32 kernel.
 __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
                               const float* v1, const float* v2, uint32_t* bm, float* ov, CountsB& cnt) {
-  const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
+  const U4 u = philox<true>(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
   const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
   const int npairs = (int)floorf(base + unif24(u.x));
   for (int s = 0; s < npairs; ++s) {
-    const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
-    const U4 b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+    const U4 b0 = philox<true>(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
+    const U4 b1 = philox<true>(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
     uint32_t q = draw_index(b0.y, (uint32_t)c);
     if (q == p) {
@@ -328,7 +328,7 @@ __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint
       uint32_t blk = 2;
       while (q == p) {
         if (blk > 255u) { q = (p + 1u) % (uint32_t)c; break; }
-        const U4 bb = philox(c0, cell, (uint32_t)s, (o << 8) | blk, P.key0, P.key1);
+        const U4 bb = philox<true>(c0, cell, (uint32_t)s, (o << 8) | blk, P.key0, P.key1);
         q = draw_index(bb.x, (uint32_t)c);
         if (q == p) q = draw_index(bb.y, (uint32_t)c);
         if (q == p) q = draw_index(bb.z, (uint32_t)c);
@@ -410,19 +410,19 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) kb_dsmc(BDsmcArgs a) {
                       cnt);
       __syncwarp();
       const bool last = ch == nchunks - 1;
-      for (int cl = 0; cl < ncl; ++cl) {
-        const int32_t cs = start[cell0 + cl];
-        const int cc = start[cell0 + cl + 1] - cs;
-        const bool coll_ok = cc >= 2 && cc <= a.max_ppc;
-        const int kmax = min(Kc, P.K - ch * Kc);
-        for (int w = 0; w < (cc + 31) / 32; ++w) {
-          uint32_t mine = 0u;
-          if (coll_ok) {
-            const bool owner = lane >= cl * Kc && lane < cl * Kc + kmax;
-            mine = warp_transpose32(owner ? bm[w] : 0u, lane);
-          }
-          const int jj = 32 * w + lane;
+      // one transpose per 32-particle word serves every cell of the group
+      // (lane l holds outcome l % Kc of cell l / Kc; lanes without
+      // collisions hold zero words), as in the single-domain kernel
+      const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)((c + 31) / 32));
+      const uint32_t kseg = Kc == 32 ? 0xffffffffu : ((1u << Kc) - 1u);
+      for (int w = 0; w < wmax; ++w) {
+        const uint32_t tw = warp_transpose32(w < a.bm_words ? bm[w] : 0u, lane);
+        const int jj = 32 * w + lane;
+        for (int cl = 0; cl < ncl; ++cl) {
+          const int32_t cs = __shfl_sync(0xffffffffu, s, cl * Kc);
+          const int cc = __shfl_sync(0xffffffffu, c, cl * Kc);
           if (jj >= cc) continue;
+          uint32_t mine = tw & (kseg << (cl * Kc));
           const int32_t j = cs + jj;
           const float w0 = a.v0[j], w1 = a.v1[j], w2 = a.v2[j];
           float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;

@@ -98,12 +98,23 @@ struct U4 {
   uint32_t x, y, z, w;
 };
 
+// kWide: each product as one 32 x 32 -> 64 multiply (the same bits; see
+// philox_rk for when each form is used).
+template <bool kWide = false>
 __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                      uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t hi0, lo0, hi1, lo1;
+    if (kWide) {
+      const unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53ull;
+      const unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57ull;
+      hi0 = (uint32_t)(p0 >> 32); lo0 = (uint32_t)p0;
+      hi1 = (uint32_t)(p1 >> 32); lo1 = (uint32_t)p1;
+    } else {
+      hi0 = __umulhi(0xD2511F53u, c0); lo0 = 0xD2511F53u * c0;
+      hi1 = __umulhi(0xCD9E8D57u, c2); lo1 = 0xCD9E8D57u * c2;
+    }
     const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
     c0 = n0;
     c1 = lo1;
