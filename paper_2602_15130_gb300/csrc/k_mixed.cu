@@ -577,7 +577,7 @@ struct Kick32Args {
   const float *m0, *m1, *m2;
   const uint32_t* pid;
   const float *dv0, *dv1, *dv2;
-  const float *E0, *E1, *E2;
+  const float4* E4;
   float *L0, *L1, *L2;
   int lor_mode;  // 0: compute, 1: compute and store, 2: load
   TimeTermsF tE, th;
@@ -626,9 +626,10 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
         for (int q = 0; q < 2; ++q) {
           const int node = ii[q] + jj[b] + kk[cc];
           const float w = wx[q] * wy[b] * wz[cc];
-          e0 = fmaf(w, __ldg(a.E0 + node), e0);
-          e1 = fmaf(w, __ldg(a.E1 + node), e1);
-          e2 = fmaf(w, __ldg(a.E2 + node), e2);
+          const float4 en = __ldg(a.E4 + node);
+          e0 = fmaf(w, en.x, e0);
+          e1 = fmaf(w, en.y, e1);
+          e2 = fmaf(w, en.z, e2);
         }
     float s0, c0, s1, c1, s2, c2;
     sincospif(2.f * (((float)ci[0] + o[0]) * P.h - P.phi_shift[0]), &s0, &c0);
@@ -700,7 +701,7 @@ struct Cg32Args {
   double* res;
   double tol;
   int maxit;
-  float *E0, *E1, *E2;
+  float4* E4;  // (Ex, Ey, Ez, 0) per node
 };
 
 constexpr long long kBarrierCycles = 4000000000LL;
@@ -969,9 +970,8 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   for (int id = t0; id < m; id += stride) {
     const Nbr q = neighbours(id, n, nn);
     const float* x = a.x;
-    a.E0[id] = -(x[q.xp] - x[q.xm]) * a.inv_2h;
-    a.E1[id] = -(x[q.yp] - x[q.ym]) * a.inv_2h;
-    a.E2[id] = -(x[q.zp] - x[q.zm]) * a.inv_2h;
+    a.E4[id] = make_float4(-(x[q.xp] - x[q.xm]) * a.inv_2h, -(x[q.yp] - x[q.ym]) * a.inv_2h,
+                           -(x[q.zp] - x[q.zm]) * a.inv_2h, 0.f);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[0] = it;
@@ -1060,7 +1060,8 @@ __global__ void __launch_bounds__(kThreads) k_err_partial32(Err32Args a) {
 
 struct StoreField32Args {
   int64_t ncell;
-  const float *phi, *E0, *E1, *E2;
+  const float* phi;
+  const float4* E4;
   double *ophi, *oE;
 };
 
@@ -1069,9 +1070,10 @@ __global__ void __launch_bounds__(kThreads) k_store_field32(StoreField32Args a) 
   if (id >= a.ncell) return;
   if (a.ophi) a.ophi[id] = a.phi[id];
   if (a.oE) {
-    a.oE[3 * id] = a.E0[id];
-    a.oE[3 * id + 1] = a.E1[id];
-    a.oE[3 * id + 2] = a.E2[id];
+    const float4 e = a.E4[id];
+    a.oE[3 * id] = e.x;
+    a.oE[3 * id + 1] = e.y;
+    a.oE[3 * id + 2] = e.z;
   }
 }
 
@@ -1206,7 +1208,7 @@ cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, dou
   a.pid = c->pid[b];
   if (with_coll) { a.dv0 = c->dvf[0]; a.dv1 = c->dvf[1]; a.dv2 = c->dvf[2]; }
   else { a.dv0 = a.dv1 = a.dv2 = nullptr; }
-  a.E0 = c->Ef[0]; a.E1 = c->Ef[1]; a.E2 = c->Ef[2];
+  a.E4 = c->Ef4;
   a.L0 = c->lorf[0]; a.L1 = c->lorf[1]; a.L2 = c->lorf[2];
   a.lor_mode = drift ? (c->lor_valid ? 2 : 0) : 1;
   a.tE = to_float(time_terms(c->P, tE));
@@ -1250,9 +1252,7 @@ cudaError_t launch_cg32(pic_ctx* c) {
   a.res = c->cg_res;
   a.tol = c->cfg.cg_tol;
   a.maxit = c->cfg.cg_maxit;
-  a.E0 = c->Ef[0];
-  a.E1 = c->Ef[1];
-  a.E2 = c->Ef[2];
+  a.E4 = c->Ef4;
   cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c->cg_info, 0, 3 * sizeof(int), c->stream);
@@ -1364,7 +1364,7 @@ cudaError_t launch_store_field32(pic_ctx* c, double* phi, double* E) {
   StoreField32Args a;
   a.ncell = c->P.ncell;
   a.phi = c->phif;
-  a.E0 = c->Ef[0]; a.E1 = c->Ef[1]; a.E2 = c->Ef[2];
+  a.E4 = c->Ef4;
   a.ophi = phi;
   a.oE = E;
   prof_begin(c);

@@ -317,8 +317,9 @@ void for_each_buffer(pic_ctx* c, F f) {
       f((void**)&c->lorf[d], np * 4);
       f((void**)&c->dvf[d], np * 4);
       if (c->nrep == 0) f((void**)&c->dvmf[d], np * 4);  // pic_collide_avg only
-      f((void**)&c->Ef[d], nc * 4);
+      if (c->nrep > 0) f((void**)&c->Ef[d], nc * 4);
     }
+    if (c->nrep == 0) f((void**)&c->Ef4, nc * 16);
     f((void**)&c->bf, nc * 4);
     f((void**)&c->phif, nc * 4);
     f((void**)&c->cgf_r, nc * 4);
@@ -938,20 +939,26 @@ pic_status pic_get_field(pic_ctx* c, double* rho, double* phi, double* E) {
   } else if (phi || E) {
     // fewer particles than nodes: stage through host memory
     const size_t esz = c->mixed ? 4 : 8;
-    unsigned char* comp = (unsigned char*)malloc(nc * esz);
+    // the precision form's field is interleaved (Ex, Ey, Ez, 0) per node
+    unsigned char* comp = (unsigned char*)malloc(nc * (c->mixed ? 16 : esz));
     double* tmp = (double*)malloc(3 * nc * 8);
     if (!comp || !tmp) { free(comp); free(tmp); return PIC_ENOMEM; }
     const void* srcs[4] = {c->mixed ? (const void*)c->phif : (const void*)c->phi,
-                           c->mixed ? (const void*)c->Ef[0] : (const void*)c->E[0],
-                           c->mixed ? (const void*)c->Ef[1] : (const void*)c->E[1],
-                           c->mixed ? (const void*)c->Ef[2] : (const void*)c->E[2]};
+                           c->mixed ? (const void*)c->Ef4 : (const void*)c->E[0],
+                           c->mixed ? nullptr : (const void*)c->E[1],
+                           c->mixed ? nullptr : (const void*)c->E[2]};
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
-      if ((q == 0 && !phi) || (q > 0 && !E)) continue;
-      e = cudaMemcpyAsync(comp, srcs[q], nc * esz, cudaMemcpyDeviceToHost, c->stream);
+      if ((q == 0 && !phi) || (q > 0 && !E) || !srcs[q]) continue;
+      const bool e4 = c->mixed && q == 1;  // all three components at once
+      e = cudaMemcpyAsync(comp, srcs[q], nc * (e4 ? 16 : esz), cudaMemcpyDeviceToHost, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) break;
       for (size_t i = 0; i < nc; ++i) {
+        if (e4) {
+          for (int d = 0; d < 3; ++d) tmp[3 * i + d] = (double)((const float*)comp)[4 * i + d];
+          continue;
+        }
         const double val = c->mixed ? (double)((const float*)comp)[i] : ((const double*)comp)[i];
         if (q == 0) tmp[i] = val;
         else tmp[3 * i + (q - 1)] = val;
