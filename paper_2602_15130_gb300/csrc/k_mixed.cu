@@ -357,13 +357,16 @@ struct Counts32 {
   unsigned long long cand, coll, gmax, tie;
 };
 
+// a particle's working velocity: the lane's overlay copy where this outcome
+// has touched it, else the cell's velocity; the source addresses are
+// selected so that lanes of both kinds load together (no divergent branch)
 __device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const float* ov, const float* v0,
                                            const float* v1, const float* v2, float* o) {
-  if ((bm[p >> 5] >> (p & 31)) & 1u) {
-    o[0] = ov[3 * p]; o[1] = ov[3 * p + 1]; o[2] = ov[3 * p + 2];
-  } else {
-    o[0] = v0[p]; o[1] = v1[p]; o[2] = v2[p];
-  }
+  const bool t = (bm[p >> 5] >> (p & 31)) & 1u;
+  const float* s0 = t ? ov + 3 * p : v0 + p;
+  const float* s1 = t ? ov + 3 * p + 1 : v1 + p;
+  const float* s2 = t ? ov + 3 * p + 2 : v2 + p;
+  o[0] = *s0; o[1] = *s1; o[2] = *s2;
 }
 
 template <bool kVerify>
