@@ -25,6 +25,7 @@ struct Sample32Args {
   Params P;
   TimeTerms tt;
   const double* xv;  // optional caller state (pid order, [N][3] x then [N][3] v)
+  const float *vin0, *vin1, *vin2;  // optional v^M (tau for the paper's f_v) in pid order
   int32_t* cell;
   float *o0, *o1, *o2, *v0, *v1, *v2, *m0, *m1, *m2;
   uint32_t* pid;
@@ -34,16 +35,25 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Params& P = a.P;
   if (i >= P.np) return;
-  const U4 b0 = sample_block(P, (uint64_t)i, 0), b1 = sample_block(P, (uint64_t)i, 1),
-           b2 = sample_block(P, (uint64_t)i, 2);
-  const double xi[6] = {unif52(b0.x, b0.y), unif52(b0.z, b0.w), unif52(b1.x, b1.y),
-                        unif52(b1.z, b1.w), unif52(b2.x, b2.y), unif52(b2.z, b2.w)};
+  double xi[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const bool given_vm = a.vin0 != nullptr;
+  if (!a.xv || !given_vm) {
+    const U4 b0 = sample_block(P, (uint64_t)i, 0), b1 = sample_block(P, (uint64_t)i, 1),
+             b2 = sample_block(P, (uint64_t)i, 2);
+    xi[0] = unif52(b0.x, b0.y); xi[1] = unif52(b0.z, b0.w); xi[2] = unif52(b1.x, b1.y);
+    xi[3] = unif52(b1.z, b1.w); xi[4] = unif52(b2.x, b2.y); xi[5] = unif52(b2.z, b2.w);
+  }
+  const float* vin[3] = {a.vin0, a.vin1, a.vin2};
   double x[3], v[3], vm[3];
   const bool paper = P.dist == PIC_DIST_PAPER;
   for (int d = 0; d < 3; ++d) {
     double s, cc;
-    // the paper's f_v: the v^M array holds tau, v^M(t) = vh(t) tau
-    vm[d] = paper ? tau_inv(xi[3 + d]) : P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
+    // the paper's f_v: the v^M array holds tau, v^M(t) = vh(t) tau; a state
+    // loaded into a context that already holds one keeps its v^M values
+    if (given_vm)
+      vm[d] = (double)vin[d][i];
+    else
+      vm[d] = paper ? tau_inv(xi[3 + d]) : P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
     if (a.xv) {
       x[d] = a.xv[3 * i + d];
       v[d] = a.xv[3 * P.np + 3 * i + d];
@@ -1098,11 +1108,43 @@ __global__ void __launch_bounds__(kThreads) k_store_dv32(StoreDv32Args a) {
 }  // namespace
 
 // ============================================================== launches ==
-cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv) {
+// v^M (tau) of the current state from sorted order into pid order (a free
+// per-particle scratch), for a state load that keeps them
+struct VmPid32Args {
+  int64_t np;
+  const uint32_t* pid;
+  const float *m0, *m1, *m2;
+  float *o0, *o1, *o2;
+};
+__global__ void __launch_bounds__(kThreads) k_vm_to_pid32(VmPid32Args a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.np) return;
+  const uint32_t p = a.pid[j];
+  a.o0[p] = a.m0[j]; a.o1[p] = a.m1[j]; a.o2[p] = a.m2[j];
+}
+
+cudaError_t launch_vm_to_pid32(pic_ctx* c, float* const* out) {
+  VmPid32Args a;
+  a.np = c->P.np;
+  const int b = c->cur;
+  a.pid = c->pid[b];
+  a.m0 = c->vmf[b][0]; a.m1 = c->vmf[b][1]; a.m2 = c->vmf[b][2];
+  a.o0 = out[0]; a.o1 = out[1]; a.o2 = out[2];
+  prof_begin(c);
+  k_vm_to_pid32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv, float* const* vm_in) {
   Sample32Args a;
   a.P = c->P;
   a.tt = time_terms(c->P, t0);
   a.xv = xv;
+  a.vin0 = vm_in ? vm_in[0] : nullptr;
+  a.vin1 = vm_in ? vm_in[1] : nullptr;
+  a.vin2 = vm_in ? vm_in[2] : nullptr;
   const int b = c->cur;
   a.cell = c->cell32[b];
   a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];

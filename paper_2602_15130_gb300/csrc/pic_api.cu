@@ -821,9 +821,18 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
   CK(cudaMemcpyAsync(c->stage + 3 * c->P.np, v, bytes, cudaMemcpyDefault, c->stream));
   c->t0 = t0;
   c->step = step;
-  c->cur = 0;
-  if (c->mixed) CK(launch_sample32(c, time_at(c, (double)step), c->stage));
-  else CK(launch_load_state(c, c->stage, time_at(c, (double)step)));
+  if (c->mixed) {
+    // v^M is a per-particle constant (tau for the paper's f_v): a context that
+    // already holds a state keeps its values (into pid order through the
+    // free collision-term arrays) instead of re-deriving them from xi in FP64
+    const bool keep_vm = c->sampled;
+    if (keep_vm) CK(launch_vm_to_pid32(c, c->dvf));
+    c->cur = 0;
+    CK(launch_sample32(c, time_at(c, (double)step), c->stage, keep_vm ? c->dvf : nullptr));
+  } else {
+    c->cur = 0;
+    CK(launch_load_state(c, c->stage, time_at(c, (double)step)));
+  }
   pic_status s = sort_and_field(c, time_at(c, (double)step));
   if (s != PIC_OK) return s;
   c->sampled = true;
