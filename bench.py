@@ -125,11 +125,11 @@ def measured_peaks() -> dict:
 # two key additions; GB300 issues 64 INT32 lanes per SM per clock.
 INT_OPS_PER_PHILOX = 100
 INT32_LANES_PER_SM = 64
-# DRAM bytes per particle of one k_dsmc32 launch (read 202.1 MB + write
-# 120.7 MB for 8,388,608 particles at 32 per cell, K = 16; mean of the two
+# DRAM bytes per particle of one k_dsmc32 launch (read 200.7 MB + write
+# 119.9 MB for 8,388,608 particles at 32 per cell, K = 16; mean of the two
 # launches), from the capture summarised in profiles/ncu_full_mixed_refine3.md;
 # valid while that kernel is unchanged
-NCU_DSMC32_DRAM_BYTES_PER_PARTICLE = (202.1e6 + 120.7e6) / 8388608
+NCU_DSMC32_DRAM_BYTES_PER_PARTICLE = (200.7e6 + 119.9e6) / 8388608
 
 BYTES_PER_UNIT = {
     "fp64": {
