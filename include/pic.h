@@ -279,7 +279,10 @@ pic_status pic_mms_error(pic_ctx* ctx, pic_errors* out);
 pic_status pic_get_state(pic_ctx* ctx, double* x, double* v);
 
 /* Replace the particle state (x in [0,1)^3, v; [N_p][3], pid indexed, host
- * or device), set the time to t0 + step dt, re-sort and re-solve the field. */
+ * or device), set the time to t0 + step dt, re-sort and re-solve the field
+ * (the CG starts from the potential the context holds). v^M of a particle
+ * depends only on its pid and the distribution, so a context that already
+ * holds a state keeps those values rather than deriving them again. */
 pic_status pic_set_state(pic_ctx* ctx, const double* x, const double* v, double t0,
                          int64_t step);
 
