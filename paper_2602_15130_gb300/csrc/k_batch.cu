@@ -146,7 +146,8 @@ struct BCgArgs {
   const BatchRep* reps;
   const int* order;
   int R;
-  float *b, *x, *r, *p, *q, *E0, *E1, *E2;
+  float *b, *x, *r, *p, *q;
+  float4* E4;  // (Ex, Ey, Ez, 0) per node
   double tol;
   int maxit;
   int* iters;
@@ -267,9 +268,8 @@ __global__ void __launch_bounds__(kCgThreads) kb_cg(BCgArgs a) {
     for (int id = threadIdx.x; id < m; id += blockDim.x) {
       int o[6];
       nbr(id, o);
-      a.E0[B.coff + id] = -(x[o[0]] - x[o[1]]) * inv_2h;
-      a.E1[B.coff + id] = -(x[o[2]] - x[o[3]]) * inv_2h;
-      a.E2[B.coff + id] = -(x[o[4]] - x[o[5]]) * inv_2h;
+      a.E4[B.coff + id] = make_float4(-(x[o[0]] - x[o[1]]) * inv_2h, -(x[o[2]] - x[o[3]]) * inv_2h,
+                                      -(x[o[4]] - x[o[5]]) * inv_2h, 0.f);
     }
     if (threadIdx.x == 0) {
       a.iters[rep] = it;
@@ -482,7 +482,7 @@ struct BKickArgs {
   const float *m0, *m1, *m2;
   const uint32_t* pid;
   const float *dv0, *dv1, *dv2;
-  const float *E0, *E1, *E2;
+  const float4* E4;
   float *L0, *L1, *L2;
   int lor_mode;
   int drift;
@@ -522,9 +522,10 @@ __global__ void __launch_bounds__(512) kb_kick(BKickArgs a) {
         for (int q = 0; q < 2; ++q) {
           const int64_t node = base + ii[q] + jj[b] + kk[cc];
           const float w = wx[q] * wy[b] * wz[cc];
-          e0 = fmaf(w, __ldg(a.E0 + node), e0);
-          e1 = fmaf(w, __ldg(a.E1 + node), e1);
-          e2 = fmaf(w, __ldg(a.E2 + node), e2);
+          const float4 en = __ldg(a.E4 + node);
+          e0 = fmaf(w, en.x, e0);
+          e1 = fmaf(w, en.y, e1);
+          e2 = fmaf(w, en.z, e2);
         }
     const TimeTerms& tE = a.tt[3 * r + a.slotE];
     float s0, c0, s1, c1, s2, c2;
@@ -621,9 +622,7 @@ cudaError_t launch_batch_cg(pic_ctx* c) {
   a.r = c->cgf_r;
   a.p = c->cgf_p;
   a.q = c->cgf_q;
-  a.E0 = c->Ef[0];
-  a.E1 = c->Ef[1];
-  a.E2 = c->Ef[2];
+  a.E4 = c->Ef4;
   a.tol = c->cfg.cg_tol;
   a.maxit = c->cfg.cg_maxit;
   a.iters = c->cg_iters_rep;
@@ -679,7 +678,7 @@ cudaError_t launch_batch_kick(pic_ctx* c, bool with_coll, bool drift) {
   a.pid = c->pid[b];
   if (with_coll) { a.dv0 = c->dvf[0]; a.dv1 = c->dvf[1]; a.dv2 = c->dvf[2]; }
   else { a.dv0 = a.dv1 = a.dv2 = nullptr; }
-  a.E0 = c->Ef[0]; a.E1 = c->Ef[1]; a.E2 = c->Ef[2];
+  a.E4 = c->Ef4;
   a.L0 = c->lorf[0]; a.L1 = c->lorf[1]; a.L2 = c->lorf[2];
   a.lor_mode = drift ? (c->lor_valid ? 2 : 0) : 1;
   a.drift = drift ? 1 : 0;

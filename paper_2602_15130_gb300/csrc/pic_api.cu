@@ -317,9 +317,8 @@ void for_each_buffer(pic_ctx* c, F f) {
       f((void**)&c->lorf[d], np * 4);
       f((void**)&c->dvf[d], np * 4);
       if (c->nrep == 0) f((void**)&c->dvmf[d], np * 4);  // pic_collide_avg only
-      if (c->nrep > 0) f((void**)&c->Ef[d], nc * 4);
     }
-    if (c->nrep == 0) f((void**)&c->Ef4, nc * 16);
+    f((void**)&c->Ef4, nc * 16);
     f((void**)&c->bf, nc * 4);
     f((void**)&c->phif, nc * 4);
     f((void**)&c->cgf_r, nc * 4);

@@ -565,8 +565,7 @@ struct pic_ctx {
   float* dvf[3];
   float* dvmf[3];
   float* lorf[3];
-  float* Ef[3];     // batched form: E per axis
-  float4* Ef4;      // single context: (Ex, Ey, Ez, 0) per node, one 16-byte load per node in the gather
+  float4* Ef4;      // (Ex, Ey, Ez, 0) per node: one 16-byte load per node in the gather
   float* phif;
   float* bf;
   float* cgf_r;
