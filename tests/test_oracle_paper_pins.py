@@ -12,7 +12,10 @@ mathematics fix, independently of the oracle's own arithmetic:
 - the scale-family property v^M(xi, t) / vh(t) = const in t;
 - sample moments of the paper's f_v within 4 sigma / sqrt(N);
 - (sigma g)_max against a dense brute-force scan, and the Maxwell-molecule
-  special case sigma = sigma_0 / g (every candidate accepted).
+  special case sigma = sigma_0 / g (every candidate accepted);
+- the manufactured anisotropy's constants (1/2, 12/29) as the solution of
+  the least-squares problem of Sec. 5.1, and the oracle's CDF as the
+  integral of that ansatz.
 """
 import math
 
@@ -251,3 +254,38 @@ def test_maxwell_molecules_accept_every_candidate():
     o.collide_avg(0)
     st = o.stats()
     assert 0 < st["n_coll"] < 0.2 * st["n_cand"]
+
+
+# ------------------------------------------------- manufactured anisotropy --
+def _p_chi(chi, c0, c1):
+    """The ansatz of Eq. pchi_ms with the two constraints imposed."""
+    c = np.cos(chi)
+    return (c0 + c1 * c - 1.5 * (2 * c0 - 1) * c * c - 5 * c1 / 3 * c ** 3) * np.sin(chi)
+
+
+def test_anisotropy_constants_minimise_the_distance_to_the_soft_sphere_target():
+    """Sec. 5.1: with the variable-soft-sphere target p_bar = 2 cos^3(chi/2)
+    sin(chi/2) (alpha = 2, Eq. pbar) the least-squares problem of Eq.
+    anisotropy_opt is linear in (C0, C1); its solution is the printed (1/2,
+    12/29), and the oracle's CDF of the manufactured anisotropy is the
+    integral of the ansatz with these constants."""
+    pbar = lambda x: 2 * np.cos(x / 2) ** 3 * np.sin(x / 2)
+    # p = a0(chi) + C0 a1(chi) + C1 a2(chi)
+    c = lambda x: np.cos(x)
+    a0 = lambda x: 1.5 * c(x) ** 2 * np.sin(x)
+    a1 = lambda x: (1 - 3 * c(x) ** 2) * np.sin(x)
+    a2 = lambda x: (c(x) - 5 / 3 * c(x) ** 3) * np.sin(x)
+    q = lambda f: integrate.quad(f, 0, np.pi, epsabs=1e-14, epsrel=1e-13)[0]
+    M = np.array([[q(lambda x: a1(x) * a1(x)), q(lambda x: a1(x) * a2(x))],
+                  [q(lambda x: a2(x) * a1(x)), q(lambda x: a2(x) * a2(x))]])
+    rhs = np.array([q(lambda x: (pbar(x) - a0(x)) * a1(x)), q(lambda x: (pbar(x) - a0(x)) * a2(x))])
+    c0, c1 = np.linalg.solve(M, rhs)
+    assert abs(c0 - 0.5) < 1e-10 and abs(c1 - 12 / 29) < 1e-10, (c0, c1)
+    # constraints hold for any constants: unit mass and zero mean cos chi
+    for cc0, cc1 in ((0.5, 12 / 29), (0.3, -0.2), (0.9, 1.1)):
+        assert abs(q(lambda x: _p_chi(x, cc0, cc1)) - 1.0) < 1e-12
+        assert abs(q(lambda x: _p_chi(x, cc0, cc1) * np.cos(x))) < 1e-12
+    # the oracle's F(u), u = sin^2(chi/2), is the CDF of the optimal ansatz
+    for chi in (0.2, 0.9, 1.7, 2.5, 3.1):
+        F = integrate.quad(lambda x: _p_chi(x, 0.5, 12 / 29), 0, chi, epsabs=1e-14)[0]
+        assert abs(O.lib().orc_aniso_F(np.sin(chi / 2) ** 2) - F) < 1e-12, chi
