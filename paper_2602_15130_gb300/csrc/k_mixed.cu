@@ -1469,7 +1469,6 @@ ParamsF params_f(const Params& P) {
   f.pmax = (float)P.pmax;
   f.gmax = (float)P.gmax;
   f.gmax2 = (float)(P.gmax * P.gmax);
-  for (int j = 0; j < 5; ++j) f.R_series[j] = (float)P.R_series[j];
   f.ginv_f = P.ginv_f;
   f.ginv_M = P.ginv_M;
   f.verify = P.verify;

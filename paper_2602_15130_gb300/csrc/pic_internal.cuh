@@ -71,7 +71,6 @@ struct ParamsF {
   float vmean[3], vsig, inv_vsig;
   float src_pref, pmax, gmax, gmax2;
   float phi_shift[3];
-  float R_series[5];
   const float* ginv_f;
   int ginv_M;
   int verify;                      // PIC_VERIFY_* bits
