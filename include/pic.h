@@ -91,10 +91,11 @@ enum {
  *                   with vh = v_bar (1 + sin(pi t/(2T))/5, 1 + cos(pi t/T)/5,
  *                   1 + sin(3 pi t/(2T))/5). v^M(t) = vh(t) tau(xi) and
  *                   vdot^M = vh'(t) tau(xi) enter the kicks (Eq.
- *                   velocity_verlet). FP64 single contexts only; collisions
- *                   need the odd-power cross section (n_sigma >= 1), whose
- *                   source is closed-form for this f_v (Eq. fn); the
- *                   isolated-collision switch is not available. */
+ *                   velocity_verlet). Single contexts of either precision
+ *                   (pic_create_batch and pic_adjoint_gradient reject it);
+ *                   collisions need the odd-power cross section (n_sigma >=
+ *                   1), whose source is closed-form for this f_v (Eq. fn);
+ *                   the isolated-collision switch is not available. */
 enum { PIC_DIST_CONFIG = 0, PIC_DIST_PAPER = 1 };
 
 /* Bins per angle of the recorded-angle histograms. */
@@ -136,7 +137,8 @@ enum { PIC_DIST_CONFIG = 0, PIC_DIST_PAPER = 1 };
  *                section sigma(g) = sum_{k<n_sigma} sigma_n[k] g^{2k-1} of
  *                Eq. sigma_ms with the source of Eqs. vel_change_3 and fn;
  *                (sigma g)_max is its maximum over [0, g_max] (Sec. 5.2),
- *                and sigma(g) g must be >= 0 there. FP64 contexts only.
+ *                and sigma(g) g must be >= 0 there. Single contexts (batches
+ *                and the adjoint reject it).
  *  v_bar, t_ref  PIC_DIST_PAPER: vbar and T of the manufactured solution. */
 typedef struct {
   int32_t n;
