@@ -119,8 +119,11 @@ def measured_peaks() -> dict:
 
 
 # Algorithmic HBM bytes per unit for each kernel class of one step. Units:
-# particles for the particle kernels, nodes x CG iterations for the CG. The
-# derivations are listed in the design doc (data layout and roofline section).
+# particles for the particle kernels, nodes x CG iterations for the CG; each
+# figure counts the arrays the kernel must read and write once (for example
+# the precision-form drift kick: cell, three offsets, three velocities, three
+# v^M, pid, three collision terms and three Lorentz terms in; three offsets,
+# three velocities, key and slot out: 100 B; the closing kick 64 B).
 # Philox4x32-10: 10 rounds of two 32x32->64 products (4 ops), four xors and
 # two key additions; GB300 issues 64 INT32 lanes per SM per clock.
 INT_OPS_PER_PHILOX = 100
