@@ -19,7 +19,17 @@ __all__ = ["Pic", "Batch", "PicConfig", "PicError", "PicObjective", "make_config
 
 
 def make_config(p: dict) -> PicConfig:
-    """pic_config from a workload dict (see ``workloads``)."""
+    """pic_config from a workload dict (see ``workloads``).
+
+    Keys are the pic_config fields of ``include/pic.h``: ``n``, ``K``,
+    ``n_particles`` and ``dt`` are required; ``qm``, ``q``, ``eps0``,
+    ``n_phys``, ``sigma0``, ``g_max``, ``fx_amp``, ``fx_speed``, ``v_mean``,
+    ``v_sigma``, ``phi_amp``, ``phi_T``, ``phi_shift``, ``couple_qm_zero``,
+    ``couple_q_zero``, ``precision`` (0 FP64, 1 the precision form),
+    ``max_ppc``, ``seed``, ``cg_tol``, ``cg_maxit``, ``verify``
+    (PIC_VERIFY_* bits), ``dist`` (PIC_DIST_*), ``n_sigma`` and ``sigma_n``
+    (odd-power cross section), ``v_bar`` and ``t_ref`` (the paper's problem)
+    are optional and default to the library's defaults."""
     L = load()
     c = PicConfig()
     check(L.pic_config_default(ctypes.byref(c)), "pic_config_default")
