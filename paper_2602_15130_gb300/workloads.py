@@ -1,6 +1,7 @@
 """Synthetic manufactured-solution workloads (parameter recipes only).
 
-Every workload is the periodic unit cube [0,1)^3 with the separable
+The benchmark and study workloads (all recipes except ``paper_*``) are the
+periodic unit cube [0,1)^3 with the separable
 manufactured position density prod_d (1 + 0.3 sin(2 pi (x_d - 0.1 t))),
 Gaussian velocities (mean 0.2, sigma 1 per axis), q/m = q = eps0 = 1, one
 physical particle in the box (w = 1/N_p, mean charge density 1), the
@@ -13,6 +14,11 @@ The hard-sphere cross section sigma0 is chosen so that a particle undergoes
 particles per cell and time step: with the mean relative speed of two
 Gaussian samples <g> = 4 s / sqrt(pi), Eq. p_coll gives
 (c - 1) sigma0 <g> w dt / dV = coll_per_call.
+
+The ``paper_*`` recipes are the paper's own problem of Sec. 5.2 (per-axis
+f_x with time-varying amplitude and phase, the non-Maxwellian f_v with
+vh(t), the odd-power cross section) expressed in box units; see
+``paper_units``.
 
 Nothing here performs any step of the method; these are inputs.
 """
