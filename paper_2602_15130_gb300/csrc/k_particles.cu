@@ -1,8 +1,9 @@
 // Particle-parallel kernels: manufactured sampling (Sec. 3.2), state
 // load/store, K-averaged NTC collisions (Algorithm 1, Eq. avg_outcome) with
-// the hard-sphere source (Eq. vel_change_1c), the velocity-Verlet kick and
-// drift (Eq. velocity_verlet with the sources of Eq. eom_mms) and the error
-// norms of Sec. 4.3.
+// the hard-sphere source (Eq. vel_change_1c) or the odd-power one (Eqs.
+// vel_change_3, fn), the velocity-Verlet kick and drift (Eq.
+// velocity_verlet with the sources of Eq. eom_mms, for the travelling-wave
+// and the paper's manufactured problem) and the error norms of Sec. 4.3.
 #include "pic_internal.cuh"
 #include "ntc_fp64.cuh"
 
