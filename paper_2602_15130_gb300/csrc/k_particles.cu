@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
 
 // --------------------------------------------------------------------------
 // Kick (and optionally drift) in sorted order:
-//   v += 1/2 (dt q/m (E_p - E^M_p) + dv + dt vdot^M),   vdot^M = 0 here,
+//   v += 1/2 (dt q/m (E_p - E^M_p) + dv + dt vdot^M) (vdot^M = 0 for the
+//   Gaussian f_v, vh'(t) tau for the paper's f_v),
 //   x += dt (v + xdot^M - v^M) at t_half (drift), wrapped; new cell key.
 // --------------------------------------------------------------------------
 struct KickArgs {
