@@ -156,3 +156,30 @@ def test_mixed_set_get_state_round_trip_and_determinism():
     ya, wa = a.get_state()
     yb, wb = b.get_state()
     assert np.array_equal(ya, yb) and np.array_equal(wa, wb)
+
+
+@pytest.mark.parametrize("which", ["smallest", "paper"])
+def test_state_load_into_a_running_context_keeps_v_manufactured(which):
+    """A state load into a context that already holds a state keeps the
+    per-pid v^M (tau for the paper's f_v) instead of deriving it again; a
+    fresh context derives it from xi. Both then step alike: a wrongly mapped
+    v^M would move x by dt (v^M_wrong - v^M) in the drift."""
+    p = CASES["smallest"] if which == "smallest" else workloads.mixed(workloads.paper_small())
+    src = Pic(p)
+    src.sample_mms(0.0)
+    src.step(3)
+    x, v = src.get_state()
+    fresh, running = Pic(p), Pic(p)
+    running.sample_mms(0.0)
+    running.step(1)
+    fresh.set_state(x, v, 0.0, 3)
+    running.set_state(x, v, 0.0, 3)
+    fresh.step(2)
+    running.step(2)
+    xf, vf = fresh.get_state()
+    xr, vr = running.get_state()
+    far_x = (dpos(xf, xr) > 1e-5).any(axis=1)
+    far_v = (np.abs(vf - vr) > 1e-4 * np.abs(vf).max()).any(axis=1)
+    assert far_x.mean() <= 0.01 and far_v.mean() <= 0.02, (far_x.mean(), far_v.mean())
+    ef, er = fresh.mms_error()["array"], running.mms_error()["array"]
+    assert np.all(np.abs(ef - er) <= 0.01 * ef + 1e-9), (ef, er)
