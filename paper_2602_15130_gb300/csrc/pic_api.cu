@@ -64,7 +64,11 @@ static bool prof_slot(pic_ctx* c) {
   if (!cls) return false;
   c->ev_class = cls;
   for (int i = 2 * c->ev_cap; i < 2 * cap; ++i)
-    if (cudaEventCreate(&c->ev_pool[i]) != cudaSuccess) return false;
+    if (cudaEventCreate(&c->ev_pool[i]) != cudaSuccess) {
+      for (int j = 2 * c->ev_cap; j < i; ++j) cudaEventDestroy(c->ev_pool[j]);
+      cudaGetLastError();
+      return false;
+    }
   c->ev_cap = cap;
   return true;
 }
@@ -354,7 +358,7 @@ void for_each_buffer(pic_ctx* c, F f) {
   }
   // host-boundary staging: the largest replicate of a batch, else everything
   size_t stage_np = np;
-  if (c->nrep > 0) {
+  if (c->nrep > 0 && c->prm_host) {  // (null only when a failed create is released)
     stage_np = 1;
     for (int r = 0; r < c->nrep; ++r)
       stage_np = (size_t)c->prm_host[r].np > stage_np ? (size_t)c->prm_host[r].np : stage_np;
@@ -444,6 +448,15 @@ cudaError_t batch_enqueue_step(pic_ctx* c, bool coll) {
 constexpr int kTuneCandidates = 3;
 const int kKickBlocks[kTuneCandidates] = {128, 256, 512};
 
+// the two timing events of one tuning step, released on every return
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
 // One batched step: the first steps time the candidate kick block sizes
 // (the result does not depend on the block size), later steady-state steps
 // replay a captured graph per buffer parity.
@@ -451,9 +464,10 @@ pic_status batch_step(pic_ctx* c, int64_t n, bool coll) {
   pic_status s = batch_time_terms(c, n);
   if (s != PIC_OK) return s;
   if (c->tune_step < kTuneCandidates) {
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    EventPair ev;
+    CK(cudaEventCreate(&ev.e0));
+    CK(cudaEventCreate(&ev.e1));
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     c->kick_block = kKickBlocks[c->tune_step];
     CK(batch_enqueue_times(c));
     if (coll) CK(launch_batch_dsmc(c, 0));
@@ -470,8 +484,6 @@ pic_status batch_step(pic_ctx* c, int64_t n, bool coll) {
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->tune_ms[c->tune_step] = ms;
     if (++c->tune_step == kTuneCandidates) {
       int best = 0;
