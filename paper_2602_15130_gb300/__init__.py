@@ -90,14 +90,23 @@ class _TorchAllocator:
         self.live.pop(ptr, None)
 
 
-def _ptr(a):
-    """(pointer, keepalive) for a numpy array or torch tensor."""
+def _ptr(a, count=None, dtype=np.float64):
+    """(pointer, keepalive) for a C-contiguous numpy array or torch tensor of
+    ``dtype`` with exactly ``count`` elements (any count when None); anything
+    else raises ValueError, so the library never reads or writes past it."""
     if a is None:
         return None, None
+    want = np.dtype(dtype)
     if isinstance(a, np.ndarray):
-        assert a.flags.c_contiguous
-        return a.ctypes.data, a
-    return a.data_ptr(), a
+        ok, n, dt = a.flags.c_contiguous and a.dtype == want, a.size, a.dtype
+    else:
+        import torch
+
+        tdt = {np.dtype(np.float64): torch.float64, np.dtype(np.int32): torch.int32}[want]
+        ok, n, dt = a.is_contiguous() and a.dtype == tdt, a.numel(), a.dtype
+    if not ok or (count is not None and n != count):
+        raise ValueError(f"expected a contiguous {want} buffer of {count} elements, got {dt} with {n}")
+    return (a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()), a
 
 
 class Pic:
@@ -151,8 +160,8 @@ class Pic:
         """(<dv>, <dv^M>) [N_p, 3] pid-indexed; numpy unless ``out`` tensors given."""
         if out is None:
             out = (np.zeros((self.np, 3)), np.zeros((self.np, 3)))
-        pa, ka = _ptr(out[0])
-        pb, kb = _ptr(out[1])
+        pa, ka = _ptr(out[0], 3 * self.np)
+        pb, kb = _ptr(out[1], 3 * self.np)
         check(self.L.pic_collide_avg(self.ctx, int(phase), pa, pb), "pic_collide_avg")
         return out
 
@@ -167,8 +176,8 @@ class Pic:
     def get_state(self, out=None):
         if out is None:
             out = (np.zeros((self.np, 3)), np.zeros((self.np, 3)))
-        pa, ka = _ptr(out[0])
-        pb, kb = _ptr(out[1])
+        pa, ka = _ptr(out[0], 3 * self.np)
+        pb, kb = _ptr(out[1], 3 * self.np)
         check(self.L.pic_get_state(self.ctx, pa, pb), "pic_get_state")
         return out
 
@@ -176,8 +185,8 @@ class Pic:
         if isinstance(x, np.ndarray):
             x = np.ascontiguousarray(x, dtype=np.float64)
             v = np.ascontiguousarray(v, dtype=np.float64)
-        pa, ka = _ptr(x)
-        pb, kb = _ptr(v)
+        pa, ka = _ptr(x, 3 * self.np)
+        pb, kb = _ptr(v, 3 * self.np)
         return check(self.L.pic_set_state(self.ctx, pa, pb, float(t0), int(step)), "pic_set_state", allow)
 
     def get_field(self):
@@ -215,8 +224,8 @@ class Pic:
         dv = np.zeros((self.np, 3)) if grad else None
         if v0 is not None and isinstance(v0, np.ndarray):
             v0 = np.ascontiguousarray(v0, dtype=np.float64)
-        pv, kv = _ptr(v0)
-        pd, kd = _ptr(dv)
+        pv, kv = _ptr(v0, 3 * self.np)
+        pd, kd = _ptr(dv, 3 * self.np)
         check(self.L.pic_adjoint_gradient(self.ctx, int(nsteps), int(every), ea, pv, J, dE, pd),
               "pic_adjoint_gradient")
         out = {"J": J[0], "J_field": J[1], "J_vel": J[2]}
@@ -276,8 +285,8 @@ class Batch(Pic):
         n = self.np_rep[rep]
         if out is None:
             out = (np.zeros((n, 3)), np.zeros((n, 3)))
-        pa, ka = _ptr(out[0])
-        pb, kb = _ptr(out[1])
+        pa, ka = _ptr(out[0], 3 * n)
+        pb, kb = _ptr(out[1], 3 * n)
         check(self.L.pic_batch_get_state(self.ctx, int(rep), pa, pb), "pic_batch_get_state")
         return out
 

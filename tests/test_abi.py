@@ -162,3 +162,25 @@ def test_batch_rejects_the_paper_problem(L):
         cfgs = (_lib.PicConfig * 2)(*[make_config(dict(p, **over)) for p in workloads.batched(n_rep=2)])
         ctx = ctypes.c_void_p()
         assert L.pic_create_batch(cfgs, 2, None, None, ctypes.byref(ctx)) == _lib.PIC_EINVAL
+
+
+def test_binding_rejects_buffers_the_library_would_overrun():
+    """The binding passes only contiguous buffers of the right type and size
+    to the library: [N_p][3] doubles for N_p = 4 here."""
+    import numpy as np
+    import torch
+
+    from paper_2602_15130_gb300 import _ptr
+
+    good = np.zeros((4, 3))
+    assert _ptr(good, 12)[0] == good.ctypes.data
+    t = torch.zeros(4, 3, dtype=torch.float64)
+    assert _ptr(t, 12)[0] == t.data_ptr()
+    assert _ptr(None, 12) == (None, None)
+    bad = (np.zeros((4, 3), np.float32), np.zeros((3, 3)), np.zeros((3, 4)).T,
+           torch.zeros(12, dtype=torch.float32), torch.zeros(11, dtype=torch.float64),
+           torch.zeros(4, 6, dtype=torch.float64)[:, ::2])
+    for b in bad:
+        with pytest.raises(ValueError):
+            _ptr(b, 12)
+    assert _ptr(np.zeros(5, np.int32), 5, np.int32)[1] is not None
