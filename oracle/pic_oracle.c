@@ -30,9 +30,34 @@
  *   sigma(g) = sum_{k<n_sigma} sigma_k g^{2k-1} (Eq. sigma_ms) with its
  *   exact source (Eqs. vel_change_3, fn); isotropic scattering (Eq. chi_iso)
  *
- * Parity status of each function is given beside it; every function here is
- * pinned by tests in tests/test_oracle_pins.py (closed forms, invariants,
- * library special cases, quadrature, brute force).
+ * Every function is pinned to something other than itself, in
+ * tests/test_oracle_pins.py, test_oracle_verification_pins.py and
+ * test_oracle_paper_pins.py; none is left unpinned:
+ *  - orc_philox, orc_u52, orc_u32, orc_index: published known-answer
+ *    vectors; uniform and index conventions.
+ *  - orc_sample_xi: uniformity, distinct draws.
+ *  - orc_fxd, orc_Fxd, orc_xM, orc_xMdot, orc_fx_terms, orc_fx, orc_Fx,
+ *    orc_xM_d, orc_xMdot_d: printed forms, quadrature of f_x, inversion to
+ *    1e-14, central differences in t.
+ *  - orc_Phi, orc_Phi_inv, orc_vM, orc_vhat, orc_fv_paper, orc_Fv_paper,
+ *    orc_vM_t, orc_vMdot: scipy ndtri, printed forms, inversion, central
+ *    differences, sampled moments.
+ *  - orc_phiM, orc_EM, orc_lap_phiM, orc_rhoM: finite differences, integral.
+ *  - orc_hs_R, orc_hs_source: series against the closed form, Monte Carlo
+ *    vector, expected NTC change.
+ *  - orc_fn, orc_odd_source: printed formulas, Gauss-Hermite quadrature.
+ *  - orc_sigma_g, orc_sg_max, orc_pmax: dense scan, Table 1 column.
+ *  - orc_cell_of, orc_sort, orc_deposit, orc_gather, orc_rhs: brute force,
+ *    total charge, affine fields.
+ *  - orc_neg_lap, orc_cg, orc_efield, orc_field: Fourier eigenvalues, FFT
+ *    solve, closed forms, uncoupled phi^M.
+ *  - orc_ntc_cell, orc_dsmc_avg, orc_aniso_F, orc_aniso_u: momentum and
+ *    energy, relative speed, isotropy, brute-force expectation, Errors 1
+ *    and 2, anisotropic CDF and its inverse.
+ *  - orc_step, orc_source_all, orc_wrap: observed second order, zero-mean
+ *    collision error, sign of the source, wrap convention.
+ *  - orc_errors, orc_objective and the angle metric of oracle.py:
+ *    hand-computed values, KS bound, field energy plus velocity error.
  */
 #include <math.h>
 #include <stdint.h>
