@@ -20,9 +20,13 @@
  *    arrays are [n^3] with x fastest (node (i,j,k) at index i + n (j + n k),
  *    position (i h, j h, k h), h = 1/n), vector fields [n^3][3].
  *  - Pointers marked "host or device" may point to host memory (pageable or
- *    pinned) or device memory of the context's GPU; the library copies with
- *    cudaMemcpyDefault. The caller owns every pointer it passes; the library
- *    never keeps one after the call returns.
+ *    pinned) or device memory of the context's GPU, 8-byte aligned for FP64
+ *    arrays. Device memory and pinned (registered) host memory may be read
+ *    or written by the kernels in place, the latter over NVLink-C2C;
+ *    pageable memory is staged through a copy (cudaMemcpyDefault). Either
+ *    way the array must hold the stated number of elements. The caller owns
+ *    every pointer it passes; the library never keeps one after the call
+ *    returns.
  *  - No call throws. Every call returns a pic_status; a failed call leaves
  *    the context usable unless it returns PIC_ESTATE or PIC_ECUDA.
  *  - The context owns all device buffers. pic_destroy(NULL) is a no-op.

@@ -24,7 +24,7 @@ inline int blocks_for(int64_t n, int t = kThreads) {
 struct Sample32Args {
   Params P;
   TimeTerms tt;
-  const double* xv;  // optional caller state (pid order, [N][3] x then [N][3] v)
+  const double *xs, *vs;  // optional caller state (pid order, [N][3] each; device or mapped host)
   const float *vin0, *vin1, *vin2;  // optional v^M (tau for the paper's f_v) in pid order
   int32_t* cell;
   float *o0, *o1, *o2, *v0, *v1, *v2, *m0, *m1, *m2;
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
   if (i >= P.np) return;
   double xi[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const bool given_vm = a.vin0 != nullptr;
-  if (!a.xv || !given_vm) {
+  if (!a.xs || !given_vm) {
     const U4 b0 = sample_block(P, (uint64_t)i, 0), b1 = sample_block(P, (uint64_t)i, 1),
              b2 = sample_block(P, (uint64_t)i, 2);
     xi[0] = unif52(b0.x, b0.y); xi[1] = unif52(b0.z, b0.w); xi[2] = unif52(b1.x, b1.y);
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
       vm[d] = (double)vin[d][i];
     else
       vm[d] = paper ? tau_inv(xi[3 + d]) : P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
-    if (a.xv) {
-      x[d] = a.xv[3 * i + d];
-      v[d] = a.xv[3 * P.np + 3 * i + d];
+    if (a.xs) {
+      x[d] = a.xs[3 * i + d];
+      v[d] = a.vs[3 * i + d];
     } else if (paper) {
       x[d] = wrap_unit(xm_solve_gen(a.tt, d, xi[d], &s, &cc));
       v[d] = vm[d] * a.tt.vh[d];
@@ -119,6 +119,54 @@ __global__ void __launch_bounds__(kThreads) k_store_state32(Store32Args a) {
   a.xv[3 * p + 2] = ((double)ck + (double)a.o2[j]) * a.h;
   double* vs = a.xv + 3 * a.np;
   vs[3 * p] = a.v0[j]; vs[3 * p + 1] = a.v1[j]; vs[3 * p + 2] = a.v2[j];
+}
+
+// Inverse of the sort permutation: the slot of every pid.
+struct InvPerm32Args {
+  int64_t np;
+  const uint32_t* pid;
+  int32_t* slot;
+};
+
+__global__ void __launch_bounds__(kThreads) k_inv_perm32(InvPerm32Args a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.np) return;
+  a.slot[a.pid[j]] = (int32_t)j;
+}
+
+// The state in pid order for a destination the kernel writes in place
+// (device memory, or pinned host memory reached over NVLink-C2C): each
+// thread gathers one pid through the inverse permutation, the block's rows
+// go through shared memory, and the stores cover contiguous spans. Same
+// arithmetic as k_store_state32.
+struct StoreByPid32Args {
+  int64_t np;
+  int n;
+  double h;
+  const int32_t *slot, *cell;
+  const float *o0, *o1, *o2, *v0, *v1, *v2;
+  double *x, *v;
+};
+
+__global__ void __launch_bounds__(kThreads) k_store_state32_by_pid(StoreByPid32Args a) {
+  __shared__ double sx[3 * kThreads], sv[3 * kThreads];
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int t = threadIdx.x;
+  if (base + t < a.np) {
+    const int64_t j = a.slot[base + t];
+    const int n = a.n, c = a.cell[j];
+    const int ci = c % n, cj = (c / n) % n, ck = c / (n * n);
+    sx[3 * t] = ((double)ci + (double)a.o0[j]) * a.h;
+    sx[3 * t + 1] = ((double)cj + (double)a.o1[j]) * a.h;
+    sx[3 * t + 2] = ((double)ck + (double)a.o2[j]) * a.h;
+    sv[3 * t] = a.v0[j]; sv[3 * t + 1] = a.v1[j]; sv[3 * t + 2] = a.v2[j];
+  }
+  __syncthreads();
+  const int64_t rows = a.np - base < kThreads ? a.np - base : kThreads;
+  for (int64_t k = t; k < 3 * rows; k += kThreads) {
+    a.x[3 * base + k] = sx[k];
+    a.v[3 * base + k] = sv[k];
+  }
 }
 
 // ----------------------------------------------------- sort gather + CIC --
@@ -1137,11 +1185,12 @@ cudaError_t launch_vm_to_pid32(pic_ctx* c, float* const* out) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv, float* const* vm_in) {
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v, float* const* vm_in) {
   Sample32Args a;
   a.P = c->P;
   a.tt = time_terms(c->P, t0);
-  a.xv = xv;
+  a.xs = x;
+  a.vs = v;
   a.vin0 = vm_in ? vm_in[0] : nullptr;
   a.vin1 = vm_in ? vm_in[1] : nullptr;
   a.vin2 = vm_in ? vm_in[2] : nullptr;
@@ -1153,7 +1202,7 @@ cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv, float* cons
   a.pid = c->pid[b];
   prof_begin(c);
   k_sample32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
-  prof_end(c, xv ? KC_OTHER : KC_SAMPLE);
+  prof_end(c, x ? KC_OTHER : KC_SAMPLE);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1347,6 +1396,38 @@ cudaError_t launch_store_state32(pic_ctx* c, double* xv, int32_t* cell_of_pid) {
   a.cell_of_pid = cell_of_pid;
   prof_begin(c);
   k_store_state32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// x, v [N_p][3] in pid order written in place (device or mapped pinned host
+// memory, 8-byte aligned); the inverse permutation goes into the sort's
+// free permutation buffer
+cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {
+  const int b = c->cur;
+  InvPerm32Args ia;
+  ia.np = c->P.np;
+  ia.pid = c->pid[b];
+  ia.slot = c->perm;
+  prof_begin(c);
+  k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->stream>>>(ia);
+  prof_end(c, KC_OTHER);
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  StoreByPid32Args a;
+  a.np = c->P.np;
+  a.n = c->P.n;
+  a.h = c->P.h;
+  a.slot = c->perm;
+  a.cell = c->cell32[b];
+  a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
+  a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
+  a.x = x;
+  a.v = v;
+  prof_begin(c);
+  k_store_state32_by_pid<<<blocks_for(a.np), kThreads, 0, c->stream>>>(a);
   prof_end(c, KC_OTHER);
   c->launches++;
   return cudaGetLastError();

@@ -61,11 +61,11 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a) {
   a.pid[i] = (uint32_t)i;
 }
 
-// Load a caller state ([N_p][3] x then [N_p][3] v, pid order) into SoA.
+// Load a caller state (x and v, each [N_p][3] in pid order) into SoA.
 struct LoadArgs {
   Params P;
   TimeTerms tt;
-  const double* xv;  // 6 N_p: x AoS then v AoS
+  const double *xs, *vs;  // device memory or mapped pinned host memory
   double *x0, *x1, *x2, *v0, *v1, *v2, *vm0, *vm1, *vm2;
   uint32_t* pid;
 };
@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(kThreads) k_load_state(LoadArgs a) {
     a.vm1[i] = P.vmean[1] + P.vsig * normcdfinv(xi[4]);
     a.vm2[i] = P.vmean[2] + P.vsig * normcdfinv(xi[5]);
   }
-  const double* xs = a.xv;
-  const double* vs = a.xv + 3 * P.np;
+  const double* xs = a.xs;
+  const double* vs = a.vs;
   a.x0[i] = xs[3 * i]; a.x1[i] = xs[3 * i + 1]; a.x2[i] = xs[3 * i + 2];
   a.v0[i] = vs[3 * i]; a.v1[i] = vs[3 * i + 1]; a.v2[i] = vs[3 * i + 2];
   a.pid[i] = (uint32_t)i;
@@ -501,11 +501,12 @@ cudaError_t launch_sample(pic_ctx* c, double t0) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_load_state(pic_ctx* c, const double* xv, double t) {
+cudaError_t launch_load_state(pic_ctx* c, const double* x, const double* v, double t) {
   LoadArgs a;
   a.P = c->P;
   a.tt = time_terms(c->P, t);
-  a.xv = xv;
+  a.xs = x;
+  a.vs = v;
   const int b = c->cur;
   a.x0 = c->x[b][0]; a.x1 = c->x[b][1]; a.x2 = c->x[b][2];
   a.v0 = c->v[b][0]; a.v1 = c->v[b][1]; a.v2 = c->v[b][2];

@@ -2,6 +2,7 @@
 // constants, device buffers, the step schedule of Eq. velocity_verlet and
 // the boundary copies.
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -365,6 +366,24 @@ void for_each_buffer(pic_ctx* c, F f) {
   }
   f((void**)&c->stage, 6 * stage_np * 8);
   f((void**)&c->stage_i, (stage_np + 1) * 4);
+}
+
+// The address at which a kernel may use a caller array in place: device
+// memory of the context's GPU, or pinned (registered) host memory mapped
+// into the device address space, which kernels reach over NVLink-C2C
+// without a staging copy. nullptr: pageable or other memory, staged through
+// a copy.
+template <class T>
+T* in_place(const pic_ctx* c, T* p) {
+  if (((uintptr_t)p & 7) != 0) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, (const void*)p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice && at.device == c->device) return p;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) return (T*)at.devicePointer;
+  return nullptr;
 }
 
 // Read and clear the sticky device flags of the work enqueued so far
@@ -813,7 +832,7 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
   if (c->ang_hist) CK(cudaMemsetAsync(c->ang_hist, 0, (size_t)2 * PIC_ANGLE_BINS * 8, c->stream));
   if (c->mixed) {
     CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
-    CK(launch_sample32(c, t0, nullptr));
+    CK(launch_sample32(c, t0, nullptr, nullptr));
   } else {
     CK(cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream));
     CK(launch_sample(c, t0));
@@ -827,9 +846,18 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
 pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0, int64_t step) {
   if (!c || !x || !v || !isfinite(t0) || step < 0) return PIC_EINVAL;
   if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
+  // the load kernels read device and pinned host arrays in place
   const size_t bytes = (size_t)c->P.np * 3 * 8;
-  CK(cudaMemcpyAsync(c->stage, x, bytes, cudaMemcpyDefault, c->stream));
-  CK(cudaMemcpyAsync(c->stage + 3 * c->P.np, v, bytes, cudaMemcpyDefault, c->stream));
+  const double* xs = in_place(c, x);
+  const double* vs = in_place(c, v);
+  if (!xs) {
+    CK(cudaMemcpyAsync(c->stage, x, bytes, cudaMemcpyDefault, c->stream));
+    xs = c->stage;
+  }
+  if (!vs) {
+    CK(cudaMemcpyAsync(c->stage + 3 * c->P.np, v, bytes, cudaMemcpyDefault, c->stream));
+    vs = c->stage + 3 * c->P.np;
+  }
   c->t0 = t0;
   c->step = step;
   if (c->mixed) {
@@ -839,10 +867,10 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
     const bool keep_vm = c->sampled;
     if (keep_vm) CK(launch_vm_to_pid32(c, c->dvf));
     c->cur = 0;
-    CK(launch_sample32(c, time_at(c, (double)step), c->stage, keep_vm ? c->dvf : nullptr));
+    CK(launch_sample32(c, time_at(c, (double)step), xs, vs, keep_vm ? c->dvf : nullptr));
   } else {
     c->cur = 0;
-    CK(launch_load_state(c, c->stage, time_at(c, (double)step)));
+    CK(launch_load_state(c, xs, vs, time_at(c, (double)step)));
   }
   pic_status s = sort_and_field(c, time_at(c, (double)step));
   if (s != PIC_OK) return s;
@@ -934,8 +962,19 @@ pic_status pic_get_state(pic_ctx* c, double* x, double* v) {
   if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls
   if (!c->sampled) return PIC_ESTATE;
   const size_t bytes = (size_t)c->P.np * 3 * 8;
-  if (c->mixed) CK(launch_store_state32(c, c->stage, nullptr));
-  else CK(launch_store_state(c, c->stage));
+  if (c->mixed) {
+    // device and pinned host destinations are written in place, in pid order
+    double* xd = in_place(c, x);
+    double* vd = in_place(c, v);
+    if (xd && vd) {
+      CK(launch_store_state32_by_pid(c, xd, vd));
+      CK(cudaStreamSynchronize(c->stream));
+      return PIC_OK;
+    }
+    CK(launch_store_state32(c, c->stage, nullptr));
+  } else {
+    CK(launch_store_state(c, c->stage));
+  }
   CK(cudaMemcpyAsync(x, c->stage, bytes, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(v, c->stage + 3 * c->P.np, bytes, cudaMemcpyDefault, c->stream));
   CK(cudaStreamSynchronize(c->stream));

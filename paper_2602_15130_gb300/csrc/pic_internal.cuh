@@ -668,7 +668,7 @@ enum KernelClass {
 
 // Kernel-launching helpers (each returns cudaGetLastError()).
 cudaError_t launch_sample(pic_ctx* c, double t0);
-cudaError_t launch_load_state(pic_ctx* c, const double* xv_dev, double t);
+cudaError_t launch_load_state(pic_ctx* c, const double* x, const double* v, double t);
 cudaError_t launch_store_state(pic_ctx* c, double* xv_dev);
 cudaError_t launch_keys(pic_ctx* c);
 cudaError_t launch_sort(pic_ctx* c);            // scan + scatter + in-cell sort + gather + CIC
@@ -702,7 +702,8 @@ cudaError_t launch_scan_scatter(pic_ctx* c);   // scan of counts + scatter into 
 cudaError_t launch_err_final(pic_ctx* c, int nblocks);
 // precision form
 // vm_in: v^M (tau) in pid order to keep instead of recomputing them (state loads)
-cudaError_t launch_sample32(pic_ctx* c, double t0, const double* xv_dev, float* const* vm_in = nullptr);
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v,
+                           float* const* vm_in = nullptr);
 cudaError_t launch_vm_to_pid32(pic_ctx* c, float* const* out);
 cudaError_t launch_keys32(pic_ctx* c);
 cudaError_t launch_gather32(pic_ctx* c);
@@ -717,6 +718,7 @@ void adjoint_free(pic_ctx* c);
 cudaError_t launch_cg32(pic_ctx* c);
 cudaError_t launch_errors32(pic_ctx* c, double t);
 cudaError_t launch_store_state32(pic_ctx* c, double* xv_dev, int32_t* cell_of_pid);
+cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v);
 cudaError_t launch_store_field32(pic_ctx* c, double* phi, double* E);
 cudaError_t launch_store_dv32(pic_ctx* c, double* dv, double* dvm);
 

@@ -183,3 +183,30 @@ def test_state_load_into_a_running_context_keeps_v_manufactured(which):
     assert far_x.mean() <= 0.01 and far_v.mean() <= 0.02, (far_x.mean(), far_v.mean())
     ef, er = fresh.mms_error()["array"], running.mms_error()["array"]
     assert np.all(np.abs(ef - er) <= 0.01 * ef + 1e-9), (ef, er)
+
+
+@pytest.mark.parametrize("form", ["mixed", "fp64"])
+def test_state_in_place_through_pinned_and_device_buffers(form):
+    """Pinned host and CUDA arrays are read (and, by the precision form,
+    written) by the kernels in place, without a staging copy; the states
+    equal those through pageable numpy arrays bit for bit."""
+    import torch
+
+    kw = dict(n=12, n_particles=12 ** 3 * 9 + 37)
+    p = mixed(**kw) if form == "mixed" else workloads.smallest(**kw)
+    x, v = inputs.particles(p["n_particles"], seed=11)
+    ref = Pic(p)
+    ref.set_state(x, v, 0.0, 1)
+    x0, v0 = ref.get_state()
+    ref.step(2)
+    x2, v2 = ref.get_state()
+    places = {"pinned": lambda a: torch.from_numpy(a).pin_memory(), "cuda": lambda a: torch.from_numpy(a).cuda()}
+    for where, put in places.items():
+        g = Pic(p)
+        g.set_state(put(x), put(v), 0.0, 1)
+        outs = (put(np.zeros_like(x)), put(np.zeros_like(v)))
+        g.get_state(outs)
+        assert np.array_equal(outs[0].cpu().numpy(), x0) and np.array_equal(outs[1].cpu().numpy(), v0), where
+        g.step(2)
+        g.get_state(outs)
+        assert np.array_equal(outs[0].cpu().numpy(), x2) and np.array_equal(outs[1].cpu().numpy(), v2), where
