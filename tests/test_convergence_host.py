@@ -71,3 +71,20 @@ def test_paper_table1_schedule():
         assert p["n_particles"] == np_coll and p["K"] == navg and q["n_particles"] == np_free and q["K"] == 0
         assert abs(1.0 / derived(p)["pmax"] / inv_p - 1.0) < 2e-4
         assert p["dist"] == 1 and p["n_sigma"] == 3 and q["n_sigma"] == 0
+
+
+def test_batched_study_replicates_match_the_committed_list():
+    """The batched study's replicate draws (mesh edge on {8, 16, 32, 64},
+    particles per cell in [8, 64], K in [4, 64], host generator seed 42)
+    equal the committed list, and each follows its stated recipe."""
+    rows = [l.split() for l in (GOLDEN / "batched_replicates.txt").read_text().splitlines()
+            if l.strip() and not l.startswith("#")]
+    reps = W.batched()
+    assert len(rows) == len(reps) == 256
+    for r, (row, p) in enumerate(zip(rows, reps)):
+        assert [int(x) for x in row[:5]] == [r, p["n"], p["n_particles"], p["K"], p["seed"]]
+        assert float(row[5]) == p["sigma0"]
+        ppc = p["n_particles"] // p["n"] ** 3
+        assert p["n"] in (8, 16, 32, 64) and 8 <= ppc <= 64 and p["n_particles"] == ppc * p["n"] ** 3
+        assert 4 <= p["K"] <= 64 and p["seed"] == 1000 + r
+    assert len({p["n"] for p in reps}) == 4
