@@ -52,8 +52,9 @@
  *  - orc_neg_lap, orc_cg, orc_efield, orc_field: Fourier eigenvalues, FFT
  *    solve, closed forms, uncoupled phi^M.
  *  - orc_ntc_cell, orc_dsmc_avg, orc_aniso_F, orc_aniso_u: momentum and
- *    energy, relative speed, isotropy, brute-force expectation, Errors 1
- *    and 2, anisotropic CDF and its inverse.
+ *    energy, relative speed, isotropy, brute-force expectation, variance
+ *    falling as 1/K and growing as dt (Eq. var), Errors 1 and 2,
+ *    anisotropic CDF and its inverse.
  *  - orc_step, orc_source_all, orc_wrap: observed second order, zero-mean
  *    collision error, sign of the source, wrap convention.
  *  - orc_errors, orc_objective and the angle metric of oracle.py:

@@ -405,6 +405,37 @@ def test_ntc_expectation_brute_force():
     assert np.all(np.abs(mean - ref) < 4.5 * se + 1e-3 * np.abs(ref).max())
 
 
+def _repeated_calls(K, dt, sigma0, M, c=48):
+    """<Delta v> of M K-averaged calls on one fixed cell state (48 particles
+    in one cell of a 2^3 mesh), each call with its own Philox counter."""
+    g = np.random.default_rng(5)
+    x = g.random((c, 3)) * 0.5
+    v = 0.2 + g.standard_normal((c, 3))
+    o = O.Oracle(W.smallest(n=2, n_particles=c, K=K, dt=dt, sigma0=sigma0))
+    out = np.empty((M, c, 3))
+    for s in range(M):
+        o.set_state(x, v, 0.0, s)
+        out[s], _ = o.collide_avg(0)
+    return out
+
+
+def test_algorithmic_variance_falls_as_one_over_K_and_grows_with_dt():
+    """Eq. var, algorithmic term: for a fixed velocity set the K outcomes of
+    Eq. avg_outcome are independent, so Var[<Delta v>] = C_alg dt / N_avg
+    exactly in K, and linear in dt while collisions per particle are rare.
+    Shared outcome streams, a wrong 1/K, or dt missing from (or squared in)
+    P_coll,max fail it. Here about 2% (dt ratio) and 1.5% (K ratio) are
+    sampling spread, and O(lambda) of the dt ratio is the memory loss of a
+    particle that collides twice."""
+    var = lambda a: a.var(axis=0, ddof=1).mean()
+    v1 = var(_repeated_calls(1, 0.01, 0.5, 2000))
+    for K in (4, 16):
+        r = K * var(_repeated_calls(K, 0.01, 0.5, 2000)) / v1
+        assert 0.92 < r < 1.08, (K, r)
+    r = var(_repeated_calls(4, 0.01, 0.2, 4000)) / var(_repeated_calls(4, 0.005, 0.2, 4000))
+    assert 1.88 < r < 2.08, r
+
+
 def test_collisions_off_is_exactly_zero():
     p = W.smallest(K=0)
     o = O.Oracle(p)
