@@ -1,8 +1,10 @@
-"""The benchmark's workload at full size, launched as the benchmark launches
-it: the finest refinement level (128^3 cells, 67,108,864 particles, K = 16,
-dt = 0.00125) in the precision form, on a side stream. At this size the
-oracle cannot run the whole state, so the checks are outputs it computes
-one by one and properties that hold at any size:
+"""The precision form at full size, launched as the benchmark launches it
+(one context on a side stream), on two workloads: the benchmark's, the
+finest refinement level (128^3 cells, 67,108,864 particles, K = 16, dt =
+0.00125), and the precision-form study's (128^3 cells, 134,217,728
+particles, K = 32, dt = 0.005). At these sizes the oracle cannot run the
+whole state, so the checks are outputs it computes one by one and
+properties that hold at any size:
 
   - sampling: x^M and v^M of 4096 sampled pids from the oracle's xi;
   - sort: the cell of every particle from its position, the counts, the
@@ -149,15 +151,18 @@ def check_collision_call(p, v, count, start, perm, dv, dvm, stats, cells, c0=0):
     assert src_err <= 1e-5 * max(1.0, src_max)
 
 
-@pytest.fixture(scope="module")
-def big():
+FULL = {"refine4": lambda: W.mixed(W.refinement_level(4)), "precision": W.precision_form}
+
+
+@pytest.fixture(scope="module", params=list(FULL))
+def big(request):
     import torch
 
     import __graft_entry__ as g
 
     g.build()
     assert torch.cuda.is_available()
-    p = W.mixed(W.refinement_level(4))
+    p = FULL[request.param]()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = Pic(p, stream=stream)
@@ -203,7 +208,7 @@ def test_fullsize_one_step_and_fp64_error_norms(big):
     exp, tol = expected_candidates(p, [count0, count])
     assert abs(st["n_cand"] - exp) <= tol, (st["n_cand"], exp)
     e32 = sim.mms_error()["array"]
-    f = Pic(W.refinement_level(4))
+    f = Pic(dict(p, precision=0, cg_tol=1e-10))
     f.sample_mms(0.0)
     f.step(1)
     e64 = f.mms_error()["array"]
