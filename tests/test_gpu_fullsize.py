@@ -33,7 +33,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from paper_2602_15130_gb300 import Pic, derived, workloads as W
+from paper_2602_15130_gb300 import Batch, Pic, derived, workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -217,3 +217,41 @@ def test_fullsize_one_step_and_fp64_error_norms(big):
     # a maximum over 67M particles that one FP32 near-tie flip can move
     keep = list(range(7)) + [13]
     assert np.all(np.abs(e32 - e64)[keep] <= 0.03 * e64[keep] + 1e-7), (e32, e64)
+
+
+def test_fullsize_batched_study():
+    """The batched study at full size (256 replicates, 828.6M particles),
+    launched as the benchmark launches it: 1024 sampled pids of three
+    replicates (the largest, the smallest, and replicate 128) against the
+    oracle's x^M and v^M; then 5 steps (3 autotuning steps, then captured
+    graphs replayed), finite norms for every replicate, and the largest and
+    smallest replicates' eps_2 norms (and eps_inf of phi) within 3% of
+    single-domain runs of the same configurations (the batched Poisson solve
+    sums in another order)."""
+    import torch
+
+    cfgs = W.batched()
+    sizes = [p["n_particles"] for p in cfgs]
+    pick = [int(np.argmax(sizes)), int(np.argmin(sizes)), 128]
+    rng = np.random.default_rng(7)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = Batch(cfgs, stream=stream)
+        b.sample_mms(0.0)
+        for r in pick:
+            x, v = b.get_state(r)
+            check_sampling(cfgs[r], x, v, rng.choice(cfgs[r]["n_particles"], 1024, replace=False))
+        b.step(5)
+        eb = b.mms_error()
+        assert eb.shape == (256, 14) and np.all(np.isfinite(eb))
+        assert b.stats()["graph_replays"] >= 1
+        for r in pick[:2]:
+            s = Pic(cfgs[r], stream=stream)
+            s.sample_mms(0.0)
+            s.step(5)
+            es = s.mms_error()["array"]
+            s.close()
+            keep = list(range(7)) + [13]
+            assert np.all(np.abs(eb[r] - es)[keep] <= 0.03 * es[keep] + 1e-7), (r, eb[r], es)
+        b.close()
+    torch.cuda.empty_cache()
