@@ -132,7 +132,8 @@ enum { PIC_DIST_CONFIG = 0, PIC_DIST_PAPER = 1 };
  *                field and CG vectors; per-cell charge sums, CG inner
  *                products and residual, and the error norms FP64-accurate.
  *  max_ppc       most particles one cell may hold during collisions (working
- *                set of the collision kernel); 0 selects 512.
+ *                set of the collision kernel), 0 .. 65536, rounded up to a
+ *                multiple of 32; 0 selects 512.
  *  seed          Philox4x32-10 key (low word, high word).
  *  cg_tol, cg_maxit  CG stops at ||r||_2 <= cg_tol ||b||_2 or cg_maxit.
  *  verify        PIC_VERIFY_* bit flags (0: the method as stated).

@@ -58,6 +58,20 @@ def test_invalid_configs_are_rejected(L, field, value):
     assert not out.value
 
 
+@pytest.mark.parametrize("field,ok,bad", [
+    ("n", 1024, 1025), ("n", 2, 1), ("n_particles", 2 ** 31 - 1, 2 ** 31), ("n_particles", 1, 0),
+    ("K", 1 << 20, (1 << 20) + 1), ("K", 0, -1), ("max_ppc", 65536, 65537), ("max_ppc", 0, -1),
+])
+def test_size_limits_are_exact(L, field, ok, bad):
+    """The largest (and smallest) sizes include/pic.h allows validate; one
+    past them does not."""
+    c = make_config(workloads.smallest())
+    setattr(c, field, ok)
+    assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_OK
+    setattr(c, field, bad)
+    assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_EINVAL
+
+
 def test_null_arguments(L):
     assert L.pic_validate_config(None) == _lib.PIC_EINVAL
     assert L.pic_config_default(None) == _lib.PIC_EINVAL
