@@ -133,7 +133,9 @@ enum { PIC_DIST_CONFIG = 0, PIC_DIST_PAPER = 1 };
  *                products and residual, and the error norms FP64-accurate.
  *  max_ppc       most particles one cell may hold during collisions (working
  *                set of the collision kernel), 0 .. 65536, rounded up to a
- *                multiple of 32; 0 selects 512.
+ *                multiple of 32; 0 selects 512. The collision kernel keeps
+ *                16 max_ppc bytes of bitmaps in shared memory per block, so
+ *                pic_create accepts at most 14,528 on a GB300 (227 KB).
  *  seed          Philox4x32-10 key (low word, high word).
  *  cg_tol, cg_maxit  CG stops at ||r||_2 <= cg_tol ||b||_2 or cg_maxit.
  *  verify        PIC_VERIFY_* bit flags (0: the method as stated).
@@ -248,7 +250,9 @@ pic_status pic_derived(const pic_config* cfg, double out[5]);
 /* Create a context on the current CUDA device: validates cfg, allocates
  * all device buffers (via alloc, or cudaMalloc when alloc is NULL) and
  * binds the stream (a cudaStream_t; NULL = legacy default stream).
- * *out is set to NULL on failure. */
+ * *out is set to NULL on failure: PIC_EINVAL also when max_ppc needs more
+ * shared memory than the device gives a block, PIC_ENOMEM when a buffer
+ * cannot be allocated. */
 pic_status pic_create(const pic_config* cfg, void* cuda_stream, const pic_allocator* alloc,
                       pic_ctx** out);
 
