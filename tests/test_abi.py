@@ -26,12 +26,54 @@ def test_exports_every_declared_symbol(L):
     assert sorted(_lib.SIGNATURES) == names
 
 
-def test_struct_layout_matches_header(L):
-    # pic_config: 2 int32, int64, 13 doubles incl. arrays..., checked by size
-    assert ctypes.sizeof(_lib.PicConfig) == (4 + 4 + 8 + 8 * 5 + 8 * 2 + 8 * 2 + 24 + 8 + 8 * 2 + 24 + 4 * 4 + 8 + 8
-                                             + 4 + 4 + 4 + 4 + 24 + 8 + 8)
-    assert ctypes.sizeof(_lib.PicErrors) == 14 * 8
-    assert ctypes.sizeof(_lib.PicAngleStats) == 8 + 16 + 4 * 8
+STRUCTS = {"pic_config": _lib.PicConfig, "pic_errors": _lib.PicErrors, "pic_stats": _lib.PicStats,
+           "pic_angle_stats": _lib.PicAngleStats, "pic_allocator": _lib.PicAllocator,
+           "pic_kernel_times": _lib.PicKernelTimes}
+CONSTANTS = {**{n: getattr(_lib, n) for n in (
+    "PIC_OK", "PIC_EINVAL", "PIC_ENOMEM", "PIC_ECUDA", "PIC_ENOCONV", "PIC_ETIMEOUT", "PIC_ESTATE", "PIC_ECAPACITY",
+    "PIC_FP64", "PIC_MIXED", "PIC_VERIFY_ISOLATE", "PIC_VERIFY_ERROR1", "PIC_VERIFY_ERROR2", "PIC_VERIFY_ANGLES",
+    "PIC_VERIFY_ANISO", "PIC_DIST_CONFIG", "PIC_DIST_PAPER", "PIC_ANGLE_BINS")},
+    "PIC_NUM_KERNEL_CLASSES": _lib.NUM_KERNEL_CLASSES}
+
+
+def test_header_layout_and_constants_match_the_binding(tmp_path):
+    """A program compiled against include/pic.h as strict C99 (and the
+    header alone as C++17, warnings as errors) prints the offset and size of
+    every field of every struct and the value of every constant; the
+    binding's ctypes declarations agree field by field."""
+    import shutil
+    import subprocess
+
+    cc, cxx = shutil.which("gcc"), shutil.which("g++")
+    if not cc or not cxx:
+        pytest.skip("no host C/C++ compiler")
+    inc = str(_lib.HEADER.parent)
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pic.h"', "int main(void) {"]
+    for name, T in STRUCTS.items():
+        lines.append(f'  printf("{name} . %zu %zu\\n", (size_t)0, sizeof({name}));')
+        for f, _ in T._fields_:
+            lines.append(f'  printf("{name} {f} %zu %zu\\n", offsetof({name}, {f}), sizeof((({name}*)0)->{f}));')
+    for name in CONSTANTS:
+        lines.append(f'  printf("const {name} %ld 0\\n", (long)({name}));')
+    lines += ["  return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    flags = ["-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc]
+    subprocess.run([cc, "-std=c99", *flags, str(src), "-o", str(exe)], check=True, capture_output=True)
+    hdr = tmp_path / "hdr.cpp"
+    hdr.write_text('#include "pic.h"\nint main() { return PIC_OK; }\n')
+    subprocess.run([cxx, "-std=c++17", *flags, str(hdr), "-o", str(tmp_path / "hdr")], check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, c, d = line.split()
+        got[(a, b)] = (int(c), int(d))
+    for name, T in STRUCTS.items():
+        assert got[(name, ".")][1] == ctypes.sizeof(T), name
+        for f, _ in T._fields_:
+            desc = getattr(T, f)
+            assert got[(name, f)] == (desc.offset, desc.size), (name, f)
+    for name, value in CONSTANTS.items():
+        assert got[("const", name)][0] == value, name
 
 
 def test_default_config_is_valid_and_is_the_smallest_workload(L):
