@@ -76,6 +76,44 @@ def test_header_layout_and_constants_match_the_binding(tmp_path):
         assert got[("const", name)][0] == value, name
 
 
+def test_library_links_and_runs_from_c(L, tmp_path):
+    """A C program linked against libpic_gb300.so alone uses the host-only
+    entry points: defaults, validation, derived constants and status
+    strings, with the same values as the binding."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc")
+    if not cc:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "use.c"
+    src.write_text("""#include <stdio.h>
+#include "pic.h"
+int main(void) {
+  pic_config c;
+  double d[5];
+  if (pic_config_default(&c) != PIC_OK || pic_validate_config(&c) != PIC_OK) return 1;
+  c.n = 16;
+  c.n_particles = 16 * 16 * 16 * 32;
+  if (pic_derived(&c, d) != PIC_OK) return 2;
+  printf("%.17g %.17g %.17g %.17g %.17g\\n", d[0], d[1], d[2], d[3], d[4]);
+  c.n = 1;
+  printf("%s\\n", pic_status_string(pic_validate_config(&c)));
+  return 0;
+}
+""")
+    lib = _lib.LIB_PATH
+    exe = tmp_path / "use"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", str(_lib.HEADER.parent), str(src), "-o", str(exe),
+                    "-L", str(lib.parent), "-lpic_gb300", f"-Wl,-rpath,{lib.parent}"], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    ref = derived(dict(workloads.smallest(), n=16, n_particles=16 ** 3 * 32))
+    got = [float(t) for t in out[0].split()]
+    want = [ref["w"], ref["dV"], ref["pmax"], ref["ppc"], ref["inv_pmax"]]
+    assert all(abs(g - w) <= 1e-14 * abs(w) for g, w in zip(got, want)), (got, want)
+    assert out[1] == L.pic_status_string(_lib.PIC_EINVAL).decode()
+
+
 def test_default_config_is_valid_and_is_the_smallest_workload(L):
     c = _lib.PicConfig()
     assert L.pic_config_default(ctypes.byref(c)) == _lib.PIC_OK
