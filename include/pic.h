@@ -138,9 +138,10 @@ enum { PIC_DIST_CONFIG = 0, PIC_DIST_PAPER = 1 };
  *                pic_create accepts at most 14,528 on a GB300 (227 KB).
  *  seed          Philox4x32-10 key (low word, high word).
  *  cg_tol, cg_maxit  CG stops at ||r||_2 <= cg_tol ||b||_2 or cg_maxit.
- *                The precision form's FP32 vectors reach about 1e-6 (use
- *                1e-6 there); a smaller cg_tol runs to cg_maxit and the
- *                call returns PIC_ENOCONV.
+ *                The precision form's FP32 vectors limit the attainable
+ *                accuracy to about 1e-6 relative, so use 1e-6 there: a
+ *                smaller cg_tol costs iterations without adding accuracy
+ *                and can end at cg_maxit with PIC_ENOCONV.
  *  verify        PIC_VERIFY_* bit flags (0: the method as stated).
  *  dist          PIC_DIST_* (0: the fields fx_*, v_mean, v_sigma above).
  *  n_sigma       0: hard spheres (sigma0). 1..3: the manufactured cross
