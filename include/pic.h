@@ -301,6 +301,17 @@ pic_status pic_get_state(pic_ctx* ctx, double* x, double* v);
 pic_status pic_set_state(pic_ctx* ctx, const double* x, const double* v, double t0,
                          int64_t step);
 
+/* Failure injection for tests, made on the host and caught by a bounded
+ * device wait: the next Poisson solve (of pic_sample_mms, pic_set_state or
+ * pic_step) launches one block that leaves before its first grid barrier,
+ * so the other blocks wait for an arrival that never comes. Their bounded
+ * wait (4e9 SM cycles, about 2 s) ends the solve. That call returns
+ * PIC_ETIMEOUT, and the field and the state it moves are invalid. The
+ * context stays usable: the next pic_sample_mms or pic_set_state starts
+ * clean. PIC_EINVAL for batches (their solves have no grid barrier) and
+ * for a solve of one block (nothing would wait). */
+pic_status pic_inject_barrier_stall(pic_ctx* ctx);
+
 /* Copy mesh quantities out (any pointer may be NULL): rho [n^3] (the CIC
  * charge density of Sec. 2), phi [n^3], E [n^3][3]; host or device. */
 pic_status pic_get_field(pic_ctx* ctx, double* rho, double* phi, double* E);

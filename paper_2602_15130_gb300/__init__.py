@@ -189,6 +189,11 @@ class Pic:
         pb, kb = _ptr(v, 3 * self.np)
         return check(self.L.pic_set_state(self.ctx, pa, pb, float(t0), int(step)), "pic_set_state", allow)
 
+    def inject_barrier_stall(self):
+        """Make the next Poisson solve's bounded barrier wait run out
+        (pic_inject_barrier_stall): that call then returns PIC_ETIMEOUT."""
+        check(self.L.pic_inject_barrier_stall(self.ctx), "pic_inject_barrier_stall")
+
     def get_field(self):
         nc = self.n ** 3
         rho, phi, E = np.zeros(nc), np.zeros(nc), np.zeros((nc, 3))

@@ -140,6 +140,7 @@ SIGNATURES = {
     "pic_batch_get_state": (_S, [_V, ctypes.c_int32, _V, _V]),
     "pic_batch_info": (_S, [_V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                             ctypes.POINTER(ctypes.c_int32)]),
+    "pic_inject_barrier_stall": (_S, [_V]),
     "pic_poisson_solve_noalloc": (_S, [ctypes.c_int32, _V, _V, _V, ctypes.c_double, ctypes.c_int32, _V,
                                       ctypes.POINTER(ctypes.c_int32), _D]),
 }

@@ -147,6 +147,7 @@ struct CgArgs {
   int* info;    // [0] iterations [1] status (1 = no convergence) [2] timeout
   int* flags;   // sticky context flags
   double* res;
+  int skip_block = -1;  // failure injection: this block leaves before its first barrier
   double tol;
   int maxit;
   double *E0, *E1, *E2;
@@ -227,6 +228,8 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CgArgs a) {
   const int G = gridDim.x;
   int ph = 0;  // alternating reduction slots
   auto slot = [&](int q) { return a.red + (size_t)q * 2 * G; };
+  // the others then wait for an arrival that never comes, until the bound
+  if ((int)blockIdx.x == a.skip_block) return;
 
   // phase 0: zero-mean b, r = b - A x, ||r||^2 and ||b||^2
   const double mean_b = grid_total(a.rhs_part, a.rhs_blocks, sh) / (double)m;
@@ -422,6 +425,8 @@ cudaError_t launch_cg_on(pic_ctx* c, double* b, double* x, const double* rhs_par
   a.E0 = E0;
   a.E1 = E1;
   a.E2 = E2;
+  a.skip_block = c->stall_next_cg ? c->cg_grid - 1 : -1;
+  c->stall_next_cg = false;
   cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c->cg_info, 0, 3 * sizeof(int), c->stream);

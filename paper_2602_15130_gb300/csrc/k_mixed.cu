@@ -763,6 +763,7 @@ struct Cg32Args {
   double tol;
   int maxit;
   float4* E4;  // (Ex, Ey, Ez, 0) per node
+  int skip_block = -1;  // failure injection: this block leaves before its first barrier
 };
 
 constexpr long long kBarrierCycles = 4000000000LL;
@@ -902,6 +903,8 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   __shared__ double sh[72];
   __shared__ float fscal[2];  // alpha, beta formed once per block by thread 0
   __shared__ int stop;
+  // the others then wait for an arrival that never comes, until the bound
+  if ((int)blockIdx.x == a.skip_block) return;
   const int n = a.n, nn = a.n * a.n;
   const int m = (int)a.ncell;
   const int stride = gridDim.x * blockDim.x;
@@ -1347,6 +1350,8 @@ cudaError_t launch_cg32(pic_ctx* c) {
   a.tol = c->cfg.cg_tol;
   a.maxit = c->cfg.cg_maxit;
   a.E4 = c->Ef4;
+  a.skip_block = c->stall_next_cg ? c->cg_grid - 1 : -1;
+  c->stall_next_cg = false;
   cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c->cg_info, 0, 3 * sizeof(int), c->stream);

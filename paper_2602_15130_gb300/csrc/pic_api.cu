@@ -981,6 +981,12 @@ pic_status pic_get_state(pic_ctx* c, double* x, double* v) {
   return PIC_OK;
 }
 
+pic_status pic_inject_barrier_stall(pic_ctx* c) {
+  if (!c || c->nrep > 0 || c->cg_grid < 2) return PIC_EINVAL;
+  c->stall_next_cg = true;
+  return PIC_OK;
+}
+
 pic_status pic_get_field(pic_ctx* c, double* rho, double* phi, double* E) {
   if (!c) return PIC_EINVAL;
   if (c->nrep > 0) return PIC_EINVAL;  // batches: use the pic_batch_* calls

@@ -588,6 +588,7 @@ struct pic_ctx {
   int* cg_info;     // [0] iterations, [1] status (0 ok, 1 noconv, 2 timeout)
   double* cg_res;   // relative residual
   int cg_grid, cg_block;
+  bool stall_next_cg;  // failure injection: the next CG launch has one block leave before its first barrier
 
   // G^{-1} knot tables (FP64 and FP32)
   double* ginv;
