@@ -4,7 +4,6 @@ power laws."""
 import math
 from pathlib import Path
 
-import numpy as np
 import pytest
 
 from paper_2602_15130_gb300 import convergence as C

@@ -13,7 +13,6 @@ metric tracks the oracle's within a few samples' worth (5/N).
 import numpy as np
 import pytest
 
-import inputs
 from oracle import oracle as O
 from paper_2602_15130_gb300 import Pic, workloads
 from paper_2602_15130_gb300 import _lib

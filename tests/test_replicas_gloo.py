@@ -5,7 +5,6 @@ rank-level logic is exercised here with world_size 2 on gloo (CPU)."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 
