@@ -544,7 +544,6 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
       s = a.start[cell0 + mycl];
       c = a.start[cell0 + mycl + 1] - s;
     }
-    const int32_t gs = a.start[cell0], ge = a.start[cell0 + ncl];
     for (int ch = 0; ch < a.nchunks; ++ch) {
       const int o = ch * a.Kc + lane % a.Kc;
       bool run = lane_cell && o < P.K && c >= 2;
