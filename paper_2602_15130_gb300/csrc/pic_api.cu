@@ -1,6 +1,7 @@
 // Host runtime and C ABI (include/pic.h): configuration checks, derived
 // constants, device buffers, the step schedule of Eq. velocity_verlet and
-// the boundary copies.
+// the boundary: caller arrays in device or pinned host memory are read and
+// written by the kernels in place, pageable ones are staged through a copy.
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
