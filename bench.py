@@ -11,8 +11,12 @@ kick, drift, sort, deposit, Poisson CG and E. Prints one JSON line
 (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload refine4|precision|refineL|smallest] [--form mixed|fp64]
+                  [--workload refine4|precision|refineL|smallest|batched|batchedN|adjoint]
+                  [--form mixed|fp64] [--no-fp64-beside] [--no-cpu-baseline]
 
+The end-to-end figure (key "e2e") runs pic_set_state from pinned host
+arrays, one step and pic_get_state into pinned host arrays; the library
+reads and writes those arrays in place from its kernels (NVLink-C2C).
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on a bounded sample of the same workload on the host cores.
 Multi-GPU: independent replicas (one per rank, own Philox seed), no
