@@ -278,3 +278,39 @@ def test_binding_rejects_buffers_the_library_would_overrun():
         with pytest.raises(ValueError):
             _ptr(b, 12)
     assert _ptr(np.zeros(5, np.int32), 5, np.int32)[1] is not None
+
+
+def test_odd_power_pmax_matches_oracle_on_random_cross_sections(L):
+    """(sigma g)_max of sigma(g) = sum_k sigma_k g^{2k-1} over [0, g_max] is
+    the maximum of a polynomial of degree < 3 in u = g^2: at u = 0, at
+    u = g_max^2 or at the stationary point. The host's P_coll,max equals the
+    oracle's to 1e-15 for random one- to three-term cross sections (the
+    stationary point inside and outside the interval), and configurations
+    where sigma(g) g turns negative are rejected."""
+    import numpy as np
+
+    rng = np.random.default_rng(42)
+    base = workloads.smallest()
+    checked = rejected = 0
+    for _ in range(400):
+        ns = int(rng.integers(1, 4))
+        sig = [float(x) for x in rng.normal(0.0, 1.0, 3) * [1.0, 0.05, 1e-4]]
+        sig[0] = abs(sig[0]) + 0.1
+        p = dict(base, n_sigma=ns, sigma_n=tuple(sig[:ns] + [0.0] * (3 - ns)))
+        c = make_config(p)
+        u = np.linspace(0.0, p["g_max"] ** 2, 20001)
+        poly = sum(sig[k] * u ** k for k in range(ns))
+        if poly.min() < -1e-12 * abs(poly).max():
+            assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_EINVAL
+            rejected += 1
+            continue
+        if poly.min() < 0.0:
+            continue  # within rounding of zero: either verdict is fine
+        assert L.pic_validate_config(ctypes.byref(c)) == _lib.PIC_OK
+        ours, theirs = derived(p)["pmax"], O.pmax(O.make_cfg(p))
+        assert abs(ours - theirs) <= 1e-15 * theirs, (sig[:ns], ours, theirs)
+        # and it is the maximum of the dense scan (within its resolution)
+        scan = poly.max() * derived(p)["w"] * p["dt"] / derived(p)["dV"]
+        assert ours >= scan * (1 - 1e-12) and ours <= scan * (1 + 1e-6)
+        checked += 1
+    assert checked > 100 and rejected > 20, (checked, rejected)
