@@ -289,3 +289,50 @@ def test_anisotropy_constants_minimise_the_distance_to_the_soft_sphere_target():
     for chi in (0.2, 0.9, 1.7, 2.5, 3.1):
         F = integrate.quad(lambda x: _p_chi(x, 0.5, 12 / 29), 0, chi, epsabs=1e-14)[0]
         assert abs(O.lib().orc_aniso_F(np.sin(chi / 2) ** 2) - F) < 1e-12, chi
+
+
+# ------------------------------------------------------ norms and push -----
+def _paper(**kw):
+    from paper_2602_15130_gb300 import workloads as W
+
+    return W.paper_small(**kw)
+
+
+@pytest.mark.parametrize("t0", [0.0, 0.3])
+def test_paper_error_norms_hand_computed(t0):
+    """Sec. 4.3 norms on the paper's problem: known offsets from the
+    manufactured state at the context time (v^M(t0) = tau vh(t0))."""
+    p = _paper(n=4, n_particles=3, K=0)
+    o = O.Oracle(p)
+    o.sample(t0)
+    x, v = o.state()
+    dx = np.array([[0.01, -0.02, 0.0], [0.0, 0.0, 0.03], [-0.5 + 1e-9, 0.0, 0.0]])
+    dv = np.array([[0.1, 0.0, 0.0], [0.0, -0.2, 0.0], [0.0, 0.0, 0.05]])
+    o.set_state((x + dx) % 1.0, v + dv, t0, 0)
+    e = o.errors()
+    assert abs(e[0] - np.sqrt((np.array([0.01, 0.0, 0.5 - 1e-9]) ** 2).mean())) < 1e-12
+    assert abs(e[1] - np.sqrt((np.array([0.02, 0.0, 0.0]) ** 2).mean())) < 1e-12
+    assert abs(e[7] - (0.5 - 1e-9)) < 1e-12
+    assert abs(e[3] - np.sqrt(0.01 / 3.0)) < 1e-13 and abs(e[10] - 0.1) < 1e-13
+    assert abs(e[4] - np.sqrt(0.04 / 3.0)) < 1e-13 and abs(e[11] - 0.2) < 1e-13
+    assert abs(e[5] - np.sqrt(0.0025 / 3.0)) < 1e-13 and abs(e[12] - 0.05) < 1e-13
+
+
+def test_paper_uncoupled_push_is_second_order():
+    """q/m = 0, q = 0, no collisions on the paper's problem: the exact
+    solution is x^M(t), v^M(t) = tau vh(t), and Eq. velocity_verlet with the
+    sources of Eq. eom_mms (vdot^M in both half kicks, the general xdot^M in
+    the drift) leaves errors that fall as dt^2. A dropped or sign-flipped
+    vdot^M term leaves an O(1) velocity error and fails it."""
+    ex, ev = [], []
+    for m in (8, 16, 32):
+        p = _paper(n=4, n_particles=200, K=0, n_sigma=0, dt=1.0 / m, couple_qm_zero=1, couple_q_zero=1)
+        o = O.Oracle(p)
+        o.sample(0.0)
+        o.step(m)
+        e = o.errors()
+        ex.append(e[7])
+        ev.append(max(e[10], e[11], e[12]))
+    for errs in (ex, ev):
+        r1, r2 = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
+        assert 1.8 < r1 < 2.2 and 1.8 < r2 < 2.2, (errs, r1, r2)
