@@ -336,3 +336,20 @@ def test_paper_uncoupled_push_is_second_order():
     for errs in (ex, ev):
         r1, r2 = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
         assert 1.8 < r1 < 2.2 and 1.8 < r2 < 2.2, (errs, r1, r2)
+
+
+@pytest.mark.parametrize("t", [0.0, 0.37])
+def test_paper_rhoM_is_the_printed_density_and_integrates_to_qN(t):
+    """rho^M = q f_x (Eq. poisson_mms) with the paper's printed per-axis f_x
+    at random points, and its integral over the box is q N (scipy)."""
+    q, N = 2.5, 3.0
+    c = paper_cfg(n_phys=N)
+    e = math.exp(t / T_REF)
+    for x in inputs.rng(3).random((25, 3)):
+        want = q * N * ((1 + e / 5 * math.sin(2 * math.pi * x[0]))
+                        * (1 + 1 / 5 * math.sin(2 * math.pi * (x[1] - 3 * e / 20)))
+                        * (1 - e / 6 * math.sin(2 * math.pi * (x[2] + e / 15))))
+        assert abs(O.rhoM(c, q, x, t) - want) <= 1e-14 * abs(want)
+    total, _ = integrate.tplquad(lambda z, y, x: O.rhoM(c, q, np.array([x, y, z]), t), 0, 1, 0, 1, 0, 1,
+                                 epsabs=1e-9, epsrel=1e-9)
+    assert abs(total - q * N) < 1e-7
