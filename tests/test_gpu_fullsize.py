@@ -33,7 +33,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from paper_2602_15130_gb300 import Batch, Pic, derived, workloads as W
+from paper_2602_15130_gb300 import Batch, Pic, workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -82,7 +82,7 @@ def check_deposit(p, x, count, start, perm, rho, nodes, charge_tol):
     the particles of the 8 cells around each node."""
     n = p["n"]
     h = 1.0 / n
-    w = derived(p)["w"]
+    w = p["n_phys"] / p["n_particles"]
     q = p["q"]
     Q = q * w * p["n_particles"]
     assert abs(rho.sum() * h ** 3 - Q) <= charge_tol * Q
@@ -115,9 +115,10 @@ def check_field(p, phi, E, cg_res):
 
 
 def expected_candidates(p, counts):
-    """K sum_cells C(c, 2) P_coll,max per call (E floor(a + U) = a) and a
-    bound of 6 standard deviations of the floors' rounding."""
-    pm = derived(p)["pmax"]
+    """K sum_cells C(c, 2) P_coll,max per call (E floor(a + U) = a), with
+    the oracle's P_coll,max, and a bound of 6 standard deviations of the
+    floors' rounding."""
+    pm = O.pmax(O.make_cfg(p))
     exp = sum(p["K"] * pm * float(np.sum(c.astype(np.float64) * (c - 1) / 2.0)) for c in counts)
     sd = math.sqrt(0.25 * p["K"] * sum(len(c) for c in counts))
     return exp, 6.0 * sd + 1e-6 * exp
