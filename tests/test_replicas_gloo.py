@@ -79,3 +79,22 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_clock_summary_reports_median_max_and_active_reasons():
+    """The clock record beside each bench number: median SM clock under load,
+    the maximum clock, and every throttle reason seen active (nvidia-smi CSV
+    rows, synthetic here)."""
+    import bench
+
+    s = bench.ClockSampler(0)
+    assert s.summary()["samples"] == 0 and s.summary()["reasons"] == ["clock samples unavailable"]
+    na, a = "Not Active", "Active"
+    s.rows = [["0", "2070", "2070", "900.5", "0x0", na, na, na, na],
+              ["0", "1980", "2070", "1400.0", "0x4", na, na, na, a],
+              ["0", "2070", "2070", "1395.1", "0x0", na, na, na, na]]
+    d = s.summary()
+    assert d["sm_mhz"] == 2070.0 and d["sm_max_mhz"] == 2070.0 and d["samples"] == 3
+    assert d["reasons"] == ["sw_power_cap"]
+    s.rows.append(["0", "1500", "2070", "1200.0", "0x48", a, na, a, na])
+    assert bench.ClockSampler.summary(s)["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
