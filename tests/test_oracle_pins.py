@@ -349,6 +349,41 @@ def _cell_velocities(c, seed):
     return 0.2 + np.random.default_rng(seed).standard_normal((c, 3))
 
 
+@pytest.mark.parametrize("dist", [0, 1])
+def test_rhs_terms_signs_and_scales(dist):
+    """Eq. poisson_mms: b = rho/eps0 - Lap phi^M - rho^M/eps0 with the mean
+    removed, rebuilt from independent pieces: the deposited rho (pinned
+    above), Lap phi^M = -12 pi^2 phi^M for the product of sines, and rho^M =
+    q N f_x from the printed densities; q, eps0 and N away from 1 so that a
+    dropped, sign-flipped or misscaled term fails."""
+    import ctypes
+
+    q, eps0, N, t = 2.0, 1.5, 1.3, 0.37
+    if dist == 0:
+        p = W.smallest(n=6, n_particles=6 ** 3 * 20, K=0, q=q, eps0=eps0, n_phys=N)
+    else:
+        p = W.paper_small(n=6, n_particles=6 ** 3 * 20, K=0, n_sigma=0, q=q, eps0=eps0, n_phys=N)
+    o = O.Oracle(p)
+    o.sample(t)
+    rho, _, _ = o.field()
+    n = p["n"]
+    b = np.zeros(n ** 3)
+    O.lib().orc_rhs(o.h, t, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    X = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1) / n
+    amp = p["phi_amp"] * math.exp(t / (2 * p["phi_T"]))
+    phiM = amp * np.prod(np.sin(2 * math.pi * (X - np.array(p["phi_shift"]))), axis=1)
+    if dist == 0:
+        fx = np.prod(1 + p["fx_amp"] * np.sin(2 * math.pi * (X - p["fx_speed"] * t)), axis=1)
+    else:
+        e = math.exp(t / p["t_ref"])
+        fx = ((1 + e / 5 * np.sin(2 * math.pi * X[:, 0])) * (1 + 0.2 * np.sin(2 * math.pi * (X[:, 1] - 3 * e / 20)))
+              * (1 - e / 6 * np.sin(2 * math.pi * (X[:, 2] + e / 15))))
+    ref = rho / eps0 + 12 * math.pi ** 2 * phiM - q * N * fx / eps0
+    ref -= ref.mean()
+    assert np.abs(b - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("c", [2, 3, 7, 40])
 def test_ntc_conserves_momentum_and_energy(c):
     cf = O.make_cfg(W.smallest(dt=0.5))  # large P_max: many collisions per outcome
