@@ -48,7 +48,8 @@
  *  - orc_fn, orc_odd_source: printed formulas, Gauss-Hermite quadrature.
  *  - orc_sigma_g, orc_sg_max, orc_pmax: dense scan, Table 1 column.
  *  - orc_cell_of, orc_sort, orc_deposit, orc_gather, orc_rhs: brute force,
- *    total charge, affine fields.
+ *    total charge, affine fields, the right-hand side rebuilt term by term
+ *    from closed forms.
  *  - orc_neg_lap, orc_cg, orc_efield, orc_field: Fourier eigenvalues, FFT
  *    solve, closed forms, uncoupled phi^M.
  *  - orc_ntc_cell, orc_dsmc_avg, orc_aniso_F, orc_aniso_u: momentum and
