@@ -78,8 +78,9 @@ def test_header_layout_and_constants_match_the_binding(tmp_path):
 
 def test_library_links_and_runs_from_c(L, tmp_path):
     """A C program linked against libpic_gb300.so alone uses the host-only
-    entry points: defaults, validation, derived constants and status
-    strings, with the same values as the binding."""
+    entry points (defaults, validation, derived constants and status
+    strings, with the same values as the binding) and pic_create, which
+    without a GPU returns PIC_ECUDA and a NULL context."""
     import shutil
     import subprocess
 
@@ -99,6 +100,11 @@ int main(void) {
   printf("%.17g %.17g %.17g %.17g %.17g\\n", d[0], d[1], d[2], d[3], d[4]);
   c.n = 1;
   printf("%s\\n", pic_status_string(pic_validate_config(&c)));
+  c.n = 16;
+  pic_ctx* ctx = (pic_ctx*)&c;  /* must be cleared on failure */
+  pic_status s = pic_create(&c, NULL, NULL, &ctx);
+  printf("%d %d\\n", (int)s, ctx == NULL);
+  pic_destroy(ctx);
   return 0;
 }
 """)
@@ -112,6 +118,15 @@ int main(void) {
     want = [ref["w"], ref["dV"], ref["pmax"], ref["ppc"], ref["inv_pmax"]]
     assert all(abs(g - w) <= 1e-14 * abs(w) for g, w in zip(got, want)), (got, want)
     assert out[1] == L.pic_status_string(_lib.PIC_EINVAL).decode()
+    # without a GPU, pic_create fails with a status and a NULL context (no
+    # CPU fallback); with one, it creates and the program destroys it
+    import torch
+
+    status, null = (int(t) for t in out[2].split())
+    if torch.cuda.is_available():
+        assert status == _lib.PIC_OK and null == 0
+    else:
+        assert status == _lib.PIC_ECUDA and null == 1
 
 
 def test_default_config_is_valid_and_is_the_smallest_workload(L):
