@@ -329,3 +329,21 @@ def test_odd_power_pmax_matches_oracle_on_random_cross_sections(L):
         assert ours >= scan * (1 - 1e-12) and ours <= scan * (1 + 1e-6)
         checked += 1
     assert checked > 100 and rejected > 20, (checked, rejected)
+
+
+def test_no_cpu_fallback(monkeypatch, tmp_path):
+    """The product path fails loudly: without the built library the binding
+    raises instead of computing anything, and without a GPU no context is
+    created."""
+    import torch
+
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", tmp_path / "libpic_gb300.so")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load()
+    monkeypatch.undo()
+    if not torch.cuda.is_available():
+        from paper_2602_15130_gb300 import Pic
+
+        with pytest.raises(Exception):
+            Pic(workloads.smallest())
