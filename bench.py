@@ -1,24 +1,26 @@
 """Throughput of the manufactured-solution PIC + DSMC step on GB300.
 
-Default workload: the finest level of the refinement sweep (128^3 cells,
-32 particles per cell = 67,108,864 particles, K = 16, dt = 0.02/16,
-collisions on). The headline value is the precision form (FP32 particle
-state, int32 cell + FP32 offset, FP64-accurate charge sums, CG inner
-products and error norms); the plain FP64 path runs the same workload
-beside it, and both sets of MMS error norms are reported. A step is one
-full velocity-Verlet step of every particle: two K-averaged DSMC calls,
-kick, drift, sort, deposit, Poisson CG and E. Prints one JSON line
-(rank 0).
+Default workload: the precision-form study (128^3 cells, 64 particles per
+cell = 134,217,728 particles, K = 32, dt = 0.005, hard-sphere collisions at
+0.01 expected collisions per particle per call). The headline value is the
+precision form (FP32 particle state, int32 cell + FP32 offset, FP64-accurate
+charge sums, CG inner products and error norms); the plain FP64 path runs
+the same workload beside it, and both sets of MMS error norms are
+reported. A step is one full velocity-Verlet step of every particle: two
+K-averaged DSMC calls, kick, drift, sort, deposit, Poisson CG and E. The
+library records, per timed step, the CG iterations and the candidate,
+collision and g > g_max counts (its per-step history), which the line
+carries. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload refine4|precision|refineL|smallest|batched|batchedN|adjoint]
+                  [--workload precision|refine4|refineL|smallest|batched|batchedN|adjoint]
                   [--form mixed|fp64] [--no-fp64-beside] [--no-cpu-baseline]
 
 The end-to-end figure (key "e2e") runs pic_set_state from pinned host
 arrays, one step and pic_get_state into pinned host arrays; the library
 reads and writes those arrays in place from its kernels (NVLink-C2C).
 --impl reference times the FP64 CPU oracle (the only reference this method
-has) on a bounded sample of the same workload on the host cores.
+has) on a bounded sample of the same workload on all host cores.
 Multi-GPU: independent replicas (one per rank, own Philox seed), no
 collective on the data path; value = particles x steps of all ranks / max
 rank time.
@@ -26,6 +28,7 @@ rank time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -117,45 +120,60 @@ def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json: STREAM-style copy)"}
     except Exception:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-# Algorithmic HBM bytes per unit for each kernel class of one step. Units:
-# particles for the particle kernels, nodes x CG iterations for the CG; each
-# figure counts the arrays the kernel must read and write once (for example
-# the precision-form drift kick: cell, three offsets, three velocities, three
-# v^M, pid, three collision terms and three Lorentz terms in; three offsets,
-# three velocities, key and slot out: 100 B; the closing kick 64 B).
-# Philox4x32-10: 10 rounds of two 32x32->64 products (4 ops), four xors and
-# two key additions; GB300 issues 64 INT32 lanes per SM per clock.
-INT_OPS_PER_PHILOX = 100
-INT32_LANES_PER_SM = 64
-# DRAM bytes per particle of one k_dsmc32 launch (read 200.7 MB + write
-# 119.9 MB for 8,388,608 particles at 32 per cell, K = 16; mean of the two
-# launches), from the capture summarised in profiles/ncu_full_mixed_refine3.md;
-# valid while that kernel is unchanged
-NCU_DSMC32_DRAM_BYTES_PER_PARTICLE = (200.7e6 + 119.9e6) / 8388608
-
+# Algorithmic HBM bytes per unit of each kernel class of one step: what the
+# method must move, per particle for the particle kernels (one launch
+# processes every particle), per node for the RHS and per node-iteration for
+# the CG. "method": the per-particle-step figures the method implies for
+# the FP32 state of 56 B (cell, three offsets, three velocities, three v^M
+# as the manufactured velocity, pid) or the FP64 state of 104 B: the push
+# reads and writes the state once per step (two launches: half each), the
+# sort scatter reads and writes it once, the deposit reads the positions
+# once, and each CG iteration moves about 28 B (FP32) or 56 B (FP64) per
+# node. "impl": the arrays this implementation's kernels read and write once
+# (for example the precision-form drift launch: cell, three offsets, three
+# velocities, three v^M, pid, three collision and three Lorentz terms in;
+# three offsets, three velocities, key and slot out: 100 B; the closing kick
+# 64 B).
 BYTES_PER_UNIT = {
     "fp64": {
-        "kick_drift": (228 + 120) / 2.0,   # mean of the drift (228 B) and closing (120 B) kick launches
-        "sort_gather_deposit": 208 + 64 / 32.0,
-        "dsmc": 48.0,
-        "sort": 12.0,
-        "cg_efield": 88.0,
-        "rhs": 8 * 8 + 16,                 # per node: 8 corner partials in, rho and b out
+        "method": {"kick_drift": 104.0, "sort_gather_deposit": 208.0 + 24.0, "cg_efield": 56.0},
+        "impl": {"kick_drift": (228 + 120) / 2.0, "sort_gather_deposit": 208 + 64 / 32.0, "dsmc": 48.0,
+                 "sort": 12.0, "cg_efield": 88.0, "rhs": 8 * 8 + 16},
     },
     "mixed": {
-        "kick_drift": (100 + 64) / 2.0,
-        "sort_gather_deposit": 88 + 64 / 32.0,
-        "dsmc": 24.0,
-        "sort": 12.0,
-        "cg_efield": 44.0,
-        "rhs": 8 * 8 + 8 + 4,              # per node: 8 corner partials in, rho (FP64) and b (FP32) out
+        "method": {"kick_drift": 56.0, "sort_gather_deposit": 112.0 + 16.0, "cg_efield": 28.0},
+        "impl": {"kick_drift": (100 + 64) / 2.0, "sort_gather_deposit": 88 + 64 / 32.0, "dsmc": 24.0,
+                 "sort": 12.0, "cg_efield": 44.0, "rhs": 8 * 8 + 8 + 4},
     },
 }
+
+# Philox4x32-10 integer operations per block by its definition: ten rounds of
+# two 32 x 32 -> 64 products (four ops: high and low halves), two 3-input
+# xors (four ops) and two key additions
+INT_OPS_PER_PHILOX = 100
+
+# DRAM bytes of one launch of the dominant kernels, per unit, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# kernel source it was taken on: bench.py compares the source file's hash
+# and reports null traffic once the kernel has changed.
+NCU_TRAFFIC = {}
+
+
+def source_hash(path: str) -> str:
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch(form: str, kernel: str, units: float):
+    e = NCU_TRAFFIC.get((form, kernel))
+    if not e or source_hash(e["source"]) != e["sha16"]:
+        return None, None
+    return e["bytes_per_unit"] * units, e["how"]
 
 
 # ------------------------------------------------------------- replicas -----
@@ -184,11 +202,39 @@ def aggregate_value(n_particles: int, steps: int, world: int, max_ms: float) -> 
 
 
 # ----------------------------------------------------------------- GPU arm ---
+def per_step(hist) -> dict:
+    """The library's per-step history of the timed steps, as lists."""
+    return {"cg_iters": [int(r[0]) for r in hist], "n_cand": [int(r[1]) for r in hist],
+            "n_coll": [int(r[2]) for r in hist], "n_gmax_exceed": [int(r[3]) for r in hist]}
+
+
+def class_rates(p: dict, form: str, kt: dict, st: dict, hbm: float) -> dict:
+    """Per kernel class: ms per launch and the achieved fraction of the
+    measured HBM bandwidth by the method's bytes and by the implementation's."""
+    out = {}
+    for k, v in kt.items():
+        if not v["launches"]:
+            continue
+        ms = v["ms"] / v["launches"]
+        units = p["n"] ** 3 * max(1, st["cg_iters_mean"]) if k == "cg_efield" else (
+            p["n"] ** 3 if k == "rhs" else p["n_particles"])
+        row = {"ms_per_launch": round(ms, 4), "launches": v["launches"], "units_per_launch": units}
+        for which in ("method", "impl"):
+            b = BYTES_PER_UNIT[form][which].get(k)
+            if b is not None and ms > 0:
+                gbs = b * units / (ms * 1e-3) / 1e9
+                row[f"bytes_per_unit_{which}"] = b
+                row[f"gbs_{which}"] = round(gbs, 1)
+                row[f"frac_of_measured_hbm_{which}"] = round(gbs / hbm, 4)
+        out[k] = row
+    return out
+
+
 def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> dict | None:
     import numpy as np
     import torch
 
-    from paper_2602_15130_gb300 import Pic, workloads as W
+    from paper_2602_15130_gb300 import Pic, measure_alu_peaks, workloads as W
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -208,7 +254,7 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
             import torch.distributed as td
             td.barrier()
         torch.cuda.synchronize()
-        sim.reset_stats()
+        sim.reset_stats()  # counters, and the per-step history starts here
         sim.set_profiling(True)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(dev) as clk:
@@ -220,19 +266,25 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
         ms = ev0.elapsed_time(ev1)
         kt = sim.kernel_times()
         st = sim.stats()
+        hist = sim.step_history()
         sim.set_profiling(False)
         ms = max_over_ranks(ms, "cuda")
         errs = sim.mms_error()
         npart = p["n_particles"]
+        st["cg_iters_mean"] = float(np.mean(hist[:, 0])) if len(hist) else float(st["cg_iters_max"])
+        stats = {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_gmax_exceed": st["n_gmax_exceed"],
+                 "n_near_ties": st["n_near_ties"], "n_floor_ties": st["n_floor_ties"],
+                 "cg_iters_mean": round(st["cg_iters_mean"], 2), "cg_iters_max": st["cg_iters_max"],
+                 "cg_res_last": st["cg_res_last"]}
         if not with_e2e:
             sim.close()
             if rank != 0:
                 return None
             return {"value": aggregate_value(npart, args.steps, world, ms), "ms_per_step": ms / args.steps,
                     "kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items()},
+                    "kernels": class_rates(p, form, kt, st, measured_peaks()["hbm_gbs"]),
                     "mms_error": {"eps2": errs["eps2"], "epsinf": errs["epsinf"]},
-                    "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
-                              "cg_iters_max": st["cg_iters_max"]}, "clocks": clk.summary()}
+                    "stats": stats, "per_step": per_step(hist), "clocks": clk.summary()}
         # end to end through the C ABI with host buffers: pinned x, v in, step, x, v out
         xh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
         vh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
@@ -248,52 +300,41 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
             sim.get_state((xh, vh))
         e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
         sim.close()
+        alu = measure_alu_peaks(stream) if rank == 0 else None
     if rank != 0:
         return None
     value = aggregate_value(npart, args.steps, world, ms)
     peaks = measured_peaks()
-    bpu = BYTES_PER_UNIT[form]
-
-    def units_of(k):
-        if k == "cg_efield":
-            return p["n"] ** 3 * max(1, st["cg_iters_max"])
-        return p["n"] ** 3 if k == "rhs" else npart
-
-    def hbm_gbs(k):
-        per_launch_ms = kt[k]["ms"] / max(1, kt[k]["launches"])
-        return bpu.get(k, 0.0) * units_of(k) / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
-
+    kernels = class_rates(p, form, kt, st, peaks["hbm_gbs"])
     # dominant kernel class by device time inside the timed region
     dom = max(kt, key=lambda k: kt[k]["ms"])
-    achieved = hbm_gbs(dom)
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
-            "bytes_per_unit": bpu.get(dom), "units_per_launch": units_of(dom)}
+    row = kernels[dom]
     if dom == "dsmc":
         # integer-ALU bound: the Philox4x32-10 blocks the method draws per
-        # launch (one per (cell, outcome) lane for N_pairs, one per candidate
-        # pair, one more per accepted pair) at INT_OPS_PER_PHILOX each,
-        # against INT32_LANES_PER_SM x SMs x the sampled maximum SM clock
+        # launch (one per (cell, outcome) for N_pairs, one per candidate
+        # pair, one more per accepted pair for chi), against the measured
+        # rate of this GPU at forming those blocks
         nl = max(1, kt["dsmc"]["launches"])
-        blocks = p["n"] ** 3 * p["K"] + (st["n_cand"] + st["n_coll"]) / nl
-        ops = blocks * INT_OPS_PER_PHILOX
+        ncell2 = p["n"] ** 3  # cells with two or more particles: all at these occupancies
+        blocks = ncell2 * p["K"] + (st["n_cand"] + st["n_coll"]) / nl
         per_launch_s = kt["dsmc"]["ms"] / nl / 1000.0
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        mhz = clk.summary().get("sm_max_mhz") or 2070.0
-        peak = INT32_LANES_PER_SM * sms * mhz * 1e6
-        traffic = (NCU_DSMC32_DRAM_BYTES_PER_PARTICLE * npart
-                   if form == "mixed" and (p["n"], p["K"]) == (128, 16) else None)
-        roof = {"bound": "alu", "kernel": "dsmc", "achieved": ops / per_launch_s / 1e12, "peak": peak / 1e12,
-                "unit": "Tops/s (INT32)", "frac": ops / per_launch_s / peak, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read+write of k_dsmc32 at 64^3 (8.4M particles, K=16), "
-                                  "scaled by particles; profiles/ncu_full_mixed_refine3.md",
-                "peak_source": "derived: %d INT32 lanes/SM x %d SMs x %.0f MHz" % (INT32_LANES_PER_SM, sms, mhz),
-                "ops_per_launch": ops, "philox_blocks_per_launch": blocks,
-                "hbm_frac_of_measured": round(achieved / peaks["hbm_gbs"], 4)}
-    step_kernels = {k: {"ms_per_launch": round(kt[k]["ms"] / max(1, kt[k]["launches"]), 4),
-                        "bytes_per_unit": bpu[k], "achieved_gbs": round(hbm_gbs(k), 1),
-                        "frac_of_measured_hbm": round(hbm_gbs(k) / peaks["hbm_gbs"], 4)}
-                    for k in bpu if kt.get(k, {}).get("launches")}
+        achieved = blocks * INT_OPS_PER_PHILOX / per_launch_s / 1e12
+        peak = alu["philox_blocks"] * INT_OPS_PER_PHILOX / 1e12
+        traffic, how = traffic_per_launch(form, "dsmc", npart)
+        roof = {"bound": "alu", "kernel": "dsmc", "achieved": achieved, "peak": peak, "unit": "Tops/s (INT32)",
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": how,
+                "peak_source": "measured in this run: Philox4x32-10 blocks/s of a full-grid generator kernel "
+                               "(pic_measure_alu_peaks) x %d integer ops per block" % INT_OPS_PER_PHILOX,
+                "philox_blocks_per_launch": blocks, "ms_per_launch": row["ms_per_launch"]}
+    else:
+        b = BYTES_PER_UNIT[form]["method"].get(dom) or BYTES_PER_UNIT[form]["impl"].get(dom, 0.0)
+        units = row["units_per_launch"]
+        achieved = b * units / (row["ms_per_launch"] * 1e-3) / 1e9
+        traffic, how = traffic_per_launch(form, dom, units)
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": how,
+                "peak_source": peaks["source"], "bytes_per_unit": b, "units_per_launch": units,
+                "ms_per_launch": row["ms_per_launch"]}
     launches = int(st["kernel_launches"])
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -301,18 +342,18 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
         "vs_baseline": None, "dtype": "f32" if form == "mixed" else "f64",
         "data": "synthetic manufactured-solution workload",
         "config": {"workload": describe(args.workload, p), "n": p["n"], "n_particles": npart, "K": p["K"],
-                   "dt": p["dt"], "form": form, "parallelism": f"replicas{world}",
+                   "dt": p["dt"], "sigma0": p["sigma0"], "form": form, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (particle state %.1f GB)" % (npart * (44 if form == "mixed" else 100) / 1e9)},
         "e2e": {"value": aggregate_value(npart, e2e_steps, world, e2e_s * 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": npart * 48, "d2h_bytes_per_step": npart * 48,
                 "path": "pic_set_state(host) + pic_step(1) + pic_get_state(host), pinned buffers"},
         "gpu_launches": launches,
         "roofline": roof,
-        "step_kernels_hbm": step_kernels,
+        "kernels": kernels,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items()},
-        "kernel_launches_by_class": {k: v["launches"] for k, v in kt.items()},
-        "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
-                  "cg_iters_max": st["cg_iters_max"], "cg_res_last": st["cg_res_last"]},
+        "alu_peaks_per_s": alu,
+        "stats": stats,
+        "per_step": per_step(hist),
         "mms_error": {"eps2": errs["eps2"], "epsinf": errs["epsinf"]},
         "clocks": clk.summary(),
     }
@@ -441,47 +482,69 @@ def run_adjoint(args) -> dict:
 
 
 # ------------------------------------------------------------ CPU oracle ----
-def oracle_sample_params(args) -> tuple[dict, str]:
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_params(args, n_small: int) -> tuple[dict, str]:
     from paper_2602_15130_gb300 import workloads as W
 
     p = workload(args.workload)
-    n_small = min(p["n"], args.cpu_mesh)
+    n_small = min(p["n"], n_small)
     q = W.scaled(p, n_small)
-    return q, (f"oracle on a {n_small}^3 sub-problem with the workload's particles per cell, K and dt "
-               f"({q['n_particles']} particles), single host thread")
+    return q, (f"oracle on a {n_small}^3 sub-problem with the workload's particles per cell, K, dt and sigma0 "
+               f"({q['n_particles']} particles)")
 
 
-def run_oracle_steps(q: dict, steps: int, warmup: int) -> tuple[float, float]:
+def run_oracle_steps(q: dict, steps: int, warmup: int, threads: int) -> tuple[float, float, int]:
     from oracle import oracle as O
 
-    o = O.Oracle(q)
-    o.sample(0.0)
-    if warmup:
-        o.step(warmup)
-    t0 = time.perf_counter()
-    o.step(steps)
-    dt = time.perf_counter() - t0
-    o.close()
-    return q["n_particles"] * steps / dt, dt
+    used = O.set_threads(threads)
+    try:
+        o = O.Oracle(q)
+        o.sample(0.0)
+        if warmup:
+            o.step(warmup)
+        t0 = time.perf_counter()
+        o.step(steps)
+        dt = time.perf_counter() - t0
+        o.close()
+    finally:
+        O.set_threads(1)
+    return q["n_particles"] * steps / dt, dt, used
 
 
 def cpu_baseline(args) -> dict:
-    q, sample = oracle_sample_params(args)
-    rate, dt = run_oracle_steps(q, args.cpu_steps, 0)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + f", {args.cpu_steps} step(s), {dt:.1f} s"}
+    """The oracle as it stands on the host cores: threaded over independent
+    cells and particles on every core (the same bits as one thread), and
+    single-threaded on a smaller sample."""
+    cores = host_cores()
+    q, sample = oracle_sample_params(args, args.cpu_mesh)
+    rate, dt, used = run_oracle_steps(q, args.cpu_steps, 0, cores)
+    q1, sample1 = oracle_sample_params(args, args.cpu_mesh_1thread)
+    rate1, dt1, _ = run_oracle_steps(q1, 1, 0, 1)
+    return {"value": rate, "unit": UNIT, "cores": used, "host_cores": cores, "kind": "oracle",
+            "sample": sample + f", {used} threads, {args.cpu_steps} step(s), {dt:.1f} s",
+            "value_1thread": rate1, "sample_1thread": sample1 + f", 1 thread, 1 step, {dt1:.1f} s"}
 
 
 def run_reference(args, rank: int) -> dict | None:
     if rank != 0:
         return None
-    q, sample = oracle_sample_params(args)
-    rate, dt = run_oracle_steps(q, args.steps, args.warmup)
+    cores = host_cores()
+    q, sample = oracle_sample_params(args, args.cpu_mesh)
+    rate, dt, used = run_oracle_steps(q, args.steps, args.warmup, cores)
+    sample += f", {used} threads"
     return {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1000 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic manufactured-solution workload",
         "config": {"workload": describe(args.workload, workload(args.workload)), "sample": sample},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": used, "host_cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -489,13 +552,14 @@ def run_reference(args, rank: int) -> dict | None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="refine4")
+    ap.add_argument("--workload", default="precision")
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-beside", action="store_true")
     ap.add_argument("--cpu-mesh", type=int, default=24)
+    ap.add_argument("--cpu-mesh-1thread", type=int, default=12)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

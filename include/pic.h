@@ -188,7 +188,12 @@ typedef struct {
   int64_t n_cand;         /* candidate pairs drawn (Algorithm 1 loop)       */
   int64_t n_coll;         /* accepted collisions                            */
   int64_t n_gmax_exceed;  /* candidates with g > g_max (ratio above 1)      */
-  int64_t n_near_ties;    /* |U - sigma g/(sigma g)_max| < 1e-12            */
+  int64_t n_near_ties;    /* accept decisions within the tie bound: FP64
+                             |U - sigma g/(sigma g)_max| < 1e-12; precision
+                             form |U g_max - g| <= 2^-19 (g_max + U g_max)
+                             (hard spheres) or |U (sigma g)_max - sigma g|
+                             <= 2^-17 ((sigma g)_max + sigma g), the bound of
+                             its FP32 uniforms and velocities (flagged)     */
   int64_t kernel_launches;/* kernels this library launched                  */
   int64_t step;           /* steps taken since sampling                     */
   double t;               /* current time t0 + step dt                      */
@@ -198,6 +203,9 @@ typedef struct {
   int64_t graph_replays;  /* batched steps replayed from a captured CUDA graph */
   int32_t tuned_kick_block; /* block size the batch autotuner chose (0: none) */
   int32_t reserved;
+  int64_t n_floor_ties;   /* precision form: N_pairs draws whose FP32 sum lay
+                             within its rounding bound of an integer, so that
+                             its floor may differ from the FP64 one (flagged) */
 } pic_stats;
 
 /* Scattering-angle CDF errors of Sec. 4.4 over every collision recorded
@@ -326,6 +334,49 @@ pic_status pic_get_stats(pic_ctx* ctx, pic_stats* out);
 /* Zero the counters of pic_stats and the recorded scattering angles. */
 pic_status pic_reset_stats(pic_ctx* ctx);
 
+/* Per-step record of the steps taken since the last pic_reset_stats,
+ * pic_sample_mms or pic_set_state (the first 4096 of them), written by the
+ * kernels themselves, so reading it afterwards does not perturb the timing
+ * of the steps: out[i][0] = CG iterations of step i's Poisson solve,
+ * out[i][1] = candidate pairs, out[i][2] = accepted collisions, out[i][3] =
+ * candidates with g > g_max, the last three summed over both collision
+ * calls of the step. out is int64 [cap][4], host or device; *n = the steps
+ * written (min(steps recorded, cap)). PIC_EINVAL for a batch. */
+pic_status pic_get_step_history(pic_ctx* ctx, int64_t* out, int64_t cap, int64_t* n);
+
+/* Decision log of the collision calls (a verification hook for Algorithm 1;
+ * the paper has no counterpart). While on, the collision kernels append one
+ * record of 8 int32 per logged decision:
+ *   (c0, cell, outcome, slot, p, q, result, kind)
+ * c0 = 2 step + phase (Philox counter word 0 of the call), the linear cell
+ * index, the outcome k < K, and
+ *  - for the N_pairs draw of a (cell, outcome): slot = -1, p = q = -1,
+ *    result = N_pairs, kind has PIC_DLOG_NPAIRS;
+ *  - for candidate pair s: slot = s, the in-cell indices p and q (0-based,
+ *    ascending-pid order of the cell), result = 1 accepted / 0 rejected.
+ * kind also carries PIC_DLOG_TIE for an accept decision inside the tie bound
+ * of pic_stats.n_near_ties and PIC_DLOG_FLOOR for an N_pairs draw inside the
+ * bound of pic_stats.n_floor_ties: the decisions on which the precision
+ * form may differ from an FP64 evaluation of the same draws.
+ *  mode      PIC_DLOG_OFF (0, the default), PIC_DLOG_FLAGGED (only records
+ *            with PIC_DLOG_TIE or PIC_DLOG_FLOOR) or PIC_DLOG_ALL (every
+ *            N_pairs draw and candidate pair; slower kernels, for small
+ *            problems).
+ *  capacity  records kept, 1 .. 2^31-1; the buffer (32 capacity bytes)
+ *            comes from the context's allocator. Records beyond it are
+ *            counted but dropped.
+ * Setting the mode clears the log. Records are appended in no particular
+ * order (sort them by (c0, cell, outcome, slot)). PIC_EINVAL for a batch. */
+enum { PIC_DLOG_OFF = 0, PIC_DLOG_FLAGGED = 1, PIC_DLOG_ALL = 2 };
+enum { PIC_DLOG_TIE = 1, PIC_DLOG_FLOOR = 2, PIC_DLOG_NPAIRS = 4 };
+pic_status pic_set_decision_log(pic_ctx* ctx, int32_t mode, int64_t capacity);
+
+/* Copy the logged records into out [cap][8] (host or device; NULL with cap
+ * 0 to query), set *n_total to the number of records produced since the
+ * log was last cleared (it may exceed the capacity and cap: the first
+ * min(n_total, capacity, cap) records are written), and clear the log. */
+pic_status pic_get_decision_log(pic_ctx* ctx, int32_t* out, int64_t cap, int64_t* n_total);
+
 /* Pathwise gradient (an extension of the method; the paper has no adjoint):
  * runs nsteps FP64 steps from x^M(0) and the velocities v0 with a uniform
  * applied field E_app in the push, L = dt q/m (E_p + E_app - E^M_p), and
@@ -390,6 +441,20 @@ pic_status pic_batch_info(pic_ctx* ctx, int32_t* nrep, int64_t* n_particles, int
 void pic_destroy(pic_ctx* ctx);
 const char* pic_status_string(pic_status s);
 
+/* Issue rates of the current GPU, measured by short kernels on cuda_stream
+ * (NULL = legacy default stream; about 30 ms in all, synchronised), for
+ * the roofline of the compute-bound collision kernel (no counterpart in the
+ * paper). Every thread of a full grid (8 blocks of 256 threads per SM) runs
+ * independent chains of one instruction; out[i] is operations per second
+ * over the whole GPU at the clocks it ran at:
+ *  out[0] INT32 multiply-add (mad.lo.u32)   out[1] 3-input logic (lop3.b32)
+ *  out[2] FP32 FMA (fma.rn.f32)             out[3] FP64 FMA (fma.rn.f64)
+ *  out[4] Philox4x32-10 blocks (the collision kernel's generator, round
+ *         keys as kernel parameters).
+ * PIC_ENOMEM if its 16 KB scratch cannot be allocated, PIC_ECUDA on a CUDA
+ * error. */
+pic_status pic_measure_alu_peaks(void* cuda_stream, double out[5]);
+
 /* Poisson solve that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when
  * they solve (a memory budget fixed at start-up, or a host framework that
@@ -407,13 +472,15 @@ const char* pic_status_string(pic_status s);
  *  cuda_stream  stream to run on (NULL = legacy default stream); the call
  *           synchronises it before returning.
  *  iters, rel_res  optional host outputs: iterations and ||r|| / ||b||.
- * Its scratch (about 4.4 MB) is one fixed array inside the library, held on
- * every GPU that loads the library until the process exits. The first call
+ * Its scratch (569,792 doubles: 4.56 MB = 4.35 MiB) is one fixed array
+ * inside the library, held on every GPU that loads the library until the
+ * process exits. The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress)
  * with the device current; make that first call before any stream capture.
  * Every call shares the array: calls whose work overlaps on the GPU (two
- * streams, two host threads) race and give wrong results. Host or non-device
- * pointers return PIC_EINVAL. Calls no allocating routine. */
+ * streams, two host threads) race and give wrong results. Host pointers and
+ * device memory of another GPU return PIC_EINVAL. Calls no allocating
+ * routine. */
 pic_status pic_poisson_solve_noalloc(int32_t n, const double* b, double* phi, double* E, double tol,
                                      int32_t maxit, void* cuda_stream, int32_t* iters, double* rel_res);
 

@@ -27,12 +27,22 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
 
 
 def build(force: bool = False) -> Path:
-    """Compile the oracle with gcc into ``oracle/liboracle.so``."""
+    """Compile the oracle with gcc into ``oracle/liboracle.so``, with OpenMP
+    where the compiler has it (threads only over independent cells and
+    particles; see ``orc_set_threads``), else serial."""
     if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = _LIB.with_suffix(f".so.{os.getpid()}.tmp")
-        subprocess.run(["gcc", *CFLAGS, str(_SRC), "-o", str(tmp), "-lm"], check=True)
+        r = subprocess.run(["gcc", *CFLAGS, "-fopenmp", str(_SRC), "-o", str(tmp), "-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(["gcc", *CFLAGS, str(_SRC), "-o", str(tmp), "-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's independent loops (1 = serial, the
+    default); returns the count in effect (1 without OpenMP)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 class OrcCfg(ctypes.Structure):
@@ -140,6 +150,10 @@ def lib():
             "orc_ntc_cell": (ctypes.c_int64, [_CFG, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                               ctypes.c_int64, _D]),
             "orc_angle_count": (ctypes.c_int64, [ctypes.c_void_p]),
+            "orc_set_pair_log": (None, [ctypes.c_void_p, ctypes.c_int]),
+            "orc_set_threads": (ctypes.c_int, [ctypes.c_int]),
+            "orc_pair_log": (ctypes.c_int64, [ctypes.c_void_p, _I32, ctypes.c_int64]),
+            "orc_pair_log_peek": (ctypes.c_int64, [ctypes.c_void_p, _I32, ctypes.c_int64]),
             "orc_aniso_F": (ctypes.c_double, [ctypes.c_double]),
             "orc_objective": (None, [ctypes.c_void_p, _D]),
             "orc_aniso_u": (ctypes.c_double, [ctypes.c_double]),
@@ -163,6 +177,7 @@ def lib():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
+        L.orc_set_threads(1)
         _lib = L
     return _lib
 
@@ -315,6 +330,26 @@ class Oracle:
         out = np.zeros(3)
         self.L.orc_objective(self.h, _dp(out))
         return out
+
+    def set_pair_log(self, on: bool = True):
+        """Record the pair list of every collision call from now on (and
+        clear what was recorded), or stop recording."""
+        self.L.orc_set_pair_log(self.h, 1 if on else 0)
+
+    def pair_log(self) -> np.ndarray:
+        """The recorded pair list, ``[n, 8]`` int32 rows (c0, cell, outcome,
+        slot, p, q, result, kind) in draw order; clears the log. slot = -1
+        rows carry N_pairs in ``result`` (kind 4); candidate rows carry the
+        in-cell indices p, q and 1/0 for accepted/rejected, kind 1 marking a
+        near tie |U - sigma g/(sigma g)_max| < 1e-12."""
+        cap = 1 << 16
+        while True:
+            out = np.zeros((cap, 8), np.int32)
+            n = int(self.L.orc_pair_log_peek(self.h, _ip(out), cap))
+            if n <= cap:
+                self.L.orc_pair_log(self.h, None, 0)
+                return out[:n].copy()
+            cap = n
 
     def angles(self) -> np.ndarray:
         """(chi, eps) of every recorded collision, ``[N_coll, 2]``."""

@@ -11,7 +11,10 @@
  * loops, array-of-structures layouts ([particle][component]), FP64
  * throughout, no blocking, no fusion, no reordering beyond what the paper
  * states. It must be compiled with -ffp-contract=off so that x86 and Arm
- * builds give the same bits.
+ * builds give the same bits. Loops over independent cells or particles
+ * may run on several host threads (OpenMP, orc_set_threads; one thread by
+ * default): each iteration writes only its own cell's or particle's
+ * results, so the bits do not depend on the thread count.
  *
  * Workloads, on the periodic unit cube [0,1)^3 with n^3 cells of size
  * h = 1/n and node i at x = i h:
@@ -65,6 +68,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PI 3.14159265358979323846
 
@@ -540,6 +546,9 @@ typedef struct {
   double cg_res;
   double* ang;          /* [n_ang][2]: (chi, eps) of recorded collisions  */
   int64_t n_ang, cap_ang;
+  int32_t* plog;        /* [n_plog][8] pair-list records, when logging     */
+  int64_t n_plog, cap_plog;
+  int plog_on;
 } orc_state;
 
 static int64_t ncell(const orc_cfg* c) { return c->n * c->n * c->n; }
@@ -583,6 +592,7 @@ void orc_destroy(orc_state* s) {
   free(s->xi); free(s->x); free(s->v); free(s->rho); free(s->phi); free(s->E);
   free(s->cell); free(s->count); free(s->start); free(s->perm);
   free(s->ang);
+  free(s->plog);
   free(s);
 }
 
@@ -810,10 +820,39 @@ typedef struct {
   int64_t n, cap;
 } orc_angles;
 
+/* Pair list of Algorithm 1: one record of 8 int32 per N_pairs draw and
+ * per candidate pair, in the order the oracle draws them:
+ *   (c0, cell, outcome, slot, p, q, result, kind)
+ * slot = -1, p = q = -1, result = N_pairs, kind = 4 for the N_pairs draw;
+ * slot = s, the in-cell indices p, q, result = 1 accepted / 0 rejected,
+ * kind = 1 where |U - sigma g/(sigma g)_max| < 1e-12 (a near tie), else 0,
+ * for candidate s.                                                        */
+typedef struct {
+  int32_t* r;
+  int64_t n, cap;
+} orc_pairlog;
+
 typedef struct {
   int64_t n_cand, n_coll, n_gmax, n_tie;
   orc_angles* rec;  /* NULL: angles not recorded */
+  orc_pairlog* log; /* NULL: pair list not recorded */
 } orc_dsmc_stats;
+
+static void log_pair(orc_pairlog* lg, uint32_t c0, uint32_t cell, uint32_t o, int64_t slot, int64_t p,
+                     int64_t q, int64_t result, int32_t kind) {
+  if (!lg) return;
+  if (lg->n == lg->cap) {
+    int64_t cap = lg->cap ? 2 * lg->cap : 1024;
+    int32_t* r = (int32_t*)realloc(lg->r, (size_t)(8 * cap) * sizeof(int32_t));
+    if (!r) return;
+    lg->r = r;
+    lg->cap = cap;
+  }
+  int32_t* e = lg->r + 8 * lg->n;
+  e[0] = (int32_t)c0; e[1] = (int32_t)cell; e[2] = (int32_t)o; e[3] = (int32_t)slot;
+  e[4] = (int32_t)p; e[5] = (int32_t)q; e[6] = (int32_t)result; e[7] = kind;
+  lg->n++;
+}
 
 /* Manufactured anisotropy (Sec. 5.1): with u = sin^2(chi/2) the CDF of chi
  * is F(u) = (13 u + 96 u^2 - 160 u^3 + 80 u^4)/29, increasing on [0, 1]
@@ -869,7 +908,8 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
   uint32_t u[4];
   philox4(c0, cellk, 0xFFFFFFFFu, o << 8, cf->seed, u);
   double npairs_real = ((double)(c * (c - 1)) * Pmax) * 0.5 + orc_u52(u[0], u[1]);
-  int64_t npairs = (int64_t)floor(npairs_real);       /* Algorithm 1, line 4 */
+  int64_t npairs = (int64_t)floor(npairs_real);       /* Algorithm 1: NTC pair count */
+  log_pair(st->log, c0, cellk, o, -1, -1, -1, npairs, 4);
   for (int64_t sl = 0; sl < npairs; sl++) {
     uint32_t b0[4], b1[4];
     philox4(c0, cellk, (uint32_t)sl, (o << 8) | 0u, cf->seed, b0);
@@ -901,6 +941,7 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
     double U = orc_u32(b0[2]);
     if (g > cf->gmax) st->n_gmax++;
     if (fabs(U - ratio) < 1e-12) st->n_tie++;
+    log_pair(st->log, c0, cellk, o, sl, p, q, U < ratio, fabs(U - ratio) < 1e-12 ? 1 : 0);
     if (U < ratio) {
       if (cf->verify & ORC_ERROR2) {
         /* injected Error 2 (Sec. 5.4): swap with probability beta = 1/2,
@@ -945,13 +986,24 @@ void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
   const orc_cfg* cf = &s->c;
   int64_t nc = ncell(cf);
   orc_angles rec = {s->ang, s->n_ang, s->cap_ang};
-  orc_dsmc_stats st = {0, 0, 0, 0, (cf->verify & ORC_ANGLES) ? &rec : NULL};
+  orc_pairlog lg = {s->plog, s->n_plog, s->cap_plog};
+  orc_dsmc_stats st = {0, 0, 0, 0, (cf->verify & ORC_ANGLES) ? &rec : NULL, s->plog_on ? &lg : NULL};
   for (int64_t p = 0; p < 3 * cf->np; p++) dv[p] = 0.0;
   if (cf->K <= 0) return;
+  /* Cells are independent (each writes only its own particles' dv), so
+   * threads may take different cells; the recorded angles and the pair
+   * log keep the serial cell order, so they run on one thread. The counters
+   * are integers: their sum does not depend on the order.                 */
+  int serial = st.rec != NULL || st.log != NULL;
+  (void)serial;
+#pragma omp parallel if (!serial)
+  {
+  orc_dsmc_stats lst = {0, 0, 0, 0, st.rec, st.log};
   double* v0 = NULL;
   double* vloc = NULL;
   double* acc = NULL;
   int64_t cap = 0;
+#pragma omp for schedule(dynamic, 16)
   for (int64_t k = 0; k < nc; k++) {
     int64_t c = s->count[k];
     if (c < 2) continue;
@@ -970,7 +1022,7 @@ void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
     }
     for (int64_t o = 0; o < cf->K; o++) {
       memcpy(vloc, v0, (size_t)(3 * c) * sizeof(double));
-      ntc_one_outcome(cf, c0, (uint32_t)k, (uint32_t)o, c, vloc, &st);
+      ntc_one_outcome(cf, c0, (uint32_t)k, (uint32_t)o, c, vloc, &lst);
       for (int64_t j = 0; j < 3 * c; j++) acc[j] += vloc[j] - v0[j];
     }
     for (int64_t j = 0; j < c; j++) {
@@ -979,6 +1031,17 @@ void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
     }
   }
   free(v0); free(vloc); free(acc);
+#pragma omp critical
+  {
+    st.n_cand += lst.n_cand;
+    st.n_coll += lst.n_coll;
+    st.n_gmax += lst.n_gmax;
+    st.n_tie += lst.n_tie;
+  }
+  }
+  s->plog = lg.r;
+  s->n_plog = lg.n;
+  s->cap_plog = lg.cap;
   s->ang = rec.a;
   s->n_ang = rec.n;
   s->cap_ang = rec.cap;
@@ -992,6 +1055,7 @@ void orc_dsmc_avg(orc_state* s, const double* v, uint32_t c0, double* dv) {
  * the call's time t.                                                     */
 void orc_source_all(orc_state* s, const double* v, double t, double* dvM) {
   const orc_cfg* cf = &s->c;
+#pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < cf->np; p++) {
     if (cf->K <= 0) {
       dvM[3 * p] = dvM[3 * p + 1] = dvM[3 * p + 2] = 0.0;
@@ -1012,6 +1076,7 @@ void orc_sample(orc_state* s, double t0) {
   s->t0 = t0;
   s->step = 0;
   s->n_ang = 0;
+#pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < cf->np; p++) {
     for (int d = 0; d < 3; d++) {
       s->x[3 * p + d] = orc_xM_d(cf, d, s->xi[6 * p + d], t0);
@@ -1043,6 +1108,7 @@ double orc_wrap(double x) {
 static void lorentz_term(orc_state* s, double t, double* out) {
   const orc_cfg* cf = &s->c;
   double qm = cf->couple_qm_zero ? 0.0 : cf->qm;
+#pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < cf->np; p++) {
     double Ep[3], EMp[3];
     orc_gather(cf, s->E, s->x + 3 * p, Ep);
@@ -1067,6 +1133,7 @@ void orc_step(orc_state* s, int64_t nsteps) {
     lorentz_term(s, tn, L);
     orc_dsmc_avg(s, s->v, (uint32_t)(2 * n + 0), dv);
     orc_source_all(s, s->v, tn, dvM);
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < np; p++)
       for (int d = 0; d < 3; d++) {
         int64_t j = 3 * p + d;
@@ -1077,6 +1144,7 @@ void orc_step(orc_state* s, int64_t nsteps) {
     /* x^{n+1} = x^n + dt (v + xdot^M - v^M)^{n+1/2}, wrapped; in the
      * isolated-collision mode dt xdot^M(t_{n+1/2}) becomes the exact
      * increment x^M(t_{n+1}) - x^M(t_n) (Sec. 5.4)                       */
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < np; p++) {
       for (int d = 0; d < 3; d++) {
         double vm = orc_vM_t(cf, d, s->xi[6 * p + 3 + d], th);
@@ -1097,6 +1165,7 @@ void orc_step(orc_state* s, int64_t nsteps) {
     lorentz_term(s, tn1, L);
     orc_dsmc_avg(s, vh, (uint32_t)(2 * n + 1), dv);
     orc_source_all(s, vh, th, dvM);
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < np; p++)
       for (int d = 0; d < 3; d++) {
         int64_t j = 3 * p + d;
@@ -1210,9 +1279,46 @@ void orc_set_phi(orc_state* s, const double* phi) {
  * in place, returns the number of collisions.                            */
 int64_t orc_ntc_cell(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint32_t o, int64_t c,
                      double* v) {
-  orc_dsmc_stats st = {0, 0, 0, 0, NULL};
+  orc_dsmc_stats st = {0, 0, 0, 0, NULL, NULL};
   ntc_one_outcome(cf, c0, cellk, o, c, v, &st);
   return st.n_coll;
+}
+
+/* Host threads for the loops over independent cells and particles (1 =
+ * serial; without OpenMP the oracle is always serial). Every other loop
+ * (the sort, the deposit's scatter, the mesh sums and CG) runs serially,
+ * and so does the collision loop while angles or the pair list are
+ * recorded: results are the same bits for any thread count. Returns the
+ * thread count in effect.                                                 */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
+/* Pair-list logging of the collision calls (orc_pairlog records): on != 0
+ * starts (and clears) the log, 0 stops it. orc_pair_log copies up to cap
+ * records into out[cap][8], returns how many the log holds, and clears it;
+ * orc_pair_log_peek does the same without clearing.                       */
+void orc_set_pair_log(orc_state* s, int on) {
+  s->plog_on = on != 0;
+  s->n_plog = 0;
+}
+
+int64_t orc_pair_log_peek(const orc_state* s, int32_t* out, int64_t cap) {
+  int64_t n = s->n_plog;
+  if (out && cap > 0 && n > 0) memcpy(out, s->plog, (size_t)(8 * (n < cap ? n : cap)) * sizeof(int32_t));
+  return n;
+}
+
+int64_t orc_pair_log(orc_state* s, int32_t* out, int64_t cap) {
+  int64_t n = orc_pair_log_peek(s, out, cap);
+  s->n_plog = 0;
+  return n;
 }
 
 /* Recorded (chi, eps) pairs of every collision since sampling or the last

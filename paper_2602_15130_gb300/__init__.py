@@ -218,6 +218,32 @@ class Pic:
     def reset_stats(self):
         check(self.L.pic_reset_stats(self.ctx), "pic_reset_stats")
 
+    def step_history(self) -> np.ndarray:
+        """[steps, 4] int64 per step since the last reset/sampling: CG
+        iterations, candidate pairs, collisions, candidates with g > g_max."""
+        out = np.zeros((4096, 4), np.int64)
+        n = ctypes.c_int64()
+        check(self.L.pic_get_step_history(self.ctx, out.ctypes.data, 4096, ctypes.byref(n)), "pic_get_step_history")
+        return out[:n.value].copy()
+
+    def set_decision_log(self, mode: int, capacity: int = 1 << 20):
+        """Log the collision calls' decisions (pic_set_decision_log):
+        mode 0 off, 1 flagged FP32 decisions only, 2 every N_pairs draw and
+        candidate pair."""
+        check(self.L.pic_set_decision_log(self.ctx, int(mode), int(capacity)), "pic_set_decision_log")
+        self._dlog_cap = int(capacity)
+
+    def decision_log(self) -> np.ndarray:
+        """The logged records [n, 8] int32 (c0, cell, outcome, slot, p, q,
+        result, kind) and clear the log; raises if records were dropped."""
+        cap = getattr(self, "_dlog_cap", 0)
+        out = np.zeros((max(cap, 1), 8), np.int32)
+        n = ctypes.c_int64()
+        check(self.L.pic_get_decision_log(self.ctx, out.ctypes.data, cap, ctypes.byref(n)), "pic_get_decision_log")
+        if n.value > cap:
+            raise RuntimeError(f"decision log overflow: {n.value} records, capacity {cap}")
+        return out[:n.value].copy()
+
     def adjoint_gradient(self, nsteps: int, every: int = 20, E_app=(0.1, 0.1, 0.1), v0=None, grad: bool = True):
         """Objective J = J_field + J_vel at t_N and, with ``grad``, its
         pathwise gradient (dJ/dE_app [3], dJ/dv0 [N_p, 3]) by the library's
@@ -299,6 +325,17 @@ class Batch(Pic):
         it = (ctypes.c_int32 * self.nrep)()
         check(self.L.pic_batch_info(self.ctx, None, None, it), "pic_batch_info")
         return list(it)
+
+
+def measure_alu_peaks(stream=None) -> dict:
+    """Measured issue rates of the current GPU (pic_measure_alu_peaks), per
+    second: INT32 multiply-add, 3-input logic, FP32 FMA, FP64 FMA and
+    Philox4x32-10 blocks."""
+    L = load()
+    out = (ctypes.c_double * 5)()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    check(L.pic_measure_alu_peaks(ctypes.c_void_p(handle), out), "pic_measure_alu_peaks")
+    return dict(zip(["imad", "lop3", "ffma", "dfma", "philox_blocks"], list(out)))
 
 
 def derived(params: dict) -> dict:

@@ -15,7 +15,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build_objs"
 LIB = PKG / "libpic_gb300.so"
-SOURCES = ["pic_api.cu", "k_particles.cu", "k_sort.cu", "k_field.cu", "k_mixed.cu", "k_batch.cu", "k_angles.cu", "k_adjoint.cu"]
+SOURCES = ["pic_api.cu", "k_particles.cu", "k_sort.cu", "k_field.cu", "k_mixed.cu", "k_batch.cu", "k_angles.cu",
+           "k_adjoint.cu", "k_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = [
     "-O3", "-std=c++17", "-lineinfo", *ARCH,

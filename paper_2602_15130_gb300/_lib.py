@@ -84,6 +84,7 @@ class PicStats(ctypes.Structure):
         ("graph_replays", ctypes.c_int64),
         ("tuned_kick_block", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("n_floor_ties", ctypes.c_int64),
     ]
 
 
@@ -141,6 +142,10 @@ SIGNATURES = {
     "pic_batch_info": (_S, [_V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                             ctypes.POINTER(ctypes.c_int32)]),
     "pic_inject_barrier_stall": (_S, [_V]),
+    "pic_get_step_history": (_S, [_V, _V, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "pic_set_decision_log": (_S, [_V, ctypes.c_int32, ctypes.c_int64]),
+    "pic_get_decision_log": (_S, [_V, _V, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "pic_measure_alu_peaks": (_S, [_V, _D]),
     "pic_poisson_solve_noalloc": (_S, [ctypes.c_int32, _V, _V, _V, ctypes.c_double, ctypes.c_int32, _V,
                                       ctypes.POINTER(ctypes.c_int32), _D]),
 }

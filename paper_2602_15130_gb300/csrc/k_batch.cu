@@ -310,7 +310,7 @@ __device__ __forceinline__ void load_vel_b(int p, const uint32_t* bm, const floa
 }
 
 struct CountsB {
-  unsigned long long cand, coll, gmax, tie;
+  unsigned long long cand, coll, gmax, tie, ftie;
 };
 
 // Algorithm 1 for one (cell, outcome), as in the single-domain FP32 kernel.
@@ -318,7 +318,10 @@ __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint
                               const float* v1, const float* v2, uint32_t* bm, float* ov, CountsB& cnt) {
   const U4 u = philox<true>(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
   const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
-  const int npairs = (int)floorf(base + unif24(u.x));
+  const float S = base + unif24(u.x);
+  const int npairs = (int)floorf(S);
+  // flagged FP32 decisions: the bounds of the single-domain kernel
+  if (fabsf(S - rintf(S)) <= fmaf(base + S, 0x1p-22f, 0x1p-24f)) ++cnt.ftie;
   for (int s = 0; s < npairs; ++s) {
     const U4 b0 = philox<true>(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
     const U4 b1 = philox<true>(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
@@ -348,7 +351,8 @@ __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint
     const float ug2 = ug * ug;
     ++cnt.cand;
     if (g2 > P.gmax2) ++cnt.gmax;
-    if (fabsf(ug2 - g2) < 2e-6f * g2) ++cnt.tie;
+    const float dg = (P.gmax + ug) * 0x1p-19f;
+    if (fabsf(ug2 - g2) <= dg * fmaf(2.f, ug, dg)) ++cnt.tie;
     if (ug2 < g2) {
       float se, ce;
       sincospif(2.f * unif24(b0.w), &se, &ce);
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) kb_dsmc(BDsmcArgs a) {
   float* ov = wov + (size_t)lane * a.max_ppc * 3;
   for (int i = 0; i < a.bm_words; ++i) bm[i] = 0u;
   __syncwarp();
-  CountsB cnt = {0, 0, 0, 0};
+  CountsB cnt = {0, 0, 0, 0, 0};
   const uint32_t c0 = (uint32_t)(2 * (*a.step) + a.phase);
   for (int64_t it = gwarp; it < a.n_items; it += nwarps) {
     const int2 item = a.items[it];
@@ -461,12 +465,14 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) kb_dsmc(BDsmcArgs a) {
     cnt.coll += __shfl_down_sync(0xffffffffu, cnt.coll, off);
     cnt.gmax += __shfl_down_sync(0xffffffffu, cnt.gmax, off);
     cnt.tie += __shfl_down_sync(0xffffffffu, cnt.tie, off);
+    cnt.ftie += __shfl_down_sync(0xffffffffu, cnt.ftie, off);
   }
   if (lane == 0) {
     if (cnt.cand) atomicAdd(a.counters + 0, cnt.cand);
     if (cnt.coll) atomicAdd(a.counters + 1, cnt.coll);
     if (cnt.gmax) atomicAdd(a.counters + 2, cnt.gmax);
     if (cnt.tie) atomicAdd(a.counters + 3, cnt.tie);
+    if (cnt.ftie) atomicAdd(a.counters + 4, cnt.ftie);
   }
 }
 

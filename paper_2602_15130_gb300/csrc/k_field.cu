@@ -151,6 +151,7 @@ struct CgArgs {
   double tol;
   int maxit;
   double *E0, *E1, *E2;
+  long long* hist = nullptr;  // per-step history row: [0] iterations
 };
 
 // Grid barrier for a cooperative grid, bounded in time.
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CgArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[0] = it;
     a.info[1] = status;
+    if (a.hist) a.hist[0] = it;
     a.res[0] = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
     if (status) atomicOr(a.flags, 2);
     atomicMax(a.flags + 1, it);
@@ -426,6 +428,7 @@ cudaError_t launch_cg_on(pic_ctx* c, double* b, double* x, const double* rhs_par
   a.E1 = E1;
   a.E2 = E2;
   a.skip_block = c->stall_next_cg ? c->cg_grid - 1 : -1;
+  a.hist = c->hist_row;
   c->stall_next_cg = false;
   cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
   if (e != cudaSuccess) return e;
@@ -529,6 +532,9 @@ extern "C" pic_status pic_poisson_solve_noalloc(int32_t n, const double* b, doub
       return PIC_EINVAL;
     }
     if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return PIC_EINVAL;
+    // device memory of another GPU would be read across the link, or fault
+    // without peer access: only the current device's memory is accepted
+    if (at.type == cudaMemoryTypeDevice && at.device != dev) return PIC_EINVAL;
   }
   // one-time set-up per device: the scratch array's device address
   double* base = nullptr;

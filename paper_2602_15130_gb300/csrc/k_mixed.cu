@@ -409,10 +409,12 @@ struct Dsmc32Args {
   unsigned long long* counters;
   int* flags;
   float vh[3];             // PIC_DIST_PAPER: f_v scales at the call's time
+  DLog lg;                 // decision log (mode 0: off)
+  long long* hist;         // per-step history row: [1] candidates, [2] collisions, [3] g > g_max
 };
 
 struct Counts32 {
-  unsigned long long cand, coll, gmax, tie;
+  unsigned long long cand, coll, gmax, tie, ftie;
 };
 
 // a particle's working velocity: the lane's overlay copy where this outcome
@@ -427,12 +429,33 @@ __device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const floa
   o[0] = *s0; o[1] = *s1; o[2] = *s2;
 }
 
+// Decisions the FP32 arithmetic may take differently from an FP64
+// evaluation of the same draws are counted and, with a decision log, logged:
+//  - N_pairs = floor(S), S = base + U: base carries 2^-23 relative error
+//    (P_coll,max rounded to FP32, one product), the 24-bit uniform is within
+//    2^-25 of the 52-bit one, and the sum rounds by 2^-24 S; S within twice
+//    that bound of an integer is flagged;
+//  - accept: the 24-bit uniform times g_max is within 2^-25 g_max of the
+//    32-bit one's, and g carries the rounding of the FP32 velocities (a few
+//    ulp per collision they took part in); |U g_max - g| <= 2^-19 (g_max +
+//    U g_max) is flagged (tested on the squares: |(U g_max)^2 - g^2| <=
+//    dg (2 U g_max + dg) holds whenever |U g_max - g| <= dg). For the
+//    odd-power cross section the same margin is 2^-17 of the compared
+//    values.
+// Every decision is logged only in the kVerify instantiation.
 template <bool kVerify>
 __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
-                              const float* v1, const float* v2, uint32_t* bm, float* ov, Counts32& cnt) {
+                              const float* v1, const float* v2, uint32_t* bm, float* ov, Counts32& cnt,
+                              const DLog& lg) {
   const U4 u = philox_rk<true>(c0, cell, 0xFFFFFFFFu, o << 8, P.rk);
   const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
-  const int npairs = (int)floorf(base + unif24(u.x));
+  const float S = base + unif24(u.x);
+  const int npairs = (int)floorf(S);
+  const bool ftie = fabsf(S - rintf(S)) <= fmaf(base + S, 0x1p-22f, 0x1p-24f);
+  if (ftie) ++cnt.ftie;
+  const bool log_all = kVerify && lg.mode == PIC_DLOG_ALL;
+  if (log_all || (ftie && lg.mode != PIC_DLOG_OFF))
+    dlog_put(lg, c0, cell, o, -1, -1, -1, npairs, PIC_DLOG_NPAIRS | (ftie ? PIC_DLOG_FLOOR : 0));
   const float gmax = P.gmax;
   for (int s = 0; s < npairs; ++s) {
     // both blocks of the candidate up front: two independent Philox chains
@@ -462,18 +485,24 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
     const float g2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     // accept if U < sigma g / (sigma g)_max: hard spheres g / g_max, i.e.
     // (U g_max)^2 < g^2; odd-power sigma U (sigma g)_max < sum_k sigma_k g^2k
-    float lhs, rhs;
+    float lhs, rhs, tol;
     if (P.n_sigma == 0) {
       const float ug = unif24(b0.z) * gmax;
       lhs = ug * ug;
       rhs = g2;
+      const float dg = (gmax + ug) * 0x1p-19f;
+      tol = dg * fmaf(2.f, ug, dg);
     } else {
       lhs = unif24(b0.z) * P.sgmax;
       rhs = fmaf(fmaf(P.sigma_n[2], g2, P.sigma_n[1]), g2, P.sigma_n[0]);
+      tol = (P.sgmax + fabsf(rhs)) * 0x1p-17f;
     }
     ++cnt.cand;
     if (g2 > P.gmax2) ++cnt.gmax;
-    if (fabsf(lhs - rhs) < 2e-6f * fabsf(rhs)) ++cnt.tie;
+    const bool tie = fabsf(lhs - rhs) <= tol;
+    if (tie) ++cnt.tie;
+    if (log_all || (tie && lg.mode != PIC_DLOG_OFF))
+      dlog_put(lg, c0, cell, o, s, (int)p, (int)q, lhs < rhs ? 1 : 0, tie ? PIC_DLOG_TIE : 0);
     if (lhs < rhs) {
       const float g = sqrtf(g2);
       if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
@@ -528,7 +557,7 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
   float* ov = wov + (size_t)lane * a.max_ppc * 3;
   for (int i = 0; i < a.bm_words; ++i) bm[i] = 0u;
   __syncwarp();
-  Counts32 cnt = {0, 0, 0, 0};
+  Counts32 cnt = {0, 0, 0, 0, 0};
   const bool separate = a.m0 != nullptr;
   const float invK = 1.f / (float)P.K;
   const float mu0 = P.vmean[0], mu1 = P.vmean[1], mu2 = P.vmean[2];
@@ -553,7 +582,7 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
       }
       if (run)
         ntc_outcome_f<kVerify>(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s,
-                               bm, ov, cnt);
+                               bm, ov, cnt, a.lg);
       __syncwarp();
       // per 32-particle word: one transpose of the lanes' bitmap words across
       // the warp serves every cell of the group, since lane l holds outcome
@@ -620,12 +649,19 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
     cnt.coll += __shfl_down_sync(0xffffffffu, cnt.coll, off);
     cnt.gmax += __shfl_down_sync(0xffffffffu, cnt.gmax, off);
     cnt.tie += __shfl_down_sync(0xffffffffu, cnt.tie, off);
+    cnt.ftie += __shfl_down_sync(0xffffffffu, cnt.ftie, off);
   }
   if (lane == 0) {
     if (cnt.cand) atomicAdd(a.counters + 0, cnt.cand);
     if (cnt.coll) atomicAdd(a.counters + 1, cnt.coll);
     if (cnt.gmax) atomicAdd(a.counters + 2, cnt.gmax);
     if (cnt.tie) atomicAdd(a.counters + 3, cnt.tie);
+    if (cnt.ftie) atomicAdd(a.counters + 4, cnt.ftie);
+    if (a.hist) {
+      if (cnt.cand) atomicAdd((unsigned long long*)a.hist + 1, cnt.cand);
+      if (cnt.coll) atomicAdd((unsigned long long*)a.hist + 2, cnt.coll);
+      if (cnt.gmax) atomicAdd((unsigned long long*)a.hist + 3, cnt.gmax);
+    }
   }
 }
 
@@ -763,6 +799,7 @@ struct Cg32Args {
   int maxit;
   float4* E4;  // (Ex, Ey, Ez, 0) per node
   int skip_block = -1;  // failure injection: this block leaves before its first barrier
+  long long* hist = nullptr;  // per-step history row: [0] iterations
 };
 
 constexpr long long kBarrierCycles = 4000000000LL;
@@ -1039,6 +1076,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[0] = it;
     a.info[1] = status;
+    if (a.hist) a.hist[0] = it;
     a.res[0] = bb > 0.0 ? sqrt(gamma) / sqrt(bb) : 0.0;
     if (status) atomicOr(a.flags, 2);
     atomicMax(a.flags + 1, it);
@@ -1283,8 +1321,10 @@ cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate, double t_src) 
   a.ngroups = c->dsmc_groups;
   a.counters = c->counters;
   a.flags = c->flags;
+  a.lg = DLog{c->dlog, c->dlog_n, (long long)c->dlog_cap, c->dlog ? c->dlog_mode : 0};
+  a.hist = c->hist_row;
   prof_begin(c);
-  if (c->P.verify)
+  if (c->P.verify || a.lg.mode == PIC_DLOG_ALL)
     k_dsmc32<true><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
   else
     k_dsmc32<false><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
@@ -1350,6 +1390,7 @@ cudaError_t launch_cg32(pic_ctx* c) {
   a.maxit = c->cfg.cg_maxit;
   a.E4 = c->Ef4;
   a.skip_block = c->stall_next_cg ? c->cg_grid - 1 : -1;
+  a.hist = c->hist_row;
   c->stall_next_cg = false;
   cudaError_t e = cudaMemsetAsync(c->cg_bar, 0, 2 * sizeof(unsigned int), c->stream);
   if (e != cudaSuccess) return e;

@@ -146,6 +146,8 @@ struct DsmcArgs {
   unsigned long long* counters;
   int* flags;
   double vh[3];             // PIC_DIST_PAPER: f_v scales at the call's time
+  DLog lg;                  // decision log (mode 0: off)
+  long long* hist;          // per-step history row: [1] candidates, [2] collisions, [3] g > g_max
 };
 
 constexpr int kDsmcThreads = 128;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
       {
         NoRecord none;
         ntc_outcome<kVerify>(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s,
-                             bm, ov, cnt, none);
+                             bm, ov, cnt, none, a.lg);
       }
       __syncwarp();
       // sum this chunk's changes per particle in ascending outcome order
@@ -255,6 +257,11 @@ __global__ void __launch_bounds__(kDsmcThreads) k_dsmc(DsmcArgs a) {
     if (cnt.coll) atomicAdd(a.counters + 1, cnt.coll);
     if (cnt.gmax) atomicAdd(a.counters + 2, cnt.gmax);
     if (cnt.tie) atomicAdd(a.counters + 3, cnt.tie);
+    if (a.hist) {
+      if (cnt.cand) atomicAdd((unsigned long long*)a.hist + 1, cnt.cand);
+      if (cnt.coll) atomicAdd((unsigned long long*)a.hist + 2, cnt.coll);
+      if (cnt.gmax) atomicAdd((unsigned long long*)a.hist + 3, cnt.gmax);
+    }
   }
 }
 
@@ -570,8 +577,10 @@ cudaError_t launch_dsmc(pic_ctx* c, uint32_t c0, bool separate, double t_src) {
   a.ngroups = c->dsmc_groups;
   a.counters = c->counters;
   a.flags = c->flags;
+  a.lg = DLog{c->dlog, c->dlog_n, (long long)c->dlog_cap, c->dlog ? c->dlog_mode : 0};
+  a.hist = c->hist_row;
   prof_begin(c);
-  if (c->P.verify)
+  if (c->P.verify || a.lg.mode == PIC_DLOG_ALL)
     k_dsmc<true><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
   else
     k_dsmc<false><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);

@@ -31,13 +31,17 @@ __device__ __forceinline__ void load_vel(int p, const uint32_t* bm, const double
 
 // kVerify: the verification switches of Sec. 5.4 (injected Errors 1 and 2,
 // manufactured anisotropy, angle recording) are compiled in.
+// lg: decision log (mode 0 off); every decision is logged only in the
+// kVerify instantiation, flagged near ties in both.
 template <bool kVerify, class Rec>
 __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_t o, int c,
                             const double* v0, const double* v1, const double* v2, uint32_t* bm,
-                            double* ov, LaneCounts& cnt, Rec& rec) {
+                            double* ov, LaneCounts& cnt, Rec& rec, const DLog lg = DLog{nullptr, nullptr, 0, 0}) {
   const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
   const double base = __dmul_rn(__dmul_rn((double)((long long)c * (long long)(c - 1)), P.pmax), 0.5);
   const long long npairs = (long long)floor(__dadd_rn(base, unif52(u.x, u.y)));
+  const bool log_all = kVerify && lg.mode == PIC_DLOG_ALL;
+  if (log_all) dlog_put(lg, c0, cell, o, -1, -1, -1, (int)npairs, PIC_DLOG_NPAIRS);
   for (long long s = 0; s < npairs; ++s) {
     const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
@@ -73,7 +77,10 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
     const double U = unif32(b0.z);
     ++cnt.cand;
     if (g > P.gmax) ++cnt.gmax;
-    if (fabs(U - ratio) < 1e-12) ++cnt.tie;
+    const bool tie = fabs(U - ratio) < 1e-12;
+    if (tie) ++cnt.tie;
+    if (log_all || (tie && lg.mode != PIC_DLOG_OFF))
+      dlog_put(lg, c0, cell, o, (int)s, (int)p, (int)q, U < ratio ? 1 : 0, tie ? PIC_DLOG_TIE : 0);
     if (U < ratio) {
       if (!have_b1) b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
       if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {

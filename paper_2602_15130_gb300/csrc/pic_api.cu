@@ -347,6 +347,7 @@ void for_each_buffer(pic_ctx* c, F f) {
   f((void**)&c->cg_info, 64);
   f((void**)&c->cg_res, 64);
   f((void**)&c->counters, 8 * 8);
+  f((void**)&c->step_hist, (size_t)kHistSteps * 4 * 8);
   f((void**)&c->flags, 64);
   f((void**)&c->err_part, (size_t)c->err_blocks * 14 * 8);
   f((void**)&c->err_out, 14 * 8);
@@ -665,6 +666,8 @@ pic_status pic_derived(const pic_config* cfg, double out[5]) {
 void pic_destroy(pic_ctx* c) {
   if (!c) return;
   adjoint_free(c);
+  dev_free(c, c->dlog);
+  dev_free(c, c->dlog_n);
   for_each_buffer(c, [&](void** p, size_t) {
     dev_free(c, *p);
     *p = nullptr;
@@ -809,11 +812,23 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   return PIC_OK;
 }
 
+}  // extern "C"
+namespace {
+// a new state starts a new per-step history
+cudaError_t restart_history(pic_ctx* c) {
+  c->hist_base = c->step;
+  return cudaMemsetAsync(c->step_hist, 0, (size_t)kHistSteps * 4 * 8, c->stream);
+}
+pic_status step_loop(pic_ctx* c, int32_t nsteps);
+}  // namespace
+extern "C" {
+
 pic_status pic_sample_mms(pic_ctx* c, double t0) {
   if (!c || !isfinite(t0)) return PIC_EINVAL;
   c->t0 = t0;
   c->step = 0;
   c->cur = 0;
+  CK(restart_history(c));
   if (c->nrep > 0) {
     c->lor_valid = false;
     CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
@@ -861,6 +876,7 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
   }
   c->t0 = t0;
   c->step = step;
+  CK(restart_history(c));
   if (c->mixed) {
     // v^M is a per-particle constant (tau for the paper's f_v): a context that
     // already holds a state keeps its values (into pid order through the
@@ -880,12 +896,22 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
 }
 
 pic_status pic_step(pic_ctx* c, int32_t nsteps) {
+  const pic_status s = step_loop(c, nsteps);
+  if (c) c->hist_row = nullptr;  // also on an early return: no later launch writes the history
+  return s;
+}
+
+}  // extern "C"
+namespace {
+pic_status step_loop(pic_ctx* c, int32_t nsteps) {
   if (!c || nsteps < 0) return PIC_EINVAL;
   if (!c->sampled) return PIC_ESTATE;
   const bool coll = c->cfg.K > 0;
   for (int32_t it = 0; it < nsteps; ++it) {
     const int64_t n = c->step;
     const double tn = time_at(c, (double)n), th = time_at(c, (double)n + 0.5), tn1 = time_at(c, (double)(n + 1));
+    const int64_t row = n - c->hist_base;
+    c->hist_row = (c->nrep == 0 && row >= 0 && row < kHistSteps) ? c->step_hist + 4 * row : nullptr;
     if (c->nrep > 0) {
       pic_status s = batch_step(c, n, coll);
       if (s != PIC_OK) return s;
@@ -904,8 +930,11 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     }
     c->step = n + 1;
   }
+  c->hist_row = nullptr;
   return nsteps > 0 ? check_pending(c) : PIC_OK;
 }
+}  // namespace
+extern "C" {
 
 pic_status pic_collide_avg(pic_ctx* c, int32_t phase, double* dv, double* dvM) {
   if (!c || !dv || !dvM || (phase != 0 && phase != 1)) return PIC_EINVAL;
@@ -1063,7 +1092,7 @@ pic_status pic_get_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* count, int32_
 
 pic_status pic_get_stats(pic_ctx* c, pic_stats* out) {
   if (!c || !out) return PIC_EINVAL;
-  unsigned long long h[4] = {0, 0, 0, 0};
+  unsigned long long h[5] = {0, 0, 0, 0, 0};
   CK(cudaMemcpyAsync(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   pic_status s = c->sampled ? check_pending(c) : PIC_OK;
@@ -1072,6 +1101,7 @@ pic_status pic_get_stats(pic_ctx* c, pic_stats* out) {
   out->n_coll = (int64_t)h[1];
   out->n_gmax_exceed = (int64_t)h[2];
   out->n_near_ties = (int64_t)h[3];
+  out->n_floor_ties = (int64_t)h[4];
   out->kernel_launches = c->launches;
   out->step = c->step;
   out->t = time_at(c, (double)c->step);
@@ -1086,11 +1116,78 @@ pic_status pic_get_stats(pic_ctx* c, pic_stats* out) {
 pic_status pic_reset_stats(pic_ctx* c) {
   if (!c) return PIC_EINVAL;
   CK(cudaMemsetAsync(c->counters, 0, 64, c->stream));
+  CK(cudaMemsetAsync(c->step_hist, 0, (size_t)kHistSteps * 4 * 8, c->stream));
+  c->hist_base = c->step;
   CK(cudaMemsetAsync(c->flags, 0, 64, c->stream));
   if (c->ang_hist) CK(cudaMemsetAsync(c->ang_hist, 0, (size_t)2 * PIC_ANGLE_BINS * 8, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->launches = 0;
   c->cg_iters_max = 0;
+  return PIC_OK;
+}
+
+pic_status pic_get_step_history(pic_ctx* c, int64_t* out, int64_t cap, int64_t* n) {
+  if (!c || !n || cap < 0 || (cap > 0 && !out)) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;
+  int64_t k = c->step - c->hist_base;
+  if (k < 0) k = 0;
+  if (k > kHistSteps) k = kHistSteps;
+  if (k > cap) k = cap;
+  if (k > 0) {
+    CK(cudaMemcpyAsync(out, c->step_hist, (size_t)k * 32, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  *n = k;
+  return PIC_OK;
+}
+
+pic_status pic_set_decision_log(pic_ctx* c, int32_t mode, int64_t capacity) {
+  if (!c || c->nrep > 0) return PIC_EINVAL;
+  if (mode != PIC_DLOG_OFF && mode != PIC_DLOG_FLAGGED && mode != PIC_DLOG_ALL) return PIC_EINVAL;
+  if (mode != PIC_DLOG_OFF && (capacity < 1 || capacity > INT32_MAX)) return PIC_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));  // no kernel of an earlier call still writes the old buffer
+  if (mode == PIC_DLOG_OFF || capacity != c->dlog_cap) {
+    dev_free(c, c->dlog);
+    dev_free(c, c->dlog_n);
+    c->dlog = nullptr;
+    c->dlog_n = nullptr;
+    c->dlog_cap = 0;
+  }
+  c->dlog_mode = mode;
+  if (mode == PIC_DLOG_OFF) return PIC_OK;
+  if (!c->dlog) {
+    c->dlog = (int32_t*)dev_alloc(c, (size_t)capacity * 32);
+    c->dlog_n = (unsigned long long*)dev_alloc(c, 64);
+    if (!c->dlog || !c->dlog_n) {
+      dev_free(c, c->dlog);
+      dev_free(c, c->dlog_n);
+      c->dlog = nullptr;
+      c->dlog_n = nullptr;
+      c->dlog_mode = PIC_DLOG_OFF;
+      return PIC_ENOMEM;
+    }
+    c->dlog_cap = capacity;
+  }
+  CK(cudaMemsetAsync(c->dlog_n, 0, 8, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_get_decision_log(pic_ctx* c, int32_t* out, int64_t cap, int64_t* n_total) {
+  if (!c || !n_total || cap < 0 || (cap > 0 && !out)) return PIC_EINVAL;
+  if (c->nrep > 0) return PIC_EINVAL;
+  *n_total = 0;
+  if (!c->dlog) return PIC_OK;
+  unsigned long long n = 0;
+  CK(cudaMemcpyAsync(&n, c->dlog_n, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int64_t k = (int64_t)n;
+  if (k > c->dlog_cap) k = c->dlog_cap;
+  if (k > cap) k = cap;
+  if (k > 0) CK(cudaMemcpyAsync(out, c->dlog, (size_t)k * 32, cudaMemcpyDefault, c->stream));
+  CK(cudaMemsetAsync(c->dlog_n, 0, 8, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *n_total = (int64_t)n;
   return PIC_OK;
 }
 

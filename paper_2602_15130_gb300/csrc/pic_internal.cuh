@@ -18,6 +18,8 @@ constexpr int kSeriesTerms = 10;
 // intervals of cubic Hermite knots (R, dR/da), stored after the two G^{-1}
 // tables of the precision form
 constexpr int kRTabM = 512;
+// steps of the per-step history (pic_get_step_history)
+constexpr int kHistSteps = 4096;
 constexpr float kRTabAmax = 8.f;
 
 // ---------------------------------------------------------------------------
@@ -79,6 +81,25 @@ struct ParamsF {
   int dist, n_sigma;               // PIC_DIST_*, odd-power cross section terms (0: hard sphere)
   float sigma_n[3], sgmax, src_pref_n, dt;
 };
+
+// Decision log of the collision kernels (pic_set_decision_log): records of
+// 8 int32 (c0, cell, outcome, slot, p, q, result, kind). mode 0 is off.
+struct DLog {
+  int32_t* buf;
+  unsigned long long* n;
+  long long cap;
+  int mode;
+};
+
+__device__ __forceinline__ void dlog_put(const DLog& L, uint32_t c0, uint32_t cell, uint32_t o, int slot, int p,
+                                         int q, int result, int kind) {
+  const unsigned long long i = atomicAdd(L.n, 1ull);
+  if ((long long)i < L.cap) {
+    int4* e = reinterpret_cast<int4*>(L.buf + 8 * (size_t)i);
+    e[0] = make_int4((int)c0, (int)cell, (int)o, slot);
+    e[1] = make_int4(p, q, result, kind);
+  }
+}
 
 // Per-replicate data of a batch (device copy).
 struct BatchRep {
@@ -600,7 +621,18 @@ struct pic_ctx {
   int64_t dsmc_groups;
   size_t dsmc_smem;
   pic::AdjointBuffers* adj;      // pathwise-adjoint working set, allocated on first use
-  unsigned long long* counters;  // n_cand, n_coll, n_gmax, n_tie
+  unsigned long long* counters;  // n_cand, n_coll, n_gmax, n_tie, n_floor_tie
+  // decision log of the collision calls (pic_set_decision_log)
+  // per-step record since pic_reset_stats: [kHistSteps][4] (CG iterations,
+  // candidates, collisions, g > g_max); hist_row is the current step's row
+  // while pic_step enqueues it, else nullptr
+  long long* step_hist;
+  long long* hist_row;
+  int64_t hist_base;
+  int32_t* dlog;                 // [dlog_cap][8]
+  unsigned long long* dlog_n;    // records produced
+  int64_t dlog_cap;
+  int dlog_mode;
   // recorded scattering angles (PIC_VERIFY_ANGLES): histograms of F^M(chi)
   // and eps/(2 pi), and the scratch of their CDF-error reduction
   unsigned long long* ang_hist;  // [2][PIC_ANGLE_BINS]

@@ -5,18 +5,21 @@ Stated error of the precision form (checked here):
     width h), velocities within 1e-6 relative; sort bit-exact;
   - charge density within 1e-6 relative, potential and field within 1e-4
     relative (FP32 vectors, CG to 1e-6);
-  - collisions: candidate pairs identical except where FP32 changes an
-    N_pairs floor; accept decisions identical except FP32 near ties; all
-    but a small fraction of particles (those touched by a differing
-    decision) within 2e-5 of the oracle's <dv>;
-  - steps: all but a small fraction of particles within 1e-5 (positions)
-    and 1e-4 (velocities) after 10 steps; error norms within 3% of the
-    FP64 ones, so the precision form does not raise the error floor.
+  - collisions, with the oracle started from the precision form's own FP32
+    state: the pair list equals the oracle's record by record except after
+    a decision the kernel flagged (an N_pairs draw or an accept test inside
+    its FP32 rounding bound); every particle outside the cells holding such
+    a flag is within 2e-5 of the oracle's <dv>;
+  - steps: every particle that no flagged decision (nor an FP32 position on
+    the other side of a cell face) can have reached is within 1e-5
+    (positions) and 1e-4 (velocities) after 10 steps; error norms within 3%
+    of the FP64 ones, so the precision form does not raise the error floor.
 """
 import numpy as np
 import pytest
 
 import inputs
+import pairlists
 from oracle import oracle as O
 from paper_2602_15130_gb300 import Pic, workloads
 
@@ -93,37 +96,62 @@ def test_mixed_field(name):
     assert np.abs(E - Eo).max() <= 1e-4 * np.abs(Eo).max()
 
 
+def oracle_on_gpu_state(p, g, **kw):
+    """An oracle holding exactly the precision form's FP32 state (as FP64
+    numbers), with the same cells and (cell, pid) order."""
+    x, v = g.get_state()
+    st = g.stats()
+    o = O.Oracle(dict(p, **kw))
+    o.set_state(x, v, 0.0, int(st["step"]))
+    for a, b in zip(g.get_sort(), o.sort()):
+        assert np.array_equal(a, b)
+    return o
+
+
 @pytest.mark.parametrize("name", ["smallest", "ragged", "k40"])
-def test_mixed_collisions(name):
+@pytest.mark.parametrize("phase", [0, 1])
+def test_mixed_collisions_differ_only_after_flagged_decisions(name, phase):
     p = CASES[name]
-    g, o = Pic(p), O.Oracle(p)
+    g = Pic(p)
     g.sample_mms(0.0)
-    o.sample(0.0)
+    o = oracle_on_gpu_state(p, g)
+    # the production kernel (flagged decisions only), then the same call
+    # with every decision logged: the same bits
+    g.set_decision_log(1, 1 << 16)
     g.reset_stats()
     o.reset_stats()
-    dv, dvm = g.collide_avg(0)
-    dvo, dvmo = o.collide_avg(0)
-    sg, so = g.stats(), o.stats()
-    assert abs(sg["n_cand"] - so["n_cand"]) <= 2 + 1e-4 * so["n_cand"]
-    assert abs(sg["n_coll"] - so["n_coll"]) <= 2 + 1e-3 * so["n_coll"]
+    dv, dvm = g.collide_avg(phase)
+    flags1 = g.decision_log()
+    g.set_decision_log(2, 1 << 20)
+    dv2, dvm2 = g.collide_avg(phase)
+    assert np.array_equal(dv, dv2) and np.array_equal(dvm, dvm2)
+    o.set_pair_log(True)
+    dvo, dvmo = o.collide_avg(phase)
+    flagged, nflags = pairlists.compare_flagged(g.decision_log(), o.pair_log())
+    assert {(int(c0), int(c)) for c0, c in flags1[:, :2]} == flagged and len(flags1) == nflags
+    st = g.stats()
+    assert st["n_near_ties"] + st["n_floor_ties"] == 2 * nflags
+    cell = g.get_sort()[0]
+    reached = np.isin(cell, [c for _, c in flagged])
+    off = (np.abs(dv - dvo) > 2e-5).any(axis=1)
+    assert not (off & ~reached).any(), np.flatnonzero(off & ~reached)[:10]
+    assert reached.mean() <= 0.05
     assert np.abs(dvm - dvmo).max() <= 1e-5 * max(1.0, np.abs(dvmo).max())
-    bad = (np.abs(dv - dvo) > 2e-5).any(axis=1)
-    assert bad.mean() <= 0.01, bad.mean()
 
 
 @pytest.mark.parametrize("name", ["smallest", "ragged"])
 def test_mixed_steps_track_oracle(name):
     p = CASES[name]
-    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-12))
+    g = Pic(p)
     g.sample_mms(0.0)
-    o.sample(0.0)
-    g.step(10)
-    o.step(10)
+    o = oracle_on_gpu_state(p, g, cg_tol=1e-12)
+    g.set_decision_log(1, 1 << 16)
+    reached = pairlists.step_tracking_flags(g, o, 10)
     x, v = g.get_state()
     xo, vo = o.state()
-    far_x = (dpos(x, xo) > 1e-5).any(axis=1)
-    far_v = (np.abs(v - vo) > 1e-4).any(axis=1)
-    assert far_x.mean() <= 0.01 and far_v.mean() <= 0.02, (far_x.mean(), far_v.mean())
+    far = (dpos(x, xo) > 1e-5).any(axis=1) | (np.abs(v - vo) > 1e-4).any(axis=1)
+    assert not (far & ~reached).any(), (np.flatnonzero(far & ~reached)[:10], reached.mean())
+    assert reached.mean() <= 0.05, reached.mean()
     eg = g.mms_error()["array"]
     eo = o.errors()
     assert np.all(np.abs(eg - eo) <= 0.03 * eo + 1e-7), (eg, eo)

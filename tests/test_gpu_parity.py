@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import inputs
+import pairlists
 from oracle import oracle as O
 from paper_2602_15130_gb300 import Pic, workloads
 
@@ -151,6 +152,44 @@ def test_collisions_match_oracle(name, phase):
     assert ok, e
     ok, e = close(dvm, dvmo, scale=1.0)
     assert ok, e
+
+
+@pytest.mark.parametrize("name", ["smallest", "ragged", "k40", "k5", "n2"])
+@pytest.mark.parametrize("phase", [0, 1])
+def test_pair_lists_bit_exact(name, phase):
+    """Algorithm 1's pair list of one K-averaged call, record by record:
+    N_pairs of every (cell, outcome), then (p, q, accepted) of every
+    candidate slot, equal to the oracle's (near ties: none here)."""
+    p = CASES[name]
+    g, o = pair(p)
+    g.sample_mms(0.0)
+    o.sample(0.0)
+    g.set_decision_log(2, 1 << 20)
+    o.set_pair_log(True)
+    g.collide_avg(phase)
+    o.collide_avg(phase)
+    lg, lo = pairlists.canonical(g.decision_log()), pairlists.canonical(o.pair_log())
+    assert len(lo) > 0 and (lo[:, 3] >= 0).any()
+    assert lg.shape == lo.shape and np.array_equal(lg, lo)
+
+
+def test_pair_lists_bit_exact_over_steps_and_crowded_cells():
+    """The same over three whole steps (both calls of each, counter word
+    2 step + phase) from a state with about 300 particles in each of ten
+    cells and a large dt (long in-place chains of collisions)."""
+    p = workloads.smallest(n=8, n_particles=3000, K=12, dt=0.05, cg_tol=1e-12)
+    g, o = pair(p)
+    x, v = inputs.particles(3000, seed=9, clustered_cells=10, n=8)
+    g.set_state(x, v)
+    o.set_state(x, v)
+    g.set_decision_log(2, 1 << 21)
+    o.set_pair_log(True)
+    g.step(3)
+    o.step(3)
+    lg, lo = pairlists.canonical(g.decision_log()), pairlists.canonical(o.pair_log())
+    assert sorted(set(lo[:, 0])) == list(range(6))
+    assert (lo[lo[:, 3] >= 0, 6] == 1).sum() > 1000
+    assert lg.shape == lo.shape and np.array_equal(lg, lo)
 
 
 def test_collisions_crowded_cells_large_dt():

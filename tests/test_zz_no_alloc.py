@@ -86,3 +86,57 @@ def test_noalloc_rejects_oversize_and_host_pointers():
     dE = torch.zeros(3 * 8 ** 3, dtype=torch.float64, device="cuda")
     assert L.pic_poisson_solve_noalloc(8, hb.ctypes.data, d.data_ptr(), dE.data_ptr(), 1e-10, 100, None,
                                        None, None) == _lib.PIC_EINVAL
+
+
+def _solve(L, n, b, phi, E, tol, maxit):
+    import torch
+
+    iters = ctypes.c_int32(-1)
+    res = ctypes.c_double(-1.0)
+    st = L.pic_poisson_solve_noalloc(n, b.data_ptr(), phi.data_ptr(), E.data_ptr(), tol, maxit,
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                     ctypes.byref(iters), ctypes.byref(res))
+    return st, iters.value, res.value
+
+
+def test_noalloc_maxit_and_warm_start():
+    """maxit = 1 stops after one iteration with PIC_ENOCONV and phi holding
+    that iterate; a solve warm-started from the converged phi (the documented
+    use of phi as input) takes no iteration and returns the same phi and E."""
+    import torch
+
+    L = _lib.load()
+    p = workloads.smallest(n=12, n_particles=12 ** 3 * 8, cg_tol=1e-13)
+    n, m = p["n"], p["n"] ** 3
+    rho, phi_ref, E_ref = _context_field(p, 9, 0.2)
+    b = torch.tensor(_rhs(p, rho, 0.2), device="cuda")
+    phi = torch.zeros(m, dtype=torch.float64, device="cuda")
+    E = torch.zeros((3, m), dtype=torch.float64, device="cuda")
+    st, it, res = _solve(L, n, b, phi, E, 1e-13, 1)
+    assert st == _lib.PIC_ENOCONV and it == 1 and res > 1e-13, (st, it, res)
+    assert np.abs(phi.cpu().numpy()).max() > 0.0  # the first iterate was written
+    st, it, res = _solve(L, n, b, phi, E, 1e-13, 20000)
+    assert st == _lib.PIC_OK and it > 1 and res <= 1e-13
+    phi1, E1 = phi.cpu().numpy().copy(), E.cpu().numpy().copy()
+    assert np.abs(phi1 - phi_ref).max() <= TOL * np.abs(phi_ref).max()
+    # the true residual of the 1e-13 solution is far below 1e-10: no iteration
+    st, it, res = _solve(L, n, b, phi, E, 1e-10, 20000)
+    assert st == _lib.PIC_OK and it == 0 and res <= 1e-10, (st, it, res)
+    assert np.abs(phi.cpu().numpy() - phi1).max() <= 1e-14 * np.abs(phi1).max()
+    assert np.abs(E.cpu().numpy() - E1).max() <= 1e-13 * np.abs(E1).max()
+
+
+def test_noalloc_rejects_another_devices_memory():
+    import torch
+
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one visible GPU: no memory of another device to pass")
+    L = _lib.load()
+    n, m = 8, 8 ** 3
+    with torch.cuda.device(1):
+        b1 = torch.zeros(m, dtype=torch.float64, device="cuda:1")
+    phi = torch.zeros(m, dtype=torch.float64, device="cuda:0")
+    E = torch.zeros(3 * m, dtype=torch.float64, device="cuda:0")
+    torch.cuda.set_device(0)
+    assert L.pic_poisson_solve_noalloc(n, b1.data_ptr(), phi.data_ptr(), E.data_ptr(), 1e-10, 100, None,
+                                       None, None) == _lib.PIC_EINVAL
