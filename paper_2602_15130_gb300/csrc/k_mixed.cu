@@ -417,16 +417,56 @@ struct Counts32 {
   unsigned long long cand, coll, gmax, tie, ftie;
 };
 
-// a particle's working velocity: the lane's overlay copy where this outcome
-// has touched it, else the cell's velocity; the source addresses are
-// selected so that lanes of both kinds load together (no divergent branch)
-__device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const float* ov, const float* v0,
-                                           const float* v1, const float* v2, float* o) {
-  const bool t = (bm[p >> 5] >> (p & 31)) & 1u;
-  const float* s0 = t ? ov + 3 * p : v0 + p;
-  const float* s1 = t ? ov + 3 * p + 1 : v1 + p;
-  const float* s2 = t ? ov + 3 * p + 2 : v2 + p;
-  o[0] = *s0; o[1] = *s1; o[2] = *s2;
+// The working velocities of a (cell, outcome) lane: the cell's velocities,
+// except for the particles this outcome has changed (their bits are set in
+// the lane's bitmap). The first kList changed particles keep their working
+// velocity in a list in shared memory (entry k of lane l at list[32 k + l]:
+// x, y, z and the in-cell index as w), any further ones in the lane's
+// particle-indexed overlay in global memory; at these collision rates an
+// outcome changes a few particles, so the overlay is almost never touched.
+constexpr int kList = 4;
+
+// position k < t of particle p in a lane's list, or -1
+__device__ __forceinline__ int wl_find(const float4* wl, int t, int p) {
+  int k = -1;
+#pragma unroll
+  for (int i = 0; i < kList; ++i)
+    if (i < t && __float_as_int(wl[32 * i].w) == p) k = i;
+  return k;
+}
+
+__device__ __forceinline__ void vel_get(int p, const uint32_t* bm, const float4* wl, int t, const float* ov,
+                                        const float* v0, const float* v1, const float* v2, float* o) {
+  if ((bm[p >> 5] >> (p & 31)) & 1u) {
+    const int k = wl_find(wl, t, p);
+    if (k >= 0) {
+      const float4 e = wl[32 * k];
+      o[0] = e.x; o[1] = e.y; o[2] = e.z;
+    } else {
+      o[0] = ov[3 * p]; o[1] = ov[3 * p + 1]; o[2] = ov[3 * p + 2];
+    }
+  } else {
+    o[0] = v0[p]; o[1] = v1[p]; o[2] = v2[p];
+  }
+}
+
+__device__ __forceinline__ void vel_put(int p, const float* v, uint32_t* bm, float4* wl, int& t, float* ov) {
+  const uint32_t bit = 1u << (p & 31);
+  if (bm[p >> 5] & bit) {
+    const int k = wl_find(wl, t, p);
+    if (k >= 0) {
+      wl[32 * k] = make_float4(v[0], v[1], v[2], __int_as_float(p));
+      return;
+    }
+  } else {
+    bm[p >> 5] |= bit;
+    if (t < kList) {
+      wl[32 * t] = make_float4(v[0], v[1], v[2], __int_as_float(p));
+      ++t;
+      return;
+    }
+  }
+  ov[3 * p] = v[0]; ov[3 * p + 1] = v[1]; ov[3 * p + 2] = v[2];
 }
 
 // Decisions the FP32 arithmetic may take differently from an FP64
@@ -445,8 +485,8 @@ __device__ __forceinline__ void load_vel_f(int p, const uint32_t* bm, const floa
 // Every decision is logged only in the kVerify instantiation.
 template <bool kVerify>
 __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
-                              const float* v1, const float* v2, uint32_t* bm, float* ov, Counts32& cnt,
-                              const DLog& lg) {
+                              const float* v1, const float* v2, uint32_t* bm, float4* wl, int& t, float* ov,
+                              Counts32& cnt, const DLog& lg) {
   const U4 u = philox_rk<true>(c0, cell, 0xFFFFFFFFu, o << 8, P.rk);
   const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
   const float S = base + unif24(u.x);
@@ -479,8 +519,8 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
       }
     }
     float vp[3], vq[3];
-    load_vel_f((int)p, bm, ov, v0, v1, v2, vp);
-    load_vel_f((int)q, bm, ov, v0, v1, v2, vq);
+    vel_get((int)p, bm, wl, t, ov, v0, v1, v2, vp);
+    vel_get((int)q, bm, wl, t, ov, v0, v1, v2, vq);
     const float dx = vp[0] - vq[0], dy = vp[1] - vq[1], dz = vp[2] - vq[2];
     const float g2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     // accept if U < sigma g / (sigma g)_max: hard spheres g / g_max, i.e.
@@ -505,13 +545,14 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
       dlog_put(lg, c0, cell, o, s, (int)p, (int)q, lhs < rhs ? 1 : 0, tie ? PIC_DLOG_TIE : 0);
     if (lhs < rhs) {
       const float g = sqrtf(g2);
+      float np_[3], nq_[3];
       if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
         // injected Error 2: swap with probability 1/2 (coin = chi draw)
         const bool swap = unif24(b1.x) < 0.5f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          ov[3 * p + d] = swap ? vq[d] : vp[d];
-          ov[3 * q + d] = swap ? vp[d] : vq[d];
+          np_[d] = swap ? vq[d] : vp[d];
+          nq_[d] = swap ? vp[d] : vq[d];
         }
       } else {
         float se, ce;
@@ -527,21 +568,26 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
           // Eq. v_cm; injected Error 1 flips the sign of v_q
           const float cm = 0.5f * (err1 ? vp[d] - vq[d] : vp[d] + vq[d]);
           const float hg = 0.5f * g * nv[d];
-          ov[3 * p + d] = cm + hg;
-          ov[3 * q + d] = cm - hg;
+          np_[d] = cm + hg;
+          nq_[d] = cm - hg;
         }
       }
       if (kVerify && P.ang_hist)
-        record_angles_f(P.ang_hist, (P.verify & PIC_VERIFY_ANISO) != 0, g, ov[3 * p] - ov[3 * q],
-                        ov[3 * p + 1] - ov[3 * q + 1], ov[3 * p + 2] - ov[3 * q + 2]);
-      bm[p >> 5] |= 1u << (p & 31);
-      bm[q >> 5] |= 1u << (q & 31);
+        record_angles_f(P.ang_hist, (P.verify & PIC_VERIFY_ANISO) != 0, g, np_[0] - nq_[0], np_[1] - nq_[1],
+                        np_[2] - nq_[2]);
+      vel_put((int)p, np_, bm, wl, t, ov);
+      vel_put((int)q, nq_, bm, wl, t, ov);
       ++cnt.coll;
     }
   }
 }
 
 constexpr int kDsmcThreads = 128;
+
+// shared memory of one warp, in 32-bit words: bitmaps, lists, list lengths
+__host__ __device__ constexpr size_t dsmc32_smem_words(int bm_words) {
+  return (size_t)32 * bm_words + (size_t)kList * 32 * 4 + 32;
+}
 
 template <bool kVerify>
 __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
@@ -551,8 +597,13 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
   const int wpb = blockDim.x >> 5;
   const int64_t gwarp = (int64_t)blockIdx.x * wpb + wib;
   const int64_t nwarps = (int64_t)gridDim.x * wpb;
-  uint32_t* wbm = smem + (size_t)wib * 32 * a.bm_words;
+  // per warp: the lanes' bitmaps [32][bm_words], their lists [kList][32]
+  // and list lengths [32]
+  uint32_t* wbm = smem + (size_t)wib * dsmc32_smem_words(a.bm_words);
   uint32_t* bm = wbm + (size_t)lane * a.bm_words;
+  float4* wlist = reinterpret_cast<float4*>(wbm + 32 * a.bm_words);
+  float4* wl = wlist + lane;
+  int* wlen = reinterpret_cast<int*>(wlist + 32 * kList);
   float* wov = a.overlay + (size_t)gwarp * 32 * a.max_ppc * 3;
   float* ov = wov + (size_t)lane * a.max_ppc * 3;
   for (int i = 0; i < a.bm_words; ++i) bm[i] = 0u;
@@ -580,9 +631,11 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
         atomicOr(a.flags, 1);
         run = false;
       }
+      int t = 0;
       if (run)
         ntc_outcome_f<kVerify>(P, a.c0, (uint32_t)(cell0 + mycl), (uint32_t)o, c, a.v0 + s, a.v1 + s, a.v2 + s,
-                               bm, ov, cnt, a.lg);
+                               bm, wl, t, ov, cnt, a.lg);
+      wlen[lane] = t;
       __syncwarp();
       // per 32-particle word: one transpose of the lanes' bitmap words across
       // the warp serves every cell of the group, since lane l holds outcome
@@ -609,10 +662,19 @@ __global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
           while (mine) {
             const int L = __ffs(mine) - 1;
             mine &= mine - 1u;
-            const float* W = wov + ((size_t)L * a.max_ppc + jj) * 3;
-            acc0 += W[0] - w0;
-            acc1 += W[1] - w1;
-            acc2 += W[2] - w2;
+            // lane L's working velocity of particle jj: its list, else its overlay
+            const int k = wl_find(wlist + L, wlen[L], jj);
+            float W0, W1, W2;
+            if (k >= 0) {
+              const float4 e = wlist[32 * k + L];
+              W0 = e.x; W1 = e.y; W2 = e.z;
+            } else {
+              const float* W = wov + ((size_t)L * a.max_ppc + jj) * 3;
+              W0 = W[0]; W1 = W[1]; W2 = W[2];
+            }
+            acc0 += W0 - w0;
+            acc1 += W1 - w1;
+            acc2 += W2 - w2;
           }
           if (!last) {
             a.dv0[j] = acc0; a.dv1[j] = acc1; a.dv2[j] = acc2;
@@ -1294,6 +1356,7 @@ cudaError_t launch_gather32(pic_ctx* c) {
 
 const void* sort_big32_kernel_ptr() { return (const void*)k_sort_big32; }
 int dsmc32_threads() { return kDsmcThreads; }
+size_t dsmc32_smem_bytes(int bm_words) { return (size_t)(kDsmcThreads / 32) * dsmc32_smem_words(bm_words) * 4; }
 const void* dsmc32_kernel_ptr(bool verify) {
   return verify ? (const void*)k_dsmc32<true> : (const void*)k_dsmc32<false>;
 }

