@@ -812,8 +812,11 @@ int64_t orc_field(orc_state* s, double t) {
  * outcome o:
  *   N_pairs : Philox(c0, k, 0xFFFFFFFF, o<<8)      -> U52(w0, w1)
  *   pair s  : Philox(c0, k, s, o<<8 | 0)  = (p, q, accept, epsilon)
- *             Philox(c0, k, s, o<<8 | 1)  = (chi, q redraw, q redraw, q redraw)
- *             Philox(c0, k, s, o<<8 | b), b >= 2: four more q redraws each
+ *             Philox(c0, k, s/4, o<<8 | 1), word s mod 4 = chi
+ * p = floor(U c) over the c particles; q = floor(U (c-1)) over the other
+ * c - 1, counted past p (q' >= p gives q' + 1). That is the distribution of
+ * Algorithm 1's second draw repeated until it differs from the first:
+ * uniform over the particles other than p.
  * ---------------------------------------------------------------------- */
 typedef struct {
   double* a;  /* [n][2] (chi, eps) */
@@ -911,25 +914,13 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
   int64_t npairs = (int64_t)floor(npairs_real);       /* Algorithm 1: NTC pair count */
   log_pair(st->log, c0, cellk, o, -1, -1, -1, npairs, 4);
   for (int64_t sl = 0; sl < npairs; sl++) {
-    uint32_t b0[4], b1[4];
+    uint32_t b0[4], bchi[4];
     philox4(c0, cellk, (uint32_t)sl, (o << 8) | 0u, cf->seed, b0);
-    philox4(c0, cellk, (uint32_t)sl, (o << 8) | 1u, cf->seed, b1);
+    philox4(c0, cellk, (uint32_t)(sl / 4), (o << 8) | 1u, cf->seed, bchi);
     uint32_t p = orc_index(b0[0], (uint32_t)c);
-    uint32_t q = orc_index(b0[1], (uint32_t)c);
-    /* redraw q while q == p: words b1[1..3], then blocks 2, 3, ... */
-    int widx = 1;
-    uint32_t blk[4] = {b1[0], b1[1], b1[2], b1[3]};
-    uint32_t bnum = 1;
-    while (q == p) {
-      if (widx == 4) {
-        bnum++;
-        if (bnum > 255) { q = (p + 1) % (uint32_t)c; break; }
-        philox4(c0, cellk, (uint32_t)sl, (o << 8) | bnum, cf->seed, blk);
-        widx = 0;
-      }
-      q = orc_index(blk[widx], (uint32_t)c);
-      widx++;
-    }
+    uint32_t q = orc_index(b0[1], (uint32_t)(c - 1)); /* one of the others */
+    if (q >= p) q++;
+    uint32_t wchi = bchi[sl % 4];
     st->n_cand++;
     double* vp = vloc + 3 * p;
     double* vq = vloc + 3 * q;
@@ -945,8 +936,8 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
     if (U < ratio) {
       if (cf->verify & ORC_ERROR2) {
         /* injected Error 2 (Sec. 5.4): swap with probability beta = 1/2,
-         * the coin being the chi word of block 1                          */
-        if (orc_u32(b1[0]) < 0.5) {
+         * the coin being the candidate's chi word                        */
+        if (orc_u32(wchi) < 0.5) {
           for (int d = 0; d < 3; d++) {
             double tmp = vp[d];
             vp[d] = vq[d];
@@ -956,7 +947,7 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
       } else {
         double eps = 2.0 * ORC_PI * orc_u32(b0[3]);     /* epsilon = 2 pi U        */
         /* chi = F^{-1}(U) (Eq. chi): cos chi = 1 - 2U isotropic, 1 - 2u(U) anisotropic */
-        double uchi = (cf->verify & ORC_ANISO) ? orc_aniso_u(orc_u32(b1[0])) : orc_u32(b1[0]);
+        double uchi = (cf->verify & ORC_ANISO) ? orc_aniso_u(orc_u32(wchi)) : orc_u32(wchi);
         double cchi = 1.0 - 2.0 * uchi;
         double schi = sqrt(1.0 - cchi * cchi);
         double n[3] = {cos(eps) * schi, sin(eps) * schi, cchi}; /* Eq. n (lab frame) */

@@ -322,26 +322,17 @@ __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint
   const int npairs = (int)floorf(S);
   // flagged FP32 decisions: the bounds of the single-domain kernel
   if (fabsf(S - rintf(S)) <= fmaf(base + S, 0x1p-22f, 0x1p-24f)) ++cnt.ftie;
+  // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon);
+  // chi is word s mod 4 of block (c0, cell, s / 4, (o << 8) | 1)
+  U4 bchi{0u, 0u, 0u, 0u};
   for (int s = 0; s < npairs; ++s) {
     const U4 b0 = philox<true>(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
-    const U4 b1 = philox<true>(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+    if ((s & 3) == 0) bchi = philox<true>(c0, cell, (uint32_t)(s >> 2), (o << 8) | 1u, P.key0, P.key1);
+    const uint32_t wchi = (s & 3) == 0 ? bchi.x : (s & 3) == 1 ? bchi.y : (s & 3) == 2 ? bchi.z : bchi.w;
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
-    uint32_t q = draw_index(b0.y, (uint32_t)c);
-    if (q == p) {
-      q = draw_index(b1.y, (uint32_t)c);
-      if (q == p) q = draw_index(b1.z, (uint32_t)c);
-      if (q == p) q = draw_index(b1.w, (uint32_t)c);
-      uint32_t blk = 2;
-      while (q == p) {
-        if (blk > 255u) { q = (p + 1u) % (uint32_t)c; break; }
-        const U4 bb = philox<true>(c0, cell, (uint32_t)s, (o << 8) | blk, P.key0, P.key1);
-        q = draw_index(bb.x, (uint32_t)c);
-        if (q == p) q = draw_index(bb.y, (uint32_t)c);
-        if (q == p) q = draw_index(bb.z, (uint32_t)c);
-        if (q == p) q = draw_index(bb.w, (uint32_t)c);
-        ++blk;
-      }
-    }
+    // q uniform over the other c - 1 particles
+    uint32_t q = draw_index(b0.y, (uint32_t)(c - 1));
+    q += q >= p ? 1u : 0u;
     float vp[3], vq[3];
     load_vel_b((int)p, bm, ov, v0, v1, v2, vp);
     load_vel_b((int)q, bm, ov, v0, v1, v2, vq);
@@ -356,7 +347,7 @@ __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint
     if (ug2 < g2) {
       float se, ce;
       sincospif(2.f * unif24(b0.w), &se, &ce);
-      const float cchi = 1.f - 2.f * unif24(b1.x);
+      const float cchi = 1.f - 2.f * unif24(wchi);
       const float schi = sqrtf(fmaxf(0.f, 1.f - cchi * cchi));
       const float g = sqrtf(g2);
       const float nv[3] = {ce * schi, se * schi, cchi};

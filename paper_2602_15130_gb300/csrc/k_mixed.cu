@@ -497,30 +497,25 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
   if (log_all || (ftie && lg.mode != PIC_DLOG_OFF))
     dlog_put(lg, c0, cell, o, -1, -1, -1, npairs, PIC_DLOG_NPAIRS | (ftie ? PIC_DLOG_FLOOR : 0));
   const float gmax = P.gmax;
+  // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon);
+  // chi is word s mod 4 of block (c0, cell, s / 4, (o << 8) | 1). The next
+  // candidate's block is formed while this one's velocities load: the draws
+  // depend on no velocity.
+  U4 bnext = philox_rk<true>(c0, cell, 0u, o << 8, P.rk);
+  U4 bchi{0u, 0u, 0u, 0u};
   for (int s = 0; s < npairs; ++s) {
-    // both blocks of the candidate up front: two independent Philox chains
-    const U4 b0 = philox_rk<true>(c0, cell, (uint32_t)s, o << 8, P.rk);
-    const U4 b1 = philox_rk<true>(c0, cell, (uint32_t)s, (o << 8) | 1u, P.rk);
+    const U4 b0 = bnext;
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
-    uint32_t q = draw_index(b0.y, (uint32_t)c);
-    if (q == p) {
-      q = draw_index(b1.y, (uint32_t)c);
-      if (q == p) q = draw_index(b1.z, (uint32_t)c);
-      if (q == p) q = draw_index(b1.w, (uint32_t)c);
-      uint32_t blk = 2;
-      while (q == p) {
-        if (blk > 255u) { q = (p + 1u) % (uint32_t)c; break; }
-        const U4 bb = philox_rk<true>(c0, cell, (uint32_t)s, (o << 8) | blk, P.rk);
-        q = draw_index(bb.x, (uint32_t)c);
-        if (q == p) q = draw_index(bb.y, (uint32_t)c);
-        if (q == p) q = draw_index(bb.z, (uint32_t)c);
-        if (q == p) q = draw_index(bb.w, (uint32_t)c);
-        ++blk;
-      }
-    }
+    // q uniform over the other c - 1 particles: the distribution of
+    // drawing again until q != p
+    uint32_t q = draw_index(b0.y, (uint32_t)(c - 1));
+    q += q >= p ? 1u : 0u;
     float vp[3], vq[3];
     vel_get((int)p, bm, wl, t, ov, v0, v1, v2, vp);
     vel_get((int)q, bm, wl, t, ov, v0, v1, v2, vq);
+    if ((s & 3) == 0) bchi = philox_rk<true>(c0, cell, (uint32_t)(s >> 2), (o << 8) | 1u, P.rk);
+    if (s + 1 < npairs) bnext = philox_rk<true>(c0, cell, (uint32_t)(s + 1), o << 8, P.rk);
+    const uint32_t wchi = (s & 3) == 0 ? bchi.x : (s & 3) == 1 ? bchi.y : (s & 3) == 2 ? bchi.z : bchi.w;
     const float dx = vp[0] - vq[0], dy = vp[1] - vq[1], dz = vp[2] - vq[2];
     const float g2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     // accept if U < sigma g / (sigma g)_max: hard spheres g / g_max, i.e.
@@ -548,7 +543,7 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
       float np_[3], nq_[3];
       if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
         // injected Error 2: swap with probability 1/2 (coin = chi draw)
-        const bool swap = unif24(b1.x) < 0.5f;
+        const bool swap = unif24(wchi) < 0.5f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           np_[d] = swap ? vq[d] : vp[d];
@@ -557,7 +552,7 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
       } else {
         float se, ce;
         sincospif(2.f * unif24(b0.w), &se, &ce);
-        float uchi = unif24(b1.x);
+        float uchi = unif24(wchi);
         if (kVerify && (P.verify & PIC_VERIFY_ANISO)) uchi = aniso_u_f(uchi);
         const float cchi = 1.f - 2.f * uchi;
         const float schi = sqrtf(fmaxf(0.f, 1.f - cchi * cchi));
@@ -590,7 +585,7 @@ __host__ __device__ constexpr size_t dsmc32_smem_words(int bm_words) {
 }
 
 template <bool kVerify>
-__global__ void __launch_bounds__(kDsmcThreads, 7) k_dsmc32(Dsmc32Args a) {
+__global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
   extern __shared__ uint32_t smem[];
   const ParamsF& P = a.P;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;

@@ -42,29 +42,18 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
   const long long npairs = (long long)floor(__dadd_rn(base, unif52(u.x, u.y)));
   const bool log_all = kVerify && lg.mode == PIC_DLOG_ALL;
   if (log_all) dlog_put(lg, c0, cell, o, -1, -1, -1, (int)npairs, PIC_DLOG_NPAIRS);
+  // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon);
+  // chi is word s mod 4 of block (c0, cell, s / 4, (o << 8) | 1), formed
+  // once per group of four candidates when one of them is accepted
+  U4 bchi{0u, 0u, 0u, 0u};
+  long long chi_group = -1;
   for (long long s = 0; s < npairs; ++s) {
     const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
-    uint32_t q = draw_index(b0.y, (uint32_t)c);
-    U4 b1;
-    bool have_b1 = false;
-    if (q == p) {
-      b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
-      have_b1 = true;
-      q = draw_index(b1.y, (uint32_t)c);
-      if (q == p) q = draw_index(b1.z, (uint32_t)c);
-      if (q == p) q = draw_index(b1.w, (uint32_t)c);
-      uint32_t blk = 2;
-      while (q == p) {
-        if (blk > 255u) { q = (p + 1u) % (uint32_t)c; break; }
-        const U4 bb = philox(c0, cell, (uint32_t)s, (o << 8) | blk, P.key0, P.key1);
-        q = draw_index(bb.x, (uint32_t)c);
-        if (q == p) q = draw_index(bb.y, (uint32_t)c);
-        if (q == p) q = draw_index(bb.z, (uint32_t)c);
-        if (q == p) q = draw_index(bb.w, (uint32_t)c);
-        ++blk;
-      }
-    }
+    // q uniform over the other c - 1 particles: the distribution of
+    // drawing again until q != p
+    uint32_t q = draw_index(b0.y, (uint32_t)(c - 1));
+    q += q >= p ? 1u : 0u;
     double vp[3], vq[3];
     load_vel((int)p, bm, ov, v0, v1, v2, vp);
     load_vel((int)q, bm, ov, v0, v1, v2, vq);
@@ -82,10 +71,14 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
     if (log_all || (tie && lg.mode != PIC_DLOG_OFF))
       dlog_put(lg, c0, cell, o, (int)s, (int)p, (int)q, U < ratio ? 1 : 0, tie ? PIC_DLOG_TIE : 0);
     if (U < ratio) {
-      if (!have_b1) b1 = philox(c0, cell, (uint32_t)s, (o << 8) | 1u, P.key0, P.key1);
+      if ((s >> 2) != chi_group) {
+        chi_group = s >> 2;
+        bchi = philox(c0, cell, (uint32_t)chi_group, (o << 8) | 1u, P.key0, P.key1);
+      }
+      const uint32_t wchi = (s & 3) == 0 ? bchi.x : (s & 3) == 1 ? bchi.y : (s & 3) == 2 ? bchi.z : bchi.w;
       if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
         // injected Error 2: swap with probability 1/2 (coin = chi draw)
-        const bool swap = unif32(b1.x) < 0.5;
+        const bool swap = unif32(wchi) < 0.5;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           ov[3 * p + d] = swap ? vq[d] : vp[d];
@@ -95,7 +88,7 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
         const double eps = __dmul_rn(kTwoPi, unif32(b0.w));
         double se, ce;
         sincos(eps, &se, &ce);
-        double uchi = unif32(b1.x);
+        double uchi = unif32(wchi);
         if (kVerify && (P.verify & PIC_VERIFY_ANISO)) uchi = aniso_u(uchi);
         const double cchi = __dsub_rn(1.0, __dmul_rn(2.0, uchi));
         const double schi = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(cchi, cchi)));

@@ -103,3 +103,28 @@ def test_a_changed_index_draw_is_caught_even_after_a_flag(logged):
     bad[i, 5] = (bad[i, 5] + 1) % 8 if bad[i, 5] + 1 != bad[i, 4] else (bad[i, 5] + 2) % 8
     with pytest.raises(AssertionError):
         pairlists.compare_flagged(bad, log)
+
+
+def test_pair_draws_are_uniform_over_ordered_pairs():
+    """Algorithm 1 draws p uniformly over the cell and q uniformly over the
+    others (the distribution of redrawing q until it differs from p): over
+    every candidate of many outcomes in one cell of six particles the 30
+    ordered pairs are equally frequent (chi-square at the 0.1% level) and
+    no candidate has p = q."""
+    import inputs
+    from scipy import stats
+
+    p = workloads.smallest(n=2, n_particles=6, K=400, dt=0.5)
+    o = O.Oracle(p)
+    x, v = inputs.particles(6, seed=4, clustered_cells=1, n=2)
+    o.set_state(x, v)
+    o.set_pair_log(True)
+    o.collide_avg(0)
+    cand = o.pair_log()
+    cand = cand[cand[:, 3] >= 0]
+    assert (cand[:, 4] != cand[:, 5]).all()
+    counts = np.zeros((6, 6))
+    np.add.at(counts, (cand[:, 4], cand[:, 5]), 1)
+    off = counts[~np.eye(6, dtype=bool)]
+    assert off.sum() == len(cand) > 3000
+    assert stats.chisquare(off).pvalue > 1e-3
