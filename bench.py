@@ -386,7 +386,8 @@ def run_batched(args, rank: int, world: int) -> dict | None:
             torch.cuda.synchronize()
         ms = max_over_ranks(ev0.elapsed_time(ev1), "cuda")
         st = b.stats()
-        # per-kernel times from a profiled pass (direct launches)
+        # per-phase times from a profiled pass (one launch per phase instead
+        # of the persistent step)
         b.set_profiling(True)
         b.step(1)
         kt = b.kernel_times()
@@ -408,7 +409,8 @@ def run_batched(args, rank: int, world: int) -> dict | None:
                    "l2": "inputs larger than L2"},
         "e2e": None, "e2e_note": "batches have no host-buffer input path (states are sampled on the device)",
         "gpu_launches": int(st["kernel_launches"]), "graph_replays": int(st["graph_replays"]),
-        "tuned_kick_block": int(st["tuned_kick_block"]),
+        "launches_per_step": int(st["kernel_launches"]) / max(1, args.steps),
+        "tuned_block": int(st["tuned_block"]), "tuned_tile": int(st["tuned_tile"]),
         "kernel_ms_one_profiled_step": {k: round(v["ms"], 3) for k, v in kt.items()},
         "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
                   "cg_iters_max": st["cg_iters_max"], "cg_iters_median": sorted(iters)[len(iters) // 2]},

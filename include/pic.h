@@ -201,8 +201,9 @@ typedef struct {
   int32_t cg_iters_max;
   double cg_res_last;     /* last relative residual ||r|| / ||b||           */
   int64_t graph_replays;  /* batched steps replayed from a captured CUDA graph */
-  int32_t tuned_kick_block; /* block size the batch autotuner chose (0: none) */
-  int32_t reserved;
+  int32_t tuned_block;    /* batches: block size of the persistent step the
+                             autotuner chose (0: not tuned yet)            */
+  int32_t tuned_tile;     /* batches: its tile-shape configuration (0, 1)   */
   int64_t n_floor_ties;   /* precision form: N_pairs draws whose FP32 sum lay
                              within its rounding bound of an integer, so that
                              its floor may differ from the FP64 one (flagged) */
@@ -310,14 +311,17 @@ pic_status pic_set_state(pic_ctx* ctx, const double* x, const double* v, double 
                          int64_t step);
 
 /* Failure injection for tests, made on the host and caught by a bounded
- * device wait: the next Poisson solve (of pic_sample_mms, pic_set_state or
- * pic_step) launches one block that leaves before its first grid barrier,
- * so the other blocks wait for an arrival that never comes. Their bounded
- * wait (4e9 SM cycles, about 2 s) ends the solve. That call returns
+ * device wait. Single contexts: the next Poisson solve (of pic_sample_mms,
+ * pic_set_state or pic_step) launches one block that leaves before its
+ * first grid barrier, so the other blocks wait for an arrival that never
+ * comes. Batches: the next pic_step's persistent launch leaves one work
+ * item (the first drift-kick tile of a replicate) uncounted, so the items
+ * that depend on it wait for a completion that never comes. Either bounded
+ * wait (4e9 SM cycles, about 2 s) ends the launch. That call returns
  * PIC_ETIMEOUT, and the field and the state it moves are invalid. The
  * context stays usable: the next pic_sample_mms or pic_set_state starts
- * clean. PIC_EINVAL for batches (their solves have no grid barrier) and
- * for a solve of one block (nothing would wait). */
+ * clean. PIC_EINVAL for a single-context solve of one block (nothing would
+ * wait). */
 pic_status pic_inject_barrier_stall(pic_ctx* ctx);
 
 /* Copy mesh quantities out (any pointer may be NULL): rho [n^3] (the CIC
@@ -415,7 +419,13 @@ pic_status pic_get_kernel_times(pic_ctx* ctx, pic_kernel_times* out);
 /* ---- Batched form: independent replicates advanced together ----------
  * pic_create_batch builds one context holding nrep independent replicates
  * (the refinement-study use of the method: many runs of uneven mesh edge,
- * particle count and N_avg). cfgs[r] gives replicate r; all must use
+ * particle count and N_avg). pic_step advances them with one persistent
+ * launch per step: a queue of (phase, replicate, tile) work items that
+ * blocks take in order, each waiting (bounded) until the earlier phases of
+ * its replicate are complete; the first steps time the launch for each
+ * block size and tile shape (pic_stats.tuned_block, tuned_tile), and steady
+ * steps replay it from a captured CUDA graph when the context has a
+ * non-default stream. cfgs[r] gives replicate r; all must use
  * PIC_MIXED and share every field except n, n_particles, K, dt, sigma0
  * and seed (PIC_EINVAL otherwise); 1 <= nrep <= 65534. Replicate r draws
  * from its own Philox key, local pids and local cell indices, so it

@@ -82,8 +82,8 @@ class PicStats(ctypes.Structure):
         ("cg_iters_max", ctypes.c_int32),
         ("cg_res_last", ctypes.c_double),
         ("graph_replays", ctypes.c_int64),
-        ("tuned_kick_block", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tuned_block", ctypes.c_int32),
+        ("tuned_tile", ctypes.c_int32),
         ("n_floor_ties", ctypes.c_int64),
     ]
 

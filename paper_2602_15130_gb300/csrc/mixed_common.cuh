@@ -222,4 +222,168 @@ __device__ __forceinline__ void cell_ijk(const ParamsF& P, int c, int* ci) {
   }
 }
 
+// ----------------------------------------------------- sort gather + CIC --
+struct Gather32Args {
+  int n;
+  int64_t ncell;
+  const int32_t *start, *perm;
+  const float* in[9];   // o0..2, v0..2, m0..2
+  float* out[9];
+  const uint32_t* pid_in;
+  uint32_t* pid_out;
+  int32_t* cell_out;
+  double* corner;       // [8][ncell]
+  int big_lo;             // cells above this count go to the block sort
+};
+
+// CIC corner weights of one particle (offsets in cell units) in 64-bit fixed
+// point: integer sums are exact in any order, so a cell's corner partials do
+// not depend on the order its particles are visited in. The conversion
+// rounds with FP32 arithmetic only (64-bit float-to-integer conversions run
+// on the slow FP64 pipe): adding 1.5 2^23 rounds w 2^22 to an integer held
+// in the low mantissa bits, an FMA recovers the remainder exactly, and the
+// remainder is rounded the same way to lo_bits more bits. Resolution 2^-40
+// (error <= 2^-41 per weight) below 2^23 particles per cell, 2^-30 above, so
+// a corner sum never leaves int64.
+struct CicFixed {
+  float lo_scale;  // 2^lo_bits
+  int lo_bits;     // 18 or 8
+  double inv;      // 2^-(22 + lo_bits)
+};
+__device__ __forceinline__ CicFixed cic_fixed_for(int32_t cnt) {
+  return cnt < (1 << 23) ? CicFixed{262144.f, 18, 1.0 / 1099511627776.0} : CicFixed{256.f, 8, 1.0 / 1073741824.0};
+}
+__device__ __forceinline__ long long to_fixed(float w, const CicFixed& f) {
+  constexpr float M = 12582912.f;  // 1.5 2^23
+  const float hs = fmaf(w, 4194304.f, M);
+  const int hi = __float_as_int(hs) - 0x4B400000;
+  const float rem = fmaf(w, 4194304.f, -(hs - M));
+  const int lo = __float_as_int(fmaf(rem, f.lo_scale, M)) - 0x4B400000;
+  return ((long long)hi << f.lo_bits) + lo;
+}
+
+__device__ __forceinline__ void cic_add_fixed(long long* acc, float ox, float oy, float oz, const CicFixed& f) {
+  const float wx[2] = {1.f - ox, ox}, wy[2] = {1.f - oy, oy}, wz[2] = {1.f - oz, oz};
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float wyz = wy[b] * wz[c];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) acc[q + 2 * b + 4 * c] += to_fixed(wx[q] * wyz, f);
+    }
+}
+
+__device__ __forceinline__ long long shfl_xor_ll(long long v, int off) {
+  return (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, off);
+}
+
+// warp sum of 8 fixed-point corner partials: each xor level halves the
+// values a lane keeps; lane l then holds corner 4 [l & 16] + 2 [l & 8] + [l & 4]
+__device__ __forceinline__ void store_corners_fixed(const long long* acc, int lane, double* corner, int64_t ncell,
+                                                    int64_t cell, double inv) {
+  const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+  long long a4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a4[i] = (u16 ? acc[4 + i] : acc[i]) + shfl_xor_ll(u16 ? acc[i] : acc[4 + i], 16);
+  long long a2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) a2[i] = (u8 ? a4[2 + i] : a4[i]) + shfl_xor_ll(u8 ? a4[i] : a4[2 + i], 8);
+  long long a1 = (u4 ? a2[1] : a2[0]) + shfl_xor_ll(u4 ? a2[0] : a2[1], 4);
+  a1 += shfl_xor_ll(a1, 2);
+  a1 += shfl_xor_ll(a1, 1);
+  if ((lane & 3) == 0) {
+    const int c = (u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0);
+    corner[(int64_t)c * ncell + cell] = (double)a1 * inv;
+  }
+}
+
+// One cell of the sort gather (a warp): the cell's particles in ascending
+// pid order (their in-cell rank by pid), copied to the destination arrays,
+// and the cell's eight CIC corner partials. Cells of big_lo < count <=
+// kMaxBlockSort are left to the block sort.
+__device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cell, int lane) {
+  const int32_t s = a.start[cell];
+  const int32_t cnt = a.start[cell + 1] - s;
+  if (cnt > a.big_lo && cnt <= kMaxBlockSort) return;  // k_sort_big32
+  const CicFixed fx = cic_fixed_for(cnt);
+  long long acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0;
+  if (cnt <= 64) {
+    // both 32-element chunks in registers; the particle data is loaded
+    // with the pids (one memory round trip), then ranked in one pass
+    int32_t src0 = 0, src1 = 0;
+    uint32_t p0 = 0xFFFFFFFFu, p1 = 0xFFFFFFFFu;
+    float d0[9], d1[9];
+    const bool h0 = lane < cnt, h1 = lane + 32 < cnt;
+    if (h0) src0 = a.perm[s + lane];
+    if (h1) src1 = a.perm[s + 32 + lane];
+    if (h0) {
+      p0 = a.pid_in[src0];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) d0[q] = a.in[q][src0];
+    }
+    if (h1) {
+      p1 = a.pid_in[src1];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) d1[q] = a.in[q][src1];
+    }
+    int r0 = 0, r1 = 0;
+    if (cnt <= 32) {
+      for (int l = 0; l < cnt; ++l) r0 += __shfl_sync(0xffffffffu, p0, l) < p0 ? 1 : 0;
+    } else {
+      for (int l = 0; l < 32; ++l) {
+        const uint32_t x0 = __shfl_sync(0xffffffffu, p0, l), x1 = __shfl_sync(0xffffffffu, p1, l);
+        r0 += (x0 < p0) + (x1 < p0);
+        r1 += (x0 < p1) + (x1 < p1);
+      }
+    }
+    if (h0) {
+      const int32_t dst = s + r0;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) a.out[q][dst] = d0[q];
+      a.pid_out[dst] = p0;
+      a.cell_out[dst] = (int32_t)cell;
+      cic_add_fixed(acc, d0[0], d0[1], d0[2], fx);
+    }
+    if (h1) {
+      const int32_t dst = s + r1;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) a.out[q][dst] = d1[q];
+      a.pid_out[dst] = p1;
+      a.cell_out[dst] = (int32_t)cell;
+      cic_add_fixed(acc, d1[0], d1[1], d1[2], fx);
+    }
+  } else {
+    for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
+      const int32_t e = e0 + lane;
+      int32_t src = 0;
+      uint32_t mp = 0xFFFFFFFFu;
+      if (e < cnt) {
+        src = a.perm[s + e];
+        mp = a.pid_in[src];
+      }
+      int32_t r = 0;
+      for (int32_t f0 = 0; f0 < cnt; f0 += 32) {
+        const uint32_t other = f0 == e0 ? mp : ((f0 + lane < cnt) ? a.pid_in[a.perm[s + f0 + lane]] : 0xFFFFFFFFu);
+        const int lim = min(32, cnt - f0);
+        for (int l = 0; l < lim; ++l) r += __shfl_sync(0xffffffffu, other, l) < mp ? 1 : 0;
+      }
+      if (e < cnt) {
+        const int32_t dst = s + r;
+        float d[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] = a.in[q][src];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a.out[q][dst] = d[q];
+        a.pid_out[dst] = mp;
+        a.cell_out[dst] = (int32_t)cell;
+        cic_add_fixed(acc, d[0], d[1], d[2], fx);
+      }
+    }
+  }
+  store_corners_fixed(acc, lane, a.corner, a.ncell, cell, fx.inv);
+}
+
 }  // namespace pic

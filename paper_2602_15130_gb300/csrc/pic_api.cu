@@ -290,7 +290,8 @@ void dev_free(pic_ctx* c, void* p) {
 template <class F>
 void for_each_buffer(pic_ctx* c, F f) {
   const size_t np = (size_t)c->P.np, nc = (size_t)c->P.ncell;
-  const size_t lanes = (size_t)c->dsmc_grid * (c->dsmc_block / 32) * 32 * (size_t)c->cfg.max_ppc * 3;
+  const size_t warps = c->overlay_warps > 0 ? (size_t)c->overlay_warps : (size_t)c->dsmc_grid * (c->dsmc_block / 32);
+  const size_t lanes = warps * 32 * (size_t)c->cfg.max_ppc * 3;
   if (!c->mixed) {
     for (int b = 0; b < 2; ++b)
       for (int d = 0; d < 3; ++d) {
@@ -467,9 +468,6 @@ cudaError_t batch_enqueue_step(pic_ctx* c, bool coll) {
   return e;
 }
 
-constexpr int kTuneCandidates = 3;
-const int kKickBlocks[kTuneCandidates] = {128, 256, 512};
-
 // the two timing events of one tuning step, released on every return
 struct EventPair {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -479,44 +477,54 @@ struct EventPair {
   }
 };
 
-// One batched step: the first steps time the candidate kick block sizes
-// (the result does not depend on the block size), later steady-state steps
-// replay a captured graph per buffer parity.
+// per-step work of the persistent batched step: the time terms, then its
+// one launch (and two memsets)
+cudaError_t batch_enqueue_persistent(pic_ctx* c, bool coll, bool stall) {
+  cudaError_t e = batch_enqueue_times(c);
+  if (e == cudaSuccess) e = launch_batch_step(c, coll, stall);
+  return e;
+}
+
+// One batched step: one launch of the persistent step kernel. The first
+// steps time every candidate (block size, tile shapes) of it, one step each
+// (the result does not depend on the candidate); later steady-state steps
+// replay a captured graph per buffer parity. With profiling on, the step
+// runs as one launch per phase, so that each phase is timed.
 pic_status batch_step(pic_ctx* c, int64_t n, bool coll) {
   pic_status s = batch_time_terms(c, n);
   if (s != PIC_OK) return s;
-  if (c->tune_step < kTuneCandidates) {
+  const bool stall = c->stall_next_cg;
+  c->stall_next_cg = false;
+  if (c->profiling) {
+    CK(batch_enqueue_step(c, coll));
+    return PIC_OK;
+  }
+  const int ncand = step_candidates();
+  while (c->tune_step < ncand && c->step_grid[step_block_of(c->tune_step) == 128 ? 0 : 1] == 0)
+    c->tune_ms[c->tune_step++] = 1e30f;  // a block size whose shared memory does not fit
+  if (c->tune_step < ncand && !stall) {
+    const int cand = c->tune_step;
+    if (c->step_cand != cand) CK(build_step_items(c, cand));
     EventPair ev;
     CK(cudaEventCreate(&ev.e0));
     CK(cudaEventCreate(&ev.e1));
-    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
-    c->kick_block = kKickBlocks[c->tune_step];
-    CK(batch_enqueue_times(c));
-    if (coll) CK(launch_batch_dsmc(c, 0));
-    CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-    CK(cudaEventRecord(e0, c->stream));
-    CK(launch_batch_kick(c, coll, true));
-    CK(cudaEventRecord(e1, c->stream));
-    CK(launch_scan_scatter(c));
-    CK(launch_gather32(c));
-    CK(launch_batch_rhs(c, 2));
-    CK(launch_batch_cg(c));
-    if (coll) CK(launch_batch_dsmc(c, 1));
-    CK(launch_batch_kick(c, coll, false));
-    CK(cudaEventSynchronize(e1));
+    CK(cudaEventRecord(ev.e0, c->stream));
+    CK(batch_enqueue_persistent(c, coll, false));
+    CK(cudaEventRecord(ev.e1, c->stream));
+    CK(cudaEventSynchronize(ev.e1));
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    c->tune_ms[c->tune_step] = ms;
-    if (++c->tune_step == kTuneCandidates) {
+    CK(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
+    c->tune_ms[cand] = ms;
+    if (++c->tune_step == ncand) {
       int best = 0;
-      for (int k = 1; k < kTuneCandidates; ++k)
+      for (int k = 1; k < ncand; ++k)
         if (c->tune_ms[k] < c->tune_ms[best]) best = k;
-      c->kick_block = kKickBlocks[best];
+      CK(build_step_items(c, best));
     }
     return PIC_OK;
   }
-  if (!c->use_graphs || c->profiling || !c->lor_valid) {
-    CK(batch_enqueue_step(c, coll));
+  if (stall || !c->use_graphs || !c->lor_valid) {
+    CK(batch_enqueue_persistent(c, coll, stall));
     return PIC_OK;
   }
   const int parity = c->cur;
@@ -524,7 +532,7 @@ pic_status batch_step(pic_ctx* c, int64_t n, bool coll) {
     const int64_t l0 = c->launches;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = batch_enqueue_step(c, coll);
+    cudaError_t e = batch_enqueue_persistent(c, coll, false);
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -557,6 +565,7 @@ pic_status batch_step(pic_ctx* c, int64_t n, bool coll) {
 namespace pic {
 
 void* ctx_alloc(pic_ctx* c, size_t bytes) { return dev_alloc(c, bytes); }
+void dev_free_ctx(pic_ctx* c, void* p) { dev_free(c, p); }
 void ctx_free(pic_ctx* c, void* p) { dev_free(c, p); }
 
 // One FP64 step of Eq. velocity_verlet. hook(where), if given, runs at
@@ -674,7 +683,9 @@ void pic_destroy(pic_ctx* c) {
     *p = nullptr;
   });
   void* batch_dev[] = {c->reps_dev, c->prm_dev, c->rep_of_cell, c->poff_dev, c->dsmc_items, c->cg_order,
-                       c->cg_iters_rep, c->cg_res_rep, c->tt_dev};
+                       c->cg_iters_rep, c->cg_res_rep, c->tt_dev, c->step_items, c->step_need, c->step_sync,
+                       c->cg_team_bar, c->cg_team_red, c->cg_parts, c->cg_head};
+  free(c->step_items_host);
   for (void* p : batch_dev) dev_free(c, p);
   if (c->tt_host) cudaFreeHost(c->tt_host);
   for (int k = 0; k < 2; ++k)
@@ -1013,7 +1024,7 @@ pic_status pic_get_state(pic_ctx* c, double* x, double* v) {
 }
 
 pic_status pic_inject_barrier_stall(pic_ctx* c) {
-  if (!c || c->nrep > 0 || c->cg_grid < 2) return PIC_EINVAL;
+  if (!c || (c->nrep == 0 && c->cg_grid < 2)) return PIC_EINVAL;
   c->stall_next_cg = true;
   return PIC_OK;
 }
@@ -1110,7 +1121,10 @@ pic_status pic_get_stats(pic_ctx* c, pic_stats* out) {
   out->cg_iters_max = c->cg_iters_max;
   out->cg_res_last = c->cg_res_last;
   out->graph_replays = c->graph_replays;
-  out->tuned_kick_block = c->kick_block;
+  if (c->nrep > 0 && c->tune_step >= step_candidates()) {
+    out->tuned_block = step_block_of(c->step_cand);
+    out->tuned_tile = step_tile_of(c->step_cand);
+  }
   return s;
 }
 
@@ -1308,6 +1322,27 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   if (dgrid > (int64_t)docc * c->num_sms) dgrid = (int64_t)docc * c->num_sms;
   c->dsmc_grid = (int)(dgrid < 1 ? 1 : dgrid);
   c->n_items = items;
+  // persistent step: one block per resident slot for each block size it
+  // may run with (0 where its shared memory does not fit)
+  c->overlay_warps = (int64_t)c->dsmc_grid * wpb;
+  for (int k = 0; k < 2; ++k) {
+    const int blk = k == 0 ? 128 : 256;
+    const size_t sm = step_smem(c, blk);
+    int occ = 0;
+    if (sm > 48 * 1024 &&
+        cudaFuncSetAttribute(step_kernel_ptr(blk), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      occ = 0;
+    else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel_ptr(blk), blk, sm) != cudaSuccess)
+      occ = 0;
+    cudaGetLastError();
+    c->step_grid[k] = occ * c->num_sms;
+    const int64_t w = (int64_t)c->step_grid[k] * (blk / 32);
+    if (w > c->overlay_warps) c->overlay_warps = w;
+  }
+  if (c->step_grid[0] == 0 && c->step_grid[1] == 0) {
+    delete c;
+    return PIC_EINVAL;
+  }
 
   // host tables
   c->reps_host = (BatchRep*)calloc((size_t)nrep, sizeof(BatchRep));
@@ -1368,6 +1403,15 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   grab((void**)&c->cg_iters_rep, sizeof(int) * nrep);
   grab((void**)&c->cg_res_rep, sizeof(double) * nrep);
   grab((void**)&c->tt_dev, sizeof(TimeTerms) * (3 * nrep + 1));
+  int n_parts = 0;
+  for (int r = 0; r < nrep; ++r) n_parts += cg_team_size(cfgs[r].n * cfgs[r].n * cfgs[r].n);
+  c->n_cg_parts = n_parts;
+  grab((void**)&c->cg_team_bar, sizeof(unsigned) * nrep);
+  grab((void**)&c->cg_team_red, sizeof(double) * (size_t)nrep * 2 * kTeamMax);
+  grab((void**)&c->cg_parts, sizeof(int2) * n_parts);
+  grab((void**)&c->cg_head, 64);
+  grab((void**)&c->step_need, sizeof(int) * (size_t)nrep * kStepPhases);
+  grab((void**)&c->step_sync, sizeof(int) * (1 + (size_t)nrep * kStepPhases));
   if (ok && cudaMallocHost((void**)&c->tt_host, sizeof(TimeTerms) * (3 * nrep + 1)) != cudaSuccess) {
     cudaGetLastError();
     c->tt_host = nullptr;
@@ -1409,11 +1453,35 @@ pic_status pic_create_batch(const pic_config* cfgs, int32_t nrep, void* stream, 
   if (e == cudaSuccess) e = cudaMemcpy(c->poff_dev, poff, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && items > 0) e = cudaMemcpy(c->dsmc_items, it_h, sizeof(int2) * items, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->cg_order, order, sizeof(int) * nrep, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    // the per-phase solve's (replicate, part) queue, largest replicates first
+    int2* parts = (int2*)malloc(sizeof(int2) * (size_t)c->n_cg_parts);
+    if (!parts) {
+      e = cudaErrorMemoryAllocation;
+    } else {
+      int k = 0;
+      for (int i = 0; i < nrep; ++i) {
+        const int r = order[i];
+        const int T = cg_team_size(cfgs[r].n * cfgs[r].n * cfgs[r].n);
+        for (int t = 0; t < T; ++t) parts[k++] = make_int2(r, t);
+      }
+      e = cudaMemcpy(c->cg_parts, parts, sizeof(int2) * (size_t)c->n_cg_parts, cudaMemcpyHostToDevice);
+      free(parts);
+    }
+  }
   free(roc); free(poff); free(it_h); free(order);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cg_info, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pic_destroy(c);
+    return cuda_status(e);
+  }
+  // the step's work items for the first candidate the autotuner tries (a
+  // block size that fits)
+  e = build_step_items(c, c->step_grid[0] > 0 ? 0 : step_candidates() / 2);
   if (e != cudaSuccess) {
     cudaGetLastError();
     pic_destroy(c);

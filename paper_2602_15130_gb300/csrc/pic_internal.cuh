@@ -108,6 +108,14 @@ struct BatchRep {
   int Kc, G, nchunks;
 };
 constexpr int kBatchTile = 256;
+// a batched replicate's Poisson solve runs on a team of blocks: one per
+// kTeamNodes nodes, at most kTeamMax
+constexpr int kTeamNodes = 16384;
+constexpr int kTeamMax = 32;
+__host__ __device__ inline int cg_team_size(int m) {
+  const int T = m / kTeamNodes;
+  return T < 1 ? 1 : (T > kTeamMax ? kTeamMax : T);
+}
 
 
 // ---------------------------------------------------------------------------
@@ -676,9 +684,27 @@ struct pic_ctx {
   double* cg_res_rep;            // [nrep]
   pic::TimeTerms* tt_dev;        // [nrep][3]: t_n, t_{n+1/2}, t_{n+1}, then the step (int64)
   pic::TimeTerms* tt_host;       // pinned mirror
-  int kick_block;                // autotuned block size of the batched kick
+  int kick_block;                // autotuned block size of the batched kick (per-phase launches)
   int tune_step;
-  float tune_ms[4];
+  float tune_ms[8];
+  // persistent batched step (one launch per step): work items of the chosen
+  // candidate (block size, tile shapes), items per (replicate, phase), queue
+  // head and completion counters, the persistent grid per block size
+  int4* step_items;
+  int4* step_items_host;
+  int64_t step_items_cap;
+  int n_step_items;
+  int* step_need;                // [nrep][kStepPhases]
+  int* step_sync;                // [0] queue head, then [nrep][kStepPhases] completed items
+  int step_stall_item;           // the item a stall injection leaves uncounted
+  int step_cand;                 // candidate the items were built for
+  int step_grid[2];              // persistent grid for 128- and 256-thread blocks (0: unavailable)
+  int64_t overlay_warps;         // warps the collision overlay is sized for (batches)
+  unsigned* cg_team_bar;         // [nrep] team barrier counters of the batched solves
+  double* cg_team_red;           // [nrep][2][kTeamMax] part totals
+  int2* cg_parts;                // (replicate, part) items of the per-phase batched solve, CG order
+  int n_cg_parts;
+  int* cg_head;                  // its queue head
   cudaGraphExec_t graph[2];      // steady-state step, by buffer parity
   int64_t graph_launches;        // kernels per captured step
   int64_t graph_replays;
@@ -746,6 +772,16 @@ cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_collisions, bool drif
 cudaError_t launch_angle_stats(pic_ctx* c, pic_angle_stats* out);
 // device memory through the context's allocator; adjoint buffers (k_adjoint.cu)
 void* ctx_alloc(pic_ctx* c, size_t bytes);
+void dev_free_ctx(pic_ctx* c, void* p);
+// persistent batched step (k_batch.cu)
+constexpr int kStepPhases = 9;
+int step_candidates();
+int step_block_of(int cand);
+int step_tile_of(int cand);
+const void* step_kernel_ptr(int block);
+size_t step_smem(const pic_ctx* c, int block);
+cudaError_t build_step_items(pic_ctx* c, int cand);
+cudaError_t launch_batch_step(pic_ctx* c, bool coll, bool stall);
 void ctx_free(pic_ctx* c, void* p);
 void adjoint_free(pic_ctx* c);
 cudaError_t launch_cg32(pic_ctx* c);
