@@ -152,10 +152,12 @@ BYTES_PER_UNIT = {
     },
 }
 
-# Philox4x32-10 integer operations per block by its definition: ten rounds of
-# two 32 x 32 -> 64 products (four ops: high and low halves), two 3-input
-# xors (four ops) and two key additions
-INT_OPS_PER_PHILOX = 100
+# Integer and FP operations per candidate pair of the collision algorithm
+# (the middle of the 200-300 range of the method's statement of work: one
+# Philox4x32-10 block and a quarter at about 100 integer operations each,
+# the index draws, the relative speed, the accept test, and the scattering
+# of the accepted ones)
+OPS_PER_CANDIDATE = 250
 
 # DRAM bytes of one launch of the dominant kernels, per unit, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
@@ -310,22 +312,25 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
     dom = max(kt, key=lambda k: kt[k]["ms"])
     row = kernels[dom]
     if dom == "dsmc":
-        # integer-ALU bound: the Philox4x32-10 blocks the method draws per
-        # launch (one per (cell, outcome) for N_pairs, one per candidate
-        # pair, one more per accepted pair for chi), against the measured
-        # rate of this GPU at forming those blocks
+        # integer/FP ALU bound: the method's work is its candidate pairs at
+        # OPS_PER_CANDIDATE integer and FP operations each (one Philox4x32-10
+        # block and a quarter, the index draws, g, the accept test and, for
+        # the accepted ones, the scattering), against this GPU's INT32 issue
+        # rate measured in this run (the multiply-add pipe that Philox loads)
         nl = max(1, kt["dsmc"]["launches"])
-        ncell2 = p["n"] ** 3  # cells with two or more particles: all at these occupancies
-        blocks = ncell2 * p["K"] + (st["n_cand"] + st["n_coll"]) / nl
+        cand = st["n_cand"] / nl
         per_launch_s = kt["dsmc"]["ms"] / nl / 1000.0
-        achieved = blocks * INT_OPS_PER_PHILOX / per_launch_s / 1e12
-        peak = alu["philox_blocks"] * INT_OPS_PER_PHILOX / 1e12
+        achieved = cand * OPS_PER_CANDIDATE / per_launch_s / 1e12
+        peak = alu["imad"] / 1e12
+        blocks = p["n"] ** 3 * p["K"] + (st["n_cand"] * 1.25 + 0.0) / nl
         traffic, how = traffic_per_launch(form, "dsmc", npart)
         roof = {"bound": "alu", "kernel": "dsmc", "achieved": achieved, "peak": peak, "unit": "Tops/s (INT32)",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": how,
-                "peak_source": "measured in this run: Philox4x32-10 blocks/s of a full-grid generator kernel "
-                               "(pic_measure_alu_peaks) x %d integer ops per block" % INT_OPS_PER_PHILOX,
-                "philox_blocks_per_launch": blocks, "ms_per_launch": row["ms_per_launch"]}
+                "ops_per_candidate": OPS_PER_CANDIDATE, "candidates_per_launch": cand,
+                "peak_source": "measured in this run: INT32 multiply-add issue rate of a full-grid kernel "
+                               "(pic_measure_alu_peaks); 64 lanes x SMs x clock gives the same",
+                "philox_block_frac": blocks / per_launch_s / alu["philox_blocks"],
+                "ms_per_launch": row["ms_per_launch"]}
     else:
         b = BYTES_PER_UNIT[form]["method"].get(dom) or BYTES_PER_UNIT[form]["impl"].get(dom, 0.0)
         units = row["units_per_launch"]

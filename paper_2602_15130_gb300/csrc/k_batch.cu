@@ -702,6 +702,7 @@ struct BStepArgs {
   int64_t ncell_total;
   const int32_t *key, *rank;
   int32_t *count, *start, *perm;
+  uint32_t* spid;           // pids in arrival order for the gather (the gather's pid output)
   const int4* items;        // (phase | rep << 8, lo, hi, 0)
   int n_items;
   int* head;                // queue head, zero at launch
@@ -841,7 +842,11 @@ __global__ void __launch_bounds__(kT, 768 / kT) kb_step(BStepArgs a) {
         case BP_SCAN: scan_rep(a, rep, scan_sh); break;
         case BP_SCATTER: {
           const int64_t p0 = a.poff[rep] + e.y, p1 = a.poff[rep] + e.z;
-          for (int64_t j = p0 + threadIdx.x; j < p1; j += kT) a.perm[a.start[a.key[j]] + a.rank[j]] = (int32_t)j;
+          for (int64_t j = p0 + threadIdx.x; j < p1; j += kT) {
+            const int32_t slot = a.start[a.key[j]] + a.rank[j];
+            a.perm[slot] = (int32_t)j;
+            a.spid[slot] = a.g.pid_in[j];
+          }
           break;
         }
         case BP_GATHER: {
@@ -1178,6 +1183,7 @@ cudaError_t launch_batch_step(pic_ctx* c, bool coll, bool stall) {
   g.cell_out = c->cell32[o];
   g.corner = c->corner;
   g.big_lo = INT_MAX;  // every cell by its warp (no block sort inside the step)
+  g.spid = c->pid[o];  // written in arrival order by the scatter phase
   a.rh.prm = c->prm_dev;
   a.rh.reps = c->reps_dev;
   a.rh.tt = c->tt_dev;
@@ -1214,6 +1220,7 @@ cudaError_t launch_batch_step(pic_ctx* c, bool coll, bool stall) {
   a.count = c->count;
   a.start = c->start;
   a.perm = c->perm;
+  a.spid = c->pid[o];
   a.items = c->step_items;
   a.n_items = c->n_step_items;
   a.head = c->step_sync;

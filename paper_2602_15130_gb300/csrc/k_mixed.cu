@@ -690,6 +690,7 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
 // ---------------------------------------------------------------- CG32 --
 struct Cg32Args {
   int n;
+  int log2n;  // log2(n) when n is a power of two, else -1
   int64_t ncell;
   float inv_h2, inv_2h;
   float *b, *x, *r, *p, *q;
@@ -819,8 +820,19 @@ __device__ __forceinline__ double grid_total32(const double* part, int m, double
 struct Nbr {
   int xp, xm, yp, ym, zp, zm;
 };
-__device__ __forceinline__ Nbr neighbours(int id, int n, int nn) {
-  const int i = id % n, j = (id / n) % n, k = id / nn;
+// log2n >= 0: n = 2^log2n, the coordinates by shifts and masks instead of
+// integer divisions (the same neighbours)
+__device__ __forceinline__ Nbr neighbours(int id, int n, int nn, int log2n) {
+  int i, j, k;
+  if (log2n >= 0) {
+    i = id & (n - 1);
+    j = (id >> log2n) & (n - 1);
+    k = id >> (2 * log2n);
+  } else {
+    i = id % n;
+    j = (id / n) % n;
+    k = id / nn;
+  }
   Nbr b;
   b.xp = i == n - 1 ? id - (n - 1) : id + 1;
   b.xm = i == 0 ? id + (n - 1) : id - 1;
@@ -859,7 +871,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   const float mean_b = (float)(grid_total32(a.rhs_part, a.rhs_blocks, sh) / (double)m);
   DF rr_loc{0.f, 0.f}, bb_loc{0.f, 0.f};
   for (int id = t0; id < m; id += stride) {
-    const Nbr q = neighbours(id, n, nn);
+    const Nbr q = neighbours(id, n, nn, a.log2n);
     const float bv = a.b[id] - mean_b;
     const float* x = a.x;
     const float nb = x[q.xp] + x[q.xm] + x[q.yp] + x[q.ym] + x[q.zp] + x[q.zm];
@@ -885,7 +897,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   {
     DF rw_loc{0.f, 0.f};
     for (int id = t0; id < m; id += stride) {
-      const Nbr q = neighbours(id, n, nn);
+      const Nbr q = neighbours(id, n, nn, a.log2n);
       const float* r = a.r;
       const float rc = r[id];
       const float wv = (6.f * rc - (r[q.xp] + r[q.xm] + r[q.yp] + r[q.ym] + r[q.zp] + r[q.zm])) * a.inv_h2;
@@ -934,7 +946,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
     if (!grid_barrier32(a.bar, a.info, a.flags)) return;
     DF rr_l{0.f, 0.f}, rw_l{0.f, 0.f};
     for (int id = t0; id < m; id += stride) {
-      const Nbr q = neighbours(id, n, nn);
+      const Nbr q = neighbours(id, n, nn, a.log2n);
       const float* r = a.r;
       const float rc = r[id];
       const float wv = (6.f * rc - (r[q.xp] + r[q.xm] + r[q.yp] + r[q.ym] + r[q.zp] + r[q.zm])) * a.inv_h2;
@@ -973,7 +985,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   for (int id = t0; id < m; id += stride) a.x[id] -= mean_x;
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
   for (int id = t0; id < m; id += stride) {
-    const Nbr q = neighbours(id, n, nn);
+    const Nbr q = neighbours(id, n, nn, a.log2n);
     const float* x = a.x;
     a.E4[id] = make_float4(-(x[q.xp] - x[q.xm]) * a.inv_2h, -(x[q.yp] - x[q.ym]) * a.inv_2h,
                            -(x[q.zp] - x[q.zm]) * a.inv_2h, 0.f);
@@ -1182,6 +1194,7 @@ cudaError_t launch_gather32(pic_ctx* c) {
   g.cell_out = c->cell32[o];
   g.corner = c->corner;
   g.big_lo = big_cell_threshold(g.ncell, c->P.np);
+  g.spid = c->pid[o];  // written in arrival order by the scatter
   int64_t blocks = (c->P.ncell * 32 + kGatherThreads - 1) / kGatherThreads;
   const int64_t cap = (int64_t)c->num_sms * 16;
   if (blocks > cap) blocks = cap;
@@ -1277,6 +1290,7 @@ cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, dou
 cudaError_t launch_cg32(pic_ctx* c) {
   Cg32Args a;
   a.n = c->P.n;
+  a.log2n = (c->P.n & (c->P.n - 1)) == 0 ? __builtin_ctz((unsigned)c->P.n) : -1;
   a.ncell = c->P.ncell;
   a.inv_h2 = (float)((double)c->P.n * (double)c->P.n);
   a.inv_2h = (float)(0.5 * (double)c->P.n);

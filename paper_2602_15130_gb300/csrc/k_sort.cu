@@ -123,12 +123,16 @@ struct ScatterArgs {
   int64_t np;
   const int32_t *key, *rank, *start;
   int32_t* perm;
+  const uint32_t* pid;  // optional: each particle's pid also goes to its arrival slot
+  uint32_t* spid;
 };
 
 __global__ void __launch_bounds__(kThreads) k_scatter(ScatterArgs a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.np) return;
-  a.perm[a.start[a.key[j]] + a.rank[j]] = (int32_t)j;
+  const int32_t slot = a.start[a.key[j]] + a.rank[j];
+  a.perm[slot] = (int32_t)j;
+  if (a.spid) a.spid[slot] = a.pid[j];
 }
 
 struct GatherArgs {
@@ -334,6 +338,10 @@ cudaError_t launch_scan_scatter(pic_ctx* c) {
   s.rank = c->rank;
   s.start = c->start;
   s.perm = c->perm;
+  // the precision form's gather reads each cell's pids in arrival order
+  // from the output pid array (coalesced) instead of through perm
+  s.pid = c->mixed ? c->pid[c->cur] : nullptr;
+  s.spid = c->mixed ? c->pid[1 - c->cur] : nullptr;
   k_scatter<<<blocks_for(s.np), kThreads, 0, c->stream>>>(s);
   prof_end(c, KC_SORT);
   c->launches += 4;

@@ -234,6 +234,7 @@ struct Gather32Args {
   int32_t* cell_out;
   double* corner;       // [8][ncell]
   int big_lo;             // cells above this count go to the block sort
+  const uint32_t* spid;   // optional: pids in arrival order (slot s + e holds perm[s + e]'s pid)
 };
 
 // CIC corner weights of one particle (offsets in cell units) in 64-bit fixed
@@ -319,13 +320,17 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
     const bool h0 = lane < cnt, h1 = lane + 32 < cnt;
     if (h0) src0 = a.perm[s + lane];
     if (h1) src1 = a.perm[s + 32 + lane];
+    if (a.spid) {
+      if (h0) p0 = a.spid[s + lane];
+      if (h1) p1 = a.spid[s + 32 + lane];
+    }
     if (h0) {
-      p0 = a.pid_in[src0];
+      if (!a.spid) p0 = a.pid_in[src0];
 #pragma unroll
       for (int q = 0; q < 9; ++q) d0[q] = a.in[q][src0];
     }
     if (h1) {
-      p1 = a.pid_in[src1];
+      if (!a.spid) p1 = a.pid_in[src1];
 #pragma unroll
       for (int q = 0; q < 9; ++q) d1[q] = a.in[q][src1];
     }
