@@ -851,7 +851,7 @@ __global__ void __launch_bounds__(kT, 768 / kT) kb_step(BStepArgs a) {
         }
         case BP_GATHER: {
           const int64_t cbase = a.reps[rep].coff;
-          for (int64_t cl = e.y + wib; cl < e.z; cl += wpb) gather_cell32(a.g, cbase + cl, lane);
+          for (int64_t cl = e.y + wib; cl < e.z; cl += wpb) gather_cell32<2>(a.g, cbase + cl, lane);
           break;
         }
         case BP_RHS: {

@@ -249,6 +249,7 @@ struct Dsmc32Args {
   int max_ppc, bm_words, G, Kc, nchunks;
   int64_t ngroups;
   unsigned long long* counters;
+  unsigned long long* queue;  // next cell group to take (zero at launch)
   int* flags;
   float vh[3];             // PIC_DIST_PAPER: f_v scales at the call's time
   DLog lg;                 // decision log (mode 0: off)
@@ -420,6 +421,10 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
 }
 
 constexpr int kDsmcThreads = 128;
+// cell groups a warp takes from the launch's queue at a time: a cell's work
+// varies with its particle count, and a static split left the SMs idle
+// through the last warps' tails
+constexpr int kDsmcChunk = 8;
 
 // shared memory of one warp, in 32-bit words: bitmaps, lists, list lengths
 __host__ __device__ constexpr size_t dsmc32_smem_words(int bm_words) {
@@ -433,7 +438,6 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int64_t gwarp = (int64_t)blockIdx.x * wpb + wib;
-  const int64_t nwarps = (int64_t)gridDim.x * wpb;
   // per warp: the lanes' bitmaps [32][bm_words], their lists [kList][32]
   // and list lengths [32]
   uint32_t* wbm = smem + (size_t)wib * dsmc32_smem_words(a.bm_words);
@@ -451,7 +455,17 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
   const float mu0 = P.vmean[0], mu1 = P.vmean[1], mu2 = P.vmean[2];
   const float vs = P.vsig, ivs = P.inv_vsig, pref = P.src_pref;
 
-  for (int64_t grp = gwarp; grp < a.ngroups; grp += nwarps) {
+  int64_t gbase = 0;
+  int gk = kDsmcChunk;
+  for (;;) {
+    if (gk == kDsmcChunk) {
+      unsigned long long q = 0;
+      if (lane == 0) q = atomicAdd(a.queue, (unsigned long long)kDsmcChunk);
+      gbase = (int64_t)__shfl_sync(0xffffffffu, q, 0);
+      gk = 0;
+    }
+    const int64_t grp = gbase + gk++;
+    if (grp >= a.ngroups) break;  // warp-uniform
     const int64_t cell0 = grp * a.G;
     const int ncl = (int)min((int64_t)a.G, P.ncell - cell0);
     const int mycl = lane / a.Kc;
@@ -737,72 +751,61 @@ __device__ __forceinline__ bool grid_barrier32(unsigned int* bar, int* info, int
   return ok != 0;
 }
 
-// block total of a double-float partial in FP64 (thread 0 only; sh holds
-// at least 32 doubles)
-__device__ __forceinline__ double block_total_df(DF v, double* sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Block and grid totals of double-float partials, in double-float
+// arithmetic throughout: each warp sums by shuffles, then warp 0 sums the
+// warps' (or the blocks') values the same way, in a fixed order. A serial
+// chain of FP64 adds on one thread costs several microseconds per
+// iteration on this part's narrow FP64 pipe; FP32 pairs cost a few hundred
+// cycles. Results are valid in thread 0.
+__device__ __forceinline__ DF warp_total_df(DF v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
-  __syncthreads();
-  if (lane == 0) sh[w] = df_to_double(v);
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < nw; ++i) t += sh[i];
-  return t;
+  return v;
 }
 
-// two block totals at once (thread 0 only; sh holds at least 64 doubles)
-__device__ __forceinline__ void block_total_df2(DF u, DF v, double* sh, double* tu, double* tv) {
+// two block totals at once (sh holds at least 32 float4)
+__device__ __forceinline__ void block_total_df2(DF u, DF v, float4* sh, DF* tu, DF* tv) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    u = df_add(u, df_shfl_xor(u, off));
-    v = df_add(v, df_shfl_xor(v, off));
-  }
+  u = warp_total_df(u);
+  v = warp_total_df(v);
+  __syncthreads();  // sh is free
+  if (lane == 0) sh[w] = make_float4(u.hi, u.lo, v.hi, v.lo);
   __syncthreads();
-  if (lane == 0) {
-    sh[w] = df_to_double(u);
-    sh[32 + w] = df_to_double(v);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < nw; ++i) {
-      a += sh[i];
-      b += sh[32 + i];
-    }
-    *tu = a;
-    *tv = b;
-  }
-}
-
-// totals of two partial arrays in one pass, in every thread
-__device__ __forceinline__ void grid_total32x2(const double* pa, const double* pb, int m, double* sh, double* ta,
-                                               double* tb) {
-  const int lane = threadIdx.x & 31;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double a = 0.0, b = 0.0;
-    for (int i = lane; i < m; i += 32) {
-      a += ((volatile const double*)pa)[i];
-      b += ((volatile const double*)pb)[i];
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, off);
-      b += __shfl_xor_sync(0xffffffffu, b, off);
-    }
+  if (w == 0) {
+    const float4 e = lane < nw ? sh[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const DF a = warp_total_df(DF{e.x, e.y}), b = warp_total_df(DF{e.z, e.w});
     if (lane == 0) {
-      sh[0] = a;
-      sh[1] = b;
+      *tu = a;
+      *tv = b;
     }
   }
-  __syncthreads();
-  *ta = sh[0];
-  *tb = sh[1];
 }
 
+// a partial published by another block before a grid barrier, read at L2
+__device__ __forceinline__ DF ld_partial(const float2* p) {
+  float hi, lo;
+  asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(hi), "=f"(lo) : "l"(p) : "memory");
+  return DF{hi, lo};
+}
+
+// totals of two arrays of m block partials, by warp 0
+__device__ __forceinline__ void grid_total_df2(const float2* pa, const float2* pb, int m, DF* ta, DF* tb) {
+  if (threadIdx.x < 32) {
+    DF a{0.f, 0.f}, b{0.f, 0.f};
+    for (int i = threadIdx.x; i < m; i += 32) {
+      a = df_add(a, ld_partial(pa + i));
+      b = df_add(b, ld_partial(pb + i));
+    }
+    a = warp_total_df(a);
+    b = warp_total_df(b);
+    if (threadIdx.x == 0) {
+      *ta = a;
+      *tb = b;
+    }
+  }
+}
+
+// total of FP64 partials (another kernel's), in every thread
 __device__ __forceinline__ double grid_total32(const double* part, int m, double* sh) {
   const int lane = threadIdx.x & 31;
   __syncthreads();
@@ -844,7 +847,8 @@ __device__ __forceinline__ Nbr neighbours(int id, int n, int nn, int log2n) {
 }
 
 // FP32 vectors and stencil; inner products and the residual in double-float
-// per thread, FP64 across blocks. Chronopoulos-Gear form of CG: with
+// (per thread, across a block and across blocks), the scalar recurrences in
+// FP64 on thread 0 of each block. Chronopoulos-Gear form of CG: with
 // w = A r and s = A p carried by recurrence, (r, r) and (r, w) come from one
 // reduction, so an iteration needs two grid barriers (r complete before
 // the stencil; the partial sums published) instead of three. The iterates
@@ -853,7 +857,8 @@ __device__ __forceinline__ Nbr neighbours(int id, int n, int nn, int log2n) {
 constexpr int kCgThreads = 1024;
 
 __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
-  __shared__ double sh[72];
+  __shared__ double sh[1];
+  __shared__ float4 sh4[32];
   __shared__ float fscal[2];  // alpha, beta formed once per block by thread 0
   __shared__ int stop;
   // the others then wait for an arrival that never comes, until the bound
@@ -864,7 +869,14 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int G = gridDim.x;
   int ph = 0;
-  auto slot = [&](int q) { return a.red + (size_t)q * 2 * G; };
+  // block partials, double-buffered: slot q holds 2 G double-float values
+  auto slot = [&](int q) { return reinterpret_cast<float2*>(a.red) + (size_t)q * 2 * G; };
+  auto publish = [&](int q, DF u, DF v) {
+    if (threadIdx.x == 0) {
+      slot(q)[blockIdx.x] = make_float2(u.hi, u.lo);
+      slot(q)[G + blockIdx.x] = make_float2(v.hi, v.lo);
+    }
+  };
   float* const w = a.b;  // reused after the initial residual
   float* const s = a.q;
 
@@ -881,16 +893,21 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
     bb_loc = df_fma(bb_loc, bv, bv);
   }
   {
-    const double s1 = block_total_df(rr_loc, sh);
-    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s1;
-    const double s2 = block_total_df(bb_loc, sh);
-    if (threadIdx.x == 0) slot(ph)[G + blockIdx.x] = s2;
+    DF u, v;
+    block_total_df2(rr_loc, bb_loc, sh4, &u, &v);
+    publish(ph, u, v);
   }
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-  double gamma = grid_total32(slot(ph), G, sh);
-  const double bb = grid_total32(slot(ph) + G, G, sh);
+  // the scalars below are meaningful in thread 0 only
+  double gamma = 0.0, bb = 0.0;
+  {
+    DF u, v;
+    grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+    gamma = df_to_double(u);
+    bb = df_to_double(v);
+  }
   ph ^= 1;
-  const double thresh = a.tol * sqrt(bb);
+  const double thresh = a.tol * sqrt(bb), thresh2 = thresh * thresh;
   int it = 0, status = 0;
   double alpha = 0.0;
   // w = A r and delta = (r, w) for the first step
@@ -904,16 +921,22 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
       w[id] = wv;
       rw_loc = df_fma(rw_loc, rc, wv);
     }
-    const double s1 = block_total_df(rw_loc, sh);
-    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s1;
+    DF u, v;
+    block_total_df2(rw_loc, DF{0.f, 0.f}, sh4, &u, &v);
+    publish(ph, u, v);
   }
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-  double delta = grid_total32(slot(ph), G, sh);
+  double delta = 0.0;
+  {
+    DF u, v;
+    grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+    delta = df_to_double(u);
+  }
   ph ^= 1;
   double beta = 0.0;
   while (true) {
     if (threadIdx.x == 0) {
-      stop = (bb == 0.0 || sqrt(gamma) <= thresh) ? 1 : (it >= a.maxit ? 2 : 0);
+      stop = (bb == 0.0 || gamma <= thresh2) ? 1 : (it >= a.maxit ? 2 : 0);
       if (!stop) {
         const double den = it == 0 ? delta : delta - beta * gamma / alpha;
         alpha = gamma / den;
@@ -925,23 +948,14 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
     if (stop == 1) break;
     if (stop == 2) { status = 1; break; }
     const float al = fscal[0], be = fscal[1];
-    if (it == 0) {
-      for (int id = t0; id < m; id += stride) {
-        const float pv = a.r[id], sv = w[id];
-        a.p[id] = pv;
-        s[id] = sv;
-        a.x[id] = fmaf(al, pv, a.x[id]);
-        a.r[id] = fmaf(-al, sv, pv);
-      }
-    } else {
-      for (int id = t0; id < m; id += stride) {
-        const float pv = fmaf(be, a.p[id], a.r[id]);
-        const float sv = fmaf(be, s[id], w[id]);
-        a.p[id] = pv;
-        s[id] = sv;
-        a.x[id] = fmaf(al, pv, a.x[id]);
-        a.r[id] = fmaf(-al, sv, a.r[id]);
-      }
+    for (int id = t0; id < m; id += stride) {
+      const float rv = a.r[id], wv = w[id];
+      const float pn = it == 0 ? rv : fmaf(be, a.p[id], rv);
+      const float sn = it == 0 ? wv : fmaf(be, s[id], wv);
+      a.p[id] = pn;
+      s[id] = sn;
+      a.x[id] = fmaf(al, pn, a.x[id]);
+      a.r[id] = fmaf(-al, sn, rv);
     }
     if (!grid_barrier32(a.bar, a.info, a.flags)) return;
     DF rr_l{0.f, 0.f}, rw_l{0.f, 0.f};
@@ -955,30 +969,37 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
       rw_l = df_fma(rw_l, rc, wv);
     }
     {
-      double s1 = 0.0, s2 = 0.0;
-      block_total_df2(rr_l, rw_l, sh, &s1, &s2);
-      if (threadIdx.x == 0) {
-        slot(ph)[blockIdx.x] = s1;
-        slot(ph)[G + blockIdx.x] = s2;
-      }
+      DF u, v;
+      block_total_df2(rr_l, rw_l, sh4, &u, &v);
+      publish(ph, u, v);
     }
     if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-    double gamma_new;
-    grid_total32x2(slot(ph), slot(ph) + G, G, sh, &gamma_new, &delta);
+    {
+      DF u, v;
+      grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+      if (threadIdx.x == 0) {
+        const double gamma_new = df_to_double(u);
+        delta = df_to_double(v);
+        beta = gamma_new / gamma;
+        gamma = gamma_new;
+      }
+    }
     ph ^= 1;
     ++it;
-    beta = gamma_new / gamma;
-    gamma = gamma_new;
   }
   DF xs{0.f, 0.f};
   for (int id = t0; id < m; id += stride) xs = df_add_f(xs, a.x[id]);
   {
-    const double s1 = block_total_df(xs, sh);
-    if (threadIdx.x == 0) slot(ph)[blockIdx.x] = s1;
+    DF u, v;
+    block_total_df2(xs, DF{0.f, 0.f}, sh4, &u, &v);
+    publish(ph, u, v);
   }
   if (!grid_barrier32(a.bar, a.info, a.flags)) return;
-  const double xsum = grid_total32(slot(ph), G, sh);  // every thread calls it: it synchronises the block
-  if (threadIdx.x == 0) fscal[0] = (float)(xsum / (double)m);
+  {
+    DF u, v;
+    grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+    if (threadIdx.x == 0) fscal[0] = (float)(df_to_double(u) / (double)m);
+  }
   __syncthreads();
   const float mean_x = fscal[0];
   ph ^= 1;
@@ -1239,10 +1260,13 @@ cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate, double t_src) 
   a.nchunks = (c->P.K + c->dsmc_Kc - 1) / c->dsmc_Kc;
   a.ngroups = c->dsmc_groups;
   a.counters = c->counters;
+  a.queue = c->dsmc_queue;
   a.flags = c->flags;
   a.lg = DLog{c->dlog, c->dlog_n, (long long)c->dlog_cap, c->dlog ? c->dlog_mode : 0};
   a.hist = c->hist_row;
   prof_begin(c);
+  const cudaError_t eq = cudaMemsetAsync(c->dsmc_queue, 0, 8, c->stream);
+  if (eq != cudaSuccess) return eq;
   if (c->P.verify || a.lg.mode == PIC_DLOG_ALL)
     k_dsmc32<true><<<c->dsmc_grid, kDsmcThreads, c->dsmc_smem, c->stream>>>(a);
   else

@@ -299,10 +299,77 @@ __device__ __forceinline__ void store_corners_fixed(const long long* acc, int la
   }
 }
 
+// C chunks of 32 arrival slots of one cell (C * 32 >= cnt) held in
+// registers: each particle's in-cell rank counted against every pid of the
+// cell, then the particle copied to slot s + rank and its CIC weights
+// added. Up to two chunks load the particle data with the pids (one memory
+// round trip); wider cells load it after the count, to bound the registers.
+template <int C>
+__device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t cell, int32_t s, int32_t cnt, int lane,
+                                                const CicFixed& fx, long long* acc) {
+  constexpr bool kPre = C <= 2;
+  int32_t src[C];
+  uint32_t p[C];
+  float d[kPre ? C : 1][9];
+#pragma unroll
+  for (int k = 0; k < C; ++k) {
+    const int32_t e = 32 * k + lane;
+    src[k] = 0;
+    p[k] = 0xFFFFFFFFu;
+    if (e < cnt) {
+      src[k] = a.perm[s + e];
+      if (a.spid) p[k] = a.spid[s + e];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < C; ++k)
+    if (32 * k + lane < cnt) {
+      if (!a.spid) p[k] = a.pid_in[src[k]];
+      if constexpr (kPre) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[k][q] = a.in[q][src[k]];
+      }
+    }
+  int r[C];
+#pragma unroll
+  for (int k = 0; k < C; ++k) r[k] = 0;
+  if (C == 1) {
+    for (int l = 0; l < cnt; ++l) r[0] += __shfl_sync(0xffffffffu, p[0], l) < p[0] ? 1 : 0;
+  } else {
+    // unused slots hold pid 0xFFFFFFFF, above every particle's
+    for (int l = 0; l < 32; ++l) {
+      uint32_t x[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) x[j] = __shfl_sync(0xffffffffu, p[j], l);
+#pragma unroll
+      for (int k = 0; k < C; ++k)
+#pragma unroll
+        for (int j = 0; j < C; ++j) r[k] += x[j] < p[k] ? 1 : 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < C; ++k)
+    if (32 * k + lane < cnt) {
+      const int32_t dst = s + r[k];
+      float* dk = d[kPre ? k : 0];
+      if constexpr (!kPre) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dk[q] = a.in[q][src[k]];
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) a.out[q][dst] = dk[q];
+      a.pid_out[dst] = p[k];
+      a.cell_out[dst] = (int32_t)cell;
+      cic_add_fixed(acc, dk[0], dk[1], dk[2], fx);
+    }
+}
+
 // One cell of the sort gather (a warp): the cell's particles in ascending
 // pid order (their in-cell rank by pid), copied to the destination arrays,
 // and the cell's eight CIC corner partials. Cells of big_lo < count <=
-// kMaxBlockSort are left to the block sort.
+// kMaxBlockSort are left to the block sort. Cells of up to 32 kRegChunks
+// particles take the register path, larger ones the chunked pairwise count.
+template <int kRegChunks = 4>
 __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cell, int lane) {
   const int32_t s = a.start[cell];
   const int32_t cnt = a.start[cell + 1] - s;
@@ -311,55 +378,15 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
   long long acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0;
-  if (cnt <= 64) {
-    // both 32-element chunks in registers; the particle data is loaded
-    // with the pids (one memory round trip), then ranked in one pass
-    int32_t src0 = 0, src1 = 0;
-    uint32_t p0 = 0xFFFFFFFFu, p1 = 0xFFFFFFFFu;
-    float d0[9], d1[9];
-    const bool h0 = lane < cnt, h1 = lane + 32 < cnt;
-    if (h0) src0 = a.perm[s + lane];
-    if (h1) src1 = a.perm[s + 32 + lane];
-    if (a.spid) {
-      if (h0) p0 = a.spid[s + lane];
-      if (h1) p1 = a.spid[s + 32 + lane];
-    }
-    if (h0) {
-      if (!a.spid) p0 = a.pid_in[src0];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) d0[q] = a.in[q][src0];
-    }
-    if (h1) {
-      if (!a.spid) p1 = a.pid_in[src1];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) d1[q] = a.in[q][src1];
-    }
-    int r0 = 0, r1 = 0;
-    if (cnt <= 32) {
-      for (int l = 0; l < cnt; ++l) r0 += __shfl_sync(0xffffffffu, p0, l) < p0 ? 1 : 0;
-    } else {
-      for (int l = 0; l < 32; ++l) {
-        const uint32_t x0 = __shfl_sync(0xffffffffu, p0, l), x1 = __shfl_sync(0xffffffffu, p1, l);
-        r0 += (x0 < p0) + (x1 < p0);
-        r1 += (x0 < p1) + (x1 < p1);
-      }
-    }
-    if (h0) {
-      const int32_t dst = s + r0;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) a.out[q][dst] = d0[q];
-      a.pid_out[dst] = p0;
-      a.cell_out[dst] = (int32_t)cell;
-      cic_add_fixed(acc, d0[0], d0[1], d0[2], fx);
-    }
-    if (h1) {
-      const int32_t dst = s + r1;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) a.out[q][dst] = d1[q];
-      a.pid_out[dst] = p1;
-      a.cell_out[dst] = (int32_t)cell;
-      cic_add_fixed(acc, d1[0], d1[1], d1[2], fx);
-    }
+  const int32_t nch = (cnt + 31) >> 5;  // warp-uniform
+  if (nch <= 1) {
+    gather_chunks32<1>(a, cell, s, cnt, lane, fx, acc);
+  } else if (nch == 2) {
+    gather_chunks32<2>(a, cell, s, cnt, lane, fx, acc);
+  } else if (kRegChunks >= 3 && nch == 3) {
+    if constexpr (kRegChunks >= 3) gather_chunks32<3>(a, cell, s, cnt, lane, fx, acc);
+  } else if (kRegChunks >= 4 && nch == 4) {
+    if constexpr (kRegChunks >= 4) gather_chunks32<4>(a, cell, s, cnt, lane, fx, acc);
   } else {
     for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
       const int32_t e = e0 + lane;
@@ -367,11 +394,15 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
       uint32_t mp = 0xFFFFFFFFu;
       if (e < cnt) {
         src = a.perm[s + e];
-        mp = a.pid_in[src];
+        mp = a.pid_in[src];  // spid is pid_out: rewritten by earlier chunks
       }
       int32_t r = 0;
       for (int32_t f0 = 0; f0 < cnt; f0 += 32) {
-        const uint32_t other = f0 == e0 ? mp : ((f0 + lane < cnt) ? a.pid_in[a.perm[s + f0 + lane]] : 0xFFFFFFFFu);
+        uint32_t other = mp;
+        if (f0 != e0) {
+          const int32_t f = f0 + lane;
+          other = f < cnt ? a.pid_in[a.perm[s + f]] : 0xFFFFFFFFu;
+        }
         const int lim = min(32, cnt - f0);
         for (int l = 0; l < lim; ++l) r += __shfl_sync(0xffffffffu, other, l) < mp ? 1 : 0;
       }

@@ -349,6 +349,7 @@ void for_each_buffer(pic_ctx* c, F f) {
   f((void**)&c->cg_info, 64);
   f((void**)&c->cg_res, 64);
   f((void**)&c->counters, 8 * 8);
+  f((void**)&c->dsmc_queue, 64);
   f((void**)&c->step_hist, (size_t)kHistSteps * 4 * 8);
   f((void**)&c->flags, 64);
   f((void**)&c->err_part, (size_t)c->err_blocks * 14 * 8);

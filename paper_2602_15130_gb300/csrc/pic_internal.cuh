@@ -630,6 +630,7 @@ struct pic_ctx {
   size_t dsmc_smem;
   pic::AdjointBuffers* adj;      // pathwise-adjoint working set, allocated on first use
   unsigned long long* counters;  // n_cand, n_coll, n_gmax, n_tie, n_floor_tie
+  unsigned long long* dsmc_queue;  // next cell group of the FP32 collision kernel (zeroed per launch)
   // decision log of the collision calls (pic_set_decision_log)
   // per-step record since pic_reset_stats: [kHistSteps][4] (CG iterations,
   // candidates, collisions, g > g_max); hist_row is the current step's row
