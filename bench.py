@@ -13,7 +13,7 @@ collision and g > g_max counts (its per-step history), which the line
 carries. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload precision|refine4|refineL|smallest|batched|batchedN|adjoint]
+                  [--workload precision|precisionN|refine4|refineL|smallest|batched|batchedN|adjoint]
                   [--form mixed|fp64] [--no-fp64-beside] [--no-cpu-baseline]
 
 The end-to-end figure (key "e2e") runs pic_set_state from pinned host
@@ -49,6 +49,10 @@ def workload(name: str) -> dict:
 
     if name == "precision":
         return W.precision_form()
+    if name.startswith("precision"):
+        # "precisionN": the same workload on N^3 cells (64 particles per cell)
+        n = int(name[9:])
+        return W.precision_form(n=n, n_particles=64 * n ** 3)
     if name.startswith("batched"):
         # "batched": the 256-replicate study; "batchedN": its first N replicates
         return {"batch": W.batched(int(name[7:]) if name[7:] else 256)}

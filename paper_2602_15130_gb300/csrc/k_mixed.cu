@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_store_state32_by_pid(StoreByPid32A
   }
 }
 
-constexpr int kGatherThreads = 256;
+constexpr int kGatherThreads = 128;
 
 __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a) {
   const int lane = threadIdx.x & 31;
@@ -582,6 +582,47 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
 }
 
 // ------------------------------------------------------------ kick/drift --
+// The Lorentz term dt q/m (E + E^M) of Eq. velocity_verlet at a particle of
+// cell ci with offsets o: E trilinear from the cell's eight corner nodes
+// (corner q + 2 b + 4 c at i + q, j + b, k + c), the manufactured field
+// analytic. Every kernel that forms the term calls this one function, so a
+// stored term and a recomputed one agree bit for bit.
+__device__ __forceinline__ void lorentz32(const ParamsF& P, const TimeTermsF& tE, const int* ci, const float* o,
+                                          const float4* corner, float* L) {
+  const float wx[2] = {1.f - o[0], o[0]}, wy[2] = {1.f - o[1], o[1]}, wz[2] = {1.f - o[2], o[2]};
+  float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll
+  for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float w = wx[q] * wy[b] * wz[cc];
+        const float4 en = corner[q + 2 * b + 4 * cc];
+        e0 = fmaf(w, en.x, e0);
+        e1 = fmaf(w, en.y, e1);
+        e2 = fmaf(w, en.z, e2);
+      }
+  float s0, c0, s1, c1, s2, c2;
+  sincospif(2.f * (((float)ci[0] + o[0]) * P.h - P.phi_shift[0]), &s0, &c0);
+  sincospif(2.f * (((float)ci[1] + o[1]) * P.h - P.phi_shift[1]), &s1, &c1);
+  sincospif(2.f * (((float)ci[2] + o[2]) * P.h - P.phi_shift[2]), &s2, &c2);
+  const float amp = tE.em_amp, k = P.dt_qm;
+  L[0] = k * (e0 + amp * c0 * s1 * s2);
+  L[1] = k * (e1 + amp * s0 * c1 * s2);
+  L[2] = k * (e2 + amp * s0 * s1 * c2);
+}
+
+// node index of corner q + 2 b + 4 c of cell ci (periodic)
+__device__ __forceinline__ int corner_node(const ParamsF& P, const int* ci, int corner) {
+  const int n = P.n;
+  const int q = corner & 1, b = (corner >> 1) & 1, cc = corner >> 2;
+  const int i = ci[0] + q == n ? 0 : ci[0] + q;
+  const int j = ci[1] + b == n ? 0 : ci[1] + b;
+  const int k = ci[2] + cc == n ? 0 : ci[2] + cc;
+  return i + n * j + P.nn * k;
+}
+
 struct Kick32Args {
   ParamsF P;
   const int32_t* cell;
@@ -606,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const ParamsF& P = a.P;
   if (j >= P.np) return;
-  const int n = P.n, nn = P.nn;
+  const int n = P.n;
   // every independent load first (memory-level parallelism), then the
   // dependent field gather
   const int c = a.cell[j];
@@ -628,32 +669,10 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   if (a.lor_mode == 2) {
     L[0] = a.L0[j]; L[1] = a.L1[j]; L[2] = a.L2[j];
   } else {
-    const int i1 = ci[0] + 1 == n ? 0 : ci[0] + 1, j1 = ci[1] + 1 == n ? 0 : ci[1] + 1,
-              k1 = ci[2] + 1 == n ? 0 : ci[2] + 1;
-    const int ii[2] = {ci[0], i1}, jj[2] = {ci[1] * n, j1 * n}, kk[2] = {ci[2] * nn, k1 * nn};
-    const float wx[2] = {1.f - o[0], o[0]}, wy[2] = {1.f - o[1], o[1]}, wz[2] = {1.f - o[2], o[2]};
-    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+    float4 corner[8];
 #pragma unroll
-    for (int cc = 0; cc < 2; ++cc)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int node = ii[q] + jj[b] + kk[cc];
-          const float w = wx[q] * wy[b] * wz[cc];
-          const float4 en = __ldg(a.E4 + node);
-          e0 = fmaf(w, en.x, e0);
-          e1 = fmaf(w, en.y, e1);
-          e2 = fmaf(w, en.z, e2);
-        }
-    float s0, c0, s1, c1, s2, c2;
-    sincospif(2.f * (((float)ci[0] + o[0]) * P.h - P.phi_shift[0]), &s0, &c0);
-    sincospif(2.f * (((float)ci[1] + o[1]) * P.h - P.phi_shift[1]), &s1, &c1);
-    sincospif(2.f * (((float)ci[2] + o[2]) * P.h - P.phi_shift[2]), &s2, &c2);
-    const float amp = a.tE.em_amp, k = P.dt_qm;
-    L[0] = k * (e0 + amp * c0 * s1 * s2);
-    L[1] = k * (e1 + amp * s0 * c1 * s2);
-    L[2] = k * (e2 + amp * s0 * s1 * c2);
+    for (int q = 0; q < 8; ++q) corner[q] = __ldg(a.E4 + corner_node(P, ci, q));
+    lorentz32(P, a.tE, ci, o, corner, L);
     if (a.lor_mode == 1) {
       a.L0[j] = L[0]; a.L1[j] = L[1]; a.L2[j] = L[2];
     }
@@ -699,6 +718,61 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
   const int32_t k = ci[0] + n * (ci[1] + n * ci[2]);
   a.key[j] = k;
   a.rank[j] = cell_slot(a.count, k);
+}
+
+// The closing half kick of a step (Eq. velocity_verlet, second half) by
+// cells: one warp per cell of the sorted order loads the cell's eight
+// corner values of E once into shared memory, then its lanes take the
+// cell's particles. The per-particle arithmetic is k_kick32's (lorentz32),
+// and the term is stored for the next step's first half kick.
+constexpr int kCloseThreads = 128;
+
+struct Close32Args {
+  ParamsF P;
+  int64_t ncell;
+  const int32_t* start;
+  const float *o0, *o1, *o2;
+  float *v0, *v1, *v2;
+  const float *dv0, *dv1, *dv2;  // v + (<dv> - <dv^M>)/2 from the collision call, or nullptr: read v
+  const float *m0, *m1, *m2;     // PIC_DIST_PAPER: tau
+  const float4* E4;
+  float *L0, *L1, *L2;
+  TimeTermsF tE;
+};
+
+template <bool kPaper>
+__global__ void __launch_bounds__(kCloseThreads) k_close32(Close32Args a) {
+  __shared__ float4 sE[kCloseThreads / 32][8];
+  const ParamsF& P = a.P;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t cell = gw; cell < a.ncell; cell += nw) {
+    const int32_t s = a.start[cell], e = a.start[cell + 1];
+    int ci[3];
+    cell_ijk(P, (int)cell, ci);
+    __syncwarp();  // the previous cell's corners are no longer read
+    if (lane < 8) sE[wib][lane] = __ldg(a.E4 + corner_node(P, ci, lane));
+    __syncwarp();
+    for (int32_t j = s + lane; j < e; j += 32) {
+      const float o[3] = {a.o0[j], a.o1[j], a.o2[j]};
+      float v[3];
+      if (a.dv0) { v[0] = a.dv0[j]; v[1] = a.dv1[j]; v[2] = a.dv2[j]; }
+      else { v[0] = a.v0[j]; v[1] = a.v1[j]; v[2] = a.v2[j]; }
+      float L[3];
+      lorentz32(P, a.tE, ci, o, sE[wib], L);
+      a.L0[j] = L[0]; a.L1[j] = L[1]; a.L2[j] = L[2];
+      if (kPaper) {
+        const float vm[3] = {a.m0[j], a.m1[j], a.m2[j]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, (L[d] + 0.f) + P.dt * (vm[d] * a.tE.dvh[d]), v[d]);
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[d] = fmaf(0.5f, L[d] + 0.f, v[d]);
+      }
+      a.v0[j] = v[0]; a.v1[j] = v[1]; a.v2[j] = v[2];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- CG32 --
@@ -1216,9 +1290,11 @@ cudaError_t launch_gather32(pic_ctx* c) {
   g.corner = c->corner;
   g.big_lo = big_cell_threshold(g.ncell, c->P.np);
   g.spid = c->pid[o];  // written in arrival order by the scatter
+  // one warp per cell: blocks of consecutive cells, handed to the SMs as
+  // they free up (measured faster than resident warps walking the cells
+  // with a grid stride)
   int64_t blocks = (c->P.ncell * 32 + kGatherThreads - 1) / kGatherThreads;
-  const int64_t cap = (int64_t)c->num_sms * 16;
-  if (blocks > cap) blocks = cap;
+  if (blocks > INT_MAX) blocks = INT_MAX;  // the grid-stride loop takes the rest
   prof_begin(c);
   k_sort_gather32<<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
   if (g.big_lo < INT_MAX) {
@@ -1299,7 +1375,26 @@ cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, dou
   a.rank = c->rank;
   a.count = c->count;
   prof_begin(c);
-  if (c->P.dist == PIC_DIST_PAPER)
+  if (!drift) {
+    // the closing half kick: by cells
+    Close32Args k;
+    k.P = a.P;
+    k.ncell = c->P.ncell;
+    k.start = c->start;
+    k.o0 = a.o0; k.o1 = a.o1; k.o2 = a.o2;
+    k.v0 = a.v0; k.v1 = a.v1; k.v2 = a.v2;
+    k.dv0 = a.dv0; k.dv1 = a.dv1; k.dv2 = a.dv2;
+    k.m0 = a.m0; k.m1 = a.m1; k.m2 = a.m2;
+    k.E4 = a.E4;
+    k.L0 = a.L0; k.L1 = a.L1; k.L2 = a.L2;
+    k.tE = a.tE;
+    int64_t blocks = (c->P.ncell * 32 + kCloseThreads - 1) / kCloseThreads;
+    if (blocks > INT_MAX) blocks = INT_MAX;
+    if (c->P.dist == PIC_DIST_PAPER)
+      k_close32<true><<<(int)blocks, kCloseThreads, 0, c->stream>>>(k);
+    else
+      k_close32<false><<<(int)blocks, kCloseThreads, 0, c->stream>>>(k);
+  } else if (c->P.dist == PIC_DIST_PAPER)
     k_kick32<2><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
   else if (c->P.verify & PIC_VERIFY_ISOLATE)
     k_kick32<1><<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);

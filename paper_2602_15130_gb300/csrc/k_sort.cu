@@ -368,9 +368,9 @@ cudaError_t launch_sort(pic_ctx* c) {
   g.corner = c->corner;
   g.big_lo = big_cell_threshold(m, c->P.np);
   const int64_t warps = m;
+  // one warp per cell, blocks handed out as SMs free up
   int64_t blocks = (warps * 32 + kGatherThreads - 1) / kGatherThreads;
-  const int64_t cap = (int64_t)c->num_sms * 16;
-  if (blocks > cap) blocks = cap;
+  if (blocks > INT_MAX) blocks = INT_MAX;  // the grid-stride loop takes the rest
   prof_begin(c);
   k_sort_gather<<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
   if (g.big_lo < INT_MAX) {
