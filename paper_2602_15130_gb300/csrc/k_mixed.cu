@@ -25,18 +25,46 @@ struct Sample32Args {
   Params P;
   TimeTerms tt;
   const double *xs, *vs;  // optional caller state (pid order, [N][3] each; device or mapped host)
-  const float *vin0, *vin1, *vin2;  // optional v^M (tau for the paper's f_v) in pid order
+  // optional v^M (tau for the paper's f_v) to keep: a context's sorted
+  // arrays, read for pid i at vslot[i] (the inverse sort permutation)
+  const int32_t* vslot;
+  const float *vin0, *vin1, *vin2;
   int32_t* cell;
   float *o0, *o1, *o2, *v0, *v1, *v2, *m0, *m1, *m2;
   uint32_t* pid;
 };
 
+// A caller's state ([N][3] rows, in place in pinned host memory over
+// NVLink-C2C or in device memory) is read by the block in contiguous spans
+// into shared memory (16-byte loads where the rows allow), so each byte
+// crosses the link once; a thread's three components are then three
+// shared-memory reads.
 __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ __align__(16) double sxs[3 * kThreads], svs[3 * kThreads];
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int64_t i = base + threadIdx.x;
   const Params& P = a.P;
+  if (a.xs) {
+    const int64_t rows = P.np - base < kThreads ? P.np - base : kThreads;
+    const double* gx = a.xs + 3 * base;
+    const double* gv = a.vs + 3 * base;
+    if (rows == kThreads && ((reinterpret_cast<uintptr_t>(gx) | reinterpret_cast<uintptr_t>(gv)) & 15) == 0) {
+      for (int k = threadIdx.x; k < 3 * kThreads / 2; k += kThreads) {
+        reinterpret_cast<double2*>(sxs)[k] = reinterpret_cast<const double2*>(gx)[k];
+        reinterpret_cast<double2*>(svs)[k] = reinterpret_cast<const double2*>(gv)[k];
+      }
+    } else {
+      for (int64_t k = threadIdx.x; k < 3 * rows; k += kThreads) {
+        sxs[k] = gx[k];
+        svs[k] = gv[k];
+      }
+    }
+    __syncthreads();
+  }
   if (i >= P.np) return;
   double xi[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  const bool given_vm = a.vin0 != nullptr;
+  const bool given_vm = a.vslot != nullptr;
+  const int32_t vj = given_vm ? a.vslot[i] : 0;
   if (!a.xs || !given_vm) {
     const U4 b0 = sample_block(P, (uint64_t)i, 0), b1 = sample_block(P, (uint64_t)i, 1),
              b2 = sample_block(P, (uint64_t)i, 2);
@@ -51,12 +79,12 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
     // the paper's f_v: the v^M array holds tau, v^M(t) = vh(t) tau; a state
     // loaded into a context that already holds one keeps its v^M values
     if (given_vm)
-      vm[d] = (double)vin[d][i];
+      vm[d] = (double)vin[d][vj];
     else
       vm[d] = paper ? tau_inv(xi[3 + d]) : P.vmean[d] + P.vsig * normcdfinv(xi[3 + d]);
     if (a.xs) {
-      x[d] = a.xs[3 * i + d];
-      v[d] = a.vs[3 * i + d];
+      x[d] = sxs[3 * threadIdx.x + d];
+      v[d] = svs[3 * threadIdx.x + d];
     } else if (paper) {
       x[d] = wrap_unit(xm_solve_gen(a.tt, d, xi[d], &s, &cc));
       v[d] = vm[d] * a.tt.vh[d];
@@ -149,7 +177,7 @@ struct StoreByPid32Args {
 };
 
 __global__ void __launch_bounds__(kThreads) k_store_state32_by_pid(StoreByPid32Args a) {
-  __shared__ double sx[3 * kThreads], sv[3 * kThreads];
+  __shared__ __align__(16) double sx[3 * kThreads], sv[3 * kThreads];
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int t = threadIdx.x;
   if (base + t < a.np) {
@@ -163,9 +191,18 @@ __global__ void __launch_bounds__(kThreads) k_store_state32_by_pid(StoreByPid32A
   }
   __syncthreads();
   const int64_t rows = a.np - base < kThreads ? a.np - base : kThreads;
-  for (int64_t k = t; k < 3 * rows; k += kThreads) {
-    a.x[3 * base + k] = sx[k];
-    a.v[3 * base + k] = sv[k];
+  double* gx = a.x + 3 * base;
+  double* gv = a.v + 3 * base;
+  if (rows == kThreads && ((reinterpret_cast<uintptr_t>(gx) | reinterpret_cast<uintptr_t>(gv)) & 15) == 0) {
+    for (int k = t; k < 3 * kThreads / 2; k += kThreads) {
+      reinterpret_cast<double2*>(gx)[k] = reinterpret_cast<const double2*>(sx)[k];
+      reinterpret_cast<double2*>(gv)[k] = reinterpret_cast<const double2*>(sv)[k];
+    }
+  } else {
+    for (int64_t k = t; k < 3 * rows; k += kThreads) {
+      gx[k] = sx[k];
+      gv[k] = sv[k];
+    }
   }
 }
 
@@ -1208,44 +1245,17 @@ __global__ void __launch_bounds__(kThreads) k_store_dv32(StoreDv32Args a) {
 }  // namespace
 
 // ============================================================== launches ==
-// v^M (tau) of the current state from sorted order into pid order (a free
-// per-particle scratch), for a state load that keeps them
-struct VmPid32Args {
-  int64_t np;
-  const uint32_t* pid;
-  const float *m0, *m1, *m2;
-  float *o0, *o1, *o2;
-};
-__global__ void __launch_bounds__(kThreads) k_vm_to_pid32(VmPid32Args a) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.np) return;
-  const uint32_t p = a.pid[j];
-  a.o0[p] = a.m0[j]; a.o1[p] = a.m1[j]; a.o2[p] = a.m2[j];
-}
-
-cudaError_t launch_vm_to_pid32(pic_ctx* c, float* const* out) {
-  VmPid32Args a;
-  a.np = c->P.np;
-  const int b = c->cur;
-  a.pid = c->pid[b];
-  a.m0 = c->vmf[b][0]; a.m1 = c->vmf[b][1]; a.m2 = c->vmf[b][2];
-  a.o0 = out[0]; a.o1 = out[1]; a.o2 = out[2];
-  prof_begin(c);
-  k_vm_to_pid32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
-  prof_end(c, KC_OTHER);
-  c->launches++;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v, float* const* vm_in) {
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v, const int32_t* vm_slot,
+                            float* const* vm_src) {
   Sample32Args a;
   a.P = c->P;
   a.tt = time_terms(c->P, t0);
   a.xs = x;
   a.vs = v;
-  a.vin0 = vm_in ? vm_in[0] : nullptr;
-  a.vin1 = vm_in ? vm_in[1] : nullptr;
-  a.vin2 = vm_in ? vm_in[2] : nullptr;
+  a.vslot = vm_slot;
+  a.vin0 = vm_slot ? vm_src[0] : nullptr;
+  a.vin1 = vm_slot ? vm_src[1] : nullptr;
+  a.vin2 = vm_slot ? vm_src[2] : nullptr;
   const int b = c->cur;
   a.cell = c->cell32[b];
   a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
@@ -1488,17 +1498,21 @@ cudaError_t launch_store_state32(pic_ctx* c, double* xv, int32_t* cell_of_pid) {
 // x, v [N_p][3] in pid order written in place (device or mapped pinned host
 // memory, 8-byte aligned); the inverse permutation goes into the sort's
 // free permutation buffer
-cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {
-  const int b = c->cur;
+cudaError_t launch_inv_perm32(pic_ctx* c) {
   InvPerm32Args ia;
   ia.np = c->P.np;
-  ia.pid = c->pid[b];
+  ia.pid = c->pid[c->cur];
   ia.slot = c->perm;
   prof_begin(c);
   k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->stream>>>(ia);
   prof_end(c, KC_OTHER);
   c->launches++;
-  cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {
+  const int b = c->cur;
+  cudaError_t e = launch_inv_perm32(c);
   if (e != cudaSuccess) return e;
   StoreByPid32Args a;
   a.np = c->P.np;

@@ -892,12 +892,18 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
   CK(restart_history(c));
   if (c->mixed) {
     // v^M is a per-particle constant (tau for the paper's f_v): a context that
-    // already holds a state keeps its values (into pid order through the
-    // free collision-term arrays) instead of re-deriving them from xi in FP64
-    const bool keep_vm = c->sampled;
-    if (keep_vm) CK(launch_vm_to_pid32(c, c->dvf));
-    c->cur = 0;
-    CK(launch_sample32(c, time_at(c, (double)step), xs, vs, keep_vm ? c->dvf : nullptr));
+    // already holds a state keeps its values, read through the inverse sort
+    // permutation by the load into the other buffer, instead of re-deriving
+    // them from xi in FP64
+    if (c->sampled) {
+      CK(launch_inv_perm32(c));
+      const int src = c->cur;
+      c->cur = 1 - src;
+      CK(launch_sample32(c, time_at(c, (double)step), xs, vs, c->perm, c->vmf[src]));
+    } else {
+      c->cur = 0;
+      CK(launch_sample32(c, time_at(c, (double)step), xs, vs));
+    }
   } else {
     c->cur = 0;
     CK(launch_load_state(c, xs, vs, time_at(c, (double)step)));

@@ -761,10 +761,11 @@ cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm);
 cudaError_t launch_scan_scatter(pic_ctx* c);   // scan of counts + scatter into perm
 cudaError_t launch_err_final(pic_ctx* c, int nblocks);
 // precision form
-// vm_in: v^M (tau) in pid order to keep instead of recomputing them (state loads)
+// vm_slot, vm_src: v^M (tau) to keep instead of recomputing them (state
+// loads), read from the sorted arrays vm_src at the inverse permutation
 cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v,
-                           float* const* vm_in = nullptr);
-cudaError_t launch_vm_to_pid32(pic_ctx* c, float* const* out);
+                           const int32_t* vm_slot = nullptr, float* const* vm_src = nullptr);
+cudaError_t launch_inv_perm32(pic_ctx* c);  // c->perm[pid] = slot of pid in the current order
 cudaError_t launch_keys32(pic_ctx* c);
 cudaError_t launch_gather32(pic_ctx* c);
 cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate_source, double t_src);
