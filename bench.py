@@ -140,9 +140,10 @@ def measured_peaks() -> dict:
 # once, and each CG iteration moves about 28 B (FP32) or 56 B (FP64) per
 # node. "impl": the arrays this implementation's kernels read and write once
 # (for example the precision-form drift launch: cell, three offsets, three
-# velocities, three v^M, pid, three collision and three Lorentz terms in;
-# three offsets, three velocities, key and slot out: 100 B; the closing kick
-# 64 B).
+# velocities after the collision half kick, three v^M, pid and three Lorentz
+# terms in; three offsets, three velocities, key and slot out: 88 B; the
+# closing kick, by cells: three offsets and three velocities in, three
+# velocities and three Lorentz terms out: 48 B).
 BYTES_PER_UNIT = {
     "fp64": {
         "method": {"kick_drift": 104.0, "sort_gather_deposit": 208.0 + 24.0, "cg_efield": 56.0},
@@ -151,7 +152,7 @@ BYTES_PER_UNIT = {
     },
     "mixed": {
         "method": {"kick_drift": 56.0, "sort_gather_deposit": 112.0 + 16.0, "cg_efield": 28.0},
-        "impl": {"kick_drift": (100 + 64) / 2.0, "sort_gather_deposit": 88 + 64 / 32.0, "dsmc": 24.0,
+        "impl": {"kick_drift": (88 + 48) / 2.0, "sort_gather_deposit": 88 + 64 / 32.0, "dsmc": 24.0,
                  "sort": 12.0, "cg_efield": 44.0, "rhs": 8 * 8 + 8 + 4},
     },
 }

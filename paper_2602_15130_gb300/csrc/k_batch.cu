@@ -9,8 +9,8 @@
 //
 //  - sampling: binary search of the particle's replicate;
 //  - RHS: the node's replicate from rep_of_cell, FP64 manufactured terms;
-//  - CG: one block per replicate (largest first), block-level phases only
-//    (no grid-wide barriers), double-float inner products;
+//  - CG: a team of blocks per replicate (one per 16,384 nodes, at most 32)
+//    meeting at bounded per-replicate barriers, double-float inner products;
 //  - DSMC: a static list of (replicate, cell group) work items so warps of
 //    one launch serve replicates of different K and cell size;
 //  - kick/drift: per particle, the replicate of its cell.
@@ -143,10 +143,10 @@ __global__ void __launch_bounds__(kThreads) kb_rhs(BRhsArgs a) {
 }
 
 // -------------------------------------------------------------------- CG --
-// One block per replicate; phases separated by __syncthreads only. The
-// solve is done by kCgWidth threads in every kernel that runs it (the
-// per-phase CG launch and the persistent step), so it gives the same bits
-// whatever block size the step was tuned to.
+// The solve's node loops are done by kCgWidth threads of each block in
+// every kernel that runs it (the per-phase CG launch and the persistent
+// step), so it gives the same bits whatever block size the step was tuned
+// to.
 constexpr int kCgWidth = 128;
 constexpr int kCgThreads = kCgWidth;
 
