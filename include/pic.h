@@ -486,8 +486,7 @@ pic_status pic_measure_alu_peaks(void* cuda_stream, double out[5]);
  * inside the library, held on every GPU that loads the library until the
  * process exits. The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current; make that first call before any stream capture.
- * Every call shares the array: calls whose work overlaps on the GPU (two
+ * with the device current. Every call shares the array: calls whose work overlaps on the GPU (two
  * streams, two host threads) race and give wrong results. Host pointers and
  * device memory of another GPU return PIC_EINVAL. Calls no allocating
  * routine. */

@@ -29,6 +29,12 @@ struct Sample32Args {
   // arrays, read for pid i at vslot[i] (the inverse sort permutation)
   const int32_t* vslot;
   const float *vin0, *vin1, *vin2;
+  // optional: the state as 48-byte records in pid order (o0 o1 o2 v0 | v1 v2
+  // m0 m1 | m2 cell pid -) with its cell keys and in-cell arrival ranks,
+  // instead of the structure-of-arrays buffers (a state load followed by
+  // the sort: its gather reads the records at random)
+  float4* rec = nullptr;
+  int32_t *key = nullptr, *rank = nullptr, *count = nullptr;
   int32_t* cell;
   float *o0, *o1, *o2, *v0, *v1, *v2, *m0, *m1, *m2;
   uint32_t* pid;
@@ -101,7 +107,17 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
     float o = (float)(x[d] * (double)n - (double)ci[d]);
     off[d] = o >= 1.f ? 0x1.fffffep-1f : (o < 0.f ? 0.f : o);
   }
-  a.cell[i] = ci[0] + n * (ci[1] + n * ci[2]);
+  const int32_t cell = ci[0] + n * (ci[1] + n * ci[2]);
+  if (a.rec) {
+    float4* r = a.rec + 3 * i;
+    r[0] = make_float4(off[0], off[1], off[2], (float)v[0]);
+    r[1] = make_float4((float)v[1], (float)v[2], (float)vm[0], (float)vm[1]);
+    r[2] = make_float4((float)vm[2], __int_as_float(cell), __uint_as_float((uint32_t)i), 0.f);
+    a.key[i] = cell;
+    a.rank[i] = cell_slot(a.count, cell);
+    return;
+  }
+  a.cell[i] = cell;
   a.o0[i] = off[0]; a.o1[i] = off[1]; a.o2[i] = off[2];
   a.v0[i] = (float)v[0]; a.v1[i] = (float)v[1]; a.v2[i] = (float)v[2];
   a.m0[i] = (float)vm[0]; a.m1[i] = (float)vm[1]; a.m2[i] = (float)vm[2];
@@ -208,11 +224,12 @@ __global__ void __launch_bounds__(kThreads) k_store_state32_by_pid(StoreByPid32A
 
 constexpr int kGatherThreads = 128;
 
+template <bool kRec>
 __global__ void __launch_bounds__(kGatherThreads) k_sort_gather32(Gather32Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t cell = gw; cell < a.ncell; cell += nw) gather_cell32(a, cell, lane);
+  for (int64_t cell = gw; cell < a.ncell; cell += nw) gather_cell32<4, kRec>(a, cell, lane);
 }
 
 // Cells of kBigCell < count <= kMaxBlockSort particles: one block per cell,
@@ -234,7 +251,7 @@ __global__ void __launch_bounds__(kBigThreads) k_sort_big32(Gather32Args a) {
     for (int e = threadIdx.x; e < np2; e += blockDim.x) {
       if (e < cnt) {
         const int32_t src = a.perm[s + e];
-        key[e] = a.pid_in[src];
+        key[e] = a.rec ? gather_pid32<true>(a, src) : gather_pid32<false>(a, src);
         val[e] = src;
       } else {
         key[e] = 0xFFFFFFFFu;
@@ -245,8 +262,11 @@ __global__ void __launch_bounds__(kBigThreads) k_sort_big32(Gather32Args a) {
     block_bitonic_sort(key, val, np2);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const int32_t src = val[e], dst = s + e;
+      float d[9];
+      if (a.rec) gather_load32<true>(a, src, d);
+      else gather_load32<false>(a, src, d);
 #pragma unroll
-      for (int q = 0; q < 9; ++q) a.out[q][dst] = a.in[q][src];
+      for (int q = 0; q < 9; ++q) a.out[q][dst] = d[q];
       a.pid_out[dst] = key[e];
       a.cell_out[dst] = (int32_t)cell;
     }
@@ -1246,7 +1266,7 @@ __global__ void __launch_bounds__(kThreads) k_store_dv32(StoreDv32Args a) {
 
 // ============================================================== launches ==
 cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v, const int32_t* vm_slot,
-                            float* const* vm_src) {
+                            float* const* vm_src, bool to_records) {
   Sample32Args a;
   a.P = c->P;
   a.tt = time_terms(c->P, t0);
@@ -1262,6 +1282,12 @@ cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double
   a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
   a.m0 = c->vmf[b][0]; a.m1 = c->vmf[b][1]; a.m2 = c->vmf[b][2];
   a.pid = c->pid[b];
+  if (to_records) {
+    a.rec = reinterpret_cast<float4*>(c->stage);
+    a.key = c->key;
+    a.rank = c->rank;
+    a.count = c->count;
+  }
   prof_begin(c);
   k_sample32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
   prof_end(c, x ? KC_OTHER : KC_SAMPLE);
@@ -1300,13 +1326,17 @@ cudaError_t launch_gather32(pic_ctx* c) {
   g.corner = c->corner;
   g.big_lo = big_cell_threshold(g.ncell, c->P.np);
   g.spid = c->pid[o];  // written in arrival order by the scatter
+  if (c->rec_state) g.rec = reinterpret_cast<const float4*>(c->stage);
   // one warp per cell: blocks of consecutive cells, handed to the SMs as
   // they free up (measured faster than resident warps walking the cells
   // with a grid stride)
   int64_t blocks = (c->P.ncell * 32 + kGatherThreads - 1) / kGatherThreads;
   if (blocks > INT_MAX) blocks = INT_MAX;  // the grid-stride loop takes the rest
   prof_begin(c);
-  k_sort_gather32<<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
+  if (g.rec)
+    k_sort_gather32<true><<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
+  else
+    k_sort_gather32<false><<<(int)blocks, kGatherThreads, 0, c->stream>>>(g);
   if (g.big_lo < INT_MAX) {
     k_sort_big32<<<2 * c->num_sms, kBigThreads, (size_t)kMaxBlockSort * 8, c->stream>>>(g);
     c->launches++;
@@ -1314,6 +1344,7 @@ cudaError_t launch_gather32(pic_ctx* c) {
   prof_end(c, KC_GATHER);
   c->launches++;
   c->cur = o;
+  c->rec_state = false;
   return cudaGetLastError();
 }
 

@@ -123,8 +123,8 @@ struct ScatterArgs {
   int64_t np;
   const int32_t *key, *rank, *start;
   int32_t* perm;
-  const uint32_t* pid;  // optional: each particle's pid also goes to its arrival slot
-  uint32_t* spid;
+  const uint32_t* pid;  // each particle's pid, also written to its arrival slot (nullptr: pid = j)
+  uint32_t* spid;       // optional
 };
 
 __global__ void __launch_bounds__(kThreads) k_scatter(ScatterArgs a) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(ScatterArgs a) {
   if (j >= a.np) return;
   const int32_t slot = a.start[a.key[j]] + a.rank[j];
   a.perm[slot] = (int32_t)j;
-  if (a.spid) a.spid[slot] = a.pid[j];
+  if (a.spid) a.spid[slot] = a.pid ? a.pid[j] : (uint32_t)j;
 }
 
 struct GatherArgs {
@@ -340,7 +340,8 @@ cudaError_t launch_scan_scatter(pic_ctx* c) {
   s.perm = c->perm;
   // the precision form's gather reads each cell's pids in arrival order
   // from the output pid array (coalesced) instead of through perm
-  s.pid = c->mixed ? c->pid[c->cur] : nullptr;
+  // (a state loaded as records is in pid order: particle j has pid j)
+  s.pid = c->mixed && !c->rec_state ? c->pid[c->cur] : nullptr;
   s.spid = c->mixed ? c->pid[1 - c->cur] : nullptr;
   k_scatter<<<blocks_for(s.np), kThreads, 0, c->stream>>>(s);
   prof_end(c, KC_SORT);

@@ -235,7 +235,32 @@ struct Gather32Args {
   double* corner;       // [8][ncell]
   int big_lo;             // cells above this count go to the block sort
   const uint32_t* spid;   // optional: pids in arrival order (slot s + e holds perm[s + e]'s pid)
+  // optional: the source as 48-byte records (o0 o1 o2 v0 | v1 v2 m0 m1 |
+  // m2 cell pid -) instead of in[] and pid_in: a random source read as
+  // records touches two 32-byte sectors a particle instead of nine
+  const float4* rec = nullptr;
 };
+
+// particle src of the gather's source: o0..o2, v0..v2, m0..m2 (kRec: from
+// the records)
+template <bool kRec>
+__device__ __forceinline__ void gather_load32(const Gather32Args& a, int32_t src, float* d) {
+  if constexpr (kRec) {
+    const float4 r0 = __ldg(a.rec + 3 * (int64_t)src), r1 = __ldg(a.rec + 3 * (int64_t)src + 1),
+                 r2 = __ldg(a.rec + 3 * (int64_t)src + 2);
+    d[0] = r0.x; d[1] = r0.y; d[2] = r0.z; d[3] = r0.w;
+    d[4] = r1.x; d[5] = r1.y; d[6] = r1.z; d[7] = r1.w;
+    d[8] = r2.x;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) d[q] = a.in[q][src];
+  }
+}
+template <bool kRec>
+__device__ __forceinline__ uint32_t gather_pid32(const Gather32Args& a, int32_t src) {
+  if constexpr (kRec) return __float_as_uint(__ldg(a.rec + 3 * (int64_t)src + 2).z);
+  else return a.pid_in[src];
+}
 
 // CIC corner weights of one particle (offsets in cell units) in 64-bit fixed
 // point: integer sums are exact in any order, so a cell's corner partials do
@@ -304,7 +329,7 @@ __device__ __forceinline__ void store_corners_fixed(const long long* acc, int la
 // cell, then the particle copied to slot s + rank and its CIC weights
 // added. Up to two chunks load the particle data with the pids (one memory
 // round trip); wider cells load it after the count, to bound the registers.
-template <int C>
+template <int C, bool kRec>
 __device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t cell, int32_t s, int32_t cnt, int lane,
                                                 const CicFixed& fx, long long* acc) {
   constexpr bool kPre = C <= 2;
@@ -324,11 +349,8 @@ __device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t c
 #pragma unroll
   for (int k = 0; k < C; ++k)
     if (32 * k + lane < cnt) {
-      if (!a.spid) p[k] = a.pid_in[src[k]];
-      if constexpr (kPre) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) d[k][q] = a.in[q][src[k]];
-      }
+      if (!a.spid) p[k] = gather_pid32<kRec>(a, src[k]);
+      if constexpr (kPre) gather_load32<kRec>(a, src[k], d[k]);
     }
   int r[C];
 #pragma unroll
@@ -352,10 +374,7 @@ __device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t c
     if (32 * k + lane < cnt) {
       const int32_t dst = s + r[k];
       float* dk = d[kPre ? k : 0];
-      if constexpr (!kPre) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) dk[q] = a.in[q][src[k]];
-      }
+      if constexpr (!kPre) gather_load32<kRec>(a, src[k], dk);
 #pragma unroll
       for (int q = 0; q < 9; ++q) a.out[q][dst] = dk[q];
       a.pid_out[dst] = p[k];
@@ -369,7 +388,7 @@ __device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t c
 // and the cell's eight CIC corner partials. Cells of big_lo < count <=
 // kMaxBlockSort are left to the block sort. Cells of up to 32 kRegChunks
 // particles take the register path, larger ones the chunked pairwise count.
-template <int kRegChunks = 4>
+template <int kRegChunks = 4, bool kRec = false>
 __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cell, int lane) {
   const int32_t s = a.start[cell];
   const int32_t cnt = a.start[cell + 1] - s;
@@ -380,13 +399,13 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
   for (int q = 0; q < 8; ++q) acc[q] = 0;
   const int32_t nch = (cnt + 31) >> 5;  // warp-uniform
   if (nch <= 1) {
-    gather_chunks32<1>(a, cell, s, cnt, lane, fx, acc);
+    gather_chunks32<1, kRec>(a, cell, s, cnt, lane, fx, acc);
   } else if (nch == 2) {
-    gather_chunks32<2>(a, cell, s, cnt, lane, fx, acc);
+    gather_chunks32<2, kRec>(a, cell, s, cnt, lane, fx, acc);
   } else if (kRegChunks >= 3 && nch == 3) {
-    if constexpr (kRegChunks >= 3) gather_chunks32<3>(a, cell, s, cnt, lane, fx, acc);
+    if constexpr (kRegChunks >= 3) gather_chunks32<3, kRec>(a, cell, s, cnt, lane, fx, acc);
   } else if (kRegChunks >= 4 && nch == 4) {
-    if constexpr (kRegChunks >= 4) gather_chunks32<4>(a, cell, s, cnt, lane, fx, acc);
+    if constexpr (kRegChunks >= 4) gather_chunks32<4, kRec>(a, cell, s, cnt, lane, fx, acc);
   } else {
     for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
       const int32_t e = e0 + lane;
@@ -394,14 +413,14 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
       uint32_t mp = 0xFFFFFFFFu;
       if (e < cnt) {
         src = a.perm[s + e];
-        mp = a.pid_in[src];  // spid is pid_out: rewritten by earlier chunks
+        mp = gather_pid32<kRec>(a, src);  // spid is pid_out: rewritten by earlier chunks
       }
       int32_t r = 0;
       for (int32_t f0 = 0; f0 < cnt; f0 += 32) {
         uint32_t other = mp;
         if (f0 != e0) {
           const int32_t f = f0 + lane;
-          other = f < cnt ? a.pid_in[a.perm[s + f]] : 0xFFFFFFFFu;
+          other = f < cnt ? gather_pid32<kRec>(a, a.perm[s + f]) : 0xFFFFFFFFu;
         }
         const int lim = min(32, cnt - f0);
         for (int l = 0; l < lim; ++l) r += __shfl_sync(0xffffffffu, other, l) < mp ? 1 : 0;
@@ -409,8 +428,7 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
       if (e < cnt) {
         const int32_t dst = s + r;
         float d[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) d[q] = a.in[q][src];
+        gather_load32<kRec>(a, src, d);
 #pragma unroll
         for (int q = 0; q < 9; ++q) a.out[q][dst] = d[q];
         a.pid_out[dst] = mp;

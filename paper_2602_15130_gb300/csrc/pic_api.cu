@@ -412,11 +412,12 @@ pic_status check_pending(pic_ctx* c) {
 }
 
 // sort by (cell, pid) from the current positions and solve the field at t
-pic_status sort_and_field(pic_ctx* c, double t) {
+// keys_done: the state load wrote the keys, ranks and counts itself
+pic_status sort_and_field(pic_ctx* c, double t, bool keys_done = false) {
   c->lor_valid = false;
-  CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+  if (!keys_done) CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
   if (c->mixed) {
-    CK(launch_keys32(c));
+    if (!keys_done) CK(launch_keys32(c));
     CK(launch_scan_scatter(c));
     CK(launch_gather32(c));
     CK(launch_rhs(c, t));
@@ -893,8 +894,25 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
   if (c->mixed) {
     // v^M is a per-particle constant (tau for the paper's f_v): a context that
     // already holds a state keeps its values, read through the inverse sort
-    // permutation by the load into the other buffer, instead of re-deriving
-    // them from xi in FP64
+    // permutation by the load, instead of re-deriving them from xi in FP64.
+    // Caller arrays used in place leave the staging area free: the load then
+    // writes the state there as records, which the sort's random gather
+    // reads in two sectors a particle instead of nine.
+    const bool records = xs != c->stage && vs != c->stage + 3 * c->P.np;
+    if (records) {
+      if (c->sampled) CK(launch_inv_perm32(c));
+      CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+      CK(launch_sample32(c, time_at(c, (double)step), xs, vs, c->sampled ? c->perm : nullptr,
+                         c->sampled ? c->vmf[c->cur] : nullptr, true));
+      c->rec_state = true;
+      pic_status s = sort_and_field(c, time_at(c, (double)step), true);
+      if (s != PIC_OK) {
+        c->rec_state = false;
+        return s;
+      }
+      c->sampled = true;
+      return check_pending(c);
+    }
     if (c->sampled) {
       CK(launch_inv_perm32(c));
       const int src = c->cur;

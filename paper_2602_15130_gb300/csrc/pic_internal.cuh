@@ -583,6 +583,7 @@ struct pic_ctx {
   double* dv[3];    // collision term per particle (sorted order)
   double* lor[3];   // dt q/m (E_p - E^M_p) of the last kick without drift
   bool lor_valid;   // lor matches the current order, positions and field
+  bool rec_state;   // the next sort reads the state from records in the staging area
   double* dvm[3];   // source term when requested separately
 
   // precision form: int32 cell + FP32 offset, FP32 v and v^M, FP32 mesh
@@ -763,8 +764,12 @@ cudaError_t launch_err_final(pic_ctx* c, int nblocks);
 // precision form
 // vm_slot, vm_src: v^M (tau) to keep instead of recomputing them (state
 // loads), read from the sorted arrays vm_src at the inverse permutation
+// to_records: write the state into the staging area as 48-byte records with
+// their cell keys and ranks (sort_and_field then skips the keys), for a
+// state load whose caller arrays are used in place
 cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v,
-                           const int32_t* vm_slot = nullptr, float* const* vm_src = nullptr);
+                           const int32_t* vm_slot = nullptr, float* const* vm_src = nullptr,
+                           bool to_records = false);
 cudaError_t launch_inv_perm32(pic_ctx* c);  // c->perm[pid] = slot of pid in the current order
 cudaError_t launch_keys32(pic_ctx* c);
 cudaError_t launch_gather32(pic_ctx* c);
