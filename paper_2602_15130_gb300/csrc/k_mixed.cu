@@ -768,7 +768,9 @@ __global__ void __launch_bounds__(kThreads) k_kick32(Kick32Args a) {
     on -= fl;
     int shift = (int)fl;
     if (on >= 1.f) { on = 0.f; shift += 1; }
-    int cd = (ci[d] + shift) % n;
+    // periodic wrap: a mask when n is a power of two (exact for negative
+    // shifts in two's complement), else a remainder
+    int cd = P.log2n >= 0 ? (ci[d] + shift) & (n - 1) : (ci[d] + shift) % n;
     ci[d] = cd < 0 ? cd + n : cd;
     op[d][j] = on;
   }
