@@ -168,7 +168,16 @@ OPS_PER_CANDIDATE = 250
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel source it was taken on: bench.py compares the source file's hash
 # and reports null traffic once the kernel has changed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("mixed", "dsmc"): {
+        "bytes_per_unit": 22.70,
+        "source": "paper_2602_15130_gb300/csrc/k_mixed.cu",
+        "sha16": "d9b0cacbf90f3788",
+        "how": "ncu --set full of k_dsmc32 at 64^3 (--workload precision64, both calls of a step): "
+               "dram__bytes_read.sum + dram__bytes_write.sum = 22.70 B per particle, times the "
+               "launch's particles (the state exceeds L2 at both sizes)",
+    },
+}
 
 
 def source_hash(path: str) -> str:
