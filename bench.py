@@ -133,8 +133,9 @@ def measured_peaks() -> dict:
 # method must move, per particle for the particle kernels (one launch
 # processes every particle), per node for the RHS and per node-iteration for
 # the CG. "method": the per-particle-step figures the method implies for
-# the FP32 state of 56 B (cell, three offsets, three velocities, three v^M
-# as the manufactured velocity, pid) or the FP64 state of 104 B: the push
+# the FP32 state of 56 B (cell, three offsets, three velocities, three xi,
+# three v^M, pid; this implementation regenerates xi from the pid instead
+# of storing it) or the FP64 state of 104 B: the push
 # reads and writes the state once per step (two launches: half each), the
 # sort scatter reads and writes it once, the deposit reads the positions
 # once, and each CG iteration moves about 28 B (FP32) or 56 B (FP64) per
