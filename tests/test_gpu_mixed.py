@@ -215,6 +215,39 @@ def test_state_load_into_a_running_context_keeps_v_manufactured(which):
     assert np.all(np.abs(ef - er) <= 0.01 * ef + 1e-9), (ef, er)
 
 
+def test_state_load_through_records_matches_the_array_path():
+    """A precision-form state load from arrays used in place (pinned host or
+    device) writes the state as records that the first sort gathers; one
+    from pageable arrays goes through the per-array buffers. Both must give
+    the same sorted state, the same v^M (through the error norms) and the
+    same field, bit for bit: into a fresh context, and into one that
+    already holds a state (which keeps v^M through the inverse permutation).
+    The first state packs the particles into five cells of a 4^3 mesh
+    (mean occupancy 200), so its big cells take the block sort."""
+    import torch
+
+    n = 4
+    p = mixed(n=n, n_particles=n ** 3 * 200 + 13, K=4)
+    xa, va = inputs.particles(p["n_particles"], seed=21, clustered_cells=5, n=n)
+    xb, vb = inputs.particles(p["n_particles"], seed=22)
+    ref = Pic(p)
+    want = []
+    for x, v in ((xa, va), (xb, vb)):
+        ref.set_state(x, v, 0.1, 3)
+        want.append((ref.get_state(), ref.get_sort()[3], ref.mms_error()["array"], ref.get_field()[1]))
+        if not want[1:]:
+            assert ref.get_sort()[1].max() > 256  # the block sort's cells
+    places = {"pinned": lambda a: torch.from_numpy(a).pin_memory(), "cuda": lambda a: torch.from_numpy(a).cuda()}
+    for where, put in places.items():
+        g = Pic(p)
+        for k, (x, v) in enumerate(((xa, va), (xb, vb))):
+            g.set_state(put(x), put(v), 0.1, 3)
+            (xs, vs), perm, err, phi = g.get_state(), g.get_sort()[3], g.mms_error()["array"], g.get_field()[1]
+            (xw, vw), pw, ew, fw = want[k]
+            assert np.array_equal(xs, xw) and np.array_equal(vs, vw), (where, k)
+            assert np.array_equal(perm, pw) and np.array_equal(err, ew) and np.array_equal(phi, fw), (where, k)
+
+
 @pytest.mark.parametrize("form", ["mixed", "fp64"])
 def test_state_in_place_through_pinned_and_device_buffers(form):
     """Pinned host and CUDA arrays are read (and, by the precision form,
