@@ -215,6 +215,46 @@ def test_state_load_into_a_running_context_keeps_v_manufactured(which):
     assert np.all(np.abs(ef - er) <= 0.01 * ef + 1e-9), (ef, er)
 
 
+def sort_is_canonical(x, n, cell, count, start, perm):
+    """The sort's invariants: each pid's cell from its position, the counts
+    and exclusive starts, and perm listing the pids in (cell, pid) order."""
+    ci = np.minimum((x * n).astype(np.int64), n - 1)
+    want = ci[:, 0] + n * (ci[:, 1] + n * ci[:, 2])
+    assert np.array_equal(cell, want)
+    assert np.array_equal(count, np.bincount(cell, minlength=n ** 3))
+    assert start[0] == 0 and np.array_equal(np.diff(start), count)
+    key = cell[perm].astype(np.int64) * len(perm) + perm
+    assert np.all(np.diff(key) > 0)
+
+
+def test_mixed_sort_register_path_widths():
+    """Cells of up to 32, 64, 96 and 128 particles take the sort gather's
+    register paths of one to four 32-particle chunks, larger ones the
+    chunked pairwise count (the mean occupancy stays below 128, so no cell
+    goes to the block sort). The sort equals the oracle's after a state
+    load, and is canonical after each of two steps."""
+    n = 6
+    parts = [inputs.particles(n ** 3 * 30, seed=31)]  # about 30 a cell
+    for k, (m, cells) in enumerate(((500, 10), (800, 10), (600, 3))):  # about +50, +80, +200
+        parts.append(inputs.particles(m, seed=32 + k, clustered_cells=cells, n=n))
+    x, v = np.vstack([a for a, _ in parts]), np.vstack([b for _, b in parts])
+    p = workloads.mixed(workloads.smallest(n=n, n_particles=len(x), K=4))
+    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-12))
+    g.set_state(x, v)
+    o.set_state(x, v)
+    srt = o.sort()
+    c = srt[1]
+    assert c.mean() < 128 and c.max() > 128
+    for lo, hi in ((0, 32), (32, 64), (64, 96), (96, 128)):
+        assert ((c > lo) & (c <= hi)).any(), (lo, hi)
+    for a, b in zip(g.get_sort(), srt):
+        assert np.array_equal(a, b)
+    for _ in range(2):
+        g.step(1)
+        xs, _ = g.get_state()
+        sort_is_canonical(xs, n, *g.get_sort())
+
+
 def test_state_load_through_records_matches_the_array_path():
     """A precision-form state load from arrays used in place (pinned host or
     device) writes the state as records that the first sort gathers; one
