@@ -172,8 +172,16 @@ OPS_PER_CANDIDATE = 250
 NCU_TRAFFIC = {
     ("mixed", "dsmc"): {
         "bytes_per_unit": 22.70,
-        "source": "paper_2602_15130_gb300/csrc/k_mixed.cu",
-        "sha16": "d9b0cacbf90f3788",
+        # the collision kernel and its device routines, its launch, and the
+        # headers they include: (path, first line, line after) or whole files
+        "sources": [
+            ("paper_2602_15130_gb300/csrc/k_mixed.cu", "struct Counts32 {",
+             "// ------------------------------------------------------------ kick/drift --"),
+            ("paper_2602_15130_gb300/csrc/k_mixed.cu", "cudaError_t launch_dsmc32(", "\n}\n"),
+            ("paper_2602_15130_gb300/csrc/mixed_common.cuh", None, None),
+            ("paper_2602_15130_gb300/csrc/pic_internal.cuh", None, None),
+        ],
+        "sha16": "d16071af5357f519",
         "how": "ncu --set full of k_dsmc32 at 64^3 (--workload precision64, both calls of a step): "
                "dram__bytes_read.sum + dram__bytes_write.sum = 22.70 B per particle, times the "
                "launch's particles (the state exceeds L2 at both sizes)",
@@ -181,14 +189,27 @@ NCU_TRAFFIC = {
 }
 
 
-def source_hash(path: str) -> str:
-    with open(os.path.join(ROOT, path), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def source_hash(sources) -> str:
+    """Hash of the source text a kernel is built from: whole files, or the
+    span of a file from a first line to the next occurrence of an end
+    marker; empty when a marker is missing."""
+    h = hashlib.sha256()
+    for path, first, end in sources:
+        with open(os.path.join(ROOT, path), "rb") as f:
+            text = f.read()
+        if first is not None:
+            i = text.find(first.encode())
+            j = text.find(end.encode(), i + 1) if i >= 0 else -1
+            if i < 0 or j < 0:
+                return ""
+            text = text[i:j]
+        h.update(text)
+    return h.hexdigest()[:16]
 
 
 def traffic_per_launch(form: str, kernel: str, units: float):
     e = NCU_TRAFFIC.get((form, kernel))
-    if not e or source_hash(e["source"]) != e["sha16"]:
+    if not e or source_hash(e["sources"]) != e["sha16"]:
         return None, None
     return e["bytes_per_unit"] * units, e["how"]
 
