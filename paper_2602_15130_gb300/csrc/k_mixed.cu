@@ -3,11 +3,12 @@
 // velocity, FP32 v^M and the pid; velocities, field gather, manufactured
 // terms and scattering are FP32. Kept FP64-accurate: the per-cell charge
 // sums, the CG inner products and residual, and the error norms. On this
-// GPU the FP64 pipe runs at 1/58 of the FP32 rate, so the FP64-accurate
-// sums are formed in double-float arithmetic (an unevaluated sum hi + lo
-// of two floats, error-free TwoSum / TwoProd of Knuth and Dekker, relative
-// error about 2^-44) on the FP32 pipe and only the few per-block totals are
-// combined in true FP64.
+// GPU the FP64 pipe runs at 1/74 of the FP32 FMA rate, so the charge sums
+// are exact 64-bit fixed point and the CG's inner products are formed in
+// double-float arithmetic (an unevaluated sum hi + lo of two floats,
+// error-free TwoSum / TwoProd of Knuth and Dekker, relative error about
+// 2^-44) on the FP32 pipe, within and across blocks; the CG's scalar
+// recurrences and the error norms are true FP64.
 #include "mixed_common.cuh"
 
 namespace pic {
