@@ -1157,6 +1157,336 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
   }
 }
 
+// ------------------------------------------- multigrid-preconditioned CG --
+// The precision form's Poisson solve on meshes of 2^k >= 32 nodes an edge:
+// CG preconditioned by one multigrid V-cycle (the same discrete system
+// -Delta_h phi = b and the same stopping rule ||r|| <= tol ||b|| as the
+// plain CG above, in far fewer iterations). Levels halve the edge down to
+// 4; each level takes two damped-Jacobi sweeps (omega = 6/7) before and
+// after its coarse correction, full-weighting restriction (per axis 1/4,
+// 1/2, 1/4) and trilinear prolongation, so the V-cycle is a symmetric
+// positive operator on zero-mean vectors, as CG needs. The coarsest level
+// takes Jacobi sweeps from zero and is projected to zero mean. Levels above
+// kMgLocalNodes nodes run on the whole grid between grid barriers; the
+// smaller ones on block 0 alone between block barriers.
+constexpr int kMgMaxLevels = 12;
+constexpr int kMgLocalNodes = 32768;
+constexpr int kMgCoarseSweeps = 16;
+constexpr float kMgOmega = 6.f / 7.f;
+
+struct Mg32Level {
+  int n, log2n;
+  float inv_h2;      // 1 / h_l^2
+  float *ua, *ub;    // the level's iterate and a second buffer
+  float* f;          // its right-hand side (level 0: the CG residual)
+};
+
+struct MgCg32Args {
+  Cg32Args cg;       // the fine level's vectors, barrier words and outputs
+  float *z, *z2;     // the preconditioned residual and a second buffer
+  int nlev, nlev_grid;
+  Mg32Level lev[kMgMaxLevels];
+};
+
+__device__ __forceinline__ float lap32(const float* u, int id, int n, int log2n, float inv_h2) {
+  const Nbr q = neighbours(id, n, n * n, log2n);
+  return (6.f * u[id] - (u[q.xp] + u[q.xm] + u[q.yp] + u[q.ym] + u[q.zp] + u[q.zm])) * inv_h2;
+}
+
+// full weighting at coarse node I of the fine field r (edge n = 2 nc)
+__device__ __forceinline__ float restrict_fw(const float* r, int I, int log2nc, int log2n) {
+  const int mc = (1 << log2nc) - 1, m = (1 << log2n) - 1;
+  const int ci = I & mc, cj = (I >> log2nc) & mc, ck = I >> (2 * log2nc);
+  float acc = 0.f;
+#pragma unroll
+  for (int c = -1; c <= 1; ++c) {
+    const int kk = (2 * ck + c) & m;
+    const float wz = c == 0 ? 0.5f : 0.25f;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+      const int jj = (2 * cj + b) & m;
+      const float wyz = (b == 0 ? 0.5f : 0.25f) * wz;
+      const int row = (jj << log2n) + (kk << (2 * log2n));
+#pragma unroll
+      for (int a = -1; a <= 1; ++a) acc = fmaf((a == 0 ? 0.5f : 0.25f) * wyz, r[((2 * ci + a) & m) + row], acc);
+    }
+  }
+  return acc;
+}
+
+// trilinear prolongation at fine node id of the coarse field e (edge nc):
+// the eight surrounding coarse values (repeated where a fine coordinate is
+// even) with weight 1/8 each
+__device__ __forceinline__ float prolong_tl(const float* e, int id, int log2n, int log2nc) {
+  const int m = (1 << log2n) - 1, mc = (1 << log2nc) - 1;
+  const int i = id & m, j = (id >> log2n) & m, k = id >> (2 * log2n);
+  const int i0 = i >> 1, i1 = (i0 + (i & 1)) & mc;
+  const int j0 = j >> 1, j1 = (j0 + (j & 1)) & mc;
+  const int k0 = k >> 1, k1 = (k0 + (k & 1)) & mc;
+  const int r00 = (j0 << log2nc) + (k0 << (2 * log2nc)), r10 = (j1 << log2nc) + (k0 << (2 * log2nc));
+  const int r01 = (j0 << log2nc) + (k1 << (2 * log2nc)), r11 = (j1 << log2nc) + (k1 << (2 * log2nc));
+  const float s = ((e[i0 + r00] + e[i1 + r00]) + (e[i0 + r10] + e[i1 + r10])) +
+                  ((e[i0 + r01] + e[i1 + r01]) + (e[i0 + r11] + e[i1 + r11]));
+  return 0.125f * s;
+}
+
+// node range and barrier of a V-cycle stage: the whole grid or block 0
+template <bool kGrid>
+struct MgSync {
+  const Cg32Args* cg;
+  __device__ int first() const { return kGrid ? (int)(blockIdx.x * blockDim.x + threadIdx.x) : (int)threadIdx.x; }
+  __device__ int stride() const { return kGrid ? (int)(gridDim.x * blockDim.x) : (int)blockDim.x; }
+  __device__ bool sync() const {
+    if (kGrid) return grid_barrier32(cg->bar, cg->info, cg->flags);
+    __syncthreads();
+    return true;
+  }
+};
+
+// level l's descent: two Jacobi sweeps from zero (the first, u = c f, is
+// done by the caller at level 0), the residual, and its restriction to
+// level l + 1. On entry L.f is complete; on exit C.f is.
+template <bool kGrid>
+__device__ bool mg_down(const MgSync<kGrid>& S, const Mg32Level& L, const Mg32Level& C, bool first_done) {
+  const int m = 1 << (3 * L.log2n);
+  const float cw = kMgOmega / (6.f * L.inv_h2);
+  if (!first_done) {
+    for (int id = S.first(); id < m; id += S.stride()) L.ub[id] = cw * L.f[id];
+    if (!S.sync()) return false;
+  }
+  for (int id = S.first(); id < m; id += S.stride())
+    L.ua[id] = fmaf(cw, L.f[id] - lap32(L.ub, id, L.n, L.log2n, L.inv_h2), L.ub[id]);
+  if (!S.sync()) return false;
+  for (int id = S.first(); id < m; id += S.stride()) L.ub[id] = L.f[id] - lap32(L.ua, id, L.n, L.log2n, L.inv_h2);
+  if (!S.sync()) return false;
+  const int mc = 1 << (3 * C.log2n);
+  for (int I = S.first(); I < mc; I += S.stride()) C.f[I] = restrict_fw(L.ub, I, C.log2n, L.log2n);
+  return S.sync();
+}
+
+// level l's ascent: the coarse correction added, then two Jacobi sweeps;
+// the result is in L.ua. The last sweep is left to the caller at level 0.
+template <bool kGrid>
+__device__ bool mg_up(const MgSync<kGrid>& S, const Mg32Level& L, const Mg32Level& C, bool last_by_caller) {
+  const int m = 1 << (3 * L.log2n);
+  const float cw = kMgOmega / (6.f * L.inv_h2);
+  for (int id = S.first(); id < m; id += S.stride()) L.ua[id] += prolong_tl(C.ua, id, L.log2n, C.log2n);
+  if (!S.sync()) return false;
+  for (int id = S.first(); id < m; id += S.stride())
+    L.ub[id] = fmaf(cw, L.f[id] - lap32(L.ua, id, L.n, L.log2n, L.inv_h2), L.ua[id]);
+  if (!S.sync()) return false;
+  if (last_by_caller) return true;
+  for (int id = S.first(); id < m; id += S.stride())
+    L.ua[id] = fmaf(cw, L.f[id] - lap32(L.ub, id, L.n, L.log2n, L.inv_h2), L.ub[id]);
+  return S.sync();
+}
+
+// the coarsest level by one block: Jacobi sweeps from zero, then the mean
+// removed (the periodic operator's null space); the result in L.ua
+__device__ void mg_coarsest(const Mg32Level& L, float* sh) {
+  const int m = 1 << (3 * L.log2n);
+  const float cw = kMgOmega / (6.f * L.inv_h2);
+  for (int id = threadIdx.x; id < m; id += blockDim.x) L.ua[id] = cw * L.f[id];
+  __syncthreads();
+  for (int s = 1; s < kMgCoarseSweeps; ++s) {
+    const float* src = (s & 1) ? L.ua : L.ub;
+    float* dst = (s & 1) ? L.ub : L.ua;
+    for (int id = threadIdx.x; id < m; id += blockDim.x)
+      dst[id] = fmaf(cw, L.f[id] - lap32(src, id, L.n, L.log2n, L.inv_h2), src[id]);
+    __syncthreads();
+  }
+  // kMgCoarseSweeps is even: the last sweep wrote ub
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int id = 0; id < m; ++id) s += L.ub[id];
+    sh[0] = s / (float)m;
+  }
+  __syncthreads();
+  for (int id = threadIdx.x; id < m; id += blockDim.x) L.ua[id] = L.ub[id] - sh[0];
+  __syncthreads();
+}
+
+// z = M r for levels from l0 down (their right-hand side f[l0] complete on
+// entry; at l0 = 0 the first sweep has been done by the caller); the
+// levels from nlev_grid on are done by block 0. At level 0 the last sweep
+// is left to the caller.
+__device__ bool mg_vcycle(const MgCg32Args& a, float* sh) {
+  const MgSync<true> G{&a.cg};
+  const MgSync<false> B{&a.cg};
+  for (int l = 0; l + 1 < a.nlev_grid; ++l)
+    if (!mg_down(G, a.lev[l], a.lev[l + 1], l == 0)) return false;
+  // the local levels on block 0: descent, coarsest, ascent
+  if (blockIdx.x == 0) {
+    const int lg = a.nlev_grid - 1;
+    for (int l = lg; l + 1 < a.nlev; ++l) mg_down(B, a.lev[l], a.lev[l + 1], l == 0);
+    mg_coarsest(a.lev[a.nlev - 1], sh);
+    for (int l = a.nlev - 2; l >= lg; --l) mg_up(B, a.lev[l], a.lev[l + 1], l == 0);
+  }
+  if (!G.sync()) return false;
+  for (int l = a.nlev_grid - 2; l >= 0; --l)
+    if (!mg_up(G, a.lev[l], a.lev[l + 1], l == 0)) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(kCgThreads) k_mgcg32(MgCg32Args a) {
+  __shared__ double shd[1];
+  __shared__ float4 sh4[32];
+  __shared__ float sh[2];
+  __shared__ float fscal[2];
+  __shared__ int stop;
+  const Cg32Args& c = a.cg;
+  if ((int)blockIdx.x == c.skip_block) return;
+  const int n = c.n, nn = n * n;
+  const int m = (int)c.ncell;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int G = gridDim.x;
+  int ph = 0;
+  auto slot = [&](int q) { return reinterpret_cast<float2*>(c.red) + (size_t)q * 2 * G; };
+  auto publish = [&](int q, DF u, DF v) {
+    if (threadIdx.x == 0) {
+      slot(q)[blockIdx.x] = make_float2(u.hi, u.lo);
+      slot(q)[G + blockIdx.x] = make_float2(v.hi, v.lo);
+    }
+  };
+  const Mg32Level& L0 = a.lev[0];
+  const float cw0 = kMgOmega / (6.f * L0.inv_h2);
+  float* const z = a.z;
+
+  // r = (b - mean b) - A x; the first sweep of the V-cycle, z2 = c r, in the
+  // same pass needs r at this node only
+  const float mean_b = (float)(grid_total32(c.rhs_part, c.rhs_blocks, shd) / (double)m);
+  DF bb_loc{0.f, 0.f};
+  for (int id = t0; id < m; id += stride) {
+    const float bv = c.b[id] - mean_b;
+    const float rv = bv - lap32(c.x, id, n, c.log2n, c.inv_h2);
+    c.r[id] = rv;
+    a.z2[id] = cw0 * rv;
+    bb_loc = df_fma(bb_loc, bv, bv);
+  }
+  {
+    DF u, v;
+    block_total_df2(bb_loc, DF{0.f, 0.f}, sh4, &u, &v);
+    publish(ph, u, v);
+  }
+  if (!grid_barrier32(c.bar, c.info, c.flags)) return;
+  double bb = 0.0;
+  {
+    DF u, v;
+    grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+    bb = df_to_double(u);
+  }
+  ph ^= 1;
+  const double thresh = c.tol * sqrt(bb), thresh2 = thresh * thresh;
+  double gamma = 0.0, rr = 0.0, alpha = 0.0;
+  int it = 0, status = 0;
+  bool first = true;
+  while (true) {
+    // z = M r (its first sweep is done), then the last sweep with (r, z)
+    // and (r, r)
+    if (!mg_vcycle(a, sh)) return;
+    DF rz_l{0.f, 0.f}, rr_l{0.f, 0.f};
+    for (int id = t0; id < m; id += stride) {
+      const float zv = fmaf(cw0, c.r[id] - lap32(a.z2, id, n, c.log2n, L0.inv_h2), a.z2[id]);
+      z[id] = zv;
+      const float rv = c.r[id];
+      rz_l = df_fma(rz_l, rv, zv);
+      rr_l = df_fma(rr_l, rv, rv);
+    }
+    {
+      DF u, v;
+      block_total_df2(rz_l, rr_l, sh4, &u, &v);
+      publish(ph, u, v);
+    }
+    if (!grid_barrier32(c.bar, c.info, c.flags)) return;
+    {
+      DF u, v;
+      grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+      if (threadIdx.x == 0) {
+        const double g_new = df_to_double(u);
+        rr = df_to_double(v);
+        fscal[1] = first ? 0.f : (float)(g_new / gamma);
+        gamma = g_new;
+        stop = (bb == 0.0 || rr <= thresh2) ? 1 : (it >= c.maxit ? 2 : 0);
+      }
+    }
+    ph ^= 1;
+    __syncthreads();
+    if (stop == 1) break;
+    if (stop == 2) { status = 1; break; }
+    // p = z + beta p
+    const float be = fscal[1];
+    for (int id = t0; id < m; id += stride) c.p[id] = first ? z[id] : fmaf(be, c.p[id], z[id]);
+    first = false;
+    if (!grid_barrier32(c.bar, c.info, c.flags)) return;
+    // q = A p and (p, q)
+    DF pq_l{0.f, 0.f};
+    for (int id = t0; id < m; id += stride) {
+      const float qv = lap32(c.p, id, n, c.log2n, c.inv_h2);
+      c.q[id] = qv;
+      pq_l = df_fma(pq_l, c.p[id], qv);
+    }
+    {
+      DF u, v;
+      block_total_df2(pq_l, DF{0.f, 0.f}, sh4, &u, &v);
+      publish(ph, u, v);
+    }
+    if (!grid_barrier32(c.bar, c.info, c.flags)) return;
+    {
+      DF u, v;
+      grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+      if (threadIdx.x == 0) {
+        alpha = gamma / df_to_double(u);
+        fscal[0] = (float)alpha;
+      }
+    }
+    ph ^= 1;
+    __syncthreads();
+    // x += alpha p, r -= alpha q, and the next V-cycle's first sweep
+    const float al = fscal[0];
+    for (int id = t0; id < m; id += stride) {
+      c.x[id] = fmaf(al, c.p[id], c.x[id]);
+      const float rv = fmaf(-al, c.q[id], c.r[id]);
+      c.r[id] = rv;
+      a.z2[id] = cw0 * rv;
+    }
+    ++it;
+    if (!grid_barrier32(c.bar, c.info, c.flags)) return;
+  }
+  // zero-mean potential and E, as in k_cg32
+  DF xs{0.f, 0.f};
+  for (int id = t0; id < m; id += stride) xs = df_add_f(xs, c.x[id]);
+  {
+    DF u, v;
+    block_total_df2(xs, DF{0.f, 0.f}, sh4, &u, &v);
+    publish(ph, u, v);
+  }
+  if (!grid_barrier32(c.bar, c.info, c.flags)) return;
+  {
+    DF u, v;
+    grid_total_df2(slot(ph), slot(ph) + G, G, &u, &v);
+    if (threadIdx.x == 0) fscal[0] = (float)(df_to_double(u) / (double)m);
+  }
+  __syncthreads();
+  const float mean_x = fscal[0];
+  for (int id = t0; id < m; id += stride) c.x[id] -= mean_x;
+  if (!grid_barrier32(c.bar, c.info, c.flags)) return;
+  for (int id = t0; id < m; id += stride) {
+    const Nbr q = neighbours(id, n, nn, c.log2n);
+    const float* x = c.x;
+    c.E4[id] = make_float4(-(x[q.xp] - x[q.xm]) * c.inv_2h, -(x[q.yp] - x[q.ym]) * c.inv_2h,
+                           -(x[q.zp] - x[q.zm]) * c.inv_2h, 0.f);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c.info[0] = it;
+    c.info[1] = status;
+    if (c.hist) c.hist[0] = it;
+    c.res[0] = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
+    if (status) atomicOr(c.flags, 2);
+    atomicMax(c.flags + 1, it);
+  }
+}
+
 // --------------------------------------------------------- error norms --
 struct Err32Args {
   Params P;
@@ -1452,6 +1782,20 @@ cudaError_t launch_kick32(pic_ctx* c, double tE, bool with_coll, bool drift, dou
   return cudaGetLastError();
 }
 
+int mg_levels(int n, int* nlev_grid, size_t* work_floats) {
+  *nlev_grid = 0;
+  *work_floats = 0;
+  if (n < 16 || (n & (n - 1)) != 0) return 0;
+  int nlev = 0, first_local = -1;
+  for (int e = n; e >= 4; e >>= 1, ++nlev) {
+    if (first_local < 0 && (int64_t)e * e * e <= kMgLocalNodes) first_local = nlev;
+    if (nlev > 0) *work_floats += 3 * (size_t)e * e * e;
+  }
+  if (nlev > kMgMaxLevels) return 0;
+  *nlev_grid = first_local + 1;
+  return nlev;
+}
+
 cudaError_t launch_cg32(pic_ctx* c) {
   Cg32Args a;
   a.n = c->P.n;
@@ -1481,9 +1825,39 @@ cudaError_t launch_cg32(pic_ctx* c) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c->cg_info, 0, 3 * sizeof(int), c->stream);
   if (e != cudaSuccess) return e;
-  void* args[] = {&a};
   prof_begin(c);
-  e = cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(c->cg_grid), dim3(kCgThreads), args, 0, c->stream);
+  if (c->mg_nlev > 0) {
+    MgCg32Args m;
+    m.cg = a;
+    m.z = c->mg_z;
+    m.z2 = c->mg_z2;
+    m.nlev = c->mg_nlev;
+    m.nlev_grid = c->mg_nlev_grid;
+    float* w = c->mg_work;
+    for (int l = 0; l < m.nlev; ++l) {
+      Mg32Level& L = m.lev[l];
+      L.n = c->P.n >> l;
+      L.log2n = a.log2n - l;
+      L.inv_h2 = (float)((double)L.n * (double)L.n);
+      if (l == 0) {
+        L.ua = c->mg_z;
+        L.ub = c->mg_z2;
+        L.f = c->cgf_r;
+      } else {
+        const size_t nl = (size_t)L.n * L.n * L.n;
+        L.ua = w;
+        L.ub = w + nl;
+        L.f = w + 2 * nl;
+        w += 3 * nl;
+      }
+    }
+    for (int l = m.nlev; l < kMgMaxLevels; ++l) m.lev[l] = Mg32Level{0, 0, 0.f, nullptr, nullptr, nullptr};
+    void* args[] = {&m};
+    e = cudaLaunchCooperativeKernel((const void*)k_mgcg32, dim3(c->cg_grid), dim3(kCgThreads), args, 0, c->stream);
+  } else {
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)k_cg32, dim3(c->cg_grid), dim3(kCgThreads), args, 0, c->stream);
+  }
   prof_end(c, KC_CG);
   c->launches++;
   if (e != cudaSuccess) return e;

@@ -332,6 +332,14 @@ void for_each_buffer(pic_ctx* c, F f) {
     f((void**)&c->cgf_r, nc * 4);
     f((void**)&c->cgf_p, nc * 4);
     f((void**)&c->cgf_q, nc * 4);
+    if (c->mg_nlev > 0) {
+      int ng = 0;
+      size_t wf = 0;
+      mg_levels(c->P.n, &ng, &wf);
+      f((void**)&c->mg_z, nc * 4);
+      f((void**)&c->mg_z2, nc * 4);
+      f((void**)&c->mg_work, wf * 4);
+    }
     f((void**)&c->overlay32, lanes * 4);
   }
   for (int b = 0; b < 2; ++b) f((void**)&c->pid[b], np * 4);
@@ -745,6 +753,12 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   int64_t cg_need = (c->P.ncell + c->cg_block - 1) / c->cg_block;
   c->cg_grid = (int)(cg_need < (int64_t)occ * c->num_sms ? cg_need : (int64_t)occ * c->num_sms);
   if (c->cg_grid < 1) c->cg_grid = 1;
+  // the precision form's Poisson solve: CG preconditioned by a multigrid
+  // V-cycle on meshes of 2^k >= 16 nodes an edge, plain CG otherwise
+  if (c->mixed) {
+    size_t wf = 0;
+    c->mg_nlev = mg_levels(c->P.n, &c->mg_nlev_grid, &wf);
+  }
   // collisions: lanes = (cell in group, outcome); bitmaps in shared memory
   const int K = c->cfg.K > 0 ? c->cfg.K : 1;
   c->dsmc_Kc = K < 32 ? K : 32;

@@ -584,6 +584,10 @@ struct pic_ctx {
   double* lor[3];   // dt q/m (E_p - E^M_p) of the last kick without drift
   bool lor_valid;   // lor matches the current order, positions and field
   bool rec_state;   // the next sort reads the state from records in the staging area
+  // multigrid-preconditioned CG of the precision form (0 levels: plain CG)
+  int mg_nlev, mg_nlev_grid;
+  float *mg_z, *mg_z2;  // the preconditioned residual and a second buffer
+  float* mg_work;       // the coarse levels' iterate, second buffer and rhs, level after level
   double* dvm[3];   // source term when requested separately
 
   // precision form: int32 cell + FP32 offset, FP32 v and v^M, FP32 mesh
@@ -771,6 +775,9 @@ cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double
                            const int32_t* vm_slot = nullptr, float* const* vm_src = nullptr,
                            bool to_records = false);
 cudaError_t launch_inv_perm32(pic_ctx* c);  // c->perm[pid] = slot of pid in the current order
+// the multigrid levels of an n^3 mesh (n a power of two >= 16, else 0) and
+// the floats their coarse levels need
+int mg_levels(int n, int* nlev_grid, size_t* work_floats);
 cudaError_t launch_keys32(pic_ctx* c);
 cudaError_t launch_gather32(pic_ctx* c);
 cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate_source, double t_src);
