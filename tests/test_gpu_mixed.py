@@ -96,6 +96,35 @@ def test_mixed_field(name):
     assert np.abs(E - Eo).max() <= 1e-4 * np.abs(Eo).max()
 
 
+@pytest.mark.parametrize("n", [16, 32, 64])
+def test_multigrid_cg_field(n):
+    """Meshes of 2^k >= 16 nodes an edge solve the precision form's Poisson
+    equation by CG preconditioned with a multigrid V-cycle: at 16 and 32 the
+    whole V-cycle runs on one block, at 64 the finest level on the whole
+    grid. The field matches the oracle's textbook CG (to 1e-13) within the
+    bounds of the plain-CG cases, in a few iterations, with the stated
+    residual; CG is stopped after one iteration with PIC_ENOCONV."""
+    from paper_2602_15130_gb300._lib import PIC_ENOCONV
+
+    p = mixed(n=n, n_particles=n ** 3 * 6 + 7)
+    g, o = Pic(p), O.Oracle(dict(p, cg_tol=1e-13))
+    g.sample_mms(0.1)
+    o.sample(0.1)
+    rho, phi, E = g.get_field()
+    ro, po, Eo = o.field()
+    assert np.abs(rho - ro).max() <= 1e-6 * np.abs(ro).max()
+    assert np.abs(phi - po).max() <= 1e-4 * np.abs(po).max()
+    assert np.abs(E - Eo).max() <= 1e-4 * np.abs(Eo).max()
+    st = g.stats()
+    assert 1 <= st["cg_iters_last"] <= 12 and st["cg_res_last"] <= p["cg_tol"], st
+    g.step(2)
+    st = g.stats()
+    assert 1 <= st["cg_iters_last"] <= 12 and st["cg_res_last"] <= p["cg_tol"], st
+    one = Pic(dict(p, cg_maxit=1))
+    assert one.sample_mms(0.1, allow=(PIC_ENOCONV,)) == PIC_ENOCONV
+    assert one.stats()["cg_iters_last"] == 1
+
+
 def oracle_on_gpu_state(p, g, **kw):
     """An oracle holding exactly the precision form's FP32 state (as FP64
     numbers), with the same cells and (cell, pid) order."""
