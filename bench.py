@@ -171,7 +171,7 @@ OPS_PER_CANDIDATE = 250
 # and reports null traffic once the kernel has changed.
 NCU_TRAFFIC = {
     ("mixed", "dsmc"): {
-        "bytes_per_unit": 22.70,
+        "bytes_per_unit": 22.71,
         # the collision kernel and its device routines, its launch, and the
         # headers they include: (path, first line, line after) or whole files
         "sources": [
@@ -181,9 +181,9 @@ NCU_TRAFFIC = {
             ("paper_2602_15130_gb300/csrc/mixed_common.cuh", None, None),
             ("paper_2602_15130_gb300/csrc/pic_internal.cuh", None, None),
         ],
-        "sha16": "d16071af5357f519",
+        "sha16": "afdb8a40b24d8ae3",
         "how": "ncu --set full of k_dsmc32 at 64^3 (--workload precision64, both calls of a step): "
-               "dram__bytes_read.sum + dram__bytes_write.sum = 22.70 B per particle, times the "
+               "dram__bytes_read.sum + dram__bytes_write.sum = 22.71 B per particle, times the "
                "launch's particles (the state exceeds L2 at both sizes)",
     },
 }
@@ -246,10 +246,25 @@ def per_step(hist) -> dict:
             "n_coll": [int(r[2]) for r in hist], "n_gmax_exceed": [int(r[3]) for r in hist]}
 
 
+# The precision form solves meshes of 2^k >= 16 nodes an edge by CG
+# preconditioned with a multigrid V-cycle: an iteration then moves about
+# 125 B a fine node (the product A p, the vector updates, the V-cycle's
+# four smoothing sweeps, residual, restriction and prolongation on the
+# finest level, and about a seventh more on the coarser ones), and the
+# plain CG's per-iteration figure of the method does not apply.
+MG_CG_BYTES_PER_NODE_ITERATION = 125.0
+
+
+def multigrid_cg(p: dict, form: str) -> bool:
+    n = int(p["n"])
+    return form == "mixed" and n >= 16 and n & (n - 1) == 0
+
+
 def class_rates(p: dict, form: str, kt: dict, st: dict, hbm: float) -> dict:
     """Per kernel class: ms per launch and the achieved fraction of the
     measured HBM bandwidth by the method's bytes and by the implementation's."""
     out = {}
+    mg = multigrid_cg(p, form)
     for k, v in kt.items():
         if not v["launches"]:
             continue
@@ -259,6 +274,8 @@ def class_rates(p: dict, form: str, kt: dict, st: dict, hbm: float) -> dict:
         row = {"ms_per_launch": round(ms, 4), "launches": v["launches"], "units_per_launch": units}
         for which in ("method", "impl"):
             b = BYTES_PER_UNIT[form][which].get(k)
+            if mg and k == "cg_efield":
+                b = MG_CG_BYTES_PER_NODE_ITERATION if which == "impl" else None
             if b is not None and ms > 0:
                 gbs = b * units / (ms * 1e-3) / 1e9
                 row[f"bytes_per_unit_{which}"] = b
