@@ -1170,7 +1170,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
 // kMgLocalNodes nodes run on the whole grid between grid barriers; the
 // smaller ones on block 0 alone between block barriers.
 constexpr int kMgMaxLevels = 12;
-constexpr int kMgLocalNodes = 32768;
+constexpr int kMgLocalNodes = 4096;
 constexpr int kMgCoarseSweeps = 16;
 constexpr float kMgOmega = 6.f / 7.f;
 

@@ -99,9 +99,9 @@ def test_mixed_field(name):
 @pytest.mark.parametrize("n", [16, 32, 64])
 def test_multigrid_cg_field(n):
     """Meshes of 2^k >= 16 nodes an edge solve the precision form's Poisson
-    equation by CG preconditioned with a multigrid V-cycle: at 16 and 32 the
-    whole V-cycle runs on one block, at 64 the finest level on the whole
-    grid. The field matches the oracle's textbook CG (to 1e-13) within the
+    equation by CG preconditioned with a multigrid V-cycle: at 16 the whole
+    V-cycle runs on one block, at 32 the finest level and at 64 the two
+    finest on the whole grid. The field matches the oracle's textbook CG (to 1e-13) within the
     bounds of the plain-CG cases, in a few iterations, with the stated
     residual; CG is stopped after one iteration with PIC_ENOCONV."""
     from paper_2602_15130_gb300._lib import PIC_ENOCONV
