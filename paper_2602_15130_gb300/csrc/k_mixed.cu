@@ -1909,6 +1909,7 @@ cudaError_t launch_store_state32(pic_ctx* c, double* xv, int32_t* cell_of_pid) {
 // memory, 8-byte aligned); the inverse permutation goes into the sort's
 // free permutation buffer
 cudaError_t launch_inv_perm32(pic_ctx* c) {
+  if (c->inv_valid) return cudaSuccess;
   InvPerm32Args ia;
   ia.np = c->P.np;
   ia.pid = c->pid[c->cur];
@@ -1917,7 +1918,9 @@ cudaError_t launch_inv_perm32(pic_ctx* c) {
   k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->stream>>>(ia);
   prof_end(c, KC_OTHER);
   c->launches++;
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  c->inv_valid = e == cudaSuccess;
+  return e;
 }
 
 cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {

@@ -326,6 +326,7 @@ cudaError_t launch_keys(pic_ctx* c) {
 int64_t scan_blocks_needed(int64_t ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 
 cudaError_t launch_scan_scatter(pic_ctx* c) {
+  c->inv_valid = false;  // perm becomes the sort's permutation
   const int64_t m = c->P.ncell;
   const int64_t nb = scan_blocks_needed(m);
   prof_begin(c);
@@ -350,6 +351,7 @@ cudaError_t launch_scan_scatter(pic_ctx* c) {
 }
 
 cudaError_t launch_sort(pic_ctx* c) {
+  c->inv_valid = false;
   const int64_t m = c->P.ncell;
   cudaError_t e = launch_scan_scatter(c);
   if (e != cudaSuccess) return e;

@@ -584,6 +584,7 @@ struct pic_ctx {
   double* lor[3];   // dt q/m (E_p - E^M_p) of the last kick without drift
   bool lor_valid;   // lor matches the current order, positions and field
   bool rec_state;   // the next sort reads the state from records in the staging area
+  bool inv_valid;   // perm holds the inverse of the current sort permutation
   // multigrid-preconditioned CG of the precision form (0 levels: plain CG)
   int mg_nlev, mg_nlev_grid;
   float *mg_z, *mg_z2;  // the preconditioned residual and a second buffer
@@ -774,7 +775,9 @@ cudaError_t launch_err_final(pic_ctx* c, int nblocks);
 cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v,
                            const int32_t* vm_slot = nullptr, float* const* vm_src = nullptr,
                            bool to_records = false);
-cudaError_t launch_inv_perm32(pic_ctx* c);  // c->perm[pid] = slot of pid in the current order
+// c->perm[pid] = slot of pid in the current order (nothing to do while it
+// still holds it: no sort since the last call)
+cudaError_t launch_inv_perm32(pic_ctx* c);
 // the multigrid levels of an n^3 mesh (n a power of two >= 16, else 0) and
 // the floats their coarse levels need
 int mg_levels(int n, int* nlev_grid, size_t* work_floats);
