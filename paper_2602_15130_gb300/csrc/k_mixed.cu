@@ -1661,7 +1661,10 @@ cudaError_t launch_gather32(pic_ctx* c) {
   g.corner = c->corner;
   g.big_lo = big_cell_threshold(g.ncell, c->P.np);
   g.spid = c->pid[o];  // written in arrival order by the scatter
-  if (c->rec_state) g.rec = reinterpret_cast<const float4*>(c->stage);
+  if (c->rec_state) {
+    g.rec = reinterpret_cast<const float4*>(c->stage);
+    g.spid = nullptr;  // the pids come with the records
+  }
   // one warp per cell: blocks of consecutive cells, handed to the SMs as
   // they free up (measured faster than resident warps walking the cells
   // with a grid stride)

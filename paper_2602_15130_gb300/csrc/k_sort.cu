@@ -340,10 +340,11 @@ cudaError_t launch_scan_scatter(pic_ctx* c) {
   s.start = c->start;
   s.perm = c->perm;
   // the precision form's gather reads each cell's pids in arrival order
-  // from the output pid array (coalesced) instead of through perm
-  // (a state loaded as records is in pid order: particle j has pid j)
-  s.pid = c->mixed && !c->rec_state ? c->pid[c->cur] : nullptr;
-  s.spid = c->mixed ? c->pid[1 - c->cur] : nullptr;
+  // from the output pid array (coalesced) instead of through perm; a state
+  // loaded as records carries its pids in the records, which the gather
+  // reads anyway, so the scatter writes only perm
+  s.pid = c->mixed ? c->pid[c->cur] : nullptr;
+  s.spid = c->mixed && !c->rec_state ? c->pid[1 - c->cur] : nullptr;
   k_scatter<<<blocks_for(s.np), kThreads, 0, c->stream>>>(s);
   prof_end(c, KC_SORT);
   c->launches += 4;
