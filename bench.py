@@ -173,15 +173,17 @@ NCU_TRAFFIC = {
     ("mixed", "dsmc"): {
         "bytes_per_unit": 22.71,
         # the collision kernel and its device routines, its launch, and the
-        # headers they include: (path, first line, line after) or whole files
+        # device code of the headers they include: (path, first line, line
+        # after) or whole files
         "sources": [
             ("paper_2602_15130_gb300/csrc/k_mixed.cu", "struct Counts32 {",
              "// ------------------------------------------------------------ kick/drift --"),
             ("paper_2602_15130_gb300/csrc/k_mixed.cu", "cudaError_t launch_dsmc32(", "\n}\n"),
             ("paper_2602_15130_gb300/csrc/mixed_common.cuh", None, None),
-            ("paper_2602_15130_gb300/csrc/pic_internal.cuh", None, None),
+            ("paper_2602_15130_gb300/csrc/pic_internal.cuh", "// Internal definitions",
+             "// Context (host side)"),
         ],
-        "sha16": "afdb8a40b24d8ae3",
+        "sha16": "6e5ea5fe47ce6a84",
         "how": "ncu --set full of k_dsmc32 at 64^3 (--workload precision64, both calls of a step): "
                "dram__bytes_read.sum + dram__bytes_write.sum = 22.71 B per particle, times the "
                "launch's particles (the state exceeds L2 at both sizes)",
