@@ -788,7 +788,6 @@ __global__ void __launch_bounds__(kT, 768 / kT) kb_step(BStepArgs a) {
   float* ov = wov + (size_t)lane * a.max_ppc * 3;
   for (int i = 0; i < a.bm_words; ++i) bm[i] = 0u;
   __syncwarp();
-  CountsB cntA = {0, 0, 0, 0, 0}, cntB = {0, 0, 0, 0, 0};
   const uint32_t c0A = (uint32_t)(2 * (*a.dA.step)), c0B = c0A + 1u;
   while (true) {
     if (threadIdx.x == 0) {
@@ -827,9 +826,12 @@ __global__ void __launch_bounds__(kT, 768 / kT) kb_step(BStepArgs a) {
         case BP_DSMC_A:
         case BP_DSMC_B: {
           const BDsmcArgs& d = ph == BP_DSMC_A ? a.dA : a.dB;
+          // the item's counts leave with the item: no counters stay live
+          // across the other phases
+          CountsB cnt = {0, 0, 0, 0, 0};
           for (int gi = e.y + wib; gi < e.z; gi += wpb)
-            dsmc_group(d, d.items[gi], ph == BP_DSMC_A ? c0A : c0B, lane, bm, wov, ov,
-                       ph == BP_DSMC_A ? cntA : cntB);
+            dsmc_group(d, d.items[gi], ph == BP_DSMC_A ? c0A : c0B, lane, bm, wov, ov, cnt);
+          dsmc_counts_out(d, cnt, lane);
           break;
         }
         case BP_KICK_DRIFT:
@@ -869,8 +871,6 @@ __global__ void __launch_bounds__(kT, 768 / kT) kb_step(BStepArgs a) {
       atomicAdd(a.done + rep * BP_N + ph, 1);
     }
   }
-  dsmc_counts_out(a.dA, cntA, lane);
-  dsmc_counts_out(a.dB, cntB, lane);
 }
 
 }  // namespace
