@@ -173,17 +173,20 @@ NCU_TRAFFIC = {
     ("mixed", "dsmc"): {
         "bytes_per_unit": 22.71,
         # the collision kernel and its device routines, its launch, and the
-        # device code of the headers they include: (path, first line, line
-        # after) or whole files
+        # device code of the headers they include (the shared header up to
+        # its sort-gather section, which the collision kernel does not use):
+        # (path, first line, line after) or whole files
         "sources": [
             ("paper_2602_15130_gb300/csrc/k_mixed.cu", "struct Counts32 {",
              "// ------------------------------------------------------------ kick/drift --"),
             ("paper_2602_15130_gb300/csrc/k_mixed.cu", "cudaError_t launch_dsmc32(", "\n}\n"),
-            ("paper_2602_15130_gb300/csrc/mixed_common.cuh", None, None),
+            ("paper_2602_15130_gb300/csrc/mixed_common.cuh",
+             "// Device helpers shared by the precision-form kernels (single domain and",
+             "// ----------------------------------------------------- sort gather + CIC --"),
             ("paper_2602_15130_gb300/csrc/pic_internal.cuh", "// Internal definitions",
              "// Context (host side)"),
         ],
-        "sha16": "6e5ea5fe47ce6a84",
+        "sha16": "1042e6230ca6fbdc",
         "how": "ncu --set full of k_dsmc32 at 64^3 (--workload precision64, both calls of a step): "
                "dram__bytes_read.sum + dram__bytes_write.sum = 22.71 B per particle, times the "
                "launch's particles (the state exceeds L2 at both sizes)",
@@ -287,6 +290,32 @@ def class_rates(p: dict, form: str, kt: dict, st: dict, hbm: float) -> dict:
     return out
 
 
+def measure_link(h_in, h_out, stream, reps: int = 3) -> dict:
+    """The host link's rate each way, on the end-to-end run's own pinned
+    buffers: one cudaMemcpyAsync per copy (torch's copy of a pinned tensor),
+    timed with CUDA events on the stream. It is the ceiling of the state's
+    load and store, which read and write the same buffers over the link."""
+    import torch
+
+    d = torch.empty(h_in.shape, dtype=h_in.dtype, device="cuda")
+    nbytes = h_in.numel() * h_in.element_size()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    d.copy_(h_in, non_blocking=True)
+    ev[0].record(stream)
+    for _ in range(reps):
+        d.copy_(h_in, non_blocking=True)
+    ev[1].record(stream)
+    for _ in range(reps):
+        h_out.copy_(d, non_blocking=True)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    h2d = reps * nbytes / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
+    d2h = reps * nbytes / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
+    del d
+    return {"h2d_gbs": h2d, "d2h_gbs": d2h, "bytes": nbytes,
+            "source": "cudaMemcpyAsync of the end-to-end pinned buffers in this run"}
+
+
 def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> dict | None:
     import numpy as np
     import torch
@@ -351,11 +380,20 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
         if dist:
             td.barrier()
         t0 = time.perf_counter()
+        call_s = [0.0, 0.0, 0.0]  # each call returns with its stream synchronised
         for _ in range(e2e_steps):
+            ta = time.perf_counter()
             sim.set_state(xh, vh, 0.0, int(st["step"]))
+            tb = time.perf_counter()
             sim.step(1)
+            tc = time.perf_counter()
             sim.get_state((xh, vh))
+            te = time.perf_counter()
+            call_s[0] += tb - ta
+            call_s[1] += tc - tb
+            call_s[2] += te - tc
         e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
+        link = measure_link(xh, vh, stream)
         sim.close()
         alu = measure_alu_peaks(stream) if rank == 0 else None
     if rank != 0:
@@ -396,6 +434,12 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
                 "peak_source": peaks["source"], "bytes_per_unit": b, "units_per_launch": units,
                 "ms_per_launch": row["ms_per_launch"]}
     launches = int(st["kernel_launches"])
+    # the link's share of the end-to-end step: 48 B a particle each way
+    # (x and v in FP64) at the rates measured on the same buffers
+    e2e_ms = e2e_s * 1000.0 / e2e_steps
+    h2d_ms = npart * 48 / (link["h2d_gbs"] * 1e9) * 1e3
+    d2h_ms = npart * 48 / (link["d2h_gbs"] * 1e9) * 1e3
+    calls = {k: v * 1000.0 / e2e_steps for k, v in zip(("set_state", "step", "get_state"), call_s)}
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -406,7 +450,12 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
                    "l2": "inputs larger than L2 (particle state %.1f GB)" % (npart * (44 if form == "mixed" else 100) / 1e9)},
         "e2e": {"value": aggregate_value(npart, e2e_steps, world, e2e_s * 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": npart * 48, "d2h_bytes_per_step": npart * 48,
-                "path": "pic_set_state(host) + pic_step(1) + pic_get_state(host), pinned buffers"},
+                "path": "pic_set_state(host) + pic_step(1) + pic_get_state(host), pinned buffers",
+                "ms_per_step": e2e_ms, "ms_per_call": calls,
+                "link": dict(link, h2d_ms_floor=h2d_ms, d2h_ms_floor=d2h_ms,
+                             set_state_link_frac=h2d_ms / calls["set_state"],
+                             get_state_link_frac=d2h_ms / calls["get_state"],
+                             floor_ms_per_step=h2d_ms + d2h_ms + ms / args.steps)},
         "gpu_launches": launches,
         "roofline": roof,
         "kernels": kernels,
