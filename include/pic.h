@@ -207,6 +207,9 @@ typedef struct {
   int64_t n_floor_ties;   /* precision form: N_pairs draws whose FP32 sum lay
                              within its rounding bound of an integer, so that
                              its floor may differ from the FP64 one (flagged) */
+  int64_t binned_loads;   /* precision form: pic_set_state calls whose sort
+                             read the loaded records binned by cell (arrays
+                             used in place, every cell within its bin)      */
 } pic_stats;
 
 /* Scattering-angle CDF errors of Sec. 4.4 over every collision recorded

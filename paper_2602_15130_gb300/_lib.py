@@ -85,6 +85,7 @@ class PicStats(ctypes.Structure):
         ("tuned_block", ctypes.c_int32),
         ("tuned_tile", ctypes.c_int32),
         ("n_floor_ties", ctypes.c_int64),
+        ("binned_loads", ctypes.c_int64),
     ]
 
 

@@ -36,6 +36,11 @@ struct Sample32Args {
   // the sort: its gather reads the records at random)
   float4* rec = nullptr;
   int32_t *key = nullptr, *rank = nullptr, *count = nullptr;
+  // optional, with rec: the records also binned by cell ([ncell][bin_cap],
+  // arrival rank r at slot r); a rank at or above bin_cap sets *bin_over
+  float4* bins = nullptr;
+  int64_t bin_cap = 0;
+  int* bin_over = nullptr;
   int32_t* cell;
   float *o0, *o1, *o2, *v0, *v1, *v2, *m0, *m1, *m2;
   uint32_t* pid;
@@ -110,12 +115,24 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
   }
   const int32_t cell = ci[0] + n * (ci[1] + n * ci[2]);
   if (a.rec) {
+    const float4 r0 = make_float4(off[0], off[1], off[2], (float)v[0]);
+    const float4 r1 = make_float4((float)v[1], (float)v[2], (float)vm[0], (float)vm[1]);
+    const float4 r2 = make_float4((float)vm[2], __int_as_float(cell), __uint_as_float((uint32_t)i), 0.f);
     float4* r = a.rec + 3 * i;
-    r[0] = make_float4(off[0], off[1], off[2], (float)v[0]);
-    r[1] = make_float4((float)v[1], (float)v[2], (float)vm[0], (float)vm[1]);
-    r[2] = make_float4((float)vm[2], __int_as_float(cell), __uint_as_float((uint32_t)i), 0.f);
+    r[0] = r0; r[1] = r1; r[2] = r2;
     a.key[i] = cell;
-    a.rank[i] = cell_slot(a.count, cell);
+    const int32_t rk = cell_slot(a.count, cell);
+    a.rank[i] = rk;
+    if (a.bins) {
+      // random 48-byte stores into HBM, while the load itself waits on the
+      // host link
+      if (rk < a.bin_cap) {
+        float4* q = a.bins + 3 * ((int64_t)cell * a.bin_cap + rk);
+        q[0] = r0; q[1] = r1; q[2] = r2;
+      } else {
+        *a.bin_over = 1;
+      }
+    }
     return;
   }
   a.cell[i] = cell;
@@ -166,17 +183,25 @@ __global__ void __launch_bounds__(kThreads) k_store_state32(Store32Args a) {
   vs[3 * p] = a.v0[j]; vs[3 * p + 1] = a.v1[j]; vs[3 * p + 2] = a.v2[j];
 }
 
-// Inverse of the sort permutation: the slot of every pid.
+// Inverse of the sort permutation: the slot of every pid, in passes over
+// windows of kInvWindow pids. Each pass streams every pid and writes only
+// the slots of its window, so its random 4-byte stores land in a span L2
+// holds (64 MB) and reach HBM as whole sectors; one pass over all pids
+// scattered its stores over the whole array.
+constexpr int64_t kInvWindow = int64_t(1) << 24;
+
 struct InvPerm32Args {
   int64_t np;
   const uint32_t* pid;
   int32_t* slot;
+  int64_t lo, hi;  // the pass's window of pids
 };
 
 __global__ void __launch_bounds__(kThreads) k_inv_perm32(InvPerm32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.np) return;
-  a.slot[a.pid[j]] = (int32_t)j;
+  const int64_t p = (int64_t)__ldcs(a.pid + j);
+  if (p >= a.lo && p < a.hi) a.slot[p] = (int32_t)j;
 }
 
 // The state in pid order for a destination the kernel writes in place
@@ -251,8 +276,10 @@ __global__ void __launch_bounds__(kBigThreads) k_sort_big32(Gather32Args a) {
     while (np2 < cnt) np2 <<= 1;
     for (int e = threadIdx.x; e < np2; e += blockDim.x) {
       if (e < cnt) {
+        // never binned: a binned load holds no cell above its bin, which
+        // is at most kBigCell
         const int32_t src = a.perm[s + e];
-        key[e] = a.rec ? gather_pid32<true>(a, src) : gather_pid32<false>(a, src);
+        key[e] = a.rec ? gather_pid32<true>(a, a.rec, src) : gather_pid32<false>(a, a.rec, src);
         val[e] = src;
       } else {
         key[e] = 0xFFFFFFFFu;
@@ -264,8 +291,8 @@ __global__ void __launch_bounds__(kBigThreads) k_sort_big32(Gather32Args a) {
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const int32_t src = val[e], dst = s + e;
       float d[9];
-      if (a.rec) gather_load32<true>(a, src, d);
-      else gather_load32<false>(a, src, d);
+      if (a.rec) gather_load32<true>(a, a.rec, src, d);
+      else gather_load32<false>(a, a.rec, src, d);
 #pragma unroll
       for (int q = 0; q < 9; ++q) a.out[q][dst] = d[q];
       a.pid_out[dst] = key[e];
@@ -1158,7 +1185,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg32(Cg32Args a) {
 }
 
 // ------------------------------------------- multigrid-preconditioned CG --
-// The precision form's Poisson solve on meshes of 2^k >= 32 nodes an edge:
+// The precision form's Poisson solve on meshes of 2^k >= 16 nodes per edge:
 // CG preconditioned by one multigrid V-cycle (the same discrete system
 // -Delta_h phi = b and the same stopping rule ||r|| <= tol ||b|| as the
 // plain CG above, in far fewer iterations). Levels halve the edge down to
@@ -1622,6 +1649,11 @@ cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double
     a.key = c->key;
     a.rank = c->rank;
     a.count = c->count;
+    if (c->bins) {
+      a.bins = c->bins;
+      a.bin_cap = c->bin_cap;
+      a.bin_over = c->bin_over;
+    }
   }
   prof_begin(c);
   k_sample32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
@@ -1662,7 +1694,8 @@ cudaError_t launch_gather32(pic_ctx* c) {
   g.big_lo = big_cell_threshold(g.ncell, c->P.np);
   g.spid = c->pid[o];  // written in arrival order by the scatter
   if (c->rec_state) {
-    g.rec = reinterpret_cast<const float4*>(c->stage);
+    g.rec = c->bin_state ? c->bins : reinterpret_cast<const float4*>(c->stage);
+    g.bin_cap = c->bin_state ? c->bin_cap : 0;
     g.spid = nullptr;  // the pids come with the records
   }
   // one warp per cell: blocks of consecutive cells, handed to the SMs as
@@ -1683,6 +1716,7 @@ cudaError_t launch_gather32(pic_ctx* c) {
   c->launches++;
   c->cur = o;
   c->rec_state = false;
+  c->bin_state = false;
   return cudaGetLastError();
 }
 
@@ -1918,9 +1952,13 @@ cudaError_t launch_inv_perm32(pic_ctx* c) {
   ia.pid = c->pid[c->cur];
   ia.slot = c->perm;
   prof_begin(c);
-  k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->stream>>>(ia);
+  for (int64_t lo = 0; lo < ia.np; lo += kInvWindow) {
+    ia.lo = lo;
+    ia.hi = lo + kInvWindow < ia.np ? lo + kInvWindow : ia.np;
+    k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->stream>>>(ia);
+    c->launches++;
+  }
   prof_end(c, KC_OTHER);
-  c->launches++;
   const cudaError_t e = cudaGetLastError();
   c->inv_valid = e == cudaSuccess;
   return e;

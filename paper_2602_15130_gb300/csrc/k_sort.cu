@@ -325,14 +325,27 @@ cudaError_t launch_keys(pic_ctx* c) {
 
 int64_t scan_blocks_needed(int64_t ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 
-cudaError_t launch_scan_scatter(pic_ctx* c) {
-  c->inv_valid = false;  // perm becomes the sort's permutation
+// the three scan launches (no profiling region of their own)
+void enqueue_scan(pic_ctx* c) {
+  c->inv_valid = false;  // a new sorted order follows
   const int64_t m = c->P.ncell;
   const int64_t nb = scan_blocks_needed(m);
-  prof_begin(c);
   k_scan_reduce<<<(int)nb, kThreads, 0, c->stream>>>(c->count, m, c->scan_blocks);
   k_scan_blocks<<<1, 1024, 0, c->stream>>>(c->scan_blocks, nb);
   k_scan_final<<<(int)nb, kThreads, 0, c->stream>>>(c->count, m, c->scan_blocks, c->start);
+  c->launches += 3;
+}
+
+cudaError_t launch_scan(pic_ctx* c) {
+  prof_begin(c);
+  enqueue_scan(c);
+  prof_end(c, KC_SORT);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_scatter(pic_ctx* c) {
+  prof_begin(c);
+  enqueue_scan(c);  // perm becomes the sort's permutation
   ScatterArgs s;
   s.np = c->P.np;
   s.key = c->key;
@@ -347,7 +360,7 @@ cudaError_t launch_scan_scatter(pic_ctx* c) {
   s.spid = c->mixed && !c->rec_state ? c->pid[1 - c->cur] : nullptr;
   k_scatter<<<blocks_for(s.np), kThreads, 0, c->stream>>>(s);
   prof_end(c, KC_SORT);
-  c->launches += 4;
+  c->launches++;
   return cudaGetLastError();
 }
 

@@ -239,15 +239,19 @@ struct Gather32Args {
   // m2 cell pid -) instead of in[] and pid_in: a random source read as
   // records touches two 32-byte sectors a particle instead of nine
   const float4* rec = nullptr;
+  // records binned by cell (rec holds [ncell][bin_cap] records, a cell's
+  // arrival e at its slot e): each cell reads its own contiguous span, and
+  // perm is not used
+  int64_t bin_cap = 0;
 };
 
-// particle src of the gather's source: o0..o2, v0..v2, m0..m2 (kRec: from
-// the records)
+// particle src of the gather's source: o0..o2, v0..v2, m0..m2 (kRec: record
+// src of rb, the records or the cell's bin)
 template <bool kRec>
-__device__ __forceinline__ void gather_load32(const Gather32Args& a, int32_t src, float* d) {
+__device__ __forceinline__ void gather_load32(const Gather32Args& a, const float4* rb, int32_t src, float* d) {
   if constexpr (kRec) {
-    const float4 r0 = __ldg(a.rec + 3 * (int64_t)src), r1 = __ldg(a.rec + 3 * (int64_t)src + 1),
-                 r2 = __ldg(a.rec + 3 * (int64_t)src + 2);
+    const float4 r0 = __ldg(rb + 3 * (int64_t)src), r1 = __ldg(rb + 3 * (int64_t)src + 1),
+                 r2 = __ldg(rb + 3 * (int64_t)src + 2);
     d[0] = r0.x; d[1] = r0.y; d[2] = r0.z; d[3] = r0.w;
     d[4] = r1.x; d[5] = r1.y; d[6] = r1.z; d[7] = r1.w;
     d[8] = r2.x;
@@ -257,8 +261,8 @@ __device__ __forceinline__ void gather_load32(const Gather32Args& a, int32_t src
   }
 }
 template <bool kRec>
-__device__ __forceinline__ uint32_t gather_pid32(const Gather32Args& a, int32_t src) {
-  if constexpr (kRec) return __float_as_uint(__ldg(a.rec + 3 * (int64_t)src + 2).z);
+__device__ __forceinline__ uint32_t gather_pid32(const Gather32Args& a, const float4* rb, int32_t src) {
+  if constexpr (kRec) return __float_as_uint(__ldg(rb + 3 * (int64_t)src + 2).z);
   else return a.pid_in[src];
 }
 
@@ -330,8 +334,9 @@ __device__ __forceinline__ void store_corners_fixed(const long long* acc, int la
 // added. Up to two chunks load the particle data with the pids (one memory
 // round trip); wider cells load it after the count, to bound the registers.
 template <int C, bool kRec>
-__device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t cell, int32_t s, int32_t cnt, int lane,
-                                                const CicFixed& fx, long long* acc) {
+__device__ __forceinline__ void gather_chunks32(const Gather32Args& a, const float4* rb, bool binned, int64_t cell,
+                                                int32_t s, int32_t cnt, int lane, const CicFixed& fx,
+                                                long long* acc) {
   constexpr bool kPre = C <= 2;
   int32_t src[C];
   uint32_t p[C];
@@ -342,15 +347,15 @@ __device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t c
     src[k] = 0;
     p[k] = 0xFFFFFFFFu;
     if (e < cnt) {
-      src[k] = a.perm[s + e];
+      src[k] = binned ? e : a.perm[s + e];
       if (a.spid) p[k] = a.spid[s + e];
     }
   }
 #pragma unroll
   for (int k = 0; k < C; ++k)
     if (32 * k + lane < cnt) {
-      if (!a.spid) p[k] = gather_pid32<kRec>(a, src[k]);
-      if constexpr (kPre) gather_load32<kRec>(a, src[k], d[k]);
+      if (!a.spid) p[k] = gather_pid32<kRec>(a, rb, src[k]);
+      if constexpr (kPre) gather_load32<kRec>(a, rb, src[k], d[k]);
     }
   int r[C];
 #pragma unroll
@@ -374,7 +379,7 @@ __device__ __forceinline__ void gather_chunks32(const Gather32Args& a, int64_t c
     if (32 * k + lane < cnt) {
       const int32_t dst = s + r[k];
       float* dk = d[kPre ? k : 0];
-      if constexpr (!kPre) gather_load32<kRec>(a, src[k], dk);
+      if constexpr (!kPre) gather_load32<kRec>(a, rb, src[k], dk);
 #pragma unroll
       for (int q = 0; q < 9; ++q) a.out[q][dst] = dk[q];
       a.pid_out[dst] = p[k];
@@ -397,30 +402,39 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
   long long acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0;
+  // the source of arrival e: records at perm[s + e], or slot e of the cell's bin
+  const float4* rb = a.rec;
+  bool binned = false;
+  if constexpr (kRec) {
+    if (a.bin_cap > 0) {
+      binned = true;
+      rb += 3 * cell * a.bin_cap;
+    }
+  }
   const int32_t nch = (cnt + 31) >> 5;  // warp-uniform
   if (nch <= 1) {
-    gather_chunks32<1, kRec>(a, cell, s, cnt, lane, fx, acc);
+    gather_chunks32<1, kRec>(a, rb, binned, cell, s, cnt, lane, fx, acc);
   } else if (nch == 2) {
-    gather_chunks32<2, kRec>(a, cell, s, cnt, lane, fx, acc);
+    gather_chunks32<2, kRec>(a, rb, binned, cell, s, cnt, lane, fx, acc);
   } else if (kRegChunks >= 3 && nch == 3) {
-    if constexpr (kRegChunks >= 3) gather_chunks32<3, kRec>(a, cell, s, cnt, lane, fx, acc);
+    if constexpr (kRegChunks >= 3) gather_chunks32<3, kRec>(a, rb, binned, cell, s, cnt, lane, fx, acc);
   } else if (kRegChunks >= 4 && nch == 4) {
-    if constexpr (kRegChunks >= 4) gather_chunks32<4, kRec>(a, cell, s, cnt, lane, fx, acc);
+    if constexpr (kRegChunks >= 4) gather_chunks32<4, kRec>(a, rb, binned, cell, s, cnt, lane, fx, acc);
   } else {
     for (int32_t e0 = 0; e0 < cnt; e0 += 32) {
       const int32_t e = e0 + lane;
       int32_t src = 0;
       uint32_t mp = 0xFFFFFFFFu;
       if (e < cnt) {
-        src = a.perm[s + e];
-        mp = gather_pid32<kRec>(a, src);  // spid is pid_out: rewritten by earlier chunks
+        src = binned ? e : a.perm[s + e];
+        mp = gather_pid32<kRec>(a, rb, src);  // spid is pid_out: rewritten by earlier chunks
       }
       int32_t r = 0;
       for (int32_t f0 = 0; f0 < cnt; f0 += 32) {
         uint32_t other = mp;
         if (f0 != e0) {
           const int32_t f = f0 + lane;
-          other = f < cnt ? gather_pid32<kRec>(a, a.perm[s + f]) : 0xFFFFFFFFu;
+          other = f < cnt ? gather_pid32<kRec>(a, rb, binned ? f : a.perm[s + f]) : 0xFFFFFFFFu;
         }
         const int lim = min(32, cnt - f0);
         for (int l = 0; l < lim; ++l) r += __shfl_sync(0xffffffffu, other, l) < mp ? 1 : 0;
@@ -428,7 +442,7 @@ __device__ __forceinline__ void gather_cell32(const Gather32Args& a, int64_t cel
       if (e < cnt) {
         const int32_t dst = s + r;
         float d[9];
-        gather_load32<kRec>(a, src, d);
+        gather_load32<kRec>(a, rb, src, d);
 #pragma unroll
         for (int q = 0; q < 9; ++q) a.out[q][dst] = d[q];
         a.pid_out[dst] = mp;

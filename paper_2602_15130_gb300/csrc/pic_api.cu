@@ -421,12 +421,46 @@ pic_status check_pending(pic_ctx* c) {
 
 // sort by (cell, pid) from the current positions and solve the field at t
 // keys_done: the state load wrote the keys, ranks and counts itself
+// Bins for a state load's records, by cell: a capacity of four times the
+// mean particles per cell (a multiple of 32), if that is at most kBigCell
+// (larger cells take the block sort, which reads through perm) and the
+// bins take at most a quarter of the free device memory. Tried once per
+// context; without bins the loads take the scatter and a random gather.
+void ensure_bins(pic_ctx* c) {
+  if (c->bin_tried) return;
+  c->bin_tried = true;
+  if (c->P.ncell <= 0 || c->P.np <= 0) return;
+  const int64_t mean = (c->P.np + c->P.ncell - 1) / c->P.ncell;
+  int64_t cap = (4 * mean + 31) / 32 * 32;
+  if (cap > kBigCell) return;
+  const size_t bytes = (size_t)c->P.ncell * (size_t)cap * 48;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (bytes > free_b / 4) return;
+  c->bins = (float4*)dev_alloc(c, bytes);
+  c->bin_over = (int*)dev_alloc(c, sizeof(int));
+  if (!c->bins || !c->bin_over) {
+    dev_free(c, c->bins);
+    dev_free(c, c->bin_over);
+    c->bins = nullptr;
+    c->bin_over = nullptr;
+    return;
+  }
+  c->bin_cap = cap;
+}
+
 pic_status sort_and_field(pic_ctx* c, double t, bool keys_done = false) {
   c->lor_valid = false;
   if (!keys_done) CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
   if (c->mixed) {
     if (!keys_done) CK(launch_keys32(c));
-    CK(launch_scan_scatter(c));
+    // records binned by cell need no permutation: the gather reads each
+    // cell's bin
+    if (c->bin_state) CK(launch_scan(c));
+    else CK(launch_scan_scatter(c));
     CK(launch_gather32(c));
     CK(launch_rhs(c, t));
     CK(launch_cg32(c));
@@ -688,6 +722,8 @@ void pic_destroy(pic_ctx* c) {
   adjoint_free(c);
   dev_free(c, c->dlog);
   dev_free(c, c->dlog_n);
+  dev_free(c, c->bins);
+  dev_free(c, c->bin_over);
   for_each_buffer(c, [&](void** p, size_t) {
     dev_free(c, *p);
     *p = nullptr;
@@ -754,7 +790,7 @@ pic_status pic_create(const pic_config* cfg, void* stream, const pic_allocator* 
   c->cg_grid = (int)(cg_need < (int64_t)occ * c->num_sms ? cg_need : (int64_t)occ * c->num_sms);
   if (c->cg_grid < 1) c->cg_grid = 1;
   // the precision form's Poisson solve: CG preconditioned by a multigrid
-  // V-cycle on meshes of 2^k >= 16 nodes an edge, plain CG otherwise
+  // V-cycle on meshes of 2^k >= 16 nodes per edge, plain CG otherwise
   if (c->mixed) {
     size_t wf = 0;
     c->mg_nlev = mg_levels(c->P.n, &c->mg_nlev_grid, &wf);
@@ -915,15 +951,27 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
     const bool records = xs != c->stage && vs != c->stage + 3 * c->P.np;
     if (records) {
       if (c->sampled) CK(launch_inv_perm32(c));
+      ensure_bins(c);
       CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+      if (c->bins) CK(cudaMemsetAsync(c->bin_over, 0, sizeof(int), c->stream));
       CK(launch_sample32(c, time_at(c, (double)step), xs, vs, c->sampled ? c->perm : nullptr,
                          c->sampled ? c->vmf[c->cur] : nullptr, true));
+      bool binned = false;
+      if (c->bins) {
+        int over = 1;
+        CK(cudaMemcpyAsync(&over, c->bin_over, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        binned = over == 0;
+      }
       c->rec_state = true;
+      c->bin_state = binned;
       pic_status s = sort_and_field(c, time_at(c, (double)step), true);
       if (s != PIC_OK) {
         c->rec_state = false;
+        c->bin_state = false;
         return s;
       }
+      if (binned) c->binned_loads++;
       c->sampled = true;
       return check_pending(c);
     }
@@ -1160,6 +1208,7 @@ pic_status pic_get_stats(pic_ctx* c, pic_stats* out) {
   out->cg_iters_max = c->cg_iters_max;
   out->cg_res_last = c->cg_res_last;
   out->graph_replays = c->graph_replays;
+  out->binned_loads = c->binned_loads;
   if (c->nrep > 0 && c->tune_step >= step_candidates()) {
     out->tuned_block = step_block_of(c->step_cand);
     out->tuned_tile = step_tile_of(c->step_cand);
@@ -1177,6 +1226,7 @@ pic_status pic_reset_stats(pic_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
   c->launches = 0;
   c->cg_iters_max = 0;
+  c->binned_loads = 0;
   return PIC_OK;
 }
 

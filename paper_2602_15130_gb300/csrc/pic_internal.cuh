@@ -584,6 +584,16 @@ struct pic_ctx {
   double* lor[3];   // dt q/m (E_p - E^M_p) of the last kick without drift
   bool lor_valid;   // lor matches the current order, positions and field
   bool rec_state;   // the next sort reads the state from records in the staging area
+  // A state load's records binned by cell as well ([ncell][bin_cap]
+  // records; allocated at the first load that reads the caller's arrays
+  // in place, when they fit): the sort then reads each cell's records as
+  // one span, and skips its scatter, unless a cell outgrew its bin.
+  float4* bins;
+  int64_t bin_cap;  // 0: no bins
+  int* bin_over;    // device flag: some cell held more than bin_cap particles
+  bool bin_tried;   // the bins' allocation was attempted
+  bool bin_state;   // the next sort reads the records from the bins
+  int64_t binned_loads;  // state loads sorted from the bins (pic_stats)
   bool inv_valid;   // perm holds the inverse of the current sort permutation
   // multigrid-preconditioned CG of the precision form (0 levels: plain CG)
   int mg_nlev, mg_nlev_grid;
@@ -764,6 +774,7 @@ cudaError_t launch_batch_store_state(pic_ctx* c, int rep, double* xv);
 cudaError_t launch_store_field(pic_ctx* c, double* rho, double* phi, double* E);
 cudaError_t launch_store_sort(pic_ctx* c, int32_t* cell_of_pid, int32_t* perm);
 cudaError_t launch_store_dv(pic_ctx* c, double* dv, double* dvm);
+cudaError_t launch_scan(pic_ctx* c);           // scan of counts into start
 cudaError_t launch_scan_scatter(pic_ctx* c);   // scan of counts + scatter into perm
 cudaError_t launch_err_final(pic_ctx* c, int nblocks);
 // precision form

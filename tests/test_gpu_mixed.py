@@ -98,7 +98,7 @@ def test_mixed_field(name):
 
 @pytest.mark.parametrize("n", [16, 32, 64])
 def test_multigrid_cg_field(n):
-    """Meshes of 2^k >= 16 nodes an edge solve the precision form's Poisson
+    """Meshes of 2^k >= 16 nodes per edge solve the precision form's Poisson
     equation by CG preconditioned with a multigrid V-cycle: at 16 the whole
     V-cycle runs on one block, at 32 the finest level and at 64 the two
     finest on the whole grid. The field matches the oracle's textbook CG (to 1e-13) within the
@@ -315,6 +315,52 @@ def test_state_load_through_records_matches_the_array_path():
             (xw, vw), pw, ew, fw = want[k]
             assert np.array_equal(xs, xw) and np.array_equal(vs, vw), (where, k)
             assert np.array_equal(perm, pw) and np.array_equal(err, ew) and np.array_equal(phi, fw), (where, k)
+
+
+def test_state_load_binned_by_cell_matches_the_array_path():
+    """A state load from arrays used in place also bins its records by cell
+    (four times the mean occupancy a bin, here 192), and the sort then reads
+    each cell's bin without a scatter; a load in which a cell outgrows its
+    bin falls back to the scatter and the random gather of the records.
+    One context takes, in turn, a uniform state, one with a cell of about
+    160 particles (ranked from its bin by the chunked pairwise count), one
+    packed into five cells (its bins overflow) and the uniform one again.
+    Every load, and a step after it, must equal the pageable-array path bit
+    for bit, and the binned-load counter must show which path each took."""
+    import torch
+
+    n = 8
+    p = mixed(n=n, n_particles=n ** 3 * 40 + 7, K=4)
+    N = p["n_particles"]
+    xa, va = inputs.particles(N, seed=31)
+    xb, vb = inputs.particles(N, seed=32)
+    xb[:120] /= n  # 120 more particles in cell (0, 0, 0)
+    xc, vc = inputs.particles(N, seed=33, clustered_cells=5, n=n)
+    states = ((xa, va, True), (xb, vb, True), (xc, vc, False), (xa, va, True))
+    ref = Pic(p)
+    want = []
+    for x, v, _ in states:
+        ref.set_state(x, v, 0.1, 3)
+        sort = ref.get_sort()
+        loaded = (ref.get_state(), sort[3], ref.mms_error()["array"], ref.get_field()[1])
+        ref.step(1)
+        want.append((loaded, ref.get_state(), sort[1].max()))
+    assert 128 < want[1][2] <= 192 and want[2][2] > 192
+    places = {"pinned": lambda a: torch.from_numpy(a).pin_memory(), "cuda": lambda a: torch.from_numpy(a).cuda()}
+    for where, put in places.items():
+        g = Pic(p)
+        binned = 0
+        for k, (x, v, fits) in enumerate(states):
+            g.set_state(put(x), put(v), 0.1, 3)
+            binned += 1 if fits else 0
+            assert g.stats()["binned_loads"] == binned, (where, k)
+            (xs, vs), perm, err, phi = g.get_state(), g.get_sort()[3], g.mms_error()["array"], g.get_field()[1]
+            ((xw, vw), pw, ew, fw), (xw1, vw1), _ = want[k]
+            assert np.array_equal(xs, xw) and np.array_equal(vs, vw), (where, k)
+            assert np.array_equal(perm, pw) and np.array_equal(err, ew) and np.array_equal(phi, fw), (where, k)
+            g.step(1)
+            xs1, vs1 = g.get_state()
+            assert np.array_equal(xs1, xw1) and np.array_equal(vs1, vw1), (where, k)
 
 
 @pytest.mark.parametrize("form", ["mixed", "fp64"])
