@@ -290,37 +290,11 @@ def class_rates(p: dict, form: str, kt: dict, st: dict, hbm: float) -> dict:
     return out
 
 
-def measure_link(h_in, h_out, stream, reps: int = 3) -> dict:
-    """The host link's rate each way, on the end-to-end run's own pinned
-    buffers: one cudaMemcpyAsync per copy (torch's copy of a pinned tensor),
-    timed with CUDA events on the stream. It is the ceiling of the state's
-    load and store, which read and write the same buffers over the link."""
-    import torch
-
-    d = torch.empty(h_in.shape, dtype=h_in.dtype, device="cuda")
-    nbytes = h_in.numel() * h_in.element_size()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    d.copy_(h_in, non_blocking=True)
-    ev[0].record(stream)
-    for _ in range(reps):
-        d.copy_(h_in, non_blocking=True)
-    ev[1].record(stream)
-    for _ in range(reps):
-        h_out.copy_(d, non_blocking=True)
-    ev[2].record(stream)
-    torch.cuda.synchronize()
-    h2d = reps * nbytes / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
-    d2h = reps * nbytes / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
-    del d
-    return {"h2d_gbs": h2d, "d2h_gbs": d2h, "bytes": nbytes,
-            "source": "cudaMemcpyAsync of the end-to-end pinned buffers in this run"}
-
-
 def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> dict | None:
     import numpy as np
     import torch
 
-    from paper_2602_15130_gb300 import Pic, measure_alu_peaks, workloads as W
+    from paper_2602_15130_gb300 import Pic, measure_alu_peaks, measure_link, workloads as W
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -393,7 +367,11 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
             call_s[1] += tc - tb
             call_s[2] += te - tc
         e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
-        link = measure_link(xh, vh, stream)
+        # the host link's own rate each way, by DMA copies of the same pinned
+        # buffer (pic_measure_link): the ceiling of the state's load and store
+        lk = measure_link(xh, stream)
+        link = {"h2d_gbs": lk["h2d"] / 1e9, "d2h_gbs": lk["d2h"] / 1e9, "bytes": lk["bytes"],
+                "source": "pic_measure_link: cudaMemcpyAsync of an end-to-end pinned buffer in this run"}
         sim.close()
         alu = measure_alu_peaks(stream) if rank == 0 else None
     if rank != 0:

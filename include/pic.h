@@ -468,6 +468,22 @@ const char* pic_status_string(pic_status s);
  * error. */
 pic_status pic_measure_alu_peaks(void* cuda_stream, double out[5]);
 
+/* Rate of the host link each way, measured by DMA copies (cudaMemcpyAsync)
+ * between a caller's pinned host buffer and a device buffer of the same
+ * size on cuda_stream (NULL = legacy default stream; synchronised): one
+ * copy each way to warm up, then three host-to-device copies and three
+ * device-to-host copies, timed with events. It is the ceiling of
+ * pic_set_state and pic_get_state with pinned arrays used in place (no
+ * counterpart in the paper).
+ *  host   pinned (page-locked) host memory of at least `bytes` bytes; its
+ *         content is copied to the device and back, so it is unchanged.
+ *  bytes  > 0; the call allocates that much device memory for its duration.
+ *  out    out[0] host-to-device, out[1] device-to-host, bytes per second.
+ * PIC_EINVAL for a null or non-pinned host pointer or bytes == 0,
+ * PIC_ENOMEM if the device buffer cannot be allocated, PIC_ECUDA on a CUDA
+ * error. */
+pic_status pic_measure_link(void* host, uint64_t bytes, void* cuda_stream, double out[2]);
+
 /* Poisson solve that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when
  * they solve (a memory budget fixed at start-up, or a host framework that

@@ -338,6 +338,19 @@ def measure_alu_peaks(stream=None) -> dict:
     return dict(zip(["imad", "lop3", "ffma", "dfma", "philox_blocks"], list(out)))
 
 
+def measure_link(host, stream=None) -> dict:
+    """Rate of the host link each way (pic_measure_link), bytes per second:
+    DMA copies between the pinned host tensor ``host`` and a device buffer
+    of its size."""
+    L = load()
+    out = (ctypes.c_double * 2)()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    nbytes = host.numel() * host.element_size()
+    check(L.pic_measure_link(ctypes.c_void_p(host.data_ptr()), ctypes.c_uint64(nbytes), ctypes.c_void_p(handle), out),
+          "pic_measure_link")
+    return {"h2d": out[0], "d2h": out[1], "bytes": nbytes}
+
+
 def derived(params: dict) -> dict:
     """Host-only derived constants (no GPU needed)."""
     L = load()

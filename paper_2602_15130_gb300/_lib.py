@@ -147,6 +147,7 @@ SIGNATURES = {
     "pic_set_decision_log": (_S, [_V, ctypes.c_int32, ctypes.c_int64]),
     "pic_get_decision_log": (_S, [_V, _V, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "pic_measure_alu_peaks": (_S, [_V, _D]),
+    "pic_measure_link": (_S, [_V, ctypes.c_uint64, _V, _D]),
     "pic_poisson_solve_noalloc": (_S, [ctypes.c_int32, _V, _V, _V, ctypes.c_double, ctypes.c_int32, _V,
                                       ctypes.POINTER(ctypes.c_int32), _D]),
 }

@@ -171,3 +171,46 @@ extern "C" pic_status pic_measure_alu_peaks(void* cuda_stream, double out[5]) {
   }
   return cudaStreamSynchronize(st) == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
+
+extern "C" pic_status pic_measure_link(void* host, uint64_t bytes, void* cuda_stream, double out[2]) {
+  if (!host || bytes == 0 || !out) return PIC_EINVAL;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();
+    return PIC_EINVAL;
+  }
+  if (at.type != cudaMemoryTypeHost) return PIC_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  void* dev = nullptr;
+  if (cudaMallocAsync(&dev, (size_t)bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return PIC_ENOMEM;
+  }
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < 3 && err == cudaSuccess; ++i) err = cudaEventCreate(&ev[i]);
+  const int reps = 3;
+  // warm-up, one copy each way
+  if (err == cudaSuccess) err = cudaMemcpyAsync(dev, host, (size_t)bytes, cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(host, dev, (size_t)bytes, cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaEventRecord(ev[0], st);
+  for (int r = 0; r < reps && err == cudaSuccess; ++r)
+    err = cudaMemcpyAsync(dev, host, (size_t)bytes, cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaEventRecord(ev[1], st);
+  for (int r = 0; r < reps && err == cudaSuccess; ++r)
+    err = cudaMemcpyAsync(host, dev, (size_t)bytes, cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaEventRecord(ev[2], st);
+  if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
+  float ms[2] = {0.f, 0.f};
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+  for (int i = 0; i < 2; ++i) out[i] = (err == cudaSuccess && ms[i] > 0.f) ? reps * (double)bytes / (ms[i] * 1e-3) : 0.0;
+  cudaFreeAsync(dev, st);
+  for (int i = 0; i < 3; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  return cudaStreamSynchronize(st) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
