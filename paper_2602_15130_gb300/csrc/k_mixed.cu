@@ -208,9 +208,9 @@ __global__ void __launch_bounds__(kThreads) k_inv_perm32(InvPerm32Args a) {
 // (device memory, or pinned host memory reached over NVLink-C2C): each
 // thread gathers one pid through the inverse permutation, the block's rows
 // go through shared memory, and the stores cover contiguous spans. Same
-// arithmetic as k_store_state32.
+// arithmetic as k_store_state32. Rows row0 .. row_end - 1.
 struct StoreByPid32Args {
-  int64_t np;
+  int64_t row0, row_end;
   int n;
   double h;
   const int32_t *slot, *cell;
@@ -220,9 +220,9 @@ struct StoreByPid32Args {
 
 __global__ void __launch_bounds__(kThreads) k_store_state32_by_pid(StoreByPid32Args a) {
   __shared__ __align__(16) double sx[3 * kThreads], sv[3 * kThreads];
-  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int64_t base = a.row0 + (int64_t)blockIdx.x * kThreads;
   const int t = threadIdx.x;
-  if (base + t < a.np) {
+  if (base + t < a.row_end) {
     const int64_t j = a.slot[base + t];
     const int n = a.n, c = a.cell[j];
     const int ci = c % n, cj = (c / n) % n, ck = c / (n * n);
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_store_state32_by_pid(StoreByPid32A
     sv[3 * t] = a.v0[j]; sv[3 * t + 1] = a.v1[j]; sv[3 * t + 2] = a.v2[j];
   }
   __syncthreads();
-  const int64_t rows = a.np - base < kThreads ? a.np - base : kThreads;
+  const int64_t rows = a.row_end - base < kThreads ? a.row_end - base : kThreads;
   double* gx = a.x + 3 * base;
   double* gv = a.v + 3 * base;
   if (rows == kThreads && ((reinterpret_cast<uintptr_t>(gx) | reinterpret_cast<uintptr_t>(gv)) & 15) == 0) {
@@ -1964,12 +1964,16 @@ cudaError_t launch_inv_perm32(pic_ctx* c) {
   return e;
 }
 
+// Without a valid inverse permutation the store goes by windows of
+// kInvWindow pids: window r's inverse is formed on the context's auxiliary
+// stream (higher priority) while the store of window r - 1, which waits on
+// the host link when the destination is pinned host memory, runs on the
+// context's stream; only the first window's pass is not hidden.
 cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {
   const int b = c->cur;
-  cudaError_t e = launch_inv_perm32(c);
-  if (e != cudaSuccess) return e;
   StoreByPid32Args a;
-  a.np = c->P.np;
+  a.row0 = 0;
+  a.row_end = c->P.np;
   a.n = c->P.n;
   a.h = c->P.h;
   a.slot = c->perm;
@@ -1978,11 +1982,43 @@ cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {
   a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
   a.x = x;
   a.v = v;
+  if (c->inv_valid) {
+    prof_begin(c);
+    k_store_state32_by_pid<<<blocks_for(a.row_end), kThreads, 0, c->stream>>>(a);
+    prof_end(c, KC_OTHER);
+    c->launches++;
+    return cudaGetLastError();
+  }
+  cudaError_t e = ensure_aux_stream(c);
+  if (e != cudaSuccess) return e;
+  InvPerm32Args ia;
+  ia.np = c->P.np;
+  ia.pid = c->pid[b];
+  ia.slot = c->perm;
   prof_begin(c);
-  k_store_state32_by_pid<<<blocks_for(a.np), kThreads, 0, c->stream>>>(a);
+  // the auxiliary stream starts after the work already on the context's
+  e = cudaEventRecord(c->aux_fork, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->aux_fork, 0);
+  for (int64_t lo = 0; lo < ia.np && e == cudaSuccess; lo += kInvWindow) {
+    ia.lo = lo;
+    ia.hi = lo + kInvWindow < ia.np ? lo + kInvWindow : ia.np;
+    k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->aux>>>(ia);
+    c->launches++;
+    // the wait takes the record made just before it, so one event serves
+    // every window
+    e = cudaEventRecord(c->aux_join, c->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->aux_join, 0);
+    if (e == cudaSuccess) {
+      a.row0 = ia.lo;
+      a.row_end = ia.hi;
+      k_store_state32_by_pid<<<blocks_for(ia.hi - ia.lo), kThreads, 0, c->stream>>>(a);
+      c->launches++;
+    }
+  }
   prof_end(c, KC_OTHER);
-  c->launches++;
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  c->inv_valid = e == cudaSuccess;
+  return e;
 }
 
 // replicate rep of a batch: the single-domain kernels on its sub-ranges

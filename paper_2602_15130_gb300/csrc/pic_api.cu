@@ -612,6 +612,30 @@ void* ctx_alloc(pic_ctx* c, size_t bytes) { return dev_alloc(c, bytes); }
 void dev_free_ctx(pic_ctx* c, void* p) { dev_free(c, p); }
 void ctx_free(pic_ctx* c, void* p) { dev_free(c, p); }
 
+// The context's auxiliary stream (non-blocking, the device's highest
+// priority, so that its short kernels start as soon as SMs free up) and its
+// fork and join events, created at first use.
+cudaError_t ensure_aux_stream(pic_ctx* c) {
+  if (c->aux) return cudaSuccess;
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaStream_t s = nullptr;
+  cudaEvent_t f = nullptr, j = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    if (j) cudaEventDestroy(j);
+    if (f) cudaEventDestroy(f);
+    if (s) cudaStreamDestroy(s);
+    return e;
+  }
+  c->aux = s;
+  c->aux_fork = f;
+  c->aux_join = j;
+  return cudaSuccess;
+}
+
 // One FP64 step of Eq. velocity_verlet. hook(where), if given, runs at
 // 0: the start (x^n, v^n in the current buffers), 1: after the drift and the
 // sort (x^{n+1}, v^{n+1/2}), 2: after the field solve (E^{n+1}).
@@ -724,6 +748,12 @@ void pic_destroy(pic_ctx* c) {
   dev_free(c, c->dlog_n);
   dev_free(c, c->bins);
   dev_free(c, c->bin_over);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaEventDestroy(c->aux_fork);
+    cudaEventDestroy(c->aux_join);
+    cudaStreamDestroy(c->aux);
+  }
   for_each_buffer(c, [&](void** p, size_t) {
     dev_free(c, *p);
     *p = nullptr;

@@ -595,6 +595,10 @@ struct pic_ctx {
   bool bin_state;   // the next sort reads the records from the bins
   int64_t binned_loads;  // state loads sorted from the bins (pic_stats)
   bool inv_valid;   // perm holds the inverse of the current sort permutation
+  // auxiliary stream (created at first use, higher priority) and its fork
+  // and join events: the inverse permutation overlaps the state store
+  cudaStream_t aux;
+  cudaEvent_t aux_fork, aux_join;
   // multigrid-preconditioned CG of the precision form (0 levels: plain CG)
   int mg_nlev, mg_nlev_grid;
   float *mg_z, *mg_z2;  // the preconditioned residual and a second buffer
@@ -789,6 +793,7 @@ cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double
 // c->perm[pid] = slot of pid in the current order (nothing to do while it
 // still holds it: no sort since the last call)
 cudaError_t launch_inv_perm32(pic_ctx* c);
+cudaError_t ensure_aux_stream(pic_ctx* c);    // the auxiliary stream and its events
 // the multigrid levels of an n^3 mesh (n a power of two >= 16, else 0) and
 // the floats their coarse levels need
 int mg_levels(int n, int* nlev_grid, size_t* work_floats);
