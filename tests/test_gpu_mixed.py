@@ -372,7 +372,7 @@ def test_state_store_by_pid_windows_matches_the_staged_path():
     two windows, the second ragged) the pinned and device destinations must
     equal the staged path's (pageable arrays) bit for bit after steps, and a
     state load from them, which keeps v^M through that inverse, must give
-    the same state and error norms back."""
+    the same state and the same particle error norms back."""
     import torch
 
     n = 64
@@ -394,7 +394,13 @@ def test_state_store_by_pid_windows_matches_the_staged_path():
         g.set_state(out[0], out[1], 0.0, int(g.stats()["step"]))
         x2, v2 = g.get_state()
         assert np.array_equal(x2, x1) and np.array_equal(v2, v1), where
-        assert np.array_equal(g.mms_error()["array"], e1), where
+        # the particles' norms (eps2, epsinf of x, y, z, u, v, w) depend on
+        # the v^M kept through the inverse: bit for bit; the load solves the
+        # field again (CG from the last potential, to 1e-6), so phi's move
+        e2 = g.mms_error()["array"]
+        part = np.r_[0:6, 7:13]
+        assert np.array_equal(e2[part], e1[part]), where
+        assert np.allclose(e2[[6, 13]], e1[[6, 13]], rtol=1e-3), (where, e2[[6, 13]], e1[[6, 13]])
     assert not np.array_equal(x1, x0) and e0.shape == e1.shape
 
 
