@@ -25,6 +25,7 @@ inline int blocks_for(int64_t n, int t = kThreads) {
 struct Sample32Args {
   Params P;
   TimeTerms tt;
+  int64_t row0, row_end;  // the particles (pids) this launch takes
   const double *xs, *vs;  // optional caller state (pid order, [N][3] each; device or mapped host)
   // optional v^M (tau for the paper's f_v) to keep: a context's sorted
   // arrays, read for pid i at vslot[i] (the inverse sort permutation)
@@ -53,11 +54,11 @@ struct Sample32Args {
 // shared-memory reads.
 __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
   __shared__ __align__(16) double sxs[3 * kThreads], svs[3 * kThreads];
-  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int64_t base = a.row0 + (int64_t)blockIdx.x * kThreads;
   const int64_t i = base + threadIdx.x;
   const Params& P = a.P;
   if (a.xs) {
-    const int64_t rows = P.np - base < kThreads ? P.np - base : kThreads;
+    const int64_t rows = a.row_end - base < kThreads ? a.row_end - base : kThreads;
     const double* gx = a.xs + 3 * base;
     const double* gv = a.vs + 3 * base;
     if (rows == kThreads && ((reinterpret_cast<uintptr_t>(gx) | reinterpret_cast<uintptr_t>(gv)) & 15) == 0) {
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_sample32(Sample32Args a) {
     }
     __syncthreads();
   }
-  if (i >= P.np) return;
+  if (i >= a.row_end) return;
   double xi[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const bool given_vm = a.vslot != nullptr;
   const int32_t vj = given_vm ? a.vslot[i] : 0;
@@ -197,11 +198,29 @@ struct InvPerm32Args {
   int64_t lo, hi;  // the pass's window of pids
 };
 
+// One thread per pid: the fastest pass on its own.
 __global__ void __launch_bounds__(kThreads) k_inv_perm32(InvPerm32Args a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.np) return;
   const int64_t p = (int64_t)__ldcs(a.pid + j);
   if (p >= a.lo && p < a.hi) a.slot[p] = (int32_t)j;
+}
+
+// Grid-stride, four independent loads a thread in flight, for a small grid
+// that leaves the SMs to a kernel running beside it.
+__global__ void __launch_bounds__(kThreads) k_inv_perm32_gs(InvPerm32Args a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < a.np; j0 += 4 * stride) {
+    int64_t p[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = j0 + u * stride;
+      p[u] = j < a.np ? (int64_t)__ldcs(a.pid + j) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (p[u] >= a.lo && p[u] < a.hi) a.slot[p[u]] = (int32_t)(j0 + u * stride);
+  }
 }
 
 // The state in pid order for a destination the kernel writes in place
@@ -1627,17 +1646,55 @@ __global__ void __launch_bounds__(kThreads) k_store_dv32(StoreDv32Args a) {
 }  // namespace
 
 // ============================================================== launches ==
-cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v, const int32_t* vm_slot,
-                            float* const* vm_src, bool to_records) {
+// The inverse of a sort permutation (slot[pid[j]] = j) by windows of
+// kInvWindow pids, each window's pass on the context's auxiliary stream
+// (higher priority) ahead of consume(lo, hi), which the caller launches on
+// the context's stream for the rows (pids) lo .. hi - 1 of a load or store
+// that waits on the host link: window r's pass runs beside the consumer of
+// window r - 1. Only the first pass is not hidden; it takes a grid of one
+// thread per pid, the later ones two blocks per SM, so that they do not
+// hold the SMs the consumer needs (full-grid passes there took every SM a
+// consumer block freed, and the two kernels took turns).
+template <class Consume>
+cudaError_t inverse_by_windows(pic_ctx* c, const uint32_t* pid, Consume consume) {
+  cudaError_t e = ensure_aux_stream(c);
+  if (e != cudaSuccess) return e;
+  InvPerm32Args ia;
+  ia.np = c->P.np;
+  ia.pid = pid;
+  ia.slot = c->perm;
+  // the auxiliary stream starts after the work already on the context's
+  e = cudaEventRecord(c->aux_fork, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->aux_fork, 0);
+  for (int64_t lo = 0; lo < ia.np && e == cudaSuccess; lo += kInvWindow) {
+    ia.lo = lo;
+    ia.hi = lo + kInvWindow < ia.np ? lo + kInvWindow : ia.np;
+    if (lo == 0)
+      k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->aux>>>(ia);
+    else
+      k_inv_perm32_gs<<<2 * c->num_sms, kThreads, 0, c->aux>>>(ia);
+    c->launches++;
+    // the wait takes the record made just before it, so one event serves
+    // every window
+    e = cudaEventRecord(c->aux_join, c->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->aux_join, 0);
+    if (e == cudaSuccess) consume(ia.lo, ia.hi);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v, int held, bool to_records) {
   Sample32Args a;
   a.P = c->P;
   a.tt = time_terms(c->P, t0);
+  a.row0 = 0;
+  a.row_end = c->P.np;
   a.xs = x;
   a.vs = v;
-  a.vslot = vm_slot;
-  a.vin0 = vm_slot ? vm_src[0] : nullptr;
-  a.vin1 = vm_slot ? vm_src[1] : nullptr;
-  a.vin2 = vm_slot ? vm_src[2] : nullptr;
+  a.vslot = held >= 0 ? c->perm : nullptr;
+  a.vin0 = held >= 0 ? c->vmf[held][0] : nullptr;
+  a.vin1 = held >= 0 ? c->vmf[held][1] : nullptr;
+  a.vin2 = held >= 0 ? c->vmf[held][2] : nullptr;
   const int b = c->cur;
   a.cell = c->cell32[b];
   a.o0 = c->off[b][0]; a.o1 = c->off[b][1]; a.o2 = c->off[b][2];
@@ -1655,11 +1712,26 @@ cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double
       a.bin_over = c->bin_over;
     }
   }
+  if (held < 0 || c->inv_valid) {
+    prof_begin(c);
+    k_sample32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
+    prof_end(c, x ? KC_OTHER : KC_SAMPLE);
+    c->launches++;
+    return cudaGetLastError();
+  }
+  // v^M read through the inverse of the held state's permutation, formed
+  // by windows ahead of the load of the same rows (pids)
   prof_begin(c);
-  k_sample32<<<blocks_for(c->P.np), kThreads, 0, c->stream>>>(a);
-  prof_end(c, x ? KC_OTHER : KC_SAMPLE);
-  c->launches++;
-  return cudaGetLastError();
+  const cudaError_t e = inverse_by_windows(c, c->pid[held], [&](int64_t lo, int64_t hi) {
+    a.row0 = lo;
+    a.row_end = hi;
+    k_sample32<<<blocks_for(hi - lo), kThreads, 0, c->stream>>>(a);
+    c->launches++;
+  });
+  prof_end(c, KC_OTHER);
+  // perm now holds the inverse of the held state's order, which the sort
+  // that follows replaces
+  return e;
 }
 
 cudaError_t launch_keys32(pic_ctx* c) {
@@ -1945,30 +2017,9 @@ cudaError_t launch_store_state32(pic_ctx* c, double* xv, int32_t* cell_of_pid) {
 // x, v [N_p][3] in pid order written in place (device or mapped pinned host
 // memory, 8-byte aligned); the inverse permutation goes into the sort's
 // free permutation buffer
-cudaError_t launch_inv_perm32(pic_ctx* c) {
-  if (c->inv_valid) return cudaSuccess;
-  InvPerm32Args ia;
-  ia.np = c->P.np;
-  ia.pid = c->pid[c->cur];
-  ia.slot = c->perm;
-  prof_begin(c);
-  for (int64_t lo = 0; lo < ia.np; lo += kInvWindow) {
-    ia.lo = lo;
-    ia.hi = lo + kInvWindow < ia.np ? lo + kInvWindow : ia.np;
-    k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->stream>>>(ia);
-    c->launches++;
-  }
-  prof_end(c, KC_OTHER);
-  const cudaError_t e = cudaGetLastError();
-  c->inv_valid = e == cudaSuccess;
-  return e;
-}
 
-// Without a valid inverse permutation the store goes by windows of
-// kInvWindow pids: window r's inverse is formed on the context's auxiliary
-// stream (higher priority) while the store of window r - 1, which waits on
-// the host link when the destination is pinned host memory, runs on the
-// context's stream; only the first window's pass is not hidden.
+// Into arrays in pid order used in place; without a valid inverse the
+// store goes by windows of the inverse.
 cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {
   const int b = c->cur;
   StoreByPid32Args a;
@@ -1982,42 +2033,22 @@ cudaError_t launch_store_state32_by_pid(pic_ctx* c, double* x, double* v) {
   a.v0 = c->vf[b][0]; a.v1 = c->vf[b][1]; a.v2 = c->vf[b][2];
   a.x = x;
   a.v = v;
-  if (c->inv_valid) {
-    prof_begin(c);
-    k_store_state32_by_pid<<<blocks_for(a.row_end), kThreads, 0, c->stream>>>(a);
-    prof_end(c, KC_OTHER);
-    c->launches++;
-    return cudaGetLastError();
-  }
-  cudaError_t e = ensure_aux_stream(c);
-  if (e != cudaSuccess) return e;
-  InvPerm32Args ia;
-  ia.np = c->P.np;
-  ia.pid = c->pid[b];
-  ia.slot = c->perm;
   prof_begin(c);
-  // the auxiliary stream starts after the work already on the context's
-  e = cudaEventRecord(c->aux_fork, c->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->aux_fork, 0);
-  for (int64_t lo = 0; lo < ia.np && e == cudaSuccess; lo += kInvWindow) {
-    ia.lo = lo;
-    ia.hi = lo + kInvWindow < ia.np ? lo + kInvWindow : ia.np;
-    k_inv_perm32<<<blocks_for(ia.np), kThreads, 0, c->aux>>>(ia);
+  cudaError_t e;
+  if (c->inv_valid) {
+    k_store_state32_by_pid<<<blocks_for(a.row_end), kThreads, 0, c->stream>>>(a);
     c->launches++;
-    // the wait takes the record made just before it, so one event serves
-    // every window
-    e = cudaEventRecord(c->aux_join, c->aux);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->aux_join, 0);
-    if (e == cudaSuccess) {
-      a.row0 = ia.lo;
-      a.row_end = ia.hi;
-      k_store_state32_by_pid<<<blocks_for(ia.hi - ia.lo), kThreads, 0, c->stream>>>(a);
+    e = cudaGetLastError();
+  } else {
+    e = inverse_by_windows(c, c->pid[b], [&](int64_t lo, int64_t hi) {
+      a.row0 = lo;
+      a.row_end = hi;
+      k_store_state32_by_pid<<<blocks_for(hi - lo), kThreads, 0, c->stream>>>(a);
       c->launches++;
-    }
+    });
+    c->inv_valid = e == cudaSuccess;
   }
   prof_end(c, KC_OTHER);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  c->inv_valid = e == cudaSuccess;
   return e;
 }
 

@@ -980,12 +980,10 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
     // reads in two sectors a particle instead of nine.
     const bool records = xs != c->stage && vs != c->stage + 3 * c->P.np;
     if (records) {
-      if (c->sampled) CK(launch_inv_perm32(c));
       ensure_bins(c);
       CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
       if (c->bins) CK(cudaMemsetAsync(c->bin_over, 0, sizeof(int), c->stream));
-      CK(launch_sample32(c, time_at(c, (double)step), xs, vs, c->sampled ? c->perm : nullptr,
-                         c->sampled ? c->vmf[c->cur] : nullptr, true));
+      CK(launch_sample32(c, time_at(c, (double)step), xs, vs, c->sampled ? c->cur : -1, true));
       bool binned = false;
       if (c->bins) {
         int over = 1;
@@ -1006,10 +1004,9 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
       return check_pending(c);
     }
     if (c->sampled) {
-      CK(launch_inv_perm32(c));
       const int src = c->cur;
       c->cur = 1 - src;
-      CK(launch_sample32(c, time_at(c, (double)step), xs, vs, c->perm, c->vmf[src]));
+      CK(launch_sample32(c, time_at(c, (double)step), xs, vs, src));
     } else {
       c->cur = 0;
       CK(launch_sample32(c, time_at(c, (double)step), xs, vs));

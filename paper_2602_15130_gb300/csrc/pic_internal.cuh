@@ -782,17 +782,14 @@ cudaError_t launch_scan(pic_ctx* c);           // scan of counts into start
 cudaError_t launch_scan_scatter(pic_ctx* c);   // scan of counts + scatter into perm
 cudaError_t launch_err_final(pic_ctx* c, int nblocks);
 // precision form
-// vm_slot, vm_src: v^M (tau) to keep instead of recomputing them (state
-// loads), read from the sorted arrays vm_src at the inverse permutation
-// to_records: write the state into the staging area as 48-byte records with
-// their cell keys and ranks (sort_and_field then skips the keys), for a
-// state load whose caller arrays are used in place
-cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v,
-                           const int32_t* vm_slot = nullptr, float* const* vm_src = nullptr,
+// held >= 0: the buffer of a state the context holds, whose v^M (tau) the
+// load keeps instead of recomputing them, read from its sorted arrays at
+// the inverse of its sort permutation (formed here when perm does not hold
+// it); to_records: write the state into the staging area as 48-byte records
+// with their cell keys and ranks (sort_and_field then skips the keys), for
+// a state load whose caller arrays are used in place
+cudaError_t launch_sample32(pic_ctx* c, double t0, const double* x, const double* v, int held = -1,
                            bool to_records = false);
-// c->perm[pid] = slot of pid in the current order (nothing to do while it
-// still holds it: no sort since the last call)
-cudaError_t launch_inv_perm32(pic_ctx* c);
 cudaError_t ensure_aux_stream(pic_ctx* c);    // the auxiliary stream and its events
 // the multigrid levels of an n^3 mesh (n a power of two >= 16, else 0) and
 // the floats their coarse levels need

@@ -372,7 +372,8 @@ def test_state_store_by_pid_windows_matches_the_staged_path():
     two windows, the second ragged) the pinned and device destinations must
     equal the staged path's (pageable arrays) bit for bit after steps, and a
     state load from them, which keeps v^M through that inverse, must give
-    the same state and the same particle error norms back."""
+    the same state and the same particle error norms back; so must a load
+    right after a step, which forms the inverse by windows itself."""
     import torch
 
     n = 64
@@ -402,6 +403,16 @@ def test_state_store_by_pid_windows_matches_the_staged_path():
         assert np.array_equal(e2[part], e1[part]), where
         assert np.allclose(e2[[6, 13]], e1[[6, 13]], rtol=1e-3), (where, e2[[6, 13]], e1[[6, 13]])
     assert not np.array_equal(x1, x0) and e0.shape == e1.shape
+    # a load right after a step forms the inverse itself, window by window
+    # ahead of the load of the same pids
+    g.step(1)
+    x3, v3 = g.get_state()  # the staged store does not form the inverse
+    e3 = g.mms_error()["array"]
+    g.set_state(torch.from_numpy(x3).pin_memory(), torch.from_numpy(v3).pin_memory(), 0.0, int(g.stats()["step"]))
+    x4, v4 = g.get_state()
+    assert np.array_equal(x4, x3) and np.array_equal(v4, v3)
+    part = np.r_[0:6, 7:13]
+    assert np.array_equal(g.mms_error()["array"][part], e3[part])
 
 
 @pytest.mark.parametrize("form", ["mixed", "fp64"])
