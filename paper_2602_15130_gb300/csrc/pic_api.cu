@@ -475,6 +475,34 @@ pic_status sort_and_field(pic_ctx* c, double t, bool keys_done = false) {
 
 double time_at(const pic_ctx* c, double steps) { return c->t0 + steps * c->cfg.dt; }
 
+// The precision form's state in pid order (sampled, or a caller's rows used
+// in place, keeping the v^M of a held state buffer) written by the sampling
+// kernel as records in the staging area and into the per-cell bins, then
+// sorted with its field: from the bins, or, when a cell outgrew its bin
+// (or there are no bins), by the scatter and a random gather of the
+// records. *binned: the sort read the bins.
+pic_status records_then_sort(pic_ctx* c, double t, const double* xs, const double* vs, int held, bool* binned) {
+  ensure_bins(c);
+  CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
+  if (c->bins) CK(cudaMemsetAsync(c->bin_over, 0, sizeof(int), c->stream));
+  CK(launch_sample32(c, t, xs, vs, held, true));
+  *binned = false;
+  if (c->bins) {
+    int over = 1;
+    CK(cudaMemcpyAsync(&over, c->bin_over, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *binned = over == 0;
+  }
+  c->rec_state = true;
+  c->bin_state = *binned;
+  pic_status s = sort_and_field(c, t, true);
+  if (s != PIC_OK) {
+    c->rec_state = false;
+    c->bin_state = false;
+  }
+  return s;
+}
+
 // Per-replicate time terms of step n (t_n, t_{n+1/2}, t_{n+1}) and the step
 // number into the pinned mirror (every replicate has its own dt); the copy
 // to the device is enqueued by batch_enqueue_times (and captured in graphs).
@@ -941,8 +969,14 @@ pic_status pic_sample_mms(pic_ctx* c, double t0) {
   }
   if (c->ang_hist) CK(cudaMemsetAsync(c->ang_hist, 0, (size_t)2 * PIC_ANGLE_BINS * 8, c->stream));
   if (c->mixed) {
+    // the sampled state is in pid order, which the first sort would read
+    // at random: through the records and the bins, as a state load
     CK(cudaMemsetAsync(c->phif, 0, (size_t)c->P.ncell * 4, c->stream));
-    CK(launch_sample32(c, t0, nullptr, nullptr));
+    bool binned = false;
+    pic_status s = records_then_sort(c, t0, nullptr, nullptr, -1, &binned);
+    if (s != PIC_OK) return s;
+    c->sampled = true;
+    return check_pending(c);
   } else {
     CK(cudaMemsetAsync(c->phi, 0, (size_t)c->P.ncell * 8, c->stream));
     CK(launch_sample(c, t0));
@@ -980,25 +1014,9 @@ pic_status pic_set_state(pic_ctx* c, const double* x, const double* v, double t0
     // reads in two sectors a particle instead of nine.
     const bool records = xs != c->stage && vs != c->stage + 3 * c->P.np;
     if (records) {
-      ensure_bins(c);
-      CK(cudaMemsetAsync(c->count, 0, (size_t)c->P.ncell * 4, c->stream));
-      if (c->bins) CK(cudaMemsetAsync(c->bin_over, 0, sizeof(int), c->stream));
-      CK(launch_sample32(c, time_at(c, (double)step), xs, vs, c->sampled ? c->cur : -1, true));
       bool binned = false;
-      if (c->bins) {
-        int over = 1;
-        CK(cudaMemcpyAsync(&over, c->bin_over, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        binned = over == 0;
-      }
-      c->rec_state = true;
-      c->bin_state = binned;
-      pic_status s = sort_and_field(c, time_at(c, (double)step), true);
-      if (s != PIC_OK) {
-        c->rec_state = false;
-        c->bin_state = false;
-        return s;
-      }
+      pic_status s = records_then_sort(c, time_at(c, (double)step), xs, vs, c->sampled ? c->cur : -1, &binned);
+      if (s != PIC_OK) return s;
       if (binned) c->binned_loads++;
       c->sampled = true;
       return check_pending(c);
