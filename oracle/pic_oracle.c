@@ -810,9 +810,11 @@ int64_t orc_field(orc_state* s, double t) {
  * run K times from the same pre-collision velocities and averaged
  * (Eq. avg_outcome). Draws for call counter c0 = 2 step + phase, cell k,
  * outcome o:
- *   N_pairs : Philox(c0, k, 0xFFFFFFFF, o<<8)      -> U52(w0, w1)
+ *   N_pairs : Philox(c0, k, 0, o<<8 | 1), word 0   -> U32
  *   pair s  : Philox(c0, k, s, o<<8 | 0)  = (p, q, accept, epsilon)
- *             Philox(c0, k, s/4, o<<8 | 1), word s mod 4 = chi
+ *             Philox(c0, k, (s+1)/4, o<<8 | 1), word (s+1) mod 4 = chi
+ * (the o<<8 | 1 stream's words in order: the N_pairs uniform, then one chi
+ * per candidate)
  * p = floor(U c) over the c particles; q = floor(U (c-1)) over the other
  * c - 1, counted past p (q' >= p gives q' + 1). That is the distribution of
  * Algorithm 1's second draw repeated until it differs from the first:
@@ -909,18 +911,18 @@ static void ntc_one_outcome(const orc_cfg* cf, uint32_t c0, uint32_t cellk, uint
   double sg_max = orc_sg_max(cf);                     /* (sigma g)_max              */
   double Pmax = orc_pmax(cf);
   uint32_t u[4];
-  philox4(c0, cellk, 0xFFFFFFFFu, o << 8, cf->seed, u);
-  double npairs_real = ((double)(c * (c - 1)) * Pmax) * 0.5 + orc_u52(u[0], u[1]);
+  philox4(c0, cellk, 0u, (o << 8) | 1u, cf->seed, u);
+  double npairs_real = ((double)(c * (c - 1)) * Pmax) * 0.5 + orc_u32(u[0]);
   int64_t npairs = (int64_t)floor(npairs_real);       /* Algorithm 1: NTC pair count */
   log_pair(st->log, c0, cellk, o, -1, -1, -1, npairs, 4);
   for (int64_t sl = 0; sl < npairs; sl++) {
     uint32_t b0[4], bchi[4];
     philox4(c0, cellk, (uint32_t)sl, (o << 8) | 0u, cf->seed, b0);
-    philox4(c0, cellk, (uint32_t)(sl / 4), (o << 8) | 1u, cf->seed, bchi);
+    philox4(c0, cellk, (uint32_t)((sl + 1) / 4), (o << 8) | 1u, cf->seed, bchi);
     uint32_t p = orc_index(b0[0], (uint32_t)c);
     uint32_t q = orc_index(b0[1], (uint32_t)(c - 1)); /* one of the others */
     if (q >= p) q++;
-    uint32_t wchi = bchi[sl % 4];
+    uint32_t wchi = bchi[(sl + 1) % 4];
     st->n_cand++;
     double* vp = vloc + 3 * p;
     double* vq = vloc + 3 * q;
