@@ -412,19 +412,20 @@ struct CountsB {
 // Algorithm 1 for one (cell, outcome), as in the single-domain FP32 kernel.
 __device__ void ntc_outcome_b(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
                               const float* v1, const float* v2, uint32_t* bm, float* ov, CountsB& cnt) {
-  const U4 u = philox<true>(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
+  // the chi stream: word 0 of slot 0 is the N_pairs uniform, word (s + 1)
+  // mod 4 of slot (s + 1) / 4 the chi of candidate s
+  U4 bchi = philox<true>(c0, cell, 0u, (o << 8) | 1u, P.key0, P.key1);
   const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
-  const float S = base + unif24(u.x);
+  const float S = base + unif24(bchi.x);
   const int npairs = (int)floorf(S);
   // flagged FP32 decisions: the bounds of the single-domain kernel
   if (fabsf(S - rintf(S)) <= fmaf(base + S, 0x1p-22f, 0x1p-24f)) ++cnt.ftie;
-  // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon);
-  // chi is word s mod 4 of block (c0, cell, s / 4, (o << 8) | 1)
-  U4 bchi{0u, 0u, 0u, 0u};
+  // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon)
   for (int s = 0; s < npairs; ++s) {
     const U4 b0 = philox<true>(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
-    if ((s & 3) == 0) bchi = philox<true>(c0, cell, (uint32_t)(s >> 2), (o << 8) | 1u, P.key0, P.key1);
-    const uint32_t wchi = (s & 3) == 0 ? bchi.x : (s & 3) == 1 ? bchi.y : (s & 3) == 2 ? bchi.z : bchi.w;
+    const int js = s + 1;
+    if ((js & 3) == 0) bchi = philox<true>(c0, cell, (uint32_t)(js >> 2), (o << 8) | 1u, P.key0, P.key1);
+    const uint32_t wchi = (js & 3) == 0 ? bchi.x : (js & 3) == 1 ? bchi.y : (js & 3) == 2 ? bchi.z : bchi.w;
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
     // q uniform over the other c - 1 particles
     uint32_t q = draw_index(b0.y, (uint32_t)(c - 1));

@@ -420,7 +420,7 @@ __device__ __forceinline__ void vel_put(int p, const float* v, uint32_t* bm, flo
 // evaluation of the same draws are counted and, with a decision log, logged:
 //  - N_pairs = floor(S), S = base + U: base carries 2^-23 relative error
 //    (P_coll,max rounded to FP32, one product), the 24-bit uniform is within
-//    2^-25 of the 52-bit one, and the sum rounds by 2^-24 S; S within twice
+//    2^-25 of the 32-bit one, and the sum rounds by 2^-24 S; S within twice
 //    that bound of an integer is flagged;
 //  - accept: the 24-bit uniform times g_max is within 2^-25 g_max of the
 //    32-bit one's, and g carries the rounding of the FP32 velocities (a few
@@ -434,9 +434,12 @@ template <bool kVerify>
 __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint32_t o, int c, const float* v0,
                               const float* v1, const float* v2, uint32_t* bm, float4* wl, int& t, float* ov,
                               Counts32& cnt, const DLog& lg) {
-  const U4 u = philox_rk<true>(c0, cell, 0xFFFFFFFFu, o << 8, P.rk);
+  // the chi stream (c0, cell, slot, (o << 8) | 1): word 0 of slot 0 is the
+  // N_pairs uniform, word (s + 1) mod 4 of slot (s + 1) / 4 the chi of
+  // candidate s
+  U4 bchi = philox_rk<true>(c0, cell, 0u, (o << 8) | 1u, P.rk);
   const float base = (float)(((long long)c * (long long)(c - 1)) >> 1) * P.pmax;
-  const float S = base + unif24(u.x);
+  const float S = base + unif24(bchi.x);
   const int npairs = (int)floorf(S);
   const bool ftie = fabsf(S - rintf(S)) <= fmaf(base + S, 0x1p-22f, 0x1p-24f);
   if (ftie) ++cnt.ftie;
@@ -444,12 +447,11 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
   if (log_all || (ftie && lg.mode != PIC_DLOG_OFF))
     dlog_put(lg, c0, cell, o, -1, -1, -1, npairs, PIC_DLOG_NPAIRS | (ftie ? PIC_DLOG_FLOOR : 0));
   const float gmax = P.gmax;
-  // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon);
-  // chi is word s mod 4 of block (c0, cell, s / 4, (o << 8) | 1). The next
-  // candidate's block is formed while this one's velocities load: the draws
-  // depend on no velocity.
-  U4 bnext = philox_rk<true>(c0, cell, 0u, o << 8, P.rk);
-  U4 bchi{0u, 0u, 0u, 0u};
+  // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon). The
+  // next candidate's block is formed while this one's velocities load: the
+  // draws depend on no velocity.
+  U4 bnext{0u, 0u, 0u, 0u};
+  if (npairs > 0) bnext = philox_rk<true>(c0, cell, 0u, o << 8, P.rk);
   for (int s = 0; s < npairs; ++s) {
     const U4 b0 = bnext;
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
@@ -460,9 +462,10 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
     float vp[3], vq[3];
     vel_get((int)p, bm, wl, t, ov, v0, v1, v2, vp);
     vel_get((int)q, bm, wl, t, ov, v0, v1, v2, vq);
-    if ((s & 3) == 0) bchi = philox_rk<true>(c0, cell, (uint32_t)(s >> 2), (o << 8) | 1u, P.rk);
+    const int js = s + 1;
+    if ((js & 3) == 0) bchi = philox_rk<true>(c0, cell, (uint32_t)(js >> 2), (o << 8) | 1u, P.rk);
     if (s + 1 < npairs) bnext = philox_rk<true>(c0, cell, (uint32_t)(s + 1), o << 8, P.rk);
-    const uint32_t wchi = (s & 3) == 0 ? bchi.x : (s & 3) == 1 ? bchi.y : (s & 3) == 2 ? bchi.z : bchi.w;
+    const uint32_t wchi = (js & 3) == 0 ? bchi.x : (js & 3) == 1 ? bchi.y : (js & 3) == 2 ? bchi.z : bchi.w;
     const float dx = vp[0] - vq[0], dy = vp[1] - vq[1], dz = vp[2] - vq[2];
     const float g2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     // accept if U < sigma g / (sigma g)_max: hard spheres g / g_max, i.e.

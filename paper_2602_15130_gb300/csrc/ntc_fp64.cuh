@@ -37,16 +37,17 @@ template <bool kVerify, class Rec>
 __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_t o, int c,
                             const double* v0, const double* v1, const double* v2, uint32_t* bm,
                             double* ov, LaneCounts& cnt, Rec& rec, const DLog lg = DLog{nullptr, nullptr, 0, 0}) {
-  const U4 u = philox(c0, cell, 0xFFFFFFFFu, o << 8, P.key0, P.key1);
+  // the chi stream (c0, cell, slot, (o << 8) | 1): word 0 of slot 0 is the
+  // N_pairs uniform, word (s + 1) mod 4 of slot (s + 1) / 4 the chi of
+  // candidate s
+  U4 bchi = philox(c0, cell, 0u, (o << 8) | 1u, P.key0, P.key1);
+  long long chi_group = 0;
   const double base = __dmul_rn(__dmul_rn((double)((long long)c * (long long)(c - 1)), P.pmax), 0.5);
-  const long long npairs = (long long)floor(__dadd_rn(base, unif52(u.x, u.y)));
+  const long long npairs = (long long)floor(__dadd_rn(base, unif32(bchi.x)));
   const bool log_all = kVerify && lg.mode == PIC_DLOG_ALL;
   if (log_all) dlog_put(lg, c0, cell, o, -1, -1, -1, (int)npairs, PIC_DLOG_NPAIRS);
   // candidate s: block (c0, cell, s, o << 8) = (p, q, accept, epsilon);
-  // chi is word s mod 4 of block (c0, cell, s / 4, (o << 8) | 1), formed
-  // once per group of four candidates when one of them is accepted
-  U4 bchi{0u, 0u, 0u, 0u};
-  long long chi_group = -1;
+  // its chi block is formed when an accepted candidate needs it
   for (long long s = 0; s < npairs; ++s) {
     const U4 b0 = philox(c0, cell, (uint32_t)s, o << 8, P.key0, P.key1);
     const uint32_t p = draw_index(b0.x, (uint32_t)c);
@@ -71,11 +72,12 @@ __device__ void ntc_outcome(const Params& P, uint32_t c0, uint32_t cell, uint32_
     if (log_all || (tie && lg.mode != PIC_DLOG_OFF))
       dlog_put(lg, c0, cell, o, (int)s, (int)p, (int)q, U < ratio ? 1 : 0, tie ? PIC_DLOG_TIE : 0);
     if (U < ratio) {
-      if ((s >> 2) != chi_group) {
-        chi_group = s >> 2;
+      const long long js = s + 1;
+      if ((js >> 2) != chi_group) {
+        chi_group = js >> 2;
         bchi = philox(c0, cell, (uint32_t)chi_group, (o << 8) | 1u, P.key0, P.key1);
       }
-      const uint32_t wchi = (s & 3) == 0 ? bchi.x : (s & 3) == 1 ? bchi.y : (s & 3) == 2 ? bchi.z : bchi.w;
+      const uint32_t wchi = (js & 3) == 0 ? bchi.x : (js & 3) == 1 ? bchi.y : (js & 3) == 2 ? bchi.z : bchi.w;
       if (kVerify && (P.verify & PIC_VERIFY_ERROR2)) {
         // injected Error 2: swap with probability 1/2 (coin = chi draw)
         const bool swap = unif32(wchi) < 0.5;
