@@ -405,14 +405,19 @@ def run_gpu(args, rank: int, world: int, form: str, with_e2e: bool = True) -> di
         per_launch_s = kt["dsmc"]["ms"] / nl / 1000.0
         achieved = cand * OPS_PER_CANDIDATE / per_launch_s / 1e12
         peak = alu["imad"] / 1e12
-        blocks = p["n"] ** 3 * p["K"] + (st["n_cand"] * 1.25 + 0.0) / nl
+        # Philox blocks per launch: an outcome with N candidates takes
+        # N + floor(N / 4) + 1 (the chi stream's first block carries the
+        # N_pairs uniform), so the totals bound them between outcomes +
+        # candidates and outcomes + 1.25 candidates
+        outcomes = p["n"] ** 3 * p["K"]
+        blocks = (outcomes + cand, outcomes + 1.25 * cand)
         traffic, how = traffic_per_launch(form, "dsmc", npart)
         roof = {"bound": "alu", "kernel": "dsmc", "achieved": achieved, "peak": peak, "unit": "Tops/s (INT32)",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": how,
                 "ops_per_candidate": OPS_PER_CANDIDATE, "candidates_per_launch": cand,
                 "peak_source": "measured in this run: INT32 multiply-add issue rate of a full-grid kernel "
                                "(pic_measure_alu_peaks); 64 lanes x SMs x clock gives the same",
-                "philox_block_frac": blocks / per_launch_s / alu["philox_blocks"],
+                "philox_block_frac_range": [b / per_launch_s / alu["philox_blocks"] for b in blocks],
                 "ms_per_launch": row["ms_per_launch"]}
     else:
         b = BYTES_PER_UNIT[form]["method"].get(dom) or BYTES_PER_UNIT[form]["impl"].get(dom, 0.0)
