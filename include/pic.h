@@ -291,7 +291,12 @@ pic_status pic_sample_mms(pic_ctx* ctx, double t0);
 pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
 
 /* One K-averaged collision call (Eq. avg_outcome, Algorithm 1) on the
- * current state: counter word 2 step + phase (phase 0 or 1). Writes
+ * current state: counter word 2 step + phase (phase 0 or 1). The draws of
+ * cell k, outcome o come from Philox4x32-10 with counter (2 step + phase,
+ * k, slot, (o << 8) | b): the words of stream b = 1 in slot order are the
+ * N_pairs uniform, then one chi per candidate (candidate s: word (s + 1)
+ * mod 4 of slot (s + 1) / 4); candidate s takes stream b = 0 at slot s,
+ * (p, q, accept, epsilon). Writes
  * <Delta v_p>_coll to dv and the analytic <Delta v_p^M>_coll to dvM (Eq.
  * vel_change_1c for hard spheres with the Gaussian f_v, Eqs. vel_change_3
  * and fn for the odd-power cross section, f_v at the context's current
