@@ -307,14 +307,24 @@ pic_status pic_collide_avg(pic_ctx* ctx, int32_t phase, double* dv, double* dvM)
 /* Error norms of Sec. 4.3 at the current time into *out (host). */
 pic_status pic_mms_error(pic_ctx* ctx, pic_errors* out);
 
-/* Copy the particle state out: x, v [N_p][3], pid indexed, host or device. */
+/* Copy the particle state out: x, v [N_p][3], pid indexed, host or device.
+ * Pinned host and device arrays of the context's GPU are written in place
+ * by the kernels (other memory through a staging copy). */
 pic_status pic_get_state(pic_ctx* ctx, double* x, double* v);
 
 /* Replace the particle state (x in [0,1)^3, v; [N_p][3], pid indexed, host
  * or device), set the time to t0 + step dt, re-sort and re-solve the field
  * (the CG starts from the potential the context holds). v^M of a particle
  * depends only on its pid and the distribution, so a context that already
- * holds a state keeps those values rather than deriving them again. */
+ * holds a state keeps those values rather than deriving them again.
+ * Pinned host and device arrays of the context's GPU are read in place.
+ * Memory: in the precision form, the first such load (or pic_sample_mms)
+ * allocates per-cell bins of the loaded records, ncell x (four times the
+ * mean particles per cell, rounded up to 32) x 48 bytes (about four times
+ * the particle state), when they take at most a quarter of the free device
+ * memory; they stay with the context (released by pic_destroy). Without
+ * them, or when a cell holds more particles than its bin, the load sorts
+ * the same state by a scatter and a random gather. */
 pic_status pic_set_state(pic_ctx* ctx, const double* x, const double* v, double t0,
                          int64_t step);
 
