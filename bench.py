@@ -469,7 +469,7 @@ def run_batched(args, rank: int, world: int) -> dict | None:
     """256 uneven replicates advanced together (pic_create_batch)."""
     import torch
 
-    from paper_2602_15130_gb300 import Batch
+    from paper_2602_15130_gb300 import Batch, measure_alu_peaks
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -497,12 +497,27 @@ def run_batched(args, rank: int, world: int) -> dict | None:
         b.step(1)
         kt = b.kernel_times()
         b.set_profiling(False)
+        cand_prof = b.stats()["n_cand"] - st["n_cand"]
         errs = b.mms_error()
         iters = b.cg_iters()
         b.close()
+        alu = measure_alu_peaks(stream) if rank == 0 else None
     if rank != 0:
         return None
     ns = sorted({p["n"] for p in cfgs})
+    # the dominant phase, collisions, against the INT32 issue rate measured in
+    # this run: the profiled step's candidate pairs at OPS_PER_CANDIDATE
+    # operations each over its collision launches' time (the per-phase pass
+    # runs the collision phase as launches of its own)
+    dsmc_s = kt["dsmc"]["ms"] / 1000.0
+    achieved = cand_prof * OPS_PER_CANDIDATE / dsmc_s / 1e12 if dsmc_s > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "dsmc (kb_dsmc, the profiled step's collision launches)",
+            "achieved": achieved, "peak": alu["imad"] / 1e12, "unit": "Tops/s (INT32)",
+            "frac": achieved / (alu["imad"] / 1e12), "traffic": None,
+            "traffic_source": "not captured for the batched collision kernel",
+            "ops_per_candidate": OPS_PER_CANDIDATE, "candidates": cand_prof,
+            "peak_source": "measured in this run (pic_measure_alu_peaks)",
+            "ms": kt["dsmc"]["ms"], "launches": kt["dsmc"]["launches"]}
     return {
         "metric": METRIC, "value": aggregate_value(npart, args.steps, world, ms), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 4), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -517,6 +532,7 @@ def run_batched(args, rank: int, world: int) -> dict | None:
         "launches_per_step": int(st["kernel_launches"]) / max(1, args.steps),
         "tuned_block": int(st["tuned_block"]), "tuned_tile": int(st["tuned_tile"]),
         "kernel_ms_one_profiled_step": {k: round(v["ms"], 3) for k, v in kt.items()},
+        "roofline": roof,
         "stats": {"n_coll": st["n_coll"], "n_cand": st["n_cand"], "n_near_ties": st["n_near_ties"],
                   "cg_iters_max": st["cg_iters_max"], "cg_iters_median": sorted(iters)[len(iters) // 2]},
         "mms_error_eps2_x_median": float(sorted(e[0] for e in errs)[len(errs) // 2]),
