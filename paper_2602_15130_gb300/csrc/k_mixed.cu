@@ -354,6 +354,7 @@ struct Dsmc32Args {
   int64_t ngroups;
   unsigned long long* counters;
   unsigned long long* queue;  // next cell group to take (zero at launch)
+  int chunk;                  // cell groups a warp takes from the queue at a time
   int* flags;
   float vh[3];             // PIC_DIST_PAPER: f_v scales at the call's time
   DLog lg;                 // decision log (mode 0: off)
@@ -528,9 +529,10 @@ __device__ void ntc_outcome_f(const ParamsF& P, uint32_t c0, uint32_t cell, uint
 }
 
 constexpr int kDsmcThreads = 128;
-// cell groups a warp takes from the launch's queue at a time: a cell's work
-// varies with its particle count, and a static split left the SMs idle
-// through the last warps' tails
+// cell groups a warp takes from the launch's queue at a time, at most: a
+// cell's work varies with its particle count, and a static split left the
+// SMs idle through the last warps' tails. Launches with few groups per
+// warp take fewer at a time, so that every resident warp gets work.
 constexpr int kDsmcChunk = 8;
 
 // shared memory of one warp, in 32-bit words: bitmaps, lists, list lengths
@@ -563,11 +565,11 @@ __global__ void __launch_bounds__(kDsmcThreads, 6) k_dsmc32(Dsmc32Args a) {
   const float vs = P.vsig, ivs = P.inv_vsig, pref = P.src_pref;
 
   int64_t gbase = 0;
-  int gk = kDsmcChunk;
+  int gk = a.chunk;
   for (;;) {
-    if (gk == kDsmcChunk) {
+    if (gk == a.chunk) {
       unsigned long long q = 0;
-      if (lane == 0) q = atomicAdd(a.queue, (unsigned long long)kDsmcChunk);
+      if (lane == 0) q = atomicAdd(a.queue, (unsigned long long)a.chunk);
       gbase = (int64_t)__shfl_sync(0xffffffffu, q, 0);
       gk = 0;
     }
@@ -1823,6 +1825,13 @@ cudaError_t launch_dsmc32(pic_ctx* c, uint32_t c0, bool separate, double t_src) 
   a.Kc = c->dsmc_Kc;
   a.nchunks = (c->P.K + c->dsmc_Kc - 1) / c->dsmc_Kc;
   a.ngroups = c->dsmc_groups;
+  {
+    // groups per take: kDsmcChunk while every resident warp gets at least
+    // four takes, fewer (down to one) on launches with few groups per warp
+    const int64_t warps = (int64_t)c->dsmc_grid * (kDsmcThreads / 32);
+    const int64_t ch = a.ngroups / (4 * warps);
+    a.chunk = (int)(ch < 1 ? 1 : (ch > kDsmcChunk ? kDsmcChunk : ch));
+  }
   a.counters = c->counters;
   a.queue = c->dsmc_queue;
   a.flags = c->flags;
