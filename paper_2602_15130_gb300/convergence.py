@@ -97,12 +97,24 @@ def run_one(p: dict, precision: str) -> dict:
     if precision == "mixed":
         p = workloads.mixed(p)
     t0 = time.perf_counter()
-    sim = Pic(p)
-    sim.sample_mms(0.0)
-    sim.set_profiling(True)
-    # a diverging run (velocities past g_max run away; see the refine study)
-    # ends in a non-finite field: record it instead of stopping the study
-    status = sim.step(int(p["steps"]), allow=(_lib.PIC_ENOCONV,))
+    # a cell that outgrows max_ppc has its collisions skipped and the steps
+    # return PIC_ECAPACITY: the level runs again from the start with twice
+    # the capacity (which changes no result, only which cells fit)
+    for attempt in range(4):
+        sim = Pic(p)
+        sim.sample_mms(0.0)
+        sim.set_profiling(True)
+        try:
+            # a diverging run (velocities past g_max run away; see the refine
+            # study) ends in a non-finite field: record it instead of
+            # stopping the study
+            status = sim.step(int(p["steps"]), allow=(_lib.PIC_ENOCONV,))
+            break
+        except _lib.PicError as e:
+            if e.status != _lib.PIC_ECAPACITY or attempt == 3:
+                raise
+            sim.close()
+            p = dict(p, max_ppc=2 * int(p["max_ppc"]))
     kt = sim.kernel_times()
     err = sim.mms_error()
     st = sim.stats()
@@ -110,7 +122,7 @@ def run_one(p: dict, precision: str) -> dict:
            "steps": p["steps"], "eps2": err["eps2"], "epsinf": err["epsinf"], "n_coll": st["n_coll"],
            "n_cand": st["n_cand"], "cg_iters_max": st["cg_iters_max"],
            "step_kernel_ms": {k: round(v["ms"], 3) for k, v in kt.items() if v["launches"]},
-           "n_gmax_exceed": st["n_gmax_exceed"], "status": _lib.STATUS[status]}
+           "n_gmax_exceed": st["n_gmax_exceed"], "status": _lib.STATUS[status], "max_ppc": int(p["max_ppc"])}
     if p.get("verify", 0) & ANG:
         out["angles"] = sim.angle_stats()
     out["seconds"] = time.perf_counter() - t0

@@ -87,3 +87,53 @@ def test_batched_study_replicates_match_the_committed_list():
         assert p["n"] in (8, 16, 32, 64) and 8 <= ppc <= 64 and p["n_particles"] == ppc * p["n"] ** 3
         assert 4 <= p["K"] <= 64 and p["seed"] == 1000 + r
     assert len({p["n"] for p in reps}) == 4
+
+
+def test_a_level_that_outgrows_max_ppc_runs_again_with_twice_the_capacity(monkeypatch):
+    """run_one: a cell over max_ppc makes the steps return PIC_ECAPACITY;
+    the level starts over with max_ppc doubled, and the record names the
+    capacity it ran with. Other errors still stop the study."""
+    from paper_2602_15130_gb300 import _lib
+
+    made = []
+
+    class FakePic:
+        def __init__(self, p):
+            self.p = p
+            made.append(p["max_ppc"])
+
+        def sample_mms(self, t0):
+            pass
+
+        def set_profiling(self, on):
+            pass
+
+        def step(self, n, allow=()):
+            if self.p["max_ppc"] < 1000:
+                raise _lib.PicError(_lib.PIC_ECAPACITY, "pic_step")
+            return _lib.PIC_OK
+
+        def kernel_times(self):
+            return {"dsmc": {"ms": 1.0, "launches": 2}}
+
+        def mms_error(self):
+            e = {k: 1.0 for k in ("x", "y", "z", "u", "v", "w", "phi")}
+            return {"eps2": e, "epsinf": e}
+
+        def stats(self):
+            return {"n_coll": 0, "n_cand": 0, "cg_iters_max": 1, "n_gmax_exceed": 0}
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(C, "Pic", FakePic)
+    rec = C.run_one(dict(W.paper_table1_level(1), max_ppc=384), "mixed")
+    assert made == [384, 768, 1536] and rec["max_ppc"] == 1536 and rec["status"] == "PIC_OK"
+
+    class Failing(FakePic):
+        def step(self, n, allow=()):
+            raise _lib.PicError(_lib.PIC_ETIMEOUT, "pic_step")
+
+    monkeypatch.setattr(C, "Pic", Failing)
+    with pytest.raises(_lib.PicError):
+        C.run_one(W.paper_table1_level(1), "mixed")
