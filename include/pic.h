@@ -321,8 +321,9 @@ pic_status pic_get_state(pic_ctx* ctx, double* x, double* v);
  * Memory: in the precision form, the first such load (or pic_sample_mms)
  * allocates per-cell bins of the loaded records, ncell x (four times the
  * mean particles per cell, rounded up to 32) x 48 bytes (about four times
- * the particle state), when they take at most a quarter of the free device
- * memory; they stay with the context (released by pic_destroy). Without
+ * the particle state), when they hold at most eight times the loaded
+ * records and take at most a quarter of the free device memory; they stay
+ * with the context (released by pic_destroy). Without
  * them, or when a cell holds more particles than its bin, the load sorts
  * the same state by a scatter and a random gather. */
 pic_status pic_set_state(pic_ctx* ctx, const double* x, const double* v, double t0,

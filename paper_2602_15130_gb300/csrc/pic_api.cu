@@ -423,9 +423,11 @@ pic_status check_pending(pic_ctx* c) {
 // keys_done: the state load wrote the keys, ranks and counts itself
 // Bins for a state load's records, by cell: a capacity of four times the
 // mean particles per cell (a multiple of 32), if that is at most kBigCell
-// (larger cells take the block sort, which reads through perm) and the
-// bins take at most a quarter of the free device memory. Tried once per
-// context; without bins the loads take the scatter and a random gather.
+// (larger cells take the block sort, which reads through perm), the bins
+// hold at most eight times the records (a sparse state on a fine mesh
+// would mostly bin nothing) and take at most a quarter of the free device
+// memory. Tried once per context; without bins the loads take the scatter
+// and a random gather.
 void ensure_bins(pic_ctx* c) {
   if (c->bin_tried) return;
   c->bin_tried = true;
@@ -434,6 +436,7 @@ void ensure_bins(pic_ctx* c) {
   int64_t cap = (4 * mean + 31) / 32 * 32;
   if (cap > kBigCell) return;
   const size_t bytes = (size_t)c->P.ncell * (size_t)cap * 48;
+  if (bytes > (size_t)8 * 48 * (size_t)c->P.np) return;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
     cudaGetLastError();
